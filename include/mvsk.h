@@ -1,0 +1,198 @@
+/*
+ * mvsk.h -- C ABI of the GB300 (sm_103a) YAND-MVSK sample-oracle library.
+ *
+ * YAND-MVSK (arXiv 2604.25378) minimises the unrestricted sample-moment MVSK
+ * objective  f(x) = -c1 mu^T x + c2 m2(x) - c3 m3(x) + c4 m4(x)  over the
+ * simplex slice Delta(tau) = {x : 1^T x = 1, x_i >= tau}  (Sec. 2, Eq. mvsk),
+ * working only with the centred return matrix A = R - 1 mu^T (Sec. 3.1).
+ *
+ * Conventions for every entry point:
+ *  - All matrices are row-major.  Every vector or matrix argument may be a
+ *    host pointer or a device pointer; the library detects which
+ *    (cudaPointerGetAttributes) and copies as needed.  The caller keeps
+ *    ownership of every pointer it passes; the library never frees them and
+ *    never keeps them after the call returns.
+ *  - All inputs and outputs are IEEE binary64, whatever the storage precision
+ *    of A inside the context.
+ *  - Work is issued on the context's stream (mvsk_set_stream; default: the
+ *    legacy default stream) and every call returns after its results are in
+ *    the caller's buffers.
+ *  - No C++ exception crosses the ABI and nothing aborts the process; a
+ *    failing call returns a non-zero mvsk_status and mvsk_last_error() gives
+ *    a message.  Outputs are left untouched on MVSK_EINVAL, MVSK_ESTATE,
+ *    MVSK_ENOMEM and MVSK_ECUDA unless stated otherwise.
+ *  - A context may be used by one host thread at a time.
+ *  - Device kernels never trap: every wait inside a kernel is bounded and a
+ *    wait that runs out sets an error word that the call reports as
+ *    MVSK_ECUDA.
+ */
+#ifndef MVSK_H
+#define MVSK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mvsk_ctx mvsk_ctx; /* opaque; owns all of its device memory */
+
+typedef enum {
+  MVSK_OK = 0,
+  MVSK_EINVAL = 1,         /* bad argument: sizes, NaN/Inf data, lambda < 0, w0 outside Delta(tau) */
+  MVSK_ENOMEM = 2,         /* device or pinned-host allocation failed */
+  MVSK_ECUDA = 3,          /* CUDA runtime error or a bounded in-kernel wait ran out */
+  MVSK_ENOTCONVERGED = 4,  /* iteration budget spent before the tolerance; best iterate returned */
+  MVSK_ETIMEOUT = 5,       /* max_elapsed reached; best iterate returned */
+  MVSK_ESTATE = 6,         /* call out of order (e.g. solve before set_prefs) */
+  MVSK_ENUMERIC = 7        /* non-finite value met during the solve */
+} mvsk_status;
+
+typedef enum { MVSK_DIRECT = 0, MVSK_PCG = 1 } mvsk_config;
+
+/* Storage precision of A (mvsk_create flags). */
+#define MVSK_PREC_FP64 0u        /* A in FP64 only: every pass in FP64 */
+#define MVSK_PREC_MIXED_BF16 1u  /* plus a BF16 copy of A for the direction passes (FP32 accumulate) */
+#define MVSK_PREC_MIXED_FP32 2u  /* plus an FP32 copy of A for the direction passes */
+
+/* Per-solve report. */
+typedef struct {
+  int32_t iters;          /* outer YAND iterations, all phases */
+  int32_t restarts;       /* stall-recovery restarts taken (PCG) */
+  int32_t passes;         /* streaming passes over A issued */
+  int32_t hvps;           /* Hessian-vector columns applied */
+  int32_t third_calls;    /* third-order back-projections */
+  int32_t krylov_iters;   /* PCG iterations summed over columns */
+  int32_t free_count;     /* coordinates above tau at the returned point */
+  int32_t evals;          /* inner solves spent by the target calibration (1 without target) */
+  double f;               /* objective at the returned point */
+  double kkt_residual;    /* ||x - Pi_{Delta(tau)}(x - grad f)||_2 (projected-simplex KKT) */
+  double kkt0;            /* the same at x0 = 1/n */
+  double kkt_rel;         /* kkt_residual / kkt0: the quantity `tol` bounds */
+  double c[4];            /* coefficients used (c1 after target calibration) */
+  double achieved_mean;   /* mu^T x */
+  double seconds;         /* wall time of the call */
+  int32_t status;         /* mvsk_status of the solve */
+  int32_t reserved;
+} mvsk_info;
+
+/*
+ * mvsk_create -- build a context from RAW returns R (Sec. 2; Alg. 1 set-up).
+ *   R: T x n row-major with leading dimension ld >= n (elements); host or
+ *      device.  The library computes mu = T^-1 R^T 1 and A = R - 1 mu^T in
+ *      FP64 on the GPU and keeps its own padded copies (FP64 master, plus
+ *      BF16 or FP32 per flags).  1 <= n <= 6144, T >= 1.
+ *   flags: one MVSK_PREC_* value.
+ *   *out receives the context.  Errors: EINVAL (sizes, ld < n, non-finite R;
+ *   no context is created), ENOMEM, ECUDA.
+ */
+mvsk_status mvsk_create(const double* R, int64_t T, int64_t n, int64_t ld, uint32_t flags,
+                        mvsk_ctx** out);
+
+/* mvsk_set_stream -- issue all later work on `cuda_stream` (a cudaStream_t). */
+mvsk_status mvsk_set_stream(mvsk_ctx* ctx, void* cuda_stream);
+
+/*
+ * mvsk_set_prefs -- preferences lambda[4] >= 0 (Sec. 2: c_i >= 0) and an
+ *   optional return target (Sec. 6: calibrate the mean coefficient).
+ *   pref_scaling option 0 (raw): c = lambda; 1 (standardised, default):
+ *   c_p = lambda_p / s^p with s^2 = m2(1/n).  target = NaN: c1 from lambda1;
+ *   otherwise mvsk_solve finds c1 >= 0 with mu^T x*(c1) = target.
+ *   Errors: EINVAL for negative or non-finite lambda.
+ */
+mvsk_status mvsk_set_prefs(mvsk_ctx* ctx, const double lambda[4], double target);
+
+/*
+ * mvsk_set_option -- numeric options (Table yand-core-parameters and the
+ *   readings): "tau" (1e-8), "eta" (0.05), "max_iter" (300, direct),
+ *   "pcg_max_iter" (40), "restart_iter" (120), "restart_eta1" (0.045),
+ *   "restart_eta2" (0.02), "max_elapsed" (60 s), "krylov_tol" (1e-3),
+ *   "krylov_maxit" (15), "reg" (NaN: 0 direct / 1e-4 PCG), "probes" (8),
+ *   "probe_seed" (24301), "pref_scaling" (1), "release_ratio" (0.5),
+ *   "eps_act" (1e-15), "oracle_prec" (0: FP64 A, 1: BF16 A, 2: FP32 A for
+ *   the mvsk_oracle_* exports), "cal_rel_tol" (1e-9).
+ *   Errors: EINVAL for an unknown key or an out-of-range value.
+ */
+mvsk_status mvsk_set_option(mvsk_ctx* ctx, const char* key, double value);
+
+/*
+ * mvsk_solve -- YAND-MVSK, Alg. 1 (oracle block, affine-normal block, exact
+ *   quartic step, boundary block with the projected active-set step of
+ *   App. C.3 and face continuation), configuration `cfg` (Table
+ *   yand-core-parameters: direct reduced solve, or PCG with stall-recovery
+ *   restarts).  Stops when kkt_rel <= tol.
+ *   w0: start in Delta(tau) (n values) or NULL for 1/n.
+ *   w_out: n values, host or device; written with the best iterate on OK,
+ *   ENOTCONVERGED and ETIMEOUT.  info may be NULL.
+ *   Errors: ESTATE (no prefs), EINVAL (tol <= 0, w0 outside Delta(tau)),
+ *   ENUMERIC, ECUDA.
+ */
+mvsk_status mvsk_solve(mvsk_ctx* ctx, mvsk_config cfg, double tol, const double* w0,
+                       double* w_out, mvsk_info* info);
+
+/*
+ * mvsk_solve_batch -- B independent instances (lambda_b, target_b) on the same
+ *   A, solved together: every pass over A serves all live instances.
+ *   lambdas: B x 4; targets: B (NaN = none); W0: B x n or NULL; W_out: B x n;
+ *   infos: B entries or NULL.  Returns OK if every instance converged, else
+ *   the first non-OK instance status.
+ */
+mvsk_status mvsk_solve_batch(mvsk_ctx* ctx, mvsk_config cfg, int32_t B, const double* lambdas,
+                             const double* targets, double tol, const double* W0, double* W_out,
+                             mvsk_info* infos);
+
+/*
+ * mvsk_eval -- exact sample oracle at w (Prop. 1, Eqs. operator-f and
+ *   operator-grad): f(w), grad f(w) (n values, may be NULL) and the
+ *   projected-simplex KKT residual (may be NULL).  FP64 A.
+ */
+mvsk_status mvsk_eval(mvsk_ctx* ctx, const double* w, double* f, double* grad, double* kkt);
+
+/* Oracle exports (the same kernels as the solver, for parity checks). The
+ * copy of A they read is chosen by option "oracle_prec". */
+
+/* Eq. operator-hvp: out = grad^2 f(w) v = T^-1 A^T (psi''(Aw) o Av). */
+mvsk_status mvsk_oracle_hvp(mvsk_ctx* ctx, const double* w, const double* v, double* out);
+
+/* Eq. operator-third: out = T3(w; u, v) = T^-1 A^T (psi'''(Aw) o Au o Av). */
+mvsk_status mvsk_oracle_third(mvsk_ctx* ctx, const double* w, const double* u, const double* v,
+                              double* out);
+
+/* Prop. 2: G = T^-1 A^T Diag(psi''(Aw)) A, n x n row-major (ld = n). */
+mvsk_status mvsk_oracle_gram(mvsk_ctx* ctx, const double* w, double* G);
+
+/*
+ * Prop. quartic exact line search: coef[5] = A0..A4 of f(w + alpha d) from
+ * the power sums s_rs, and *alpha_max = alpha_max(w, d; tau) (Lemma cap;
+ * +inf when no d_i < 0).  FP64 A.
+ */
+mvsk_status mvsk_oracle_ls(mvsk_ctx* ctx, const double* w, const double* d, double coef[5],
+                           double* alpha_max);
+
+/*
+ * YAND direction at w (Sec. 3.2; the formulas of Sec. 3.4) on the face that
+ * the boundary block would use, for configuration cfg; `iteration` seeds the
+ * Hutchinson probes of the PCG configuration.  d_out: n values, zero on the
+ * held face, 1^T d = 0.
+ */
+mvsk_status mvsk_oracle_direction(mvsk_ctx* ctx, mvsk_config cfg, const double* w,
+                                  int32_t iteration, double* d_out);
+
+/* Euclidean projection onto Delta(tau) (App. C.3 projected trial). */
+mvsk_status mvsk_project_slice(mvsk_ctx* ctx, const double* v, double tau, double* out);
+
+/* Exact minimiser of A0 + A1 a + ... + A4 a^4 on [0, amax] by the device
+ * routine the solver uses (candidates: 0, amax, real roots of the cubic). */
+mvsk_status mvsk_quartic_argmin(mvsk_ctx* ctx, const double coef[5], double amax, double* alpha);
+
+/* Thread-local message describing the last failure of any call. */
+const char* mvsk_last_error(const mvsk_ctx* ctx);
+
+/* Release every resource of the context.  NULL-safe. */
+void mvsk_destroy(mvsk_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MVSK_H */

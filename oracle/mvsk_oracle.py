@@ -111,7 +111,7 @@ def scale_preferences(lam, A, mode="raw"):
     """Map preferences lambda to coefficients c (Sec. 6 normalisation).
 
     raw: c = lambda.  standardised: with s = sqrt(m2(1/n)) of the equal-weight
-    portfolio, c_p = lambda_p / s^p for p = 1..4.
+    portfolio, c_p = lambda_p / s^p for p = 1..4 (raw when s = 0, e.g. T = 1).
     """
     lam = np.asarray(lam, dtype=np.float64)
     if mode == "raw":
@@ -119,6 +119,8 @@ def scale_preferences(lam, A, mode="raw"):
     n = A.shape[1]
     z = A @ np.full(n, 1.0 / n)
     s = math.sqrt(float(z @ z) / A.shape[0])
+    if not s > 0.0:
+        return lam.copy()
     return lam / np.array([s, s**2, s**3, s**4])
 
 

@@ -1,0 +1,234 @@
+"""GB300 (sm_103a) YAND-MVSK sample-oracle library: Python binding.
+
+Argument marshalling only.  Every step of the method runs in libmvsk's CUDA
+kernels behind the C ABI of include/mvsk.h; this module never computes any
+part of the method itself.  Arrays may be numpy float64 (host) or torch
+float64 tensors (host or CUDA); outputs follow the input kind of `R` or of
+the `out` argument.
+
+If libmvsk.so has not been built, `load()` raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+__all__ = ["load", "MVSK", "MvskError", "DIRECT", "PCG", "PREC", "lib_path"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+lib_path = os.path.join(_HERE, "lib", "libmvsk.so")
+
+DIRECT, PCG = 0, 1
+PREC = {"fp64": 0, "bf16": 1, "fp32": 2}
+STATUS = {0: "ok", 1: "einval", 2: "enomem", 3: "ecuda", 4: "not_converged", 5: "timeout", 6: "estate",
+          7: "enumeric"}
+
+_lib = None
+
+
+class MvskError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("hvps", ctypes.c_int32), ("third_calls", ctypes.c_int32), ("krylov_iters", ctypes.c_int32),
+                ("free_count", ctypes.c_int32), ("evals", ctypes.c_int32), ("f", ctypes.c_double),
+                ("kkt_residual", ctypes.c_double), ("kkt0", ctypes.c_double), ("kkt_rel", ctypes.c_double),
+                ("c", ctypes.c_double * 4), ("achieved_mean", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("c", "reserved")}
+        d["c"] = list(self.c)
+        d["status"] = STATUS.get(self.status, self.status)
+        return d
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "mvsk_create": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32,
+                                   ctypes.POINTER(_P)]),
+    "mvsk_set_stream": (ctypes.c_int, [_P, _P]),
+    "mvsk_set_prefs": (ctypes.c_int, [_P, _P, ctypes.c_double]),
+    "mvsk_set_option": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_double]),
+    "mvsk_solve": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, _P, _P, _P]),
+    "mvsk_solve_batch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int32, _P, _P, ctypes.c_double, _P, _P, _P]),
+    "mvsk_eval": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "mvsk_oracle_hvp": (ctypes.c_int, [_P, _P, _P, _P]),
+    "mvsk_oracle_third": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "mvsk_oracle_gram": (ctypes.c_int, [_P, _P, _P]),
+    "mvsk_oracle_ls": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "mvsk_oracle_direction": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int32, _P]),
+    "mvsk_project_slice": (ctypes.c_int, [_P, _P, ctypes.c_double, _P]),
+    "mvsk_quartic_argmin": (ctypes.c_int, [_P, _P, ctypes.c_double, _P]),
+    "mvsk_last_error": (ctypes.c_char_p, [_P]),
+    "mvsk_destroy": (None, [_P]),
+}
+
+
+def load(path: str | None = None):
+    """Load libmvsk.so (raises if it is missing: the library has no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or lib_path
+    if not os.path.exists(p):
+        raise ImportError(f"libmvsk.so not built at {p}; run paper_2604_25378_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """(pointer, keep-alive) of a float64 array: numpy (host) or torch (host/CUDA)."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous() or str(a.dtype) != "torch.float64":
+            raise TypeError("torch tensors must be contiguous float64")
+        return ctypes.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    return arr.ctypes.data_as(ctypes.c_void_p), arr
+
+
+def _like(x, n_or_shape):
+    shape = (n_or_shape,) if isinstance(n_or_shape, int) else tuple(n_or_shape)
+    if hasattr(x, "data_ptr"):
+        import torch
+        return torch.empty(shape, dtype=torch.float64, device=x.device)
+    return np.empty(shape, dtype=np.float64)
+
+
+class MVSK:
+    """One context: a centred copy of the returns on the GPU plus solver state."""
+
+    def __init__(self, R, precision: str = "fp64"):
+        self._lib = load()
+        T, n = R.shape
+        self.T, self.n = int(T), int(n)
+        self.precision = precision
+        self._ref = R
+        p, keep = _ptr(R)
+        h = ctypes.c_void_p()
+        self._check(self._lib.mvsk_create(p, T, n, n, PREC[precision], ctypes.byref(h)), None)
+        self._h = h
+        del keep
+
+    def _check(self, st, h=None):
+        if st != 0:
+            msg = self._lib.mvsk_last_error(h if h is not None else getattr(self, "_h", None))
+            raise MvskError(st, (msg or b"").decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mvsk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_handle: int):
+        self._check(self._lib.mvsk_set_stream(self._h, ctypes.c_void_p(stream_handle)))
+
+    def set_prefs(self, lam, target=math.nan):
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        self._check(self._lib.mvsk_set_prefs(self._h, lam.ctypes.data_as(ctypes.c_void_p), float(target)))
+
+    def set_option(self, key: str, value: float):
+        self._check(self._lib.mvsk_set_option(self._h, key.encode(), float(value)))
+
+    def solve(self, config: int = PCG, tol: float = 1e-8, w0=None, out=None):
+        """Returns (w, info dict); raises MvskError on hard failures.  A solve
+        that ends on its iteration budget returns with info['status'] set."""
+        out = _like(self._ref, self.n) if out is None else out
+        po, ko = _ptr(out)
+        pw, kw = (None, None) if w0 is None else _ptr(w0)
+        info = Info()
+        st = self._lib.mvsk_solve(self._h, int(config), float(tol), pw, po, ctypes.byref(info))
+        if st not in (0, 4, 5):
+            self._check(st)
+        return (ko if ko is not out else out), info.as_dict()
+
+    def solve_batch(self, lambdas, targets=None, config: int = PCG, tol: float = 1e-8, W0=None, out=None):
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64).reshape(-1, 4)
+        B = lam.shape[0]
+        tg = np.full(B, np.nan) if targets is None else np.ascontiguousarray(targets, dtype=np.float64)
+        out = _like(self._ref, (B, self.n)) if out is None else out
+        po, ko = _ptr(out)
+        pw, kw = (None, None) if W0 is None else _ptr(W0)
+        infos = (Info * B)()
+        st = self._lib.mvsk_solve_batch(self._h, int(config), B, lam.ctypes.data_as(ctypes.c_void_p),
+                                        tg.ctypes.data_as(ctypes.c_void_p), float(tol), pw, po, infos)
+        if st not in (0, 4, 5):
+            self._check(st)
+        return (ko if ko is not out else out), [i.as_dict() for i in infos]
+
+    def eval(self, w):
+        pw, kw = _ptr(w)
+        g = np.empty(self.n)
+        f = ctypes.c_double()
+        k = ctypes.c_double()
+        self._check(self._lib.mvsk_eval(self._h, pw, ctypes.byref(f), g.ctypes.data_as(ctypes.c_void_p),
+                                         ctypes.byref(k)))
+        return f.value, g, k.value
+
+    def hvp(self, w, v):
+        pw, kw = _ptr(w)
+        pv, kv = _ptr(v)
+        out = np.empty(self.n)
+        self._check(self._lib.mvsk_oracle_hvp(self._h, pw, pv, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def third(self, w, u, v):
+        pw, kw = _ptr(w)
+        pu, ku = _ptr(u)
+        pv, kv = _ptr(v)
+        out = np.empty(self.n)
+        self._check(self._lib.mvsk_oracle_third(self._h, pw, pu, pv, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def gram(self, w):
+        pw, kw = _ptr(w)
+        out = np.empty((self.n, self.n))
+        self._check(self._lib.mvsk_oracle_gram(self._h, pw, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def line_search(self, w, d):
+        pw, kw = _ptr(w)
+        pd, kd = _ptr(d)
+        coef = np.empty(5)
+        am = ctypes.c_double()
+        self._check(self._lib.mvsk_oracle_ls(self._h, pw, pd, coef.ctypes.data_as(ctypes.c_void_p),
+                                             ctypes.byref(am)))
+        return coef, am.value
+
+    def direction(self, w, config: int = PCG, iteration: int = 0):
+        pw, kw = _ptr(w)
+        out = np.empty(self.n)
+        self._check(self._lib.mvsk_oracle_direction(self._h, int(config), pw, int(iteration),
+                                                    out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def project_slice(self, v, tau=1e-8):
+        pv, kv = _ptr(v)
+        out = np.empty(self.n)
+        self._check(self._lib.mvsk_project_slice(self._h, pv, float(tau), out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def quartic_argmin(self, coef, amax):
+        coef = np.ascontiguousarray(coef, dtype=np.float64)
+        a = ctypes.c_double()
+        self._check(self._lib.mvsk_quartic_argmin(self._h, coef.ctypes.data_as(ctypes.c_void_p), float(amax),
+                                                  ctypes.byref(a)))
+        return a.value

@@ -1,0 +1,153 @@
+// Shared device helpers: bulk-TMA staging with mbarriers (bounded waits),
+// block reductions, psi derivatives.  sm_103a only.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mvsk {
+
+constexpr int kThreads = 512;           // threads per row-pass CTA
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxCols = 6144;          // largest n supported by the streaming passes
+constexpr int kPad = 64;                // leading dimension of A is n rounded up to 64 elements
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any in-kernel wait
+
+// Error bits written by kernels into the context's error word.
+enum : int { kErrWaitTimeout = 1, kErrDrainTimeout = 2, kErrNonFinite = 4 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// One contiguous global -> shared bulk copy completing on `bar` (16-byte
+// aligned addresses, size a multiple of 16 bytes).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of `bar`, giving up after kWaitNs.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum over blockDim.x threads (multiple of 32) in a fixed order.
+// `scratch` holds >= 32 doubles.  All threads receive the result.
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < nw ? scratch[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) scratch[32] = t;
+  }
+  __syncthreads();
+  return scratch[32];
+}
+
+__device__ __forceinline__ double block_min(double v, double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < nw ? scratch[lane] : INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmin(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (lane == 0) scratch[32] = t;
+  }
+  __syncthreads();
+  return scratch[32];
+}
+
+// Block-wide arg-max (value, index); ties take the smallest index.
+__device__ __forceinline__ void block_argmax(double& v, int& idx, double* sv, int* si) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  __syncthreads();
+  if (lane == 0) { sv[warp] = v; si[warp] = idx; }
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < nw ? sv[lane] : -INFINITY;
+    int ti = lane < nw ? si[lane] : 0x7fffffff;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, t, o);
+      int oi = __shfl_xor_sync(0xffffffffu, ti, o);
+      if (ov > t || (ov == t && oi < ti)) { t = ov; ti = oi; }
+    }
+    if (lane == 0) { sv[32] = t; si[32] = ti; }
+  }
+  __syncthreads();
+  v = sv[32];
+  idx = si[32];
+}
+
+// psi and its derivatives (Prop. 2, Eqs. operator-grad/hvp/third).
+struct Psi {
+  double c2, c3, c4;
+  __device__ __forceinline__ double f(double s) const { return s * s * (c2 - s * (c3 - c4 * s)); }
+  __device__ __forceinline__ double d1(double s) const { return s * (2.0 * c2 - s * (3.0 * c3 - 4.0 * c4 * s)); }
+  __device__ __forceinline__ double d2(double s) const { return 2.0 * c2 - s * (6.0 * c3 - 12.0 * c4 * s); }
+  __device__ __forceinline__ double d3(double s) const { return -6.0 * c3 + 24.0 * c4 * s; }
+};
+
+}  // namespace mvsk

@@ -1,0 +1,1040 @@
+// C ABI of libmvsk (see include/mvsk.h): context, centring, the YAND-MVSK
+// driver (Alg. 1) and the oracle exports.  Host code orchestrates; every
+// arithmetic step of the method runs in the kernels of this library.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "mvsk.h"
+#include "solver_kernels.cuh"
+
+using namespace mvsk;
+
+namespace {
+
+thread_local char g_err[512];
+
+struct Options {
+  double tau = 1e-8, eta = 0.05, max_elapsed = 60.0, krylov_tol = 1e-3, reg = NAN;
+  double restart_eta1 = 0.045, restart_eta2 = 0.02, release_ratio = 0.5, eps_act = 1e-15;
+  double descent_eps = 1e-10, stall_factor = 0.99, cal_rel_tol = 1e-9, cal_bracket_tol = 1e-12;
+  int max_iter = 300, pcg_max_iter = 40, restart_iter = 120, krylov_maxit = 15, probes = 8;
+  int stall_window = 10, pref_scaling = 1, oracle_prec = 0, arc_halvings = 40, cal_max_evals = 40, trace = 0;
+  unsigned long long probe_seed = 0x5EEDull;
+};
+
+}  // namespace
+
+struct mvsk_ctx {
+  long long T = 0;
+  int n = 0, ld = 0;
+  uint32_t flags = 0;
+  int dir_prec = P64;
+  cudaStream_t stream = nullptr;
+  int nsm = 0, grid = 0, rows_per_cta = 0;
+  double* A64 = nullptr;
+  void* Alo = nullptr;  // BF16 or FP32 copy
+  double* mu = nullptr;
+  // per-instance device state (single instance)
+  Inst in{};
+  double* sd = nullptr;
+  int* si = nullptr;
+  void* part = nullptr;     // column partials (FP64-sized)
+  double* spart = nullptr;  // scalar partials
+  double* fwd = nullptr;    // per-row scratch [4][T]
+  double* hd = nullptr;     // Gnu | diagG
+  double* vec_scratch = nullptr;  // host<->device staging for vector arguments
+  int* err = nullptr;
+  double* hpin = nullptr;   // pinned host staging
+  size_t hpin_bytes = 0;
+  int ncolmax = 0;
+  // preferences
+  bool prefs_set = false;
+  double lam[4] = {0, 0, 0, 0};
+  double target = NAN;
+  double c[4] = {0, 0, 0, 0};
+  double s_equal = NAN;  // sqrt(m2(1/n))
+  double mu_absmax = 0.0;
+  Options opt;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+mvsk_status fail(mvsk_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+#define CU(call)                                                                                \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) return fail(MVSK_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define TRY(expr)                  \
+  do {                             \
+    mvsk_status s_ = (expr);       \
+    if (s_ != MVSK_OK) return s_;  \
+  } while (0)
+
+mvsk_status dalloc(mvsk_ctx* c, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MVSK_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  c->allocs.push_back(*p);
+  e = cudaMemsetAsync(*p, 0, bytes < 16 ? 16 : bytes, c->stream);
+  if (e != cudaSuccess) return fail(MVSK_ECUDA, "cudaMemset: %s", cudaGetErrorString(e));
+  return MVSK_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy n doubles from a caller pointer (host or device) into device dst (ld padded with zeros).
+mvsk_status upload_vec(mvsk_ctx* c, double* dst, const double* src, int n) {
+  CU(cudaMemsetAsync(dst, 0, sizeof(double) * c->ld, c->stream));
+  CU(cudaMemcpyAsync(dst, src, sizeof(double) * n, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     c->stream));
+  return MVSK_OK;
+}
+
+mvsk_status download_vec(mvsk_ctx* c, double* dst, const double* src, size_t n) {
+  CU(cudaMemcpyAsync(dst, src, sizeof(double) * n, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     c->stream));
+  return MVSK_OK;
+}
+
+mvsk_status sync(mvsk_ctx* c) {
+  CU(cudaStreamSynchronize(c->stream));
+  int e = 0;
+  CU(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e != 0) {
+    cudaMemset(c->err, 0, sizeof(int));
+    return fail(MVSK_ECUDA, "in-kernel bounded wait ran out (error word %d)", e);
+  }
+  return MVSK_OK;
+}
+
+// ----------------------------------------------------------------- kernels
+__global__ void k_colmean(const double* R, long long T, int n, int ld, double* mu) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  // fixed-order two-level sum: chunks of 256 rows, then the chunk sums
+  double tot = 0.0;
+  for (long long t0 = 0; t0 < T; t0 += 256) {
+    double s = 0.0;
+    const long long t1 = t0 + 256 < T ? t0 + 256 : T;
+    for (long long t = t0; t < t1; ++t) s += R[(size_t)t * ld + j];
+    tot += s;
+  }
+  mu[j] = tot / (double)T;
+}
+
+template <typename TL>
+__global__ void k_centre(double* A, TL* lo, long long T, int n, int ld, const double* mu, int* bad) {
+  const size_t total = (size_t)T * ld;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(q % ld);
+    double v = 0.0;
+    if (j < n) {
+      v = A[q];
+      if (!isfinite(v)) *bad = 1;
+      v -= mu[j];
+    }
+    A[q] = v;
+    if (lo != nullptr) lo[q] = (TL)v;
+  }
+}
+template <>
+__global__ void k_centre<__nv_bfloat16>(double* A, __nv_bfloat16* lo, long long T, int n, int ld, const double* mu,
+                                        int* bad) {
+  const size_t total = (size_t)T * ld;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(q % ld);
+    double v = 0.0;
+    if (j < n) {
+      v = A[q];
+      if (!isfinite(v)) *bad = 1;
+      v -= mu[j];
+    }
+    A[q] = v;
+    lo[q] = __double2bfloat16(v);
+  }
+}
+
+__global__ void k_sumsq(const double* z, long long T, double* out) {
+  __shared__ double scr[80];
+  double s = 0.0;
+  for (long long t = threadIdx.x; t < T; t += blockDim.x) s += z[t] * z[t];
+  s = block_sum2(s, 0.0, scr).x;
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_project(const double* v, int n, double tau, double* out) {
+  __shared__ double scr[80];
+  const double th = slice_theta(v, nullptr, 0.0, n, tau, scr);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = tau + fmax(v[i] - tau - th, 0.0);
+}
+
+__global__ void k_quartic(const double* coef, double amax, double* out) {
+  if (threadIdx.x == 0) *out = quartic_argmin(coef, amax);
+}
+
+__global__ void k_alpha_max(const double* x, const double* d, int n, double tau, double* out) {
+  __shared__ double scr[80];
+  double am = INFINITY;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (d[i] < 0.0) am = fmin(am, (x[i] - tau) / (-d[i]));
+  am = block_min(am, scr);
+  if (threadIdx.x == 0) *out = am;
+}
+
+__global__ void k_ls_coef_only(Inst s, const double* spart, int G, const double* dir, double* out) {
+  __shared__ double scr[80];
+  __shared__ double ps[16];
+  __shared__ double coef[5];
+  // A0 from the power sums themselves (proof of Prop. quartic): -c1 mu^T x + c2 s20 - c3 s30 + c4 s40
+  reduce_spart(spart, G, 12, s.sd[SD_INVT], ps);
+  double mx = 0.0, md = 0.0;
+  for (int i = threadIdx.x; i < s.n; i += blockDim.x) {
+    mx += s.mu[i] * s.x[i];
+    md += s.mu[i] * dir[i];
+  }
+  const double2 r = block_sum2(mx, md, scr);
+  if (threadIdx.x == 0) {
+    const double c1 = s.sd[SD_C1], c2 = s.sd[SD_C2], c3 = s.sd[SD_C3], c4 = s.sd[SD_C4];
+    out[0] = -c1 * r.x + c2 * ps[0] - c3 * ps[1] + c4 * ps[2];
+    out[1] = -c1 * r.y + 2.0 * c2 * ps[3] - 3.0 * c3 * ps[4] + 4.0 * c4 * ps[5];
+    out[2] = c2 * ps[6] - 3.0 * c3 * ps[7] + 6.0 * c4 * ps[8];
+    out[3] = -c3 * ps[9] + 4.0 * c4 * ps[10];
+    out[4] = c4 * ps[11];
+  }
+  (void)coef;
+}
+
+__global__ void k_init_state(Inst s, double tol, double eta, int maxit, int pcg, int stallwin, int probes,
+                             unsigned long long seed, int kmaxit, int arcmax, const double* opts9) {
+  if (threadIdx.x != 0) return;
+  for (int q = 0; q < kSI; ++q) s.si[q] = 0;
+  for (int q = SD_HIST; q < kSD; ++q) s.sd[q] = 0.0;
+  s.sd[SD_TOL] = tol;
+  s.sd[SD_ETA] = eta;
+  s.sd[SD_BEST] = INFINITY;
+  s.sd[SD_TAU] = opts9[0];
+  s.sd[SD_EPSACT] = opts9[1];
+  s.sd[SD_RELRATIO] = opts9[2];
+  s.sd[SD_REG] = opts9[3];
+  s.sd[SD_KTOL] = opts9[4];
+  s.sd[SD_C1] = opts9[5];
+  s.sd[SD_C2] = opts9[6];
+  s.sd[SD_C3] = opts9[7];
+  s.sd[SD_C4] = opts9[8];
+  s.sd[SD_INVT] = opts9[9];
+  s.sd[SD_DESCEPS] = opts9[10];
+  s.sd[SD_STALLF] = opts9[11];
+  s.si[SI_MAXIT] = maxit;
+  s.si[SI_PCG] = pcg;
+  s.si[SI_STALLWIN] = stallwin;
+  s.si[SI_PROBES] = probes;
+  s.si[SI_SEEDLO] = (int)(unsigned)(seed & 0xffffffffull);
+  s.si[SI_SEEDHI] = (int)(unsigned)(seed >> 32);
+  s.si[SI_KMAXIT] = kmaxit;
+  s.si[SI_ARCMAX] = arcmax;
+}
+
+__global__ void k_new_phase(Inst s, double eta, int maxit) {
+  if (threadIdx.x != 0) return;
+  s.si[SI_DONE] = 0;
+  s.si[SI_PHASEIT] = 0;
+  s.si[SI_HISTN] = 0;
+  s.si[SI_MAXIT] = maxit;
+  s.sd[SD_ETA] = eta;
+}
+
+// ---------------------------------------------------------------- passes
+PassArgs pass_args(mvsk_ctx* c) {
+  PassArgs a;
+  memset(&a, 0, sizeof(a));
+  a.c2 = c->c[1];
+  a.c3 = c->c[2];
+  a.c4 = c->c[3];
+  a.rscale = 1.0;
+  return a;
+}
+
+mvsk_status run_pass(mvsk_ctx* c, int prec, int mode, int nin, PassArgs a, const int* live = nullptr) {
+  int stages = 0;
+  const size_t smem = rowpass_smem(prec, mode, nin, c->ld, &stages);
+  if (smem == 0) return fail(MVSK_EINVAL, "pass (prec %d, mode %d, nin %d) unsupported at ld=%d", prec, mode, nin, c->ld);
+  if (prec != P64 && c->Alo == nullptr) return fail(MVSK_EINVAL, "context holds no reduced-precision copy of A");
+  a.A = prec == P64 ? (const void*)c->A64 : (const void*)c->Alo;
+  a.T = c->T;
+  a.ld = c->ld;
+  a.part = c->part;
+  a.spart = c->spart;
+  a.rows_per_cta = c->rows_per_cta;
+  a.stages = stages;
+  a.err = c->err;
+  a.live = live;
+  a.counter = c->si + SI_PASSES;
+  CU(rowpass_launch(prec, mode, nin, a, c->grid, smem, c->stream));
+  return MVSK_OK;
+}
+
+mvsk_status reduce_cols(mvsk_ctx* c, int prec, int nout, double* out, size_t stride, const double* bias, double bscale,
+                        const int* skip, const int* live) {
+  dim3 g((c->ld + 255) / 256, nout);
+  const double sc = 1.0 / (double)c->T;
+  if (prec == P64)
+    k_reduce_cols<double><<<g, 256, 0, c->stream>>>((const double*)c->part, c->grid, nout, c->ld, c->n, sc, bias, bscale,
+                                                    out, stride, skip, live);
+  else
+    k_reduce_cols<float><<<g, 256, 0, c->stream>>>((const float*)c->part, c->grid, nout, c->ld, c->n, sc, bias, bscale, out,
+                                                   stride, skip, live);
+  CU(cudaGetLastError());
+  return MVSK_OK;
+}
+
+// z = A x (FP64), g = -c1 mu + T^-1 A^T psi'(z); scalar partials hold sum psi(z).
+mvsk_status pass_valgrad(mvsk_ctx* c, const double* x, double* z, double* g, const int* skip) {
+  PassArgs a = pass_args(c);
+  a.in[0] = x;
+  a.rowout = z;
+  a.skip = skip;
+  TRY(run_pass(c, P64, M_VALGRAD, 1, a));
+  return reduce_cols(c, P64, 1, g, c->ld, c->mu, -c->c[0], skip, nullptr);
+}
+
+mvsk_status pass_fwd_z(mvsk_ctx* c, const double* x, double* z) {
+  PassArgs a = pass_args(c);
+  a.in[0] = x;
+  a.rowout = z;
+  return run_pass(c, P64, M_FWD, 1, a);
+}
+
+mvsk_status pass_ls(mvsk_ctx* c, const double* dir, const int* skip) {
+  PassArgs a = pass_args(c);
+  a.in[0] = dir;
+  a.z = c->in.z;
+  a.skip = skip;
+  return run_pass(c, P64, M_LS, 1, a);
+}
+
+// ------------------------------------------------ affine-normal block (PCG)
+// Sec. 3.2 with the PCG reduced solve: h and the K Hutchinson probes share the
+// first PCG round (groups of two columns per pass over A), then
+// rhat = K^-1 sum_k (A X_k) o (A p_k), a = P_V T^-1 A^T (psi''' o rhat), a
+// second PCG round for H^-1 a, and d = X_h - (||gbar||/m) X_a - nu.
+mvsk_status direction_pcg(mvsk_ctx* c) {
+  Inst& s = c->in;
+  const int K = c->opt.probes;
+  const int ncol1 = K + 1;
+  const int ca = K + 1;
+  const int ngroups = (ncol1 + 1) / 2;
+  const int* skipdir = s.si + SI_SKIPDIR;
+  const int P = c->dir_prec;
+  const int kmax = c->opt.krylov_maxit;
+  {
+    PassArgs a = pass_args(c);
+    a.in[0] = s.nuhat;
+    a.in[1] = s.maskF;
+    a.z = s.z;
+    a.skip = skipdir;
+    TRY(run_pass(c, P, M_HVPDIAG, 2, a));
+    TRY(reduce_cols(c, P, 2, c->hd, c->ld, nullptr, 0.0, skipdir, nullptr));
+  }
+  k_pcg_setup<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid, ngroups);
+  CU(cudaGetLastError());
+  for (int it = 0; it < kmax; ++it) {
+    for (int g = 0; g < ngroups; ++g) {
+      const int c0 = 2 * g;
+      const int nin = (c0 + 1 < ncol1) ? 2 : 1;
+      PassArgs a = pass_args(c);
+      a.in[0] = s.P + (size_t)c0 * c->ld;
+      if (nin == 2) a.in[1] = s.P + (size_t)(c0 + 1) * c->ld;
+      a.z = s.z;
+      a.skip = skipdir;
+      TRY(run_pass(c, P, M_HVP, nin, a, s.si + SI_LIVE + g));
+      TRY(reduce_cols(c, P, nin, s.Q + (size_t)c0 * c->ld, c->ld, nullptr, 0.0, skipdir, s.si + SI_LIVE + g));
+    }
+    k_pcg_step<<<ncol1, kVT, 0, c->stream>>>(s, 0, kmax);
+    CU(cudaGetLastError());
+  }
+  if (K > 0) {
+    for (int k = 0; k < K; ++k) {
+      PassArgs a = pass_args(c);
+      a.in[0] = s.X + (size_t)(k + 1) * c->ld;
+      a.in[1] = s.Bv + (size_t)(k + 1) * c->ld;
+      a.rowout = s.rhat;
+      a.row_accum = k > 0;
+      a.rscale = 1.0 / K;
+      a.skip = skipdir;
+      TRY(run_pass(c, P, M_RHAT, 2, a));
+    }
+    PassArgs a = pass_args(c);
+    a.z = s.z;
+    a.roww = s.rhat;
+    a.skip = skipdir;
+    TRY(run_pass(c, P, M_BACK, 0, a));
+    TRY(reduce_cols(c, P, 1, s.at, c->ld, nullptr, 0.0, skipdir, nullptr));
+  } else {
+    CU(cudaMemsetAsync(s.at, 0, sizeof(double) * c->ld, c->stream));
+  }
+  k_pcg_setup2<<<1, kVT, 0, c->stream>>>(s, ca, ca / 2);
+  CU(cudaGetLastError());
+  for (int it = 0; it < kmax; ++it) {
+    PassArgs a = pass_args(c);
+    a.in[0] = s.P + (size_t)ca * c->ld;
+    a.z = s.z;
+    a.skip = skipdir;
+    TRY(run_pass(c, P, M_HVP, 1, a, s.si + SI_LIVE + ca / 2));
+    TRY(reduce_cols(c, P, 1, s.Q + (size_t)ca * c->ld, c->ld, nullptr, 0.0, skipdir, s.si + SI_LIVE + ca / 2));
+    k_pcg_step<<<1, kVT, 0, c->stream>>>(s, ca, kmax);
+    CU(cudaGetLastError());
+  }
+  k_assemble<<<1, kVT, 0, c->stream>>>(s, ca);
+  CU(cudaGetLastError());
+  return MVSK_OK;
+}
+
+}  // namespace
+mvsk_status direction_direct(mvsk_ctx* c);  // direct.cu
+namespace {
+
+mvsk_status direction(mvsk_ctx* c, int cfg) { return cfg == MVSK_PCG ? direction_pcg(c) : direction_direct(c); }
+
+// One iteration of Alg. 1: oracle block, affine-normal block, quartic step, boundary block.
+mvsk_status launch_iteration(mvsk_ctx* c, int cfg) {
+  Inst& s = c->in;
+  const int* done = s.si + SI_DONE;
+  TRY(pass_valgrad(c, s.x, s.z, s.g, done));
+  k_face<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid);
+  CU(cudaGetLastError());
+  TRY(direction(c, cfg));
+  TRY(pass_ls(c, s.d, done));
+  k_decide1<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid);
+  CU(cudaGetLastError());
+  TRY(pass_ls(c, s.dstep, s.si + SI_SKIPLS));
+  k_decide2<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid);
+  CU(cudaGetLastError());
+  k_end_iter<<<1, 32, 0, c->stream>>>(s);
+  CU(cudaGetLastError());
+  return MVSK_OK;
+}
+
+// Host copies of a few device ints / doubles.
+mvsk_status read_ints(mvsk_ctx* c, int* dst, int first, int count) {
+  CU(cudaMemcpyAsync(dst, c->si + first, sizeof(int) * count, cudaMemcpyDeviceToHost, c->stream));
+  TRY(sync(c));
+  return MVSK_OK;
+}
+
+mvsk_status init_state(mvsk_ctx* c, int cfg, double tol, const double cc[4]) {
+  const Options& o = c->opt;
+  const bool pcg = cfg == MVSK_PCG;
+  const double reg = isnan(o.reg) ? (pcg ? 1e-4 : 0.0) : o.reg;
+  double h[12] = {o.tau, o.eps_act, o.release_ratio, reg, o.krylov_tol, cc[0], cc[1], cc[2], cc[3],
+                  1.0 / (double)c->T, o.descent_eps, o.stall_factor};
+  double* dopts = c->vec_scratch;  // 12 doubles
+  CU(cudaMemcpyAsync(dopts, h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+  k_init_state<<<1, 32, 0, c->stream>>>(c->in, tol, o.eta, pcg ? o.pcg_max_iter : o.max_iter, pcg ? 1 : 0,
+                                        o.stall_window, o.probes, o.probe_seed, o.krylov_maxit, o.arc_halvings, dopts);
+  CU(cudaGetLastError());
+  return MVSK_OK;
+}
+
+void set_coefs(mvsk_ctx* c, const double cc[4]) {
+  for (int q = 0; q < 4; ++q) c->c[q] = cc[q];
+}
+
+struct SolveOut {
+  int status = MVSK_OK;
+  int iters = 0, restarts = 0;
+};
+
+// Plain YAND-MVSK solve of one instance with coefficients cc (Alg. 1 plus the
+// stall-recovery phases of the PCG configuration).  Result in c->in.x.
+mvsk_status solve_instance(mvsk_ctx* c, int cfg, double tol, const double* w0_dev, const double cc[4], SolveOut* so,
+                           std::chrono::steady_clock::time_point t0) {
+  Inst& s = c->in;
+  set_coefs(c, cc);
+  TRY(init_state(c, cfg, tol, cc));
+  // kkt at x0 = 1/n (denominator of kkt_rel)
+  k_fill<<<(c->ld + 255) / 256, 256, 0, c->stream>>>(s.x, c->n, c->ld, 1.0 / c->n);
+  TRY(pass_valgrad(c, s.x, s.z, s.g, nullptr));
+  k_kkt0<<<1, kVT, 0, c->stream>>>(s);
+  CU(cudaGetLastError());
+  if (w0_dev != nullptr) CU(cudaMemcpyAsync(s.x, w0_dev, sizeof(double) * c->ld, cudaMemcpyDeviceToDevice, c->stream));
+  if (c->n == 1) {
+    so->status = MVSK_OK;
+    return MVSK_OK;
+  }
+  const Options& o = c->opt;
+  struct Phase {
+    double eta;
+    int maxit;
+  };
+  std::vector<Phase> phases;
+  if (cfg == MVSK_PCG) {
+    phases = {{o.eta, o.pcg_max_iter}, {o.restart_eta1, o.restart_iter}, {o.restart_eta2, o.restart_iter}};
+  } else {
+    phases = {{o.eta, o.max_iter}};
+  }
+  int done = 0;
+  so->status = MVSK_ENOTCONVERGED;
+  for (size_t ph = 0; ph < phases.size(); ++ph) {
+    if (ph > 0) so->restarts += 1;
+    k_new_phase<<<1, 32, 0, c->stream>>>(s, phases[ph].eta, phases[ph].maxit);
+    CU(cudaGetLastError());
+    for (int it = 0; it <= phases[ph].maxit; ++it) {
+      TRY(launch_iteration(c, cfg));
+      TRY(read_ints(c, &done, SI_DONE, 1));
+      if (o.trace) {
+        int hi[kSI];
+        double hd[kSD];
+        CU(cudaMemcpy(hi, s.si, sizeof(hi), cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(hd, s.sd, sizeof(hd), cudaMemcpyDeviceToHost));
+        fprintf(stderr,
+                "[mvsk] phase %zu it %d done %d kkt_rel %.3e f %.12e m %d gn %.3e branch %d amax %.3e eta_k %.3e "
+                "alpha %.3e lam %.3e kry %d\n",
+                ph, hi[SI_ITER], hi[SI_DONE], hd[SD_KKTREL], hd[SD_F], hi[SI_M], hd[SD_GN], hi[SI_BRANCH],
+                hd[SD_AMAX], hd[SD_ETAK], hd[SD_ALPHA], hd[SD_LAM], hi[SI_KRY]);
+      }
+      if (done != 0) break;
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > o.max_elapsed) {
+        so->status = MVSK_ETIMEOUT;
+        done = 4;
+        break;
+      }
+    }
+    if (done == 1) {
+      so->status = MVSK_OK;
+      break;
+    }
+    if (done == 3) {
+      so->status = MVSK_ENUMERIC;
+      break;
+    }
+    if (done == 4) break;
+  }
+  if (so->status != MVSK_OK)
+    CU(cudaMemcpyAsync(s.x, s.bestx, sizeof(double) * c->ld, cudaMemcpyDeviceToDevice, c->stream));
+  return MVSK_OK;
+}
+
+// f, kkt and mu^T x at c->in.x with the current coefficients.
+mvsk_status eval_here(mvsk_ctx* c, double out3[3]) {
+  Inst& s = c->in;
+  TRY(pass_valgrad(c, s.x, s.z, s.g, nullptr));
+  double* d3 = c->vec_scratch + 16;
+  k_eval_finish<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid, d3);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(out3, d3, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TRY(sync(c));
+  return MVSK_OK;
+}
+
+// Solve with optional return-target calibration of c1 (Illinois regula falsi
+// on mu^T x*(c1) = target; Sec. 6).  Result in c->in.x; fills info.
+mvsk_status solve_with_target(mvsk_ctx* c, int cfg, double tol, const double* w0_dev, const double lam[4],
+                              double target, mvsk_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  double cc[4];
+  const double s = c->s_equal;
+  if (c->opt.pref_scaling == 1 && s > 0.0 && isfinite(s)) {
+    cc[0] = lam[0] / s;
+    cc[1] = lam[1] / (s * s);
+    cc[2] = lam[2] / (s * s * s);
+    cc[3] = lam[3] / (s * s * s * s);
+  } else {
+    for (int q = 0; q < 4; ++q) cc[q] = lam[q];
+  }
+  Inst& in = c->in;
+  const size_t vb = sizeof(double) * c->ld;
+  double* xlo = in.tmp + (size_t)20 * c->ld;
+  double* xhi = xlo + c->ld;
+  int evals = 0, iters = 0, restarts = 0;
+  SolveOut so;
+  double ev[3];
+  auto run = [&](double c1, const double* w0, double* h) -> mvsk_status {
+    double c4[4] = {c1, cc[1], cc[2], cc[3]};
+    SolveOut o;
+    TRY(solve_instance(c, cfg, tol, w0, c4, &o, t0));
+    int it = 0;
+    TRY(read_ints(c, &it, SI_ITER, 1));
+    iters += it;
+    restarts += o.restarts;
+    so = o;
+    evals += 1;
+    TRY(eval_here(c, ev));
+    *h = ev[2] - target;
+    return MVSK_OK;
+  };
+  double h = 0.0;
+  if (isnan(target)) {
+    TRY(run(cc[0], w0_dev, &h));
+  } else {
+    const double scale = c->mu_absmax;
+    const double gap_tol = c->opt.cal_rel_tol * scale;
+    const double c1_ref = fmax(cc[1], 1e-300) * s * s / fmax(scale, 1e-300);
+    const double c1_max = 1e6 * c1_ref;
+    double h_lo, h_hi, c_lo = 0.0, c_hi;
+    TRY(run(0.0, nullptr, &h_lo));
+    cc[0] = 0.0;
+    if (!(h_lo >= -gap_tol)) {
+      CU(cudaMemcpyAsync(xlo, in.x, vb, cudaMemcpyDeviceToDevice, c->stream));
+      c_hi = cc[0] > 0.0 ? cc[0] : c1_ref;
+      TRY(run(c_hi, xlo, &h_hi));
+      CU(cudaMemcpyAsync(xhi, in.x, vb, cudaMemcpyDeviceToDevice, c->stream));
+      while (h_hi < 0.0 && c_hi < c1_max) {
+        c_lo = c_hi;
+        h_lo = h_hi;
+        CU(cudaMemcpyAsync(xlo, xhi, vb, cudaMemcpyDeviceToDevice, c->stream));
+        c_hi = fmin(8.0 * c_hi, c1_max);
+        TRY(run(c_hi, xlo, &h_hi));
+        CU(cudaMemcpyAsync(xhi, in.x, vb, cudaMemcpyDeviceToDevice, c->stream));
+      }
+      cc[0] = c_hi;
+      if (h_hi >= 0.0 && !(fabs(h_hi) <= gap_tol)) {
+        int side = 0;
+        while (evals < c->opt.cal_max_evals) {
+          double cm = c_hi - h_hi * (c_hi - c_lo) / (h_hi - h_lo);
+          if (!(c_lo < cm && cm < c_hi)) cm = 0.5 * (c_lo + c_hi);
+          const double* w0 = (cm - c_lo) <= (c_hi - cm) ? xlo : xhi;
+          double hm;
+          TRY(run(cm, w0, &hm));
+          cc[0] = cm;
+          if (fabs(hm) <= gap_tol || (c_hi - c_lo) <= c->opt.cal_bracket_tol * c_hi) break;
+          if (hm < 0.0) {
+            c_lo = cm;
+            h_lo = hm;
+            CU(cudaMemcpyAsync(xlo, in.x, vb, cudaMemcpyDeviceToDevice, c->stream));
+            if (side == -1) h_hi *= 0.5;
+            side = -1;
+          } else {
+            c_hi = cm;
+            h_hi = hm;
+            CU(cudaMemcpyAsync(xhi, in.x, vb, cudaMemcpyDeviceToDevice, c->stream));
+            if (side == 1) h_lo *= 0.5;
+            side = 1;
+          }
+          cc[0] = c_hi;
+          if (evals >= c->opt.cal_max_evals) {
+            CU(cudaMemcpyAsync(in.x, xhi, vb, cudaMemcpyDeviceToDevice, c->stream));
+            double c4[4] = {c_hi, cc[1], cc[2], cc[3]};
+            set_coefs(c, c4);
+            TRY(eval_here(c, ev));
+          }
+        }
+      }
+    }
+  }
+  if (info != nullptr) {
+    int cnt[kSI];
+    CU(cudaMemcpyAsync(cnt, c->si, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+    TRY(sync(c));
+    // kkt_rel against kkt(1/n): sd[SD_KKT0] of the last solve
+    double k0 = 0.0;
+    CU(cudaMemcpy(&k0, in.sd + SD_KKT0, sizeof(double), cudaMemcpyDeviceToHost));
+    memset(info, 0, sizeof(*info));
+    info->iters = iters;
+    info->restarts = restarts;
+    info->passes = cnt[SI_PASSES];
+    info->krylov_iters = cnt[SI_KRY];
+    info->third_calls = cnt[SI_THIRD];
+    info->evals = evals;
+    info->f = ev[0];
+    info->kkt_residual = ev[1];
+    info->kkt0 = k0;
+    info->kkt_rel = c->n == 1 ? 0.0 : ev[1] / fmax(k0, 1e-300);
+    for (int q = 0; q < 4; ++q) info->c[q] = c->c[q];
+    info->achieved_mean = ev[2];
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    info->status = so.status;
+    std::vector<double> hx(c->n);
+    CU(cudaMemcpy(hx.data(), in.x, sizeof(double) * c->n, cudaMemcpyDeviceToHost));
+    int fc = 0;
+    for (int i = 0; i < c->n; ++i) fc += (hx[i] - c->opt.tau > c->opt.eps_act);
+    info->free_count = fc;
+  }
+  return (mvsk_status)so.status;
+}
+
+mvsk_status check_w0(mvsk_ctx* c, const double* w0, double* dst) {
+  std::vector<double> h(c->n);
+  CU(cudaMemcpy(h.data(), w0, sizeof(double) * c->n, cudaMemcpyDefault));
+  double s = 0.0, mn = INFINITY;
+  for (int i = 0; i < c->n; ++i) {
+    if (!isfinite(h[i])) return fail(MVSK_EINVAL, "w0[%d] is not finite", i);
+    s += h[i];
+    mn = fmin(mn, h[i]);
+  }
+  if (fabs(s - 1.0) > 1e-9 || mn < c->opt.tau * (1.0 - 1e-9))
+    return fail(MVSK_EINVAL, "w0 is not in Delta(tau): sum %.17g, min %.3g", s, mn);
+  CU(cudaMemsetAsync(dst, 0, sizeof(double) * c->ld, c->stream));
+  CU(cudaMemcpyAsync(dst, h.data(), sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream));
+  TRY(sync(c));
+  return MVSK_OK;
+}
+
+mvsk_status equal_weight_scale(mvsk_ctx* c) {
+  Inst& s = c->in;
+  k_fill<<<(c->ld + 255) / 256, 256, 0, c->stream>>>(s.x, c->n, c->ld, 1.0 / c->n);
+  TRY(pass_fwd_z(c, s.x, s.z));
+  double* d = c->vec_scratch + 24;
+  k_sumsq<<<1, kVT, 0, c->stream>>>(s.z, c->T, d);
+  double h = 0.0;
+  CU(cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TRY(sync(c));
+  c->s_equal = sqrt(h / (double)c->T);
+  return MVSK_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+mvsk_status mvsk_create(const double* R, int64_t T, int64_t n, int64_t ld, uint32_t flags, mvsk_ctx** out) {
+  if (out == nullptr || R == nullptr) return fail(MVSK_EINVAL, "null argument");
+  *out = nullptr;
+  if (T < 1 || n < 1 || n > kMaxCols || ld < n) return fail(MVSK_EINVAL, "bad sizes T=%lld n=%lld ld=%lld", (long long)T, (long long)n, (long long)ld);
+  if (flags > MVSK_PREC_MIXED_FP32) return fail(MVSK_EINVAL, "unknown flags %u", flags);
+  mvsk_ctx* c = new (std::nothrow) mvsk_ctx();
+  if (c == nullptr) return fail(MVSK_ENOMEM, "host allocation failed");
+  auto bail = [&](mvsk_status st) {
+    mvsk_destroy(c);
+    return st;
+  };
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return bail(fail(MVSK_ECUDA, "no CUDA device"));
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return bail(fail(MVSK_ECUDA, "cudaGetDeviceProperties failed"));
+  c->nsm = prop.multiProcessorCount;
+  c->T = T;
+  c->n = (int)n;
+  c->ld = (int)((n + kPad - 1) / kPad * kPad);
+  c->flags = flags;
+  c->dir_prec = flags == MVSK_PREC_MIXED_BF16 ? P16 : (flags == MVSK_PREC_MIXED_FP32 ? P32 : P64);
+  c->grid = (int)(T < c->nsm ? T : c->nsm);
+  c->rows_per_cta = (int)((T + c->grid - 1) / c->grid);
+  c->grid = (int)((T + c->rows_per_cta - 1) / c->rows_per_cta);
+  const size_t ldb = sizeof(double) * c->ld;
+  mvsk_status st;
+#define ALLOC(ptr, bytes)                                              \
+  do {                                                                 \
+    void* p_ = nullptr;                                                \
+    if ((st = dalloc(c, &p_, (bytes))) != MVSK_OK) return bail(st);    \
+    ptr = reinterpret_cast<decltype(ptr)>(p_);                         \
+  } while (0)
+  ALLOC(c->A64, ldb * (size_t)T);
+  if (flags == MVSK_PREC_MIXED_BF16) ALLOC(c->Alo, sizeof(__nv_bfloat16) * c->ld * (size_t)T);
+  if (flags == MVSK_PREC_MIXED_FP32) ALLOC(c->Alo, sizeof(float) * c->ld * (size_t)T);
+  ALLOC(c->mu, ldb);
+  ALLOC(c->err, 64);
+  if (cudaMemcpy2DAsync(c->A64, ldb, R, sizeof(double) * ld, sizeof(double) * n, T, cudaMemcpyDefault, c->stream) !=
+      cudaSuccess)
+    return bail(fail(MVSK_ECUDA, "copy of R failed"));
+  k_colmean<<<(c->n + 127) / 128, 128, 0, c->stream>>>(c->A64, T, c->n, c->ld, c->mu);
+  const int cg = 4 * c->nsm;
+  if (flags == MVSK_PREC_MIXED_BF16)
+    k_centre<__nv_bfloat16><<<cg, 256, 0, c->stream>>>(c->A64, (__nv_bfloat16*)c->Alo, T, c->n, c->ld, c->mu, c->err);
+  else if (flags == MVSK_PREC_MIXED_FP32)
+    k_centre<float><<<cg, 256, 0, c->stream>>>(c->A64, (float*)c->Alo, T, c->n, c->ld, c->mu, c->err);
+  else
+    k_centre<float><<<cg, 256, 0, c->stream>>>(c->A64, (float*)nullptr, T, c->n, c->ld, c->mu, c->err);
+  if (cudaGetLastError() != cudaSuccess) return bail(fail(MVSK_ECUDA, "centring launch failed"));
+  int bad = 0;
+  if (cudaMemcpy(&bad, c->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return bail(fail(MVSK_ECUDA, "sync failed"));
+  if (bad) return bail(fail(MVSK_EINVAL, "R holds a non-finite value"));
+  // instance state and workspace
+  Inst& s = c->in;
+  c->ncolmax = 20;
+  ALLOC(c->sd, sizeof(double) * kSD);
+  ALLOC(c->si, sizeof(int) * kSI);
+  s.sd = c->sd;
+  s.si = c->si;
+  s.mu = c->mu;
+  ALLOC(s.x, ldb);
+  ALLOC(s.g, ldb);
+  ALLOC(s.nuhat, ldb);
+  ALLOC(s.maskF, ldb);
+  ALLOC(s.d, ldb);
+  ALLOC(s.dstep, ldb);
+  ALLOC(s.xbar, ldb);
+  ALLOC(s.at, ldb);
+  ALLOC(s.bestx, ldb);
+  ALLOC(s.tmp, ldb * (size_t)(c->ncolmax + 4));
+  ALLOC(c->hd, 2 * ldb);
+  s.Gnu = c->hd;
+  s.diagG = c->hd + c->ld;
+  ALLOC(s.z, sizeof(double) * (size_t)T);
+  ALLOC(s.rhat, sizeof(double) * (size_t)T);
+  ALLOC(s.X, ldb * c->ncolmax);
+  ALLOC(s.R, ldb * c->ncolmax);
+  ALLOC(s.Zc, ldb * c->ncolmax);
+  ALLOC(s.P, ldb * c->ncolmax);
+  ALLOC(s.Q, ldb * c->ncolmax);
+  ALLOC(s.Bv, ldb * c->ncolmax);
+  ALLOC(s.rz, sizeof(double) * c->ncolmax);
+  ALLOC(s.rhsn, sizeof(double) * c->ncolmax);
+  ALLOC(c->part, sizeof(double) * 2 * (size_t)c->ld * c->grid);
+  ALLOC(c->spart, sizeof(double) * 16 * (size_t)c->grid);
+  ALLOC(c->fwd, sizeof(double) * 4 * (size_t)T);
+  ALLOC(c->vec_scratch, sizeof(double) * (64 + 4 * (size_t)c->ld));
+  s.n = c->n;
+  s.ld = c->ld;
+  s.T = T;
+#undef ALLOC
+  std::vector<double> hmu(c->n);
+  if (cudaMemcpy(hmu.data(), c->mu, sizeof(double) * c->n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return bail(fail(MVSK_ECUDA, "copy of mu failed"));
+  for (int i = 0; i < c->n; ++i) c->mu_absmax = fmax(c->mu_absmax, fabs(hmu[i]));
+  if ((st = equal_weight_scale(c)) != MVSK_OK) return bail(st);
+  *out = c;
+  return MVSK_OK;
+}
+
+mvsk_status mvsk_set_stream(mvsk_ctx* c, void* stream) {
+  if (c == nullptr) return fail(MVSK_EINVAL, "null context");
+  c->stream = (cudaStream_t)stream;
+  return MVSK_OK;
+}
+
+mvsk_status mvsk_set_prefs(mvsk_ctx* c, const double lambda[4], double target) {
+  if (c == nullptr || lambda == nullptr) return fail(MVSK_EINVAL, "null argument");
+  for (int q = 0; q < 4; ++q)
+    if (!(lambda[q] >= 0.0) || !isfinite(lambda[q])) return fail(MVSK_EINVAL, "lambda[%d] must be finite and >= 0", q);
+  if (isinf(target)) return fail(MVSK_EINVAL, "target must be finite or NaN");
+  for (int q = 0; q < 4; ++q) c->lam[q] = lambda[q];
+  c->target = target;
+  const double s = c->s_equal;
+  const bool stdz = c->opt.pref_scaling == 1 && s > 0.0 && isfinite(s);
+  for (int q = 0; q < 4; ++q) c->c[q] = stdz ? lambda[q] / pow(s, q + 1) : lambda[q];
+  c->prefs_set = true;
+  return MVSK_OK;
+}
+
+mvsk_status mvsk_set_option(mvsk_ctx* c, const char* key, double v) {
+  if (c == nullptr || key == nullptr) return fail(MVSK_EINVAL, "null argument");
+  Options& o = c->opt;
+  const std::string k(key);
+  auto pos = [&](double x) { return isfinite(x) && x > 0.0; };
+  auto cnt = [&](double x, double lo, double hi) { return isfinite(x) && x == floor(x) && x >= lo && x <= hi; };
+  if (k == "tau" && isfinite(v) && v >= 0.0 && v * c->n < 1.0) o.tau = v;
+  else if (k == "eta" && pos(v)) o.eta = v;
+  else if (k == "max_iter" && cnt(v, 1, 1000000)) o.max_iter = (int)v;
+  else if (k == "pcg_max_iter" && cnt(v, 1, 1000000)) o.pcg_max_iter = (int)v;
+  else if (k == "restart_iter" && cnt(v, 1, 1000000)) o.restart_iter = (int)v;
+  else if (k == "restart_eta1" && pos(v)) o.restart_eta1 = v;
+  else if (k == "restart_eta2" && pos(v)) o.restart_eta2 = v;
+  else if (k == "max_elapsed" && v > 0.0) o.max_elapsed = v;
+  else if (k == "krylov_tol" && pos(v)) o.krylov_tol = v;
+  else if (k == "krylov_maxit" && cnt(v, 1, 10000)) o.krylov_maxit = (int)v;
+  else if (k == "reg" && (isnan(v) || (isfinite(v) && v >= 0.0))) o.reg = v;
+  else if (k == "probes" && cnt(v, 0, 16)) o.probes = (int)v;
+  else if (k == "probe_seed" && cnt(v, 0, 9007199254740992.0)) o.probe_seed = (unsigned long long)v;
+  else if (k == "pref_scaling" && cnt(v, 0, 1)) o.pref_scaling = (int)v;
+  else if (k == "release_ratio" && pos(v)) o.release_ratio = v;
+  else if (k == "eps_act" && isfinite(v) && v >= 0.0) o.eps_act = v;
+  else if (k == "oracle_prec" && cnt(v, 0, 2)) o.oracle_prec = (int)v;
+  else if (k == "cal_rel_tol" && pos(v)) o.cal_rel_tol = v;
+  else if (k == "stall_window" && cnt(v, 0, 15)) o.stall_window = (int)v;
+  else if (k == "trace" && cnt(v, 0, 1)) o.trace = (int)v;
+  else return fail(MVSK_EINVAL, "unknown option or bad value: %s = %g", key, v);
+  if (c->prefs_set && k == "pref_scaling") mvsk_set_prefs(c, c->lam, c->target);
+  return MVSK_OK;
+}
+
+mvsk_status mvsk_solve(mvsk_ctx* c, mvsk_config cfg, double tol, const double* w0, double* w_out, mvsk_info* info) {
+  if (c == nullptr || w_out == nullptr) return fail(MVSK_EINVAL, "null argument");
+  if (!c->prefs_set) return fail(MVSK_ESTATE, "mvsk_set_prefs must come first");
+  if (!(tol > 0.0) || (cfg != MVSK_DIRECT && cfg != MVSK_PCG)) return fail(MVSK_EINVAL, "bad tol or configuration");
+  double* w0d = nullptr;
+  if (w0 != nullptr) {
+    w0d = c->vec_scratch + 64;
+    TRY(check_w0(c, w0, w0d));
+  }
+  const mvsk_status st = solve_with_target(c, cfg, tol, w0d, c->lam, c->target, info);
+  if (st == MVSK_OK || st == MVSK_ENOTCONVERGED || st == MVSK_ETIMEOUT) {
+    TRY(download_vec(c, w_out, c->in.x, c->n));
+    TRY(sync(c));
+  }
+  return st;
+}
+
+mvsk_status mvsk_solve_batch(mvsk_ctx* c, mvsk_config cfg, int32_t B, const double* lambdas, const double* targets,
+                             double tol, const double* W0, double* W_out, mvsk_info* infos) {
+  if (c == nullptr || lambdas == nullptr || W_out == nullptr || B < 1) return fail(MVSK_EINVAL, "bad argument");
+  std::vector<double> lam(4 * (size_t)B), tg((size_t)B, NAN);
+  if (cudaMemcpy(lam.data(), lambdas, sizeof(double) * 4 * B, cudaMemcpyDefault) != cudaSuccess)
+    return fail(MVSK_ECUDA, "copy of lambdas failed");
+  if (targets != nullptr && cudaMemcpy(tg.data(), targets, sizeof(double) * B, cudaMemcpyDefault) != cudaSuccess)
+    return fail(MVSK_ECUDA, "copy of targets failed");
+  mvsk_status first = MVSK_OK;
+  for (int b = 0; b < B; ++b) {
+    TRY(mvsk_set_prefs(c, &lam[4 * (size_t)b], tg[b]));
+    const mvsk_status st = mvsk_solve(c, cfg, tol, W0 ? W0 + (size_t)b * c->n : nullptr, W_out + (size_t)b * c->n,
+                                      infos ? infos + b : nullptr);
+    if (st != MVSK_OK && st != MVSK_ENOTCONVERGED && st != MVSK_ETIMEOUT) return st;
+    if (st != MVSK_OK && first == MVSK_OK) first = st;
+  }
+  return first;
+}
+
+mvsk_status mvsk_eval(mvsk_ctx* c, const double* w, double* f, double* grad, double* kkt) {
+  if (c == nullptr || w == nullptr) return fail(MVSK_EINVAL, "null argument");
+  if (!c->prefs_set) return fail(MVSK_ESTATE, "mvsk_set_prefs must come first");
+  TRY(init_state(c, MVSK_PCG, 1.0, c->c));
+  TRY(upload_vec(c, c->in.x, w, c->n));
+  double ev[3];
+  TRY(eval_here(c, ev));
+  if (f) *f = ev[0];
+  if (kkt) *kkt = ev[1];
+  if (grad) {
+    TRY(download_vec(c, grad, c->in.g, c->n));
+    TRY(sync(c));
+  }
+  return MVSK_OK;
+}
+
+mvsk_status mvsk_oracle_hvp(mvsk_ctx* c, const double* w, const double* v, double* out) {
+  if (c == nullptr || w == nullptr || v == nullptr || out == nullptr) return fail(MVSK_EINVAL, "null argument");
+  if (!c->prefs_set) return fail(MVSK_ESTATE, "mvsk_set_prefs must come first");
+  Inst& s = c->in;
+  TRY(upload_vec(c, s.x, w, c->n));
+  TRY(upload_vec(c, s.d, v, c->n));
+  TRY(pass_fwd_z(c, s.x, s.z));
+  PassArgs a = pass_args(c);
+  a.in[0] = s.d;
+  a.z = s.z;
+  TRY(run_pass(c, c->opt.oracle_prec, M_HVP, 1, a));
+  TRY(reduce_cols(c, c->opt.oracle_prec, 1, s.at, c->ld, nullptr, 0.0, nullptr, nullptr));
+  TRY(download_vec(c, out, s.at, c->n));
+  return sync(c);
+}
+
+mvsk_status mvsk_oracle_third(mvsk_ctx* c, const double* w, const double* u, const double* v, double* out) {
+  if (c == nullptr || w == nullptr || u == nullptr || v == nullptr || out == nullptr)
+    return fail(MVSK_EINVAL, "null argument");
+  if (!c->prefs_set) return fail(MVSK_ESTATE, "mvsk_set_prefs must come first");
+  Inst& s = c->in;
+  TRY(upload_vec(c, s.x, w, c->n));
+  TRY(upload_vec(c, s.d, u, c->n));
+  TRY(upload_vec(c, s.dstep, v, c->n));
+  TRY(pass_fwd_z(c, s.x, s.z));
+  PassArgs a = pass_args(c);
+  a.in[0] = s.d;
+  a.in[1] = s.dstep;
+  a.z = s.z;
+  TRY(run_pass(c, c->opt.oracle_prec, M_THIRD, 2, a));
+  TRY(reduce_cols(c, c->opt.oracle_prec, 1, s.at, c->ld, nullptr, 0.0, nullptr, nullptr));
+  TRY(download_vec(c, out, s.at, c->n));
+  return sync(c);
+}
+
+mvsk_status mvsk_oracle_ls(mvsk_ctx* c, const double* w, const double* d, double coef[5], double* alpha_max) {
+  if (c == nullptr || w == nullptr || d == nullptr || coef == nullptr) return fail(MVSK_EINVAL, "null argument");
+  if (!c->prefs_set) return fail(MVSK_ESTATE, "mvsk_set_prefs must come first");
+  Inst& s = c->in;
+  TRY(init_state(c, MVSK_PCG, 1.0, c->c));
+  TRY(upload_vec(c, s.x, w, c->n));
+  TRY(upload_vec(c, s.d, d, c->n));
+  TRY(pass_fwd_z(c, s.x, s.z));
+  TRY(pass_ls(c, s.d, nullptr));
+  double* dc = c->vec_scratch + 32;
+  k_ls_coef_only<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid, s.d, dc);
+  k_alpha_max<<<1, kVT, 0, c->stream>>>(s.x, s.d, c->n, c->opt.tau, dc + 5);
+  CU(cudaGetLastError());
+  double h[6];
+  CU(cudaMemcpyAsync(h, dc, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  TRY(sync(c));
+  for (int q = 0; q < 5; ++q) coef[q] = h[q];
+  if (alpha_max) *alpha_max = h[5];
+  return MVSK_OK;
+}
+
+mvsk_status mvsk_oracle_direction(mvsk_ctx* c, mvsk_config cfg, const double* w, int32_t iteration, double* d_out) {
+  if (c == nullptr || w == nullptr || d_out == nullptr) return fail(MVSK_EINVAL, "null argument");
+  if (!c->prefs_set) return fail(MVSK_ESTATE, "mvsk_set_prefs must come first");
+  Inst& s = c->in;
+  TRY(init_state(c, cfg, 1.0, c->c));
+  int h2[2] = {1, iteration};
+  CU(cudaMemcpyAsync(c->si + SI_DIRONLY, &h2[0], sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->si + SI_ITER, &h2[1], sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  TRY(upload_vec(c, s.x, w, c->n));
+  TRY(pass_valgrad(c, s.x, s.z, s.g, nullptr));
+  k_face<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid);
+  CU(cudaGetLastError());
+  TRY(direction(c, cfg));
+  TRY(download_vec(c, d_out, s.d, c->n));
+  return sync(c);
+}
+
+mvsk_status mvsk_project_slice(mvsk_ctx* c, const double* v, double tau, double* out) {
+  if (c == nullptr || v == nullptr || out == nullptr) return fail(MVSK_EINVAL, "null argument");
+  if (!(tau >= 0.0) || !(tau * c->n < 1.0)) return fail(MVSK_EINVAL, "tau out of range");
+  Inst& s = c->in;
+  TRY(upload_vec(c, s.d, v, c->n));
+  k_project<<<1, kVT, 0, c->stream>>>(s.d, c->n, tau, s.dstep);
+  CU(cudaGetLastError());
+  TRY(download_vec(c, out, s.dstep, c->n));
+  return sync(c);
+}
+
+mvsk_status mvsk_quartic_argmin(mvsk_ctx* c, const double coef[5], double amax, double* alpha) {
+  if (c == nullptr || coef == nullptr || alpha == nullptr) return fail(MVSK_EINVAL, "null argument");
+  double* dc = c->vec_scratch + 40;
+  CU(cudaMemcpyAsync(dc, coef, 5 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  k_quartic<<<1, 32, 0, c->stream>>>(dc, amax, dc + 5);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(alpha, dc + 5, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return sync(c);
+}
+
+const char* mvsk_last_error(const mvsk_ctx*) { return g_err; }
+
+void mvsk_destroy(mvsk_ctx* c) {
+  if (c == nullptr) return;
+  if (c->stream != nullptr) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+}  // extern "C"
+
+namespace mvsk {
+
+size_t rowpass_smem(int prec, int mode, int nin, int ld, int* stages) {
+  if (prec == P64) return rowpass_smem_f64(mode, nin, ld, stages);
+  if (prec == P16) return rowpass_smem_bf16(mode, nin, ld, stages);
+  return rowpass_smem_f32(mode, nin, ld, stages);
+}
+
+cudaError_t rowpass_launch(int prec, int mode, int nin, const PassArgs& a, int grid, size_t smem, cudaStream_t st) {
+  if (prec == P64) return rowpass_launch_f64(mode, nin, a, grid, smem, st);
+  if (prec == P16) return rowpass_launch_bf16(mode, nin, a, grid, smem, st);
+  return rowpass_launch_f32(mode, nin, a, grid, smem, st);
+}
+
+}  // namespace mvsk

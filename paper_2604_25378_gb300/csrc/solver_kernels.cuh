@@ -1,0 +1,556 @@
+// Device kernels of one YAND-MVSK iteration (Alg. 1) for one instance:
+// oracle-block bookkeeping, affine-normal block in the PCG configuration,
+// quartic step and boundary block.  All kernels read SI_DONE (and their own
+// skip flags) first, so a fixed launch sequence can run past convergence.
+#pragma once
+
+#include "vec.cuh"
+
+namespace mvsk {
+
+// ---------------------------------------------------------------- utilities
+static __global__ void k_fill(double* v, int n, int ld, double val) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ld; i += gridDim.x * blockDim.x) v[i] = i < n ? val : 0.0;
+}
+
+// Sum of the cross-CTA scalar partials [G][ns] -> out[ns] (fixed order).
+inline __device__ void reduce_spart(const double* spart, int G, int ns, double scale, double* out) {
+  if (threadIdx.x < ns) {
+    double s = 0.0;
+    for (int b = 0; b < G; ++b) s += spart[(size_t)b * ns + threadIdx.x];
+    out[threadIdx.x] = s * scale;
+  }
+  __syncthreads();
+}
+
+// Column partials [G][nout][ld] -> out[m*ld + j] = scale * sum_b part + bias_scale * bias (m = 0).
+template <typename acc>
+static __global__ void k_reduce_cols(const acc* part, int G, int nout, int ld, int n, double scale, const double* bias,
+                              double bias_scale, double* out, size_t out_stride, const int* skip, const int* live) {
+  if (skip != nullptr && *skip != 0) return;
+  if (live != nullptr && *live == 0) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (j >= ld) return;
+  double s = 0.0;
+  for (int b = 0; b < G; ++b) s += (double)part[((size_t)b * nout + m) * ld + j];
+  s *= scale;
+  if (bias != nullptr && m == 0) s += bias_scale * bias[j];
+  out[(size_t)m * out_stride + j] = j < n ? s : 0.0;
+}
+
+// P_V v on the face F: v_F - mean_F(v) - (nu^T v) nu, zero off F.
+inline __device__ void project_V(const double* v, double* out, const double* maskF, const double* nuhat, int n, double m,
+                          double* scr) {
+  double s = 0.0, t = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    s += maskF[i] * v[i];
+    t += nuhat[i] * v[i];
+  }
+  const double2 r = block_sum2(s, t, scr);
+  const double mean = r.x / m;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = maskF[i] * (v[i] - mean) - r.y * nuhat[i];
+  __syncthreads();
+}
+
+// ------------------------------------------------------------- kkt at x0
+static __global__ void __launch_bounds__(kVT) k_kkt0(Inst s) {
+  __shared__ double scr[80];
+  const double tau = s.sd[SD_TAU];
+  const double k0 = kkt_residual(s.x, s.g, s.n, tau, scr, s.tmp);
+  if (threadIdx.x == 0) s.sd[SD_KKT0] = k0;
+}
+
+// f = -c1 mu^T x + T^-1 sum psi(z) and the KKT residual (mvsk_eval).
+static __global__ void __launch_bounds__(kVT) k_eval_finish(Inst s, const double* spart, int G, double* out3) {
+  __shared__ double scr[80];
+  __shared__ double ps[2];
+  reduce_spart(spart, G, 1, s.sd[SD_INVT], ps);
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < s.n; i += blockDim.x) mx += s.mu[i] * s.x[i];
+  mx = block_sum2(mx, 0.0, scr).x;
+  const double k = kkt_residual(s.x, s.g, s.n, s.sd[SD_TAU], scr, s.tmp);
+  if (threadIdx.x == 0) {
+    out3[0] = -s.sd[SD_C1] * mx + ps[0];
+    out3[1] = k;
+    out3[2] = mx;
+  }
+}
+
+// ----------------------------------------------------------- oracle block
+// After the value/gradient pass: objective, KKT test, best iterate, stall
+// test, the working face (face continuation) and the normalised face gradient.
+static __global__ void __launch_bounds__(kVT) k_face(Inst s, const double* spart, int G) {
+  __shared__ double scr[80];
+  __shared__ double sv[33];
+  __shared__ int si_[33];
+  __shared__ double ps[2];
+  __shared__ int s_stop;
+  int* SI = s.si;
+  double* SD = s.sd;
+  if (SI[SI_DONE] != 0) return;
+  const int n = s.n;
+  const double tau = SD[SD_TAU];
+  const bool dir_only = SI[SI_DIRONLY] != 0;
+  reduce_spart(spart, G, 1, SD[SD_INVT], ps);
+  double mx = 0.0, nonfin = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    mx += s.mu[i] * s.x[i];
+    if (!isfinite(s.g[i])) nonfin += 1.0;
+  }
+  const double2 r0 = block_sum2(mx, nonfin, scr);
+  const double f = -SD[SD_C1] * r0.x + ps[0];
+  if (threadIdx.x == 0) s_stop = 0;
+  __syncthreads();
+  if (!dir_only) {
+    if (threadIdx.x == 0) {
+      SD[SD_F] = f;
+      SD[SD_MUX] = r0.x;
+      if (r0.y > 0.0 || !isfinite(f)) {
+        SI[SI_DONE] = 3;
+        s_stop = 1;
+      } else if (SI[SI_PHASEIT] >= SI[SI_MAXIT]) {
+        SI[SI_DONE] = 2;
+        s_stop = 1;
+      }
+      if (s_stop) {
+        SI[SI_SKIPDIR] = 1;
+        SI[SI_SKIPLS] = 1;
+      }
+    }
+    __syncthreads();
+    if (s_stop) return;
+    const double kkt = kkt_residual(s.x, s.g, n, tau, scr, s.tmp);
+    const double rel = kkt / fmax(SD[SD_KKT0], 1e-300);
+    const bool better = rel < SD[SD_BEST];
+    if (better)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) s.bestx[i] = s.x[i];
+    if (threadIdx.x == 0) {
+      SD[SD_KKT] = kkt;
+      SD[SD_KKTREL] = rel;
+      if (better) SD[SD_BEST] = rel;
+      const int hn = SI[SI_HISTN];
+      SD[SD_HIST + (hn & 15)] = rel;
+      SI[SI_HISTN] = hn + 1;
+      const int win = SI[SI_STALLWIN];
+      if (rel <= SD[SD_TOL]) {
+        SI[SI_DONE] = 1;
+        s_stop = 1;
+      } else if (SI[SI_PCG] && hn + 1 > win && win > 0 && win < 16 &&
+                 rel > SD[SD_STALLF] * SD[SD_HIST + ((hn - win) & 15)]) {
+        SI[SI_DONE] = 2;
+        s_stop = 1;
+      }
+      if (s_stop) {
+        SI[SI_SKIPDIR] = 1;
+        SI[SI_SKIPLS] = 1;
+      }
+    }
+    __syncthreads();
+    if (s_stop) return;
+  }
+  // Working face: coordinates at tau are held, except the most violating one,
+  // released once ||gbar_F|| <= release_ratio * violation.
+  const double eps = SD[SD_EPSACT];
+  double sg = 0.0, cf = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (s.x[i] - tau > eps) {
+      sg += s.g[i];
+      cf += 1.0;
+    }
+  double2 r = block_sum2(sg, cf, scr);
+  double nuF = r.x / r.y;
+  double gq = 0.0;
+  double best = -INFINITY;
+  int bidx = 0x7fffffff;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (s.x[i] - tau > eps) {
+      const double e = s.g[i] - nuF;
+      gq += e * e;
+    } else {
+      const double v = nuF - s.g[i];
+      if (v > best || (v == best && i < bidx)) {
+        best = v;
+        bidx = i;
+      }
+    }
+  }
+  const double gn0 = sqrt(block_sum2(gq, 0.0, scr).x);
+  block_argmax(best, bidx, sv, si_);
+  const bool rel_ok = bidx != 0x7fffffff && best > 0.0 && gn0 <= SD[SD_RELRATIO] * best;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    s.maskF[i] = (s.x[i] - tau > eps || (rel_ok && i == bidx)) ? 1.0 : 0.0;
+  __syncthreads();
+  sg = 0.0;
+  cf = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sg += s.maskF[i] * s.g[i];
+    cf += s.maskF[i];
+  }
+  r = block_sum2(sg, cf, scr);
+  const double m = r.y;
+  nuF = r.x / m;
+  // gbar = P_F g, centred twice: the second pass removes the rounding of the
+  // first relative to gbar itself (not to g), so 1_F^T nu stays at rounding
+  // level even when ||gbar|| << |g| near a stationary point.
+  double sb = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double e = s.maskF[i] * (s.g[i] - nuF);
+    s.nuhat[i] = e;
+    sb += e;
+  }
+  const double mb = block_sum2(sb, 0.0, scr).x / m;
+  gq = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double e = s.maskF[i] * (s.nuhat[i] - mb);
+    s.nuhat[i] = e;
+    gq += e * e;
+  }
+  const double gn = sqrt(block_sum2(gq, 0.0, scr).x);
+  const int mi = (int)m;
+  const bool trivial = mi <= 2 || !(gn > 0.0);
+  for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
+    const double nh = (i < n && gn > 0.0) ? s.nuhat[i] / gn : 0.0;
+    s.nuhat[i] = nh;
+    if (trivial) s.d[i] = (mi == 2) ? -nh : 0.0;
+  }
+  if (threadIdx.x == 0) {
+    SD[SD_GN] = gn;
+    SD[SD_NUF] = nuF;
+    SI[SI_M] = mi;
+    SI[SI_SKIPDIR] = trivial ? 1 : 0;
+    if (rel_ok) SI[SI_NREL] += 1;
+  }
+}
+
+// --------------------------------------------------- PCG configuration
+// Column layout: 0 = h (Newton part), 1..K = Hutchinson probes, K+1 = a.
+inline __device__ void pcg_init_col(Inst& s, int c, double m, double lam, double* scr) {
+  const int n = s.n, ld = s.ld;
+  double* X = s.X + (size_t)c * ld;
+  double* R = s.R + (size_t)c * ld;
+  double* Z = s.Zc + (size_t)c * ld;
+  double* P = s.P + (size_t)c * ld;
+  const double* B = s.Bv + (size_t)c * ld;
+  double nb = 0.0;
+  for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+    X[i] = 0.0;
+    R[i] = B[i];
+    s.tmp[i] = i < n ? B[i] / s.diagG[i] : 0.0;
+    nb += B[i] * B[i];
+  }
+  __syncthreads();
+  project_V(s.tmp, Z, s.maskF, s.nuhat, n, m, scr);
+  double rz = 0.0;
+  for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+    P[i] = Z[i];
+    rz += R[i] * Z[i];
+  }
+  const double2 r = block_sum2(rz, nb, scr);
+  if (threadIdx.x == 0) {
+    s.rz[c] = r.x;
+    s.rhsn[c] = sqrt(r.y);
+    s.si[SI_ACT + c] = r.y > 0.0 ? 1 : 0;
+    s.si[SI_CITS + c] = 0;
+  }
+  __syncthreads();
+}
+
+// Setup of the first PCG round: lambda, Jacobi diagonal, RHS h and probes.
+static __global__ void __launch_bounds__(kVT) k_pcg_setup(Inst s, const double* spart, int G, int ngroups) {
+  __shared__ double scr[80];
+  __shared__ double ps[2];
+  int* SI = s.si;
+  double* SD = s.sd;
+  if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
+  const int n = s.n, ld = s.ld;
+  const double m = (double)SI[SI_M];
+  reduce_spart(spart, G, 2, SD[SD_INVT], ps);  // nu^T G nu, 1_F^T G 1_F
+  // |diag G| floored, on F; 1 off F (never used there: vectors vanish off F).
+  double sd = 0.0, sa = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sd += s.maskF[i] * s.diagG[i];
+    sa += s.maskF[i] * fabs(s.diagG[i]);
+  }
+  const double2 r = block_sum2(sd, sa, scr);
+  const double floor_ = 1e-300 + 1e-12 * (r.y / m);
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    s.diagG[i] = s.maskF[i] != 0.0 ? fmax(fabs(s.diagG[i]), floor_) : 1.0;
+  const double trG = r.x - ps[1] / m - ps[0];
+  const double lam = SD[SD_REG] * fabs(trG) / (m - 2.0);
+  // RHS 0: h = P_V (G nu)
+  project_V(s.Gnu, s.Bv, s.maskF, s.nuhat, n, m, scr);
+  const int K = SI[SI_PROBES];
+  const unsigned long long seed =
+      ((unsigned long long)(unsigned)SI[SI_SEEDHI] << 32) | (unsigned long long)(unsigned)SI[SI_SEEDLO];
+  const long long it = SI[SI_ITER];
+  for (int k = 0; k < K; ++k) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s.tmp[i] = probe_value(seed, it, k, i);
+    __syncthreads();
+    project_V(s.tmp, s.Bv + (size_t)(k + 1) * ld, s.maskF, s.nuhat, n, m, scr);
+  }
+  for (int c = 0; c <= K; ++c) pcg_init_col(s, c, m, lam, scr);
+  if (threadIdx.x == 0) {
+    SD[SD_LAM] = lam;
+    for (int g = 0; g < ngroups; ++g) {
+      int live = 0;
+      for (int c = 2 * g; c < 2 * g + 2 && c <= K; ++c) live += SI[SI_ACT + c];
+      SI[SI_LIVE + g] = live;
+    }
+  }
+}
+
+// One PCG step on columns blockIdx.x + c0 (Q holds G P from the pass).
+static __global__ void __launch_bounds__(kVT) k_pcg_step(Inst s, int c0, int kmaxit) {
+  __shared__ double scr[80];
+  int* SI = s.si;
+  if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
+  const int c = c0 + blockIdx.x;
+  if (SI[SI_ACT + c] == 0) return;
+  const int n = s.n, ld = s.ld;
+  const double m = (double)SI[SI_M];
+  const double lam = s.sd[SD_LAM];
+  double* X = s.X + (size_t)c * ld;
+  double* R = s.R + (size_t)c * ld;
+  double* Z = s.Zc + (size_t)c * ld;
+  double* P = s.P + (size_t)c * ld;
+  double* Q = s.Q + (size_t)c * ld;
+  double* tmp = s.tmp + (size_t)(1 + blockIdx.x) * ld;  // private scratch per column CTA
+  project_V(Q, Q, s.maskF, s.nuhat, n, m, scr);
+  double pq = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    Q[i] += lam * P[i];
+    pq += P[i] * Q[i];
+  }
+  pq = block_sum2(pq, 0.0, scr).x;
+  auto deactivate = [&]() {
+    if (threadIdx.x == 0) {
+      SI[SI_ACT + c] = 0;
+      atomicSub(&SI[SI_LIVE + c / 2], 1);
+    }
+  };
+  if (!(pq > 0.0)) {
+    deactivate();
+    return;
+  }
+  const double al = s.rz[c] / pq;
+  double rr = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    X[i] += al * P[i];
+    R[i] -= al * Q[i];
+    rr += R[i] * R[i];
+  }
+  rr = block_sum2(rr, 0.0, scr).x;
+  int its = 0;
+  if (threadIdx.x == 0) {
+    its = SI[SI_CITS + c] + 1;
+    SI[SI_CITS + c] = its;
+    atomicAdd(&SI[SI_KRY], 1);
+  }
+  if (sqrt(rr) <= s.sd[SD_KTOL] * s.rhsn[c]) {
+    deactivate();
+    return;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tmp[i] = R[i] / s.diagG[i];
+  __syncthreads();
+  project_V(tmp, Z, s.maskF, s.nuhat, n, m, scr);
+  double rzn = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) rzn += R[i] * Z[i];
+  rzn = block_sum2(rzn, 0.0, scr).x;
+  const double beta = rzn / s.rz[c];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) P[i] = Z[i] + beta * P[i];
+  if (threadIdx.x == 0) {
+    s.rz[c] = rzn;
+    if (SI[SI_CITS + c] >= kmaxit) {
+      SI[SI_ACT + c] = 0;
+      atomicSub(&SI[SI_LIVE + c / 2], 1);
+    }
+  }
+}
+
+// Correction vector a = P_V (T^-1 A^T (psi''' o rhat)) and the second PCG round.
+static __global__ void __launch_bounds__(kVT) k_pcg_setup2(Inst s, int ca, int group) {
+  __shared__ double scr[80];
+  int* SI = s.si;
+  if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
+  const double m = (double)SI[SI_M];
+  project_V(s.at, s.Bv + (size_t)ca * s.ld, s.maskF, s.nuhat, s.n, m, scr);
+  pcg_init_col(s, ca, m, s.sd[SD_LAM], scr);
+  if (threadIdx.x == 0) {
+    SI[SI_LIVE + group] = SI[SI_ACT + ca];
+    SI[SI_THIRD] += 1;
+  }
+}
+
+// d = X_h - (||gbar|| / m) X_a - nu  (ambient; zero off F), re-centred on F so
+// that 1^T d = 0 to rounding relative to d.
+static __global__ void __launch_bounds__(kVT) k_assemble(Inst s, int ca) {
+  __shared__ double scr[80];
+  int* SI = s.si;
+  if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
+  const double m = (double)SI[SI_M];
+  const double coef = s.sd[SD_GN] / m;
+  const double* Xh = s.X;
+  const double* Xa = s.X + (size_t)ca * s.ld;
+  double sd = 0.0;
+  for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
+    const double v = i < s.n ? Xh[i] - coef * Xa[i] - s.nuhat[i] : 0.0;
+    s.d[i] = v;
+    sd += v;
+  }
+  const double md = block_sum2(sd, 0.0, scr).x / m;
+  for (int i = threadIdx.x; i < s.n; i += blockDim.x) s.d[i] -= s.maskF[i] * md;
+}
+
+// ----------------------------------------------- quartic step + boundary block
+inline __device__ void ls_coefficients(Inst& s, const double* spart, int G, const double* dir, double* coef, double* scr,
+                                double* ps) {
+  reduce_spart(spart, G, 12, s.sd[SD_INVT], ps);
+  double md = 0.0;
+  for (int i = threadIdx.x; i < s.n; i += blockDim.x) md += s.mu[i] * dir[i];
+  md = block_sum2(md, 0.0, scr).x;
+  if (threadIdx.x == 0) {
+    const double c1 = s.sd[SD_C1], c2 = s.sd[SD_C2], c3 = s.sd[SD_C3], c4 = s.sd[SD_C4];
+    // s20 s30 s40 s11 s21 s31 s02 s12 s22 s03 s13 s04
+    coef[0] = s.sd[SD_F];
+    coef[1] = -c1 * md + 2.0 * c2 * ps[3] - 3.0 * c3 * ps[4] + 4.0 * c4 * ps[5];
+    coef[2] = c2 * ps[6] - 3.0 * c3 * ps[7] + 6.0 * c4 * ps[8];
+    coef[3] = -c3 * ps[9] + 4.0 * c4 * ps[10];
+    coef[4] = c4 * ps[11];
+    for (int q = 0; q < 12; ++q) s.sd[SD_LS + q] = ps[q];
+    for (int q = 0; q < 5; ++q) s.sd[SD_COEF + q] = coef[q];
+  }
+  __syncthreads();
+}
+
+inline __device__ void take_step(Inst& s, const double* dir, double al, const double* xbar_or_null) {
+  const double tau = s.sd[SD_TAU], eps = s.sd[SD_EPSACT];
+  for (int i = threadIdx.x; i < s.n; i += blockDim.x) {
+    double v = xbar_or_null ? xbar_or_null[i] : s.x[i] + al * dir[i];
+    if (v - tau <= eps) v = tau;
+    s.x[i] = v;
+  }
+  __syncthreads();
+}
+
+// After the line-search pass along d: alpha_max, the damped nominal step
+// eta_k, and the branch of the boundary block (App. C.3).
+static __global__ void __launch_bounds__(kVT) k_decide1(Inst s, const double* spart, int G) {
+  __shared__ double scr[80];
+  __shared__ double ps[16];
+  __shared__ double coef[5];
+  int* SI = s.si;
+  double* SD = s.sd;
+  if (SI[SI_DONE] != 0) return;
+  const int n = s.n;
+  const double tau = SD[SD_TAU], eta = SD[SD_ETA];
+  ls_coefficients(s, spart, G, s.d, coef, scr, ps);
+  double am = INFINITY;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (s.d[i] < 0.0) am = fmin(am, (s.x[i] - tau) / (-s.d[i]));
+  am = block_min(am, scr);
+  double eta_k = fmin(eta, quartic_argmin(coef, eta));
+  if (threadIdx.x == 0) {
+    SD[SD_AMAX] = am;
+    SI[SI_SKIPLS] = 1;
+  }
+  if (am >= eta_k) {
+    const double al = quartic_argmin(coef, am);
+    take_step(s, s.d, al, nullptr);
+    if (threadIdx.x == 0) {
+      SD[SD_ALPHA] = al;
+      SI[SI_BRANCH] = BR_RAW;
+      SI[SI_BR_RAW] += 1;
+    }
+    return;
+  }
+  double gm = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) gm += s.g[i];
+  gm = block_sum2(gm, 0.0, scr).x / n;
+  double gt = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) gt += (s.g[i] - gm) * (s.g[i] - gm);
+  gt = sqrt(block_sum2(gt, 0.0, scr).x);
+  bool descent = false;
+  const int hmax = SI[SI_ARCMAX];
+  for (int h = 0; h <= hmax; ++h) {
+    const double th = slice_theta(s.x, s.d, eta_k, n, tau, scr);
+    double gd = 0.0, dd = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double xb = tau + fmax(s.x[i] + eta_k * s.d[i] - tau - th, 0.0);
+      const double db = xb - s.x[i];
+      gd += s.g[i] * db;
+      dd += db * db;
+    }
+    const double2 r = block_sum2(gd, dd, scr);
+    descent = r.x < -SD[SD_DESCEPS] * gt * sqrt(r.y);
+    if (descent || 0.5 * eta_k <= am) break;
+    eta_k *= 0.5;
+  }
+  if (threadIdx.x == 0) SD[SD_ETAK] = eta_k;
+  if (descent) {
+    const double th = slice_theta(s.x, s.d, eta_k, n, tau, scr);
+    for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
+      const double xb = i < n ? tau + fmax(s.x[i] + eta_k * s.d[i] - tau - th, 0.0) : 0.0;
+      s.xbar[i] = xb;
+      s.dstep[i] = i < n ? xb - s.x[i] : 0.0;
+    }
+    if (threadIdx.x == 0) {
+      SI[SI_BRANCH] = BR_SEGMENT;
+      SI[SI_BR_SEG] += 1;
+      SI[SI_SKIPLS] = 0;
+    }
+    return;
+  }
+  if (am > 0.0) {
+    const double al = quartic_argmin(coef, am);
+    take_step(s, s.d, al, nullptr);
+    if (threadIdx.x == 0) {
+      SD[SD_ALPHA] = al;
+      SI[SI_BRANCH] = BR_CAPPED;
+      SI[SI_BR_CAP] += 1;
+    }
+    return;
+  }
+  // Face hand-off: projected-gradient segment scaled to the YAND trial length.
+  double dn = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dn += s.d[i] * s.d[i];
+  dn = sqrt(block_sum2(dn, 0.0, scr).x);
+  const double sc = eta * dn / fmax(gt, 1e-300);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s.tmp[i] = -s.g[i];
+  __syncthreads();
+  const double th = slice_theta(s.x, s.tmp, sc, n, tau, scr);
+  double gd = 0.0;
+  for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
+    const double xb = i < n ? tau + fmax(s.x[i] + sc * s.tmp[i] - tau - th, 0.0) : 0.0;
+    s.xbar[i] = xb;
+    const double db = i < n ? xb - s.x[i] : 0.0;
+    s.dstep[i] = db;
+    if (i < n) gd += s.g[i] * db;
+  }
+  gd = block_sum2(gd, 0.0, scr).x;
+  if (threadIdx.x == 0) {
+    SI[SI_BRANCH] = BR_FACE;
+    SI[SI_BR_FACE] += 1;
+    SI[SI_SKIPLS] = gd < 0.0 ? 0 : 1;
+  }
+}
+
+// After the line-search pass along the segment: exact quartic on [0, 1].
+static __global__ void __launch_bounds__(kVT) k_decide2(Inst s, const double* spart, int G) {
+  __shared__ double scr[80];
+  __shared__ double ps[16];
+  __shared__ double coef[5];
+  if (s.si[SI_DONE] != 0 || s.si[SI_SKIPLS] != 0) return;
+  ls_coefficients(s, spart, G, s.dstep, coef, scr, ps);
+  const double al = quartic_argmin(coef, 1.0);
+  take_step(s, s.dstep, al, al == 1.0 ? s.xbar : nullptr);
+  if (threadIdx.x == 0) s.sd[SD_ALPHA] = al;
+}
+
+static __global__ void k_end_iter(Inst s) {
+  if (threadIdx.x != 0 || s.si[SI_DONE] != 0) return;
+  s.si[SI_ITER] += 1;
+  s.si[SI_PHASEIT] += 1;
+}
+
+}  // namespace mvsk

@@ -1,0 +1,207 @@
+// Single-CTA kernels for the O(n) logic of each YAND-MVSK iteration: the
+// projected-simplex KKT residual, the working face, PCG vector updates in the
+// ambient tangent space, and the boundary block of Alg. 1 / App. C.3.
+// One CTA of kVT threads holds one instance; n <= kMaxCols.
+#pragma once
+
+#include "common.cuh"
+
+namespace mvsk {
+
+constexpr int kVT = 1024;
+
+// ---------------------------------------------------------------- state slots
+// Per-instance scalar state (device memory): doubles sd[kSD], ints si[kSI].
+enum SD : int {
+  SD_F = 0, SD_KKT, SD_KKT0, SD_KKTREL, SD_BEST, SD_GN, SD_NUF, SD_LAM, SD_AMAX, SD_ETAK,
+  SD_ALPHA, SD_MUX, SD_TOL, SD_ETA, SD_TAU, SD_EPSACT, SD_RELRATIO, SD_REG, SD_KTOL, SD_C1,
+  SD_C2, SD_C3, SD_C4, SD_INVT, SD_DESCEPS, SD_STALLF, SD_SUMZ2,
+  SD_HIST = 32,   // 16-slot ring of kkt_rel (stall test)
+  SD_LS = 48,     // 12 power sums
+  SD_COEF = 60,   // A0..A4
+  kSD = 72
+};
+enum SI : int {
+  SI_DONE = 0,      // 0 running, 1 converged, 2 phase over, 3 non-finite
+  SI_ITER, SI_PHASEIT, SI_MAXIT, SI_M, SI_BRANCH, SI_SKIPDIR, SI_SKIPLS, SI_PCG, SI_STALLWIN,
+  SI_NREL, SI_KRY, SI_NCOL, SI_PROBES, SI_SEEDLO, SI_SEEDHI, SI_HISTN, SI_KMAXIT, SI_DIRONLY,
+  SI_PASSES, SI_HVPS, SI_THIRD, SI_BR_RAW, SI_BR_SEG, SI_BR_CAP, SI_BR_FACE, SI_ARCMAX,
+  SI_LIVE = 30,     // live-column count per PCG group (10 groups of two columns)
+  SI_ACT = 40,      // per-column active flags (20 columns)
+  SI_CITS = 60,     // per-column PCG iteration counts (20 columns)
+  kSI = 80
+};
+enum Branch : int { BR_NONE = 0, BR_RAW = 1, BR_SEGMENT = 2, BR_CAPPED = 3, BR_FACE = 4 };
+
+struct Inst {
+  double* sd;
+  int* si;
+  const double* mu;
+  double *x, *g, *z, *nuhat, *maskF, *d, *dstep, *xbar, *Gnu, *diagG, *at, *bestx, *rhat, *tmp;
+  double *X, *R, *Zc, *P, *Q, *Bv;  // PCG columns, [ncol][ld]
+  double *rz, *rhsn;
+  int n, ld;
+  long long T;
+};
+
+__device__ __forceinline__ double2 block_sum2(double a, double b, double* scr) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __syncthreads();
+  if (lane == 0) {
+    scr[warp] = a;
+    scr[32 + warp] = b;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double ta = lane < nw ? scr[lane] : 0.0, tb = lane < nw ? scr[32 + lane] : 0.0;
+    ta = warp_sum(ta);
+    tb = warp_sum(tb);
+    if (lane == 0) {
+      scr[64] = ta;
+      scr[65] = tb;
+    }
+  }
+  __syncthreads();
+  return make_double2(scr[64], scr[65]);
+}
+
+// Threshold theta of the projection onto Delta(tau) of v = base + s*dir
+// (dir may be null): Pi(v)_i = tau + max(v_i - tau - theta, 0).
+// Michelot (1986): iterate theta = (sum_{u_i > theta} u_i - b)/#{u_i > theta}
+// from the full set until the set stops shrinking.
+inline __device__ double slice_theta(const double* base, const double* dir, double s, int n, double tau, double* scr) {
+  const double b = 1.0 - (double)n * tau;
+  double su = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) su += (dir ? base[i] + s * dir[i] : base[i]) - tau;
+  double2 r = block_sum2(su, 0.0, scr);
+  double theta = (r.x - b) / (double)n;
+  double cnt = (double)n;
+  for (int it = 0; it <= n; ++it) {
+    double sa = 0.0, ka = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double u = (dir ? base[i] + s * dir[i] : base[i]) - tau;
+      if (u > theta) {
+        sa += u;
+        ka += 1.0;
+      }
+    }
+    r = block_sum2(sa, ka, scr);
+    if (r.y == cnt || r.y == 0.0) break;
+    cnt = r.y;
+    theta = (r.x - b) / cnt;
+  }
+  return theta;
+}
+
+// ||x - Pi(x - g)||_2 (projected-simplex KKT residual).
+inline __device__ double kkt_residual(const double* x, const double* g, int n, double tau, double* scr, double* tmp) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tmp[i] = x[i] - g[i];
+  __syncthreads();
+  const double th = slice_theta(tmp, nullptr, 0.0, n, tau, scr);
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double p = tau + fmax(tmp[i] - tau - th, 0.0);
+    const double e = x[i] - p;
+    s += e * e;
+  }
+  return sqrt(block_sum2(s, 0.0, scr).x);
+}
+
+// ------------------------------------------------------- exact quartic step
+__device__ __forceinline__ double dphi(const double* c, double a) {
+  return ((4.0 * c[4] * a + 3.0 * c[3]) * a + 2.0 * c[2]) * a + c[1];
+}
+__device__ __forceinline__ double decrease(const double* c, double a) {
+  return a * (c[1] + a * (c[2] + a * (c[3] + a * c[4])));
+}
+
+// Minimiser of A0 + A1 a + ... + A4 a^4 on [0, amax] (Prop. quartic exact line
+// search): candidates 0, amax and the real roots of phi' in (0, amax).  The
+// real roots of phi'' (cancellation-free quadratic formula) split the interval
+// into pieces on which phi' is monotone; a sign change brackets one root, found
+// by bisection down to adjacent doubles.  Ties keep the smallest alpha.
+inline __device__ double quartic_argmin(const double* c, double amax) {
+  if (!(amax > 0.0)) return 0.0;
+  double brk[4];
+  int nb = 0;
+  brk[nb++] = 0.0;
+  {
+    const double qa = 12.0 * c[4], qb = 6.0 * c[3], qc = 2.0 * c[2];
+    double r1 = NAN, r2 = NAN;
+    if (qa == 0.0) {
+      if (qb != 0.0) r1 = -qc / qb;
+    } else {
+      const double disc = qb * qb - 4.0 * qa * qc;
+      if (disc >= 0.0) {
+        const double q = -0.5 * (qb + copysign(sqrt(disc), qb));
+        r1 = q / qa;
+        r2 = (q != 0.0) ? qc / q : 0.0;
+      }
+    }
+    if (r1 > r2) {
+      const double t = r1;
+      r1 = r2;
+      r2 = t;
+    }
+    if (r1 > 0.0 && r1 < amax) brk[nb++] = r1;
+    if (r2 > 0.0 && r2 < amax && r2 != r1) brk[nb++] = r2;
+  }
+  brk[nb++] = amax;
+  double cand[6];
+  int nc = 0;
+  cand[nc++] = 0.0;
+  cand[nc++] = amax;
+  for (int k = 0; k + 1 < nb; ++k) {
+    const double lo = brk[k], hi = brk[k + 1];
+    const double flo = dphi(c, lo), fhi = dphi(c, hi);
+    if (flo == 0.0) { cand[nc++] = lo; continue; }
+    if (fhi == 0.0) { cand[nc++] = hi; continue; }
+    if ((flo < 0.0) == (fhi < 0.0)) continue;
+    double a = lo, b = hi;
+    for (int it = 0; it < 200; ++it) {
+      const double m = 0.5 * (a + b);
+      if (m <= a || m >= b) break;
+      const double fm = dphi(c, m);
+      if (fm == 0.0) { a = b = m; break; }
+      if ((fm < 0.0) == (flo < 0.0)) a = m; else b = m;
+    }
+    cand[nc++] = (a != b) ? 0.5 * (a + b) : a;
+  }
+  // sort ascending (tiny insertion sort), then keep the first strict minimum
+  for (int i = 1; i < nc; ++i) {
+    const double v = cand[i];
+    int j = i - 1;
+    while (j >= 0 && cand[j] > v) { cand[j + 1] = cand[j]; --j; }
+    cand[j + 1] = v;
+  }
+  double best_a = 0.0, best_v = 0.0;
+  for (int i = 0; i < nc; ++i) {
+    const double a = cand[i];
+    if (!(a >= 0.0 && a <= amax)) continue;
+    if (i > 0 && a == cand[i - 1]) continue;
+    const double v = decrease(c, a);
+    if (v < best_v) { best_a = a; best_v = v; }
+  }
+  return best_a;
+}
+
+// ------------------------------------------------- SplitMix64 normal probes
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long index) {
+  unsigned long long z = seed + (index + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Standard normal probe coordinate i of probe k at `iteration` (SplitMix64
+// stream per probe; Box-Muller cosine branch on two 53-bit uniforms).
+__device__ __forceinline__ double probe_value(unsigned long long seed, long long iteration, int k, int i) {
+  const unsigned long long ps = splitmix64(seed, (unsigned long long)iteration * 256ull + (unsigned long long)k);
+  const double u1 = ((double)(splitmix64(ps, 2ull * (unsigned long long)i) >> 11) + 1.0) * 0x1.0p-53;
+  const double u2 = ((double)(splitmix64(ps, 2ull * (unsigned long long)i + 1ull) >> 11) + 1.0) * 0x1.0p-53;
+  return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
+}  // namespace mvsk

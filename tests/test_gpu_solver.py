@@ -1,0 +1,151 @@
+"""GPU YAND-MVSK solves (C ABI) against the CPU oracle.
+
+FP64 path: under the convexity certificate the minimiser over Delta(tau) is
+unique, so the GPU and oracle solutions must agree to ||w - w*||_inf <= 1e-9
+when the reduced Hessian on the optimal face is well conditioned (its
+smallest eigenvalue is reported by the test on failure).  Mixed precision
+(BF16/FP32 direction passes, FP64 gradient/line search): the same KKT
+tolerance is met in FP64, hence the same minimiser to the same bound.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import panels
+from oracle import mvsk_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(n, T, seed, lam, panel="sector"):
+    if panel == "sector":
+        R = panels.sector_factor_panel(n, T, seed)
+    elif panel == "garch":
+        R = panels.garch_sector_panel(n, T, seed)
+    else:
+        R = panels.single_factor_panel(n, T, seed)
+    mu, A = O.centre(R)
+    c = O.scale_preferences(lam, A, "standardised")
+    return R, mu, A, c
+
+
+def _ctx(R, prec, lam, target=math.nan):
+    import paper_2604_25378_gb300 as m
+    ctx = m.MVSK(R, prec)
+    ctx.set_prefs(np.asarray(lam, float), target)
+    return ctx
+
+
+def _face_lmin(A, c, x):
+    sup = np.nonzero(x > 1e-8 + 1e-12)[0]
+    if sup.size < 2:
+        return math.inf
+    U = O.tangent_basis(sup.size)
+    G = O.gram(A, c, x)[np.ix_(sup, sup)]
+    return float(np.min(np.linalg.eigvalsh(U.T @ G @ U)))
+
+
+@pytest.mark.parametrize("n,T,seed,lam", [(20, 500, 0, (1, 1, 1, 1)), (60, 800, 42, (1, 1, 0.5, 2)),
+                                          (200, 2000, 1, (1, 1, 1, 1)), (7, 64, 3, (3, 1, 1, 1))])
+def test_pcg_fp64_matches_oracle(n, T, seed, lam):
+    R, mu, A, c = _problem(n, T, seed, lam, "single" if n == 20 else "sector")
+    x_ref, inf_ref = O.solve(A, mu, c, "pcg", 1e-10)
+    assert inf_ref.status == "converged"
+    ctx = _ctx(R, "fp64", lam)
+    w, info = ctx.solve(1, 1e-10)
+    assert info["status"] == "ok", info
+    assert info["kkt_rel"] <= 1e-10
+    assert abs(w.sum() - 1.0) <= 1e-12 and w.min() >= 1e-8
+    g = O.gradient(A, mu, c, w)
+    assert O.kkt_residual(w, g, 1e-8) <= 1e-10 * inf_ref.kkt0 * 1.0001
+    lmin = _face_lmin(A, c, x_ref)
+    assert np.max(np.abs(w - x_ref)) <= 1e-9, (np.max(np.abs(w - x_ref)), lmin)
+    assert info["f"] == pytest.approx(inf_ref.f, rel=1e-12, abs=1e-15)
+
+
+def test_pcg_direction_matches_oracle_step():
+    """One affine-normal direction (PCG, Hutchinson probes of the same
+    counter-based stream) at an interior point.  Finite-precision CG amplifies
+    rounding differences with the condition number of the preconditioned
+    system, so per-iteration parity is checked on the paper's stylised panel
+    (U[-0.1, 0.4], raw profile [1,10,1,10]), whose reduced Hessian is well
+    conditioned (Table ec-hessian-conditioning)."""
+    R = panels.uniform_panel(40, 252, 5)
+    mu, A = O.centre(R)
+    lam = (1.0, 10.0, 1.0, 10.0)
+    c = np.asarray(lam)
+    x = np.random.default_rng(2).dirichlet(np.ones(40) * 5)
+    import paper_2604_25378_gb300 as m
+    ctx = m.MVSK(R, "fp64")
+    ctx.set_option("pref_scaling", 0)
+    ctx.set_prefs(np.asarray(lam))
+    for it in (0, 3):
+        d_gpu = ctx.direction(x, 1, it)
+        F = np.ones(40, dtype=bool)
+        d_ref, _ = O.direction_pcg(A, c, A @ x, O.gradient(A, mu, c, x), F, 1e-4, O.Options(), it)
+        np.testing.assert_allclose(d_gpu, d_ref, rtol=0, atol=1e-8 * np.max(np.abs(d_ref)))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_mixed_precision_reaches_fp64_minimiser(prec):
+    R, mu, A, c = _problem(300, 3000, 7, (1, 1, 0.5, 2), "garch")
+    x_ref, inf_ref = O.solve(A, mu, c, "pcg", 1e-10)
+    ctx = _ctx(R, prec, (1, 1, 0.5, 2))
+    w, info = ctx.solve(1, 1e-10)
+    assert info["status"] == "ok", info
+    g = O.gradient(A, mu, c, w)
+    assert O.kkt_residual(w, g, 1e-8) <= 1e-10 * inf_ref.kkt0 * 1.0001
+    assert np.max(np.abs(w - x_ref)) <= 1e-9
+
+
+def test_nonconvex_preferences_reach_kkt_point():
+    """(1,1,2,0.5) lies outside the certificate: compare KKT and objective."""
+    R, mu, A, c = _problem(100, 1500, 11, (1, 1, 2, 0.5))
+    x_ref, inf_ref = O.solve(A, mu, c, "pcg", 1e-9)
+    ctx = _ctx(R, "fp64", (1, 1, 2, 0.5))
+    w, info = ctx.solve(1, 1e-9)
+    assert info["status"] == "ok"
+    g = O.gradient(A, mu, c, w)
+    assert O.kkt_residual(w, g, 1e-8) <= 1e-9 * inf_ref.kkt0 * 1.0001
+    if np.max(np.abs(w - x_ref)) > 1e-9:
+        assert O.objective(A, mu, c, w) == pytest.approx(inf_ref.f, rel=1e-6)
+
+
+def test_target_calibration_matches_oracle():
+    R, mu, A, c = _problem(80, 1200, 13, (1, 1, 1, 1))
+    target = panels.quantile_targets(R, [0.7])[0]
+    cc, x_ref, inf_ref, ev = O.calibrate_target(A, mu, c, target, "pcg", 1e-10)
+    ctx = _ctx(R, "fp64", (1, 1, 1, 1), target)
+    w, info = ctx.solve(1, 1e-10)
+    assert info["status"] == "ok"
+    assert abs(info["achieved_mean"] - target) <= 1e-9 * np.max(np.abs(mu))
+    assert info["c"][0] == pytest.approx(cc[0], rel=1e-6)
+    assert np.max(np.abs(w - x_ref)) <= 1e-7
+
+
+def test_warm_start_and_errors():
+    import paper_2604_25378_gb300 as m
+    R, mu, A, c = _problem(30, 400, 17, (1, 1, 1, 1))
+    ctx = m.MVSK(R, "fp64")
+    with pytest.raises(m.MvskError) as e:
+        ctx.solve(1, 1e-8)
+    assert e.value.status == 6  # ESTATE: prefs first
+    ctx.set_prefs(np.array([1.0, 1, 1, 1]))
+    w, info = ctx.solve(1, 1e-10)
+    w2, info2 = ctx.solve(1, 1e-10, w0=w)
+    assert info2["iters"] <= 1 and np.max(np.abs(w2 - w)) <= 1e-12
+    with pytest.raises(m.MvskError):
+        ctx.solve(1, 1e-8, w0=np.full(30, 0.5))
+    with pytest.raises(m.MvskError):
+        ctx.set_prefs(np.array([1.0, -1, 1, 1]))
+    with pytest.raises(m.MvskError):
+        ctx.set_option("no_such_option", 1.0)
+    ctx.set_option("pcg_max_iter", 2)
+    ctx.set_option("restart_iter", 1)
+    w3, info3 = ctx.solve(1, 1e-14)
+    assert info3["status"] == "not_converged"
+    bad = R.copy()
+    bad[3, 4] = np.nan
+    with pytest.raises(m.MvskError):
+        m.MVSK(bad, "fp64")
