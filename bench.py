@@ -1,0 +1,302 @@
+#!/usr/bin/env python
+"""YAND-MVSK throughput on GB300: solves/s to kkt_rel <= 1e-8 at n=5440, T=12000.
+
+One step = one batched frontier sweep: B = 64 instances (16 return targets x 4
+preference vectors (1, 1, l3, l4), l3, l4 in {0.5, 2}) on one synthetic
+fat-tailed GARCH factor panel, every instance solved from x0 = 1/n with its
+mean coefficient calibrated to its target, through the library's C ABI.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own copy
+of the batch (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("solves/sec to rel ‖∇f‖≤1e-8 at n=5440,T=12000 "
+          "(batched mixed vs plain FP64); HBM GB/s")
+WORKLOAD = "c4_batch_n5440_T12000"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
+    ap.add_argument("--batch", type=int, default=64, help="instances per step (<= 64)")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-its", type=int, default=1)
+    return ap.parse_args()
+
+
+def dist_init(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def instances(batch):
+    import panels
+    R, lams, tg = panels.workload(WORKLOAD)
+    lam_b, tg_b = [], []
+    for l in lams:
+        for t in tg:
+            lam_b.append(l)
+            tg_b.append(t)
+    import numpy as np
+    return R, np.asarray(lam_b)[:batch], np.asarray(tg_b)[:batch]
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_2604_25378_gb300 as m
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    R, lam_b, tg_b = instances(args.batch)
+    B = len(lam_b)
+    Rd = torch.from_numpy(R).cuda()
+    ctx = m.MVSK(Rd, args.precision)
+    out = torch.empty((B, R.shape[1]), dtype=torch.float64, device="cuda")
+
+    def step():
+        return ctx.solve_batch(lam_b, tg_b, m.PCG, args.tol, out=out)
+
+    for _ in range(args.warmup):
+        _, infos = step()
+    torch.cuda.synchronize()
+    bad = [i for i in infos if i["status"] != "ok" or i["kkt_rel"] > args.tol]
+    sampler = ClockSampler(torch.cuda.current_device())
+    ctx.profile_enable(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    iters = []
+    for _ in range(args.steps):
+        _, infos = step()
+        iters.append(sum(i["iters"] for i in infos))
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    prof, launches = ctx.profile_read()
+    ctx.profile_enable(False)
+    ms_max = max_over_ranks(ms, world)
+    value = B * args.steps * world / (ms_max / 1e3)
+
+    # Roofline of the dominant pass kind (live CUDA-event durations of the timed steps).
+    dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"]) if prof else None
+    pk, pk_src = peaks()
+    roof = None
+    if dom is not None:
+        name, d = dom
+        avg_s = d["total_ms"] / d["launches"] / 1e3
+        ach = d["bytes_per_launch"] / avg_s / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": round(ach / pk["hbm_gbs"], 4), "traffic": None,
+                "peak_source": pk_src, "launches": d["launches"],
+                "avg_us": round(avg_s * 1e6, 2),
+                "share_of_passes": round(d["total_ms"] / sum(v["total_ms"] for v in prof.values()), 4),
+                "share_of_step": round(d["total_ms"] / ms, 4)}
+        if "fp64" in name:
+            roof["bound"] = "alu"
+            roof["unit"] = "TFLOP/s"
+            flops = 2.0 * R.shape[0] * R.shape[1] * (2 if "valgrad" in name or "hvp" in name else 1)
+            roof["achieved"] = round(flops / avg_s / 1e12, 4)
+            roof["peak"] = 1.25
+            roof["frac"] = round(roof["achieved"] / 1.25, 4)
+            roof["peak_source"] = "nominal GB300 FP64 rate (no measured FP64 peak)"
+
+    e2e = None
+    if not args.no_e2e:
+        # Same metric through the public API with host buffers: pinned R in,
+        # weights out, every step (context creation = H2D copy + centring).
+        Rh = torch.from_numpy(R).pin_memory()
+        Wh = torch.empty((B, R.shape[1]), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            c2 = m.MVSK(Rh, args.precision)
+            c2.solve_batch(lam_b, tg_b, m.PCG, args.tol, out=Wh)
+            c2.close()
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": B * args.steps * world / dt, "unit": "solves/s",
+               "h2d_bytes_per_step": int(R.nbytes + lam_b.nbytes + tg_b.nbytes),
+               "d2h_bytes_per_step": int(Wh.numel() * 8)}
+
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f64" if args.precision == "bf16" else
+            ("fp32+f64" if args.precision == "fp32" else "f64"), "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": R.shape[1], "T": R.shape[0], "instances_per_gpu": B,
+                       "targets": 16, "preference_vectors": 4, "configuration": "pcg",
+                       "precision": args.precision, "tol": args.tol, "start": "1/n (cold)",
+                       "l2": "inputs larger than L2: A is 522 MB FP64 + 131 MB BF16",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "clocks": clocks,
+            "solve_iterations_per_step": statistics.mean(iters) if iters else None,
+            "unconverged_instances": len(bad)}
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args, R, lam_b, tg_b, statistics.mean(iters) / B)
+    line["passes"] = {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3)} for k, v in prof.items()}
+    return line
+
+
+def cpu_baseline(args, R, lam_b, tg_b, iters_per_solve):
+    """The oracle, as it stands, on the host cores: a bounded sample of the
+    same workload (a few YAND iterations of instance 0 at its calibrated c1
+    guess), scaled to solves/s by the GPU's iterations per solve."""
+    import numpy as np
+
+    from oracle import mvsk_oracle as O
+    mu, A = O.centre(R)
+    c = O.scale_preferences(lam_b[0], A, "standardised")
+    its = max(1, args.cpu_sample_its)
+    opts = O.Options(pcg_max_iter=its, restarts=())
+    t0 = time.perf_counter()
+    O.solve(A, mu, c, "pcg", args.tol, opts=opts)
+    dt = time.perf_counter() - t0
+    per_it = dt / (its + 1)
+    return {"value": 1.0 / (per_it * iters_per_solve), "unit": "solves/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{its} PCG YAND iteration(s) + final evaluation of instance 0 on the n=5440, T=12000 "
+                      f"panel ({dt:.1f} s, numpy FP64 with its default BLAS threads), scaled by the GPU's "
+                      f"{iters_per_solve:.1f} iterations per calibrated solve"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    R, lam_b, tg_b = instances(args.batch)
+    cb = None
+    times = []
+    for _ in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(args, R, lam_b, tg_b, iters_per_solve=90.0)
+        times.append(time.perf_counter() - t0)
+    v = cb["value"]
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": R.shape[1], "T": R.shape[0], "instances_per_gpu": len(lam_b),
+                       "configuration": "pcg", "precision": "fp64 (CPU oracle)", "tol": args.tol},
+            "cpu_baseline": {**cb, "value": v},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "note": "the CPU oracle timed on a bounded sample per step (90 iterations per calibrated solve "
+                    "assumed for scaling)"}
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args.gpus)
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -185,6 +185,26 @@ mvsk_status mvsk_project_slice(mvsk_ctx* ctx, const double* v, double tau, doubl
  * routine the solver uses (candidates: 0, amax, real roots of the cubic). */
 mvsk_status mvsk_quartic_argmin(mvsk_ctx* ctx, const double coef[5], double amax, double* alpha);
 
+/*
+ * Profiling of the streaming passes over A (tracing, no effect on results).
+ * mvsk_profile_enable(ctx, 1) clears the counters and brackets every later
+ * pass launch with CUDA events on the context's stream; (ctx, 0) stops.
+ * mvsk_profile_read fills up to `max` entries, one per pass kind: its label,
+ * launches, summed device time (ms) and algorithmic bytes per launch (one
+ * read of A: T * n * element size).  *count receives the number of kinds and
+ * *kernel_launches every kernel launch the library issued since enabling.
+ */
+typedef struct {
+  char name[56];
+  int64_t launches;
+  double total_ms;
+  double bytes_per_launch;
+} mvsk_prof_entry;
+
+mvsk_status mvsk_profile_enable(mvsk_ctx* ctx, int32_t on);
+mvsk_status mvsk_profile_read(mvsk_ctx* ctx, mvsk_prof_entry* out, int32_t max, int32_t* count,
+                              int64_t* kernel_launches);
+
 /* Thread-local message describing the last failure of any call. */
 const char* mvsk_last_error(const mvsk_ctx* ctx);
 

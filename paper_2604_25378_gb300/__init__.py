@@ -50,6 +50,11 @@ class Info(ctypes.Structure):
         return d
 
 
+class ProfEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 56), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("bytes_per_launch", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "mvsk_create": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32,
@@ -67,6 +72,8 @@ _SIGS = {
     "mvsk_oracle_direction": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int32, _P]),
     "mvsk_project_slice": (ctypes.c_int, [_P, _P, ctypes.c_double, _P]),
     "mvsk_quartic_argmin": (ctypes.c_int, [_P, _P, ctypes.c_double, _P]),
+    "mvsk_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "mvsk_profile_read": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
     "mvsk_last_error": (ctypes.c_char_p, [_P]),
     "mvsk_destroy": (None, [_P]),
 }
@@ -225,6 +232,21 @@ class MVSK:
         out = np.empty(self.n)
         self._check(self._lib.mvsk_project_slice(self._h, pv, float(tau), out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+    def profile_enable(self, on: bool = True):
+        self._check(self._lib.mvsk_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """({kind: {launches, total_ms, bytes_per_launch}}, kernel launches since enabling)."""
+        buf = (ProfEntry * 64)()
+        cnt = ctypes.c_int32()
+        nl = ctypes.c_int64()
+        self._check(self._lib.mvsk_profile_read(self._h, buf, 64, ctypes.byref(cnt), ctypes.byref(nl)))
+        out = {}
+        for e in buf[:cnt.value]:
+            out[e.name.decode()] = {"launches": e.launches, "total_ms": e.total_ms,
+                                    "bytes_per_launch": e.bytes_per_launch}
+        return out, nl.value
 
     def quartic_argmin(self, coef, amax):
         coef = np.ascontiguousarray(coef, dtype=np.float64)

@@ -63,6 +63,12 @@ struct mvsk_ctx {
   double mu_absmax = 0.0;
   Options opt;
   std::vector<void*> allocs;
+  // profiling of the streaming passes
+  bool prof_on = false;
+  long long launches = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_kind;  // kind id per event pair
+  size_t ev_used = 0;
 };
 
 namespace {
@@ -295,6 +301,23 @@ mvsk_status run_pass(mvsk_ctx* c, int prec, int mode, int nin, PassArgs a, const
   a.err = c->err;
   a.live = live;
   a.counter = c->si + SI_PASSES;
+  c->launches += 1;
+  if (c->prof_on) {
+    if (c->ev_used + 2 > c->ev_pool.size()) {
+      for (int q = 0; q < 512; ++q) {
+        cudaEvent_t e;
+        CU(cudaEventCreate(&e));
+        c->ev_pool.push_back(e);
+      }
+    }
+    const int kind = (prec * 16 + mode) * 8 + nin;
+    c->ev_kind.push_back(kind);
+    CU(cudaEventRecord(c->ev_pool[c->ev_used], c->stream));
+    CU(rowpass_launch(prec, mode, nin, a, c->grid, smem, c->stream));
+    CU(cudaEventRecord(c->ev_pool[c->ev_used + 1], c->stream));
+    c->ev_used += 2;
+    return MVSK_OK;
+  }
   CU(rowpass_launch(prec, mode, nin, a, c->grid, smem, c->stream));
   return MVSK_OK;
 }
@@ -303,6 +326,7 @@ mvsk_status reduce_cols(mvsk_ctx* c, int prec, int nout, double* out, size_t str
                         const int* skip, const int* live) {
   dim3 g((c->ld + 255) / 256, nout);
   const double sc = 1.0 / (double)c->T;
+  c->launches += 1;
   if (prec == P64)
     k_reduce_cols<double><<<g, 256, 0, c->stream>>>((const double*)c->part, c->grid, nout, c->ld, c->n, sc, bias, bscale,
                                                     out, stride, skip, live);
@@ -363,6 +387,7 @@ mvsk_status direction_pcg(mvsk_ctx* c) {
   }
   k_pcg_setup<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid, ngroups);
   CU(cudaGetLastError());
+  c->launches += 3 + 2 * kmax;  // setup, setup2, assemble, the pcg_step launches
   for (int it = 0; it < kmax; ++it) {
     for (int g = 0; g < ngroups; ++g) {
       const int c0 = 2 * g;
@@ -428,6 +453,7 @@ mvsk_status launch_iteration(mvsk_ctx* c, int cfg) {
   TRY(pass_valgrad(c, s.x, s.z, s.g, done));
   k_face<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid);
   CU(cudaGetLastError());
+  c->launches += 5;  // k_face, k_decide1, k_decide2, k_end_iter (+1 below)
   TRY(direction(c, cfg));
   TRY(pass_ls(c, s.d, done));
   k_decide1<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid);
@@ -985,6 +1011,7 @@ mvsk_status mvsk_oracle_direction(mvsk_ctx* c, mvsk_config cfg, const double* w,
   TRY(pass_valgrad(c, s.x, s.z, s.g, nullptr));
   k_face<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid);
   CU(cudaGetLastError());
+  c->launches += 5;  // k_face, k_decide1, k_decide2, k_end_iter (+1 below)
   TRY(direction(c, cfg));
   TRY(download_vec(c, d_out, s.d, c->n));
   return sync(c);
@@ -1011,6 +1038,53 @@ mvsk_status mvsk_quartic_argmin(mvsk_ctx* c, const double coef[5], double amax, 
   return sync(c);
 }
 
+mvsk_status mvsk_profile_enable(mvsk_ctx* c, int32_t on) {
+  if (c == nullptr) return fail(MVSK_EINVAL, "null context");
+  CU(cudaStreamSynchronize(c->stream));
+  c->prof_on = on != 0;
+  if (on) {
+    c->ev_used = 0;
+    c->ev_kind.clear();
+    c->launches = 0;
+  }
+  return MVSK_OK;
+}
+
+mvsk_status mvsk_profile_read(mvsk_ctx* c, mvsk_prof_entry* out, int32_t max, int32_t* count, int64_t* kernel_launches) {
+  if (c == nullptr) return fail(MVSK_EINVAL, "null context");
+  CU(cudaStreamSynchronize(c->stream));
+  struct Agg {
+    int kind;
+    long long n;
+    double ms;
+  };
+  std::vector<Agg> agg;
+  for (size_t q = 0; q < c->ev_kind.size(); ++q) {
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, c->ev_pool[2 * q], c->ev_pool[2 * q + 1]));
+    const int k = c->ev_kind[q];
+    size_t a = 0;
+    while (a < agg.size() && agg[a].kind != k) ++a;
+    if (a == agg.size()) agg.push_back({k, 0, 0.0});
+    agg[a].n += 1;
+    agg[a].ms += ms;
+  }
+  static const char* modes[] = {"valgrad", "fwd", "hvp", "hvpdiag", "third", "rhat", "back", "ls"};
+  static const char* precs[] = {"fp64", "bf16", "fp32"};
+  static const double esz[] = {8.0, 2.0, 4.0};
+  const int nk = (int)agg.size();
+  for (int a = 0; a < nk && a < max; ++a) {
+    const int prec = agg[a].kind / 128, mode = (agg[a].kind / 8) % 16, nin = agg[a].kind % 8;
+    snprintf(out[a].name, sizeof(out[a].name), "rowpass_%s_%s_%d", precs[prec], modes[mode], nin);
+    out[a].launches = agg[a].n;
+    out[a].total_ms = agg[a].ms;
+    out[a].bytes_per_launch = (double)c->T * (double)c->n * esz[prec];
+  }
+  if (count) *count = nk;
+  if (kernel_launches) *kernel_launches = c->launches;
+  return MVSK_OK;
+}
+
 const char* mvsk_last_error(const mvsk_ctx*) { return g_err; }
 
 void mvsk_destroy(mvsk_ctx* c) {
@@ -1018,6 +1092,7 @@ void mvsk_destroy(mvsk_ctx* c) {
   if (c->stream != nullptr) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   for (void* p : c->allocs) cudaFree(p);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }
 
