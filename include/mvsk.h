@@ -148,6 +148,30 @@ mvsk_status mvsk_solve_batch(mvsk_ctx* ctx, mvsk_config cfg, int32_t B, const do
  */
 mvsk_status mvsk_eval(mvsk_ctx* ctx, const double* w, double* f, double* grad, double* kkt);
 
+/*
+ * mvsk_eval_noalloc -- f(x), grad f(x) and z = A x for callers that cannot
+ *   allocate GPU memory.  The paper has no counterpart: it serves code that
+ *   must not call cudaMalloc (a fixed memory budget, a steady-state loop of a
+ *   larger framework that owns the allocator) and has only its own buffers.
+ *   It runs the value/gradient pass of mvsk_eval; its scratch lives in one
+ *   static device array of 8 MiB that every GPU loading the library keeps
+ *   until the process exits.  It calls no cudaMalloc/cudaFree and no
+ *   allocating library routine.
+ *   A: device, centred returns T x ld row-major FP64 (columns n..ld-1 zero),
+ *   16-byte aligned, n <= ld <= 6144, ld even; mu: device, n values; c: host,
+ *   4 coefficients; x: device, n values.  Outputs (device): z (T values),
+ *   g (n values), f (1 value).  Work is issued on `stream` (a cudaStream_t,
+ *   NULL = legacy default) and the call returns after it has finished.
+ *   The first call on each device fetches the array's device address with
+ *   cudaGetSymbolAddress (make that first call before any stream capture).
+ *   All calls share the array: calls that overlap on the GPU (other streams
+ *   or threads) race and must be serialised by the caller.  Errors: EINVAL
+ *   for sizes beyond the limits above (the message says which), ECUDA.
+ */
+mvsk_status mvsk_eval_noalloc(const double* A, const double* mu, int64_t T, int64_t n, int64_t ld,
+                              const double c[4], const double* x, double* z, double* g, double* f,
+                              void* stream);
+
 /* Oracle exports (the same kernels as the solver, for parity checks). The
  * copy of A they read is chosen by option "oracle_prec". */
 

@@ -16,7 +16,7 @@ import os
 
 import numpy as np
 
-__all__ = ["load", "MVSK", "MvskError", "DIRECT", "PCG", "PREC", "lib_path"]
+__all__ = ["load", "MVSK", "MvskError", "DIRECT", "PCG", "PREC", "lib_path", "eval_noalloc"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 lib_path = os.path.join(_HERE, "lib", "libmvsk.so")
@@ -72,6 +72,8 @@ _SIGS = {
     "mvsk_oracle_direction": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int32, _P]),
     "mvsk_project_slice": (ctypes.c_int, [_P, _P, ctypes.c_double, _P]),
     "mvsk_quartic_argmin": (ctypes.c_int, [_P, _P, ctypes.c_double, _P]),
+    "mvsk_eval_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P,
+                                         _P, _P]),
     "mvsk_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "mvsk_profile_read": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
     "mvsk_last_error": (ctypes.c_char_p, [_P]),
@@ -112,6 +114,19 @@ def _like(x, n_or_shape):
         import torch
         return torch.empty(shape, dtype=torch.float64, device=x.device)
     return np.empty(shape, dtype=np.float64)
+
+
+def eval_noalloc(A, mu, c, x, z, g, f, stream=0):
+    """f, grad f and z = A x into caller buffers (torch CUDA float64 tensors),
+    through mvsk_eval_noalloc: the library allocates no GPU memory for it."""
+    lib = load()
+    T, ld = A.shape
+    n = mu.shape[0]
+    cc = np.ascontiguousarray(c, dtype=np.float64)
+    st = lib.mvsk_eval_noalloc(_ptr(A)[0], _ptr(mu)[0], T, n, ld, cc.ctypes.data_as(ctypes.c_void_p), _ptr(x)[0],
+                               _ptr(z)[0], _ptr(g)[0], _ptr(f)[0], ctypes.c_void_p(stream))
+    if st != 0:
+        raise MvskError(st, (lib.mvsk_last_error(None) or b"").decode())
 
 
 class MVSK:

@@ -26,6 +26,9 @@ cudaError_t rowpass_launch_f64(int mode, int nin, const PassArgs& a, int grid, s
 cudaError_t rowpass_launch_f32(int mode, int nin, const PassArgs& a, int grid, size_t smem, cudaStream_t st);
 cudaError_t rowpass_launch_bf16(int mode, int nin, const PassArgs& a, int grid, size_t smem, cudaStream_t st);
 
+// Text returned by mvsk_last_error (thread-local).
+void set_last_error(const char* msg);
+
 constexpr size_t kSmemBudget = 225 * 1024;  // dynamic; static shared memory needs the rest of 227 KB
 
 }  // namespace mvsk

@@ -1100,6 +1100,8 @@ void mvsk_destroy(mvsk_ctx* c) {
 
 namespace mvsk {
 
+void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 size_t rowpass_smem(int prec, int mode, int nin, int ld, int* stages) {
   if (prec == P64) return rowpass_smem_f64(mode, nin, ld, stages);
   if (prec == P16) return rowpass_smem_bf16(mode, nin, ld, stages);
