@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "dense.cuh"
 #include "internal.h"
 #include "mvsk.h"
 #include "solver_kernels.cuh"
@@ -66,6 +67,10 @@ struct mvsk_ctx {
   // profiling of the streaming passes
   bool prof_on = false;
   long long launches = 0;
+  // dense buffers of the direct configuration (allocated at its first use)
+  double *Gm = nullptr, *Bm = nullptr, *Ub = nullptr, *Rb = nullptr, *Pb = nullptr, *GC = nullptr, *Yb = nullptr;
+  double* dvec = nullptr;
+  int* dflag = nullptr;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_kind;  // kind id per event pair
   size_t ev_used = 0;
@@ -440,9 +445,9 @@ mvsk_status direction_pcg(mvsk_ctx* c) {
   return MVSK_OK;
 }
 
-}  // namespace
-mvsk_status direction_direct(mvsk_ctx* c);  // direct.cu
-namespace {
+mvsk_status read_ints(mvsk_ctx* c, int* dst, int first, int count);
+
+#include "direct_impl.cuh"
 
 mvsk_status direction(mvsk_ctx* c, int cfg) { return cfg == MVSK_PCG ? direction_pcg(c) : direction_direct(c); }
 
@@ -975,6 +980,18 @@ mvsk_status mvsk_oracle_third(mvsk_ctx* c, const double* w, const double* u, con
   TRY(run_pass(c, c->opt.oracle_prec, M_THIRD, 2, a));
   TRY(reduce_cols(c, c->opt.oracle_prec, 1, s.at, c->ld, nullptr, 0.0, nullptr, nullptr));
   TRY(download_vec(c, out, s.at, c->n));
+  return sync(c);
+}
+
+mvsk_status mvsk_oracle_gram(mvsk_ctx* c, const double* w, double* G) {
+  if (c == nullptr || w == nullptr || G == nullptr) return fail(MVSK_EINVAL, "null argument");
+  if (!c->prefs_set) return fail(MVSK_ESTATE, "mvsk_set_prefs must come first");
+  Inst& s = c->in;
+  TRY(upload_vec(c, s.x, w, c->n));
+  TRY(pass_fwd_z(c, s.x, s.z));
+  TRY(gram_into(c, s.z));
+  CU(cudaMemcpy2DAsync(G, sizeof(double) * c->n, c->Gm, sizeof(double) * c->ld, sizeof(double) * c->n, c->n,
+                       cudaMemcpyDefault, c->stream));
   return sync(c);
 }
 
