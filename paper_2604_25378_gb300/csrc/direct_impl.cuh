@@ -169,12 +169,19 @@ mvsk_status ensure_direct_buffers(mvsk_ctx* c) {
   return MVSK_OK;
 }
 
-// Weighted Gram G = T^-1 A^T Diag(psi''(z)) A into c->Gm (ld x ld, n x n used).
-mvsk_status gram_into(mvsk_ctx* c, const double* z) {
+// Weighted Gram G = T^-1 A^T Diag(psi''(z)) A into c->Gm (ld x ld, n x n used):
+// FP64 SIMT from the FP64 master copy, or BF16 x BF16 -> FP32 on the tensor
+// cores (tcgen05) from A^T and (Diag(psi'') A)^T in BF16 when prec = P16.
+mvsk_status gram_into(mvsk_ctx* c, const double* z, int prec) {
   TRY(ensure_direct_buffers(c));
   c->launches += 1;
   k_psi2_vec<<<4 * c->nsm, 256, 0, c->stream>>>(z, c->T, c->c[1], c->c[2], c->c[3], c->dvec);
   CU(cudaGetLastError());
+  if (prec == P16) {
+    TRY(ensure_tc_operands(c));
+    TRY(transpose_bf16(c, c->dvec, c->W16T));
+    return gemm_tc_f64(c, c->A16T, c->n, c->W16T, c->n, c->T, c->Tp, 1.0 / (double)c->T, c->Gm, c->ld);
+  }
   return gemm64(c, true, true, c->n, c->n, (int)c->T, 1.0 / (double)c->T, c->A64, c->ld, c->A64, c->ld, c->dvec, 0.0,
                 c->Gm, c->ld);
 }
@@ -213,7 +220,7 @@ mvsk_status direction_direct(mvsk_ctx* c) {
   TRY(read_ints(c, h2 + 1, SI_SKIPDIR, 1));
   if (h2[0] != 0 || h2[1] != 0) return MVSK_OK;
   const int n = c->n, ld = c->ld;
-  TRY(gram_into(c, s.z));
+  TRY(gram_into(c, s.z, c->dir_prec == P16 ? P16 : P64));
   // G C (two columns: 1_F/sqrt(m) and nu); the mask vector is 1_F
   const int mvb = (n * 32 + 255) / 256;
   k_matvec<<<mvb, 256, 0, c->stream>>>(c->Gm, ld, n, s.maskF, s.maskF, c->GC);

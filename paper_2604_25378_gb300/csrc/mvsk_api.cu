@@ -10,7 +10,10 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "dense.cuh"
+#include "gemm_tc.cuh"
 #include "internal.h"
 #include "mvsk.h"
 #include "solver_kernels.cuh"
@@ -71,6 +74,10 @@ struct mvsk_ctx {
   double *Gm = nullptr, *Bm = nullptr, *Ub = nullptr, *Rb = nullptr, *Pb = nullptr, *GC = nullptr, *Yb = nullptr;
   double* dvec = nullptr;
   int* dflag = nullptr;
+  // K-major BF16 operands of the tensor-core products (n x Tp, Tp = T rounded up to 8)
+  __nv_bfloat16* A16T = nullptr;
+  __nv_bfloat16* W16T = nullptr;
+  long long Tp = 0;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_kind;  // kind id per event pair
   size_t ev_used = 0;
@@ -446,6 +453,100 @@ mvsk_status direction_pcg(mvsk_ctx* c) {
 }
 
 mvsk_status read_ints(mvsk_ctx* c, int* dst, int first, int count);
+
+// ------------------------------------------------ tensor-core helpers
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (fn == nullptr) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2-D BF16 tensor map over a row-major (outer x inner) array with 128-byte swizzle.
+mvsk_status make_tmap_bf16(CUtensorMap* tm, const void* base, unsigned long long inner, unsigned long long outer,
+                           unsigned long long row_bytes, unsigned box_inner, unsigned box_outer) {
+  auto enc = tmap_encoder();
+  if (enc == nullptr) return fail(MVSK_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (row_bytes & 15) != 0)
+    return fail(MVSK_EINVAL, "tensor map base/stride not 16-byte aligned");
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(MVSK_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return MVSK_OK;
+}
+
+// out[j*ldo + t] = bf16(sc_t * A[t*lda + j]) for j < n, t < T; zero for T <= t < Tp.
+__global__ void k_transpose_bf16(const double* A, int lda, long long T, int n, const double* sc, __nv_bfloat16* out,
+                                 long long ldo, long long Tp) {
+  __shared__ float tile[32][33];
+  const long long t0 = (long long)blockIdx.x * 32;
+  const int j0 = blockIdx.y * 32;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const long long t = t0 + threadIdx.y + 8 * k;
+    const int j = j0 + threadIdx.x;
+    double v = 0.0;
+    if (t < T && j < n) v = A[(size_t)t * lda + j] * (sc != nullptr ? sc[t] : 1.0);
+    tile[threadIdx.y + 8 * k][threadIdx.x] = (float)v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int j = j0 + threadIdx.y + 8 * k;
+    const long long t = t0 + threadIdx.x;
+    if (j < n && t < Tp) out[(size_t)j * ldo + t] = __float2bfloat16(tile[threadIdx.x][threadIdx.y + 8 * k]);
+  }
+}
+
+mvsk_status transpose_bf16(mvsk_ctx* c, const double* sc, __nv_bfloat16* out) {
+  dim3 g((unsigned)((c->Tp + 31) / 32), (unsigned)((c->n + 31) / 32));
+  k_transpose_bf16<<<g, dim3(32, 8), 0, c->stream>>>(c->A64, c->ld, c->T, c->n, sc, out, c->Tp, c->Tp);
+  c->launches += 1;
+  CU(cudaGetLastError());
+  return MVSK_OK;
+}
+
+mvsk_status ensure_tc_operands(mvsk_ctx* c) {
+  if (c->A16T != nullptr) return MVSK_OK;
+  c->Tp = (c->T + 7) / 8 * 8;
+  void* p;
+  TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * (size_t)c->n * c->Tp));
+  c->A16T = (__nv_bfloat16*)p;
+  TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * (size_t)c->n * c->Tp));
+  c->W16T = (__nv_bfloat16*)p;
+  return transpose_bf16(c, nullptr, c->A16T);
+}
+
+// C (M x N, FP64, ldc) = alpha * A B^T with A (M x K) and B (N x K) K-major BF16 (row bytes rb).
+mvsk_status gemm_tc_f64(mvsk_ctx* c, const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N, long long K,
+                        long long ldk, double alpha, double* C, long long ldc) {
+  CUtensorMap ta, tb;
+  TRY(make_tmap_bf16(&ta, A, (unsigned long long)ldk, (unsigned long long)M, (unsigned long long)ldk * 2, kTcBK, kTcBM));
+  TRY(make_tmap_bf16(&tb, B, (unsigned long long)ldk, (unsigned long long)N, (unsigned long long)ldk * 2, kTcBK, 128));
+  auto kern = k_gemm_tc<128, EpiStoreF64>;
+  static bool attr = false;
+  const size_t smem = tc_smem_bytes<128>();
+  if (!attr) {
+    CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  EpiStoreF64 epi{C, ldc, alpha, M, N};
+  dim3 grid((unsigned)((N + 127) / 128), (unsigned)((M + kTcBM - 1) / kTcBM));
+  kern<<<grid, 128, smem, c->stream>>>(ta, tb, M, N, (int)K, epi, c->err);
+  c->launches += 1;
+  CU(cudaGetLastError());
+  return MVSK_OK;
+}
 
 #include "direct_impl.cuh"
 
@@ -989,7 +1090,7 @@ mvsk_status mvsk_oracle_gram(mvsk_ctx* c, const double* w, double* G) {
   Inst& s = c->in;
   TRY(upload_vec(c, s.x, w, c->n));
   TRY(pass_fwd_z(c, s.x, s.z));
-  TRY(gram_into(c, s.z));
+  TRY(gram_into(c, s.z, c->opt.oracle_prec == 1 ? P16 : P64));
   CU(cudaMemcpy2DAsync(G, sizeof(double) * c->n, c->Gm, sizeof(double) * c->ld, sizeof(double) * c->n, c->n,
                        cudaMemcpyDefault, c->stream));
   return sync(c);

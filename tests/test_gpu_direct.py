@@ -79,3 +79,24 @@ def test_direct_target_sweep_c2():
         assert info["status"] == "ok"
         assert abs(info["achieved_mean"] - target) <= 1e-9 * np.max(np.abs(mu))
         assert np.max(np.abs(w - x_ref)) <= 1e-7
+
+
+@pytest.mark.parametrize("n,T", [(300, 3001), (20, 500), (3, 40), (129, 64)])
+def test_gram_bf16_tensor_cores(n, T):
+    """tcgen05 BF16 x BF16 -> FP32 Gram against the FP64 oracle: the operands A
+    and Diag(psi'')A are rounded to BF16 (2^-9 relative), so the bound is
+    2e-2 * (|A|^T |D| |A| / T)."""
+    R = panels.sector_factor_panel(n, T, 5) if n >= 5 else panels.single_factor_panel(n, T, 5)
+    mu, A = O.centre(R)
+    lam = (1.0, 1.0, 0.5, 2.0)
+    c = O.scale_preferences(lam, A, "standardised")
+    x = np.random.default_rng(1).dirichlet(np.ones(n))
+    ctx = _ctx(R, "bf16", lam)
+    ctx.set_option("oracle_prec", 1)
+    G = ctx.gram(x)
+    D = O.d2psi(c, A @ x)
+    scale = np.abs(A).T @ (np.abs(D)[:, None] * np.abs(A)) / T
+    Gr = O.gram(A, c, x)
+    np.testing.assert_array_less(np.abs(G - Gr), 2e-2 * scale + 1e-300)
+    # and it is not trivially small: the relative Frobenius error is at BF16 level
+    assert np.linalg.norm(G - Gr) <= 1e-2 * np.linalg.norm(Gr)
