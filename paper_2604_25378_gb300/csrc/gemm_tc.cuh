@@ -90,9 +90,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int BN>
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int CW>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[CW]) {
+  if constexpr (CW == 32) tmem_ld32(taddr, v);
+  else tmem_ld16(taddr, v);
+}
+
+template <int BN, int STAGES = kTcStages>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
-  return 1024 /* alignment slack */ + (size_t)kTcStages * (kTcBM * kTcBK * 2 + BN * kTcBK * 2) + 256;
+  return 1024 /* alignment slack */ + (size_t)STAGES * (kTcBM * kTcBK * 2 + BN * kTcBK * 2) + 256;
 }
 
 // Epilogue: FP64 store C[m*ldc + n] = alpha * acc for m < M, n < N.
@@ -101,20 +121,44 @@ struct EpiStoreF64 {
   long long ldc;
   double alpha;
   int M, N;
-  __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[32]) const {
+  template <int CW>
+  __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[CW], int) const {
     if (m >= M) return;
     double* row = C + (size_t)m * ldc;
 #pragma unroll
-    for (int i = 0; i < 32; ++i)
+    for (int i = 0; i < CW; ++i)
       if (n0 + i < N) row[n0 + i] = alpha * (double)v[i];
   }
 };
 
-template <int BN, class Epi>
+// Epilogue of split-K products: FP32 partial part[(kz*N + n)*ldp + m] = acc
+// (m < M, n < N); lanes hold consecutive m, so each column store is coalesced.
+struct EpiPartT {
+  float* part;
+  long long ldp;
+  int M, N;
+  template <int CW>
+  __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[CW], int kz) const {
+    if (m >= M) return;
+#pragma unroll
+    for (int i = 0; i < CW; ++i)
+      if (n0 + i < N) part[((size_t)kz * N + n0 + i) * ldp + m] = v[i];
+  }
+};
+
+// Split-K: CTA (x, y, z) computes output tile (n0 = x*BN, m0 = y*128) over the
+// k-tiles [z*ktps, min(nk, (z+1)*ktps)) and hands the epilogue its z.
+template <int BN, int STAGES, class Epi>
 __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
-                                                    const __grid_constant__ CUtensorMap tmB, int M, int N, int K, Epi epi,
-                                                    int* err) {
-  static_assert(BN == 128 || BN == 256, "TMEM columns must be a power of two >= 32");
+                                                    const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
+                                                    int ktps, Epi epi, int* err, const int* skip,
+                                                    const int* live) {
+  static_assert(BN == 16 || BN == 32 || BN == 64 || BN == 128 || BN == 256, "unsupported N tile");
+  constexpr int kTcStages = STAGES;
+  constexpr uint32_t TCOLS = BN < 32 ? 32 : BN;
+  constexpr int CW = BN < 32 ? BN : 32;
+  if (skip != nullptr && *skip != 0) return;
+  if (live != nullptr && *live == 0) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -131,7 +175,10 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
-  const int nk = (K + kTcBK - 1) / kTcBK;
+  const int nk_all = (K + kTcBK - 1) / kTcBK;
+  const int kt0 = blockIdx.z * ktps;
+  const int kt1 = kt0 + ktps < nk_all ? kt0 + ktps : nk_all;
+  const int nk = kt1 > kt0 ? kt1 - kt0 : 0;
   if (threadIdx.x == 0) {
     s_abort = 0;
     s_issued = 0;
@@ -142,7 +189,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
     mbar_init(done, 1);
     fence_barrier_init();
   }
-  if (warp == 0) tmem_alloc(tmem_slot, BN);
+  if (warp == 0) tmem_alloc(tmem_slot, TCOLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -158,8 +205,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
       }
       if (s_abort) break;
       mbar_expect_tx(&full[s], ABYTES + BBYTES);
-      tma_load_2d(sA + (size_t)s * ABYTES, &tmA, i * kTcBK, m0, &full[s]);
-      tma_load_2d(sB + (size_t)s * BBYTES, &tmB, i * kTcBK, n0, &full[s]);
+      tma_load_2d(sA + (size_t)s * ABYTES, &tmA, (kt0 + i) * kTcBK, m0, &full[s]);
+      tma_load_2d(sB + (size_t)s * BBYTES, &tmB, (kt0 + i) * kTcBK, n0, &full[s]);
       s_issued = i + 1;
     }
   } else if (warp == 1 && lane == 0) {
@@ -189,13 +236,13 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
     atomicOr(err, kErrWaitTimeout);
   }
   tc_fence_after();
-  if (ok && !s_abort) {
+  if (ok && !s_abort && nk > 0) {
     const int m = m0 + warp * 32 + lane;
 #pragma unroll 1
-    for (int cc = 0; cc < BN / 32; ++cc) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
-      epi(m, n0 + cc * 32, v);
+    for (int cc = 0; cc < BN / CW; ++cc) {
+      float v[CW];
+      tmem_ld<CW>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * CW), v);
+      epi.template operator()<CW>(m, n0 + cc * CW, v, (int)blockIdx.z);
     }
   }
   tc_fence_before();
@@ -207,7 +254,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
       if (!mbar_wait_bounded(&full[i % kTcStages], (uint32_t)((i / kTcStages) & 1))) atomicOr(err, kErrDrainTimeout);
   }
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, BN);
+  if (warp == 0) tmem_dealloc(tmem, TCOLS);
 }
 
 }  // namespace mvsk

@@ -78,6 +78,11 @@ struct mvsk_ctx {
   __nv_bfloat16* A16T = nullptr;
   __nv_bfloat16* W16T = nullptr;
   long long Tp = 0;
+  // tensor-core PCG products: BF16 columns, S^T, split-K partials, cached tensor maps
+  __nv_bfloat16* P16 = nullptr;
+  __nv_bfloat16* S16T = nullptr;
+  float* part32 = nullptr;
+  CUtensorMap tm_A16, tm_P16, tm_A16T, tm_S16T;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_kind;  // kind id per event pair
   size_t ev_used = 0;
@@ -374,6 +379,11 @@ mvsk_status pass_ls(mvsk_ctx* c, const double* dir, const int* skip) {
   return run_pass(c, P64, M_LS, 1, a);
 }
 
+constexpr int kTcCols = 16;  // columns per tensor-core HVP product (one N tile)
+mvsk_status ensure_tc_pcg(mvsk_ctx* c);
+mvsk_status hvp_tc(mvsk_ctx* c, int c0, int nc, const int* skip, const int* live);
+mvsk_status third_tc(mvsk_ctx* c, int K, const int* skip);
+
 // ------------------------------------------------ affine-normal block (PCG)
 // Sec. 3.2 with the PCG reduced solve: h and the K Hutchinson probes share the
 // first PCG round (groups of two columns per pass over A), then
@@ -400,6 +410,30 @@ mvsk_status direction_pcg(mvsk_ctx* c) {
   k_pcg_setup<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid, ngroups);
   CU(cudaGetLastError());
   c->launches += 3 + 2 * kmax;  // setup, setup2, assemble, the pcg_step launches
+  if (P == P16 && ncol1 <= kTcCols && 2 * K <= kTcCols) {
+    // tensor-core products: every column of a round in one pair of GEMMs
+    TRY(ensure_tc_pcg(c));
+    for (int it = 0; it < kmax; ++it) {
+      TRY(hvp_tc(c, 0, ncol1, skipdir, nullptr));
+      k_pcg_step<<<ncol1, kVT, 0, c->stream>>>(s, 0, kmax);
+      CU(cudaGetLastError());
+    }
+    if (K > 0) {
+      TRY(third_tc(c, K, skipdir));
+    } else {
+      CU(cudaMemsetAsync(s.at, 0, sizeof(double) * c->ld, c->stream));
+    }
+    k_pcg_setup2<<<1, kVT, 0, c->stream>>>(s, ca, ca / 2);
+    CU(cudaGetLastError());
+    for (int it = 0; it < kmax; ++it) {
+      TRY(hvp_tc(c, ca, 1, skipdir, s.si + SI_LIVE + ca / 2));
+      k_pcg_step<<<1, kVT, 0, c->stream>>>(s, ca, kmax);
+      CU(cudaGetLastError());
+    }
+    k_assemble<<<1, kVT, 0, c->stream>>>(s, ca);
+    CU(cudaGetLastError());
+    return MVSK_OK;
+  }
   for (int it = 0; it < kmax; ++it) {
     for (int g = 0; g < ngroups; ++g) {
       const int c0 = 2 * g;
@@ -533,7 +567,7 @@ mvsk_status gemm_tc_f64(mvsk_ctx* c, const __nv_bfloat16* A, int M, const __nv_b
   CUtensorMap ta, tb;
   TRY(make_tmap_bf16(&ta, A, (unsigned long long)ldk, (unsigned long long)M, (unsigned long long)ldk * 2, kTcBK, kTcBM));
   TRY(make_tmap_bf16(&tb, B, (unsigned long long)ldk, (unsigned long long)N, (unsigned long long)ldk * 2, kTcBK, 128));
-  auto kern = k_gemm_tc<128, EpiStoreF64>;
+  auto kern = k_gemm_tc<128, kTcStages, EpiStoreF64>;
   static bool attr = false;
   const size_t smem = tc_smem_bytes<128>();
   if (!attr) {
@@ -541,9 +575,167 @@ mvsk_status gemm_tc_f64(mvsk_ctx* c, const __nv_bfloat16* A, int M, const __nv_b
     attr = true;
   }
   EpiStoreF64 epi{C, ldc, alpha, M, N};
-  dim3 grid((unsigned)((N + 127) / 128), (unsigned)((M + kTcBM - 1) / kTcBM));
-  kern<<<grid, 128, smem, c->stream>>>(ta, tb, M, N, (int)K, epi, c->err);
+  dim3 grid((unsigned)((N + 127) / 128), (unsigned)((M + kTcBM - 1) / kTcBM), 1);
+  const int nk = (int)((K + kTcBK - 1) / kTcBK);
+  kern<<<grid, 128, smem, c->stream>>>(ta, tb, M, N, (int)K, nk, epi, c->err, nullptr, nullptr);
   c->launches += 1;
+  CU(cudaGetLastError());
+  return MVSK_OK;
+}
+
+// ------------------------------------------------ tensor-core PCG products
+
+// dst[j][i] = bf16(src_j[i]) for j < nc, i < ld; columns come from up to two strided sources
+__global__ void k_cols_bf16(const double* srcA, const double* srcB, int nc, int interleave, int ld, __nv_bfloat16* dst,
+                            const int* skip) {
+  if (skip != nullptr && *skip != 0) return;
+  const long long tot = (long long)nc * ld;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / ld), i = (int)(e % ld);
+    double v;
+    if (interleave) v = (j & 1) ? srcB[(size_t)(j >> 1) * ld + i] : srcA[(size_t)(j >> 1) * ld + i];
+    else v = srcA[(size_t)j * ld + i];
+    dst[e] = __float2bfloat16((float)v);
+  }
+}
+
+// S^T[j][t] = bf16(psi''(z_t) * sum_z part[z][j][t]) (t < T; padding t < Tp stays zero)
+__global__ void k_reduce_hvp1(const float* part, int splits, int nc, long long T, long long ldp, const double* z,
+                              double c2, double c3, double c4, __nv_bfloat16* S, long long Tp, const int* skip) {
+  if (skip != nullptr && *skip != 0) return;
+  const Psi psi{c2, c3, c4};
+  const long long tot = (long long)nc * T;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / T);
+    const long long t = e % T;
+    float acc = 0.f;
+    for (int q = 0; q < splits; ++q) acc += part[((size_t)q * nc + j) * ldp + t];
+    S[(size_t)j * Tp + t] = __float2bfloat16((float)(psi.d2(z[t]) * (double)acc));
+  }
+}
+
+// Q[j][i] = scale * sum_z part[z][j][i] for i < n, 0 for n <= i < ld
+__global__ void k_reduce_hvp2(const float* part, int splits, int nc, int n, int ld, long long ldp, double scale,
+                              double* Q, const int* skip) {
+  if (skip != nullptr && *skip != 0) return;
+  const long long tot = (long long)nc * ld;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / ld), i = (int)(e % ld);
+    double acc = 0.0;
+    if (i < n)
+      for (int q = 0; q < splits; ++q) acc += (double)part[((size_t)q * nc + j) * ldp + i];
+    Q[(size_t)j * ld + i] = scale * acc;
+  }
+}
+
+// rhat[t] = K^-1 sum_k (A X_k)_t (A p_k)_t from the interleaved product columns
+__global__ void k_reduce_rhat(const float* part, int splits, int nc, long long T, long long ldp, double* rhat,
+                              const int* skip) {
+  if (skip != nullptr && *skip != 0) return;
+  const int K = nc / 2;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (long long)gridDim.x * blockDim.x) {
+    double r = 0.0;
+    for (int k = 0; k < K; ++k) {
+      float u = 0.f, v = 0.f;
+      for (int q = 0; q < splits; ++q) {
+        u += part[((size_t)q * nc + 2 * k) * ldp + t];
+        v += part[((size_t)q * nc + 2 * k + 1) * ldp + t];
+      }
+      r += (double)u * (double)v;
+    }
+    rhat[t] = r / K;
+  }
+}
+
+// S^T[0][t] = bf16(psi3(z_t) rhat_t), psi3 the third derivative of psi
+__global__ void k_back_weights(const double* z, const double* rhat, long long T, double c3, double c4,
+                               __nv_bfloat16* S, const int* skip) {
+  if (skip != nullptr && *skip != 0) return;
+  const Psi psi{0.0, c3, c4};
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (long long)gridDim.x * blockDim.x)
+    S[t] = __float2bfloat16((float)(psi.d3(z[t]) * rhat[t]));
+}
+
+mvsk_status ensure_tc_pcg(mvsk_ctx* c) {
+  if (c->P16 != nullptr) return MVSK_OK;
+  TRY(ensure_tc_operands(c));
+  void* p;
+  TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * (size_t)kTcCols * c->ld));
+  c->P16 = (__nv_bfloat16*)p;
+  TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * (size_t)kTcCols * c->Tp));
+  c->S16T = (__nv_bfloat16*)p;
+  const size_t np = (size_t)8 * kTcCols * (size_t)(c->T > c->ld ? c->T : c->ld);
+  TRY(dalloc(c, &p, sizeof(float) * np));
+  c->part32 = (float*)p;
+  TRY(make_tmap_bf16(&c->tm_A16, c->Alo, (unsigned long long)c->ld, (unsigned long long)c->T,
+                     (unsigned long long)c->ld * 2, kTcBK, kTcBM));
+  TRY(make_tmap_bf16(&c->tm_P16, c->P16, (unsigned long long)c->ld, kTcCols, (unsigned long long)c->ld * 2, kTcBK,
+                     kTcCols));
+  TRY(make_tmap_bf16(&c->tm_A16T, c->A16T, (unsigned long long)c->Tp, (unsigned long long)c->n,
+                     (unsigned long long)c->Tp * 2, kTcBK, kTcBM));
+  TRY(make_tmap_bf16(&c->tm_S16T, c->S16T, (unsigned long long)c->Tp, kTcCols, (unsigned long long)c->Tp * 2, kTcBK,
+                     kTcCols));
+  return MVSK_OK;
+}
+
+// Split-K launch of a 128 x 16 tensor-core product writing FP32 partials; returns the split count.
+mvsk_status tc_partials(mvsk_ctx* c, const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, long long K,
+                        long long ldp, const int* skip, const int* live, int* splits_out) {
+  auto kern = k_gemm_tc<kTcCols, 8, EpiPartT>;
+  static bool attr = false;
+  const size_t smem = tc_smem_bytes<kTcCols, 8>();
+  if (!attr) {
+    CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  const int mt = (M + kTcBM - 1) / kTcBM;
+  const int nk = (int)((K + kTcBK - 1) / kTcBK);
+  int want = (2 * c->nsm + mt - 1) / mt;
+  if (want > 8) want = 8;
+  if (want > nk) want = nk;
+  if (want < 1) want = 1;
+  const int ktps = (nk + want - 1) / want;
+  const int splits = (nk + ktps - 1) / ktps;
+  EpiPartT epi{c->part32, ldp, M, N};
+  dim3 grid(1, (unsigned)mt, (unsigned)splits);
+  kern<<<grid, 128, smem, c->stream>>>(ta, tb, M, N, (int)K, ktps, epi, c->err, skip, live);
+  c->launches += 1;
+  CU(cudaGetLastError());
+  *splits_out = splits;
+  return MVSK_OK;
+}
+
+// Q[c0 .. c0+nc) = T^-1 A^T (psi''(z) o A P[c0 .. c0+nc)) on the tensor cores (BF16 A, FP32 accumulate).
+mvsk_status hvp_tc(mvsk_ctx* c, int c0, int nc, const int* skip, const int* live) {
+  Inst& s = c->in;
+  const int ld = c->ld;
+  const int gb = 2 * c->nsm;
+  k_cols_bf16<<<gb, 256, 0, c->stream>>>(s.P + (size_t)c0 * ld, nullptr, nc, 0, ld, c->P16, skip);
+  int s1 = 0, s2 = 0;
+  TRY(tc_partials(c, c->tm_A16, c->tm_P16, (int)c->T, nc, ld, c->T, skip, live, &s1));
+  k_reduce_hvp1<<<gb, 256, 0, c->stream>>>(c->part32, s1, nc, c->T, c->T, s.z, c->c[1], c->c[2], c->c[3], c->S16T,
+                                           c->Tp, skip);
+  TRY(tc_partials(c, c->tm_A16T, c->tm_S16T, c->n, nc, c->Tp, ld, skip, live, &s2));
+  k_reduce_hvp2<<<gb, 256, 0, c->stream>>>(c->part32, s2, nc, c->n, ld, ld, 1.0 / (double)c->T,
+                                           s.Q + (size_t)c0 * ld, skip);
+  c->launches += 3;
+  CU(cudaGetLastError());
+  return MVSK_OK;
+}
+
+// rhat and a = T^-1 A^T (psi3(z) o rhat) on the tensor cores.
+mvsk_status third_tc(mvsk_ctx* c, int K, const int* skip) {
+  Inst& s = c->in;
+  const int ld = c->ld;
+  const int gb = 2 * c->nsm;
+  k_cols_bf16<<<gb, 256, 0, c->stream>>>(s.X + ld, s.Bv + ld, 2 * K, 1, ld, c->P16, skip);
+  int s1 = 0, s2 = 0;
+  TRY(tc_partials(c, c->tm_A16, c->tm_P16, (int)c->T, 2 * K, ld, c->T, skip, nullptr, &s1));
+  k_reduce_rhat<<<gb, 256, 0, c->stream>>>(c->part32, s1, 2 * K, c->T, c->T, s.rhat, skip);
+  k_back_weights<<<gb, 256, 0, c->stream>>>(s.z, s.rhat, c->T, c->c[2], c->c[3], c->S16T, skip);
+  TRY(tc_partials(c, c->tm_A16T, c->tm_S16T, c->n, 1, c->Tp, ld, skip, nullptr, &s2));
+  k_reduce_hvp2<<<gb, 256, 0, c->stream>>>(c->part32, s2, 1, c->n, ld, ld, 1.0 / (double)c->T, s.at, skip);
+  c->launches += 4;
   CU(cudaGetLastError());
   return MVSK_OK;
 }
