@@ -14,9 +14,11 @@
  *    never keeps them after the call returns.
  *  - All inputs and outputs are IEEE binary64, whatever the storage precision
  *    of A inside the context.
- *  - Work is issued on the context's stream (mvsk_set_stream; default: the
- *    legacy default stream) and every call returns after its results are in
- *    the caller's buffers.
+ *  - Work is issued on the context's stream (mvsk_set_stream; default: a
+ *    blocking stream the context creates, which orders with the legacy
+ *    default stream) and every call returns after its results are in the
+ *    caller's buffers.  PCG solves replay each iteration as a CUDA graph
+ *    captured on that stream.
  *  - No C++ exception crosses the ABI and nothing aborts the process; a
  *    failing call returns a non-zero mvsk_status and mvsk_last_error() gives
  *    a message.  Outputs are left untouched on MVSK_EINVAL, MVSK_ESTATE,
@@ -89,7 +91,9 @@ typedef struct {
 mvsk_status mvsk_create(const double* R, int64_t T, int64_t n, int64_t ld, uint32_t flags,
                         mvsk_ctx** out);
 
-/* mvsk_set_stream -- issue all later work on `cuda_stream` (a cudaStream_t). */
+/* mvsk_set_stream -- issue all later work on `cuda_stream` (a cudaStream_t;
+ * NULL restores the context's own stream).  The legacy NULL stream cannot be
+ * captured, so PCG solves on it would not use graphs: pass a created stream. */
 mvsk_status mvsk_set_stream(mvsk_ctx* ctx, void* cuda_stream);
 
 /*

@@ -22,6 +22,9 @@ cudaError_t rowpass_launch(int prec, int mode, int nin, const PassArgs& args, in
 size_t rowpass_smem_f64(int mode, int nin, int ld, int* stages);
 size_t rowpass_smem_f32(int mode, int nin, int ld, int* stages);
 size_t rowpass_smem_bf16(int mode, int nin, int ld, int* stages);
+cudaError_t rowpass_init_f64();
+cudaError_t rowpass_init_f32();
+cudaError_t rowpass_init_bf16();
 cudaError_t rowpass_launch_f64(int mode, int nin, const PassArgs& a, int grid, size_t smem, cudaStream_t st);
 cudaError_t rowpass_launch_f32(int mode, int nin, const PassArgs& a, int grid, size_t smem, cudaStream_t st);
 cudaError_t rowpass_launch_bf16(int mode, int nin, const PassArgs& a, int grid, size_t smem, cudaStream_t st);

@@ -41,6 +41,8 @@ struct mvsk_ctx {
   uint32_t flags = 0;
   int dir_prec = P64;
   cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;  // blocking stream created by the context (capturable)
+  bool use_graphs = true;
   int nsm = 0, grid = 0, rows_per_cta = 0;
   double* A64 = nullptr;
   void* Alo = nullptr;  // BF16 or FP32 copy
@@ -381,6 +383,21 @@ mvsk_status pass_ls(mvsk_ctx* c, const double* dir, const int* skip) {
 
 constexpr int kTcCols = 16;  // columns per tensor-core HVP product (one N tile)
 mvsk_status ensure_tc_pcg(mvsk_ctx* c);
+
+// Kernel attributes, set once per process before any capture.
+mvsk_status init_kernel_attributes() {
+  static bool done = false;
+  if (done) return MVSK_OK;
+  CU(rowpass_init_f64());
+  CU(rowpass_init_f32());
+  CU(rowpass_init_bf16());
+  CU(cudaFuncSetAttribute(k_gemm_tc<128, kTcStages, EpiStoreF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)tc_smem_bytes<128>()));
+  CU(cudaFuncSetAttribute(k_gemm_tc<kTcCols, 8, EpiPartT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)tc_smem_bytes<kTcCols, 8>()));
+  done = true;
+  return MVSK_OK;
+}
 mvsk_status hvp_tc(mvsk_ctx* c, int c0, int nc, const int* skip, const int* live);
 mvsk_status third_tc(mvsk_ctx* c, int K, const int* skip);
 
@@ -407,6 +424,10 @@ mvsk_status direction_pcg(mvsk_ctx* c) {
     TRY(run_pass(c, P, M_HVPDIAG, 2, a));
     TRY(reduce_cols(c, P, 2, c->hd, c->ld, nullptr, 0.0, skipdir, nullptr));
   }
+  if (K > 0) {
+    k_probe_fill<<<dim3((c->ld + 255) / 256, K), 256, 0, c->stream>>>(s, K);
+    c->launches += 1;
+  }
   k_pcg_setup<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid, ngroups);
   CU(cudaGetLastError());
   c->launches += 3 + 2 * kmax;  // setup, setup2, assemble, the pcg_step launches
@@ -415,7 +436,7 @@ mvsk_status direction_pcg(mvsk_ctx* c) {
     TRY(ensure_tc_pcg(c));
     for (int it = 0; it < kmax; ++it) {
       TRY(hvp_tc(c, 0, ncol1, skipdir, nullptr));
-      k_pcg_step<<<ncol1, kVT, 0, c->stream>>>(s, 0, kmax);
+      k_pcg_step<<<ncol1, kPT, 0, c->stream>>>(s, 0, kmax);
       CU(cudaGetLastError());
     }
     if (K > 0) {
@@ -427,7 +448,7 @@ mvsk_status direction_pcg(mvsk_ctx* c) {
     CU(cudaGetLastError());
     for (int it = 0; it < kmax; ++it) {
       TRY(hvp_tc(c, ca, 1, skipdir, s.si + SI_LIVE + ca / 2));
-      k_pcg_step<<<1, kVT, 0, c->stream>>>(s, ca, kmax);
+      k_pcg_step<<<1, kPT, 0, c->stream>>>(s, ca, kmax);
       CU(cudaGetLastError());
     }
     k_assemble<<<1, kVT, 0, c->stream>>>(s, ca);
@@ -446,7 +467,7 @@ mvsk_status direction_pcg(mvsk_ctx* c) {
       TRY(run_pass(c, P, M_HVP, nin, a, s.si + SI_LIVE + g));
       TRY(reduce_cols(c, P, nin, s.Q + (size_t)c0 * c->ld, c->ld, nullptr, 0.0, skipdir, s.si + SI_LIVE + g));
     }
-    k_pcg_step<<<ncol1, kVT, 0, c->stream>>>(s, 0, kmax);
+    k_pcg_step<<<ncol1, kPT, 0, c->stream>>>(s, 0, kmax);
     CU(cudaGetLastError());
   }
   if (K > 0) {
@@ -478,7 +499,7 @@ mvsk_status direction_pcg(mvsk_ctx* c) {
     a.skip = skipdir;
     TRY(run_pass(c, P, M_HVP, 1, a, s.si + SI_LIVE + ca / 2));
     TRY(reduce_cols(c, P, 1, s.Q + (size_t)ca * c->ld, c->ld, nullptr, 0.0, skipdir, s.si + SI_LIVE + ca / 2));
-    k_pcg_step<<<1, kVT, 0, c->stream>>>(s, ca, kmax);
+    k_pcg_step<<<1, kPT, 0, c->stream>>>(s, ca, kmax);
     CU(cudaGetLastError());
   }
   k_assemble<<<1, kVT, 0, c->stream>>>(s, ca);
@@ -568,12 +589,7 @@ mvsk_status gemm_tc_f64(mvsk_ctx* c, const __nv_bfloat16* A, int M, const __nv_b
   TRY(make_tmap_bf16(&ta, A, (unsigned long long)ldk, (unsigned long long)M, (unsigned long long)ldk * 2, kTcBK, kTcBM));
   TRY(make_tmap_bf16(&tb, B, (unsigned long long)ldk, (unsigned long long)N, (unsigned long long)ldk * 2, kTcBK, 128));
   auto kern = k_gemm_tc<128, kTcStages, EpiStoreF64>;
-  static bool attr = false;
   const size_t smem = tc_smem_bytes<128>();
-  if (!attr) {
-    CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
   EpiStoreF64 epi{C, ldc, alpha, M, N};
   dim3 grid((unsigned)((N + 127) / 128), (unsigned)((M + kTcBM - 1) / kTcBM), 1);
   const int nk = (int)((K + kTcBK - 1) / kTcBK);
@@ -682,12 +698,7 @@ mvsk_status ensure_tc_pcg(mvsk_ctx* c) {
 mvsk_status tc_partials(mvsk_ctx* c, const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, long long K,
                         long long ldp, const int* skip, const int* live, int* splits_out) {
   auto kern = k_gemm_tc<kTcCols, 8, EpiPartT>;
-  static bool attr = false;
   const size_t smem = tc_smem_bytes<kTcCols, 8>();
-  if (!attr) {
-    CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
   const int mt = (M + kTcBM - 1) / kTcBM;
   const int nk = (int)((K + kTcBK - 1) / kTcBK);
   int want = (2 * c->nsm + mt - 1) / mt;
@@ -824,12 +835,48 @@ mvsk_status solve_instance(mvsk_ctx* c, int cfg, double tol, const double* w0_de
   }
   int done = 0;
   so->status = MVSK_ENOTCONVERGED;
+  // The PCG iteration is driven entirely by device flags: capture it once as a
+  // CUDA graph and replay it (three replays between host checks of the flag).
+  cudaGraphExec_t gexec = nullptr;
+  long long per_graph = 0;
+  const bool graph = cfg == MVSK_PCG && c->use_graphs && !c->prof_on && !o.trace;
+  if (graph) {
+    if (c->dir_prec == P16) TRY(ensure_tc_pcg(c));
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const long long l0 = c->launches;
+    const mvsk_status cs = launch_iteration(c, cfg);
+    per_graph = c->launches - l0;
+    c->launches = l0;
+    const cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+    if (cs != MVSK_OK) {
+      if (g) cudaGraphDestroy(g);
+      return cs;
+    }
+    CU(ce);
+    const cudaError_t ie = cudaGraphInstantiate(&gexec, g, 0);
+    cudaGraphDestroy(g);
+    CU(ie);
+  }
+  struct GraphGuard {
+    cudaGraphExec_t e;
+    ~GraphGuard() {
+      if (e) cudaGraphExecDestroy(e);
+    }
+  } guard{gexec};
+  const int every = graph ? 3 : 1;
   for (size_t ph = 0; ph < phases.size(); ++ph) {
     if (ph > 0) so->restarts += 1;
     k_new_phase<<<1, 32, 0, c->stream>>>(s, phases[ph].eta, phases[ph].maxit);
     CU(cudaGetLastError());
     for (int it = 0; it <= phases[ph].maxit; ++it) {
-      TRY(launch_iteration(c, cfg));
+      if (graph) {
+        CU(cudaGraphLaunch(gexec, c->stream));
+        c->launches += per_graph;
+        if ((it % every) != every - 1 && it != phases[ph].maxit) continue;
+      } else {
+        TRY(launch_iteration(c, cfg));
+      }
       TRY(read_ints(c, &done, SI_DONE, 1));
       if (o.trace) {
         int hi[kSI];
@@ -1045,15 +1092,19 @@ mvsk_status mvsk_create(const double* R, int64_t T, int64_t n, int64_t ld, uint3
   if (flags > MVSK_PREC_MIXED_FP32) return fail(MVSK_EINVAL, "unknown flags %u", flags);
   mvsk_ctx* c = new (std::nothrow) mvsk_ctx();
   if (c == nullptr) return fail(MVSK_ENOMEM, "host allocation failed");
-  auto bail = [&](mvsk_status st) {
+  auto bail = [&](mvsk_status st_) {
     mvsk_destroy(c);
-    return st;
+    return st_;
   };
+  mvsk_status st;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return bail(fail(MVSK_ECUDA, "no CUDA device"));
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return bail(fail(MVSK_ECUDA, "cudaGetDeviceProperties failed"));
   c->nsm = prop.multiProcessorCount;
+  if (cudaStreamCreate(&c->own_stream) != cudaSuccess) return bail(fail(MVSK_ECUDA, "cudaStreamCreate failed"));
+  c->stream = c->own_stream;
+  if ((st = init_kernel_attributes()) != MVSK_OK) return bail(st);
   c->T = T;
   c->n = (int)n;
   c->ld = (int)((n + kPad - 1) / kPad * kPad);
@@ -1063,7 +1114,6 @@ mvsk_status mvsk_create(const double* R, int64_t T, int64_t n, int64_t ld, uint3
   c->rows_per_cta = (int)((T + c->grid - 1) / c->grid);
   c->grid = (int)((T + c->rows_per_cta - 1) / c->rows_per_cta);
   const size_t ldb = sizeof(double) * c->ld;
-  mvsk_status st;
 #define ALLOC(ptr, bytes)                                              \
   do {                                                                 \
     void* p_ = nullptr;                                                \
@@ -1140,7 +1190,7 @@ mvsk_status mvsk_create(const double* R, int64_t T, int64_t n, int64_t ld, uint3
 
 mvsk_status mvsk_set_stream(mvsk_ctx* c, void* stream) {
   if (c == nullptr) return fail(MVSK_EINVAL, "null context");
-  c->stream = (cudaStream_t)stream;
+  c->stream = stream != nullptr ? (cudaStream_t)stream : c->own_stream;
   return MVSK_OK;
 }
 
@@ -1184,6 +1234,7 @@ mvsk_status mvsk_set_option(mvsk_ctx* c, const char* key, double v) {
   else if (k == "cal_rel_tol" && pos(v)) o.cal_rel_tol = v;
   else if (k == "stall_window" && cnt(v, 0, 15)) o.stall_window = (int)v;
   else if (k == "trace" && cnt(v, 0, 1)) o.trace = (int)v;
+  else if (k == "graphs" && cnt(v, 0, 1)) c->use_graphs = v != 0.0;
   else return fail(MVSK_EINVAL, "unknown option or bad value: %s = %g", key, v);
   if (c->prefs_set && k == "pref_scaling") mvsk_set_prefs(c, c->lam, c->target);
   return MVSK_OK;
@@ -1399,10 +1450,10 @@ const char* mvsk_last_error(const mvsk_ctx*) { return g_err; }
 
 void mvsk_destroy(mvsk_ctx* c) {
   if (c == nullptr) return;
-  if (c->stream != nullptr) cudaStreamSynchronize(c->stream);
-  else cudaDeviceSynchronize();
+  cudaDeviceSynchronize();
   for (void* p : c->allocs) cudaFree(p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->own_stream != nullptr) cudaStreamDestroy(c->own_stream);
   delete c;
 }
 

@@ -101,6 +101,8 @@ extern "C" mvsk_status mvsk_eval_noalloc(const double* A, const double* mu, int6
   int* err = reinterpret_cast<int*>(base + 2 * (size_t)ld);
   double* spart = base + fixed;
   double* part = spart + grid;
+  if (rowpass_init_f64() != cudaSuccess)
+    return noalloc_fail(MVSK_ECUDA, "mvsk_eval_noalloc: kernel attribute set-up failed");
   int stages = 0;
   const size_t smem = rowpass_smem(P64, M_VALGRAD, 1, (int)ld, &stages);
   if (smem == 0) return noalloc_fail(MVSK_EINVAL, "mvsk_eval_noalloc: row too long for the pass");

@@ -281,14 +281,8 @@ static __global__ void __launch_bounds__(kVT) k_pcg_setup(Inst s, const double* 
   // RHS 0: h = P_V (G nu)
   project_V(s.Gnu, s.Bv, s.maskF, s.nuhat, n, m, scr);
   const int K = SI[SI_PROBES];
-  const unsigned long long seed =
-      ((unsigned long long)(unsigned)SI[SI_SEEDHI] << 32) | (unsigned long long)(unsigned)SI[SI_SEEDLO];
-  const long long it = SI[SI_ITER];
-  for (int k = 0; k < K; ++k) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s.tmp[i] = probe_value(seed, it, k, i);
-    __syncthreads();
-    project_V(s.tmp, s.Bv + (size_t)(k + 1) * ld, s.maskF, s.nuhat, n, m, scr);
-  }
+  for (int k = 0; k < K; ++k) project_V(s.Bv + (size_t)(k + 1) * ld, s.Bv + (size_t)(k + 1) * ld, s.maskF, s.nuhat,
+                                        n, m, scr);
   for (int c = 0; c <= K; ++c) pcg_init_col(s, c, m, lam, scr);
   if (threadIdx.x == 0) {
     SD[SD_LAM] = lam;
@@ -300,8 +294,25 @@ static __global__ void __launch_bounds__(kVT) k_pcg_setup(Inst s, const double* 
   }
 }
 
-// One PCG step on columns blockIdx.x + c0 (Q holds G P from the pass).
-static __global__ void __launch_bounds__(kVT) k_pcg_step(Inst s, int c0, int kmaxit) {
+// Standard normal probes zeta_k (raw, before projection) into PCG right-hand
+// sides 1..K; the iteration index comes from the device state.
+static __global__ void k_probe_fill(Inst s, int K) {
+  if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
+  const int k = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K || i >= s.ld) return;
+  const unsigned long long seed =
+      ((unsigned long long)(unsigned)s.si[SI_SEEDHI] << 32) | (unsigned long long)(unsigned)s.si[SI_SEEDLO];
+  s.Bv[(size_t)(k + 1) * s.ld + i] = i < s.n ? probe_value(seed, s.si[SI_ITER], k, i) : 0.0;
+}
+
+// One PCG step on column blockIdx.x + c0 (Q holds G P from the products):
+// q = P_V Q + lambda P, alpha = rz / p^T q, X += alpha P, R -= alpha q,
+// Z = P_V (R / |diag G|), P = Z + beta P.  Each thread keeps its <= kPE
+// coordinates in registers; five fused block reductions.
+constexpr int kPT = 512;                          // threads per PCG column CTA
+constexpr int kPE = (kMaxCols + kPT - 1) / kPT;   // coordinates per thread
+static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s, int c0, int kmaxit) {
   __shared__ double scr[80];
   int* SI = s.si;
   if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
@@ -314,13 +325,30 @@ static __global__ void __launch_bounds__(kVT) k_pcg_step(Inst s, int c0, int kma
   double* R = s.R + (size_t)c * ld;
   double* Z = s.Zc + (size_t)c * ld;
   double* P = s.P + (size_t)c * ld;
-  double* Q = s.Q + (size_t)c * ld;
-  double* tmp = s.tmp + (size_t)(1 + blockIdx.x) * ld;  // private scratch per column CTA
-  project_V(Q, Q, s.maskF, s.nuhat, n, m, scr);
+  const double* Q = s.Q + (size_t)c * ld;
+  const double* mf = s.maskF;
+  const double* nh = s.nuhat;
+  double q[kPE], p[kPE];
+  double a1 = 0.0, a2 = 0.0;
+#pragma unroll
+  for (int e = 0; e < kPE; ++e) {
+    const int i = threadIdx.x + e * kPT;
+    const bool in = i < n;
+    q[e] = in ? Q[i] : 0.0;
+    p[e] = in ? P[i] : 0.0;
+    if (in) {
+      a1 += mf[i] * q[e];
+      a2 += nh[i] * q[e];
+    }
+  }
+  const double2 r = block_sum2(a1, a2, scr);
   double pq = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    Q[i] += lam * P[i];
-    pq += P[i] * Q[i];
+  const double qmean = r.x / m;
+#pragma unroll
+  for (int e = 0; e < kPE; ++e) {
+    const int i = threadIdx.x + e * kPT;
+    if (i < n) q[e] = mf[i] * (q[e] - qmean) - r.y * nh[i] + lam * p[e];
+    pq += p[e] * q[e];
   }
   pq = block_sum2(pq, 0.0, scr).x;
   auto deactivate = [&]() {
@@ -334,31 +362,52 @@ static __global__ void __launch_bounds__(kVT) k_pcg_step(Inst s, int c0, int kma
     return;
   }
   const double al = s.rz[c] / pq;
-  double rr = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    X[i] += al * P[i];
-    R[i] -= al * Q[i];
-    rr += R[i] * R[i];
+  double rv[kPE];
+  double rr = 0.0, b1 = 0.0, b2 = 0.0;
+#pragma unroll
+  for (int e = 0; e < kPE; ++e) {
+    const int i = threadIdx.x + e * kPT;
+    rv[e] = 0.0;
+    if (i < n) {
+      X[i] += al * p[e];
+      rv[e] = R[i] - al * q[e];
+      R[i] = rv[e];
+      rr += rv[e] * rv[e];
+      q[e] = rv[e] / s.diagG[i];  // q now holds t = R / |diag G|
+      b1 += mf[i] * q[e];
+      b2 += nh[i] * q[e];
+    } else {
+      q[e] = 0.0;
+    }
   }
-  rr = block_sum2(rr, 0.0, scr).x;
-  int its = 0;
+  const double2 r2 = block_sum2(rr, b1, scr);
+  const double b2s = block_sum2(b2, 0.0, scr).x;
   if (threadIdx.x == 0) {
-    its = SI[SI_CITS + c] + 1;
-    SI[SI_CITS + c] = its;
+    SI[SI_CITS + c] += 1;
     atomicAdd(&SI[SI_KRY], 1);
   }
-  if (sqrt(rr) <= s.sd[SD_KTOL] * s.rhsn[c]) {
+  if (sqrt(r2.x) <= s.sd[SD_KTOL] * s.rhsn[c]) {
     deactivate();
     return;
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) tmp[i] = R[i] / s.diagG[i];
-  __syncthreads();
-  project_V(tmp, Z, s.maskF, s.nuhat, n, m, scr);
+  const double tmean = r2.y / m;
   double rzn = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) rzn += R[i] * Z[i];
+#pragma unroll
+  for (int e = 0; e < kPE; ++e) {
+    const int i = threadIdx.x + e * kPT;
+    if (i < n) q[e] = mf[i] * (q[e] - tmean) - b2s * nh[i];
+    rzn += rv[e] * q[e];
+  }
   rzn = block_sum2(rzn, 0.0, scr).x;
   const double beta = rzn / s.rz[c];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) P[i] = Z[i] + beta * P[i];
+#pragma unroll
+  for (int e = 0; e < kPE; ++e) {
+    const int i = threadIdx.x + e * kPT;
+    if (i < n) {
+      Z[i] = q[e];
+      P[i] = q[e] + beta * p[e];
+    }
+  }
   if (threadIdx.x == 0) {
     s.rz[c] = rzn;
     if (SI[SI_CITS + c] >= kmaxit) {
