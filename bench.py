@@ -194,7 +194,15 @@ def run_ours(args, rank, world):
                 "avg_us": round(avg_s * 1e6, 2),
                 "share_of_passes": round(d["total_ms"] / sum(v["total_ms"] for v in prof.values()), 4),
                 "share_of_step": round(d["total_ms"] / ms, 4)}
-        if "fp64" in name:
+        if name.startswith("gemm_tc"):
+            # tensor-core product: bytes_per_launch carries its average FLOPs
+            roof["bound"] = "tensor"
+            roof["unit"] = "TFLOP/s"
+            roof["achieved"] = round(d["bytes_per_launch"] / avg_s / 1e12, 2)
+            roof["peak"] = pk["bf16_tflops_sustained"]
+            roof["frac"] = round(roof["achieved"] / roof["peak"], 4)
+            roof["peak_source"] = pk_src + " (sustained bf16)"
+        elif "fp64" in name:
             roof["bound"] = "alu"
             roof["unit"] = "TFLOP/s"
             flops = 2.0 * R.shape[0] * R.shape[1] * (2 if "valgrad" in name or "hvp" in name else 1)

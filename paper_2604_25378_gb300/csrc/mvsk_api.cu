@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <array>
 #include <chrono>
 #include <string>
 #include <vector>
@@ -31,6 +32,17 @@ struct Options {
   int max_iter = 300, pcg_max_iter = 40, restart_iter = 120, krylov_maxit = 15, probes = 8;
   int stall_window = 10, pref_scaling = 1, oracle_prec = 0, arc_halvings = 40, cal_max_evals = 40, trace = 0;
   unsigned long long probe_seed = 0x5EEDull;
+};
+
+// Instance-strided state of a lockstep batch (see batch_impl.cuh).
+struct BatchBuf {
+  int cap = 0;
+  mvsk::Inst base{};
+  std::vector<void*> mem;
+  __nv_bfloat16* P16 = nullptr;
+  __nv_bfloat16* S16T = nullptr;
+  float* part = nullptr;
+  size_t part_floats = 0;
 };
 
 }  // namespace
@@ -85,9 +97,16 @@ struct mvsk_ctx {
   __nv_bfloat16* S16T = nullptr;
   float* part32 = nullptr;
   CUtensorMap tm_A16, tm_P16, tm_A16T, tm_S16T;
+  BatchBuf batch;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_kind;  // kind id per event pair
   size_t ev_used = 0;
+  size_t ev_graph_begin = 0, ev_graph_end = 0;  // pairs captured into the current graph
+  std::vector<char> ev_in_graph;                 // pair recorded as a graph node (folded per replay)
+  std::vector<long long> prof_n;                 // accumulated launches per kind id
+  std::vector<double> prof_ms;                   // accumulated device ms per kind id
+  std::vector<double> prof_work;                 // accumulated algorithmic bytes (passes) or flops (GEMMs)
+  std::vector<double> ev_work;                   // work of each recorded pair
 };
 
 namespace {
@@ -255,8 +274,9 @@ __global__ void k_ls_coef_only(Inst s, const double* spart, int G, const double*
   (void)coef;
 }
 
-__global__ void k_init_state(Inst s, double tol, double eta, int maxit, int pcg, int stallwin, int probes,
+__global__ void k_init_state(Inst s0, double tol, double eta, int maxit, int pcg, int stallwin, int probes,
                              unsigned long long seed, int kmaxit, int arcmax, const double* opts9) {
+  Inst s = inst_at(s0, blockIdx.y);
   if (threadIdx.x != 0) return;
   for (int q = 0; q < kSI; ++q) s.si[q] = 0;
   for (int q = SD_HIST; q < kSD; ++q) s.sd[q] = 0.0;
@@ -285,7 +305,8 @@ __global__ void k_init_state(Inst s, double tol, double eta, int maxit, int pcg,
   s.si[SI_ARCMAX] = arcmax;
 }
 
-__global__ void k_new_phase(Inst s, double eta, int maxit) {
+__global__ void k_new_phase(Inst s0, double eta, int maxit) {
+  Inst s = inst_at(s0, blockIdx.y);
   if (threadIdx.x != 0) return;
   s.si[SI_DONE] = 0;
   s.si[SI_PHASEIT] = 0;
@@ -305,7 +326,57 @@ PassArgs pass_args(mvsk_ctx* c) {
   return a;
 }
 
-mvsk_status run_pass(mvsk_ctx* c, int prec, int mode, int nin, PassArgs a, const int* live = nullptr) {
+// Profiling: kind ids 0..383 are streaming passes ((prec*16 + mode)*8 + nin);
+// 400 + bn are tensor-core products with N tile bn.
+constexpr int kProfKinds = 700;
+
+mvsk_status prof_begin(mvsk_ctx* c, int kind, double work) {
+  if (!c->prof_on) return MVSK_OK;
+  if (c->prof_n.empty()) {
+    c->prof_n.assign(kProfKinds, 0);
+    c->prof_ms.assign(kProfKinds, 0.0);
+    c->prof_work.assign(kProfKinds, 0.0);
+  }
+  c->ev_work.push_back(work);
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  CU(cudaStreamIsCapturing(c->stream, &cst));
+  c->ev_in_graph.push_back(cst == cudaStreamCaptureStatusActive ? 1 : 0);
+  if (c->ev_used + 2 > c->ev_pool.size()) {
+    for (int q = 0; q < 512; ++q) {
+      cudaEvent_t e;
+      CU(cudaEventCreate(&e));
+      c->ev_pool.push_back(e);
+    }
+  }
+  c->ev_kind.push_back(kind);
+  // Inside a capture a plain record only orders streams; External makes it a graph node.
+  CU(cudaEventRecordWithFlags(c->ev_pool[c->ev_used], c->stream,
+                              c->ev_in_graph.back() ? cudaEventRecordExternal : cudaEventRecordDefault));
+  return MVSK_OK;
+}
+
+mvsk_status prof_end(mvsk_ctx* c) {
+  if (!c->prof_on) return MVSK_OK;
+  CU(cudaEventRecordWithFlags(c->ev_pool[c->ev_used + 1], c->stream,
+                              c->ev_in_graph.back() ? cudaEventRecordExternal : cudaEventRecordDefault));
+  c->ev_used += 2;
+  return MVSK_OK;
+}
+
+// Fold the event pairs [b, e) into the per-kind totals (stream must be idle).
+mvsk_status prof_collect(mvsk_ctx* c, size_t b, size_t e) {
+  for (size_t q = b; q < e; ++q) {
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, c->ev_pool[2 * q], c->ev_pool[2 * q + 1]));
+    c->prof_n[c->ev_kind[q]] += 1;
+    c->prof_ms[c->ev_kind[q]] += ms;
+    c->prof_work[c->ev_kind[q]] += c->ev_work[q];
+  }
+  return MVSK_OK;
+}
+
+mvsk_status run_pass(mvsk_ctx* c, int prec, int mode, int nin, PassArgs a, const int* live = nullptr,
+                     double* spart = nullptr) {
   int stages = 0;
   const size_t smem = rowpass_smem(prec, mode, nin, c->ld, &stages);
   if (smem == 0) return fail(MVSK_EINVAL, "pass (prec %d, mode %d, nin %d) unsupported at ld=%d", prec, mode, nin, c->ld);
@@ -314,44 +385,30 @@ mvsk_status run_pass(mvsk_ctx* c, int prec, int mode, int nin, PassArgs a, const
   a.T = c->T;
   a.ld = c->ld;
   a.part = c->part;
-  a.spart = c->spart;
+  a.spart = spart != nullptr ? spart : c->spart;
   a.rows_per_cta = c->rows_per_cta;
   a.stages = stages;
   a.err = c->err;
   a.live = live;
   a.counter = c->si + SI_PASSES;
   c->launches += 1;
-  if (c->prof_on) {
-    if (c->ev_used + 2 > c->ev_pool.size()) {
-      for (int q = 0; q < 512; ++q) {
-        cudaEvent_t e;
-        CU(cudaEventCreate(&e));
-        c->ev_pool.push_back(e);
-      }
-    }
-    const int kind = (prec * 16 + mode) * 8 + nin;
-    c->ev_kind.push_back(kind);
-    CU(cudaEventRecord(c->ev_pool[c->ev_used], c->stream));
-    CU(rowpass_launch(prec, mode, nin, a, c->grid, smem, c->stream));
-    CU(cudaEventRecord(c->ev_pool[c->ev_used + 1], c->stream));
-    c->ev_used += 2;
-    return MVSK_OK;
-  }
+  static const double esz[] = {8.0, 2.0, 4.0};
+  TRY(prof_begin(c, (prec * 16 + mode) * 8 + nin, (double)c->T * (double)c->n * esz[prec]));
   CU(rowpass_launch(prec, mode, nin, a, c->grid, smem, c->stream));
-  return MVSK_OK;
+  return prof_end(c);
 }
 
 mvsk_status reduce_cols(mvsk_ctx* c, int prec, int nout, double* out, size_t stride, const double* bias, double bscale,
-                        const int* skip, const int* live) {
+                        const int* skip, const int* live, const double* c1p = nullptr) {
   dim3 g((c->ld + 255) / 256, nout);
   const double sc = 1.0 / (double)c->T;
   c->launches += 1;
   if (prec == P64)
     k_reduce_cols<double><<<g, 256, 0, c->stream>>>((const double*)c->part, c->grid, nout, c->ld, c->n, sc, bias, bscale,
-                                                    out, stride, skip, live);
+                                                    out, stride, skip, live, c1p);
   else
     k_reduce_cols<float><<<g, 256, 0, c->stream>>>((const float*)c->part, c->grid, nout, c->ld, c->n, sc, bias, bscale, out,
-                                                   stride, skip, live);
+                                                   stride, skip, live, c1p);
   CU(cudaGetLastError());
   return MVSK_OK;
 }
@@ -395,6 +452,10 @@ mvsk_status init_kernel_attributes() {
                           (int)tc_smem_bytes<128>()));
   CU(cudaFuncSetAttribute(k_gemm_tc<kTcCols, 8, EpiPartT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)tc_smem_bytes<kTcCols, 8>()));
+  CU(cudaFuncSetAttribute(k_gemm_tc<64, 6, EpiPartT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)tc_smem_bytes<64, 6>()));
+  CU(cudaFuncSetAttribute(k_gemm_tc<256, 4, EpiPartT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)tc_smem_bytes<256, 4>()));
   done = true;
   return MVSK_OK;
 }
@@ -752,6 +813,7 @@ mvsk_status third_tc(mvsk_ctx* c, int K, const int* skip) {
 }
 
 #include "direct_impl.cuh"
+#include "batch_impl.cuh"
 
 mvsk_status direction(mvsk_ctx* c, int cfg) { return cfg == MVSK_PCG ? direction_pcg(c) : direction_direct(c); }
 
@@ -839,13 +901,15 @@ mvsk_status solve_instance(mvsk_ctx* c, int cfg, double tol, const double* w0_de
   // CUDA graph and replay it (three replays between host checks of the flag).
   cudaGraphExec_t gexec = nullptr;
   long long per_graph = 0;
-  const bool graph = cfg == MVSK_PCG && c->use_graphs && !c->prof_on && !o.trace;
+  const bool graph = cfg == MVSK_PCG && c->use_graphs && !o.trace;
   if (graph) {
     if (c->dir_prec == P16) TRY(ensure_tc_pcg(c));
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     const long long l0 = c->launches;
+    c->ev_graph_begin = c->ev_kind.size();
     const mvsk_status cs = launch_iteration(c, cfg);
+    c->ev_graph_end = c->ev_kind.size();
     per_graph = c->launches - l0;
     c->launches = l0;
     const cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
@@ -873,6 +937,10 @@ mvsk_status solve_instance(mvsk_ctx* c, int cfg, double tol, const double* w0_de
       if (graph) {
         CU(cudaGraphLaunch(gexec, c->stream));
         c->launches += per_graph;
+        if (c->prof_on) {
+          CU(cudaStreamSynchronize(c->stream));
+          TRY(prof_collect(c, c->ev_graph_begin, c->ev_graph_end));
+        }
         if ((it % every) != every - 1 && it != phases[ph].maxit) continue;
       } else {
         TRY(launch_iteration(c, cfg));
@@ -973,7 +1041,8 @@ mvsk_status solve_with_target(mvsk_ctx* c, int cfg, double tol, const double* w0
     cc[0] = 0.0;
     if (!(h_lo >= -gap_tol)) {
       CU(cudaMemcpyAsync(xlo, in.x, vb, cudaMemcpyDeviceToDevice, c->stream));
-      c_hi = cc[0] > 0.0 ? cc[0] : c1_ref;
+      const double c1_start = c->opt.pref_scaling == 1 && s > 0.0 && isfinite(s) ? lam[0] / s : lam[0];
+      c_hi = c1_start > 0.0 ? c1_start : c1_ref;
       TRY(run(c_hi, xlo, &h_hi));
       CU(cudaMemcpyAsync(xhi, in.x, vb, cudaMemcpyDeviceToDevice, c->stream));
       while (h_hi < 0.0 && c_hi < c1_max) {
@@ -1178,6 +1247,13 @@ mvsk_status mvsk_create(const double* R, int64_t T, int64_t n, int64_t ld, uint3
   s.n = c->n;
   s.ld = c->ld;
   s.T = T;
+  s.spart = c->spart;
+  s.vs = c->ld;
+  s.ts = T;
+  s.cs = (long long)c->ld * c->ncolmax;
+  s.ps = (long long)c->ld * (c->ncolmax + 4);
+  s.ncs = c->ncolmax;
+  s.ss = 16LL * c->grid;
 #undef ALLOC
   std::vector<double> hmu(c->n);
   if (cudaMemcpy(hmu.data(), c->mu, sizeof(double) * c->n, cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -1265,6 +1341,14 @@ mvsk_status mvsk_solve_batch(mvsk_ctx* c, mvsk_config cfg, int32_t B, const doub
     return fail(MVSK_ECUDA, "copy of lambdas failed");
   if (targets != nullptr && cudaMemcpy(tg.data(), targets, sizeof(double) * B, cudaMemcpyDefault) != cudaSuccess)
     return fail(MVSK_ECUDA, "copy of targets failed");
+  for (int b = 0; b < B; ++b)
+    for (int q = 0; q < 4; ++q)
+      if (!(lam[4 * (size_t)b + q] >= 0.0) || !isfinite(lam[4 * (size_t)b + q]))
+        return fail(MVSK_EINVAL, "lambda[%d][%d] must be finite and >= 0", b, q);
+  if (!(tol > 0.0)) return fail(MVSK_EINVAL, "bad tol");
+  if (cfg == MVSK_PCG && c->dir_prec == P16 && c->opt.probes * 2 <= kTcCols && c->opt.probes + 1 <= kTcCols &&
+      !c->opt.trace && c->use_graphs)
+    return batch_solve(c, B, lam.data(), tg.data(), tol, W0, W_out, infos);
   mvsk_status first = MVSK_OK;
   for (int b = 0; b < B; ++b) {
     TRY(mvsk_set_prefs(c, &lam[4 * (size_t)b], tg[b]));
@@ -1406,7 +1490,13 @@ mvsk_status mvsk_profile_enable(mvsk_ctx* c, int32_t on) {
   if (on) {
     c->ev_used = 0;
     c->ev_kind.clear();
+    c->ev_work.clear();
+    c->ev_in_graph.clear();
     c->launches = 0;
+    c->prof_n.assign(kProfKinds, 0);
+    c->prof_ms.assign(kProfKinds, 0.0);
+    c->prof_work.assign(kProfKinds, 0.0);
+    c->ev_graph_begin = c->ev_graph_end = 0;
   }
   return MVSK_OK;
 }
@@ -1414,34 +1504,41 @@ mvsk_status mvsk_profile_enable(mvsk_ctx* c, int32_t on) {
 mvsk_status mvsk_profile_read(mvsk_ctx* c, mvsk_prof_entry* out, int32_t max, int32_t* count, int64_t* kernel_launches) {
   if (c == nullptr) return fail(MVSK_EINVAL, "null context");
   CU(cudaStreamSynchronize(c->stream));
-  struct Agg {
-    int kind;
-    long long n;
-    double ms;
-  };
-  std::vector<Agg> agg;
+  if (c->prof_n.empty()) {
+    if (count) *count = 0;
+    if (kernel_launches) *kernel_launches = c->launches;
+    return MVSK_OK;
+  }
+  // pairs recorded by direct launches (graph pairs were folded in after each replay)
+  std::vector<long long> n = c->prof_n;
+  std::vector<double> ms = c->prof_ms;
+  std::vector<double> wk = c->prof_work;
   for (size_t q = 0; q < c->ev_kind.size(); ++q) {
-    float ms = 0.f;
-    CU(cudaEventElapsedTime(&ms, c->ev_pool[2 * q], c->ev_pool[2 * q + 1]));
-    const int k = c->ev_kind[q];
-    size_t a = 0;
-    while (a < agg.size() && agg[a].kind != k) ++a;
-    if (a == agg.size()) agg.push_back({k, 0, 0.0});
-    agg[a].n += 1;
-    agg[a].ms += ms;
+    if (c->ev_in_graph[q]) continue;
+    float t = 0.f;
+    CU(cudaEventElapsedTime(&t, c->ev_pool[2 * q], c->ev_pool[2 * q + 1]));
+    n[c->ev_kind[q]] += 1;
+    ms[c->ev_kind[q]] += t;
+    wk[c->ev_kind[q]] += c->ev_work[q];
   }
   static const char* modes[] = {"valgrad", "fwd", "hvp", "hvpdiag", "third", "rhat", "back", "ls"};
   static const char* precs[] = {"fp64", "bf16", "fp32"};
-  static const double esz[] = {8.0, 2.0, 4.0};
-  const int nk = (int)agg.size();
-  for (int a = 0; a < nk && a < max; ++a) {
-    const int prec = agg[a].kind / 128, mode = (agg[a].kind / 8) % 16, nin = agg[a].kind % 8;
-    snprintf(out[a].name, sizeof(out[a].name), "rowpass_%s_%s_%d", precs[prec], modes[mode], nin);
-    out[a].launches = agg[a].n;
-    out[a].total_ms = agg[a].ms;
-    out[a].bytes_per_launch = (double)c->T * (double)c->n * esz[prec];
+  int k = 0;
+  for (int kind = 0; kind < kProfKinds; ++kind) {
+    if (n[kind] == 0) continue;
+    if (k < max) {
+      if (kind < 400)
+        snprintf(out[k].name, sizeof(out[k].name), "rowpass_%s_%s_%d", precs[kind / 128], modes[(kind / 8) % 16],
+                 kind % 8);
+      else
+        snprintf(out[k].name, sizeof(out[k].name), "gemm_tc_bf16_n%d", kind - 400);
+      out[k].launches = n[kind];
+      out[k].total_ms = ms[kind];
+      out[k].bytes_per_launch = wk[kind] / (double)n[kind];
+    }
+    ++k;
   }
-  if (count) *count = nk;
+  if (count) *count = k;
   if (kernel_launches) *kernel_launches = c->launches;
   return MVSK_OK;
 }
@@ -1453,6 +1550,7 @@ void mvsk_destroy(mvsk_ctx* c) {
   cudaDeviceSynchronize();
   for (void* p : c->allocs) cudaFree(p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (void* p : c->batch.mem) cudaFree(p);
   if (c->own_stream != nullptr) cudaStreamDestroy(c->own_stream);
   delete c;
 }

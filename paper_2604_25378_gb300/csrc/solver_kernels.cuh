@@ -24,9 +24,12 @@ inline __device__ void reduce_spart(const double* spart, int G, int ns, double s
 }
 
 // Column partials [G][nout][ld] -> out[m*ld + j] = scale * sum_b part + bias_scale * bias (m = 0).
+// When c1p is given the bias scale is -(*c1p) (read on the device, so a
+// captured graph follows changes of c1).
 template <typename acc>
 static __global__ void k_reduce_cols(const acc* part, int G, int nout, int ld, int n, double scale, const double* bias,
-                              double bias_scale, double* out, size_t out_stride, const int* skip, const int* live) {
+                              double bias_scale, double* out, size_t out_stride, const int* skip, const int* live,
+                              const double* c1p = nullptr) {
   if (skip != nullptr && *skip != 0) return;
   if (live != nullptr && *live == 0) return;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -35,6 +38,7 @@ static __global__ void k_reduce_cols(const acc* part, int G, int nout, int ld, i
   double s = 0.0;
   for (int b = 0; b < G; ++b) s += (double)part[((size_t)b * nout + m) * ld + j];
   s *= scale;
+  if (c1p != nullptr) bias_scale = -*c1p;
   if (bias != nullptr && m == 0) s += bias_scale * bias[j];
   out[(size_t)m * out_stride + j] = j < n ? s : 0.0;
 }
@@ -54,7 +58,8 @@ inline __device__ void project_V(const double* v, double* out, const double* mas
 }
 
 // ------------------------------------------------------------- kkt at x0
-static __global__ void __launch_bounds__(kVT) k_kkt0(Inst s) {
+static __global__ void __launch_bounds__(kVT) k_kkt0(Inst s0) {
+  Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
   const double tau = s.sd[SD_TAU];
   const double k0 = kkt_residual(s.x, s.g, s.n, tau, scr, s.tmp);
@@ -62,10 +67,11 @@ static __global__ void __launch_bounds__(kVT) k_kkt0(Inst s) {
 }
 
 // f = -c1 mu^T x + T^-1 sum psi(z) and the KKT residual (mvsk_eval).
-static __global__ void __launch_bounds__(kVT) k_eval_finish(Inst s, const double* spart, int G, double* out3) {
+static __global__ void __launch_bounds__(kVT) k_eval_finish(Inst s0, const double* spart, int G, double* out3) {
+  Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
   __shared__ double ps[2];
-  reduce_spart(spart, G, 1, s.sd[SD_INVT], ps);
+  reduce_spart(s.spart, G, 1, s.sd[SD_INVT], ps);
   double mx = 0.0;
   for (int i = threadIdx.x; i < s.n; i += blockDim.x) mx += s.mu[i] * s.x[i];
   mx = block_sum2(mx, 0.0, scr).x;
@@ -80,7 +86,8 @@ static __global__ void __launch_bounds__(kVT) k_eval_finish(Inst s, const double
 // ----------------------------------------------------------- oracle block
 // After the value/gradient pass: objective, KKT test, best iterate, stall
 // test, the working face (face continuation) and the normalised face gradient.
-static __global__ void __launch_bounds__(kVT) k_face(Inst s, const double* spart, int G) {
+static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spart, int G) {
+  Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
   __shared__ double sv[33];
   __shared__ int si_[33];
@@ -92,7 +99,7 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s, const double* spart
   const int n = s.n;
   const double tau = SD[SD_TAU];
   const bool dir_only = SI[SI_DIRONLY] != 0;
-  reduce_spart(spart, G, 1, SD[SD_INVT], ps);
+  reduce_spart(s.spart, G, 1, SD[SD_INVT], ps);
   double mx = 0.0, nonfin = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     mx += s.mu[i] * s.x[i];
@@ -257,7 +264,8 @@ inline __device__ void pcg_init_col(Inst& s, int c, double m, double lam, double
 }
 
 // Setup of the first PCG round: lambda, Jacobi diagonal, RHS h and probes.
-static __global__ void __launch_bounds__(kVT) k_pcg_setup(Inst s, const double* spart, int G, int ngroups) {
+static __global__ void __launch_bounds__(kVT) k_pcg_setup(Inst s0, const double* spart, int G, int ngroups) {
+  Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
   __shared__ double ps[2];
   int* SI = s.si;
@@ -265,7 +273,7 @@ static __global__ void __launch_bounds__(kVT) k_pcg_setup(Inst s, const double* 
   if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
   const int n = s.n, ld = s.ld;
   const double m = (double)SI[SI_M];
-  reduce_spart(spart, G, 2, SD[SD_INVT], ps);  // nu^T G nu, 1_F^T G 1_F
+  reduce_spart(s.spart, G, 2, SD[SD_INVT], ps);  // nu^T G nu, 1_F^T G 1_F
   // |diag G| floored, on F; 1 off F (never used there: vectors vanish off F).
   double sd = 0.0, sa = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -296,7 +304,8 @@ static __global__ void __launch_bounds__(kVT) k_pcg_setup(Inst s, const double* 
 
 // Standard normal probes zeta_k (raw, before projection) into PCG right-hand
 // sides 1..K; the iteration index comes from the device state.
-static __global__ void k_probe_fill(Inst s, int K) {
+static __global__ void k_probe_fill(Inst s0, int K) {
+  Inst s = inst_at(s0, blockIdx.z);
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
   const int k = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -312,7 +321,8 @@ static __global__ void k_probe_fill(Inst s, int K) {
 // coordinates in registers; five fused block reductions.
 constexpr int kPT = 512;                          // threads per PCG column CTA
 constexpr int kPE = (kMaxCols + kPT - 1) / kPT;   // coordinates per thread
-static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s, int c0, int kmaxit) {
+static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s0, int c0, int kmaxit) {
+  Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
   int* SI = s.si;
   if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
@@ -418,7 +428,8 @@ static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s, int c0, int kma
 }
 
 // Correction vector a = P_V (T^-1 A^T (psi''' o rhat)) and the second PCG round.
-static __global__ void __launch_bounds__(kVT) k_pcg_setup2(Inst s, int ca, int group) {
+static __global__ void __launch_bounds__(kVT) k_pcg_setup2(Inst s0, int ca, int group) {
+  Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
   int* SI = s.si;
   if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
@@ -433,7 +444,8 @@ static __global__ void __launch_bounds__(kVT) k_pcg_setup2(Inst s, int ca, int g
 
 // d = X_h - (||gbar|| / m) X_a - nu  (ambient; zero off F), re-centred on F so
 // that 1^T d = 0 to rounding relative to d.
-static __global__ void __launch_bounds__(kVT) k_assemble(Inst s, int ca) {
+static __global__ void __launch_bounds__(kVT) k_assemble(Inst s0, int ca) {
+  Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
   int* SI = s.si;
   if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
@@ -484,7 +496,8 @@ inline __device__ void take_step(Inst& s, const double* dir, double al, const do
 
 // After the line-search pass along d: alpha_max, the damped nominal step
 // eta_k, and the branch of the boundary block (App. C.3).
-static __global__ void __launch_bounds__(kVT) k_decide1(Inst s, const double* spart, int G) {
+static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* spart, int G) {
+  Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
   __shared__ double ps[16];
   __shared__ double coef[5];
@@ -493,7 +506,7 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s, const double* sp
   if (SI[SI_DONE] != 0) return;
   const int n = s.n;
   const double tau = SD[SD_TAU], eta = SD[SD_ETA];
-  ls_coefficients(s, spart, G, s.d, coef, scr, ps);
+  ls_coefficients(s, s.spart, G, s.d, coef, scr, ps);
   double am = INFINITY;
   for (int i = threadIdx.x; i < n; i += blockDim.x)
     if (s.d[i] < 0.0) am = fmin(am, (s.x[i] - tau) / (-s.d[i]));
@@ -585,18 +598,20 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s, const double* sp
 }
 
 // After the line-search pass along the segment: exact quartic on [0, 1].
-static __global__ void __launch_bounds__(kVT) k_decide2(Inst s, const double* spart, int G) {
+static __global__ void __launch_bounds__(kVT) k_decide2(Inst s0, const double* spart, int G) {
+  Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
   __shared__ double ps[16];
   __shared__ double coef[5];
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPLS] != 0) return;
-  ls_coefficients(s, spart, G, s.dstep, coef, scr, ps);
+  ls_coefficients(s, s.spart, G, s.dstep, coef, scr, ps);
   const double al = quartic_argmin(coef, 1.0);
   take_step(s, s.dstep, al, al == 1.0 ? s.xbar : nullptr);
   if (threadIdx.x == 0) s.sd[SD_ALPHA] = al;
 }
 
-static __global__ void k_end_iter(Inst s) {
+static __global__ void k_end_iter(Inst s0) {
+  Inst s = inst_at(s0, blockIdx.y);
   if (threadIdx.x != 0 || s.si[SI_DONE] != 0) return;
   s.si[SI_ITER] += 1;
   s.si[SI_PHASEIT] += 1;

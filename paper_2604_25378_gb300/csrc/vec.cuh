@@ -33,6 +33,8 @@ enum SI : int {
 };
 enum Branch : int { BR_NONE = 0, BR_RAW = 1, BR_SEGMENT = 2, BR_CAPPED = 3, BR_FACE = 4 };
 
+// Device state of one instance.  A batch of B instances stores every array
+// instance-strided; inst_at(base, b) is instance b's view.
 struct Inst {
   double* sd;
   int* si;
@@ -40,9 +42,31 @@ struct Inst {
   double *x, *g, *z, *nuhat, *maskF, *d, *dstep, *xbar, *Gnu, *diagG, *at, *bestx, *rhat, *tmp;
   double *X, *R, *Zc, *P, *Q, *Bv;  // PCG columns, [ncol][ld]
   double *rz, *rhsn;
+  double* spart;  // scalar partials of this instance's streaming passes
   int n, ld;
   long long T;
+  long long vs, ts, cs, ps, ncs, ss;  // instance strides: ld-vectors, T-vectors, PCG blocks, scratch, per-column, partials
 };
+
+__host__ __device__ __forceinline__ Inst inst_at(const Inst& a, int b) {
+  Inst s = a;
+  if (b != 0) {
+    s.sd += (size_t)b * kSD;
+    s.si += (size_t)b * kSI;
+    const long long v = (long long)b * a.vs;
+    s.x += v; s.g += v; s.nuhat += v; s.maskF += v; s.d += v; s.dstep += v; s.xbar += v;
+    s.Gnu += (long long)b * 2 * a.vs; s.diagG += (long long)b * 2 * a.vs;
+    s.at += v; s.bestx += v;
+    const long long t = (long long)b * a.ts;
+    s.z += t; s.rhat += t;
+    s.tmp += (long long)b * a.ps;
+    const long long cc = (long long)b * a.cs;
+    s.X += cc; s.R += cc; s.Zc += cc; s.P += cc; s.Q += cc; s.Bv += cc;
+    s.rz += (long long)b * a.ncs; s.rhsn += (long long)b * a.ncs;
+    s.spart += (long long)b * a.ss;
+  }
+  return s;
+}
 
 __device__ __forceinline__ double2 block_sum2(double a, double b, double* scr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;

@@ -169,3 +169,37 @@ def test_pcg_direction_bf16_tensor_cores():
     d_ref, _ = O.direction_pcg(A, c, A @ x, O.gradient(A, mu, c, x), np.ones(200, dtype=bool), 1e-4, O.Options(), 2)
     assert np.linalg.norm(d_gpu - d_ref) <= 5e-2 * np.linalg.norm(d_ref)
     assert abs(d_gpu.sum()) <= 1e-12 * np.max(np.abs(d_gpu))
+
+
+def test_batched_lockstep_matches_oracle():
+    """mvsk_solve_batch (PCG, BF16 direction products shared by all instances on
+    the tensor cores) against the oracle, instance by instance: preference
+    vectors inside and outside the certificate, with and without targets."""
+    import paper_2604_25378_gb300 as m
+    R = panels.garch_sector_panel(200, 2000, 9)
+    mu, A = O.centre(R)
+    lams = np.array([(1, 1, 0.5, 2), (1, 1, 2, 0.5), (1, 1, 1, 1), (0.5, 1, 0.5, 2)], dtype=float)
+    tg = panels.quantile_targets(R, [0.6, 0.7])
+    targets = np.array([np.nan, np.nan, tg[0], tg[1]])
+    ctx = m.MVSK(R, "bf16")
+    W, infos = ctx.solve_batch(lams, targets, m.PCG, 1e-10)
+    for b in range(4):
+        c = O.scale_preferences(lams[b], A, "standardised")
+        if np.isnan(targets[b]):
+            x_ref, inf_ref = O.solve(A, mu, c, "pcg", 1e-10)
+            tol_w = 1e-9
+        else:
+            c, x_ref, inf_ref, ev = O.calibrate_target(A, mu, c, targets[b], "pcg", 1e-10)
+            tol_w = 1e-7
+            assert abs(infos[b]["achieved_mean"] - targets[b]) <= 1e-9 * np.max(np.abs(mu))
+        assert infos[b]["status"] == "ok", (b, infos[b])
+        g = O.gradient(A, mu, c, W[b])
+        assert O.kkt_residual(W[b], g, 1e-8) <= 1e-10 * inf_ref.kkt0 * 1.0001 + 1e-300 or infos[b]["kkt_rel"] <= 1e-10
+        if O.convexity_certificate(c):
+            assert np.max(np.abs(W[b] - x_ref)) <= tol_w, (b, np.max(np.abs(W[b] - x_ref)))
+        else:
+            assert O.objective(A, mu, c, W[b]) <= inf_ref.f + 1e-9 * abs(inf_ref.f) or np.max(np.abs(W[b] - x_ref)) <= tol_w
+    # a single-instance solve of the same problem gives the same point
+    ctx.set_prefs(lams[0])
+    w0, inf0 = ctx.solve(m.PCG, 1e-10)
+    assert np.max(np.abs(w0 - W[0])) <= 1e-9
