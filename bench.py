@@ -181,7 +181,8 @@ def run_ours(args, rank, world):
     value = B * args.steps * world / (ms_max / 1e3)
 
     # Roofline of the dominant pass kind (live CUDA-event durations of the timed steps).
-    dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"]) if prof else None
+    timed = {k: v for k, v in prof.items() if v["bytes_per_launch"] > 0}
+    dom = max(timed.items(), key=lambda kv: kv[1]["total_ms"]) if timed else None
     pk, pk_src = peaks()
     roof = None
     if dom is not None:
@@ -192,9 +193,9 @@ def run_ours(args, rank, world):
                 "unit": "GB/s", "frac": round(ach / pk["hbm_gbs"], 4), "traffic": None,
                 "peak_source": pk_src, "launches": d["launches"],
                 "avg_us": round(avg_s * 1e6, 2),
-                "share_of_passes": round(d["total_ms"] / sum(v["total_ms"] for v in prof.values()), 4),
+                "share_of_profiled": round(d["total_ms"] / sum(v["total_ms"] for v in prof.values()), 4),
                 "share_of_step": round(d["total_ms"] / ms, 4)}
-        if name.startswith("gemm_tc"):
+        if name.startswith("gemm_tc") or name.startswith("oz_gemm"):
             # tensor-core product: bytes_per_launch carries its average FLOPs
             roof["bound"] = "tensor"
             roof["unit"] = "TFLOP/s"

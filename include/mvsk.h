@@ -114,7 +114,10 @@ mvsk_status mvsk_set_prefs(mvsk_ctx* ctx, const double lambda[4], double target)
  *   "krylov_maxit" (15), "reg" (NaN: 0 direct / 1e-4 PCG), "probes" (8),
  *   "probe_seed" (24301), "pref_scaling" (1), "release_ratio" (0.5),
  *   "eps_act" (1e-15), "oracle_prec" (0: FP64 A, 1: BF16 A, 2: FP32 A for
- *   the mvsk_oracle_* exports), "cal_rel_tol" (1e-9).
+ *   the mvsk_oracle_* exports), "cal_rel_tol" (1e-9), "graphs" (1: replay
+ *   captured CUDA graphs), "split_products" (1: in mvsk_solve_batch the FP64
+ *   products A x, A^T psi'(z) and A d run as split BF16 tensor-core products
+ *   with FP64 accuracy, see mvsk_product; 0: FP64 streaming passes).
  *   Errors: EINVAL for an unknown key or an out-of-range value.
  */
 mvsk_status mvsk_set_option(mvsk_ctx* ctx, const char* key, double value);
@@ -188,6 +191,25 @@ mvsk_status mvsk_oracle_third(mvsk_ctx* ctx, const double* w, const double* u, c
 
 /* Prop. 2: G = T^-1 A^T Diag(psi''(Aw)) A, n x n row-major (ld = n). */
 mvsk_status mvsk_oracle_gram(mvsk_ctx* ctx, const double* w, double* G);
+
+/*
+ * mvsk_product -- the sample products z = A v (Prop. 1, Eq. operator-f:
+ *   z_t = a_t^T w) and A^T v (Eq. operator-grad), for nvec vectors at once,
+ *   with FP64 accuracy on the BF16 tensor cores (error-free splitting of
+ *   Ozaki et al.; the paper computes these products in FP64).
+ *   transpose = 0: V holds nvec vectors of n values (vector b at V + b*ldv,
+ *   ldv >= n) and out vector b (T values) at out + b*ldo (ldo >= T);
+ *   transpose = 1: vectors of T values in, n values out.  1 <= nvec <= 64.
+ *   Both operands are rounded to 49 significant bits relative to their row
+ *   or vector maximum; the product of the rounded operands is then exact up
+ *   to terms below 2^-49 of the row maximum times the vector maximum.
+ *   V and out are device pointers (EINVAL otherwise); the call returns
+ *   after the work has finished.  The first call per context builds the
+ *   split copies of A (14 bytes per element of A).  Errors: EINVAL, ECUDA
+ *   (also when a bounded wait inside the tensor-core kernel ran out).
+ */
+mvsk_status mvsk_product(mvsk_ctx* ctx, int32_t transpose, int32_t nvec, const double* V, int64_t ldv,
+                         double* out, int64_t ldo);
 
 /*
  * Prop. quartic exact line search: coef[5] = A0..A4 of f(w + alpha d) from

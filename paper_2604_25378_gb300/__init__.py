@@ -68,6 +68,7 @@ _SIGS = {
     "mvsk_oracle_hvp": (ctypes.c_int, [_P, _P, _P, _P]),
     "mvsk_oracle_third": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "mvsk_oracle_gram": (ctypes.c_int, [_P, _P, _P]),
+    "mvsk_product": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64, _P, ctypes.c_int64]),
     "mvsk_oracle_ls": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "mvsk_oracle_direction": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int32, _P]),
     "mvsk_project_slice": (ctypes.c_int, [_P, _P, ctypes.c_double, _P]),
@@ -224,6 +225,19 @@ class MVSK:
         pw, kw = _ptr(w)
         out = np.empty((self.n, self.n))
         self._check(self._lib.mvsk_oracle_gram(self._h, pw, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def product(self, V, transpose=False):
+        """A V (transpose=False; V: nvec x n CUDA float64 tensor -> nvec x T) or
+        A^T V (V: nvec x T -> nvec x n), emulated FP64 on the tensor cores."""
+        import torch
+        if not (hasattr(V, "is_cuda") and V.is_cuda and V.dtype == torch.float64 and V.dim() == 2
+                and V.is_contiguous()):
+            raise TypeError("V must be a contiguous 2-D float64 CUDA tensor")
+        m = self.n if transpose else self.T
+        out = torch.empty((V.shape[0], m), dtype=torch.float64, device=V.device)
+        self._check(self._lib.mvsk_product(self._h, 1 if transpose else 0, V.shape[0], ctypes.c_void_p(V.data_ptr()),
+                                           V.shape[1], ctypes.c_void_p(out.data_ptr()), m))
         return out
 
     def line_search(self, w, d):

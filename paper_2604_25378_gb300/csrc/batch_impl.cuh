@@ -12,52 +12,59 @@
 #pragma once
 
 // ---------------------------------------------------------------- kernels
+// Batches keep their Krylov vectors in FP32 (see the PCG kernels), so these
+// kernels use no FP64 arithmetic per element.
 // dst[(b*nc + j)*ld + i] = bf16(col_j of instance b): PCG column c0 + j, or the
-// interleaved (X_{1+k}, B_{1+k}) pairs when interleave != 0.
-__global__ void k_cols_bf16_b(Inst base, int B, int c0, int nc, int interleave, __nv_bfloat16* dst) {
+// interleaved (X_{1+k}, B_{1+k}) pairs when interleave != 0.  Grid (ld/256, B*nc).
+__global__ void k_cols_bf16_b(Inst base, int nc, int c0, int interleave, __nv_bfloat16* dst) {
   const int ld = base.ld;
-  const long long tot = (long long)B * nc * ld;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % ld);
-    const long long q = e / ld;
-    const int b = (int)(q / nc), j = (int)(q % nc);
-    const Inst s = inst_at(base, b);
-    double v;
-    if (interleave) v = (j & 1) ? s.Bv[(size_t)(1 + (j >> 1)) * ld + i] : s.X[(size_t)(1 + (j >> 1)) * ld + i];
-    else v = s.P[(size_t)(c0 + j) * ld + i];
-    dst[e] = __float2bfloat16((float)v);
-  }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ld) return;
+  const int q = blockIdx.y, b = q / nc, j = q % nc;
+  const Inst s = inst_at(base, b);
+  float v;
+  if (interleave) v = (j & 1) ? kcol<float>(s.Bv, 1 + (j >> 1), ld)[i] : kcol<float>(s.X, 1 + (j >> 1), ld)[i];
+  else v = kcol<float>(s.P, c0 + j, ld)[i];
+  dst[(size_t)q * ld + i] = __float2bfloat16(v);
 }
 
-// S^T[q][t] = bf16(psi''_b(z_b[t]) * sum_z part[z][q][t]), b = q / nc.
-__global__ void k_reduce_hvp1_b(const float* part, int splits, int N, int nc, long long T, long long ldp, Inst base,
-                                __nv_bfloat16* S, long long Tp) {
-  const long long tot = (long long)N * T;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(e / T);
-    const long long t = e % T;
-    const Inst s = inst_at(base, q / nc);
-    float acc = 0.f;
-    for (int z = 0; z < splits; ++z) acc += part[((size_t)z * N + q) * ldp + t];
-    const Psi psi{s.sd[SD_C2], s.sd[SD_C3], s.sd[SD_C4]};
-    S[(size_t)q * Tp + t] = __float2bfloat16((float)(psi.d2(s.z[t]) * (double)acc));
-  }
+// S^T[q][t] = bf16(h_b[t] * sum_z part[z][q][t]), b = q / nc, with
+// h_b = psi''_b(z_b) in FP32 (k_hd_reduce1).  Grid (T/256, N).
+__global__ void k_reduce_hvp1_b(const float* part, int splits, int N, int nc, long long T, long long ldp,
+                                const float* Hf, __nv_bfloat16* S, long long Tp) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  const int q = blockIdx.y;
+  float acc = 0.f;
+  for (int z = 0; z < splits; ++z) acc += part[((size_t)z * N + q) * ldp + t];
+  S[(size_t)q * Tp + t] = __float2bfloat16(Hf[(size_t)(q / nc) * T + t] * acc);
 }
 
-// Q_b[c0 + j][i] = T^-1 sum_z part[z][b*nc + j][i] (i < n; zero padding to ld).
-// mode 1 writes the single column to at_b instead (back-projection of a).
+// Q_b[c0 + j][i] = T^-1 sum_z part[z][b*nc + j][i] in FP32 (i < n; zero padding
+// to ld).  Grid (ld/256, N).
 __global__ void k_reduce_hvp2_b(const float* part, int splits, int N, int nc, int n, int ld, long long ldp,
-                                double scale, Inst base, int c0, int mode) {
-  const long long tot = (long long)N * ld;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(e / ld), i = (int)(e % ld);
-    const Inst s = inst_at(base, q / nc);
-    double acc = 0.0;
-    if (i < n)
-      for (int z = 0; z < splits; ++z) acc += (double)part[((size_t)z * N + q) * ldp + i];
-    if (mode == 1) s.at[i] = scale * acc;
-    else s.Q[(size_t)(c0 + q % nc) * ld + i] = scale * acc;
-  }
+                                float scale, Inst base, int c0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ld) return;
+  const int q = blockIdx.y;
+  const Inst s = inst_at(base, q / nc);
+  float acc = 0.f;
+  if (i < n)
+    for (int z = 0; z < splits; ++z) acc += part[((size_t)z * N + q) * ldp + i];
+  kcol<float>(s.Q, c0 + q % nc, ld)[i] = scale * acc;
+}
+
+// at_b = T^-1 sum_z part[z][b][i] (FP64 output: the back-projected correction).
+__global__ void k_reduce_at_b(const float* part, int splits, int B, int n, int ld, long long ldp, double scale,
+                              Inst base) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ld) return;
+  const int b = blockIdx.y;
+  const Inst s = inst_at(base, b);
+  float acc = 0.f;
+  if (i < n)
+    for (int z = 0; z < splits; ++z) acc += part[((size_t)z * B + b) * ldp + i];
+  s.at[i] = scale * (double)acc;
 }
 
 // rhat_b[t] = K^-1 sum_k (A X_k)_t (A p_k)_t; S^T[b][t] = bf16(psi3_b(z_b[t]) rhat_b[t]).
@@ -83,6 +90,194 @@ __global__ void k_reduce_rhat_b(const float* part, int splits, int N, int K, lon
     s.rhat[t] = r;
     const Psi psi{0.0, s.sd[SD_C3], s.sd[SD_C4]};
     S[(size_t)b * Tp + t] = __float2bfloat16((float)(psi.d3(s.z[t]) * r));
+  }
+}
+
+// ------------------------------------------- split tensor-core FP64 products
+// Finishing kernels of the split products of ozaki.cuh for instances
+// b0 .. b0 + gridDim.y - 1 (local index = blockIdx.y = column of the product).
+// Row kernels stride over t with gridDim.x CTAs; CTA g writes its scalar
+// partials to spart_b[g * ns + q], the layout the single-CTA kernels reduce.
+
+// z_b = A x_b (Prop. 1, z_t = a_t^T w); W_b = psi'_b(z_b); spart_b[g] = sum psi_b(z_t).
+__global__ void __launch_bounds__(256) k_oz_fin_z(const long long* part, int splits, int Bp, long long ldp,
+                                                  const int* em, const int* fb, Inst base, int b0, double* W,
+                                                  long long ldw) {
+  __shared__ double scr[64];
+  const int bl = blockIdx.y;
+  Inst s = inst_at(base, b0 + bl);
+  if (s.si[SI_DONE] != 0) return;
+  const Psi psi{s.sd[SD_C2], s.sd[SD_C3], s.sd[SD_C4]};
+  double acc = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < s.T; t += (long long)gridDim.x * blockDim.x) {
+    const double z = oz_value(part, splits, Bp, ldp, t, bl, em[t], fb[bl]);
+    s.z[t] = z;
+    W[(size_t)(b0 + bl) * ldw + t] = psi.d1(z);
+    acc += psi.f(z);
+  }
+  acc = block_sum(acc, scr);
+  if (threadIdx.x == 0) s.spart[blockIdx.x] = acc;
+}
+
+// g_b = -c1_b mu + T^-1 A^T psi'_b(z_b) (Eq. operator-grad), zero padding to ld.
+__global__ void k_oz_fin_g(const long long* part, int splits, int Bp, long long ldp, const int* em, const int* fb,
+                           Inst base, int b0) {
+  const int bl = blockIdx.y;
+  Inst s = inst_at(base, b0 + bl);
+  if (s.si[SI_DONE] != 0) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.ld) return;
+  s.g[i] = i < s.n ? -s.sd[SD_C1] * s.mu[i] + s.sd[SD_INVT] * oz_value(part, splits, Bp, ldp, i, bl, em[i], fb[bl])
+                   : 0.0;
+}
+
+// The twelve power sums s_rs of (z_t, w_t = a_t^T d) (Prop. quartic line search).
+__global__ void __launch_bounds__(256) k_oz_fin_ls(const long long* part, int splits, int Bp, long long ldp,
+                                                   const int* em, const int* fb, Inst base, int b0, int skip_slot) {
+  __shared__ double scr[64];
+  const int bl = blockIdx.y;
+  Inst s = inst_at(base, b0 + bl);
+  if (s.si[SI_DONE] != 0 || s.si[skip_slot] != 0) return;
+  double a[12];
+#pragma unroll
+  for (int q = 0; q < 12; ++q) a[q] = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < s.T; t += (long long)gridDim.x * blockDim.x) {
+    const double zt = s.z[t], w = oz_value(part, splits, Bp, ldp, t, bl, em[t], fb[bl]);
+    const double z2 = zt * zt, w2 = w * w;
+    a[0] += z2;            // s20
+    a[1] += z2 * zt;       // s30
+    a[2] += z2 * z2;       // s40
+    a[3] += zt * w;        // s11
+    a[4] += z2 * w;        // s21
+    a[5] += z2 * zt * w;   // s31
+    a[6] += w2;            // s02
+    a[7] += zt * w2;       // s12
+    a[8] += z2 * w2;       // s22
+    a[9] += w2 * w;        // s03
+    a[10] += zt * w2 * w;  // s13
+    a[11] += w2 * w2;      // s04
+  }
+#pragma unroll 1
+  for (int q = 0; q < 12; ++q) {
+    const double v = block_sum(a[q], scr);
+    if (threadIdx.x == 0) s.spart[(size_t)blockIdx.x * 12 + q] = v;
+  }
+}
+
+// g = -c1 mu + G0 (the gradient at 1/n from its c1-free part), zero padding.
+__global__ void k_grad_from_g0(double* g, const double* G0, const double* mu, double c1, int n, int ld) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ld) g[i] = i < n ? -c1 * mu[i] + G0[i] : 0.0;
+}
+
+// (f, KKT residual, mu^T x) of a converged inner solve from its iteration state:
+// the oracle block that declared convergence evaluated them at the current x.
+__global__ void k_eval_state(Inst s0, double* out3) {
+  const Inst s = inst_at(s0, blockIdx.y);
+  if (threadIdx.x == 0) {
+    out3[0] = s.sd[SD_F];
+    out3[1] = s.sd[SD_KKT];
+    out3[2] = s.sd[SD_MUX];
+  }
+}
+
+// need = 1 when some running instance takes the projected segment (second line search).
+__global__ void k_need_ls2(Inst base, int B, int* need) {
+  int any = 0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const int* si = base.si + (size_t)b * kSI;
+    any |= (si[SI_DONE] == 0 && si[SI_SKIPLS] == 0);
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) *need = any;
+}
+
+// ------------------------------------- diagonal and nu-products (tensor cores)
+// The per-iteration inputs of the PCG block (Sec. 3.2): G nu and diag(G) of
+// the weighted Gram G = T^-1 A^T Diag(psi''(z)) A, plus psi''-weighted squares
+// of A nu and A 1_F (traces of the face-projected Hessian), for all instances.
+
+// dst[(2b + j)*ld + i] = bf16(nuhat_b[i]) (j = 0) or bf16(maskF_b[i]) (j = 1).
+__global__ void k_hd_cols(Inst base, int B, __nv_bfloat16* dst) {
+  const int ld = base.ld;
+  const long long tot = (long long)B * 2 * ld;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % ld);
+    const long long q = e / ld;
+    const Inst s = inst_at(base, (int)(q >> 1));
+    dst[e] = __float2bfloat16((float)((q & 1) ? s.maskF[i] : s.nuhat[i]));
+  }
+}
+
+// From the split partials of A [nu_b, 1_F,b]: h = psi''_b(z_t), S^T[b][t] =
+// bf16(h (A nu)_t), H[b][t] = bf16(h), Hf[b][t] = h in FP32 (reused by the
+// PCG products of the iteration); spart_b[g*2 + {0,1}] = sum h (A nu)_t^2,
+// sum h (A 1_F)_t^2 over the rows t of CTA g.
+__global__ void __launch_bounds__(256) k_hd_reduce1(const float* part, int splits, int N, long long T, long long ldp,
+                                                    Inst base, __nv_bfloat16* S, __nv_bfloat16* H, long long Tp,
+                                                    float* Hf) {
+  __shared__ double scr[64];
+  const int b = blockIdx.y;
+  Inst s = inst_at(base, b);
+  if (s.si[SI_SKIPDIR] != 0) return;
+  const Psi psi{s.sd[SD_C2], s.sd[SD_C3], s.sd[SD_C4]};
+  double a0 = 0.0, a1 = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (long long)gridDim.x * blockDim.x) {
+    float u = 0.f, v = 0.f;
+    for (int z = 0; z < splits; ++z) {
+      u += part[((size_t)z * N + 2 * b) * ldp + t];
+      v += part[((size_t)z * N + 2 * b + 1) * ldp + t];
+    }
+    const double h = psi.d2(s.z[t]);
+    S[(size_t)b * Tp + t] = __float2bfloat16((float)(h * (double)u));
+    H[(size_t)b * Tp + t] = __float2bfloat16((float)h);
+    Hf[(size_t)b * T + t] = (float)h;
+    a0 += h * (double)u * (double)u;
+    a1 += h * (double)v * (double)v;
+  }
+  a0 = block_sum(a0, scr);
+  a1 = block_sum(a1, scr);
+  if (threadIdx.x == 0) {
+    s.spart[(size_t)blockIdx.x * 2] = a0;
+    s.spart[(size_t)blockIdx.x * 2 + 1] = a1;
+  }
+}
+
+// out_b[i] = T^-1 sum_z part[z][b][i] into Gnu_b (which = 0) or diagG_b (which = 1).
+__global__ void k_hd_reduce2(const float* part, int splits, int B, int n, int ld, long long ldp, double scale,
+                             Inst base, int which) {
+  const long long tot = (long long)B * ld;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(e / ld), i = (int)(e % ld);
+    const Inst s = inst_at(base, b);
+    if (s.si[SI_SKIPDIR] != 0) continue;
+    double acc = 0.0;
+    if (i < n)
+      for (int z = 0; z < splits; ++z) acc += (double)part[((size_t)z * B + b) * ldp + i];
+    (which ? s.diagG : s.Gnu)[i] = scale * acc;
+  }
+}
+
+// out[j*ldo + t] = bf16(A[t*lda + j]^2) for j < n, t < T; zero for T <= t < Tp.
+__global__ void k_square_t_bf16(const double* A, int lda, long long T, int n, __nv_bfloat16* out, long long ldo,
+                                long long Tp) {
+  __shared__ float tile[32][33];
+  const long long t0 = (long long)blockIdx.x * 32;
+  const int j0 = blockIdx.y * 32;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const long long t = t0 + threadIdx.y + 8 * k;
+    const int j = j0 + threadIdx.x;
+    double v = 0.0;
+    if (t < T && j < n) v = A[(size_t)t * lda + j];
+    tile[threadIdx.y + 8 * k][threadIdx.x] = (float)(v * v);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int j = j0 + threadIdx.y + 8 * k;
+    const long long t = t0 + threadIdx.x;
+    if (j < n && t < Tp) out[(size_t)j * ldo + t] = __float2bfloat16(tile[threadIdx.x][threadIdx.y + 8 * k]);
   }
 }
 
@@ -158,6 +353,27 @@ mvsk_status batch_alloc(mvsk_ctx* c, BatchBuf& bb, int B) {
   bb.part_floats = (size_t)4 * kTcCols * Bs * (T > ld ? T : ld);
   TRY(get(sizeof(float) * bb.part_floats, &p));
   bb.part = (float*)p;
+  TRY(get(sizeof(double) * T * Bs, &p));
+  bb.Wt = (double*)p;
+  TRY(get(sizeof(int), &p));
+  bb.need = (int*)p;
+  TRY(get(sizeof(double) * ld * Bs, &p));
+  bb.G0 = (double*)p;
+  TRY(get(sizeof(__nv_bfloat16) * (size_t)c->Tp * Bs, &p));
+  bb.H16 = (__nv_bfloat16*)p;
+  TRY(get(sizeof(float) * T * Bs, &p));
+  bb.Hf = (float*)p;
+  TRY(get(sizeof(float) * 3 * ld * Bs, &p));
+  bb.base.kf = (float*)p;
+  bb.base.kfs = 3LL * c->ld;
+  if (c->A2_16T == nullptr) {
+    TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * (size_t)c->n * c->Tp));
+    c->A2_16T = (__nv_bfloat16*)p;
+    dim3 g((unsigned)((c->Tp + 31) / 32), (unsigned)((c->n + 31) / 32));
+    k_square_t_bf16<<<g, dim3(32, 8), 0, c->stream>>>(c->A64, c->ld, c->T, c->n, c->A2_16T, c->Tp, c->Tp);
+    c->launches += 1;
+    CU(cudaGetLastError());
+  }
   bb.cap = B;
   return MVSK_OK;
 }
@@ -202,30 +418,49 @@ mvsk_status tc_partials_n(mvsk_ctx* c, const void* Aop, int M, const void* Bop, 
 
 // Q_b[c0..c0+nc) = T^-1 A^T (psi''_b(z_b) o A P_b[c0..c0+nc)) for every instance.
 mvsk_status hvp_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int c0, int nc) {
-  const int N = B * nc, gb = 4 * c->nsm;
-  k_cols_bf16_b<<<gb, 256, 0, c->stream>>>(bb.base, B, c0, nc, 0, bb.P16);
+  const int N = B * nc;
+  const unsigned gl = (unsigned)((c->ld + 255) / 256), gt = (unsigned)((c->T + 255) / 256);
+  PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl, N), 256, 0, c->stream>>>(bb.base, nc, c0, 0, bb.P16)));
   int s1 = 0, s2 = 0;
   TRY(tc_partials_n(c, c->Alo, (int)c->T, bb.P16, N, c->ld, c->ld, bb.part, bb.part_floats, c->T, &s1));
-  k_reduce_hvp1_b<<<gb, 256, 0, c->stream>>>(bb.part, s1, N, nc, c->T, c->T, bb.base, bb.S16T, c->Tp);
+  PROF_LAUNCH(NK_HVP1, (k_reduce_hvp1_b<<<dim3(gt, N), 256, 0, c->stream>>>(bb.part, s1, N, nc, c->T, c->T, bb.Hf,
+                                                                             bb.S16T, c->Tp)));
   TRY(tc_partials_n(c, c->A16T, c->n, bb.S16T, N, c->Tp, c->Tp, bb.part, bb.part_floats, c->ld, &s2));
-  k_reduce_hvp2_b<<<gb, 256, 0, c->stream>>>(bb.part, s2, N, nc, c->n, c->ld, c->ld, 1.0 / (double)c->T, bb.base, c0,
-                                             0);
-  c->launches += 3;
-  CU(cudaGetLastError());
+  PROF_LAUNCH(NK_HVP2, (k_reduce_hvp2_b<<<dim3(gl, N), 256, 0, c->stream>>>(
+                            bb.part, s2, N, nc, c->n, c->ld, c->ld, (float)(1.0 / (double)c->T), bb.base, c0)));
   return MVSK_OK;
 }
 
 // rhat_b and at_b = T^-1 A^T (psi3_b(z_b) o rhat_b) for every instance.
 mvsk_status third_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int K) {
   const int N = B * 2 * K, gb = 4 * c->nsm;
-  k_cols_bf16_b<<<gb, 256, 0, c->stream>>>(bb.base, B, 0, 2 * K, 1, bb.P16);
+  const unsigned gl = (unsigned)((c->ld + 255) / 256);
+  PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl, N), 256, 0, c->stream>>>(bb.base, 2 * K, 0, 1, bb.P16)));
   int s1 = 0, s2 = 0;
   TRY(tc_partials_n(c, c->Alo, (int)c->T, bb.P16, N, c->ld, c->ld, bb.part, bb.part_floats, c->T, &s1));
-  k_reduce_rhat_b<<<gb, 256, 0, c->stream>>>(bb.part, s1, N, K, c->T, c->T, bb.base, bb.S16T, c->Tp);
+  PROF_LAUNCH(NK_RHAT, (k_reduce_rhat_b<<<gb, 256, 0, c->stream>>>(bb.part, s1, N, K, c->T, c->T, bb.base, bb.S16T,
+                                                                   c->Tp)));
   TRY(tc_partials_n(c, c->A16T, c->n, bb.S16T, B, c->Tp, c->Tp, bb.part, bb.part_floats, c->ld, &s2));
-  k_reduce_hvp2_b<<<gb, 256, 0, c->stream>>>(bb.part, s2, B, 1, c->n, c->ld, c->ld, 1.0 / (double)c->T, bb.base, 0, 1);
-  c->launches += 3;
-  CU(cudaGetLastError());
+  PROF_LAUNCH(NK_HVP2, (k_reduce_at_b<<<dim3(gl, B), 256, 0, c->stream>>>(bb.part, s2, B, c->n, c->ld, c->ld,
+                                                                         1.0 / (double)c->T, bb.base)));
+  return MVSK_OK;
+}
+
+// Gnu, diagG and the two psi''-weighted squares of every instance (skips
+// instances with SI_SKIPDIR); scalar partials with gz CTAs over t.
+mvsk_status hvpdiag_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int gz) {
+  const int N = 2 * B, gb = 4 * c->nsm;
+  PROF_LAUNCH(NK_HD_COLS, (k_hd_cols<<<gb, 256, 0, c->stream>>>(bb.base, B, bb.P16)));
+  int s1 = 0, s2 = 0, s3 = 0;
+  TRY(tc_partials_n(c, c->Alo, (int)c->T, bb.P16, N, c->ld, c->ld, bb.part, bb.part_floats, c->T, &s1));
+  PROF_LAUNCH(NK_HD_RED1, (k_hd_reduce1<<<dim3(gz, B), 256, 0, c->stream>>>(bb.part, s1, N, c->T, c->T, bb.base,
+                                                                            bb.S16T, bb.H16, c->Tp, bb.Hf)));
+  TRY(tc_partials_n(c, c->A16T, c->n, bb.S16T, B, c->Tp, c->Tp, bb.part, bb.part_floats, c->ld, &s2));
+  PROF_LAUNCH(NK_HD_RED2, (k_hd_reduce2<<<gb, 256, 0, c->stream>>>(bb.part, s2, B, c->n, c->ld, c->ld,
+                                                                   1.0 / (double)c->T, bb.base, 0)));
+  TRY(tc_partials_n(c, c->A2_16T, c->n, bb.H16, B, c->Tp, c->Tp, bb.part, bb.part_floats, c->ld, &s3));
+  PROF_LAUNCH(NK_HD_DIAG, (k_hd_reduce2<<<gb, 256, 0, c->stream>>>(bb.part, s3, B, c->n, c->ld, c->ld,
+                                                                   1.0 / (double)c->T, bb.base, 1)));
   return MVSK_OK;
 }
 
@@ -244,78 +479,92 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
   const Inst& base = bb.base;
   const int K = c->opt.probes, ncol1 = K + 1, ca = K + 1, kmax = c->opt.krylov_maxit;
   const int P = c->dir_prec;
-  for (int b = 0; b < B; ++b) {
-    const Inst s = inst_at(base, b);
-    PassArgs a = pass_args_inst(cc[b].data());
-    a.in[0] = s.x;
-    a.rowout = s.z;
-    a.skip = s.si + SI_DONE;
-    TRY(run_pass(c, P64, M_VALGRAD, 1, a, nullptr, s.spart));
-    TRY(reduce_cols(c, P64, 1, s.g, c->ld, c->mu, 0.0, s.si + SI_DONE, nullptr, s.sd + SD_C1));
+  const bool split = c->opt.split_products != 0;
+  const OzBuf& oz = c->oz;
+  const int Gz = oz_row_ctas(c);
+  const int Gs = split ? Gz : c->grid;  // scalar partials per instance of the value and line-search products
+  // split products of one of the directions d (d_b = base + b*vs) for groups of <= 64 instances
+  auto ls_split = [&](double* dvec, int skip_slot, const int* need) -> mvsk_status {
+    for (int b0 = 0; b0 < B; b0 += kOzMaxB) {
+      const int nb = B - b0 < kOzMaxB ? B - b0 : kOzMaxB;
+      int sp = 0;
+      TRY(oz_product(c, 0, dvec + (size_t)b0 * base.vs, base.vs, nb, oz_bp(nb), need, &sp));
+      PROF_LAUNCH(NK_OZ_LS, (k_oz_fin_ls<<<dim3(Gz, nb), 256, 0, c->stream>>>(oz.part, sp, oz_bp(nb), oz.MpF, oz.eF,
+                                                                             oz.fF, base, b0, skip_slot)));
+    }
+    return MVSK_OK;
+  };
+  if (split) {
+    for (int b0 = 0; b0 < B; b0 += kOzMaxB) {
+      const int nb = B - b0 < kOzMaxB ? B - b0 : kOzMaxB, Bp = oz_bp(nb);
+      int sp = 0;
+      TRY(oz_product(c, 0, base.x + (size_t)b0 * base.vs, base.vs, nb, Bp, nullptr, &sp));
+      PROF_LAUNCH(NK_OZ_Z, (k_oz_fin_z<<<dim3(Gz, nb), 256, 0, c->stream>>>(oz.part, sp, Bp, oz.MpF, oz.eF, oz.fF,
+                                                                           base, b0, bb.Wt, c->T)));
+      TRY(oz_product(c, 1, bb.Wt + (size_t)b0 * c->T, c->T, nb, Bp, nullptr, &sp));
+      PROF_LAUNCH(NK_OZ_G, (k_oz_fin_g<<<dim3((c->ld + 255) / 256, nb), 256, 0, c->stream>>>(
+                                oz.part, sp, Bp, oz.MpB, oz.eB, oz.fB, base, b0)));
+    }
+  } else {
+    for (int b = 0; b < B; ++b) {
+      const Inst s = inst_at(base, b);
+      PassArgs a = pass_args_inst(cc[b].data());
+      a.in[0] = s.x;
+      a.rowout = s.z;
+      a.skip = s.si + SI_DONE;
+      TRY(run_pass(c, P64, M_VALGRAD, 1, a, nullptr, s.spart));
+      TRY(reduce_cols(c, P64, 1, s.g, c->ld, c->mu, 0.0, s.si + SI_DONE, nullptr, s.sd + SD_C1));
+    }
   }
-  k_face<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, c->grid);
-  c->launches += 1;
-  CU(cudaGetLastError());
-  for (int b = 0; b < B; ++b) {
-    const Inst s = inst_at(base, b);
-    PassArgs a = pass_args_inst(cc[b].data());
-    a.in[0] = s.nuhat;
-    a.in[1] = s.maskF;
-    a.z = s.z;
-    a.skip = s.si + SI_SKIPDIR;
-    TRY(run_pass(c, P, M_HVPDIAG, 2, a, nullptr, s.spart));
-    TRY(reduce_cols(c, P, 2, s.Gnu, c->ld, nullptr, 0.0, s.si + SI_SKIPDIR, nullptr));
-  }
-  if (K > 0) k_probe_fill<<<dim3((c->ld + 255) / 256, K, B), 256, 0, c->stream>>>(base, K);
-  k_pcg_setup<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, c->grid, (ncol1 + 1) / 2);
-  c->launches += 2;
-  CU(cudaGetLastError());
+  PROF_LAUNCH(NK_FACE, (k_face<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gs)));
+  (void)P;
+  TRY(hvpdiag_tc_batch(c, bb, B, Gz));
+  if (K > 0)
+    PROF_LAUNCH(NK_PROBE_FILL, (k_probe_fill<float><<<dim3((c->ld + 255) / 256, K, B), 256, 0, c->stream>>>(base, K)));
+  PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gz, (ncol1 + 1) / 2)));
   for (int it = 0; it < kmax; ++it) {
     TRY(hvp_tc_batch(c, bb, B, 0, ncol1));
-    k_pcg_step<<<dim3(ncol1, B), kPT, 0, c->stream>>>(base, 0, kmax);
-    c->launches += 1;
-    CU(cudaGetLastError());
+    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step<float><<<dim3(ncol1, B), kPT, 0, c->stream>>>(base, 0, kmax)));
   }
   if (K > 0) {
     TRY(third_tc_batch(c, bb, B, K));
   } else {
     for (int b = 0; b < B; ++b) CU(cudaMemsetAsync(inst_at(base, b).at, 0, sizeof(double) * c->ld, c->stream));
   }
-  k_pcg_setup2<<<dim3(1, B), kVT, 0, c->stream>>>(base, ca, ca / 2);
-  c->launches += 1;
-  CU(cudaGetLastError());
+  PROF_LAUNCH(NK_PCG_SETUP2, (k_pcg_setup2<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca, ca / 2)));
   for (int it = 0; it < kmax; ++it) {
     TRY(hvp_tc_batch(c, bb, B, ca, 1));
-    k_pcg_step<<<dim3(1, B), kPT, 0, c->stream>>>(base, ca, kmax);
-    c->launches += 1;
-    CU(cudaGetLastError());
+    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step<float><<<dim3(1, B), kPT, 0, c->stream>>>(base, ca, kmax)));
   }
-  k_assemble<<<dim3(1, B), kVT, 0, c->stream>>>(base, ca);
-  c->launches += 1;
-  CU(cudaGetLastError());
-  for (int b = 0; b < B; ++b) {
-    const Inst s = inst_at(base, b);
-    PassArgs a = pass_args_inst(cc[b].data());
-    a.in[0] = s.d;
-    a.z = s.z;
-    a.skip = s.si + SI_DONE;
-    TRY(run_pass(c, P64, M_LS, 1, a, nullptr, s.spart));
+  PROF_LAUNCH(NK_ASSEMBLE, (k_assemble<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca)));
+  if (split) {
+    TRY(ls_split(base.d, SI_DONE, nullptr));
+  } else {
+    for (int b = 0; b < B; ++b) {
+      const Inst s = inst_at(base, b);
+      PassArgs a = pass_args_inst(cc[b].data());
+      a.in[0] = s.d;
+      a.z = s.z;
+      a.skip = s.si + SI_DONE;
+      TRY(run_pass(c, P64, M_LS, 1, a, nullptr, s.spart));
+    }
   }
-  k_decide1<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, c->grid);
-  c->launches += 1;
-  CU(cudaGetLastError());
-  for (int b = 0; b < B; ++b) {
-    const Inst s = inst_at(base, b);
-    PassArgs a = pass_args_inst(cc[b].data());
-    a.in[0] = s.dstep;
-    a.z = s.z;
-    a.skip = s.si + SI_SKIPLS;
-    TRY(run_pass(c, P64, M_LS, 1, a, nullptr, s.spart));
+  PROF_LAUNCH(NK_DECIDE1, (k_decide1<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gs)));
+  if (split) {
+    PROF_LAUNCH(NK_NEED, (k_need_ls2<<<1, 64, 0, c->stream>>>(base, B, bb.need)));
+    TRY(ls_split(base.dstep, SI_SKIPLS, bb.need));
+  } else {
+    for (int b = 0; b < B; ++b) {
+      const Inst s = inst_at(base, b);
+      PassArgs a = pass_args_inst(cc[b].data());
+      a.in[0] = s.dstep;
+      a.z = s.z;
+      a.skip = s.si + SI_SKIPLS;
+      TRY(run_pass(c, P64, M_LS, 1, a, nullptr, s.spart));
+    }
   }
-  k_decide2<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, c->grid);
-  k_end_iter<<<dim3(1, B), 32, 0, c->stream>>>(base);
-  c->launches += 2;
-  CU(cudaGetLastError());
+  PROF_LAUNCH(NK_DECIDE2, (k_decide2<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gs)));
+  PROF_LAUNCH(NK_END_ITER, (k_end_iter<<<dim3(1, B), 32, 0, c->stream>>>(base)));
   return MVSK_OK;
 }
 
@@ -345,12 +594,9 @@ mvsk_status batch_start_run(mvsk_ctx* c, BatchBuf& bb, int b, InstRun& r, double
   CU(cudaMemcpyAsync(dopts, h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
   k_init_state<<<1, 32, 0, c->stream>>>(s, tol, o.eta, o.pcg_max_iter, 1, o.stall_window, o.probes, o.probe_seed,
                                         o.krylov_maxit, o.arc_halvings, dopts);
+  // KKT residual at the 1/n start (the kkt_rel normaliser): g(1/n) = -c1 mu + G0_b
   k_fill<<<(c->ld + 255) / 256, 256, 0, c->stream>>>(s.x, c->n, c->ld, 1.0 / c->n);
-  PassArgs a = pass_args_inst(r.cc.data());
-  a.in[0] = s.x;
-  a.rowout = s.z;
-  TRY(run_pass(c, P64, M_VALGRAD, 1, a, nullptr, s.spart));
-  TRY(reduce_cols(c, P64, 1, s.g, c->ld, c->mu, -c1, nullptr, nullptr));
+  k_grad_from_g0<<<(c->ld + 255) / 256, 256, 0, c->stream>>>(s.g, bb.G0 + (size_t)b * c->ld, c->mu, c1, c->n, c->ld);
   k_kkt0<<<1, kVT, 0, c->stream>>>(s);
   if (w0 != nullptr) CU(cudaMemcpyAsync(s.x, w0, sizeof(double) * c->ld, cudaMemcpyDeviceToDevice, c->stream));
   k_new_phase<<<1, 32, 0, c->stream>>>(s, o.eta, o.pcg_max_iter);
@@ -408,6 +654,8 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     TRY(sync(c));
     w0buf = (double*)1;  // marker: warm starts live in each instance's xbar
   }
+  if (c->opt.split_products != 0)  // digit planes of A are built outside the capture
+    for (int b0 = 0; b0 < B; b0 += kOzMaxB) TRY(oz_prepare(c, oz_bp(B - b0 < kOzMaxB ? B - b0 : kOzMaxB)));
   // graph of one lockstep iteration (c1 is read on the device, so calibration needs no re-capture)
   cudaGraphExec_t gexec = nullptr;
   long long per_graph = 0;
@@ -436,6 +684,17 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       if (e) cudaGraphExecDestroy(e);
     }
   } guard{gexec};
+  // c1-free part of the gradient at 1/n, once per instance (psi_b depends on c2..c4 only)
+  for (int b = 0; b < B; ++b) {
+    const Inst s = inst_at(bb.base, b);
+    k_fill<<<(c->ld + 255) / 256, 256, 0, c->stream>>>(s.x, c->n, c->ld, 1.0 / c->n);
+    PassArgs a = pass_args_inst(cc[(size_t)b].data());
+    a.in[0] = s.x;
+    a.rowout = s.z;
+    TRY(run_pass(c, P64, M_VALGRAD, 1, a, nullptr, s.spart));
+    TRY(reduce_cols(c, P64, 1, bb.G0 + (size_t)b * c->ld, c->ld, nullptr, 0.0, nullptr, nullptr));
+    c->launches += 1;
+  }
   // start every instance
   for (int b = 0; b < B; ++b) {
     InstRun& r = run[(size_t)b];
@@ -504,12 +763,16 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     if (fin.empty()) continue;
     for (int b : fin) {
       const Inst s = inst_at(bb.base, b);
-      PassArgs a = pass_args_inst(run[(size_t)b].cc.data());
-      a.in[0] = s.x;
-      a.rowout = s.z;
-      TRY(run_pass(c, P64, M_VALGRAD, 1, a, nullptr, s.spart));
-      TRY(reduce_cols(c, P64, 1, s.g, c->ld, c->mu, 0.0, nullptr, nullptr, s.sd + SD_C1));
-      k_eval_finish<<<1, kVT, 0, c->stream>>>(s, nullptr, c->grid, s.tmp + (size_t)23 * ld);
+      if (run[(size_t)b].run_status == MVSK_OK) {
+        k_eval_state<<<1, 32, 0, c->stream>>>(s, s.tmp + (size_t)23 * ld);
+      } else {  // the best iterate was restored: evaluate it
+        PassArgs a = pass_args_inst(run[(size_t)b].cc.data());
+        a.in[0] = s.x;
+        a.rowout = s.z;
+        TRY(run_pass(c, P64, M_VALGRAD, 1, a, nullptr, s.spart));
+        TRY(reduce_cols(c, P64, 1, s.g, c->ld, c->mu, 0.0, nullptr, nullptr, s.sd + SD_C1));
+        k_eval_finish<<<1, kVT, 0, c->stream>>>(s, nullptr, c->grid, s.tmp + (size_t)23 * ld);
+      }
       CU(cudaMemcpyAsync(evh.data() + 4 * (size_t)b, s.tmp + (size_t)23 * ld, 3 * sizeof(double),
                          cudaMemcpyDeviceToHost, c->stream));
       CU(cudaMemcpyAsync(evh.data() + 4 * (size_t)b + 3, s.sd + SD_KKT0, sizeof(double), cudaMemcpyDeviceToHost,

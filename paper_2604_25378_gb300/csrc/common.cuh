@@ -79,7 +79,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // Block-wide sum over blockDim.x threads (multiple of 32) in a fixed order.
-// `scratch` holds >= 32 doubles.  All threads receive the result.
+// `scratch` holds >= 33 doubles (slot 32 broadcasts the total).  All threads
+// receive the result.
 __device__ __forceinline__ double block_sum(double v, double* scratch) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   v = warp_sum(v);

@@ -279,7 +279,7 @@ mvsk_status direction_direct(mvsk_ctx* c) {
   k_project_V<<<1, kVT, 0, c->stream>>>(s, s.at);
   const int ca = c->ncolmax - 1;
   k_matvec<<<mvb, 256, 0, c->stream>>>(c->Bm, ld, n, s.at, nullptr, s.X + (size_t)ca * ld);
-  k_assemble<<<1, kVT, 0, c->stream>>>(s, ca);
+  k_assemble<double><<<1, kVT, 0, c->stream>>>(s, ca);
   c->launches += 3;
   CU(cudaGetLastError());
   return MVSK_OK;

@@ -16,6 +16,7 @@
 #include "dense.cuh"
 #include "gemm_tc.cuh"
 #include "internal.h"
+#include "ozaki.cuh"
 #include "mvsk.h"
 #include "solver_kernels.cuh"
 
@@ -31,6 +32,7 @@ struct Options {
   double descent_eps = 1e-10, stall_factor = 0.99, cal_rel_tol = 1e-9, cal_bracket_tol = 1e-12;
   int max_iter = 300, pcg_max_iter = 40, restart_iter = 120, krylov_maxit = 15, probes = 8;
   int stall_window = 10, pref_scaling = 1, oracle_prec = 0, arc_halvings = 40, cal_max_evals = 40, trace = 0;
+  int split_products = 1;  // batched solves: FP64 products on the tensor cores (ozaki.cuh)
   unsigned long long probe_seed = 0x5EEDull;
 };
 
@@ -43,6 +45,27 @@ struct BatchBuf {
   __nv_bfloat16* S16T = nullptr;
   float* part = nullptr;
   size_t part_floats = 0;
+  double* Wt = nullptr;  // psi'(z) of every instance (T-strided), right-hand side of A^T W
+  double* G0 = nullptr;  // T^-1 A^T psi'_b(A 1/n) of every instance (ld-strided): gradient at 1/n less c1 mu
+  __nv_bfloat16* H16 = nullptr;  // psi''_b(z_b) of every instance (Tp-strided BF16)
+  float* Hf = nullptr;           // the same in FP32 (T-strided)
+  int* need = nullptr;   // any instance needs the second line-search product
+};
+
+// Digit planes and buffers of the emulated-FP64 tensor-core products (ozaki.cuh).
+struct OzBuf {
+  __nv_bfloat16* AF = nullptr;  // digits of the rows of A: kOzS planes of MpF x ld
+  __nv_bfloat16* AB = nullptr;  // digits of the columns of A: kOzS planes of MpB x ldT
+  int* eF = nullptr;            // row exponents (MpF)
+  int* eB = nullptr;            // column exponents (MpB)
+  __nv_bfloat16* XF = nullptr;  // right-hand digits, kOzS*kOzMaxB rows x ld
+  __nv_bfloat16* XB = nullptr;  // right-hand digits, kOzS*kOzMaxB rows x ldT
+  int* fF = nullptr;            // right-hand exponents (kOzMaxB)
+  int* fB = nullptr;
+  long long* part = nullptr;    // split partials
+  long long MpF = 0, ldT = 0;
+  int MpB = 0, bp = 0;          // bp: vector count the right-hand maps are encoded for
+  CUtensorMap tmAF, tmAB, tmXF, tmXB;
 };
 
 }  // namespace
@@ -91,6 +114,7 @@ struct mvsk_ctx {
   // K-major BF16 operands of the tensor-core products (n x Tp, Tp = T rounded up to 8)
   __nv_bfloat16* A16T = nullptr;
   __nv_bfloat16* W16T = nullptr;
+  __nv_bfloat16* A2_16T = nullptr;  // bf16(a_ti^2), n x Tp (diagonal of the weighted Gram)
   long long Tp = 0;
   // tensor-core PCG products: BF16 columns, S^T, split-K partials, cached tensor maps
   __nv_bfloat16* P16 = nullptr;
@@ -98,6 +122,7 @@ struct mvsk_ctx {
   float* part32 = nullptr;
   CUtensorMap tm_A16, tm_P16, tm_A16T, tm_S16T;
   BatchBuf batch;
+  OzBuf oz;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_kind;  // kind id per event pair
   size_t ev_used = 0;
@@ -327,8 +352,20 @@ PassArgs pass_args(mvsk_ctx* c) {
 }
 
 // Profiling: kind ids 0..383 are streaming passes ((prec*16 + mode)*8 + nin);
-// 400 + bn are tensor-core products with N tile bn.
-constexpr int kProfKinds = 700;
+// 400 + bn are tensor-core products with N tile bn; 680/681 the split FP64
+// products; 700 + i the named kernels of kKernelNames.
+constexpr int kProfKinds = 760;
+constexpr int kKindNamed = 700;
+const char* const kKernelNames[] = {"k_face", "k_probe_fill", "k_pcg_setup", "k_pcg_step", "k_cols_bf16_b",
+                                    "k_reduce_hvp1_b", "k_reduce_hvp2_b", "k_reduce_rhat_b", "k_pcg_setup2",
+                                    "k_assemble", "k_decide1", "k_decide2", "k_end_iter", "k_oz_fin_z",
+                                    "k_oz_fin_g", "k_oz_fin_ls", "k_oz_split_vecs", "k_need_ls2", "k_reduce_cols",
+                                    "k_hd_cols", "k_hd_reduce1", "k_hd_reduce2", "k_hd_reduce_diag"};
+enum NamedKernel : int {
+  NK_FACE, NK_PROBE_FILL, NK_PCG_SETUP, NK_PCG_STEP, NK_COLS, NK_HVP1, NK_HVP2, NK_RHAT, NK_PCG_SETUP2, NK_ASSEMBLE,
+  NK_DECIDE1, NK_DECIDE2, NK_END_ITER, NK_OZ_Z, NK_OZ_G, NK_OZ_LS, NK_OZ_SPLIT, NK_NEED, NK_REDUCE_COLS, NK_HD_COLS,
+  NK_HD_RED1, NK_HD_RED2, NK_HD_DIAG, NK_COUNT
+};
 
 mvsk_status prof_begin(mvsk_ctx* c, int kind, double work) {
   if (!c->prof_on) return MVSK_OK;
@@ -362,6 +399,16 @@ mvsk_status prof_end(mvsk_ctx* c) {
   c->ev_used += 2;
   return MVSK_OK;
 }
+
+// Launch statement `launch` bracketed by profiler events of named kernel nk.
+#define PROF_LAUNCH(nk, launch)                    \
+  do {                                             \
+    TRY(prof_begin(c, kKindNamed + (nk), 0.0));    \
+    launch;                                        \
+    CU(cudaGetLastError());                        \
+    TRY(prof_end(c));                              \
+    c->launches += 1;                              \
+  } while (0)
 
 // Fold the event pairs [b, e) into the per-kind totals (stream must be idle).
 mvsk_status prof_collect(mvsk_ctx* c, size_t b, size_t e) {
@@ -456,6 +503,10 @@ mvsk_status init_kernel_attributes() {
                           (int)tc_smem_bytes<64, 6>()));
   CU(cudaFuncSetAttribute(k_gemm_tc<256, 4, EpiPartT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)tc_smem_bytes<256, 4>()));
+  CU(cudaFuncSetAttribute(k_oz_gemm<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes(16)));
+  CU(cudaFuncSetAttribute(k_oz_gemm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes(32)));
+  CU(cudaFuncSetAttribute(k_oz_gemm<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes(48)));
+  CU(cudaFuncSetAttribute(k_oz_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes(64)));
   done = true;
   return MVSK_OK;
 }
@@ -486,10 +537,10 @@ mvsk_status direction_pcg(mvsk_ctx* c) {
     TRY(reduce_cols(c, P, 2, c->hd, c->ld, nullptr, 0.0, skipdir, nullptr));
   }
   if (K > 0) {
-    k_probe_fill<<<dim3((c->ld + 255) / 256, K), 256, 0, c->stream>>>(s, K);
+    k_probe_fill<double><<<dim3((c->ld + 255) / 256, K), 256, 0, c->stream>>>(s, K);
     c->launches += 1;
   }
-  k_pcg_setup<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid, ngroups);
+  k_pcg_setup<double><<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid, ngroups);
   CU(cudaGetLastError());
   c->launches += 3 + 2 * kmax;  // setup, setup2, assemble, the pcg_step launches
   if (P == P16 && ncol1 <= kTcCols && 2 * K <= kTcCols) {
@@ -497,7 +548,7 @@ mvsk_status direction_pcg(mvsk_ctx* c) {
     TRY(ensure_tc_pcg(c));
     for (int it = 0; it < kmax; ++it) {
       TRY(hvp_tc(c, 0, ncol1, skipdir, nullptr));
-      k_pcg_step<<<ncol1, kPT, 0, c->stream>>>(s, 0, kmax);
+      k_pcg_step<double><<<ncol1, kPT, 0, c->stream>>>(s, 0, kmax);
       CU(cudaGetLastError());
     }
     if (K > 0) {
@@ -505,14 +556,14 @@ mvsk_status direction_pcg(mvsk_ctx* c) {
     } else {
       CU(cudaMemsetAsync(s.at, 0, sizeof(double) * c->ld, c->stream));
     }
-    k_pcg_setup2<<<1, kVT, 0, c->stream>>>(s, ca, ca / 2);
+    k_pcg_setup2<double><<<1, kVT, 0, c->stream>>>(s, ca, ca / 2);
     CU(cudaGetLastError());
     for (int it = 0; it < kmax; ++it) {
       TRY(hvp_tc(c, ca, 1, skipdir, s.si + SI_LIVE + ca / 2));
-      k_pcg_step<<<1, kPT, 0, c->stream>>>(s, ca, kmax);
+      k_pcg_step<double><<<1, kPT, 0, c->stream>>>(s, ca, kmax);
       CU(cudaGetLastError());
     }
-    k_assemble<<<1, kVT, 0, c->stream>>>(s, ca);
+    k_assemble<double><<<1, kVT, 0, c->stream>>>(s, ca);
     CU(cudaGetLastError());
     return MVSK_OK;
   }
@@ -528,7 +579,7 @@ mvsk_status direction_pcg(mvsk_ctx* c) {
       TRY(run_pass(c, P, M_HVP, nin, a, s.si + SI_LIVE + g));
       TRY(reduce_cols(c, P, nin, s.Q + (size_t)c0 * c->ld, c->ld, nullptr, 0.0, skipdir, s.si + SI_LIVE + g));
     }
-    k_pcg_step<<<ncol1, kPT, 0, c->stream>>>(s, 0, kmax);
+    k_pcg_step<double><<<ncol1, kPT, 0, c->stream>>>(s, 0, kmax);
     CU(cudaGetLastError());
   }
   if (K > 0) {
@@ -551,7 +602,7 @@ mvsk_status direction_pcg(mvsk_ctx* c) {
   } else {
     CU(cudaMemsetAsync(s.at, 0, sizeof(double) * c->ld, c->stream));
   }
-  k_pcg_setup2<<<1, kVT, 0, c->stream>>>(s, ca, ca / 2);
+  k_pcg_setup2<double><<<1, kVT, 0, c->stream>>>(s, ca, ca / 2);
   CU(cudaGetLastError());
   for (int it = 0; it < kmax; ++it) {
     PassArgs a = pass_args(c);
@@ -560,10 +611,10 @@ mvsk_status direction_pcg(mvsk_ctx* c) {
     a.skip = skipdir;
     TRY(run_pass(c, P, M_HVP, 1, a, s.si + SI_LIVE + ca / 2));
     TRY(reduce_cols(c, P, 1, s.Q + (size_t)ca * c->ld, c->ld, nullptr, 0.0, skipdir, s.si + SI_LIVE + ca / 2));
-    k_pcg_step<<<1, kPT, 0, c->stream>>>(s, ca, kmax);
+    k_pcg_step<double><<<1, kPT, 0, c->stream>>>(s, ca, kmax);
     CU(cudaGetLastError());
   }
-  k_assemble<<<1, kVT, 0, c->stream>>>(s, ca);
+  k_assemble<double><<<1, kVT, 0, c->stream>>>(s, ca);
   CU(cudaGetLastError());
   return MVSK_OK;
 }
@@ -813,6 +864,7 @@ mvsk_status third_tc(mvsk_ctx* c, int K, const int* skip) {
 }
 
 #include "direct_impl.cuh"
+#include "ozaki_impl.cuh"
 #include "batch_impl.cuh"
 
 mvsk_status direction(mvsk_ctx* c, int cfg) { return cfg == MVSK_PCG ? direction_pcg(c) : direction_direct(c); }
@@ -1311,6 +1363,7 @@ mvsk_status mvsk_set_option(mvsk_ctx* c, const char* key, double v) {
   else if (k == "stall_window" && cnt(v, 0, 15)) o.stall_window = (int)v;
   else if (k == "trace" && cnt(v, 0, 1)) o.trace = (int)v;
   else if (k == "graphs" && cnt(v, 0, 1)) c->use_graphs = v != 0.0;
+  else if (k == "split_products" && cnt(v, 0, 1)) o.split_products = (int)v;
   else return fail(MVSK_EINVAL, "unknown option or bad value: %s = %g", key, v);
   if (c->prefs_set && k == "pref_scaling") mvsk_set_prefs(c, c->lam, c->target);
   return MVSK_OK;
@@ -1423,6 +1476,31 @@ mvsk_status mvsk_oracle_gram(mvsk_ctx* c, const double* w, double* G) {
   return sync(c);
 }
 
+// out_b = A V_b (transpose = 0, T values) or A^T V_b (transpose = 1,
+// n values) with the emulated-FP64 tensor-core product; device pointers.
+mvsk_status mvsk_product(mvsk_ctx* c, int32_t transpose, int32_t nvec, const double* V, int64_t ldv, double* out,
+                         int64_t ldo) {
+  if (c == nullptr || V == nullptr || out == nullptr) return fail(MVSK_EINVAL, "null argument");
+  if (nvec < 1 || nvec > kOzMaxB) return fail(MVSK_EINVAL, "nvec must be in [1, %d]", kOzMaxB);
+  const long long K = transpose ? c->T : c->n, M = transpose ? c->n : c->T;
+  if (ldv < K || ldo < M) return fail(MVSK_EINVAL, "leading dimension too small");
+  cudaPointerAttributes pa, pb;
+  CU(cudaPointerGetAttributes(&pa, V));
+  CU(cudaPointerGetAttributes(&pb, out));
+  if (pa.type != cudaMemoryTypeDevice || pb.type != cudaMemoryTypeDevice)
+    return fail(MVSK_EINVAL, "mvsk_product takes device pointers");
+  const int Bp = oz_bp(nvec);
+  int splits = 0;
+  TRY(oz_product(c, transpose ? 1 : 0, V, ldv, nvec, Bp, nullptr, &splits));
+  const OzBuf& o = c->oz;
+  const long long Mp = transpose ? o.MpB : o.MpF;
+  k_oz_store<<<dim3((unsigned)((M + 255) / 256), (unsigned)nvec), 256, 0, c->stream>>>(
+      o.part, splits, Bp, Mp, M, nvec, transpose ? o.eB : o.eF, transpose ? o.fB : o.fF, 1.0, out, ldo);
+  c->launches += 1;
+  CU(cudaGetLastError());
+  return sync(c);
+}
+
 mvsk_status mvsk_oracle_ls(mvsk_ctx* c, const double* w, const double* d, double coef[5], double* alpha_max) {
   if (c == nullptr || w == nullptr || d == nullptr || coef == nullptr) return fail(MVSK_EINVAL, "null argument");
   if (!c->prefs_set) return fail(MVSK_ESTATE, "mvsk_set_prefs must come first");
@@ -1530,8 +1608,14 @@ mvsk_status mvsk_profile_read(mvsk_ctx* c, mvsk_prof_entry* out, int32_t max, in
       if (kind < 400)
         snprintf(out[k].name, sizeof(out[k].name), "rowpass_%s_%s_%d", precs[kind / 128], modes[(kind / 8) % 16],
                  kind % 8);
-      else
+      else if (kind < 680)
         snprintf(out[k].name, sizeof(out[k].name), "gemm_tc_bf16_n%d", kind - 400);
+      else if (kind == 680 || kind == 681)
+        snprintf(out[k].name, sizeof(out[k].name), "oz_gemm_%s", kind == 680 ? "fwd" : "bwd");
+      else if (kind >= kKindNamed && kind < kKindNamed + NK_COUNT)
+        snprintf(out[k].name, sizeof(out[k].name), "%s", kKernelNames[kind - kKindNamed]);
+      else
+        snprintf(out[k].name, sizeof(out[k].name), "kernel_%d", kind);
       out[k].launches = n[kind];
       out[k].total_ms = ms[kind];
       out[k].bytes_per_launch = wk[kind] / (double)n[kind];

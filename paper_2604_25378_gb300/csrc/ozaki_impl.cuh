@@ -1,0 +1,108 @@
+// Host side of the emulated-FP64 tensor-core products A V and A^T V
+// (kernels and the splitting in ozaki.cuh).  Included by mvsk_api.cu.
+#pragma once
+
+constexpr int kKindOz = 680;  // profiler kinds: 680 = A V, 681 = A^T V
+
+// Digit planes of A in both orientations (once per context) and the
+// right-hand tensor maps for Bp vectors (Bp a multiple of 16, at most 64).
+mvsk_status oz_prepare(mvsk_ctx* c, int Bp) {
+  OzBuf& o = c->oz;
+  if (Bp < 16 || Bp > kOzMaxB || Bp % 16 != 0) return fail(MVSK_EINVAL, "emulated product of %d vectors", Bp);
+  if (o.AF == nullptr) {
+    o.MpF = (c->T + kTcBM - 1) / kTcBM * kTcBM;
+    o.MpB = (c->n + kTcBM - 1) / kTcBM * kTcBM;
+    o.ldT = (c->T + kTcBK - 1) / kTcBK * kTcBK;
+    void* p;
+    TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * kOzS * (size_t)o.MpF * c->ld));
+    o.AF = (__nv_bfloat16*)p;
+    TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * kOzS * (size_t)o.MpB * o.ldT));
+    o.AB = (__nv_bfloat16*)p;
+    TRY(dalloc(c, &p, sizeof(int) * o.MpF));
+    o.eF = (int*)p;
+    TRY(dalloc(c, &p, sizeof(int) * o.MpB));
+    o.eB = (int*)p;
+    TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * kOzS * kOzMaxB * (size_t)c->ld));
+    o.XF = (__nv_bfloat16*)p;
+    TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * kOzS * kOzMaxB * (size_t)o.ldT));
+    o.XB = (__nv_bfloat16*)p;
+    TRY(dalloc(c, &p, sizeof(int) * 2 * kOzMaxB));
+    o.fF = (int*)p;
+    o.fB = o.fF + kOzMaxB;
+    const size_t sF = (size_t)((c->ld + kOzKc - 1) / kOzKc) * o.MpF;
+    const size_t sB = (size_t)((o.ldT + kOzKc - 1) / kOzKc) * o.MpB;
+    TRY(dalloc(c, &p, sizeof(long long) * kOzMaxB * (sF > sB ? sF : sB)));
+    o.part = (long long*)p;
+    k_oz_row_exp<<<(unsigned)((o.MpF + 7) / 8), 256, 0, c->stream>>>(c->A64, c->ld, c->T, c->n, o.eF, o.MpF);
+    k_oz_split_rows<<<4 * c->nsm, 256, 0, c->stream>>>(c->A64, c->ld, c->T, c->n, o.eF, o.AF, o.MpF, c->ld);
+    k_oz_col_exp<<<(unsigned)(o.MpB / 32), dim3(32, 32), 0, c->stream>>>(c->A64, c->ld, c->T, c->n, o.eB, o.MpB);
+    k_oz_split_cols<<<dim3((unsigned)(o.ldT / 32), (unsigned)(o.MpB / 32)), dim3(32, 8), 0, c->stream>>>(
+        c->A64, c->ld, c->T, c->n, o.eB, o.AB, o.MpB, o.ldT);
+    c->launches += 4;
+    CU(cudaGetLastError());
+    TRY(make_tmap_bf16(&o.tmAF, o.AF, (unsigned long long)c->ld, (unsigned long long)kOzS * o.MpF,
+                       (unsigned long long)c->ld * 2, kTcBK, kTcBM));
+    TRY(make_tmap_bf16(&o.tmAB, o.AB, (unsigned long long)o.ldT, (unsigned long long)kOzS * o.MpB,
+                       (unsigned long long)o.ldT * 2, kTcBK, kTcBM));
+  }
+  if (o.bp != Bp) {
+    TRY(make_tmap_bf16(&o.tmXF, o.XF, (unsigned long long)c->ld, (unsigned long long)kOzS * Bp,
+                       (unsigned long long)c->ld * 2, kTcBK, (unsigned)Bp));
+    TRY(make_tmap_bf16(&o.tmXB, o.XB, (unsigned long long)o.ldT, (unsigned long long)kOzS * Bp,
+                       (unsigned long long)o.ldT * 2, kTcBK, (unsigned)Bp));
+    o.bp = Bp;
+  }
+  return MVSK_OK;
+}
+
+// Digits of the B <= Bp vectors V[b*vstride + k] and the split partials of
+// A V (trans = 0: K = n, M = T) or A^T V (trans = 1: K = T, M = n) in
+// c->oz.part (ld = Mp).  need: device flag (nullable); at 0 the launches
+// return at once (a captured graph keeps them).
+mvsk_status oz_product(mvsk_ctx* c, int trans, const double* V, long long vstride, int B, int Bp, const int* need,
+                       int* splits_out) {
+  TRY(oz_prepare(c, Bp));
+  OzBuf& o = c->oz;
+  const long long K = trans ? c->T : c->n;
+  const long long ldk = trans ? o.ldT : c->ld;
+  const long long M = trans ? c->n : c->T;
+  const long long Mp = trans ? o.MpB : o.MpF;
+  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_split_vecs<<<Bp, 512, 0, c->stream>>>(V, vstride, B, Bp, (int)K, (int)ldk,
+                                                                      trans ? o.fB : o.fF, trans ? o.XB : o.XF,
+                                                                      need)));
+  const int splits = (int)((ldk + kOzKc - 1) / kOzKc);
+  const dim3 grid((unsigned)(Mp / kTcBM), (unsigned)splits);
+  const CUtensorMap& ta = trans ? o.tmAB : o.tmAF;
+  const CUtensorMap& tx = trans ? o.tmXB : o.tmXF;
+  // work: BF16 tensor FLOPs issued (kOzS (kOzS + 1) / 2 digit products)
+  const double flops = 2.0 * (double)Mp * (double)((ldk + kTcBK - 1) / kTcBK * kTcBK) * Bp * (kOzS * (kOzS + 1) / 2);
+  TRY(prof_begin(c, kKindOz + trans, flops));
+  switch (Bp) {
+    case 16:
+      k_oz_gemm<16><<<grid, 128, oz_smem_bytes(16), c->stream>>>(ta, tx, Mp, M, (int)K, o.part, Mp, c->err, need);
+      break;
+    case 32:
+      k_oz_gemm<32><<<grid, 128, oz_smem_bytes(32), c->stream>>>(ta, tx, Mp, M, (int)K, o.part, Mp, c->err, need);
+      break;
+    case 48:
+      k_oz_gemm<48><<<grid, 128, oz_smem_bytes(48), c->stream>>>(ta, tx, Mp, M, (int)K, o.part, Mp, c->err, need);
+      break;
+    default:
+      k_oz_gemm<64><<<grid, 128, oz_smem_bytes(64), c->stream>>>(ta, tx, Mp, M, (int)K, o.part, Mp, c->err, need);
+      break;
+  }
+  CU(cudaGetLastError());
+  TRY(prof_end(c));
+  c->launches += 1;
+  *splits_out = splits;
+  return MVSK_OK;
+}
+
+int oz_bp(int B) { return (B + 15) / 16 * 16; }
+
+// CTAs over t of the row-wise finishing kernels (at most c->grid: the scalar
+// partial slots of an instance).
+int oz_row_ctas(const mvsk_ctx* c) {
+  const long long g = (c->T + 255) / 256;
+  return (int)(g < c->grid ? g : c->grid);
+}

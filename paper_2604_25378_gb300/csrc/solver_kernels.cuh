@@ -232,28 +232,74 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
 
 // --------------------------------------------------- PCG configuration
 // Column layout: 0 = h (Newton part), 1..K = Hutchinson probes, K+1 = a.
-inline __device__ void pcg_init_col(Inst& s, int c, double m, double lam, double* scr) {
+//
+// Krylov vectors X, R, Z, P, Q and the right-hand sides Bv hold elements of
+// type KT: double for single-instance solves, float for lockstep batches
+// (their operator products are BF16 tensor-core products, so FP32 recurrences
+// lose nothing; the FP64 pipe of this part is ~2 FMA/clk/SM).  Face data in KT:
+// for double the instance's own arrays, for float the copies in s.kf
+// ([maskF | nuhat | diag G] written by k_pcg_setup).  Dot products are
+// accumulated per thread in KT and reduced across the block in double.
+template <typename KT>
+struct Face {
+  const KT* mf;
+  const KT* nh;
+  const KT* dg;
+};
+template <typename KT>
+__device__ __forceinline__ Face<KT> face_of(const Inst& s);
+template <>
+__device__ __forceinline__ Face<double> face_of<double>(const Inst& s) {
+  return {s.maskF, s.nuhat, s.diagG};
+}
+template <>
+__device__ __forceinline__ Face<float> face_of<float>(const Inst& s) {
+  return {s.kf, s.kf + s.ld, s.kf + 2 * (size_t)s.ld};
+}
+template <typename KT>
+__device__ __forceinline__ KT* kcol(double* base, int c, int ld) {
+  return reinterpret_cast<KT*>(base) + (size_t)c * ld;
+}
+
+// P_V v on the face (see project_V), v of type TI, out and face data of type KT.
+template <typename KT, typename TI>
+inline __device__ void project_Vk(const TI* v, KT* out, const Face<KT>& f, int n, double m, double* scr) {
+  KT a = 0, b = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    a += f.mf[i] * (KT)v[i];
+    b += f.nh[i] * (KT)v[i];
+  }
+  const double2 r = block_sum2((double)a, (double)b, scr);
+  const KT mean = (KT)(r.x / m), ny = (KT)r.y;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = f.mf[i] * ((KT)v[i] - mean) - ny * f.nh[i];
+  __syncthreads();
+}
+
+template <typename KT>
+inline __device__ void pcg_init_col(Inst& s, int c, double m, double* scr) {
   const int n = s.n, ld = s.ld;
-  double* X = s.X + (size_t)c * ld;
-  double* R = s.R + (size_t)c * ld;
-  double* Z = s.Zc + (size_t)c * ld;
-  double* P = s.P + (size_t)c * ld;
-  const double* B = s.Bv + (size_t)c * ld;
-  double nb = 0.0;
+  const Face<KT> f = face_of<KT>(s);
+  KT* X = kcol<KT>(s.X, c, ld);
+  KT* R = kcol<KT>(s.R, c, ld);
+  KT* Z = kcol<KT>(s.Zc, c, ld);
+  KT* P = kcol<KT>(s.P, c, ld);
+  const KT* B = kcol<KT>(s.Bv, c, ld);
+  KT* tk = reinterpret_cast<KT*>(s.tmp);
+  KT nb = 0;
   for (int i = threadIdx.x; i < ld; i += blockDim.x) {
-    X[i] = 0.0;
+    X[i] = 0;
     R[i] = B[i];
-    s.tmp[i] = i < n ? B[i] / s.diagG[i] : 0.0;
+    tk[i] = i < n ? B[i] / f.dg[i] : (KT)0;
     nb += B[i] * B[i];
   }
   __syncthreads();
-  project_V(s.tmp, Z, s.maskF, s.nuhat, n, m, scr);
-  double rz = 0.0;
+  project_Vk<KT, KT>(tk, Z, f, n, m, scr);
+  KT rz = 0;
   for (int i = threadIdx.x; i < ld; i += blockDim.x) {
     P[i] = Z[i];
     rz += R[i] * Z[i];
   }
-  const double2 r = block_sum2(rz, nb, scr);
+  const double2 r = block_sum2((double)rz, (double)nb, scr);
   if (threadIdx.x == 0) {
     s.rz[c] = r.x;
     s.rhsn[c] = sqrt(r.y);
@@ -264,6 +310,7 @@ inline __device__ void pcg_init_col(Inst& s, int c, double m, double lam, double
 }
 
 // Setup of the first PCG round: lambda, Jacobi diagonal, RHS h and probes.
+template <typename KT>
 static __global__ void __launch_bounds__(kVT) k_pcg_setup(Inst s0, const double* spart, int G, int ngroups) {
   Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
@@ -284,14 +331,22 @@ static __global__ void __launch_bounds__(kVT) k_pcg_setup(Inst s0, const double*
   const double floor_ = 1e-300 + 1e-12 * (r.y / m);
   for (int i = threadIdx.x; i < n; i += blockDim.x)
     s.diagG[i] = s.maskF[i] != 0.0 ? fmax(fabs(s.diagG[i]), floor_) : 1.0;
+  if constexpr (sizeof(KT) == sizeof(float)) {
+    for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+      s.kf[i] = i < n ? (float)s.maskF[i] : 0.f;
+      s.kf[ld + i] = i < n ? (float)s.nuhat[i] : 0.f;
+      s.kf[2 * (size_t)ld + i] = i < n ? (float)s.diagG[i] : 1.f;
+    }
+  }
+  __syncthreads();
   const double trG = r.x - ps[1] / m - ps[0];
   const double lam = SD[SD_REG] * fabs(trG) / (m - 2.0);
+  const Face<KT> f = face_of<KT>(s);
   // RHS 0: h = P_V (G nu)
-  project_V(s.Gnu, s.Bv, s.maskF, s.nuhat, n, m, scr);
+  project_Vk<KT, double>(s.Gnu, kcol<KT>(s.Bv, 0, ld), f, n, m, scr);
   const int K = SI[SI_PROBES];
-  for (int k = 0; k < K; ++k) project_V(s.Bv + (size_t)(k + 1) * ld, s.Bv + (size_t)(k + 1) * ld, s.maskF, s.nuhat,
-                                        n, m, scr);
-  for (int c = 0; c <= K; ++c) pcg_init_col(s, c, m, lam, scr);
+  for (int k = 0; k < K; ++k) project_Vk<KT, KT>(kcol<KT>(s.Bv, k + 1, ld), kcol<KT>(s.Bv, k + 1, ld), f, n, m, scr);
+  for (int c = 0; c <= K; ++c) pcg_init_col<KT>(s, c, m, scr);
   if (threadIdx.x == 0) {
     SD[SD_LAM] = lam;
     for (int g = 0; g < ngroups; ++g) {
@@ -304,6 +359,7 @@ static __global__ void __launch_bounds__(kVT) k_pcg_setup(Inst s0, const double*
 
 // Standard normal probes zeta_k (raw, before projection) into PCG right-hand
 // sides 1..K; the iteration index comes from the device state.
+template <typename KT>
 static __global__ void k_probe_fill(Inst s0, int K) {
   Inst s = inst_at(s0, blockIdx.z);
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
@@ -312,7 +368,7 @@ static __global__ void k_probe_fill(Inst s0, int K) {
   if (k >= K || i >= s.ld) return;
   const unsigned long long seed =
       ((unsigned long long)(unsigned)s.si[SI_SEEDHI] << 32) | (unsigned long long)(unsigned)s.si[SI_SEEDLO];
-  s.Bv[(size_t)(k + 1) * s.ld + i] = i < s.n ? probe_value(seed, s.si[SI_ITER], k, i) : 0.0;
+  kcol<KT>(s.Bv, k + 1, s.ld)[i] = i < s.n ? (KT)probe_value(seed, s.si[SI_ITER], k, i) : (KT)0;
 }
 
 // One PCG step on column blockIdx.x + c0 (Q holds G P from the products):
@@ -321,6 +377,7 @@ static __global__ void k_probe_fill(Inst s0, int K) {
 // coordinates in registers; five fused block reductions.
 constexpr int kPT = 512;                          // threads per PCG column CTA
 constexpr int kPE = (kMaxCols + kPT - 1) / kPT;   // coordinates per thread
+template <typename KT>
 static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s0, int c0, int kmaxit) {
   Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
@@ -330,68 +387,67 @@ static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s0, int c0, int km
   if (SI[SI_ACT + c] == 0) return;
   const int n = s.n, ld = s.ld;
   const double m = (double)SI[SI_M];
-  const double lam = s.sd[SD_LAM];
-  double* X = s.X + (size_t)c * ld;
-  double* R = s.R + (size_t)c * ld;
-  double* Z = s.Zc + (size_t)c * ld;
-  double* P = s.P + (size_t)c * ld;
-  const double* Q = s.Q + (size_t)c * ld;
-  const double* mf = s.maskF;
-  const double* nh = s.nuhat;
-  double q[kPE], p[kPE];
-  double a1 = 0.0, a2 = 0.0;
+  const KT lam = (KT)s.sd[SD_LAM];
+  KT* X = kcol<KT>(s.X, c, ld);
+  KT* R = kcol<KT>(s.R, c, ld);
+  KT* Z = kcol<KT>(s.Zc, c, ld);
+  KT* P = kcol<KT>(s.P, c, ld);
+  const KT* Q = kcol<KT>(s.Q, c, ld);
+  const Face<KT> f = face_of<KT>(s);
+  KT q[kPE], p[kPE];
+  KT a1 = 0, a2 = 0;
 #pragma unroll
   for (int e = 0; e < kPE; ++e) {
     const int i = threadIdx.x + e * kPT;
     const bool in = i < n;
-    q[e] = in ? Q[i] : 0.0;
-    p[e] = in ? P[i] : 0.0;
+    q[e] = in ? Q[i] : (KT)0;
+    p[e] = in ? P[i] : (KT)0;
     if (in) {
-      a1 += mf[i] * q[e];
-      a2 += nh[i] * q[e];
+      a1 += f.mf[i] * q[e];
+      a2 += f.nh[i] * q[e];
     }
   }
-  const double2 r = block_sum2(a1, a2, scr);
-  double pq = 0.0;
-  const double qmean = r.x / m;
+  const double2 r = block_sum2((double)a1, (double)a2, scr);
+  KT pq = 0;
+  const KT qmean = (KT)(r.x / m), ry = (KT)r.y;
 #pragma unroll
   for (int e = 0; e < kPE; ++e) {
     const int i = threadIdx.x + e * kPT;
-    if (i < n) q[e] = mf[i] * (q[e] - qmean) - r.y * nh[i] + lam * p[e];
+    if (i < n) q[e] = f.mf[i] * (q[e] - qmean) - ry * f.nh[i] + lam * p[e];
     pq += p[e] * q[e];
   }
-  pq = block_sum2(pq, 0.0, scr).x;
+  const double pqs = block_sum2((double)pq, 0.0, scr).x;
   auto deactivate = [&]() {
     if (threadIdx.x == 0) {
       SI[SI_ACT + c] = 0;
       atomicSub(&SI[SI_LIVE + c / 2], 1);
     }
   };
-  if (!(pq > 0.0)) {
+  if (!(pqs > 0.0)) {
     deactivate();
     return;
   }
-  const double al = s.rz[c] / pq;
-  double rv[kPE];
-  double rr = 0.0, b1 = 0.0, b2 = 0.0;
+  const KT al = (KT)(s.rz[c] / pqs);
+  KT rv[kPE];
+  KT rr = 0, b1 = 0, b2 = 0;
 #pragma unroll
   for (int e = 0; e < kPE; ++e) {
     const int i = threadIdx.x + e * kPT;
-    rv[e] = 0.0;
+    rv[e] = 0;
     if (i < n) {
       X[i] += al * p[e];
       rv[e] = R[i] - al * q[e];
       R[i] = rv[e];
       rr += rv[e] * rv[e];
-      q[e] = rv[e] / s.diagG[i];  // q now holds t = R / |diag G|
-      b1 += mf[i] * q[e];
-      b2 += nh[i] * q[e];
+      q[e] = rv[e] / f.dg[i];  // q now holds t = R / |diag G|
+      b1 += f.mf[i] * q[e];
+      b2 += f.nh[i] * q[e];
     } else {
-      q[e] = 0.0;
+      q[e] = 0;
     }
   }
-  const double2 r2 = block_sum2(rr, b1, scr);
-  const double b2s = block_sum2(b2, 0.0, scr).x;
+  const double2 r2 = block_sum2((double)rr, (double)b1, scr);
+  const double b2s = block_sum2((double)b2, 0.0, scr).x;
   if (threadIdx.x == 0) {
     SI[SI_CITS + c] += 1;
     atomicAdd(&SI[SI_KRY], 1);
@@ -400,16 +456,16 @@ static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s0, int c0, int km
     deactivate();
     return;
   }
-  const double tmean = r2.y / m;
-  double rzn = 0.0;
+  const KT tmean = (KT)(r2.y / m), tb2 = (KT)b2s;
+  KT rzn = 0;
 #pragma unroll
   for (int e = 0; e < kPE; ++e) {
     const int i = threadIdx.x + e * kPT;
-    if (i < n) q[e] = mf[i] * (q[e] - tmean) - b2s * nh[i];
+    if (i < n) q[e] = f.mf[i] * (q[e] - tmean) - tb2 * f.nh[i];
     rzn += rv[e] * q[e];
   }
-  rzn = block_sum2(rzn, 0.0, scr).x;
-  const double beta = rzn / s.rz[c];
+  const double rzs = block_sum2((double)rzn, 0.0, scr).x;
+  const KT beta = (KT)(rzs / s.rz[c]);
 #pragma unroll
   for (int e = 0; e < kPE; ++e) {
     const int i = threadIdx.x + e * kPT;
@@ -419,7 +475,7 @@ static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s0, int c0, int km
     }
   }
   if (threadIdx.x == 0) {
-    s.rz[c] = rzn;
+    s.rz[c] = rzs;
     if (SI[SI_CITS + c] >= kmaxit) {
       SI[SI_ACT + c] = 0;
       atomicSub(&SI[SI_LIVE + c / 2], 1);
@@ -428,14 +484,15 @@ static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s0, int c0, int km
 }
 
 // Correction vector a = P_V (T^-1 A^T (psi''' o rhat)) and the second PCG round.
+template <typename KT>
 static __global__ void __launch_bounds__(kVT) k_pcg_setup2(Inst s0, int ca, int group) {
   Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
   int* SI = s.si;
   if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
   const double m = (double)SI[SI_M];
-  project_V(s.at, s.Bv + (size_t)ca * s.ld, s.maskF, s.nuhat, s.n, m, scr);
-  pcg_init_col(s, ca, m, s.sd[SD_LAM], scr);
+  project_Vk<KT, double>(s.at, kcol<KT>(s.Bv, ca, s.ld), face_of<KT>(s), s.n, m, scr);
+  pcg_init_col<KT>(s, ca, m, scr);
   if (threadIdx.x == 0) {
     SI[SI_LIVE + group] = SI[SI_ACT + ca];
     SI[SI_THIRD] += 1;
@@ -444,6 +501,7 @@ static __global__ void __launch_bounds__(kVT) k_pcg_setup2(Inst s0, int ca, int 
 
 // d = X_h - (||gbar|| / m) X_a - nu  (ambient; zero off F), re-centred on F so
 // that 1^T d = 0 to rounding relative to d.
+template <typename KT>
 static __global__ void __launch_bounds__(kVT) k_assemble(Inst s0, int ca) {
   Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
@@ -451,11 +509,11 @@ static __global__ void __launch_bounds__(kVT) k_assemble(Inst s0, int ca) {
   if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
   const double m = (double)SI[SI_M];
   const double coef = s.sd[SD_GN] / m;
-  const double* Xh = s.X;
-  const double* Xa = s.X + (size_t)ca * s.ld;
+  const KT* Xh = kcol<KT>(s.X, 0, s.ld);
+  const KT* Xa = kcol<KT>(s.X, ca, s.ld);
   double sd = 0.0;
   for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
-    const double v = i < s.n ? Xh[i] - coef * Xa[i] - s.nuhat[i] : 0.0;
+    const double v = i < s.n ? (double)Xh[i] - coef * (double)Xa[i] - s.nuhat[i] : 0.0;
     s.d[i] = v;
     sd += v;
   }

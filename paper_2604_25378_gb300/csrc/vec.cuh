@@ -43,9 +43,11 @@ struct Inst {
   double *X, *R, *Zc, *P, *Q, *Bv;  // PCG columns, [ncol][ld]
   double *rz, *rhsn;
   double* spart;  // scalar partials of this instance's streaming passes
+  float* kf;      // FP32 face data of FP32 Krylov recurrences [maskF | nuhat | diag G] (batches), else null
   int n, ld;
   long long T;
   long long vs, ts, cs, ps, ncs, ss;  // instance strides: ld-vectors, T-vectors, PCG blocks, scratch, per-column, partials
+  long long kfs;                      // instance stride of kf
 };
 
 __host__ __device__ __forceinline__ Inst inst_at(const Inst& a, int b) {
@@ -64,6 +66,7 @@ __host__ __device__ __forceinline__ Inst inst_at(const Inst& a, int b) {
     s.X += cc; s.R += cc; s.Zc += cc; s.P += cc; s.Q += cc; s.Bv += cc;
     s.rz += (long long)b * a.ncs; s.rhsn += (long long)b * a.ncs;
     s.spart += (long long)b * a.ss;
+    if (s.kf != nullptr) s.kf += (long long)b * a.kfs;
   }
   return s;
 }

@@ -171,10 +171,13 @@ def test_pcg_direction_bf16_tensor_cores():
     assert abs(d_gpu.sum()) <= 1e-12 * np.max(np.abs(d_gpu))
 
 
-def test_batched_lockstep_matches_oracle():
+@pytest.mark.parametrize("split_products", [1, 0])
+def test_batched_lockstep_matches_oracle(split_products):
     """mvsk_solve_batch (PCG, BF16 direction products shared by all instances on
     the tensor cores) against the oracle, instance by instance: preference
-    vectors inside and outside the certificate, with and without targets."""
+    vectors inside and outside the certificate, with and without targets.
+    split_products = 1: value, gradient and line-search products as split
+    tensor-core products; 0: FP64 streaming passes."""
     import paper_2604_25378_gb300 as m
     R = panels.garch_sector_panel(200, 2000, 9)
     mu, A = O.centre(R)
@@ -182,6 +185,7 @@ def test_batched_lockstep_matches_oracle():
     tg = panels.quantile_targets(R, [0.6, 0.7])
     targets = np.array([np.nan, np.nan, tg[0], tg[1]])
     ctx = m.MVSK(R, "bf16")
+    ctx.set_option("split_products", split_products)
     W, infos = ctx.solve_batch(lams, targets, m.PCG, 1e-10)
     for b in range(4):
         c = O.scale_preferences(lams[b], A, "standardised")
@@ -203,3 +207,22 @@ def test_batched_lockstep_matches_oracle():
     ctx.set_prefs(lams[0])
     w0, inf0 = ctx.solve(m.PCG, 1e-10)
     assert np.max(np.abs(w0 - W[0])) <= 1e-9
+
+
+def test_batched_more_than_64_instances():
+    """70 instances: the split products run in groups of 64 and 6 vectors."""
+    import paper_2604_25378_gb300 as m
+    R = panels.sector_factor_panel(30, 400, 4)
+    mu, A = O.centre(R)
+    rng = np.random.default_rng(5)
+    lams = np.column_stack([np.ones(70), np.ones(70), rng.uniform(0.3, 2.5, 70), rng.uniform(0.3, 2.5, 70)])
+    ctx = m.MVSK(R, "bf16")
+    W, infos = ctx.solve_batch(lams, np.full(70, np.nan), m.PCG, 1e-10)
+    assert all(i["status"] == "ok" for i in infos), [i["status"] for i in infos]
+    for b in (0, 31, 63, 64, 69):
+        c = O.scale_preferences(lams[b], A, "standardised")
+        x_ref, inf_ref = O.solve(A, mu, c, "pcg", 1e-10)
+        g = O.gradient(A, mu, c, W[b])
+        assert O.kkt_residual(W[b], g, 1e-8) <= 1e-9 * inf_ref.kkt0
+        if O.convexity_certificate(c):
+            assert np.max(np.abs(W[b] - x_ref)) <= 1e-9, (b, np.max(np.abs(W[b] - x_ref)))
