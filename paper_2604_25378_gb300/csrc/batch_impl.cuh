@@ -170,6 +170,26 @@ __global__ void k_grad_from_g0(double* g, const double* G0, const double* mu, do
   if (i < ld) g[i] = i < n ? -c1 * mu[i] + G0[i] : 0.0;
 }
 
+// KKT residual at the 1/n start of the inner solves of instances idx[j]
+// (grid.y = j), the kkt_rel normaliser: g(1/n) = -c1_j mu + G0_b.  Scratch:
+// instance columns 18 (g) and 19 (x = 1/n) of tmp.
+__global__ void __launch_bounds__(kVT) k_kkt0_batch(Inst base, const int* idx, const double* c1, const double* G0) {
+  __shared__ double scr[80];
+  const int b = idx[blockIdx.y];
+  Inst s = inst_at(base, b);
+  const int n = s.n, ld = s.ld;
+  double* g = s.tmp + (size_t)18 * ld;
+  double* x = s.tmp + (size_t)19 * ld;
+  const double cj = c1[blockIdx.y];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    g[i] = -cj * s.mu[i] + G0[(size_t)b * ld + i];
+    x[i] = 1.0 / n;
+  }
+  __syncthreads();
+  const double k0 = kkt_residual(x, g, n, s.sd[SD_TAU], scr, s.tmp);
+  if (threadIdx.x == 0) s.sd[SD_KKT0] = k0;
+}
+
 // (f, KKT residual, mu^T x) of a converged inner solve from its iteration state:
 // the oracle block that declared convergence evaluated them at the current x.
 __global__ void k_eval_state(Inst s0, double* out3) {
@@ -366,6 +386,8 @@ mvsk_status batch_alloc(mvsk_ctx* c, BatchBuf& bb, int B) {
   TRY(get(sizeof(float) * 3 * ld * Bs, &p));
   bb.base.kf = (float*)p;
   bb.base.kfs = 3LL * c->ld;
+  TRY(get(sizeof(double) * 2 * Bs, &p));
+  bb.kq_dev = p;
   if (c->A2_16T == nullptr) {
     TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * (size_t)c->n * c->Tp));
     c->A2_16T = (__nv_bfloat16*)p;
@@ -594,17 +616,35 @@ mvsk_status batch_start_run(mvsk_ctx* c, BatchBuf& bb, int b, InstRun& r, double
   CU(cudaMemcpyAsync(dopts, h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
   k_init_state<<<1, 32, 0, c->stream>>>(s, tol, o.eta, o.pcg_max_iter, 1, o.stall_window, o.probes, o.probe_seed,
                                         o.krylov_maxit, o.arc_halvings, dopts);
-  // KKT residual at the 1/n start (the kkt_rel normaliser): g(1/n) = -c1 mu + G0_b
-  k_fill<<<(c->ld + 255) / 256, 256, 0, c->stream>>>(s.x, c->n, c->ld, 1.0 / c->n);
-  k_grad_from_g0<<<(c->ld + 255) / 256, 256, 0, c->stream>>>(s.g, bb.G0 + (size_t)b * c->ld, c->mu, c1, c->n, c->ld);
-  k_kkt0<<<1, kVT, 0, c->stream>>>(s);
+  // the KKT residual at the 1/n start (kkt_rel normaliser) of every instance
+  // started in this round is evaluated by one k_kkt0_batch (kkt0_flush)
+  bb.kq_idx.push_back(b);
+  bb.kq_c1.push_back(c1);
   if (w0 != nullptr) CU(cudaMemcpyAsync(s.x, w0, sizeof(double) * c->ld, cudaMemcpyDeviceToDevice, c->stream));
+  else k_fill<<<(c->ld + 255) / 256, 256, 0, c->stream>>>(s.x, c->n, c->ld, 1.0 / c->n);
   k_new_phase<<<1, 32, 0, c->stream>>>(s, o.eta, o.pcg_max_iter);
   c->launches += 5;
   CU(cudaGetLastError());
   r.phase = 0;
   r.evals += 1;
   r.t_start = std::chrono::steady_clock::now();
+  return MVSK_OK;
+}
+
+// One k_kkt0_batch for the inner solves started since the last flush.
+mvsk_status kkt0_flush(mvsk_ctx* c, BatchBuf& bb) {
+  const int n = (int)bb.kq_idx.size();
+  if (n == 0) return MVSK_OK;
+  // pageable sources: each copy has taken its data when the call returns
+  double* c1d = reinterpret_cast<double*>(bb.kq_dev);
+  int* idxd = reinterpret_cast<int*>(c1d + bb.cap);
+  CU(cudaMemcpyAsync(c1d, bb.kq_c1.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(idxd, bb.kq_idx.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
+  k_kkt0_batch<<<dim3(1, n), kVT, 0, c->stream>>>(bb.base, idxd, c1d, bb.G0);
+  c->launches += 1;
+  CU(cudaGetLastError());
+  bb.kq_idx.clear();
+  bb.kq_c1.clear();
   return MVSK_OK;
 }
 
@@ -707,6 +747,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       TRY(batch_start_run(c, bb, b, r, 0.0, nullptr, tol));
     }
   }
+  TRY(kkt0_flush(c, bb));
   std::vector<int> si((size_t)B * kSI);
   std::vector<double> evh((size_t)B * 4);
   double* evd = c->vec_scratch + 64;  // not used concurrently with W0 checks (done above)
@@ -714,7 +755,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
   const double phase_eta[3] = {o.eta, o.restart_eta1, o.restart_eta2};
   const int phase_it[3] = {o.pcg_max_iter, o.restart_iter, o.restart_iter};
   int remaining = B;
-  const int every = 3;
+  const int every = 1;  // host checks after every iteration: finished inner solves restart at once
   long long guard_iters = 0;
   while (remaining > 0) {
     for (int q = 0; q < every; ++q) {
@@ -853,6 +894,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
         }
       }
     }
+    TRY(kkt0_flush(c, bb));
     if (guard_iters > 1000000) return fail(MVSK_ECUDA, "batched solve did not terminate");
   }
   // results

@@ -49,6 +49,9 @@ struct BatchBuf {
   double* G0 = nullptr;  // T^-1 A^T psi'_b(A 1/n) of every instance (ld-strided): gradient at 1/n less c1 mu
   __nv_bfloat16* H16 = nullptr;  // psi''_b(z_b) of every instance (Tp-strided BF16)
   float* Hf = nullptr;           // the same in FP32 (T-strided)
+  std::vector<int> kq_idx;       // inner solves started since the last KKT0 flush
+  std::vector<double> kq_c1;
+  void* kq_dev = nullptr;        // device copy: c1 (cap doubles) then indices
   int* need = nullptr;   // any instance needs the second line-search product
 };
 

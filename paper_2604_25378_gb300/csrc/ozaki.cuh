@@ -131,34 +131,35 @@ static __global__ void k_oz_split_cols(const double* A, long long lda, long long
   }
 }
 
-// Digit planes of Bp right-hand vectors: vector b (b < B) is V[b*vstride + k],
-// k < K; out rows u*Bp + b (ldo BF16 each), zero for k >= K or b >= B.  One CTA
-// per vector.  need: when non-null and *need == 0 nothing is done.
-static __global__ void __launch_bounds__(512) k_oz_split_vecs(const double* V, long long vstride, int B, int Bp, int K,
-                                                              int ldo, int* f, __nv_bfloat16* out, const int* need) {
+// Right-hand vectors: vector b (b < B) is V[b*vstride + k], k < K.  Exponent
+// pass: f[b] = max over chunks of the chunk exponent (f preset to kOzNoExp by
+// the caller; all-zero chunks leave it).  Grid (chunks of 1024, Bp).
+constexpr int kOzNoExp = (int)0x80808080;  // byte-fill 0x80: below every exponent
+static __global__ void __launch_bounds__(256) k_oz_vec_exp(const double* V, long long vstride, int B, int K, int* f,
+                                                           const int* need) {
   if (need != nullptr && *need == 0) return;
-  __shared__ double red[32];
-  const int b = blockIdx.x;
+  const int b = blockIdx.y;
+  if (b >= B) return;
   const double* v = V + (size_t)b * vstride;
   double mx = 0.0;
-  if (b < B)
-    for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmax(mx, fabs(v[k]));
+  for (int k = blockIdx.x * 1024 + threadIdx.x; k < K && k < (blockIdx.x + 1) * 1024; k += blockDim.x)
+    mx = fmax(mx, fabs(v[k]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
-    if (threadIdx.x == 0) red[0] = t;
-  }
-  __syncthreads();
-  const int e = oz_exponent(red[0]);
-  if (threadIdx.x == 0) f[b] = e;
-  const size_t plane = (size_t)Bp * ldo;
-  for (int k = threadIdx.x; k < ldo; k += blockDim.x)
-    oz_digits((b < B && k < K) ? v[k] : 0.0, e, out + (size_t)b * ldo + k, plane);
+  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(&f[b], oz_exponent(mx));
+}
+
+// Digit pass: rows u*Bp + b of out (ldo BF16 each), zero for k >= K, b >= B or
+// an all-zero vector.  Grid (ldo / 256, Bp).
+static __global__ void k_oz_vec_digits(const double* V, long long vstride, int B, int Bp, int K, int ldo,
+                                       const int* f, __nv_bfloat16* out, const int* need) {
+  if (need != nullptr && *need == 0) return;
+  const int b = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ldo) return;
+  const int e = b < B ? f[b] : kOzNoExp;
+  const double x = (e != kOzNoExp && k < K) ? V[(size_t)b * vstride + k] : 0.0;
+  oz_digits(x, e != kOzNoExp ? e : 0, out + (size_t)b * ldo + k, (size_t)Bp * ldo);
 }
 
 // ------------------------------------------------------------------ product
@@ -301,17 +302,29 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const __grid_constant__ CUte
 #pragma unroll
       for (int q = 0; q < 16; ++q) acc[q] = 0;
       if (nk > 0) {
+        // Integer values of the FP32 levels by FP32/INT arithmetic only (a
+        // float-to-int64 conversion runs on the FP64 pipe): for |w| < 2^22,
+        // w + 1.5*2^23 rounds w to the nearest integer in the low mantissa bits.
+        constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+        constexpr int kMagicBits = 0x4B400000;
 #pragma unroll 1
         for (int l = 0; l < kOzS; ++l) {
           float v[16];
           tmem_ld16(lane_base + (uint32_t)(l * BP + b0), v);
-          if (l < kOzS - 1) {
+          if (l < kOzS - 1) {  // exact integer, |v| <= 2^24: v = 4096 hi + lo
             const int sh = kOzBits * (kOzS - 2 - l);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) acc[q] += __float2ll_rn(v[q]) * (1LL << sh);
-          } else {
+            for (int q = 0; q < 16; ++q) {
+              const float t = fmaf(v[q], 1.0f / 4096.0f, kMagic);
+              const int hi = __float_as_int(t) - kMagicBits;
+              const float lo = fmaf(-(t - kMagic), 4096.0f, v[q]);
+              const int il = __float_as_int(lo + kMagic) - kMagicBits;
+              acc[q] += (long long)hi * (1LL << (sh + 12)) + (long long)il * (1LL << sh);
+            }
+          } else {  // level kOzS-1 in units of 2^kOzBits of it, rounded
 #pragma unroll
-            for (int q = 0; q < 16; ++q) acc[q] += __float2ll_rn(v[q] * (1.0f / (float)(1 << kOzBits)));
+            for (int q = 0; q < 16; ++q)
+              acc[q] += __float_as_int(fmaf(v[q], 1.0f / (float)(1 << kOzBits), kMagic)) - kMagicBits;
           }
         }
       }
@@ -346,7 +359,7 @@ __device__ __forceinline__ double oz_value(const long long* part, int splits, in
     v += (double)s;
   }
   // digit weights 2^-7(s+1) and 2^-7(u+1), folded levels 2^(7(kOzS-2)):  2^(e + f - 49)
-  return ldexp(v, em + fb - kOzExp);
+  return fb == kOzNoExp ? 0.0 : ldexp(v, em + fb - kOzExp);
 }
 
 // Plain store of the product (the reference entry point and tests):

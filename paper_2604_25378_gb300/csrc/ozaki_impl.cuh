@@ -67,9 +67,12 @@ mvsk_status oz_product(mvsk_ctx* c, int trans, const double* V, long long vstrid
   const long long ldk = trans ? o.ldT : c->ld;
   const long long M = trans ? c->n : c->T;
   const long long Mp = trans ? o.MpB : o.MpF;
-  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_split_vecs<<<Bp, 512, 0, c->stream>>>(V, vstride, B, Bp, (int)K, (int)ldk,
-                                                                      trans ? o.fB : o.fF, trans ? o.XB : o.XF,
-                                                                      need)));
+  int* f = trans ? o.fB : o.fF;
+  CU(cudaMemsetAsync(f, 0x80, sizeof(int) * Bp, c->stream));  // kOzNoExp
+  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_vec_exp<<<dim3((unsigned)((K + 1023) / 1024), Bp), 256, 0, c->stream>>>(
+                               V, vstride, B, (int)K, f, need)));
+  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_vec_digits<<<dim3((unsigned)((ldk + 255) / 256), Bp), 256, 0, c->stream>>>(
+                               V, vstride, B, Bp, (int)K, (int)ldk, f, trans ? o.XB : o.XF, need)));
   const int splits = (int)((ldk + kOzKc - 1) / kOzKc);
   const dim3 grid((unsigned)(Mp / kTcBM), (unsigned)splits);
   const CUtensorMap& ta = trans ? o.tmAB : o.tmAF;

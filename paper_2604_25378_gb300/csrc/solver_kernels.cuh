@@ -386,7 +386,7 @@ static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s0, int c0, int km
   const int c = c0 + blockIdx.x;
   if (SI[SI_ACT + c] == 0) return;
   const int n = s.n, ld = s.ld;
-  const double m = (double)SI[SI_M];
+  const KT m = (KT)SI[SI_M];
   const KT lam = (KT)s.sd[SD_LAM];
   KT* X = kcol<KT>(s.X, c, ld);
   KT* R = kcol<KT>(s.R, c, ld);
@@ -407,27 +407,27 @@ static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s0, int c0, int km
       a2 += f.nh[i] * q[e];
     }
   }
-  const double2 r = block_sum2((double)a1, (double)a2, scr);
-  KT pq = 0;
-  const KT qmean = (KT)(r.x / m), ry = (KT)r.y;
+  block_sum2k<KT>(a1, a2, scr);
+  KT pq = 0, unused = 0;
+  const KT qmean = a1 / m;
 #pragma unroll
   for (int e = 0; e < kPE; ++e) {
     const int i = threadIdx.x + e * kPT;
-    if (i < n) q[e] = f.mf[i] * (q[e] - qmean) - ry * f.nh[i] + lam * p[e];
+    if (i < n) q[e] = f.mf[i] * (q[e] - qmean) - a2 * f.nh[i] + lam * p[e];
     pq += p[e] * q[e];
   }
-  const double pqs = block_sum2((double)pq, 0.0, scr).x;
+  block_sum2k<KT>(pq, unused, scr);
   auto deactivate = [&]() {
     if (threadIdx.x == 0) {
       SI[SI_ACT + c] = 0;
       atomicSub(&SI[SI_LIVE + c / 2], 1);
     }
   };
-  if (!(pqs > 0.0)) {
+  if (!(pq > (KT)0)) {
     deactivate();
     return;
   }
-  const KT al = (KT)(s.rz[c] / pqs);
+  const KT al = (KT)s.rz[c] / pq;
   KT rv[kPE];
   KT rr = 0, b1 = 0, b2 = 0;
 #pragma unroll
@@ -446,26 +446,26 @@ static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s0, int c0, int km
       q[e] = 0;
     }
   }
-  const double2 r2 = block_sum2((double)rr, (double)b1, scr);
-  const double b2s = block_sum2((double)b2, 0.0, scr).x;
+  block_sum2k<KT>(rr, b1, scr);
+  block_sum2k<KT>(b2, unused, scr);
   if (threadIdx.x == 0) {
     SI[SI_CITS + c] += 1;
     atomicAdd(&SI[SI_KRY], 1);
   }
-  if (sqrt(r2.x) <= s.sd[SD_KTOL] * s.rhsn[c]) {
+  if (sqrt((double)rr) <= s.sd[SD_KTOL] * s.rhsn[c]) {
     deactivate();
     return;
   }
-  const KT tmean = (KT)(r2.y / m), tb2 = (KT)b2s;
+  const KT tmean = b1 / m;
   KT rzn = 0;
 #pragma unroll
   for (int e = 0; e < kPE; ++e) {
     const int i = threadIdx.x + e * kPT;
-    if (i < n) q[e] = f.mf[i] * (q[e] - tmean) - tb2 * f.nh[i];
+    if (i < n) q[e] = f.mf[i] * (q[e] - tmean) - b2 * f.nh[i];
     rzn += rv[e] * q[e];
   }
-  const double rzs = block_sum2((double)rzn, 0.0, scr).x;
-  const KT beta = (KT)(rzs / s.rz[c]);
+  block_sum2k<KT>(rzn, unused, scr);
+  const KT beta = rzn / (KT)s.rz[c];
 #pragma unroll
   for (int e = 0; e < kPE; ++e) {
     const int i = threadIdx.x + e * kPT;
@@ -475,7 +475,7 @@ static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s0, int c0, int km
     }
   }
   if (threadIdx.x == 0) {
-    s.rz[c] = rzs;
+    s.rz[c] = (double)rzn;
     if (SI[SI_CITS + c] >= kmaxit) {
       SI[SI_ACT + c] = 0;
       atomicSub(&SI[SI_LIVE + c / 2], 1);

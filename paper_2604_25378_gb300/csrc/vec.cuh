@@ -94,6 +94,44 @@ __device__ __forceinline__ double2 block_sum2(double a, double b, double* scr) {
   return make_double2(scr[64], scr[65]);
 }
 
+// The same in FP32 (scr >= 66 floats).
+__device__ __forceinline__ float2 block_sum2f(float a, float b, float* scr) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __syncthreads();
+  if (lane == 0) {
+    scr[warp] = a;
+    scr[32 + warp] = b;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float ta = lane < nw ? scr[lane] : 0.f, tb = lane < nw ? scr[32 + lane] : 0.f;
+    ta = warp_sum(ta);
+    tb = warp_sum(tb);
+    if (lane == 0) {
+      scr[64] = ta;
+      scr[65] = tb;
+    }
+  }
+  __syncthreads();
+  return make_float2(scr[64], scr[65]);
+}
+
+// Block sums of two values of type KT; scr holds >= 66 doubles.
+template <typename KT>
+__device__ __forceinline__ void block_sum2k(KT& a, KT& b, double* scr) {
+  if constexpr (sizeof(KT) == sizeof(float)) {
+    const float2 r = block_sum2f(a, b, reinterpret_cast<float*>(scr));
+    a = r.x;
+    b = r.y;
+  } else {
+    const double2 r = block_sum2(a, b, scr);
+    a = r.x;
+    b = r.y;
+  }
+}
+
 // Threshold theta of the projection onto Delta(tau) of v = base + s*dir
 // (dir may be null): Pi(v)_i = tau + max(v_i - tau - theta, 0).
 // Michelot (1986): iterate theta = (sum_{u_i > theta} u_i - b)/#{u_i > theta}
