@@ -167,9 +167,11 @@ def run_ours(args, rank, world):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     iters = []
+    torch.cuda.nvtx.range_push("timed_step")  # lets ncu restrict a capture to the timed region
     for _ in range(args.steps):
         _, infos = step()
         iters.append(sum(i["iters"] for i in infos))
+    torch.cuda.nvtx.range_pop()
     e1.record()
     torch.cuda.synchronize()
     clocks = sampler.stop()

@@ -40,20 +40,6 @@ __global__ void k_reduce_hvp1_b(const float* part, int splits, int N, int nc, lo
   S[(size_t)q * Tp + t] = __float2bfloat16(Hf[(size_t)(q / nc) * T + t] * acc);
 }
 
-// Q_b[c0 + j][i] = T^-1 sum_z part[z][b*nc + j][i] in FP32 (i < n; zero padding
-// to ld).  Grid (ld/256, N).
-__global__ void k_reduce_hvp2_b(const float* part, int splits, int N, int nc, int n, int ld, long long ldp,
-                                float scale, Inst base, int c0) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ld) return;
-  const int q = blockIdx.y;
-  const Inst s = inst_at(base, q / nc);
-  float acc = 0.f;
-  if (i < n)
-    for (int z = 0; z < splits; ++z) acc += part[((size_t)z * N + q) * ldp + i];
-  kcol<float>(s.Q, c0 + q % nc, ld)[i] = scale * acc;
-}
-
 // at_b = T^-1 sum_z part[z][b][i] (FP64 output: the back-projected correction).
 __global__ void k_reduce_at_b(const float* part, int splits, int B, int n, int ld, long long ldp, double scale,
                               Inst base) {
@@ -401,22 +387,36 @@ mvsk_status batch_alloc(mvsk_ctx* c, BatchBuf& bb, int B) {
 }
 
 // Split-K tensor-core product with FP32 partials for N columns (N tile 16, 64 or 256).
+// Split-K count for `tiles` output tiles of nk k-blocks.  Tensor-bound tiles
+// (N tile 256): about two CTAs per SM.  Bandwidth-bound tiles (N <= 64): one
+// wave of the `slots` resident CTAs, so every SM streams A at once.  At least
+// 4 k-blocks per split, at most smax splits.
+int pick_splits(int tiles, int nk, int slots, int nsm, bool tensor_bound, int smax) {
+  int sp = tensor_bound ? (2 * nsm + tiles - 1) / tiles : slots / tiles;
+  if (sp > smax) sp = smax;
+  if (sp > nk / 4) sp = nk / 4;
+  return sp < 1 ? 1 : sp;
+}
+
+// N tile and resident CTAs per SM of the batched products.
+inline int tc_bn(int N) { return N <= 16 ? 16 : (N <= 64 ? 64 : 256); }
+inline int tc_ctas_per_sm(int bn) { return bn == 64 ? 2 : 1; }
+
+// Split-K tensor-core product with FP32 partials for N columns (N tile 16, 64 or 256).
 mvsk_status tc_partials_n(mvsk_ctx* c, const void* Aop, int M, const void* Bop, int N, long long K, long long ldk,
                           float* part, size_t part_floats, long long ldp, int* splits_out) {
   CUtensorMap ta, tb;
-  const int bn = N <= 16 ? 16 : (N <= 64 ? 64 : 256);
+  const int bn = tc_bn(N);
   TRY(make_tmap_bf16(&ta, Aop, (unsigned long long)ldk, (unsigned long long)M, (unsigned long long)ldk * 2, kTcBK,
                      kTcBM));
   TRY(make_tmap_bf16(&tb, Bop, (unsigned long long)ldk, (unsigned long long)N, (unsigned long long)ldk * 2, kTcBK,
                      (unsigned)bn));
   const int mt = (M + kTcBM - 1) / kTcBM, nt = (N + bn - 1) / bn;
   const int nk = (int)((K + kTcBK - 1) / kTcBK);
-  int want = (2 * c->nsm + mt * nt - 1) / (mt * nt);
-  const int maxs = (int)(part_floats / ((size_t)N * ldp));
-  if (want > maxs) want = maxs;
-  if (want > 8) want = 8;
-  if (want > nk) want = nk;
-  if (want < 1) want = 1;
+  int smax = (int)(part_floats / ((size_t)N * ldp));
+  if (smax > 8) smax = 8;
+  if (smax < 1) smax = 1;
+  const int want = pick_splits(mt * nt, nk, c->nsm * tc_ctas_per_sm(bn), c->nsm, bn == 256, smax);
   const int ktps = (nk + want - 1) / want;
   const int splits = (nk + ktps - 1) / ktps;
   EpiPartT epi{part, ldp, M, N};
@@ -426,7 +426,7 @@ mvsk_status tc_partials_n(mvsk_ctx* c, const void* Aop, int M, const void* Bop, 
     k_gemm_tc<16, 8, EpiPartT><<<grid, 128, tc_smem_bytes<16, 8>(), c->stream>>>(ta, tb, M, N, (int)K, ktps, epi,
                                                                                 c->err, nullptr, nullptr);
   else if (bn == 64)
-    k_gemm_tc<64, 6, EpiPartT><<<grid, 128, tc_smem_bytes<64, 6>(), c->stream>>>(ta, tb, M, N, (int)K, ktps, epi,
+    k_gemm_tc<64, 4, EpiPartT><<<grid, 128, tc_smem_bytes<64, 4>(), c->stream>>>(ta, tb, M, N, (int)K, ktps, epi,
                                                                                 c->err, nullptr, nullptr);
   else
     k_gemm_tc<256, 4, EpiPartT><<<grid, 128, tc_smem_bytes<256, 4>(), c->stream>>>(ta, tb, M, N, (int)K, ktps, epi,
@@ -438,19 +438,35 @@ mvsk_status tc_partials_n(mvsk_ctx* c, const void* Aop, int M, const void* Bop, 
   return MVSK_OK;
 }
 
-// Q_b[c0..c0+nc) = T^-1 A^T (psi''_b(z_b) o A P_b[c0..c0+nc)) for every instance.
-mvsk_status hvp_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int c0, int nc) {
+// Hessian-vector products of PCG columns c0..c0+nc of every instance, up to
+// the split partials of A^T S (the PCG step sums them):
+// S^T = bf16(psi''(z) o A P16) from the first product, fused into its
+// epilogue when it needs no split-K.  P16 holds the BF16 columns already.
+mvsk_status hvp_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int nc, int* s2) {
   const int N = B * nc;
-  const unsigned gl = (unsigned)((c->ld + 255) / 256), gt = (unsigned)((c->T + 255) / 256);
-  PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl, N), 256, 0, c->stream>>>(bb.base, nc, c0, 0, bb.P16)));
-  int s1 = 0, s2 = 0;
-  TRY(tc_partials_n(c, c->Alo, (int)c->T, bb.P16, N, c->ld, c->ld, bb.part, bb.part_floats, c->T, &s1));
-  PROF_LAUNCH(NK_HVP1, (k_reduce_hvp1_b<<<dim3(gt, N), 256, 0, c->stream>>>(bb.part, s1, N, nc, c->T, c->T, bb.Hf,
-                                                                             bb.S16T, c->Tp)));
-  TRY(tc_partials_n(c, c->A16T, c->n, bb.S16T, N, c->Tp, c->Tp, bb.part, bb.part_floats, c->ld, &s2));
-  PROF_LAUNCH(NK_HVP2, (k_reduce_hvp2_b<<<dim3(gl, N), 256, 0, c->stream>>>(
-                            bb.part, s2, N, nc, c->n, c->ld, c->ld, (float)(1.0 / (double)c->T), bb.base, c0)));
-  return MVSK_OK;
+  const unsigned gt = (unsigned)((c->T + 255) / 256);
+  const int bn = tc_bn(N), mt = (int)((c->T + kTcBM - 1) / kTcBM), nt = (N + bn - 1) / bn;
+  const int nk = (int)((c->ld + kTcBK - 1) / kTcBK);
+  if (bn == 256 && mt * nt >= c->nsm) {  // enough tiles without split-K: fuse the weighting
+    CUtensorMap ta, tb;
+    TRY(make_tmap_bf16(&ta, c->Alo, (unsigned long long)c->ld, (unsigned long long)c->T,
+                       (unsigned long long)c->ld * 2, kTcBK, kTcBM));
+    TRY(make_tmap_bf16(&tb, bb.P16, (unsigned long long)c->ld, (unsigned long long)N, (unsigned long long)c->ld * 2,
+                       kTcBK, 256));
+    EpiHvp1 epi{bb.S16T, c->Tp, bb.Hf, (int)c->T, N, nc};
+    TRY(prof_begin(c, 400 + bn, 2.0 * (double)c->T * (double)N * (double)c->ld));
+    k_gemm_tc<256, 4, EpiHvp1><<<dim3((unsigned)nt, (unsigned)mt, 1), 128, tc_smem_bytes<256, 4>(), c->stream>>>(
+        ta, tb, (int)c->T, N, c->ld, nk, epi, c->err, nullptr, nullptr);
+    c->launches += 1;
+    CU(cudaGetLastError());
+    TRY(prof_end(c));
+  } else {
+    int s1 = 0;
+    TRY(tc_partials_n(c, c->Alo, (int)c->T, bb.P16, N, c->ld, c->ld, bb.part, bb.part_floats, c->T, &s1));
+    PROF_LAUNCH(NK_HVP1, (k_reduce_hvp1_b<<<dim3(gt, N), 256, 0, c->stream>>>(bb.part, s1, N, nc, c->T, c->T, bb.Hf,
+                                                                               bb.S16T, c->Tp)));
+  }
+  return tc_partials_n(c, c->A16T, c->n, bb.S16T, N, c->Tp, c->Tp, bb.part, bb.part_floats, c->ld, s2);
 }
 
 // rhat_b and at_b = T^-1 A^T (psi3_b(z_b) o rhat_b) for every instance.
@@ -544,9 +560,14 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
   if (K > 0)
     PROF_LAUNCH(NK_PROBE_FILL, (k_probe_fill<float><<<dim3((c->ld + 255) / 256, K, B), 256, 0, c->stream>>>(base, K)));
   PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gz, (ncol1 + 1) / 2)));
+  const unsigned gl = (unsigned)((c->ld + 255) / 256);
+  const float invT = (float)(1.0 / (double)c->T);
+  PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl, B * ncol1), 256, 0, c->stream>>>(base, ncol1, 0, 0, bb.P16)));
   for (int it = 0; it < kmax; ++it) {
-    TRY(hvp_tc_batch(c, bb, B, 0, ncol1));
-    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step<float><<<dim3(ncol1, B), kPT, 0, c->stream>>>(base, 0, kmax)));
+    int s2 = 0;
+    TRY(hvp_tc_batch(c, bb, B, ncol1, &s2));
+    const KPart kp{bb.part, s2, B * ncol1, ncol1, c->ld, invT, bb.P16};
+    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step<float><<<dim3(ncol1, B), kPT, 0, c->stream>>>(base, 0, kmax, kp)));
   }
   if (K > 0) {
     TRY(third_tc_batch(c, bb, B, K));
@@ -554,9 +575,12 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     for (int b = 0; b < B; ++b) CU(cudaMemsetAsync(inst_at(base, b).at, 0, sizeof(double) * c->ld, c->stream));
   }
   PROF_LAUNCH(NK_PCG_SETUP2, (k_pcg_setup2<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca, ca / 2)));
+  PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl, B), 256, 0, c->stream>>>(base, 1, ca, 0, bb.P16)));
   for (int it = 0; it < kmax; ++it) {
-    TRY(hvp_tc_batch(c, bb, B, ca, 1));
-    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step<float><<<dim3(1, B), kPT, 0, c->stream>>>(base, ca, kmax)));
+    int s2 = 0;
+    TRY(hvp_tc_batch(c, bb, B, 1, &s2));
+    const KPart kp{bb.part, s2, B, 1, c->ld, invT, bb.P16};
+    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step<float><<<dim3(1, B), kPT, 0, c->stream>>>(base, ca, kmax, kp)));
   }
   PROF_LAUNCH(NK_ASSEMBLE, (k_assemble<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca)));
   if (split) {

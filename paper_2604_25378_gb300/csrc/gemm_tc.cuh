@@ -146,6 +146,25 @@ struct EpiPartT {
   }
 };
 
+// Epilogue of the first product of a batched Hessian-vector block (no
+// split-K): S^T[q][t] = bf16(h_{q / nc}[t] * acc) for the columns q < N of the
+// N x T output, h in FP32 (T-strided per instance).
+struct EpiHvp1 {
+  __nv_bfloat16* S;
+  long long Tp;
+  const float* Hf;
+  int T, N, nc;
+  template <int CW>
+  __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[CW], int) const {
+    if (m >= T) return;
+#pragma unroll
+    for (int i = 0; i < CW; ++i) {
+      const int q = n0 + i;
+      if (q < N) S[(size_t)q * Tp + m] = __float2bfloat16(Hf[(size_t)(q / nc) * T + m] * v[i]);
+    }
+  }
+};
+
 // Split-K: CTA (x, y, z) computes output tile (n0 = x*BN, m0 = y*128) over the
 // k-tiles [z*ktps, min(nk, (z+1)*ktps)) and hands the epilogue its z.
 template <int BN, int STAGES, class Epi>

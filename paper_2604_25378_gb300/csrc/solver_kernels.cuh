@@ -377,8 +377,19 @@ static __global__ void k_probe_fill(Inst s0, int K) {
 // coordinates in registers; five fused block reductions.
 constexpr int kPT = 512;                          // threads per PCG column CTA
 constexpr int kPE = (kMaxCols + kPT - 1) / kPT;   // coordinates per thread
+// Batched form (kp.part != null): Q is taken as kp.scale * sum of the kp.splits
+// FP32 split partials of the product (row b*nc + blockIdx.x), and the new P is
+// also written in BF16 to kp.P16 (same row) for the next product.
+struct KPart {
+  const float* part;
+  int splits, N, nc;
+  long long ldp;
+  float scale;
+  __nv_bfloat16* P16;
+};
+
 template <typename KT>
-static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s0, int c0, int kmaxit) {
+static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s0, int c0, int kmaxit, KPart kp = KPart{}) {
   Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
   int* SI = s.si;
@@ -396,11 +407,19 @@ static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s0, int c0, int km
   const Face<KT> f = face_of<KT>(s);
   KT q[kPE], p[kPE];
   KT a1 = 0, a2 = 0;
+  const size_t prow = (size_t)blockIdx.y * kp.nc + blockIdx.x;
 #pragma unroll
   for (int e = 0; e < kPE; ++e) {
     const int i = threadIdx.x + e * kPT;
     const bool in = i < n;
-    q[e] = in ? Q[i] : (KT)0;
+    if (kp.part != nullptr) {
+      float acc = 0.f;
+      if (in)
+        for (int z = 0; z < kp.splits; ++z) acc += kp.part[((size_t)z * kp.N + prow) * kp.ldp + i];
+      q[e] = (KT)(kp.scale * acc);
+    } else {
+      q[e] = in ? Q[i] : (KT)0;
+    }
     p[e] = in ? P[i] : (KT)0;
     if (in) {
       a1 += f.mf[i] * q[e];
@@ -471,7 +490,9 @@ static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s0, int c0, int km
     const int i = threadIdx.x + e * kPT;
     if (i < n) {
       Z[i] = q[e];
-      P[i] = q[e] + beta * p[e];
+      const KT pn = q[e] + beta * p[e];
+      P[i] = pn;
+      if (kp.P16 != nullptr) kp.P16[prow * ld + i] = __float2bfloat16((float)pn);
     }
   }
   if (threadIdx.x == 0) {
