@@ -411,7 +411,8 @@ mvsk_status tc_partials_n(mvsk_ctx* c, const void* Aop, int M, const void* Bop, 
                      kTcBM));
   TRY(make_tmap_bf16(&tb, Bop, (unsigned long long)ldk, (unsigned long long)N, (unsigned long long)ldk * 2, kTcBK,
                      (unsigned)bn));
-  const int mt = (M + kTcBM - 1) / kTcBM, nt = (N + bn - 1) / bn;
+  const int mrows = bn == 256 ? 2 * kTcBM : kTcBM;  // N tile 256: two 128-row subtiles per CTA
+  const int mt = (M + mrows - 1) / mrows, nt = (N + bn - 1) / bn;
   const int nk = (int)((K + kTcBK - 1) / kTcBK);
   int smax = (int)(part_floats / ((size_t)N * ldp));
   if (smax > 8) smax = 8;
@@ -429,8 +430,8 @@ mvsk_status tc_partials_n(mvsk_ctx* c, const void* Aop, int M, const void* Bop, 
     k_gemm_tc<64, 4, EpiPartT><<<grid, 128, tc_smem_bytes<64, 4>(), c->stream>>>(ta, tb, M, N, (int)K, ktps, epi,
                                                                                 c->err, nullptr, nullptr);
   else
-    k_gemm_tc<256, 4, EpiPartT><<<grid, 128, tc_smem_bytes<256, 4>(), c->stream>>>(ta, tb, M, N, (int)K, ktps, epi,
-                                                                                  c->err, nullptr, nullptr);
+    k_gemm_tc<256, 3, EpiPartT, 2><<<grid, 128, tc_smem_bytes<256, 3, 2>(), c->stream>>>(
+        ta, tb, M, N, (int)K, ktps, epi, c->err, nullptr, nullptr);
   c->launches += 1;
   CU(cudaGetLastError());
   TRY(prof_end(c));
@@ -445,9 +446,9 @@ mvsk_status tc_partials_n(mvsk_ctx* c, const void* Aop, int M, const void* Bop, 
 mvsk_status hvp_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int nc, int* s2) {
   const int N = B * nc;
   const unsigned gt = (unsigned)((c->T + 255) / 256);
-  const int bn = tc_bn(N), mt = (int)((c->T + kTcBM - 1) / kTcBM), nt = (N + bn - 1) / bn;
+  const int bn = tc_bn(N), mt = (int)((c->T + 2 * kTcBM - 1) / (2 * kTcBM)), nt = (N + bn - 1) / bn;
   const int nk = (int)((c->ld + kTcBK - 1) / kTcBK);
-  if (bn == 256 && mt * nt >= c->nsm) {  // enough tiles without split-K: fuse the weighting
+  if (bn == 256 && 2 * mt * nt >= c->nsm) {  // enough work without split-K: fuse the weighting
     CUtensorMap ta, tb;
     TRY(make_tmap_bf16(&ta, c->Alo, (unsigned long long)c->ld, (unsigned long long)c->T,
                        (unsigned long long)c->ld * 2, kTcBK, kTcBM));
@@ -455,8 +456,8 @@ mvsk_status hvp_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int nc, int* s2) {
                        kTcBK, 256));
     EpiHvp1 epi{bb.S16T, c->Tp, bb.Hf, (int)c->T, N, nc};
     TRY(prof_begin(c, 400 + bn, 2.0 * (double)c->T * (double)N * (double)c->ld));
-    k_gemm_tc<256, 4, EpiHvp1><<<dim3((unsigned)nt, (unsigned)mt, 1), 128, tc_smem_bytes<256, 4>(), c->stream>>>(
-        ta, tb, (int)c->T, N, c->ld, nk, epi, c->err, nullptr, nullptr);
+    k_gemm_tc<256, 3, EpiHvp1, 2><<<dim3((unsigned)nt, (unsigned)mt, 1), 128, tc_smem_bytes<256, 3, 2>(),
+                                   c->stream>>>(ta, tb, (int)c->T, N, c->ld, nk, epi, c->err, nullptr, nullptr);
     c->launches += 1;
     CU(cudaGetLastError());
     TRY(prof_end(c));

@@ -110,9 +110,9 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[CW]) {
   else tmem_ld16(taddr, v);
 }
 
-template <int BN, int STAGES = kTcStages>
+template <int BN, int STAGES = kTcStages, int MT = 1>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
-  return 1024 /* alignment slack */ + (size_t)STAGES * (kTcBM * kTcBK * 2 + BN * kTcBK * 2) + 256;
+  return 1024 /* alignment slack */ + (size_t)STAGES * (MT * kTcBM * kTcBK * 2 + BN * kTcBK * 2) + 256;
 }
 
 // Epilogue: FP64 store C[m*ldc + n] = alpha * acc for m < M, n < N.
@@ -165,23 +165,26 @@ struct EpiHvp1 {
   }
 };
 
-// Split-K: CTA (x, y, z) computes output tile (n0 = x*BN, m0 = y*128) over the
-// k-tiles [z*ktps, min(nk, (z+1)*ktps)) and hands the epilogue its z.
-template <int BN, int STAGES, class Epi>
+// Split-K: CTA (x, y, z) computes output tile (n0 = x*BN, m0 = y*128*MT) over the
+// k-tiles [z*ktps, min(nk, (z+1)*ktps)) and hands the epilogue its z.  MT = 2
+// stacks two 128-row subtiles that share each B tile (accumulators at TMEM
+// columns 0 and BN): a third fewer operand bytes per MAC than MT = 1.
+template <int BN, int STAGES, class Epi, int MT = 1>
 __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
                                                     int ktps, Epi epi, int* err, const int* skip,
                                                     const int* live) {
   static_assert(BN == 16 || BN == 32 || BN == 64 || BN == 128 || BN == 256, "unsupported N tile");
+  static_assert(MT == 1 || (MT == 2 && BN >= 32), "two subtiles need BN >= 32");
   constexpr int kTcStages = STAGES;
-  constexpr uint32_t TCOLS = BN < 32 ? 32 : BN;
+  constexpr uint32_t TCOLS = MT * (BN < 32 ? 32 : BN);
   constexpr int CW = BN < 32 ? BN : 32;
   if (skip != nullptr && *skip != 0) return;
   if (live != nullptr && *live == 0) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  constexpr int ABYTES = kTcBM * kTcBK * 2;
+  constexpr int ABYTES = MT * kTcBM * kTcBK * 2;
   constexpr int BBYTES = BN * kTcBK * 2;
   unsigned char* sA = sm;
   unsigned char* sB = sm + (size_t)kTcStages * ABYTES;
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
   __shared__ int s_issued;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
+  const int m0 = blockIdx.y * kTcBM * MT, n0 = blockIdx.x * BN;
   const int nk_all = (K + kTcBK - 1) / kTcBK;
   const int kt0 = blockIdx.z * ktps;
   const int kt1 = kt0 + ktps < nk_all ? kt0 + ktps : nk_all;
@@ -224,7 +227,10 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
       }
       if (s_abort) break;
       mbar_expect_tx(&full[s], ABYTES + BBYTES);
-      tma_load_2d(sA + (size_t)s * ABYTES, &tmA, (kt0 + i) * kTcBK, m0, &full[s]);
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt)
+        tma_load_2d(sA + (size_t)s * ABYTES + (size_t)mt * kTcBM * kTcBK * 2, &tmA, (kt0 + i) * kTcBK,
+                    m0 + mt * kTcBM, &full[s]);
       tma_load_2d(sB + (size_t)s * BBYTES, &tmB, (kt0 + i) * kTcBK, n0, &full[s]);
       s_issued = i + 1;
     }
@@ -238,11 +244,15 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
         break;
       }
       tc_fence_after();
-      const uint64_t da = umma_desc_sw128(sA + (size_t)s * ABYTES);
       const uint64_t db = umma_desc_sw128(sB + (size_t)s * BBYTES);
 #pragma unroll
       for (int kk = 0; kk < kTcBK / 16; ++kk)
-        umma_bf16(tmem, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+          const uint64_t da = umma_desc_sw128(sA + (size_t)s * ABYTES + (size_t)mt * kTcBM * kTcBK * 2);
+          umma_bf16(tmem + (uint32_t)(mt * (BN < 32 ? 32 : BN)), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk),
+                    idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        }
       umma_commit(&empty[s]);
     }
     umma_commit(done);  // arrives once every MMA issued above has completed
@@ -256,12 +266,15 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
   }
   tc_fence_after();
   if (ok && !s_abort && nk > 0) {
-    const int m = m0 + warp * 32 + lane;
 #pragma unroll 1
-    for (int cc = 0; cc < BN / CW; ++cc) {
-      float v[CW];
-      tmem_ld<CW>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * CW), v);
-      epi.template operator()<CW>(m, n0 + cc * CW, v, (int)blockIdx.z);
+    for (int mt = 0; mt < MT; ++mt) {
+      const int m = m0 + mt * kTcBM + warp * 32 + lane;
+#pragma unroll 1
+      for (int cc = 0; cc < BN / CW; ++cc) {
+        float v[CW];
+        tmem_ld<CW>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * (BN < 32 ? 32 : BN) + cc * CW), v);
+        epi.template operator()<CW>(m, n0 + cc * CW, v, (int)blockIdx.z);
+      }
     }
   }
   tc_fence_before();

@@ -368,7 +368,12 @@ static __global__ void k_probe_fill(Inst s0, int K) {
   if (k >= K || i >= s.ld) return;
   const unsigned long long seed =
       ((unsigned long long)(unsigned)s.si[SI_SEEDHI] << 32) | (unsigned long long)(unsigned)s.si[SI_SEEDLO];
-  kcol<KT>(s.Bv, k + 1, s.ld)[i] = i < s.n ? (KT)probe_value(seed, s.si[SI_ITER], k, i) : (KT)0;
+  KT v = 0;
+  if (i < s.n) {
+    if constexpr (sizeof(KT) == sizeof(float)) v = probe_value_f(seed, s.si[SI_ITER], k, i);
+    else v = probe_value(seed, s.si[SI_ITER], k, i);
+  }
+  kcol<KT>(s.Bv, k + 1, s.ld)[i] = v;
 }
 
 // One PCG step on column blockIdx.x + c0 (Q holds G P from the products):
@@ -389,7 +394,8 @@ struct KPart {
 };
 
 template <typename KT>
-static __global__ void __launch_bounds__(kPT) k_pcg_step(Inst s0, int c0, int kmaxit, KPart kp = KPart{}) {
+static __global__ void __launch_bounds__(kPT, sizeof(KT) == sizeof(float) ? 2 : 1)
+    k_pcg_step(Inst s0, int c0, int kmaxit, KPart kp = KPart{}) {
   Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
   int* SI = s.si;

@@ -269,4 +269,13 @@ __device__ __forceinline__ double probe_value(unsigned long long seed, long long
   return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
 }
 
+// The same normal from the same two uniforms (their top 24 bits), by Box-Muller
+// in FP32: the probes of FP32 Krylov recurrences.
+__device__ __forceinline__ float probe_value_f(unsigned long long seed, long long iteration, int k, int i) {
+  const unsigned long long ps = splitmix64(seed, (unsigned long long)iteration * 256ull + (unsigned long long)k);
+  const float u1 = ((float)(splitmix64(ps, 2ull * (unsigned long long)i) >> 40) + 1.0f) * 0x1.0p-24f;
+  const float u2 = ((float)(splitmix64(ps, 2ull * (unsigned long long)i + 1ull) >> 40) + 1.0f) * 0x1.0p-24f;
+  return sqrtf(-2.0f * logf(u1)) * cosf(6.28318530717958648f * u2);
+}
+
 }  // namespace mvsk
