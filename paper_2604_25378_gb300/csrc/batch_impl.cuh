@@ -387,20 +387,65 @@ mvsk_status batch_alloc(mvsk_ctx* c, BatchBuf& bb, int B) {
 }
 
 // Split-K tensor-core product with FP32 partials for N columns (N tile 16, 64 or 256).
-// Split-K count for `tiles` output tiles of nk k-blocks.  Tensor-bound tiles
-// (N tile 256): about two CTAs per SM.  Bandwidth-bound tiles (N <= 64): one
-// wave of the `slots` resident CTAs, so every SM streams A at once.  At least
-// 4 k-blocks per split, at most smax splits.
-int pick_splits(int tiles, int nk, int slots, int nsm, bool tensor_bound, int smax) {
-  int sp = tensor_bound ? (2 * nsm + tiles - 1) / tiles : slots / tiles;
-  if (sp > smax) sp = smax;
-  if (sp > nk / 4) sp = nk / 4;
-  return sp < 1 ? 1 : sp;
+// Split-K count for `tiles` output tiles of nk k-blocks on `slots` resident
+// CTAs.  Tensor-bound tiles: the count minimising waves * (k-blocks per split)
+// + 6 per split (prologue, epilogue and partial traffic in k-block units).
+// Bandwidth-bound tiles: one wave of resident CTAs, so every SM streams A at
+// once.  At least 4 k-blocks per split, at most smax splits.
+int pick_splits(int tiles, int nk, int slots, bool tensor_bound, int smax) {
+  if (!tensor_bound) {
+    int sp = slots / tiles;
+    if (sp > smax) sp = smax;
+    if (sp > nk / 4) sp = nk / 4;
+    return sp < 1 ? 1 : sp;
+  }
+  int best = 1;
+  long long best_cost = -1;
+  for (int sp = 1; sp <= smax; ++sp) {
+    if (sp > 1 && nk < 4 * sp) break;
+    const long long waves = ((long long)tiles * sp + slots - 1) / slots;
+    const long long cost = waves * ((nk + sp - 1) / sp) + 6LL * sp;
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = sp;
+    }
+  }
+  return best;
 }
 
-// N tile and resident CTAs per SM of the batched products.
-inline int tc_bn(int N) { return N <= 16 ? 16 : (N <= 64 ? 64 : 256); }
+// N tile and resident CTAs per SM of the batched products.  Wide products
+// take the tile among 128, 192 and 256 that pads N least (ties: the wider),
+// since padded columns still cost full MMA work.
+inline int tc_bn(int N) {
+  if (N <= 16) return 16;
+  if (N <= 64) return 64;
+  int best = 256, waste = 1 << 30;
+  for (int bn : {256, 192, 128}) {
+    const int w = (N + bn - 1) / bn * bn - N;
+    if (w < waste) {
+      waste = w;
+      best = bn;
+    }
+  }
+  return best;
+}
 inline int tc_ctas_per_sm(int bn) { return bn == 64 ? 2 : 1; }
+inline bool tc_wide(int bn) { return bn >= 128; }
+
+// Launch of the two-subtile (256-row) product with N tile bn and epilogue epi.
+template <class Epi>
+void launch_tc2(int bn, dim3 grid, cudaStream_t st, const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K,
+                int ktps, const Epi& epi, int* err) {
+  if (bn == 128)
+    k_gemm_tc<128, 3, Epi, 2><<<grid, 128, tc_smem_bytes<128, 3, 2>(), st>>>(ta, tb, M, N, K, ktps, epi, err,
+                                                                            nullptr, nullptr);
+  else if (bn == 192)
+    k_gemm_tc<192, 3, Epi, 2><<<grid, 128, tc_smem_bytes<192, 3, 2>(), st>>>(ta, tb, M, N, K, ktps, epi, err,
+                                                                            nullptr, nullptr);
+  else
+    k_gemm_tc<256, 3, Epi, 2><<<grid, 128, tc_smem_bytes<256, 3, 2>(), st>>>(ta, tb, M, N, K, ktps, epi, err,
+                                                                            nullptr, nullptr);
+}
 
 // Split-K tensor-core product with FP32 partials for N columns (N tile 16, 64 or 256).
 mvsk_status tc_partials_n(mvsk_ctx* c, const void* Aop, int M, const void* Bop, int N, long long K, long long ldk,
@@ -411,13 +456,13 @@ mvsk_status tc_partials_n(mvsk_ctx* c, const void* Aop, int M, const void* Bop, 
                      kTcBM));
   TRY(make_tmap_bf16(&tb, Bop, (unsigned long long)ldk, (unsigned long long)N, (unsigned long long)ldk * 2, kTcBK,
                      (unsigned)bn));
-  const int mrows = bn == 256 ? 2 * kTcBM : kTcBM;  // N tile 256: two 128-row subtiles per CTA
+  const int mrows = tc_wide(bn) ? 2 * kTcBM : kTcBM;  // wide N tiles: two 128-row subtiles per CTA
   const int mt = (M + mrows - 1) / mrows, nt = (N + bn - 1) / bn;
   const int nk = (int)((K + kTcBK - 1) / kTcBK);
   int smax = (int)(part_floats / ((size_t)N * ldp));
   if (smax > 8) smax = 8;
   if (smax < 1) smax = 1;
-  const int want = pick_splits(mt * nt, nk, c->nsm * tc_ctas_per_sm(bn), c->nsm, bn == 256, smax);
+  const int want = pick_splits(mt * nt, nk, c->nsm * tc_ctas_per_sm(bn), tc_wide(bn), smax);
   const int ktps = (nk + want - 1) / want;
   const int splits = (nk + ktps - 1) / ktps;
   EpiPartT epi{part, ldp, M, N};
@@ -430,8 +475,7 @@ mvsk_status tc_partials_n(mvsk_ctx* c, const void* Aop, int M, const void* Bop, 
     k_gemm_tc<64, 4, EpiPartT><<<grid, 128, tc_smem_bytes<64, 4>(), c->stream>>>(ta, tb, M, N, (int)K, ktps, epi,
                                                                                 c->err, nullptr, nullptr);
   else
-    k_gemm_tc<256, 3, EpiPartT, 2><<<grid, 128, tc_smem_bytes<256, 3, 2>(), c->stream>>>(
-        ta, tb, M, N, (int)K, ktps, epi, c->err, nullptr, nullptr);
+    launch_tc2(bn, grid, c->stream, ta, tb, M, N, (int)K, ktps, epi, c->err);
   c->launches += 1;
   CU(cudaGetLastError());
   TRY(prof_end(c));
@@ -448,16 +492,15 @@ mvsk_status hvp_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int nc, int* s2) {
   const unsigned gt = (unsigned)((c->T + 255) / 256);
   const int bn = tc_bn(N), mt = (int)((c->T + 2 * kTcBM - 1) / (2 * kTcBM)), nt = (N + bn - 1) / bn;
   const int nk = (int)((c->ld + kTcBK - 1) / kTcBK);
-  if (bn == 256 && 2 * mt * nt >= c->nsm) {  // enough work without split-K: fuse the weighting
+  if (tc_wide(bn) && 2 * mt * nt >= c->nsm) {  // enough work without split-K: fuse the weighting
     CUtensorMap ta, tb;
     TRY(make_tmap_bf16(&ta, c->Alo, (unsigned long long)c->ld, (unsigned long long)c->T,
                        (unsigned long long)c->ld * 2, kTcBK, kTcBM));
     TRY(make_tmap_bf16(&tb, bb.P16, (unsigned long long)c->ld, (unsigned long long)N, (unsigned long long)c->ld * 2,
-                       kTcBK, 256));
+                       kTcBK, (unsigned)bn));
     EpiHvp1 epi{bb.S16T, c->Tp, bb.Hf, (int)c->T, N, nc};
     TRY(prof_begin(c, 400 + bn, 2.0 * (double)c->T * (double)N * (double)c->ld));
-    k_gemm_tc<256, 3, EpiHvp1, 2><<<dim3((unsigned)nt, (unsigned)mt, 1), 128, tc_smem_bytes<256, 3, 2>(),
-                                   c->stream>>>(ta, tb, (int)c->T, N, c->ld, nk, epi, c->err, nullptr, nullptr);
+    launch_tc2(bn, dim3((unsigned)nt, (unsigned)mt, 1), c->stream, ta, tb, (int)c->T, N, c->ld, nk, epi, c->err);
     c->launches += 1;
     CU(cudaGetLastError());
     TRY(prof_end(c));

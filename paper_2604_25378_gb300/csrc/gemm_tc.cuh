@@ -174,10 +174,11 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
                                                     const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
                                                     int ktps, Epi epi, int* err, const int* skip,
                                                     const int* live) {
-  static_assert(BN == 16 || BN == 32 || BN == 64 || BN == 128 || BN == 256, "unsupported N tile");
+  static_assert(BN == 16 || BN == 32 || BN == 64 || BN == 128 || BN == 192 || BN == 256, "unsupported N tile");
   static_assert(MT == 1 || (MT == 2 && BN >= 32), "two subtiles need BN >= 32");
   constexpr int kTcStages = STAGES;
-  constexpr uint32_t TCOLS = MT * (BN < 32 ? 32 : BN);
+  constexpr uint32_t TUSED = MT * (BN < 32 ? 32 : BN);
+  constexpr uint32_t TCOLS = TUSED <= 32 ? 32 : TUSED <= 64 ? 64 : TUSED <= 128 ? 128 : TUSED <= 256 ? 256 : 512;
   constexpr int CW = BN < 32 ? BN : 32;
   if (skip != nullptr && *skip != 0) return;
   if (live != nullptr && *live == 0) return;
