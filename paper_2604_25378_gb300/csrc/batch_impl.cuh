@@ -437,10 +437,10 @@ template <class Epi>
 void launch_tc2(int bn, dim3 grid, cudaStream_t st, const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K,
                 int ktps, const Epi& epi, int* err) {
   if (bn == 128)
-    k_gemm_tc<128, 3, Epi, 2><<<grid, 128, tc_smem_bytes<128, 3, 2>(), st>>>(ta, tb, M, N, K, ktps, epi, err,
+    k_gemm_tc<128, 4, Epi, 2><<<grid, 128, tc_smem_bytes<128, 4, 2>(), st>>>(ta, tb, M, N, K, ktps, epi, err,
                                                                             nullptr, nullptr);
   else if (bn == 192)
-    k_gemm_tc<192, 3, Epi, 2><<<grid, 128, tc_smem_bytes<192, 3, 2>(), st>>>(ta, tb, M, N, K, ktps, epi, err,
+    k_gemm_tc<192, 4, Epi, 2><<<grid, 128, tc_smem_bytes<192, 4, 2>(), st>>>(ta, tb, M, N, K, ktps, epi, err,
                                                                             nullptr, nullptr);
   else
     k_gemm_tc<256, 3, Epi, 2><<<grid, 128, tc_smem_bytes<256, 3, 2>(), st>>>(ta, tb, M, N, K, ktps, epi, err,

@@ -508,15 +508,15 @@ mvsk_status init_kernel_attributes() {
                           (int)tc_smem_bytes<256, 4>()));
   CU(cudaFuncSetAttribute(k_gemm_tc<64, 4, EpiPartT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)tc_smem_bytes<64, 4>()));
-#define MVSK_TC2_ATTR(BN, EPI)                                                                         \
-  CU(cudaFuncSetAttribute(k_gemm_tc<BN, 3, EPI, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                          (int)tc_smem_bytes<BN, 3, 2>()))
-  MVSK_TC2_ATTR(128, EpiHvp1);
-  MVSK_TC2_ATTR(192, EpiHvp1);
-  MVSK_TC2_ATTR(256, EpiHvp1);
-  MVSK_TC2_ATTR(128, EpiPartT);
-  MVSK_TC2_ATTR(192, EpiPartT);
-  MVSK_TC2_ATTR(256, EpiPartT);
+#define MVSK_TC2_ATTR(BN, ST, EPI)                                                                      \
+  CU(cudaFuncSetAttribute(k_gemm_tc<BN, ST, EPI, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                          (int)tc_smem_bytes<BN, ST, 2>()))
+  MVSK_TC2_ATTR(128, 4, EpiHvp1);
+  MVSK_TC2_ATTR(192, 4, EpiHvp1);
+  MVSK_TC2_ATTR(256, 3, EpiHvp1);
+  MVSK_TC2_ATTR(128, 4, EpiPartT);
+  MVSK_TC2_ATTR(192, 4, EpiPartT);
+  MVSK_TC2_ATTR(256, 3, EpiPartT);
 #undef MVSK_TC2_ATTR
   CU(cudaFuncSetAttribute(k_oz_gemm<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes(16)));
   CU(cudaFuncSetAttribute(k_oz_gemm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes(32)));
