@@ -603,7 +603,8 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
   TRY(hvpdiag_tc_batch(c, bb, B, Gz));
   if (K > 0)
     PROF_LAUNCH(NK_PROBE_FILL, (k_probe_fill<float><<<dim3((c->ld + 255) / 256, K, B), 256, 0, c->stream>>>(base, K)));
-  PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gz, (ncol1 + 1) / 2)));
+  PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gz, -1)));
+  PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup_cols<float><<<dim3(ncol1, B), 512, 0, c->stream>>>(base)));
   const unsigned gl = (unsigned)((c->ld + 255) / 256);
   const float invT = (float)(1.0 / (double)c->T);
   PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl, B * ncol1), 256, 0, c->stream>>>(base, ncol1, 0, 0, bb.P16)));

@@ -341,6 +341,8 @@ static __global__ void __launch_bounds__(kVT) k_pcg_setup(Inst s0, const double*
   __syncthreads();
   const double trG = r.x - ps[1] / m - ps[0];
   const double lam = SD[SD_REG] * fabs(trG) / (m - 2.0);
+  if (threadIdx.x == 0) SD[SD_LAM] = lam;
+  if (ngroups < 0) return;  // the columns are set up by k_pcg_setup_cols
   const Face<KT> f = face_of<KT>(s);
   // RHS 0: h = P_V (G nu)
   project_Vk<KT, double>(s.Gnu, kcol<KT>(s.Bv, 0, ld), f, n, m, scr);
@@ -348,13 +350,34 @@ static __global__ void __launch_bounds__(kVT) k_pcg_setup(Inst s0, const double*
   for (int k = 0; k < K; ++k) project_Vk<KT, KT>(kcol<KT>(s.Bv, k + 1, ld), kcol<KT>(s.Bv, k + 1, ld), f, n, m, scr);
   for (int c = 0; c <= K; ++c) pcg_init_col<KT>(s, c, m, scr);
   if (threadIdx.x == 0) {
-    SD[SD_LAM] = lam;
     for (int g = 0; g < ngroups; ++g) {
       int live = 0;
       for (int c = 2 * g; c < 2 * g + 2 && c <= K; ++c) live += SI[SI_ACT + c];
       SI[SI_LIVE + g] = live;
     }
   }
+}
+
+// Column c = blockIdx.x of the first PCG round of instance blockIdx.y, after
+// k_pcg_setup(..., ngroups = -1): right-hand side (h = P_V G nu for c = 0, the
+// projected probe otherwise) and the PCG start.  Scratch: the instance's tmp
+// column 2 + c.  SI_LIVE is not used by the batched steps.
+template <typename KT>
+static __global__ void __launch_bounds__(512) k_pcg_setup_cols(Inst s0) {
+  Inst s = inst_at(s0, blockIdx.y);
+  __shared__ double scr[80];
+  int* SI = s.si;
+  if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
+  const int c = blockIdx.x;
+  if (c > SI[SI_PROBES]) return;
+  const int n = s.n, ld = s.ld;
+  const double m = (double)SI[SI_M];
+  const Face<KT> f = face_of<KT>(s);
+  if (c == 0) project_Vk<KT, double>(s.Gnu, kcol<KT>(s.Bv, 0, ld), f, n, m, scr);
+  else project_Vk<KT, KT>(kcol<KT>(s.Bv, c, ld), kcol<KT>(s.Bv, c, ld), f, n, m, scr);
+  Inst sc = s;
+  sc.tmp = s.tmp + (size_t)(2 + c) * ld;  // per-column scratch
+  pcg_init_col<KT>(sc, c, m, scr);
 }
 
 // Standard normal probes zeta_k (raw, before projection) into PCG right-hand
