@@ -187,6 +187,12 @@ __global__ void k_eval_state(Inst s0, double* out3) {
   }
 }
 
+// w[t] = psi'(z[t]) with coefficients (c2, c3, c4), t < T.
+__global__ void k_dpsi_into(const double* z, long long T, double c2, double c3, double c4, double* w) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < T) w[t] = Psi{c2, c3, c4}.d1(z[t]);
+}
+
 // need = 1 when some running instance takes the projected segment (second line search).
 __global__ void k_need_ls2(Inst base, int B, int* need) {
   int any = 0;
@@ -612,7 +618,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     int s2 = 0;
     TRY(hvp_tc_batch(c, bb, B, ncol1, &s2));
     const KPart kp{bb.part, s2, B * ncol1, ncol1, c->ld, invT, bb.P16};
-    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step<float><<<dim3(ncol1, B), kPT, 0, c->stream>>>(base, 0, kmax, kp)));
+    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step_f<<<dim3(ncol1, B), kPT, 0, c->stream>>>(base, 0, kmax, kp)));
   }
   if (K > 0) {
     TRY(third_tc_batch(c, bb, B, K));
@@ -625,7 +631,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     int s2 = 0;
     TRY(hvp_tc_batch(c, bb, B, 1, &s2));
     const KPart kp{bb.part, s2, B, 1, c->ld, invT, bb.P16};
-    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step<float><<<dim3(1, B), kPT, 0, c->stream>>>(base, ca, kmax, kp)));
+    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step_f<<<dim3(1, B), kPT, 0, c->stream>>>(base, ca, kmax, kp)));
   }
   PROF_LAUNCH(NK_ASSEMBLE, (k_assemble<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca)));
   if (split) {
@@ -794,15 +800,38 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     }
   } guard{gexec};
   // c1-free part of the gradient at 1/n, once per instance (psi_b depends on c2..c4 only)
-  for (int b = 0; b < B; ++b) {
-    const Inst s = inst_at(bb.base, b);
-    k_fill<<<(c->ld + 255) / 256, 256, 0, c->stream>>>(s.x, c->n, c->ld, 1.0 / c->n);
-    PassArgs a = pass_args_inst(cc[(size_t)b].data());
-    a.in[0] = s.x;
-    a.rowout = s.z;
-    TRY(run_pass(c, P64, M_VALGRAD, 1, a, nullptr, s.spart));
-    TRY(reduce_cols(c, P64, 1, bb.G0 + (size_t)b * c->ld, c->ld, nullptr, 0.0, nullptr, nullptr));
-    c->launches += 1;
+  if (c->opt.split_products != 0) {
+    // z0 = A 1/n is shared: one FP64 pass, then psi'_b(z0) for every instance and
+    // one split product A^T W for all of them
+    const Inst s0 = inst_at(bb.base, 0);
+    k_fill<<<(c->ld + 255) / 256, 256, 0, c->stream>>>(s0.x, c->n, c->ld, 1.0 / c->n);
+    TRY(pass_fwd_z(c, s0.x, s0.z));
+    for (int b = 0; b < B; ++b)
+      k_dpsi_into<<<(unsigned)((c->T + 255) / 256), 256, 0, c->stream>>>(s0.z, c->T, cc[(size_t)b][1], cc[(size_t)b][2],
+                                                                     cc[(size_t)b][3], bb.Wt + (size_t)b * c->T);
+    c->launches += 1 + B;
+    CU(cudaGetLastError());
+    for (int b0 = 0; b0 < B; b0 += kOzMaxB) {
+      const int nb = B - b0 < kOzMaxB ? B - b0 : kOzMaxB;
+      int sp = 0;
+      TRY(oz_product(c, 1, bb.Wt + (size_t)b0 * c->T, c->T, nb, oz_bp(nb), nullptr, &sp));
+      k_oz_store<<<dim3((unsigned)((c->n + 255) / 256), (unsigned)nb), 256, 0, c->stream>>>(
+          c->oz.part, sp, oz_bp(nb), c->oz.MpB, c->n, nb, c->oz.eB, c->oz.fB, 1.0 / (double)c->T,
+          bb.G0 + (size_t)b0 * c->ld, c->ld);
+      c->launches += 1;
+      CU(cudaGetLastError());
+    }
+  } else {
+    for (int b = 0; b < B; ++b) {
+      const Inst s = inst_at(bb.base, b);
+      k_fill<<<(c->ld + 255) / 256, 256, 0, c->stream>>>(s.x, c->n, c->ld, 1.0 / c->n);
+      PassArgs a = pass_args_inst(cc[(size_t)b].data());
+      a.in[0] = s.x;
+      a.rowout = s.z;
+      TRY(run_pass(c, P64, M_VALGRAD, 1, a, nullptr, s.spart));
+      TRY(reduce_cols(c, P64, 1, bb.G0 + (size_t)b * c->ld, c->ld, nullptr, 0.0, nullptr, nullptr));
+      c->launches += 1;
+    }
   }
   // start every instance
   for (int b = 0; b < B; ++b) {

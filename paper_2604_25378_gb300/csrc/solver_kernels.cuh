@@ -533,6 +533,137 @@ static __global__ void __launch_bounds__(kPT, sizeof(KT) == sizeof(float) ? 2 : 
   }
 }
 
+// Block sums of N floats in a fixed order (warp shuffles, then warp 0 over the
+// warp partials); scr holds >= 33 * N floats.  Every thread gets the totals.
+template <int N>
+__device__ __forceinline__ void block_sumNf(float (&v)[N], float* scr) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < N; ++q) v[q] = warp_sum(v[q]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < N; ++q) scr[warp * N + q] = v[q];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      float t = lane < nw ? scr[lane * N + q] : 0.f;
+      t = warp_sum(t);
+      if (lane == 0) scr[32 * N + q] = t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < N; ++q) v[q] = scr[32 * N + q];
+}
+
+// The batched FP32 PCG step (same recurrence as k_pcg_step with kp.part set)
+// with two block reductions instead of five: p^T q and the new r^T z are
+// expanded into sums over the stored vectors,
+//   p^T q   = sum p mf Q - qmean sum p mf - (nu^T Q) sum p nu + lam sum p^2,
+//   r'^T z' = sum r' mf t - tmean sum r' mf - (nu^T t) sum r' nu,  t = r' / diag,
+// so that each block reduction carries every sum of its phase.
+static __global__ void __launch_bounds__(kPT, 2) k_pcg_step_f(Inst s0, int c0, int kmaxit, KPart kp) {
+  Inst s = inst_at(s0, blockIdx.y);
+  __shared__ float scr[33 * 6 + 8];
+  int* SI = s.si;
+  if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
+  const int c = c0 + blockIdx.x;
+  if (SI[SI_ACT + c] == 0) return;
+  const int n = s.n, ld = s.ld;
+  const float m = (float)SI[SI_M];
+  const float lam = (float)s.sd[SD_LAM];
+  float* X = kcol<float>(s.X, c, ld);
+  float* R = kcol<float>(s.R, c, ld);
+  float* P = kcol<float>(s.P, c, ld);
+  const Face<float> f = face_of<float>(s);
+  const size_t prow = (size_t)blockIdx.y * kp.nc + blockIdx.x;
+  float q[kPE], p[kPE];
+  float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // mf.Q, nu.Q, p.mf.Q, p.mf, p.nu, p.p
+#pragma unroll
+  for (int e = 0; e < kPE; ++e) {
+    const int i = threadIdx.x + e * kPT;
+    q[e] = 0.f;
+    p[e] = 0.f;
+    if (i < n) {
+      float acc = 0.f;
+      for (int z = 0; z < kp.splits; ++z) acc += kp.part[((size_t)z * kp.N + prow) * kp.ldp + i];
+      q[e] = kp.scale * acc;
+      p[e] = P[i];
+      const float mq = f.mf[i] * q[e];
+      a[0] += mq;
+      a[1] += f.nh[i] * q[e];
+      a[2] += p[e] * mq;
+      a[3] += p[e] * f.mf[i];
+      a[4] += p[e] * f.nh[i];
+      a[5] += p[e] * p[e];
+    }
+  }
+  block_sumNf<6>(a, scr);
+  const float qmean = a[0] / m, ry = a[1];
+  const float pq = a[2] - qmean * a[3] - ry * a[4] + lam * a[5];
+  auto deactivate = [&]() {
+    if (threadIdx.x == 0) {
+      SI[SI_ACT + c] = 0;
+      atomicSub(&SI[SI_LIVE + c / 2], 1);
+    }
+  };
+  if (!(pq > 0.f)) {
+    deactivate();
+    return;
+  }
+  const float al = (float)s.rz[c] / pq;
+  float b[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // r.r, mf.t, nu.t, r.mf.t, r.mf, r.nu
+#pragma unroll
+  for (int e = 0; e < kPE; ++e) {
+    const int i = threadIdx.x + e * kPT;
+    if (i < n) {
+      const float qq = f.mf[i] * (q[e] - qmean) - ry * f.nh[i] + lam * p[e];
+      X[i] += al * p[e];
+      const float rv = R[i] - al * qq;
+      R[i] = rv;
+      const float t = rv / f.dg[i];
+      q[e] = t;  // q now holds t = R / |diag G|
+      b[0] += rv * rv;
+      b[1] += f.mf[i] * t;
+      b[2] += f.nh[i] * t;
+      b[3] += rv * f.mf[i] * t;
+      b[4] += rv * f.mf[i];
+      b[5] += rv * f.nh[i];
+    }
+  }
+  block_sumNf<6>(b, scr);
+  if (threadIdx.x == 0) {
+    SI[SI_CITS + c] += 1;
+    atomicAdd(&SI[SI_KRY], 1);
+  }
+  if (sqrt((double)b[0]) <= s.sd[SD_KTOL] * s.rhsn[c]) {
+    deactivate();
+    return;
+  }
+  const float tmean = b[1] / m, tb2 = b[2];
+  const float rzn = b[3] - tmean * b[4] - tb2 * b[5];
+  const float beta = rzn / (float)s.rz[c];
+#pragma unroll
+  for (int e = 0; e < kPE; ++e) {
+    const int i = threadIdx.x + e * kPT;
+    if (i < n) {
+      const float zz = f.mf[i] * (q[e] - tmean) - tb2 * f.nh[i];
+      const float pn = zz + beta * p[e];
+      P[i] = pn;
+      kp.P16[prow * ld + i] = __float2bfloat16(pn);
+    }
+  }
+  if (threadIdx.x == 0) {
+    s.rz[c] = (double)rzn;
+    if (SI[SI_CITS + c] >= kmaxit) {
+      SI[SI_ACT + c] = 0;
+      atomicSub(&SI[SI_LIVE + c / 2], 1);
+    }
+  }
+}
+
 // Correction vector a = P_V (T^-1 A^T (psi''' o rhat)) and the second PCG round.
 template <typename KT>
 static __global__ void __launch_bounds__(kVT) k_pcg_setup2(Inst s0, int ca, int group) {
