@@ -238,11 +238,18 @@ mvsk_status mvsk_quartic_argmin(mvsk_ctx* ctx, const double coef[5], double amax
 /*
  * Profiling of the streaming passes over A (tracing, no effect on results).
  * mvsk_profile_enable(ctx, 1) clears the counters and brackets every later
- * pass launch with CUDA events on the context's stream; (ctx, 0) stops.
- * mvsk_profile_read fills up to `max` entries, one per pass kind: its label,
- * launches, summed device time (ms) and algorithmic bytes per launch (one
- * read of A: T * n * element size).  *count receives the number of kinds and
- * *kernel_launches every kernel launch the library issued since enabling.
+ * kernel launch with CUDA events on the context's stream (launches inside
+ * captured CUDA graphs as event nodes, read after each replay); (ctx, 0) stops.
+ * mvsk_profile_only(ctx, prefix) restricts the brackets to kinds whose label
+ * starts with `prefix` (NULL: all kinds), which keeps the event overhead of a
+ * timed run to the kernel of interest.
+ * mvsk_profile_read fills up to `max` entries, one per kind: its label
+ * (streaming pass, tensor-core product, split FP64 product or named kernel),
+ * launches, summed device time (ms) and the average algorithmic work per
+ * launch: bytes for streaming passes (one read of A: T * n * element size),
+ * FLOPs for tensor-core products, 0 for kernels without a fixed figure.
+ * *count receives the number of kinds and *kernel_launches every kernel
+ * launch the library issued since enabling.
  */
 typedef struct {
   char name[56];
@@ -252,6 +259,7 @@ typedef struct {
 } mvsk_prof_entry;
 
 mvsk_status mvsk_profile_enable(mvsk_ctx* ctx, int32_t on);
+mvsk_status mvsk_profile_only(mvsk_ctx* ctx, const char* prefix);
 mvsk_status mvsk_profile_read(mvsk_ctx* ctx, mvsk_prof_entry* out, int32_t max, int32_t* count,
                               int64_t* kernel_launches);
 

@@ -76,6 +76,7 @@ _SIGS = {
     "mvsk_eval_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P,
                                          _P, _P]),
     "mvsk_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "mvsk_profile_only": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "mvsk_profile_read": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
     "mvsk_last_error": (ctypes.c_char_p, [_P]),
     "mvsk_destroy": (None, [_P]),
@@ -264,6 +265,10 @@ class MVSK:
 
     def profile_enable(self, on: bool = True):
         self._check(self._lib.mvsk_profile_enable(self._h, 1 if on else 0))
+
+    def profile_only(self, prefix=None):
+        """Record only kinds whose label starts with `prefix` (None: all)."""
+        self._check(self._lib.mvsk_profile_only(self._h, None if prefix is None else prefix.encode()))
 
     def profile_read(self):
         """({kind: {launches, total_ms, bytes_per_launch}}, kernel launches since enabling)."""

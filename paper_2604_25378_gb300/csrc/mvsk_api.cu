@@ -135,6 +135,8 @@ struct mvsk_ctx {
   std::vector<double> prof_ms;                   // accumulated device ms per kind id
   std::vector<double> prof_work;                 // accumulated algorithmic bytes (passes) or flops (GEMMs)
   std::vector<double> ev_work;                   // work of each recorded pair
+  std::vector<char> prof_sel;                    // kinds recorded (mvsk_profile_only); empty = all
+  bool prof_open = false;                        // a begun pair awaits its end event
 };
 
 namespace {
@@ -371,7 +373,8 @@ enum NamedKernel : int {
 };
 
 mvsk_status prof_begin(mvsk_ctx* c, int kind, double work) {
-  if (!c->prof_on) return MVSK_OK;
+  if (!c->prof_on || (!c->prof_sel.empty() && !c->prof_sel[kind])) return MVSK_OK;
+  c->prof_open = true;
   if (c->prof_n.empty()) {
     c->prof_n.assign(kProfKinds, 0);
     c->prof_ms.assign(kProfKinds, 0.0);
@@ -396,7 +399,8 @@ mvsk_status prof_begin(mvsk_ctx* c, int kind, double work) {
 }
 
 mvsk_status prof_end(mvsk_ctx* c) {
-  if (!c->prof_on) return MVSK_OK;
+  if (!c->prof_on || !c->prof_open) return MVSK_OK;
+  c->prof_open = false;
   CU(cudaEventRecordWithFlags(c->ev_pool[c->ev_used + 1], c->stream,
                               c->ev_in_graph.back() ? cudaEventRecordExternal : cudaEventRecordDefault));
   c->ev_used += 2;
@@ -1576,6 +1580,36 @@ mvsk_status mvsk_quartic_argmin(mvsk_ctx* c, const double coef[5], double amax, 
   return sync(c);
 }
 
+// Label of profiler kind `kind` (see kKernelNames and prof_begin).
+static void kind_name(int kind, char* out, size_t len) {
+  static const char* modes[] = {"valgrad", "fwd", "hvp", "hvpdiag", "third", "rhat", "back", "ls"};
+  static const char* precs[] = {"fp64", "bf16", "fp32"};
+  if (kind < 400)
+    snprintf(out, len, "rowpass_%s_%s_%d", precs[(kind / 128) % 3], modes[(kind / 8) % 16 % 8], kind % 8);
+  else if (kind < 680)
+    snprintf(out, len, "gemm_tc_bf16_n%d", kind - 400);
+  else if (kind == 680 || kind == 681)
+    snprintf(out, len, "oz_gemm_%s", kind == 680 ? "fwd" : "bwd");
+  else if (kind >= kKindNamed && kind < kKindNamed + NK_COUNT)
+    snprintf(out, len, "%s", kKernelNames[kind - kKindNamed]);
+  else
+    snprintf(out, len, "kernel_%d", kind);
+}
+
+mvsk_status mvsk_profile_only(mvsk_ctx* c, const char* prefix) {
+  if (c == nullptr) return fail(MVSK_EINVAL, "null context");
+  c->prof_sel.clear();
+  if (prefix == nullptr) return MVSK_OK;
+  c->prof_sel.assign(kProfKinds, 0);
+  const size_t len = strlen(prefix);
+  char nm[64];
+  for (int k = 0; k < kProfKinds; ++k) {
+    kind_name(k, nm, sizeof(nm));
+    c->prof_sel[k] = strncmp(nm, prefix, len) == 0 ? 1 : 0;
+  }
+  return MVSK_OK;
+}
+
 mvsk_status mvsk_profile_enable(mvsk_ctx* c, int32_t on) {
   if (c == nullptr) return fail(MVSK_EINVAL, "null context");
   CU(cudaStreamSynchronize(c->stream));
@@ -1614,23 +1648,11 @@ mvsk_status mvsk_profile_read(mvsk_ctx* c, mvsk_prof_entry* out, int32_t max, in
     ms[c->ev_kind[q]] += t;
     wk[c->ev_kind[q]] += c->ev_work[q];
   }
-  static const char* modes[] = {"valgrad", "fwd", "hvp", "hvpdiag", "third", "rhat", "back", "ls"};
-  static const char* precs[] = {"fp64", "bf16", "fp32"};
-  int k = 0;
+    int k = 0;
   for (int kind = 0; kind < kProfKinds; ++kind) {
     if (n[kind] == 0) continue;
     if (k < max) {
-      if (kind < 400)
-        snprintf(out[k].name, sizeof(out[k].name), "rowpass_%s_%s_%d", precs[kind / 128], modes[(kind / 8) % 16],
-                 kind % 8);
-      else if (kind < 680)
-        snprintf(out[k].name, sizeof(out[k].name), "gemm_tc_bf16_n%d", kind - 400);
-      else if (kind == 680 || kind == 681)
-        snprintf(out[k].name, sizeof(out[k].name), "oz_gemm_%s", kind == 680 ? "fwd" : "bwd");
-      else if (kind >= kKindNamed && kind < kKindNamed + NK_COUNT)
-        snprintf(out[k].name, sizeof(out[k].name), "%s", kKernelNames[kind - kKindNamed]);
-      else
-        snprintf(out[k].name, sizeof(out[k].name), "kernel_%d", kind);
+      kind_name(kind, out[k].name, sizeof(out[k].name));
       out[k].launches = n[kind];
       out[k].total_ms = ms[kind];
       out[k].bytes_per_launch = wk[kind] / (double)n[kind];
