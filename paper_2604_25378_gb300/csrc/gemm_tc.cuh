@@ -157,11 +157,22 @@ struct EpiHvp1 {
   template <int CW>
   __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[CW], int) const {
     if (m >= T) return;
+    __nv_bfloat16* __restrict__ out = S;
+    const float* __restrict__ h = Hf;
+    // all h loads of the chunk first (independent, read-only path), then the stores
+    float hv[CW];
+    int b = n0 / nc, j = n0 - b * nc;
 #pragma unroll
     for (int i = 0; i < CW; ++i) {
-      const int q = n0 + i;
-      if (q < N) S[(size_t)q * Tp + m] = __float2bfloat16(Hf[(size_t)(q / nc) * T + m] * v[i]);
+      hv[i] = n0 + i < N ? __ldg(h + (size_t)b * T + m) : 0.f;
+      if (++j == nc) {
+        j = 0;
+        ++b;
+      }
     }
+#pragma unroll
+    for (int i = 0; i < CW; ++i)
+      if (n0 + i < N) out[(size_t)(n0 + i) * Tp + m] = __float2bfloat16(hv[i] * v[i]);
   }
 };
 

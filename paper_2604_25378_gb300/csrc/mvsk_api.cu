@@ -68,7 +68,7 @@ struct OzBuf {
   long long* part = nullptr;    // split partials
   long long MpF = 0, ldT = 0;
   int MpB = 0, bp = 0;          // bp: vector count the right-hand maps are encoded for
-  CUtensorMap tmAF, tmAB, tmXF, tmXB;
+  CUtensorMap tmXF, tmXB;
 };
 
 }  // namespace

@@ -22,8 +22,11 @@
 // 2^(e_row + f_col - 49) once, in FP64.  The result is the exact product of
 // the 49-bit roundings of both operands, up to the dropped levels.
 //
-// GEMM layout.  Left operand: kOzS digit planes stacked row-wise (plane s at
-// rows [s*Mp, (s+1)*Mp)), each Mp x ldk BF16, K-major.  Right operand: the
+// GEMM layout.  Left operand: kOzS digit planes, each Mp x ldk BF16 stored as
+// contiguous 128 x 64 tiles (row tile, then k tile) whose bytes are already in
+// the 128-byte-swizzled order the MMA reads from shared memory, so that one
+// 16 KB bulk copy moves a tile (sequential DRAM reads instead of 128 strided
+// 128-byte rows).  Right operand: the
 // digit planes of Bp <= 64 vectors stacked as rows u*Bp + b (ldk BF16 each).
 // TMEM columns [l*Bp, (l+1)*Bp) hold level l; the MMA of left digit s takes
 // the right digits u = 0..kOzS-1-s as one N = (kOzS-s)*Bp operand and writes
@@ -44,6 +47,13 @@ constexpr int kOzExp = kOzS * kOzBits;  // 49: fixed-point bits of one operand
 
 __host__ __device__ constexpr size_t oz_smem_bytes(int Bp) {
   return 1024 + (size_t)kOzXStages * kOzS * Bp * 128 + (size_t)kOzAStages * kTcBM * kTcBK * 2 + 256;
+}
+
+// Element offset of (row r, column k) in a plane of 128 x 64 tiles with nkt
+// k-tiles per row tile: 16-byte chunk j of row r sits at chunk j ^ (r mod 8).
+__host__ __device__ __forceinline__ size_t oz_tiled(long long r, int k, int nkt) {
+  const int rr = (int)(r & 127), kk = k & 63;
+  return ((size_t)(r >> 7) * nkt + (k >> 6)) * 8192 + (size_t)rr * 64 + (size_t)((((kk >> 3) ^ (rr & 7)) << 3) | (kk & 7));
 }
 
 // Exponent e with |v| < 2^e for every |v| <= vmax (0 for vmax = 0).
@@ -95,21 +105,21 @@ static __global__ void k_oz_col_exp(const double* A, long long lda, long long M,
   }
 }
 
-// Digit planes of the rows: out[s][m][k] (plane = Mp*ldo), zero for m >= M or k >= K.
+// Digit planes of the rows (tiled, plane = Mp*ldo elements), zero for m >= M or k >= K.
 static __global__ void k_oz_split_rows(const double* A, long long lda, long long M, int K, const int* e,
                                        __nv_bfloat16* out, long long Mp, int ldo) {
   const size_t plane = (size_t)Mp * ldo;
-  const size_t tot = plane;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
+  const int nkt = ldo / 64;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
     const long long m = (long long)(i / ldo);
     const int k = (int)(i % ldo);
     const double v = (m < M && k < K) ? A[(size_t)m * lda + k] : 0.0;
-    oz_digits(v, e[m], out + i, plane);
+    oz_digits(v, e[m], out + oz_tiled(m, k, nkt), plane);
   }
 }
 
-// Digit planes of the columns (transposed): out[s][j][m] = digits of A[m][j]
-// with exponent e[j] (plane = Np*ldo), zero for j >= N or m >= M.
+// Digit planes of the columns (transposed, tiled): digits of A[m][j] at row j,
+// column m, with exponent e[j] (plane = Np*ldo), zero for j >= N or m >= M.
 static __global__ void k_oz_split_cols(const double* A, long long lda, long long M, int N, const int* e,
                                        __nv_bfloat16* out, int Np, long long ldo) {
   __shared__ double tile[32][33];
@@ -127,7 +137,7 @@ static __global__ void k_oz_split_cols(const double* A, long long lda, long long
   for (int q = 0; q < 4; ++q) {
     const int j = j0 + threadIdx.y + 8 * q;
     const long long m = m0 + threadIdx.x;
-    if (j < Np && m < ldo) oz_digits(tile[threadIdx.x][threadIdx.y + 8 * q], e[j], out + (size_t)j * ldo + m, plane);
+    if (j < Np && m < ldo) oz_digits(tile[threadIdx.x][threadIdx.y + 8 * q], e[j], out + oz_tiled(j, (int)m, (int)(ldo / 64)), plane);
   }
 }
 
@@ -166,9 +176,9 @@ static __global__ void k_oz_vec_digits(const double* V, long long vstride, int B
 // part[(z*Bp + b)*ldp + m] = folded levels of sum_{k in split z} A[m,k] V_b[k]
 // in units of 2^(e_m + f_b - 49).  Grid (Mp/128, splits); 128 threads.
 template <int BP>
-__global__ void __launch_bounds__(128, 1) k_oz_gemm(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(128, 1) k_oz_gemm(const __nv_bfloat16* __restrict__ Ad,
                                                     const __grid_constant__ CUtensorMap tmX, long long Mp, long long M,
-                                                    int K, long long* part, long long ldp, int* err,
+                                                    int K, int nkt, long long* part, long long ldp, int* err,
                                                     const int* need) {
   static_assert(BP % 16 == 0 && BP <= kOzMaxB, "vector count must be a multiple of 16, at most 64");
   constexpr int NL = kOzS * BP;                        // TMEM columns in use
@@ -240,7 +250,9 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const __grid_constant__ CUte
           break;
         }
         mbar_expect_tx(&afull[as], ABYTES);
-        tma_load_2d(sA + (size_t)as * ABYTES, &tmA, (kb0 + i) * kTcBK, (int)(s * Mp + m0), &afull[as]);
+        bulk_g2s(sA + (size_t)as * ABYTES,
+                 Ad + (size_t)s * Mp * nkt * 64 + ((size_t)blockIdx.x * nkt + (size_t)(kb0 + i)) * 8192, ABYTES,
+                 &afull[as]);
         s_aissued = ai + 1;
       }
     }

@@ -40,10 +40,7 @@ mvsk_status oz_prepare(mvsk_ctx* c, int Bp) {
         c->A64, c->ld, c->T, c->n, o.eB, o.AB, o.MpB, o.ldT);
     c->launches += 4;
     CU(cudaGetLastError());
-    TRY(make_tmap_bf16(&o.tmAF, o.AF, (unsigned long long)c->ld, (unsigned long long)kOzS * o.MpF,
-                       (unsigned long long)c->ld * 2, kTcBK, kTcBM));
-    TRY(make_tmap_bf16(&o.tmAB, o.AB, (unsigned long long)o.ldT, (unsigned long long)kOzS * o.MpB,
-                       (unsigned long long)o.ldT * 2, kTcBK, kTcBM));
+
   }
   if (o.bp != Bp) {
     TRY(make_tmap_bf16(&o.tmXF, o.XF, (unsigned long long)c->ld, (unsigned long long)kOzS * Bp,
@@ -75,23 +72,28 @@ mvsk_status oz_product(mvsk_ctx* c, int trans, const double* V, long long vstrid
                                V, vstride, B, Bp, (int)K, (int)ldk, f, trans ? o.XB : o.XF, need)));
   const int splits = (int)((ldk + kOzKc - 1) / kOzKc);
   const dim3 grid((unsigned)(Mp / kTcBM), (unsigned)splits);
-  const CUtensorMap& ta = trans ? o.tmAB : o.tmAF;
+  const __nv_bfloat16* ad = trans ? o.AB : o.AF;
+  const int nkt = (int)(ldk / kTcBK);
   const CUtensorMap& tx = trans ? o.tmXB : o.tmXF;
   // work: BF16 tensor FLOPs issued (kOzS (kOzS + 1) / 2 digit products)
   const double flops = 2.0 * (double)Mp * (double)((ldk + kTcBK - 1) / kTcBK * kTcBK) * Bp * (kOzS * (kOzS + 1) / 2);
   TRY(prof_begin(c, kKindOz + trans, flops));
   switch (Bp) {
     case 16:
-      k_oz_gemm<16><<<grid, 128, oz_smem_bytes(16), c->stream>>>(ta, tx, Mp, M, (int)K, o.part, Mp, c->err, need);
+      k_oz_gemm<16><<<grid, 128, oz_smem_bytes(16), c->stream>>>(ad, tx, Mp, M, (int)K, nkt, o.part, Mp, c->err,
+                                                                     need);
       break;
     case 32:
-      k_oz_gemm<32><<<grid, 128, oz_smem_bytes(32), c->stream>>>(ta, tx, Mp, M, (int)K, o.part, Mp, c->err, need);
+      k_oz_gemm<32><<<grid, 128, oz_smem_bytes(32), c->stream>>>(ad, tx, Mp, M, (int)K, nkt, o.part, Mp, c->err,
+                                                                     need);
       break;
     case 48:
-      k_oz_gemm<48><<<grid, 128, oz_smem_bytes(48), c->stream>>>(ta, tx, Mp, M, (int)K, o.part, Mp, c->err, need);
+      k_oz_gemm<48><<<grid, 128, oz_smem_bytes(48), c->stream>>>(ad, tx, Mp, M, (int)K, nkt, o.part, Mp, c->err,
+                                                                     need);
       break;
     default:
-      k_oz_gemm<64><<<grid, 128, oz_smem_bytes(64), c->stream>>>(ta, tx, Mp, M, (int)K, o.part, Mp, c->err, need);
+      k_oz_gemm<64><<<grid, 128, oz_smem_bytes(64), c->stream>>>(ad, tx, Mp, M, (int)K, nkt, o.part, Mp, c->err,
+                                                                     need);
       break;
   }
   CU(cudaGetLastError());
