@@ -574,10 +574,17 @@ static __global__ void __launch_bounds__(kPT, 2) k_pcg_step_f(Inst s0, int c0, i
   const int n = s.n, ld = s.ld;
   const float m = (float)SI[SI_M];
   const float lam = (float)s.sd[SD_LAM];
-  float* X = kcol<float>(s.X, c, ld);
-  float* R = kcol<float>(s.R, c, ld);
-  float* P = kcol<float>(s.P, c, ld);
-  const Face<float> f = face_of<float>(s);
+  // distinct arrays: restrict lets the loads of later coordinates move above
+  // the stores of earlier ones
+  float* __restrict__ X = kcol<float>(s.X, c, ld);
+  float* __restrict__ R = kcol<float>(s.R, c, ld);
+  float* __restrict__ P = kcol<float>(s.P, c, ld);
+  __nv_bfloat16* __restrict__ P16 = kp.P16;
+  const float* __restrict__ part = kp.part;
+  const Face<float> f0 = face_of<float>(s);
+  const float* __restrict__ fmf = f0.mf;
+  const float* __restrict__ fnh = f0.nh;
+  const float* __restrict__ fdg = f0.dg;
   const size_t prow = (size_t)blockIdx.y * kp.nc + blockIdx.x;
   float q[kPE], p[kPE];
   float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // mf.Q, nu.Q, p.mf.Q, p.mf, p.nu, p.p
@@ -588,15 +595,15 @@ static __global__ void __launch_bounds__(kPT, 2) k_pcg_step_f(Inst s0, int c0, i
     p[e] = 0.f;
     if (i < n) {
       float acc = 0.f;
-      for (int z = 0; z < kp.splits; ++z) acc += kp.part[((size_t)z * kp.N + prow) * kp.ldp + i];
+      for (int z = 0; z < kp.splits; ++z) acc += part[((size_t)z * kp.N + prow) * kp.ldp + i];
       q[e] = kp.scale * acc;
       p[e] = P[i];
-      const float mq = f.mf[i] * q[e];
+      const float mq = fmf[i] * q[e];
       a[0] += mq;
-      a[1] += f.nh[i] * q[e];
+      a[1] += fnh[i] * q[e];
       a[2] += p[e] * mq;
-      a[3] += p[e] * f.mf[i];
-      a[4] += p[e] * f.nh[i];
+      a[3] += p[e] * fmf[i];
+      a[4] += p[e] * fnh[i];
       a[5] += p[e] * p[e];
     }
   }
@@ -619,18 +626,18 @@ static __global__ void __launch_bounds__(kPT, 2) k_pcg_step_f(Inst s0, int c0, i
   for (int e = 0; e < kPE; ++e) {
     const int i = threadIdx.x + e * kPT;
     if (i < n) {
-      const float qq = f.mf[i] * (q[e] - qmean) - ry * f.nh[i] + lam * p[e];
+      const float qq = fmf[i] * (q[e] - qmean) - ry * fnh[i] + lam * p[e];
       X[i] += al * p[e];
       const float rv = R[i] - al * qq;
       R[i] = rv;
-      const float t = rv / f.dg[i];
+      const float t = rv / fdg[i];
       q[e] = t;  // q now holds t = R / |diag G|
       b[0] += rv * rv;
-      b[1] += f.mf[i] * t;
-      b[2] += f.nh[i] * t;
-      b[3] += rv * f.mf[i] * t;
-      b[4] += rv * f.mf[i];
-      b[5] += rv * f.nh[i];
+      b[1] += fmf[i] * t;
+      b[2] += fnh[i] * t;
+      b[3] += rv * fmf[i] * t;
+      b[4] += rv * fmf[i];
+      b[5] += rv * fnh[i];
     }
   }
   block_sumNf<6>(b, scr);
@@ -649,10 +656,10 @@ static __global__ void __launch_bounds__(kPT, 2) k_pcg_step_f(Inst s0, int c0, i
   for (int e = 0; e < kPE; ++e) {
     const int i = threadIdx.x + e * kPT;
     if (i < n) {
-      const float zz = f.mf[i] * (q[e] - tmean) - tb2 * f.nh[i];
+      const float zz = fmf[i] * (q[e] - tmean) - tb2 * fnh[i];
       const float pn = zz + beta * p[e];
       P[i] = pn;
-      kp.P16[prow * ld + i] = __float2bfloat16(pn);
+      P16[prow * ld + i] = __float2bfloat16(pn);
     }
   }
   if (threadIdx.x == 0) {
