@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-its", type=int, default=1)
+    ap.add_argument("--workload", default="c4", choices=["c4", "paper-synthetic"],
+                    help="c4: the batched C4 sweep (default); paper-synthetic: the paper's T=252 benchmark grid")
     return ap.parse_args()
 
 
@@ -131,6 +133,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measured_traffic(kind):
+    """DRAM bytes per launch of `kind` from profiles/traffic.json (an ncu
+    capture), or None when absent or when its kernel sources changed since."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kind]
+        for path, digest in rec["sources"].items():
+            if hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest() != digest:
+                return None
+        return rec["bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
@@ -205,6 +221,8 @@ def run_ours(args, rank, world):
                 "peak_source": pk_src, "launches": d["launches"],
                 "avg_us": round(avg_s * 1e6, 2),
                 "share_of_step": round(d["total_ms"] / ms, 4)}
+        tr = measured_traffic(name)
+        roof["traffic"] = None if tr is None else round(tr)
         if name.startswith("gemm_tc") or name.startswith("oz_gemm"):
             # tensor-core product: bytes_per_launch carries its average FLOPs
             roof["bound"] = "tensor"
@@ -304,11 +322,67 @@ def run_reference(args, rank, world):
                     "assumed for scaling)"}
 
 
+# The paper's published YAND-MVSK means on its synthetic benchmark (Table
+# synthetic-summary; hardware not stated): seconds, iterations, projected residual.
+PAPER_SYNTHETIC_YAND = {"small": {"mean_time_s": 0.0711, "mean_iters": 41.74, "mean_residual": 2.69e-7, "runs": 54},
+                        "large": {"mean_time_s": 0.332, "mean_iters": 98.56, "mean_residual": 3.56e-6, "runs": 48}}
+
+
+def run_paper_synthetic(args, rank, world):
+    """The paper's synthetic benchmark grid, one single-instance FP64 solve per
+    (dimension, profile) from 1/n: direct for n <= 100, PCG beyond.  Times are
+    wall-clock per mvsk_solve call (context and profile set up outside)."""
+    if rank != 0:
+        return None
+    import numpy as np
+    import torch
+
+    import panels
+    import paper_2604_25378_gb300 as m
+    g = panels.PAPER_SYNTHETIC
+    runs = []
+    for regime, ns, cfg in (("small", g["small_n"], m.DIRECT), ("large", g["large_n"], m.PCG)):
+        for n in ns:
+            R = panels.uniform_panel(n, g["T"], n)
+            ctx = m.MVSK(torch.from_numpy(R).cuda(), "fp64")
+            ctx.set_option("pref_scaling", 0)
+            for prof in g["profiles"]:
+                ctx.set_prefs(np.asarray(prof, dtype=np.float64))
+                for _ in range(max(args.warmup, 0)):
+                    ctx.solve(cfg, args.tol)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, info = ctx.solve(cfg, args.tol)
+                dt = time.perf_counter() - t0
+                runs.append({"regime": regime, "n": n, "profile": list(prof), "seconds": dt, "iters": info["iters"],
+                             "kkt": info["kkt_residual"], "status": info["status"]})
+            ctx.close()
+
+    def summary(rs):
+        return {"runs": len(rs), "mean_time_s": statistics.mean(r["seconds"] for r in rs),
+                "mean_iters": statistics.mean(r["iters"] for r in rs),
+                "mean_residual": statistics.mean(r["kkt"] for r in rs),
+                "converged": sum(r["status"] == "ok" for r in rs)}
+
+    small = summary([r for r in runs if r["regime"] == "small"])
+    large = summary([r for r in runs if r["regime"] == "large"])
+    return {"metric": "mean seconds per solve, paper synthetic benchmark (T=252, n=4..5000)",
+            "value": statistics.mean(r["seconds"] for r in runs), "unit": "s", "n_gpus": 1,
+            "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "paper_synthetic_T252", "T": g["T"], "small_n": g["small_n"],
+                       "large_n": g["large_n"], "profiles": g["profiles"], "tol": args.tol,
+                       "configuration": "direct for n <= 100, pcg beyond", "warmup_solves_per_run": args.warmup},
+            "small": small, "large": large, "paper_reported": PAPER_SYNTHETIC_YAND,
+            "per_dimension": [{k: r[k] for k in ("regime", "n", "seconds", "iters", "kkt", "status")} for r in runs]}
+
+
 def main():
     args = parse()
     rank, world = dist_init(args.gpus)
     if args.impl == "reference":
         line = run_reference(args, rank, world)
+    elif args.workload == "paper-synthetic":
+        line = run_paper_synthetic(args, rank, world)
     else:
         line = run_ours(args, rank, world)
     if rank == 0 and line is not None:

@@ -24,6 +24,7 @@ __all__ = [
     "uniform_panel",
     "workload",
     "WORKLOADS",
+    "PAPER_SYNTHETIC",
 ]
 
 
@@ -130,6 +131,20 @@ WORKLOADS = {
                                   lambdas=[(1.0, 1.0, l3, l4) for l3 in (0.5, 2.0) for l4 in (0.5, 2.0)],
                                   qs=list(np.linspace(0.40, 0.85, 16)), config="pcg"),
 }
+
+
+# The paper's synthetic coefficient-stress benchmark (Sec. 5.3, Table
+# synthetic-summary): T = 252, R i.i.d. U[-0.1, 0.4], the three raw profiles,
+# the direct configuration for n <= 100 and PCG with stall recovery beyond.
+# The paper names only some dimensions (4..100 in 54 runs, 120..5000 in 48
+# runs); the two grids below have 18 and 16 dimensions (3 profiles each) and
+# contain every dimension it names.  One return matrix per dimension, seed n.
+PAPER_SYNTHETIC = dict(
+    T=252,
+    profiles=[(10.0, 1.0, 10.0, 1.0), (1.0, 10.0, 1.0, 10.0), (10.0, 10.0, 10.0, 10.0)],
+    small_n=[4, 8, 12, 16, 20, 25, 30, 35, 40, 45, 50, 60, 70, 75, 80, 90, 95, 100],
+    large_n=[120, 150, 200, 250, 300, 400, 500, 600, 800, 1000, 1200, 1500, 2000, 2500, 3000, 5000],
+)
 
 
 def workload(name: str, n: int | None = None, T: int | None = None):

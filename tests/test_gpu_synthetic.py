@@ -1,0 +1,36 @@
+"""The paper's synthetic benchmark (Sec. 5.3, T = 252, R ~ U[-0.1, 0.4], the
+three raw coefficient-stress profiles) against the CPU oracle: the direct
+configuration for n <= 100 and PCG beyond, as in the paper's regime split.
+Under the certificate ([1,10,1,10], [10,10,10,10]) the minimiser is unique and
+both sides must agree on it; the return-seeking profile [10,1,10,1] lies outside
+the certificate, so the GPU point must be a KKT point whose objective is no
+worse than the oracle's (the paper's objective-tie criterion is 1e-6)."""
+import numpy as np
+import pytest
+
+import panels
+from oracle import mvsk_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n,cfg", [(4, "direct"), (20, "direct"), (100, "direct"), (120, "pcg"), (400, "pcg")])
+def test_paper_synthetic_grid_matches_oracle(n, cfg):
+    import paper_2604_25378_gb300 as m
+    g = panels.PAPER_SYNTHETIC
+    R = panels.uniform_panel(n, g["T"], n)
+    mu, A = O.centre(R)
+    ctx = m.MVSK(R, "fp64")
+    ctx.set_option("pref_scaling", 0)
+    for prof in g["profiles"]:
+        c = np.asarray(prof, dtype=np.float64)
+        ctx.set_prefs(c)
+        w, info = ctx.solve(m.DIRECT if cfg == "direct" else m.PCG, 1e-10)
+        x_ref, inf_ref = O.solve(A, mu, c, cfg, 1e-10)
+        assert info["status"] == "ok", (n, prof, info)
+        g_w = O.gradient(A, mu, c, w)
+        assert O.kkt_residual(w, g_w, 1e-8) <= 1e-10 * inf_ref.kkt0 * 1.0001
+        f_w = O.objective(A, mu, c, w)
+        if O.convexity_certificate(c):
+            assert np.max(np.abs(w - x_ref)) <= 1e-8, (n, prof, np.max(np.abs(w - x_ref)))
+        assert f_w <= inf_ref.f + 1e-6 * max(1.0, abs(inf_ref.f)), (n, prof, f_w, inf_ref.f)
