@@ -43,8 +43,10 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-its", type=int, default=1)
-    ap.add_argument("--workload", default="c4", choices=["c4", "paper-synthetic"],
-                    help="c4: the batched C4 sweep (default); paper-synthetic: the paper's T=252 benchmark grid")
+    ap.add_argument("--workload", default="c4",
+                    choices=["c4", "paper-synthetic", "paper-line-search", "paper-conditioning"],
+                    help="c4: the batched C4 sweep (default); paper-*: the paper's own benchmarks "
+                         "(T=252 synthetic grid, exact vs Armijo step rule, CRRA conditioning sweep)")
     return ap.parse_args()
 
 
@@ -376,6 +378,99 @@ def run_paper_synthetic(args, rank, world):
             "per_dimension": [{k: r[k] for k in ("regime", "n", "seconds", "iters", "kkt", "status")} for r in runs]}
 
 
+# Table yand-line-search (direct configuration, n in {4, 8, 12}, T = 252).
+PAPER_LINE_SEARCH = {"armijo": {"mean_time_s": 1.40e-2, "median_time_s": 9.93e-3, "mean_iters": 29.8,
+                                "mean_residual": 3.61e-7},
+                     "exact": {"mean_time_s": 1.17e-2, "median_time_s": 4.18e-3, "mean_iters": 19.0,
+                               "mean_residual": 8.21e-8}}
+# Tables crra-conditioning (n = 1000, T = 2000) and crra-conditioning-stress
+# (n = 5000, T = 252): median seconds and median projected residual of YAND (large).
+PAPER_CONDITIONING = {"n1000_T2000": {"1": (0.122, 1.28e-6), "10": (0.399, 1.27e-6), "100": (0.482, 1.36e-6),
+                                      "1000": (0.423, 1.40e-6)},
+                      "n5000_T252": {"1": (0.569, 5.02e-6), "10": (1.270, 5.37e-6), "100": (1.291, 5.99e-6),
+                                     "1000": (1.394, 6.61e-6)}}
+
+
+def _timed_solve(ctx, cfg, tol, warmup):
+    import torch
+    for _ in range(warmup):
+        ctx.solve(cfg, tol)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, info = ctx.solve(cfg, tol)
+    return time.perf_counter() - t0, info
+
+
+def run_paper_line_search(args, rank, world):
+    """Table yand-line-search: direct configuration, exact quartic vs Armijo
+    backtracking, n in {4, 8, 12}, T = 252, the three raw profiles."""
+    if rank != 0:
+        return None
+    import numpy as np
+    import torch
+
+    import panels
+    import paper_2604_25378_gb300 as m
+    out = {}
+    for rule, code in (("exact", 0), ("armijo", 1)):
+        rows = []
+        for n in (4, 8, 12):
+            R = panels.uniform_panel(n, 252, n)
+            ctx = m.MVSK(torch.from_numpy(R).cuda(), "fp64")
+            ctx.set_option("pref_scaling", 0)
+            ctx.set_option("line_search", code)
+            if code == 1:
+                ctx.set_option("max_iter", 120)  # Table yand-core-parameters, Armijo diagnostic row
+            for prof in panels.PAPER_SYNTHETIC["profiles"]:
+                ctx.set_prefs(np.asarray(prof))
+                dt, info = _timed_solve(ctx, m.DIRECT, args.tol, max(args.warmup, 0))
+                rows.append((dt, info["iters"], info["kkt_residual"], info["status"] == "ok"))
+            ctx.close()
+        out[rule] = {"runs": len(rows), "mean_time_s": statistics.mean(r[0] for r in rows),
+                     "median_time_s": statistics.median(r[0] for r in rows),
+                     "mean_iters": statistics.mean(r[1] for r in rows),
+                     "mean_residual": statistics.mean(r[2] for r in rows), "converged": sum(r[3] for r in rows)}
+    return {"metric": "mean seconds per solve, direct configuration, exact vs Armijo step (T=252, n=4,8,12)",
+            "value": out["exact"]["mean_time_s"], "unit": "s", "n_gpus": 1, "higher_is_better": False,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": "paper_line_search_T252", "tol": args.tol},
+            "exact": out["exact"], "armijo": out["armijo"], "paper_reported": PAPER_LINE_SEARCH}
+
+
+def run_paper_conditioning(args, rank, world):
+    """Tables crra-conditioning / crra-conditioning-stress: gamma = 6 CRRA
+    coefficients, prescribed kappa_+(A U), PCG configuration with stall
+    recovery, three instances per level, one untimed warm-up solve each; medians."""
+    if rank != 0:
+        return None
+    import numpy as np
+    import torch
+
+    import panels
+    import paper_2604_25378_gb300 as m
+    out = {}
+    for key, n, T in (("n1000_T2000", 1000, 2000), ("n5000_T252", 5000, 252)):
+        out[key] = {}
+        for kappa in (1.0, 10.0, 100.0, 1000.0):
+            rows = []
+            for seed in range(3):
+                R = panels.crra_conditioning_panel(n, T, kappa, 100 + seed)
+                ctx = m.MVSK(torch.from_numpy(R).cuda(), "fp64")
+                ctx.set_option("pref_scaling", 0)
+                ctx.set_prefs(np.asarray(panels.CRRA_GAMMA6))
+                dt, info = _timed_solve(ctx, m.PCG, args.tol, max(args.warmup, 1))
+                rows.append((dt, info["kkt_residual"], info["iters"], info["status"] == "ok"))
+                ctx.close()
+            out[key][str(int(kappa))] = {"median_time_s": statistics.median(r[0] for r in rows),
+                                         "median_residual": statistics.median(r[1] for r in rows),
+                                         "median_iters": statistics.median(r[2] for r in rows),
+                                         "converged": sum(r[3] for r in rows)}
+    return {"metric": "median seconds per solve, CRRA conditioning benchmark (gamma=6, PCG)",
+            "value": statistics.median(v["median_time_s"] for v in out["n1000_T2000"].values()), "unit": "s",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "paper_crra_conditioning", "tol": args.tol, "instances_per_level": 3},
+            "levels": out, "paper_reported_median_time_s_and_residual": PAPER_CONDITIONING}
+
+
 def main():
     args = parse()
     rank, world = dist_init(args.gpus)
@@ -383,6 +478,10 @@ def main():
         line = run_reference(args, rank, world)
     elif args.workload == "paper-synthetic":
         line = run_paper_synthetic(args, rank, world)
+    elif args.workload == "paper-line-search":
+        line = run_paper_line_search(args, rank, world)
+    elif args.workload == "paper-conditioning":
+        line = run_paper_conditioning(args, rank, world)
     else:
         line = run_ours(args, rank, world)
     if rank == 0 and line is not None:

@@ -117,7 +117,11 @@ mvsk_status mvsk_set_prefs(mvsk_ctx* ctx, const double lambda[4], double target)
  *   the mvsk_oracle_* exports), "cal_rel_tol" (1e-9), "graphs" (1: replay
  *   captured CUDA graphs), "split_products" (1: in mvsk_solve_batch the FP64
  *   products A x, A^T psi'(z) and A d run as split BF16 tensor-core products
- *   with FP64 accuracy, see mvsk_product; 0: FP64 streaming passes).
+ *   with FP64 accuracy, see mvsk_product; 0: FP64 streaming passes),
+ *   "line_search" (0: exact quartic step, Prop. quartic exact line search;
+ *   1: Armijo backtracking on the same quartic, the paper's Armijo diagnostic
+ *   of Table yand-line-search: the largest alpha_max 2^-j, j < 60, with
+ *   phi(alpha) - phi(0) <= 1e-4 alpha phi'(0)).
  *   Errors: EINVAL for an unknown key or an out-of-range value.
  */
 mvsk_status mvsk_set_option(mvsk_ctx* ctx, const char* key, double value);

@@ -277,6 +277,33 @@ def quartic_argmin(coef, amax):
     return best_a
 
 
+ARMIJO_SIGMA = 1e-4
+ARMIJO_HALVINGS = 60
+
+
+def armijo_step(coef, amax):
+    """Armijo backtracking on the exact quartic along d (the paper's Armijo
+    diagnostic, Table yand-line-search; constants are a
+    reading; App. C.1 names Armijo backtracking as the rule of the
+    convergence theory): the largest alpha = amax 2^-j, j < 60, with
+    phi(alpha) - phi(0) <= sigma alpha phi'(0), sigma = 1e-4, phi'(0) = A1;
+    0 when amax <= 0, phi'(0) >= 0 or no halving is accepted."""
+    if not (amax > 0.0) or not (coef[1] < 0.0):
+        return 0.0
+    a = amax
+    for _ in range(ARMIJO_HALVINGS):
+        if _decrease(coef, a) <= ARMIJO_SIGMA * a * coef[1]:
+            return a
+        a *= 0.5
+    return 0.0
+
+
+def line_step(coef, amax, rule):
+    """Step along a direction on [0, amax]: the exact quartic minimiser
+    (rule "exact", Prop. quartic exact line search) or Armijo backtracking."""
+    return quartic_argmin(coef, amax) if rule == "exact" else armijo_step(coef, amax)
+
+
 # ---------------------------------------------------------------------------
 # Simplex slice projection and the projected-simplex KKT residual
 # ---------------------------------------------------------------------------
@@ -398,6 +425,7 @@ class Options:
     descent_eps: float = 1e-10
     arc_halvings: int = 40
     max_elapsed: float = math.inf
+    line_search: str = "exact"        # "exact" quartic, or "armijo" backtracking on the quartic
 
 
 def _face_tangent(A, c, z, F):
@@ -592,10 +620,10 @@ class SolveInfo:
     seconds: float = 0.0
 
 
-def _ls_step(A, mu, c, x, z, d, amax):
+def _ls_step(A, mu, c, x, z, d, amax, rule="exact"):
     w = A @ d
     coef = quartic_coefficients(c, mu, x, d, power_sums(z, w))
-    return quartic_argmin(coef, amax)
+    return line_step(coef, amax, rule)
 
 
 def working_set(x, g, opts: Options, counts=None):
@@ -634,13 +662,17 @@ def boundary_step(A, mu, c, x, z, g, d, opts: Options, counts):
     raw step when alpha_max > 0; else the face hand-off: the projected-gradient
     segment Pi(x - s g) - x with s = eta ||d|| / ||P g||, exact quartic on
     [0, 1].  Coordinates within eps_act of tau are set to tau exactly.
+    With opts.line_search = "armijo" the four steps along d or the segment
+    use Armijo backtracking on the same quartic instead (eta_k keeps its exact
+    definition: it sets the projected trial, not the step rule).
     """
     tau = opts.tau
+    rule = opts.line_search
     amax = alpha_max(x, d, tau)
     coef = quartic_coefficients(c, mu, x, d, power_sums(z, A @ d))
     eta_k = min(opts.eta, quartic_argmin(coef, opts.eta))
     if amax >= eta_k:
-        al = quartic_argmin(coef, amax)
+        al = line_step(coef, amax, rule)
         x_new = x + al * d
         counts["raw"] += 1
     else:
@@ -655,11 +687,11 @@ def boundary_step(A, mu, c, x, z, g, d, opts: Options, counts):
                 break
             eta_k *= 0.5
         if descent:
-            al = _ls_step(A, mu, c, x, z, dbar, 1.0)
+            al = _ls_step(A, mu, c, x, z, dbar, 1.0, rule)
             x_new = xbar.copy() if al == 1.0 else x + al * dbar
             counts["segment"] += 1
         elif amax > 0.0:
-            al = quartic_argmin(coef, amax)
+            al = line_step(coef, amax, rule)
             x_new = x + al * d
             counts["capped"] += 1
         else:
@@ -672,7 +704,7 @@ def boundary_step(A, mu, c, x, z, g, d, opts: Options, counts):
             if not float(g @ dbar) < 0.0:
                 return x.copy()
             w = A @ dbar
-            al = quartic_argmin(quartic_coefficients(c, mu, x, dbar, power_sums(z, w)), 1.0)
+            al = line_step(quartic_coefficients(c, mu, x, dbar, power_sums(z, w)), 1.0, rule)
             x_new = xbar.copy() if al == 1.0 else x + al * dbar
     x_new = x_new.copy()
     x_new[x_new - tau <= opts.eps_act] = tau

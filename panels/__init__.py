@@ -13,6 +13,8 @@ synthetic benchmark (Sec. 5, R ~ U[-0.1, 0.4], T = 252) is `uniform_panel`.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 __all__ = [
@@ -25,6 +27,8 @@ __all__ = [
     "workload",
     "WORKLOADS",
     "PAPER_SYNTHETIC",
+    "CRRA_GAMMA6",
+    "crra_conditioning_panel",
 ]
 
 
@@ -132,6 +136,33 @@ WORKLOADS = {
                                   qs=list(np.linspace(0.40, 0.85, 16)), config="pcg"),
 }
 
+
+def crra_conditioning_panel(n: int, T: int, kappa: float, seed: int, vol: float = 2e-2, mean_hi: float = 1e-3):
+    """Controlled-conditioning panel of the CRRA benchmark (Sec. 5.2, Tables
+    crra-conditioning and crra-conditioning-stress): A = Q diag(s) W^T with
+    W = U V, U an orthonormal basis of the simplex tangent space (columns
+    orthogonal to 1_n), V an (n-1) x r matrix with orthonormal columns, Q a
+    T x r matrix with orthonormal columns orthogonal to 1_T, r = min(n-1, T-1),
+    and s log-spaced from vol sqrt(T) down to vol sqrt(T) / kappa.  Then
+    A 1/n = 0, 1^T A = 0 (A is centred) and the positive singular values of A U
+    are s, so kappa_+(A U) = kappa.  R = A + 1 mu^T with mu_i ~ U[0, mean_hi].
+    vol and mean_hi are readings (the paper fixes only kappa, n, T)."""
+    rng = _rng(seed)
+    r = min(n - 1, T - 1)
+    # U: orthonormal complement of 1_n (QR of [1, Gaussian])
+    M = rng.standard_normal((n, n - 1))
+    U = np.linalg.qr(np.column_stack([np.ones(n), M]))[0][:, 1:]
+    V = np.linalg.qr(rng.standard_normal((n - 1, r)))[0]
+    Qm = np.linalg.qr(np.column_stack([np.ones(T), rng.standard_normal((T, r))]))[0][:, 1:]
+    s = vol * math.sqrt(T) * np.logspace(0.0, -math.log10(kappa), r) if r > 1 else np.array([vol * math.sqrt(T)])
+    W = U @ V
+    A = (Qm * s) @ W.T
+    mu = rng.uniform(0.0, mean_hi, n)
+    return A + mu[None, :]
+
+
+# CRRA calibration gamma = 6 of the conditioning benchmark (Sec. 5.2).
+CRRA_GAMMA6 = (1.0, 3.0, 7.0, 14.0)
 
 # The paper's synthetic coefficient-stress benchmark (Sec. 5.3, Table
 # synthetic-summary): T = 252, R i.i.d. U[-0.1, 0.4], the three raw profiles,

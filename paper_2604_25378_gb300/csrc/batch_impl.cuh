@@ -690,7 +690,7 @@ mvsk_status batch_start_run(mvsk_ctx* c, BatchBuf& bb, int b, InstRun& r, double
   double* dopts = s.tmp + (size_t)22 * c->ld;  // 12 doubles of the instance's scratch
   CU(cudaMemcpyAsync(dopts, h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
   k_init_state<<<1, 32, 0, c->stream>>>(s, tol, o.eta, o.pcg_max_iter, 1, o.stall_window, o.probes, o.probe_seed,
-                                        o.krylov_maxit, o.arc_halvings, dopts);
+                                        o.krylov_maxit, o.arc_halvings, o.line_search, dopts);
   // the KKT residual at the 1/n start (kkt_rel normaliser) of every instance
   // started in this round is evaluated by one k_kkt0_batch (kkt0_flush)
   bb.kq_idx.push_back(b);

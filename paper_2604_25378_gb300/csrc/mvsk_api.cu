@@ -33,6 +33,7 @@ struct Options {
   int max_iter = 300, pcg_max_iter = 40, restart_iter = 120, krylov_maxit = 15, probes = 8;
   int stall_window = 10, pref_scaling = 1, oracle_prec = 0, arc_halvings = 40, cal_max_evals = 40, trace = 0;
   int split_products = 1;  // batched solves: FP64 products on the tensor cores (ozaki.cuh)
+  int line_search = 0;     // 0 exact quartic step, 1 Armijo backtracking on the quartic
   unsigned long long probe_seed = 0x5EEDull;
 };
 
@@ -305,7 +306,7 @@ __global__ void k_ls_coef_only(Inst s, const double* spart, int G, const double*
 }
 
 __global__ void k_init_state(Inst s0, double tol, double eta, int maxit, int pcg, int stallwin, int probes,
-                             unsigned long long seed, int kmaxit, int arcmax, const double* opts9) {
+                             unsigned long long seed, int kmaxit, int arcmax, int lsrule, const double* opts9) {
   Inst s = inst_at(s0, blockIdx.y);
   if (threadIdx.x != 0) return;
   for (int q = 0; q < kSI; ++q) s.si[q] = 0;
@@ -333,6 +334,7 @@ __global__ void k_init_state(Inst s0, double tol, double eta, int maxit, int pcg
   s.si[SI_SEEDHI] = (int)(unsigned)(seed >> 32);
   s.si[SI_KMAXIT] = kmaxit;
   s.si[SI_ARCMAX] = arcmax;
+  s.si[SI_LSRULE] = lsrule;
 }
 
 __global__ void k_new_phase(Inst s0, double eta, int maxit) {
@@ -924,7 +926,8 @@ mvsk_status init_state(mvsk_ctx* c, int cfg, double tol, const double cc[4]) {
   double* dopts = c->vec_scratch;  // 12 doubles
   CU(cudaMemcpyAsync(dopts, h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
   k_init_state<<<1, 32, 0, c->stream>>>(c->in, tol, o.eta, pcg ? o.pcg_max_iter : o.max_iter, pcg ? 1 : 0,
-                                        o.stall_window, o.probes, o.probe_seed, o.krylov_maxit, o.arc_halvings, dopts);
+                                        o.stall_window, o.probes, o.probe_seed, o.krylov_maxit, o.arc_halvings,
+                                        o.line_search, dopts);
   CU(cudaGetLastError());
   return MVSK_OK;
 }
@@ -1383,6 +1386,7 @@ mvsk_status mvsk_set_option(mvsk_ctx* c, const char* key, double v) {
   else if (k == "trace" && cnt(v, 0, 1)) o.trace = (int)v;
   else if (k == "graphs" && cnt(v, 0, 1)) c->use_graphs = v != 0.0;
   else if (k == "split_products" && cnt(v, 0, 1)) o.split_products = (int)v;
+  else if (k == "line_search" && cnt(v, 0, 1)) o.line_search = (int)v;
   else return fail(MVSK_EINVAL, "unknown option or bad value: %s = %g", key, v);
   if (c->prefs_set && k == "pref_scaling") mvsk_set_prefs(c, c->lam, c->target);
   return MVSK_OK;

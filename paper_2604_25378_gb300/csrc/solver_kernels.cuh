@@ -763,7 +763,7 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
     SI[SI_SKIPLS] = 1;
   }
   if (am >= eta_k) {
-    const double al = quartic_argmin(coef, am);
+    const double al = line_step(coef, am, SI[SI_LSRULE]);
     take_step(s, s.d, al, nullptr);
     if (threadIdx.x == 0) {
       SD[SD_ALPHA] = al;
@@ -810,7 +810,7 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
     return;
   }
   if (am > 0.0) {
-    const double al = quartic_argmin(coef, am);
+    const double al = line_step(coef, am, SI[SI_LSRULE]);
     take_step(s, s.d, al, nullptr);
     if (threadIdx.x == 0) {
       SD[SD_ALPHA] = al;
@@ -851,7 +851,7 @@ static __global__ void __launch_bounds__(kVT) k_decide2(Inst s0, const double* s
   __shared__ double coef[5];
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPLS] != 0) return;
   ls_coefficients(s, s.spart, G, s.dstep, coef, scr, ps);
-  const double al = quartic_argmin(coef, 1.0);
+  const double al = line_step(coef, 1.0, s.si[SI_LSRULE]);
   take_step(s, s.dstep, al, al == 1.0 ? s.xbar : nullptr);
   if (threadIdx.x == 0) s.sd[SD_ALPHA] = al;
 }

@@ -26,6 +26,7 @@ enum SI : int {
   SI_ITER, SI_PHASEIT, SI_MAXIT, SI_M, SI_BRANCH, SI_SKIPDIR, SI_SKIPLS, SI_PCG, SI_STALLWIN,
   SI_NREL, SI_KRY, SI_NCOL, SI_PROBES, SI_SEEDLO, SI_SEEDHI, SI_HISTN, SI_KMAXIT, SI_DIRONLY,
   SI_PASSES, SI_HVPS, SI_THIRD, SI_BR_RAW, SI_BR_SEG, SI_BR_CAP, SI_BR_FACE, SI_ARCMAX,
+  SI_LSRULE,        // step rule along d: 0 exact quartic, 1 Armijo backtracking on the quartic
   SI_LIVE = 30,     // live-column count per PCG group (10 groups of two columns)
   SI_ACT = 40,      // per-column active flags (20 columns)
   SI_CITS = 60,     // per-column PCG iteration counts (20 columns)
@@ -250,6 +251,24 @@ inline __device__ double quartic_argmin(const double* c, double amax) {
     if (v < best_v) { best_a = a; best_v = v; }
   }
   return best_a;
+}
+
+// Armijo backtracking on the same quartic (the paper's Armijo diagnostic,
+// Table yand-line-search): the largest alpha = amax 2^-j, j < 60, with
+// phi(alpha) - phi(0) <= 1e-4 alpha phi'(0); 0 when phi'(0) >= 0.
+inline __device__ double armijo_step(const double* c, double amax) {
+  if (!(amax > 0.0) || !(c[1] < 0.0)) return 0.0;
+  double a = amax;
+  for (int j = 0; j < 60; ++j) {
+    if (decrease(c, a) <= 1e-4 * a * c[1]) return a;
+    a *= 0.5;
+  }
+  return 0.0;
+}
+
+// Step along a direction on [0, amax] by rule (SI_LSRULE).
+inline __device__ double line_step(const double* c, double amax, int rule) {
+  return rule == 1 ? armijo_step(c, amax) : quartic_argmin(c, amax);
 }
 
 // ------------------------------------------------- SplitMix64 normal probes

@@ -34,3 +34,42 @@ def test_paper_synthetic_grid_matches_oracle(n, cfg):
         if O.convexity_certificate(c):
             assert np.max(np.abs(w - x_ref)) <= 1e-8, (n, prof, np.max(np.abs(w - x_ref)))
         assert f_w <= inf_ref.f + 1e-6 * max(1.0, abs(inf_ref.f)), (n, prof, f_w, inf_ref.f)
+
+
+@pytest.mark.parametrize("n", [4, 8, 12])
+def test_armijo_rule_matches_oracle(n):
+    """The Armijo diagnostic (Table yand-line-search): direct configuration with
+    Armijo backtracking on the quartic, on the synthetic T = 252 panels.  Under
+    the certificate both sides reach the oracle's minimiser."""
+    import paper_2604_25378_gb300 as m
+    R = panels.uniform_panel(n, 252, n)
+    mu, A = O.centre(R)
+    ctx = m.MVSK(R, "fp64")
+    ctx.set_option("pref_scaling", 0)
+    ctx.set_option("line_search", 1)
+    ctx.set_option("max_iter", 120)
+    for prof in [(1.0, 10.0, 1.0, 10.0), (10.0, 10.0, 10.0, 10.0)]:
+        c = np.asarray(prof)
+        ctx.set_prefs(c)
+        w, info = ctx.solve(m.DIRECT, 1e-10)
+        x_ref, inf_ref = O.solve(A, mu, c, "direct", 1e-10, opts=O.Options(line_search="armijo", max_iter=120))
+        assert info["status"] == "ok" and inf_ref.status == "converged"
+        assert np.max(np.abs(w - x_ref)) <= 1e-8, (n, prof, np.max(np.abs(w - x_ref)))
+
+
+@pytest.mark.parametrize("kappa", [10.0, 1000.0])
+def test_crra_conditioning_matches_oracle(kappa):
+    """CRRA conditioning benchmark (Sec. 5.2) at reduced size: gamma = 6,
+    kappa_+(A U) prescribed, PCG configuration; certified convex, so the GPU
+    and the oracle reach the same minimiser."""
+    import paper_2604_25378_gb300 as m
+    R = panels.crra_conditioning_panel(200, 400, kappa, 2)
+    mu, A = O.centre(R)
+    c = np.asarray(panels.CRRA_GAMMA6)
+    ctx = m.MVSK(R, "fp64")
+    ctx.set_option("pref_scaling", 0)
+    ctx.set_prefs(c)
+    w, info = ctx.solve(m.PCG, 1e-10)
+    x_ref, inf_ref = O.solve(A, mu, c, "pcg", 1e-10)
+    assert info["status"] == "ok" and inf_ref.status == "converged"
+    assert np.max(np.abs(w - x_ref)) <= 1e-8, np.max(np.abs(w - x_ref))

@@ -382,3 +382,52 @@ def test_reduced_hessian_spectra_match_paper_table_statistically():
         assert 0.6 * row["lmin"] <= np.median(lmins) <= 1.6 * row["lmin"]
         assert 0.75 * row["lmax"] <= np.median(lmaxs) <= 1.35 * row["lmax"]
         assert 0.5 * row["kappa"] <= np.median(kap) <= 2.0 * row["kappa"]
+
+
+# --------------------------------------------------------------- Armijo rule
+def test_armijo_step_is_the_largest_accepted_halving():
+    """Armijo backtracking on the quartic (Table yand-line-search diagnostic):
+    brute force over alpha = amax 2^-j with the polynomial evaluated by
+    numpy.polyval (not the oracle's nested form)."""
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        coef = rng.standard_normal(5) * np.array([1.0, 1.0, 3.0, 10.0, 30.0])
+        coef[1] = -abs(coef[1])
+        amax = float(rng.uniform(1e-3, 2.0))
+        a = O.armijo_step(coef, amax)
+        phi = lambda t: np.polyval(coef[::-1], t) - coef[0]
+        acc = [amax * 0.5 ** j for j in range(60) if phi(amax * 0.5 ** j) <= 1e-4 * amax * 0.5 ** j * coef[1]]
+        assert a == (acc[0] if acc else 0.0)
+    assert O.armijo_step(np.array([0.0, 1.0, 1.0, 0.0, 1.0]), 1.0) == 0.0   # phi'(0) > 0: no step
+    assert O.armijo_step(np.array([0.0, -1.0, 0.0, 0.0, 0.0]), 0.0) == 0.0  # empty interval
+
+
+def test_armijo_solve_reaches_the_exact_rule_minimiser():
+    """Under the certificate the minimiser is unique, so both step rules must end
+    at the same point (Table yand-line-search compares their iterations)."""
+    R = panels.uniform_panel(12, 252, 3)
+    mu, A = O.centre(R)
+    c = np.array([1.0, 10.0, 1.0, 10.0])
+    x_e, inf_e = O.solve(A, mu, c, "direct", 1e-10)
+    x_a, inf_a = O.solve(A, mu, c, "direct", 1e-10, opts=O.Options(line_search="armijo", max_iter=120))
+    assert inf_e.status == "converged" and inf_a.status == "converged"
+    assert np.max(np.abs(x_a - x_e)) <= 1e-8
+
+
+@pytest.mark.parametrize("n,T,kappa", [(40, 80, 10.0), (60, 30, 100.0), (30, 200, 1.0)])
+def test_crra_conditioning_construction(n, T, kappa):
+    """Table crra-conditioning construction: A = Q diag(s) W^T with W = U V and
+    A 1/n = 0 gives kappa_+(A U) = kappa and, since z = A x0 = 0 makes
+    psi'' constant, kappa_+(H_0) = kappa^2 for the reduced Hessian at 1/n
+    (checked by SVD and by eigenvalues of the oracle's Gram)."""
+    R = panels.crra_conditioning_panel(n, T, kappa, 1)
+    mu, A = O.centre(R)
+    x0 = np.full(n, 1.0 / n)
+    assert np.max(np.abs(A @ x0)) <= 1e-15
+    U = O.tangent_basis(n)
+    sv = np.linalg.svd(A @ U, compute_uv=False)
+    sv = sv[sv > 1e-10 * sv[0]]
+    assert sv[0] / sv[-1] == pytest.approx(kappa, rel=1e-9)
+    ev = np.linalg.eigvalsh(U.T @ O.gram(A, np.array(panels.CRRA_GAMMA6), x0) @ U)
+    ev = ev[ev > 1e-10 * ev.max()]
+    assert ev.max() / ev.min() == pytest.approx(kappa ** 2, rel=1e-8)
