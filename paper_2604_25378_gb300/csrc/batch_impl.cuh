@@ -618,7 +618,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     int s2 = 0;
     TRY(hvp_tc_batch(c, bb, B, ncol1, &s2));
     const KPart kp{bb.part, s2, B * ncol1, ncol1, c->ld, invT, bb.P16};
-    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step_f<<<dim3(ncol1, B), kPT, 0, c->stream>>>(base, 0, kmax, kp)));
+    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step_f<<<dim3(ncol1, B), kPTF, 0, c->stream>>>(base, 0, kmax, kp)));
   }
   if (K > 0) {
     TRY(third_tc_batch(c, bb, B, K));
@@ -631,7 +631,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     int s2 = 0;
     TRY(hvp_tc_batch(c, bb, B, 1, &s2));
     const KPart kp{bb.part, s2, B, 1, c->ld, invT, bb.P16};
-    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step_f<<<dim3(1, B), kPT, 0, c->stream>>>(base, ca, kmax, kp)));
+    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step_f<<<dim3(1, B), kPTF, 0, c->stream>>>(base, ca, kmax, kp)));
   }
   PROF_LAUNCH(NK_ASSEMBLE, (k_assemble<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca)));
   if (split) {

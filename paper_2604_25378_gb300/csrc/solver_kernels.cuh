@@ -563,8 +563,12 @@ __device__ __forceinline__ void block_sumNf(float (&v)[N], float* scr) {
 // expanded into sums over the stored vectors,
 //   p^T q   = sum p mf Q - qmean sum p mf - (nu^T Q) sum p nu + lam sum p^2,
 //   r'^T z' = sum r' mf t - tmean sum r' mf - (nu^T t) sum r' nu,  t = r' / diag,
-// so that each block reduction carries every sum of its phase.
-static __global__ void __launch_bounds__(kPT, 2) k_pcg_step_f(Inst s0, int c0, int kmaxit, KPart kp) {
+// so that each block reduction carries every sum of its phase.  Every operand
+// is loaded in the first pass (one memory round trip); 1024 threads keep
+// their kPEF coordinates of Q, P, R, X and the face data in registers.
+constexpr int kPTF = 1024;
+constexpr int kPEF = (kMaxCols + kPTF - 1) / kPTF;
+static __global__ void __launch_bounds__(kPTF, 1) k_pcg_step_f(Inst s0, int c0, int kmaxit, KPart kp) {
   Inst s = inst_at(s0, blockIdx.y);
   __shared__ float scr[33 * 6 + 8];
   int* SI = s.si;
@@ -586,24 +590,29 @@ static __global__ void __launch_bounds__(kPT, 2) k_pcg_step_f(Inst s0, int c0, i
   const float* __restrict__ fnh = f0.nh;
   const float* __restrict__ fdg = f0.dg;
   const size_t prow = (size_t)blockIdx.y * kp.nc + blockIdx.x;
-  float q[kPE], p[kPE];
+  float q[kPEF], p[kPEF], r[kPEF], xv[kPEF], mf[kPEF], nh[kPEF], dg[kPEF];
   float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // mf.Q, nu.Q, p.mf.Q, p.mf, p.nu, p.p
 #pragma unroll
-  for (int e = 0; e < kPE; ++e) {
-    const int i = threadIdx.x + e * kPT;
-    q[e] = 0.f;
-    p[e] = 0.f;
+  for (int e = 0; e < kPEF; ++e) {
+    const int i = threadIdx.x + e * kPTF;
+    q[e] = p[e] = r[e] = xv[e] = mf[e] = nh[e] = 0.f;
+    dg[e] = 1.f;
     if (i < n) {
       float acc = 0.f;
       for (int z = 0; z < kp.splits; ++z) acc += part[((size_t)z * kp.N + prow) * kp.ldp + i];
       q[e] = kp.scale * acc;
       p[e] = P[i];
-      const float mq = fmf[i] * q[e];
+      r[e] = R[i];
+      xv[e] = X[i];
+      mf[e] = fmf[i];
+      nh[e] = fnh[i];
+      dg[e] = fdg[i];
+      const float mq = mf[e] * q[e];
       a[0] += mq;
-      a[1] += fnh[i] * q[e];
+      a[1] += nh[e] * q[e];
       a[2] += p[e] * mq;
-      a[3] += p[e] * fmf[i];
-      a[4] += p[e] * fnh[i];
+      a[3] += p[e] * mf[e];
+      a[4] += p[e] * nh[e];
       a[5] += p[e] * p[e];
     }
   }
@@ -623,21 +632,22 @@ static __global__ void __launch_bounds__(kPT, 2) k_pcg_step_f(Inst s0, int c0, i
   const float al = (float)s.rz[c] / pq;
   float b[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // r.r, mf.t, nu.t, r.mf.t, r.mf, r.nu
 #pragma unroll
-  for (int e = 0; e < kPE; ++e) {
-    const int i = threadIdx.x + e * kPT;
+  for (int e = 0; e < kPEF; ++e) {
+    const int i = threadIdx.x + e * kPTF;
     if (i < n) {
-      const float qq = fmf[i] * (q[e] - qmean) - ry * fnh[i] + lam * p[e];
-      X[i] += al * p[e];
-      const float rv = R[i] - al * qq;
+      const float qq = mf[e] * (q[e] - qmean) - ry * nh[e] + lam * p[e];
+      X[i] = xv[e] + al * p[e];
+      const float rv = r[e] - al * qq;
       R[i] = rv;
-      const float t = rv / fdg[i];
+      r[e] = rv;
+      const float t = rv / dg[e];
       q[e] = t;  // q now holds t = R / |diag G|
       b[0] += rv * rv;
-      b[1] += fmf[i] * t;
-      b[2] += fnh[i] * t;
-      b[3] += rv * fmf[i] * t;
-      b[4] += rv * fmf[i];
-      b[5] += rv * fnh[i];
+      b[1] += mf[e] * t;
+      b[2] += nh[e] * t;
+      b[3] += rv * mf[e] * t;
+      b[4] += rv * mf[e];
+      b[5] += rv * nh[e];
     }
   }
   block_sumNf<6>(b, scr);
@@ -653,10 +663,10 @@ static __global__ void __launch_bounds__(kPT, 2) k_pcg_step_f(Inst s0, int c0, i
   const float rzn = b[3] - tmean * b[4] - tb2 * b[5];
   const float beta = rzn / (float)s.rz[c];
 #pragma unroll
-  for (int e = 0; e < kPE; ++e) {
-    const int i = threadIdx.x + e * kPT;
+  for (int e = 0; e < kPEF; ++e) {
+    const int i = threadIdx.x + e * kPTF;
     if (i < n) {
-      const float zz = fmf[i] * (q[e] - tmean) - tb2 * fnh[i];
+      const float zz = mf[e] * (q[e] - tmean) - tb2 * nh[e];
       const float pn = zz + beta * p[e];
       P[i] = pn;
       P16[prow * ld + i] = __float2bfloat16(pn);
