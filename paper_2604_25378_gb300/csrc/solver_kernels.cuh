@@ -216,8 +216,9 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
   const double gn = sqrt(block_sum2(gq, 0.0, scr).x);
   const int mi = (int)m;
   const bool trivial = mi <= 2 || !(gn > 0.0);
+  const double inv_gn = gn > 0.0 ? 1.0 / gn : 0.0;  // one FP64 division instead of n
   for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
-    const double nh = (i < n && gn > 0.0) ? s.nuhat[i] / gn : 0.0;
+    const double nh = (i < n && gn > 0.0) ? s.nuhat[i] * inv_gn : 0.0;
     s.nuhat[i] = nh;
     if (trivial) s.d[i] = (mi == 2) ? -nh : 0.0;
   }
@@ -763,10 +764,22 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
   const int n = s.n;
   const double tau = SD[SD_TAU], eta = SD[SD_ETA];
   ls_coefficients(s, s.spart, G, s.d, coef, scr, ps);
-  double am = INFINITY;
+  // alpha_max = min over d_i < 0 of (x_i - tau) / (-d_i), exactly rounded: FP32
+  // ratios screen the candidates within 1e-5 of their minimum, and only those
+  // take the FP64 division (tens of FP64-pipe operations each on this part).
+  // (Ratios beyond the FP32 range count as +inf.)
+  float am32 = INFINITY;
   for (int i = threadIdx.x; i < n; i += blockDim.x)
-    if (s.d[i] < 0.0) am = fmin(am, (s.x[i] - tau) / (-s.d[i]));
-  am = block_min(am, scr);
+    if (s.d[i] < 0.0) am32 = fminf(am32, (float)(s.x[i] - tau) / (float)(-s.d[i]));
+  am32 = (float)block_min((double)am32, scr);
+  double am = INFINITY;
+  if (am32 < INFINITY) {
+    const float thr = am32 * (1.0f + 1e-5f);
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (s.d[i] < 0.0 && (float)(s.x[i] - tau) / (float)(-s.d[i]) <= thr)
+        am = fmin(am, (s.x[i] - tau) / (-s.d[i]));
+    am = block_min(am, scr);
+  }
   double eta_k = fmin(eta, quartic_argmin(coef, eta));
   if (threadIdx.x == 0) {
     SD[SD_AMAX] = am;
@@ -790,11 +803,13 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
   gt = sqrt(block_sum2(gt, 0.0, scr).x);
   bool descent = false;
   const int hmax = SI[SI_ARCMAX];
+  double* u = s.tmp + s.ld;  // x + eta_k d - tau of the current trial (slice_theta scratch)
+  double th = 0.0;
   for (int h = 0; h <= hmax; ++h) {
-    const double th = slice_theta(s.x, s.d, eta_k, n, tau, scr);
+    th = slice_theta(s.x, s.d, eta_k, n, tau, scr, u);
     double gd = 0.0, dd = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const double xb = tau + fmax(s.x[i] + eta_k * s.d[i] - tau - th, 0.0);
+      const double xb = tau + fmax(u[i] - th, 0.0);
       const double db = xb - s.x[i];
       gd += s.g[i] * db;
       dd += db * db;
@@ -805,10 +820,9 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
     eta_k *= 0.5;
   }
   if (threadIdx.x == 0) SD[SD_ETAK] = eta_k;
-  if (descent) {
-    const double th = slice_theta(s.x, s.d, eta_k, n, tau, scr);
+  if (descent) {  // u and th still hold the accepted trial
     for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
-      const double xb = i < n ? tau + fmax(s.x[i] + eta_k * s.d[i] - tau - th, 0.0) : 0.0;
+      const double xb = i < n ? tau + fmax(u[i] - th, 0.0) : 0.0;
       s.xbar[i] = xb;
       s.dstep[i] = i < n ? xb - s.x[i] : 0.0;
     }
@@ -836,10 +850,10 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
   const double sc = eta * dn / fmax(gt, 1e-300);
   for (int i = threadIdx.x; i < n; i += blockDim.x) s.tmp[i] = -s.g[i];
   __syncthreads();
-  const double th = slice_theta(s.x, s.tmp, sc, n, tau, scr);
+  th = slice_theta(s.x, s.tmp, sc, n, tau, scr, u);
   double gd = 0.0;
   for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
-    const double xb = i < n ? tau + fmax(s.x[i] + sc * s.tmp[i] - tau - th, 0.0) : 0.0;
+    const double xb = i < n ? tau + fmax(u[i] - th, 0.0) : 0.0;
     s.xbar[i] = xb;
     const double db = i < n ? xb - s.x[i] : 0.0;
     s.dstep[i] = db;
