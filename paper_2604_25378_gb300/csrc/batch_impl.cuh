@@ -54,29 +54,28 @@ __global__ void k_reduce_at_b(const float* part, int splits, int B, int n, int l
 }
 
 // rhat_b[t] = K^-1 sum_k (A X_k)_t (A p_k)_t; S^T[b][t] = bf16(psi3_b(z_b[t]) rhat_b[t]).
+// Grid (T/256, B).  The pair products come from BF16 operands, so FP32 sums of
+// K of them lose nothing; only the BF16 weights are kept (the lockstep path has
+// no other reader of rhat).
 __global__ void k_reduce_rhat_b(const float* part, int splits, int N, int K, long long T, long long ldp, Inst base,
                                 __nv_bfloat16* S, long long Tp) {
-  const int B = N / (2 * K);
-  const long long tot = (long long)B * T;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(e / T);
-    const long long t = e % T;
-    const Inst s = inst_at(base, b);
-    double r = 0.0;
-    for (int k = 0; k < K; ++k) {
-      float u = 0.f, v = 0.f;
-      const int q = b * 2 * K + 2 * k;
-      for (int z = 0; z < splits; ++z) {
-        u += part[((size_t)z * N + q) * ldp + t];
-        v += part[((size_t)z * N + q + 1) * ldp + t];
-      }
-      r += (double)u * (double)v;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (t >= T) return;
+  const Inst s = inst_at(base, b);
+  float r = 0.f;
+  for (int k = 0; k < K; ++k) {
+    float u = 0.f, v = 0.f;
+    const int q = b * 2 * K + 2 * k;
+    for (int z = 0; z < splits; ++z) {
+      u += part[((size_t)z * N + q) * ldp + t];
+      v += part[((size_t)z * N + q + 1) * ldp + t];
     }
-    r /= K;
-    s.rhat[t] = r;
-    const Psi psi{0.0, s.sd[SD_C3], s.sd[SD_C4]};
-    S[(size_t)b * Tp + t] = __float2bfloat16((float)(psi.d3(s.z[t]) * r));
+    r = fmaf(u, v, r);
   }
+  const Psi psi{0.0, s.sd[SD_C3], s.sd[SD_C4]};
+  const float w = (float)psi.d3(s.z[t]);
+  S[(size_t)b * Tp + t] = __float2bfloat16(w * (r / (float)K));
 }
 
 // ------------------------------------------- split tensor-core FP64 products
@@ -120,7 +119,7 @@ __global__ void k_oz_fin_g(const long long* part, int splits, int Bp, long long 
 // The twelve power sums s_rs of (z_t, w_t = a_t^T d) (Prop. quartic line search).
 __global__ void __launch_bounds__(256) k_oz_fin_ls(const long long* part, int splits, int Bp, long long ldp,
                                                    const int* em, const int* fb, Inst base, int b0, int skip_slot) {
-  __shared__ double scr[64];
+  __shared__ double red[12][256];
   const int bl = blockIdx.y;
   Inst s = inst_at(base, b0 + bl);
   if (s.si[SI_DONE] != 0 || s.si[skip_slot] != 0) return;
@@ -143,10 +142,20 @@ __global__ void __launch_bounds__(256) k_oz_fin_ls(const long long* part, int sp
     a[10] += zt * w2 * w;  // s13
     a[11] += w2 * w2;      // s04
   }
-#pragma unroll 1
-  for (int q = 0; q < 12; ++q) {
-    const double v = block_sum(a[q], scr);
-    if (threadIdx.x == 0) s.spart[(size_t)blockIdx.x * 12 + q] = v;
+  // Staged reduction of the twelve sums: 16 threads per sum add 16 values
+  // each, then a 16-lane shuffle tree (about a fifth of the FP64 additions of
+  // twelve separate block-wide shuffle trees, and two barriers instead of 36).
+#pragma unroll
+  for (int q = 0; q < 12; ++q) red[q][threadIdx.x] = a[q];
+  __syncthreads();
+  if (threadIdx.x < 192) {
+    const int q = threadIdx.x >> 4, j = threadIdx.x & 15;
+    double v = 0.0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v += red[q][j + 16 * k];
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (j == 0) s.spart[(size_t)blockIdx.x * 12 + q] = v;
   }
 }
 
@@ -521,12 +530,12 @@ mvsk_status hvp_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int nc, int* s2) {
 
 // rhat_b and at_b = T^-1 A^T (psi3_b(z_b) o rhat_b) for every instance.
 mvsk_status third_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int K) {
-  const int N = B * 2 * K, gb = 4 * c->nsm;
+  const int N = B * 2 * K;
   const unsigned gl = (unsigned)((c->ld + 255) / 256);
   PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl, N), 256, 0, c->stream>>>(bb.base, 2 * K, 0, 1, bb.P16)));
   int s1 = 0, s2 = 0;
   TRY(tc_partials_n(c, c->Alo, (int)c->T, bb.P16, N, c->ld, c->ld, bb.part, bb.part_floats, c->T, &s1));
-  PROF_LAUNCH(NK_RHAT, (k_reduce_rhat_b<<<gb, 256, 0, c->stream>>>(bb.part, s1, N, K, c->T, c->T, bb.base, bb.S16T,
+  PROF_LAUNCH(NK_RHAT, (k_reduce_rhat_b<<<dim3((unsigned)((c->T + 255) / 256), B), 256, 0, c->stream>>>(bb.part, s1, N, K, c->T, c->T, bb.base, bb.S16T,
                                                                    c->Tp)));
   TRY(tc_partials_n(c, c->A16T, c->n, bb.S16T, B, c->Tp, c->Tp, bb.part, bb.part_floats, c->ld, &s2));
   PROF_LAUNCH(NK_HVP2, (k_reduce_at_b<<<dim3(gl, B), 256, 0, c->stream>>>(bb.part, s2, B, c->n, c->ld, c->ld,
@@ -570,14 +579,15 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
   const bool split = c->opt.split_products != 0;
   const OzBuf& oz = c->oz;
   const int Gz = oz_row_ctas(c);
-  const int Gs = split ? Gz : c->grid;  // scalar partials per instance of the value and line-search products
+  const int Gs = split ? Gz : c->grid;  // scalar partials per instance of the value product
+  const int Gl = split ? oz_ls_ctas(c) : c->grid;  // ... and of the line-search products
   // split products of one of the directions d (d_b = base + b*vs) for groups of <= 64 instances
   auto ls_split = [&](double* dvec, int skip_slot, const int* need) -> mvsk_status {
     for (int b0 = 0; b0 < B; b0 += kOzMaxB) {
       const int nb = B - b0 < kOzMaxB ? B - b0 : kOzMaxB;
       int sp = 0;
       TRY(oz_product(c, 0, dvec + (size_t)b0 * base.vs, base.vs, nb, oz_bp(nb), need, &sp));
-      PROF_LAUNCH(NK_OZ_LS, (k_oz_fin_ls<<<dim3(Gz, nb), 256, 0, c->stream>>>(oz.part, sp, oz_bp(nb), oz.MpF, oz.eF,
+      PROF_LAUNCH(NK_OZ_LS, (k_oz_fin_ls<<<dim3(Gl, nb), 256, 0, c->stream>>>(oz.part, sp, oz_bp(nb), oz.MpF, oz.eF,
                                                                              oz.fF, base, b0, skip_slot)));
     }
     return MVSK_OK;
@@ -646,7 +656,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
       TRY(run_pass(c, P64, M_LS, 1, a, nullptr, s.spart));
     }
   }
-  PROF_LAUNCH(NK_DECIDE1, (k_decide1<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gs)));
+  PROF_LAUNCH(NK_DECIDE1, (k_decide1<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gl)));
   if (split) {
     PROF_LAUNCH(NK_NEED, (k_need_ls2<<<1, 64, 0, c->stream>>>(base, B, bb.need)));
     TRY(ls_split(base.dstep, SI_SKIPLS, bb.need));
@@ -660,7 +670,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
       TRY(run_pass(c, P64, M_LS, 1, a, nullptr, s.spart));
     }
   }
-  PROF_LAUNCH(NK_DECIDE2, (k_decide2<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gs)));
+  PROF_LAUNCH(NK_DECIDE2, (k_decide2<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gl)));
   PROF_LAUNCH(NK_END_ITER, (k_end_iter<<<dim3(1, B), 32, 0, c->stream>>>(base)));
   return MVSK_OK;
 }

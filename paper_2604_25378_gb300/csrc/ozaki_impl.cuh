@@ -111,3 +111,10 @@ int oz_row_ctas(const mvsk_ctx* c) {
   const long long g = (c->T + 255) / 256;
   return (int)(g < c->grid ? g : c->grid);
 }
+
+// CTAs per instance of the line-search power sums: four rows per thread, so
+// that the twelve-sum reduction of each CTA is amortised over 1024 rows.
+int oz_ls_ctas(const mvsk_ctx* c) {
+  const long long g = (c->T + 1023) / 1024;
+  return (int)(g < c->grid ? g : c->grid);
+}

@@ -51,8 +51,8 @@ inline __device__ void project_V(const double* v, double* out, const double* mas
     s += maskF[i] * v[i];
     t += nuhat[i] * v[i];
   }
-  const double2 r = block_sum2(s, t, scr);
-  const double mean = r.x / m;
+  const double4 r = block_sum2_fin(s, t, scr, [=](double x, double) { return make_double2(x / m, 0.0); });
+  const double mean = r.z;
   for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = maskF[i] * (v[i] - mean) - r.y * nuhat[i];
   __syncthreads();
 }
@@ -127,8 +127,8 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
     }
     __syncthreads();
     if (s_stop) return;
-    const double kkt = kkt_residual(s.x, s.g, n, tau, scr, s.tmp);
-    const double rel = kkt / fmax(SD[SD_KKT0], 1e-300);
+    const double2 kr = kkt_residual_rel(s.x, s.g, n, tau, scr, s.tmp, SD[SD_KKT0]);
+    const double kkt = kr.x, rel = kr.y;
     const bool better = rel < SD[SD_BEST];
     if (better)
       for (int i = threadIdx.x; i < n; i += blockDim.x) s.bestx[i] = s.x[i];
@@ -165,8 +165,7 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
       sg += s.g[i];
       cf += 1.0;
     }
-  double2 r = block_sum2(sg, cf, scr);
-  double nuF = r.x / r.y;
+  double nuF = block_sum2_fin(sg, cf, scr, [](double x, double y) { return make_double2(x / y, 0.0); }).z;
   double gq = 0.0;
   double best = -INFINITY;
   int bidx = 0x7fffffff;
@@ -182,7 +181,7 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
       }
     }
   }
-  const double gn0 = sqrt(block_sum2(gq, 0.0, scr).x);
+  const double gn0 = block_sum2_fin(gq, 0.0, scr, [](double x, double) { return make_double2(sqrt(x), 0.0); }).z;
   block_argmax(best, bidx, sv, si_);
   const bool rel_ok = bidx != 0x7fffffff && best > 0.0 && gn0 <= SD[SD_RELRATIO] * best;
   for (int i = threadIdx.x; i < n; i += blockDim.x)
@@ -194,9 +193,9 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
     sg += s.maskF[i] * s.g[i];
     cf += s.maskF[i];
   }
-  r = block_sum2(sg, cf, scr);
+  const double4 r = block_sum2_fin(sg, cf, scr, [](double x, double y) { return make_double2(x / y, 0.0); });
   const double m = r.y;
-  nuF = r.x / m;
+  nuF = r.z;
   // gbar = P_F g, centred twice: the second pass removes the rounding of the
   // first relative to gbar itself (not to g), so 1_F^T nu stays at rounding
   // level even when ||gbar|| << |g| near a stationary point.
@@ -206,17 +205,20 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
     s.nuhat[i] = e;
     sb += e;
   }
-  const double mb = block_sum2(sb, 0.0, scr).x / m;
+  const double mb = block_sum2_fin(sb, 0.0, scr, [=](double x, double) { return make_double2(x / m, 0.0); }).z;
   gq = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double e = s.maskF[i] * (s.nuhat[i] - mb);
     s.nuhat[i] = e;
     gq += e * e;
   }
-  const double gn = sqrt(block_sum2(gq, 0.0, scr).x);
+  const double4 rg = block_sum2_fin(gq, 0.0, scr, [](double x, double) {
+    const double v = sqrt(x);
+    return make_double2(v, v > 0.0 ? 1.0 / v : 0.0);
+  });
+  const double gn = rg.z, inv_gn = rg.w;  // one FP64 division instead of n
   const int mi = (int)m;
   const bool trivial = mi <= 2 || !(gn > 0.0);
-  const double inv_gn = gn > 0.0 ? 1.0 / gn : 0.0;  // one FP64 division instead of n
   for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
     const double nh = (i < n && gn > 0.0) ? s.nuhat[i] * inv_gn : 0.0;
     s.nuhat[i] = nh;
@@ -270,8 +272,8 @@ inline __device__ void project_Vk(const TI* v, KT* out, const Face<KT>& f, int n
     a += f.mf[i] * (KT)v[i];
     b += f.nh[i] * (KT)v[i];
   }
-  const double2 r = block_sum2((double)a, (double)b, scr);
-  const KT mean = (KT)(r.x / m), ny = (KT)r.y;
+  const double4 r = block_sum2_fin((double)a, (double)b, scr, [=](double x, double) { return make_double2(x / m, 0.0); });
+  const KT mean = (KT)r.z, ny = (KT)r.y;
   for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = f.mf[i] * ((KT)v[i] - mean) - ny * f.nh[i];
   __syncthreads();
 }
@@ -303,7 +305,7 @@ inline __device__ void pcg_init_col(Inst& s, int c, double m, double* scr) {
   const double2 r = block_sum2((double)rz, (double)nb, scr);
   if (threadIdx.x == 0) {
     s.rz[c] = r.x;
-    s.rhsn[c] = sqrt(r.y);
+    s.rhsn[c] = sqrt(r.y);  // one thread
     s.si[SI_ACT + c] = r.y > 0.0 ? 1 : 0;
     s.si[SI_CITS + c] = 0;
   }
@@ -328,8 +330,12 @@ static __global__ void __launch_bounds__(kVT) k_pcg_setup(Inst s0, const double*
     sd += s.maskF[i] * s.diagG[i];
     sa += s.maskF[i] * fabs(s.diagG[i]);
   }
-  const double2 r = block_sum2(sd, sa, scr);
-  const double floor_ = 1e-300 + 1e-12 * (r.y / m);
+  const double psum1 = ps[1], psum0 = ps[0], reg = SD[SD_REG];
+  const double4 r = block_sum2_fin(sd, sa, scr, [=](double x, double y) {
+    const double trG = x - psum1 / m - psum0;
+    return make_double2(1e-300 + 1e-12 * (y / m), reg * fabs(trG) / (m - 2.0));
+  });
+  const double floor_ = r.z, lam = r.w;
   for (int i = threadIdx.x; i < n; i += blockDim.x)
     s.diagG[i] = s.maskF[i] != 0.0 ? fmax(fabs(s.diagG[i]), floor_) : 1.0;
   if constexpr (sizeof(KT) == sizeof(float)) {
@@ -340,8 +346,6 @@ static __global__ void __launch_bounds__(kVT) k_pcg_setup(Inst s0, const double*
     }
   }
   __syncthreads();
-  const double trG = r.x - ps[1] / m - ps[0];
-  const double lam = SD[SD_REG] * fabs(trG) / (m - 2.0);
   if (threadIdx.x == 0) SD[SD_LAM] = lam;
   if (ngroups < 0) return;  // the columns are set up by k_pcg_setup_cols
   const Face<KT> f = face_of<KT>(s);
@@ -707,7 +711,10 @@ static __global__ void __launch_bounds__(kVT) k_assemble(Inst s0, int ca) {
   int* SI = s.si;
   if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
   const double m = (double)SI[SI_M];
-  const double coef = s.sd[SD_GN] / m;
+  __shared__ double s_coef;
+  if (threadIdx.x == 0) s_coef = s.sd[SD_GN] / m;
+  __syncthreads();
+  const double coef = s_coef;
   const KT* Xh = kcol<KT>(s.X, 0, s.ld);
   const KT* Xa = kcol<KT>(s.X, ca, s.ld);
   double sd = 0.0;
@@ -716,7 +723,7 @@ static __global__ void __launch_bounds__(kVT) k_assemble(Inst s0, int ca) {
     s.d[i] = v;
     sd += v;
   }
-  const double md = block_sum2(sd, 0.0, scr).x / m;
+  const double md = block_sum2_fin(sd, 0.0, scr, [=](double x, double) { return make_double2(x / m, 0.0); }).z;
   for (int i = threadIdx.x; i < s.n; i += blockDim.x) s.d[i] -= s.maskF[i] * md;
 }
 
@@ -758,12 +765,15 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
   __shared__ double scr[80];
   __shared__ double ps[16];
   __shared__ double coef[5];
+  __shared__ double s_eq, s_bc;
   int* SI = s.si;
   double* SD = s.sd;
   if (SI[SI_DONE] != 0) return;
   const int n = s.n;
   const double tau = SD[SD_TAU], eta = SD[SD_ETA];
   ls_coefficients(s, s.spart, G, s.d, coef, scr, ps);
+  // The exact step on [0, eta] (one thread; read after the reductions below).
+  if (threadIdx.x == 0) s_eq = quartic_argmin(coef, eta);
   // alpha_max = min over d_i < 0 of (x_i - tau) / (-d_i), exactly rounded: FP32
   // ratios screen the candidates within 1e-5 of their minimum, and only those
   // take the FP64 division (tens of FP64-pipe operations each on this part).
@@ -780,13 +790,13 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
         am = fmin(am, (s.x[i] - tau) / (-s.d[i]));
     am = block_min(am, scr);
   }
-  double eta_k = fmin(eta, quartic_argmin(coef, eta));
+  double eta_k = fmin(eta, s_eq);
   if (threadIdx.x == 0) {
     SD[SD_AMAX] = am;
     SI[SI_SKIPLS] = 1;
   }
   if (am >= eta_k) {
-    const double al = line_step(coef, am, SI[SI_LSRULE]);
+    const double al = block_line_step(coef, am, SI[SI_LSRULE], &s_bc);
     take_step(s, s.d, al, nullptr);
     if (threadIdx.x == 0) {
       SD[SD_ALPHA] = al;
@@ -797,12 +807,13 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
   }
   double gm = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) gm += s.g[i];
-  gm = block_sum2(gm, 0.0, scr).x / n;
+  gm = block_sum2_fin(gm, 0.0, scr, [=](double x, double) { return make_double2(x / n, 0.0); }).z;
   double gt = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) gt += (s.g[i] - gm) * (s.g[i] - gm);
-  gt = sqrt(block_sum2(gt, 0.0, scr).x);
+  gt = block_sum2_fin(gt, 0.0, scr, [](double x, double) { return make_double2(sqrt(x), 0.0); }).z;
   bool descent = false;
   const int hmax = SI[SI_ARCMAX];
+  const double deps = SD[SD_DESCEPS];
   double* u = s.tmp + s.ld;  // x + eta_k d - tau of the current trial (slice_theta scratch)
   double th = 0.0;
   for (int h = 0; h <= hmax; ++h) {
@@ -814,8 +825,9 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
       gd += s.g[i] * db;
       dd += db * db;
     }
-    const double2 r = block_sum2(gd, dd, scr);
-    descent = r.x < -SD[SD_DESCEPS] * gt * sqrt(r.y);
+    descent = block_sum2_fin(gd, dd, scr, [=](double x, double y) {
+                return make_double2(x < -deps * gt * sqrt(y) ? 1.0 : 0.0, 0.0);
+              }).z != 0.0;
     if (descent || 0.5 * eta_k <= am) break;
     eta_k *= 0.5;
   }
@@ -834,7 +846,7 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
     return;
   }
   if (am > 0.0) {
-    const double al = line_step(coef, am, SI[SI_LSRULE]);
+    const double al = block_line_step(coef, am, SI[SI_LSRULE], &s_bc);
     take_step(s, s.d, al, nullptr);
     if (threadIdx.x == 0) {
       SD[SD_ALPHA] = al;
@@ -846,8 +858,9 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
   // Face hand-off: projected-gradient segment scaled to the YAND trial length.
   double dn = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) dn += s.d[i] * s.d[i];
-  dn = sqrt(block_sum2(dn, 0.0, scr).x);
-  const double sc = eta * dn / fmax(gt, 1e-300);
+  const double sc = block_sum2_fin(dn, 0.0, scr, [=](double x, double) {
+                      return make_double2(eta * sqrt(x) / fmax(gt, 1e-300), 0.0);
+                    }).z;
   for (int i = threadIdx.x; i < n; i += blockDim.x) s.tmp[i] = -s.g[i];
   __syncthreads();
   th = slice_theta(s.x, s.tmp, sc, n, tau, scr, u);
@@ -873,9 +886,10 @@ static __global__ void __launch_bounds__(kVT) k_decide2(Inst s0, const double* s
   __shared__ double scr[80];
   __shared__ double ps[16];
   __shared__ double coef[5];
+  __shared__ double s_bc;
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPLS] != 0) return;
   ls_coefficients(s, s.spart, G, s.dstep, coef, scr, ps);
-  const double al = line_step(coef, 1.0, s.si[SI_LSRULE]);
+  const double al = block_line_step(coef, 1.0, s.si[SI_LSRULE], &s_bc);
   take_step(s, s.dstep, al, al == 1.0 ? s.xbar : nullptr);
   if (threadIdx.x == 0) s.sd[SD_ALPHA] = al;
 }

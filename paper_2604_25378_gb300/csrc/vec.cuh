@@ -95,6 +95,39 @@ __device__ __forceinline__ double2 block_sum2(double a, double b, double* scr) {
   return make_double2(scr[64], scr[65]);
 }
 
+// block_sum2 whose scalar finish fin(x, y) -> (z, w) (a division, a square
+// root, a test) is evaluated once, by the thread that completes the sums, and
+// broadcast with them: an FP64 division or square root is about ten FP64-pipe
+// instructions, and that pipe retires ~2 FMA/clk/SM on this part, so the same
+// finish repeated by the 32 warps of a 1024-thread block costs microseconds.
+// Returns {x, y, z, w}; scr holds >= 68 doubles.
+template <typename F>
+__device__ __forceinline__ double4 block_sum2_fin(double a, double b, double* scr, F fin) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __syncthreads();
+  if (lane == 0) {
+    scr[warp] = a;
+    scr[32 + warp] = b;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double ta = lane < nw ? scr[lane] : 0.0, tb = lane < nw ? scr[32 + lane] : 0.0;
+    ta = warp_sum(ta);
+    tb = warp_sum(tb);
+    if (lane == 0) {
+      const double2 zw = fin(ta, tb);
+      scr[64] = ta;
+      scr[65] = tb;
+      scr[66] = zw.x;
+      scr[67] = zw.y;
+    }
+  }
+  __syncthreads();
+  return make_double4(scr[64], scr[65], scr[66], scr[67]);
+}
+
 // The same in FP32 (scr >= 66 floats).
 __device__ __forceinline__ float2 block_sum2f(float a, float b, float* scr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -148,8 +181,8 @@ inline __device__ double slice_theta(const double* base, const double* dir, doub
     if (u) u[i] = ui;
     su += ui;
   }
-  double2 r = block_sum2(su, 0.0, scr);
-  double theta = (r.x - b) / (double)n;
+  const double4 r0 = block_sum2_fin(su, 0.0, scr, [=](double x, double) { return make_double2((x - b) / (double)n, 0.0); });
+  double theta = r0.z;
   double cnt = (double)n;
   for (int it = 0; it <= n; ++it) {
     double sa = 0.0;
@@ -161,16 +194,20 @@ inline __device__ double slice_theta(const double* base, const double* dir, doub
         ka += 1;
       }
     }
-    r = block_sum2(sa, (double)ka, scr);
+    const double4 r = block_sum2_fin(sa, (double)ka, scr, [=](double x, double y) {
+      return make_double2(y > 0.0 ? (x - b) / y : 0.0, 0.0);
+    });
     if (r.y == cnt || r.y == 0.0) break;
     cnt = r.y;
-    theta = (r.x - b) / cnt;
+    theta = r.z;
   }
   return theta;
 }
 
-// ||x - Pi(x - g)||_2 (projected-simplex KKT residual); tmp receives x - g - tau.
-inline __device__ double kkt_residual(const double* x, const double* g, int n, double tau, double* scr, double* tmp) {
+// (||x - Pi(x - g)||_2, that / max(norm, 1e-300)): the projected-simplex KKT
+// residual and its relative value; tmp receives x - g - tau.
+inline __device__ double2 kkt_residual_rel(const double* x, const double* g, int n, double tau, double* scr,
+                                           double* tmp, double norm) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) tmp[i] = x[i] - g[i];
   __syncthreads();
   const double th = slice_theta(tmp, nullptr, 0.0, n, tau, scr, tmp);
@@ -180,7 +217,15 @@ inline __device__ double kkt_residual(const double* x, const double* g, int n, d
     const double e = x[i] - p;
     s += e * e;
   }
-  return sqrt(block_sum2(s, 0.0, scr).x);
+  const double4 r = block_sum2_fin(s, 0.0, scr, [=](double x2, double) {
+    const double k = sqrt(x2);
+    return make_double2(k, k / fmax(norm, 1e-300));
+  });
+  return make_double2(r.z, r.w);
+}
+
+inline __device__ double kkt_residual(const double* x, const double* g, int n, double tau, double* scr, double* tmp) {
+  return kkt_residual_rel(x, g, n, tau, scr, tmp, 1.0).x;
 }
 
 // ------------------------------------------------------- exact quartic step
@@ -277,6 +322,16 @@ inline __device__ double armijo_step(const double* c, double amax) {
 // Step along a direction on [0, amax] by rule (SI_LSRULE).
 inline __device__ double line_step(const double* c, double amax, int rule) {
   return rule == 1 ? armijo_step(c, amax) : quartic_argmin(c, amax);
+}
+
+// line_step evaluated by thread 0 and broadcast through the shared *slot: the
+// bisection is a few hundred dependent FP64 operations, which every warp of
+// the block would otherwise repeat on the FP64 pipe.  Block-uniform call.
+inline __device__ double block_line_step(const double* c, double amax, int rule, double* slot) {
+  __syncthreads();
+  if (threadIdx.x == 0) *slot = line_step(c, amax, rule);
+  __syncthreads();
+  return *slot;
 }
 
 // ------------------------------------------------- SplitMix64 normal probes
