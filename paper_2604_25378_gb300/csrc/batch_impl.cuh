@@ -463,6 +463,19 @@ void launch_tc2(int bn, dim3 grid, cudaStream_t st, const CUtensorMap& ta, const
 }
 
 // Split-K tensor-core product with FP32 partials for N columns (N tile 16, 64 or 256).
+template <class Epi>
+void launch_partials(int bn, dim3 grid, cudaStream_t st, const CUtensorMap& ta, const CUtensorMap& tb, int M, int N,
+                     int K, int ktps, const Epi& epi, int* err) {
+  if (bn == 16)
+    k_gemm_tc<16, 8, Epi><<<grid, 128, tc_smem_bytes<16, 8>(), st>>>(ta, tb, M, N, K, ktps, epi, err, nullptr,
+                                                                     nullptr);
+  else if (bn == 64)
+    k_gemm_tc<64, 4, Epi><<<grid, 128, tc_smem_bytes<64, 4>(), st>>>(ta, tb, M, N, K, ktps, epi, err, nullptr,
+                                                                     nullptr);
+  else
+    launch_tc2(bn, grid, st, ta, tb, M, N, K, ktps, epi, err);
+}
+
 mvsk_status tc_partials_n(mvsk_ctx* c, const void* Aop, int M, const void* Bop, int N, long long K, long long ldk,
                           float* part, size_t part_floats, long long ldp, int* splits_out) {
   CUtensorMap ta, tb;
@@ -480,17 +493,19 @@ mvsk_status tc_partials_n(mvsk_ctx* c, const void* Aop, int M, const void* Bop, 
   const int want = pick_splits(mt * nt, nk, c->nsm * tc_ctas_per_sm(bn), tc_wide(bn), smax);
   const int ktps = (nk + want - 1) / want;
   const int splits = (nk + ktps - 1) / ktps;
-  EpiPartT epi{part, ldp, M, N};
   dim3 grid((unsigned)nt, (unsigned)mt, (unsigned)splits);
   TRY(prof_begin(c, 400 + bn, 2.0 * (double)M * (double)N * (double)K));
-  if (bn == 16)
-    k_gemm_tc<16, 8, EpiPartT><<<grid, 128, tc_smem_bytes<16, 8>(), c->stream>>>(ta, tb, M, N, (int)K, ktps, epi,
-                                                                                c->err, nullptr, nullptr);
-  else if (bn == 64)
-    k_gemm_tc<64, 4, EpiPartT><<<grid, 128, tc_smem_bytes<64, 4>(), c->stream>>>(ta, tb, M, N, (int)K, ktps, epi,
-                                                                                c->err, nullptr, nullptr);
-  else
-    launch_tc2(bn, grid, c->stream, ta, tb, M, N, (int)K, ktps, epi, c->err);
+  if ((ldp * 4) % 16 == 0) {  // partials through bulk tensor stores (box of 32 rows x CW columns)
+    const cuuint64_t dims[3] = {(cuuint64_t)M, (cuuint64_t)N, (cuuint64_t)splits};
+    const cuuint64_t strides[2] = {(cuuint64_t)ldp * 4, (cuuint64_t)N * (cuuint64_t)ldp * 4};
+    const cuuint32_t box[3] = {32, (cuuint32_t)(bn < 32 ? bn : 32), 1};
+    EpiPartTma epi;
+    TRY(make_tmap_store(&epi.tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, part, dims, strides, box));
+    launch_partials(bn, grid, c->stream, ta, tb, M, N, (int)K, ktps, epi, c->err);
+  } else {
+    const EpiPartT epi{part, ldp, M, N};
+    launch_partials(bn, grid, c->stream, ta, tb, M, N, (int)K, ktps, epi, c->err);
+  }
   c->launches += 1;
   CU(cudaGetLastError());
   TRY(prof_end(c));
@@ -513,7 +528,16 @@ mvsk_status hvp_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int nc, int* s2) {
                        (unsigned long long)c->ld * 2, kTcBK, kTcBM));
     TRY(make_tmap_bf16(&tb, bb.P16, (unsigned long long)c->ld, (unsigned long long)N, (unsigned long long)c->ld * 2,
                        kTcBK, (unsigned)bn));
-    EpiHvp1 epi{bb.S16T, c->Tp, bb.Hf, (int)c->T, N, nc};
+    // S^T through bulk tensor stores: map {T, N} (rows T <= t < Tp stay zero), box {32, 32}
+    EpiHvp1Tma epi;
+    epi.Hf = bb.Hf;
+    epi.T = (int)c->T;
+    epi.N = N;
+    epi.nc = nc;
+    const cuuint64_t dims[2] = {(cuuint64_t)c->T, (cuuint64_t)N};
+    const cuuint64_t strides[1] = {(cuuint64_t)c->Tp * 2};
+    const cuuint32_t box[2] = {32, 32};
+    TRY(make_tmap_store(&epi.tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, bb.S16T, dims, strides, box));
     TRY(prof_begin(c, 400 + bn, 2.0 * (double)c->T * (double)N * (double)c->ld));
     launch_tc2(bn, dim3((unsigned)nt, (unsigned)mt, 1), c->stream, ta, tb, (int)c->T, N, c->ld, nk, epi, c->err);
     c->launches += 1;

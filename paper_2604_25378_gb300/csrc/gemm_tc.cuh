@@ -16,6 +16,8 @@
 
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace mvsk {
@@ -28,6 +30,34 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
       "[%4];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
+}
+
+// Bulk tensor stores (shared -> global, bulk-group completion).  The
+// coordinates address the tensor map's own dimensions; elements outside its
+// extents are not written.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* tm, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(tm)),
+               "r"(smem_u32(src)), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, const void* src, int x, int y, int z) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(tm)),
+               "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most N bulk groups still reading their shared-memory source
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+// every bulk group complete (writes performed)
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// generic-proxy shared-memory writes of this thread visible to the async proxy
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // Shared-memory matrix descriptor: K-major tile of 128-byte rows written by
@@ -176,6 +206,117 @@ struct EpiHvp1 {
   }
 };
 
+// Epilogues that stage each warp's 32-row x CW-column chunk in shared memory
+// (box layout: column-major, the 32 rows contiguous) and write it with one
+// bulk tensor store, instead of CW row-scattered stores per thread (a store
+// instruction per output line kept a CTA's epilogue at ~10 us).  They define
+// kTma = true, kElem (bytes per element), prepare() (CTA-wide set-up in the
+// idle operand ring; returns whether it used it), stage() and store().
+template <class E, class = void>
+struct EpiIsTma : std::false_type {};
+template <class E>
+struct EpiIsTma<E, std::void_t<decltype(E::kTma)>> : std::bool_constant<E::kTma> {};
+
+// FP32 split-K partials part[(kz*N + n)*ldp + m] through a 3-D tensor map
+// {M (stride 4), N (stride 4 ldp), splits (stride 4 N ldp)}, box {32, CW, 1}.
+struct EpiPartTma {
+  CUtensorMap tm;
+  static constexpr bool kTma = true;
+  static constexpr int kElem = 4;
+  template <int ROWS, int BN>
+  __device__ __forceinline__ bool prepare(float*, size_t, int, int) const {
+    return false;
+  }
+  template <int CW, int BN>
+  __device__ __forceinline__ void stage(const float (&v)[CW], unsigned char* buf, int lane, int, int, int,
+                                        const float*, int, bool) const {
+    float* b = reinterpret_cast<float*>(buf);
+#pragma unroll
+    for (int i = 0; i < CW; ++i) b[i * 32 + lane] = v[i];
+  }
+  __device__ __forceinline__ void store(const unsigned char* buf, int m, int n, int kz) const {
+    tma_store_3d(&tm, buf, m, n, kz);
+  }
+};
+
+// EpiHvp1 through a 2-D tensor map {T (stride 2), N (stride 2 Tp)} of S^T,
+// box {32, CW}; rows T <= t < Tp are outside the map and keep their zeros.
+// prepare() puts in shared memory a column table (offset of column c's
+// weights, -1 past N) and the CTA's weight block h_q[m0 .. m0 + ROWS) for the
+// instances q of its columns, read with batches of independent coalesced
+// loads; stage() then reads two shared words per column, without branches.
+// When the block does not fit, stage() loads each instance's weight once per
+// chunk from global memory.
+struct EpiHvp1Tma {
+  CUtensorMap tm;
+  const float* Hf;
+  int T, N, nc;
+  static constexpr bool kTma = true;
+  static constexpr int kElem = 2;
+  template <int ROWS, int BN>
+  __device__ __forceinline__ bool prepare(float* ext, size_t cap_floats, int m0, int n0) const {
+    const int q0 = n0 / nc, nq = ((n0 + BN < N ? n0 + BN : N) - 1) / nc - q0 + 1;
+    if ((size_t)nq * ROWS + BN > cap_floats) return false;
+    int* qtab = reinterpret_cast<int*>(ext);
+    float* hs = ext + BN;
+    for (int c = threadIdx.x; c < BN; c += blockDim.x)
+      qtab[c] = n0 + c < N ? ((n0 + c) / nc - q0) * ROWS : -1;
+    const float* __restrict__ h = Hf;
+    const int tot = nq * ROWS;
+    constexpr int kB = 16;
+#pragma unroll 1
+    for (int base = threadIdx.x; base < tot; base += kB * 128) {
+      float r[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int idx = base + u * 128, qi = idx / ROWS, m = m0 + (idx - qi * ROWS);
+        r[u] = (idx < tot && m < T) ? __ldg(h + (size_t)(q0 + qi) * T + m) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kB; ++u)
+        if (base + u * 128 < tot) hs[base + u * 128] = r[u];
+    }
+    return true;
+  }
+  template <int CW, int BN>
+  __device__ __forceinline__ void stage(const float (&v)[CW], unsigned char* buf, int lane, int m, int n0, int c0,
+                                        const float* ext, int r, bool use) const {
+    // every weight of the chunk is read before the first staging store: the
+    // stores could alias the weight reads, so interleaving them would chain
+    // each read behind the previous store (~15 us per launch)
+    float w[CW];
+    if (use) {
+      const int* __restrict__ qtab = reinterpret_cast<const int*>(ext) + c0;
+      const float* __restrict__ hs = ext + BN + r;
+#pragma unroll
+      for (int i = 0; i < CW; ++i) {
+        const int o = qtab[i];
+        w[i] = o >= 0 ? hs[o] : 0.f;
+      }
+    } else {
+      const float* __restrict__ h = Hf;
+      const bool row = m < T;
+      int q = n0 / nc, j = n0 - q * nc;
+      float hq = (row && n0 < N) ? __ldg(h + (size_t)q * T + m) : 0.f;
+#pragma unroll
+      for (int i = 0; i < CW; ++i) {
+        w[i] = hq;
+        if (++j == nc) {
+          j = 0;
+          ++q;
+          if (i + 1 < CW) hq = (row && n0 + i + 1 < N) ? __ldg(h + (size_t)q * T + m) : 0.f;
+        }
+      }
+    }
+    __nv_bfloat16* b = reinterpret_cast<__nv_bfloat16*>(buf);
+#pragma unroll
+    for (int i = 0; i < CW; ++i) b[i * 32 + lane] = __float2bfloat16(w[i] * v[i]);
+  }
+  __device__ __forceinline__ void store(const unsigned char* buf, int m, int n, int) const {
+    tma_store_2d(&tm, buf, m, n);
+  }
+};
+
 // Split-K: CTA (x, y, z) computes output tile (n0 = x*BN, m0 = y*128*MT) over the
 // k-tiles [z*ktps, min(nk, (z+1)*ktps)) and hands the epilogue its z.  MT = 2
 // stacks two 128-row subtiles that share each B tile (accumulators at TMEM
@@ -183,8 +324,8 @@ struct EpiHvp1 {
 template <int BN, int STAGES, class Epi, int MT = 1>
 __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
-                                                    int ktps, Epi epi, int* err, const int* skip,
-                                                    const int* live) {
+                                                    int ktps, const __grid_constant__ Epi epi, int* err,
+                                                    const int* skip, const int* live) {
   static_assert(BN == 16 || BN == 32 || BN == 64 || BN == 128 || BN == 192 || BN == 256, "unsupported N tile");
   static_assert(MT == 1 || (MT == 2 && BN >= 32), "two subtiles need BN >= 32");
   constexpr int kTcStages = STAGES;
@@ -277,7 +418,47 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
     atomicOr(err, kErrWaitTimeout);
   }
   tc_fence_after();
-  if (ok && !s_abort && nk > 0) {
+  if constexpr (EpiIsTma<Epi>::value) {
+    // staging in the operand ring, idle once every MMA has completed: kNBuf
+    // buffers per warp, reused after their store has read them; the rest of
+    // the ring is the epilogue's prepare() area.
+    constexpr int kSB = 32 * CW * Epi::kElem, kNBuf = 4;
+    constexpr size_t kRing = (size_t)kTcStages * (ABYTES + BBYTES), kStg = (size_t)4 * kNBuf * kSB;
+    static_assert(kStg <= kRing, "staging exceeds the operand ring");
+    if (__syncthreads_and(ok && !s_abort && nk > 0)) {
+      float* ext = reinterpret_cast<float*>(sm + kStg);
+      const bool use = epi.template prepare<MT * kTcBM, BN>(ext, (kRing - kStg) / 4, m0, n0);
+      __syncthreads();
+      unsigned char* stg = sm + (size_t)warp * kNBuf * kSB;
+      int nb = 0;
+#pragma unroll 1
+      for (int mt = 0; mt < MT; ++mt) {
+        const int mrow = m0 + mt * kTcBM + warp * 32;
+#pragma unroll 1
+        for (int cc = 0; cc < BN / CW; ++cc) {
+          const int nn = n0 + cc * CW;
+          if (mrow >= M || nn >= N) continue;  // warp-uniform: nothing of this chunk is in the output
+          float v[CW];
+          tmem_ld<CW>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * (BN < 32 ? 32 : BN) + cc * CW), v);
+          unsigned char* buf = stg + (size_t)(nb % kNBuf) * kSB;
+          if (nb >= kNBuf) {
+            if (lane == 0) bulk_wait_read<kNBuf - 1>();
+            __syncwarp();
+          }
+          epi.template stage<CW, BN>(v, buf, lane, mrow + lane, nn, cc * CW, ext, mt * kTcBM + warp * 32 + lane, use);
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            epi.store(buf, mrow, nn, (int)blockIdx.z);
+            bulk_commit();
+          }
+          ++nb;
+        }
+      }
+      if (lane == 0) bulk_wait_all();
+      __syncwarp();
+    }
+  } else if (ok && !s_abort && nk > 0) {
 #pragma unroll 1
     for (int mt = 0; mt < MT; ++mt) {
       const int m = m0 + mt * kTcBM + warp * 32 + lane;

@@ -523,7 +523,17 @@ mvsk_status init_kernel_attributes() {
   MVSK_TC2_ATTR(128, 4, EpiPartT);
   MVSK_TC2_ATTR(192, 4, EpiPartT);
   MVSK_TC2_ATTR(256, 3, EpiPartT);
+  MVSK_TC2_ATTR(128, 4, EpiHvp1Tma);
+  MVSK_TC2_ATTR(192, 4, EpiHvp1Tma);
+  MVSK_TC2_ATTR(256, 3, EpiHvp1Tma);
+  MVSK_TC2_ATTR(128, 4, EpiPartTma);
+  MVSK_TC2_ATTR(192, 4, EpiPartTma);
+  MVSK_TC2_ATTR(256, 3, EpiPartTma);
 #undef MVSK_TC2_ATTR
+  CU(cudaFuncSetAttribute(k_gemm_tc<16, 8, EpiPartTma>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)tc_smem_bytes<16, 8>()));
+  CU(cudaFuncSetAttribute(k_gemm_tc<64, 4, EpiPartTma>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)tc_smem_bytes<64, 4>()));
   CU(cudaFuncSetAttribute(k_oz_gemm<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes(16)));
   CU(cudaFuncSetAttribute(k_oz_gemm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes(32)));
   CU(cudaFuncSetAttribute(k_oz_gemm<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes(48)));
@@ -670,6 +680,23 @@ mvsk_status make_tmap_bf16(CUtensorMap* tm, const void* base, unsigned long long
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(MVSK_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return MVSK_OK;
+}
+
+// Tensor map for the bulk tensor stores of the GEMM epilogues (no swizzle):
+// rank 2 or 3, dims[0] innermost, strides in bytes for dims 1.., box in elements.
+mvsk_status make_tmap_store(CUtensorMap* tm, CUtensorMapDataType dt, int rank, const void* base,
+                            const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box) {
+  auto enc = tmap_encoder();
+  if (enc == nullptr) return fail(MVSK_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0) return fail(MVSK_EINVAL, "tensor map base not 16-byte aligned");
+  for (int i = 0; i + 1 < rank; ++i)
+    if ((strides[i] & 15) != 0) return fail(MVSK_EINVAL, "tensor map stride not a multiple of 16 bytes");
+  cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = enc(tm, dt, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(MVSK_ECUDA, "cuTensorMapEncodeTiled (store) failed (%d)", (int)r);
   return MVSK_OK;
 }
 
