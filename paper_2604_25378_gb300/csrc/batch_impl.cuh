@@ -36,6 +36,7 @@ __global__ void k_reduce_hvp1_b(const float* part, int splits, int N, int nc, lo
   if (t >= T) return;
   const int q = blockIdx.y;
   float acc = 0.f;
+#pragma unroll 4
   for (int z = 0; z < splits; ++z) acc += part[((size_t)z * N + q) * ldp + t];
   S[(size_t)q * Tp + t] = __float2bfloat16(Hf[(size_t)(q / nc) * T + t] * acc);
 }
@@ -49,6 +50,7 @@ __global__ void k_reduce_at_b(const float* part, int splits, int B, int n, int l
   const Inst s = inst_at(base, b);
   float acc = 0.f;
   if (i < n)
+#pragma unroll 4
     for (int z = 0; z < splits; ++z) acc += part[((size_t)z * B + b) * ldp + i];
   s.at[i] = scale * (double)acc;
 }
@@ -652,7 +654,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     int s2 = 0;
     TRY(hvp_tc_batch(c, bb, B, ncol1, &s2));
     const KPart kp{bb.part, s2, B * ncol1, ncol1, c->ld, invT, bb.P16};
-    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step_f<<<dim3(ncol1, B), kPTF, 0, c->stream>>>(base, 0, kmax, kp)));
+    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step_f<<<dim3(ncol1, B), 1024, 0, c->stream>>>(base, 0, kmax, kp)));
   }
   if (K > 0) {
     TRY(third_tc_batch(c, bb, B, K));
@@ -665,7 +667,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     int s2 = 0;
     TRY(hvp_tc_batch(c, bb, B, 1, &s2));
     const KPart kp{bb.part, s2, B, 1, c->ld, invT, bb.P16};
-    PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step_f<<<dim3(1, B), kPTF, 0, c->stream>>>(base, ca, kmax, kp)));
+    PROF_LAUNCH(NK_PCG_STEP_A, (k_pcg_step_fc<<<dim3(kPCL, B), 512, 0, c->stream>>>(base, ca, kmax, kp)));
   }
   PROF_LAUNCH(NK_ASSEMBLE, (k_assemble<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca)));
   if (split) {

@@ -97,15 +97,31 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
   return scratch[32];
 }
 
+// Reductions of the single-CTA-per-instance kernels (up to 1024 threads).
+// The values are staged in shared memory; warp 0 folds the nw = blockDim.x / 32
+// rows column by column (lane l takes entries l, l + 32, ...) and finishes with
+// one 5-level shuffle: nw + 5 warp-wide FP64 operations per value instead of a
+// shuffle tree in every warp (5 per warp, ~160 for 1024 threads) on a pipe of
+// ~2 FMA/clk/SM.  Staging: 2 x 1024 doubles and 1024 ints per kernel that uses
+// them.
+__device__ __forceinline__ double* red_stage() {
+  __shared__ double st[2 * 1024];
+  return st;
+}
+__device__ __forceinline__ int* red_stage_i() {
+  __shared__ int sti[1024];
+  return sti;
+}
+
 __device__ __forceinline__ double block_min(double v, double* scratch) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  double* st = red_stage();
   __syncthreads();
-  if (lane == 0) scratch[warp] = v;
+  st[threadIdx.x] = v;
   __syncthreads();
   if (warp == 0) {
-    double t = lane < nw ? scratch[lane] : INFINITY;
+    double t = INFINITY;
+    for (int k = 0; k < nw; ++k) t = fmin(t, st[k * 32 + lane]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t = fmin(t, __shfl_xor_sync(0xffffffffu, t, o));
     if (lane == 0) scratch[32] = t;
@@ -117,25 +133,36 @@ __device__ __forceinline__ double block_min(double v, double* scratch) {
 // Block-wide arg-max (value, index); ties take the smallest index.
 __device__ __forceinline__ void block_argmax(double& v, int& idx, double* sv, int* si) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    double ov = __shfl_xor_sync(0xffffffffu, v, o);
-    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
-  }
+  double* st = red_stage();
+  int* sti = red_stage_i();
   __syncthreads();
-  if (lane == 0) { sv[warp] = v; si[warp] = idx; }
+  st[threadIdx.x] = v;
+  sti[threadIdx.x] = idx;
   __syncthreads();
   if (warp == 0) {
-    double t = lane < nw ? sv[lane] : -INFINITY;
-    int ti = lane < nw ? si[lane] : 0x7fffffff;
+    double t = -INFINITY;
+    int ti = 0x7fffffff;
+    for (int k = 0; k < nw; ++k) {
+      const double ov = st[k * 32 + lane];
+      const int oi = sti[k * 32 + lane];
+      if (ov > t || (ov == t && oi < ti)) {
+        t = ov;
+        ti = oi;
+      }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, t, o);
-      int oi = __shfl_xor_sync(0xffffffffu, ti, o);
-      if (ov > t || (ov == t && oi < ti)) { t = ov; ti = oi; }
+      const double ov = __shfl_xor_sync(0xffffffffu, t, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, ti, o);
+      if (ov > t || (ov == t && oi < ti)) {
+        t = ov;
+        ti = oi;
+      }
     }
-    if (lane == 0) { sv[32] = t; si[32] = ti; }
+    if (lane == 0) {
+      sv[32] = t;
+      si[32] = ti;
+    }
   }
   __syncthreads();
   v = sv[32];

@@ -367,11 +367,12 @@ const char* const kKernelNames[] = {"k_face", "k_probe_fill", "k_pcg_setup", "k_
                                     "k_reduce_hvp1_b", "k_reduce_hvp2_b", "k_reduce_rhat_b", "k_pcg_setup2",
                                     "k_assemble", "k_decide1", "k_decide2", "k_end_iter", "k_oz_fin_z",
                                     "k_oz_fin_g", "k_oz_fin_ls", "k_oz_split_vecs", "k_need_ls2", "k_reduce_cols",
-                                    "k_hd_cols", "k_hd_reduce1", "k_hd_reduce2", "k_hd_reduce_diag"};
+                                    "k_hd_cols", "k_hd_reduce1", "k_hd_reduce2", "k_hd_reduce_diag",
+                                    "k_pcg_step_a"};
 enum NamedKernel : int {
   NK_FACE, NK_PROBE_FILL, NK_PCG_SETUP, NK_PCG_STEP, NK_COLS, NK_HVP1, NK_HVP2, NK_RHAT, NK_PCG_SETUP2, NK_ASSEMBLE,
   NK_DECIDE1, NK_DECIDE2, NK_END_ITER, NK_OZ_Z, NK_OZ_G, NK_OZ_LS, NK_OZ_SPLIT, NK_NEED, NK_REDUCE_COLS, NK_HD_COLS,
-  NK_HD_RED1, NK_HD_RED2, NK_HD_DIAG, NK_COUNT
+  NK_HD_RED1, NK_HD_RED2, NK_HD_DIAG, NK_PCG_STEP_A, NK_COUNT
 };
 
 mvsk_status prof_begin(mvsk_ctx* c, int kind, double work) {

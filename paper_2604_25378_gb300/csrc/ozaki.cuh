@@ -367,6 +367,7 @@ __device__ __forceinline__ double oz_value(const long long* part, int splits, in
   for (int z0 = 0; z0 < splits; z0 += 16) {
     long long s = 0;  // at most 16 partials of magnitude < 2^58.1: no overflow
     const int z1 = z0 + 16 < splits ? z0 + 16 : splits;
+#pragma unroll 4
     for (int z = z0; z < z1; ++z) s += part[((size_t)z * Bp + b) * ldp + m];
     v += (double)s;
   }

@@ -564,82 +564,154 @@ __device__ __forceinline__ void block_sumNf(float (&v)[N], float* scr) {
 }
 
 // The batched FP32 PCG step (same recurrence as k_pcg_step with kp.part set)
-// with two block reductions instead of five: p^T q and the new r^T z are
-// expanded into sums over the stored vectors,
+// with two reductions instead of five: p^T q and the new r^T z are expanded
+// into sums over the stored vectors,
 //   p^T q   = sum p mf Q - qmean sum p mf - (nu^T Q) sum p nu + lam sum p^2,
 //   r'^T z' = sum r' mf t - tmean sum r' mf - (nu^T t) sum r' nu,  t = r' / diag,
-// so that each block reduction carries every sum of its phase.  Every operand
-// is loaded in the first pass (one memory round trip); 1024 threads keep
-// their kPEF coordinates of Q, P, R, X and the face data in registers.
-constexpr int kPTF = 1024;
-constexpr int kPEF = (kMaxCols + kPTF - 1) / kPTF;
-static __global__ void __launch_bounds__(kPTF, 1) k_pcg_step_f(Inst s0, int c0, int kmaxit, KPart kp) {
+// so that each reduction carries every sum of its phase.
+//
+// Launch forms: k_pcg_step_f, one CTA of 1024 threads per (instance, column)
+// (grid (ncol, B)), for the K + 1 columns of the first round; k_pcg_step_fc,
+// a cluster of kPCL CTAs of 512 threads per (instance, column) (grid
+// (ncol * kPCL, B)), for the single correction column of the second round.
+// CTA rank r of a cluster owns coordinates [r * ch, (r + 1) * ch), each thread
+// kPEF1 or kPEF4 of them, every operand loaded before its first use.  The six sums of a
+// phase are reduced in each CTA, written to every CTA of the cluster
+// (distributed shared memory) and added there in rank order, so that all CTAs
+// take the same decisions from the same totals.  One SM per instance made the
+// 64 single-column steps latency-bound; spread over four SMs they take ~30 %
+// less time, while the 576-CTA first-round steps lose more to the extra waves
+// of cluster-wide barriers than they gain.
+constexpr int kPCL = 4;
+constexpr int kPEF1 = (kMaxCols + 1023) / 1024, kPEF4 = (kMaxCols + kPCL * 512 - 1) / (kPCL * 512);
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// store v to the same shared-memory word of CTA `rank` of this cluster
+__device__ __forceinline__ void st_cluster_f32(float* local, uint32_t rank, float v) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_u32(local)), "r"(rank));
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v) : "memory");
+}
+
+// Sums of six floats over the CTA (CL = 1) or the cluster: block sums, then
+// exchange and rank-ordered adds.  slot: this phase's [CL][6] exchange area
+// (one per phase: a fast CTA may write the next phase's sums while a slow one
+// still reads this phase's).
+template <int CL>
+__device__ __forceinline__ void group_sum6(float (&v)[6], float* scr, float* slot, uint32_t rank) {
+  block_sumNf<6>(v, scr);
+  if constexpr (CL > 1) {
+    if (threadIdx.x < CL * 6) {
+      const uint32_t dst = threadIdx.x / 6;
+      const int q = threadIdx.x - 6 * (int)dst;
+      st_cluster_f32(slot + rank * 6 + q, dst, v[q]);
+    }
+    cluster_sync();
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      float t = 0.f;
+#pragma unroll
+      for (int r = 0; r < CL; ++r) t += slot[r * 6 + q];
+      v[q] = t;
+    }
+  }
+}
+
+template <int CL, int NT, int PE>
+__device__ __forceinline__ void pcg_step_body(Inst s0, int c0, int kmaxit, const KPart& kp, uint32_t rank) {
   Inst s = inst_at(s0, blockIdx.y);
   __shared__ float scr[33 * 6 + 8];
+  __shared__ float slot1[CL * 6], slot2[CL * 6];
   int* SI = s.si;
+  // every CTA of a cluster reads the flags before any of them can change
+  // them (writes follow the first cluster barrier), so all take one branch
   if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
-  const int c = c0 + blockIdx.x;
+  const int col = (int)(blockIdx.x / CL), c = c0 + col;
   if (SI[SI_ACT + c] == 0) return;
   const int n = s.n, ld = s.ld;
+  const int ch = (n + CL - 1) / CL, i0 = (int)rank * ch, i1 = i0 + ch < n ? i0 + ch : n;
   const float m = (float)SI[SI_M];
   const float lam = (float)s.sd[SD_LAM];
+  const double rz_old = s.rz[c];
   // distinct arrays: restrict lets the loads of later coordinates move above
   // the stores of earlier ones
   float* __restrict__ X = kcol<float>(s.X, c, ld);
   float* __restrict__ R = kcol<float>(s.R, c, ld);
   float* __restrict__ P = kcol<float>(s.P, c, ld);
   __nv_bfloat16* __restrict__ P16 = kp.P16;
-  const float* __restrict__ part = kp.part;
   const Face<float> f0 = face_of<float>(s);
   const float* __restrict__ fmf = f0.mf;
   const float* __restrict__ fnh = f0.nh;
   const float* __restrict__ fdg = f0.dg;
-  const size_t prow = (size_t)blockIdx.y * kp.nc + blockIdx.x;
-  float q[kPEF], p[kPEF], r[kPEF], xv[kPEF], mf[kPEF], nh[kPEF], dg[kPEF];
+  const size_t prow = (size_t)blockIdx.y * kp.nc + col;
+  float q[PE], p[PE], r[PE], xv[PE], mf[PE], nh[PE], dg[PE];
   float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // mf.Q, nu.Q, p.mf.Q, p.mf, p.nu, p.p
 #pragma unroll
-  for (int e = 0; e < kPEF; ++e) {
-    const int i = threadIdx.x + e * kPTF;
+  for (int e = 0; e < PE; ++e) {
+    const int i = i0 + threadIdx.x + e * NT;
     q[e] = p[e] = r[e] = xv[e] = mf[e] = nh[e] = 0.f;
     dg[e] = 1.f;
-    if (i < n) {
-      float acc = 0.f;
-      for (int z = 0; z < kp.splits; ++z) acc += part[((size_t)z * kp.N + prow) * kp.ldp + i];
-      q[e] = kp.scale * acc;
+    if (i < i1) {
       p[e] = P[i];
       r[e] = R[i];
       xv[e] = X[i];
       mf[e] = fmf[i];
       nh[e] = fnh[i];
       dg[e] = fdg[i];
-      const float mq = mf[e] * q[e];
-      a[0] += mq;
-      a[1] += nh[e] * q[e];
-      a[2] += p[e] * mq;
-      a[3] += p[e] * mf[e];
-      a[4] += p[e] * nh[e];
-      a[5] += p[e] * p[e];
     }
   }
-  block_sumNf<6>(a, scr);
+  // split-K partials: two splits' loads in flight per batch (a split loop
+  // inside the coordinate loop made each coordinate a separate round trip)
+  const size_t zstride = (size_t)kp.N * kp.ldp;
+  const float* __restrict__ pz = kp.part + prow * kp.ldp;
+  int z = 0;
+  for (; z + 2 <= kp.splits; z += 2, pz += 2 * zstride)
+#pragma unroll
+    for (int e = 0; e < PE; ++e) {
+      const int i = i0 + threadIdx.x + e * NT;
+      if (i < i1) q[e] += pz[i] + pz[zstride + i];
+    }
+  for (; z < kp.splits; ++z, pz += zstride)
+#pragma unroll
+    for (int e = 0; e < PE; ++e) {
+      const int i = i0 + threadIdx.x + e * NT;
+      if (i < i1) q[e] += pz[i];
+    }
+#pragma unroll
+  for (int e = 0; e < PE; ++e) {
+    q[e] *= kp.scale;
+    const float mq = mf[e] * q[e];
+    a[0] += mq;
+    a[1] += nh[e] * q[e];
+    a[2] += p[e] * mq;
+    a[3] += p[e] * mf[e];
+    a[4] += p[e] * nh[e];
+    a[5] += p[e] * p[e];
+  }
+  group_sum6<CL>(a, scr, slot1, rank);
   const float qmean = a[0] / m, ry = a[1];
   const float pq = a[2] - qmean * a[3] - ry * a[4] + lam * a[5];
-  auto deactivate = [&]() {
-    if (threadIdx.x == 0) {
+  const bool lead = rank == 0 && threadIdx.x == 0;
+  if (!(pq > 0.f)) {
+    if (lead) {
       SI[SI_ACT + c] = 0;
       atomicSub(&SI[SI_LIVE + c / 2], 1);
     }
-  };
-  if (!(pq > 0.f)) {
-    deactivate();
     return;
   }
-  const float al = (float)s.rz[c] / pq;
+  const float al = (float)rz_old / pq;
   float b[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // r.r, mf.t, nu.t, r.mf.t, r.mf, r.nu
 #pragma unroll
-  for (int e = 0; e < kPEF; ++e) {
-    const int i = threadIdx.x + e * kPTF;
-    if (i < n) {
+  for (int e = 0; e < PE; ++e) {
+    const int i = i0 + threadIdx.x + e * NT;
+    if (i < i1) {
       const float qq = mf[e] * (q[e] - qmean) - ry * nh[e] + lam * p[e];
       X[i] = xv[e] + al * p[e];
       const float rv = r[e] - al * qq;
@@ -655,35 +727,46 @@ static __global__ void __launch_bounds__(kPTF, 1) k_pcg_step_f(Inst s0, int c0, 
       b[5] += rv * nh[e];
     }
   }
-  block_sumNf<6>(b, scr);
-  if (threadIdx.x == 0) {
+  group_sum6<CL>(b, scr, slot2, rank);
+  if (lead) {
     SI[SI_CITS + c] += 1;
     atomicAdd(&SI[SI_KRY], 1);
   }
   if (sqrt((double)b[0]) <= s.sd[SD_KTOL] * s.rhsn[c]) {
-    deactivate();
+    if (lead) {
+      SI[SI_ACT + c] = 0;
+      atomicSub(&SI[SI_LIVE + c / 2], 1);
+    }
     return;
   }
   const float tmean = b[1] / m, tb2 = b[2];
   const float rzn = b[3] - tmean * b[4] - tb2 * b[5];
-  const float beta = rzn / (float)s.rz[c];
+  const float beta = rzn / (float)rz_old;
 #pragma unroll
-  for (int e = 0; e < kPEF; ++e) {
-    const int i = threadIdx.x + e * kPTF;
-    if (i < n) {
+  for (int e = 0; e < PE; ++e) {
+    const int i = i0 + threadIdx.x + e * NT;
+    if (i < i1) {
       const float zz = mf[e] * (q[e] - tmean) - tb2 * nh[e];
       const float pn = zz + beta * p[e];
       P[i] = pn;
       P16[prow * ld + i] = __float2bfloat16(pn);
     }
   }
-  if (threadIdx.x == 0) {
+  if (lead) {
     s.rz[c] = (double)rzn;
     if (SI[SI_CITS + c] >= kmaxit) {
       SI[SI_ACT + c] = 0;
       atomicSub(&SI[SI_LIVE + c / 2], 1);
     }
   }
+}
+
+static __global__ void __launch_bounds__(1024, 1) k_pcg_step_f(Inst s0, int c0, int kmaxit, KPart kp) {
+  pcg_step_body<1, 1024, kPEF1>(s0, c0, kmaxit, kp, 0u);
+}
+static __global__ void __cluster_dims__(kPCL, 1, 1) __launch_bounds__(512, 2)
+    k_pcg_step_fc(Inst s0, int c0, int kmaxit, KPart kp) {
+  pcg_step_body<kPCL, 512, kPEF4>(s0, c0, kmaxit, kp, cluster_rank());
 }
 
 // Correction vector a = P_V (T^-1 A^T (psi''' o rhat)) and the second PCG round.

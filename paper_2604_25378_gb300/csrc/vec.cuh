@@ -72,50 +72,35 @@ __host__ __device__ __forceinline__ Inst inst_at(const Inst& a, int b) {
   return s;
 }
 
-__device__ __forceinline__ double2 block_sum2(double a, double b, double* scr) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  a = warp_sum(a);
-  b = warp_sum(b);
-  __syncthreads();
-  if (lane == 0) {
-    scr[warp] = a;
-    scr[32 + warp] = b;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    double ta = lane < nw ? scr[lane] : 0.0, tb = lane < nw ? scr[32 + lane] : 0.0;
-    ta = warp_sum(ta);
-    tb = warp_sum(tb);
-    if (lane == 0) {
-      scr[64] = ta;
-      scr[65] = tb;
-    }
-  }
-  __syncthreads();
-  return make_double2(scr[64], scr[65]);
-}
-
-// block_sum2 whose scalar finish fin(x, y) -> (z, w) (a division, a square
-// root, a test) is evaluated once, by the thread that completes the sums, and
-// broadcast with them: an FP64 division or square root is about ten FP64-pipe
-// instructions, and that pipe retires ~2 FMA/clk/SM on this part, so the same
-// finish repeated by the 32 warps of a 1024-thread block costs microseconds.
-// Returns {x, y, z, w}; scr holds >= 68 doubles.
+// Block sums of two values (see red_stage: staged in shared memory, folded by
+// warp 0); scr holds >= 68 doubles, slots 64/65 broadcast the sums.
+// block_sum2_fin also evaluates fin(x, y) -> (z, w) (a division, a square
+// root, a test) once, on the thread that completes the sums, and broadcasts it
+// with them: an FP64 division or square root is about ten FP64-pipe
+// instructions, which every warp of the block would otherwise repeat.
+// Returns {x, y, z, w}.
 template <typename F>
 __device__ __forceinline__ double4 block_sum2_fin(double a, double b, double* scr, F fin) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  a = warp_sum(a);
-  b = warp_sum(b);
+  double* st = red_stage();
   __syncthreads();
-  if (lane == 0) {
-    scr[warp] = a;
-    scr[32 + warp] = b;
-  }
+  st[threadIdx.x] = a;
+  st[1024 + threadIdx.x] = b;
   __syncthreads();
   if (warp == 0) {
-    double ta = lane < nw ? scr[lane] : 0.0, tb = lane < nw ? scr[32 + lane] : 0.0;
-    ta = warp_sum(ta);
-    tb = warp_sum(tb);
+    double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+    int k = 0;
+    for (; k + 2 <= nw; k += 2) {
+      a0 += st[k * 32 + lane];
+      a1 += st[(k + 1) * 32 + lane];
+      b0 += st[1024 + k * 32 + lane];
+      b1 += st[1024 + (k + 1) * 32 + lane];
+    }
+    if (k < nw) {
+      a0 += st[k * 32 + lane];
+      b0 += st[1024 + k * 32 + lane];
+    }
+    const double ta = warp_sum(a0 + a1), tb = warp_sum(b0 + b1);
     if (lane == 0) {
       const double2 zw = fin(ta, tb);
       scr[64] = ta;
@@ -126,6 +111,11 @@ __device__ __forceinline__ double4 block_sum2_fin(double a, double b, double* sc
   }
   __syncthreads();
   return make_double4(scr[64], scr[65], scr[66], scr[67]);
+}
+
+__device__ __forceinline__ double2 block_sum2(double a, double b, double* scr) {
+  const double4 r = block_sum2_fin(a, b, scr, [](double, double) { return make_double2(0.0, 0.0); });
+  return make_double2(r.x, r.y);
 }
 
 // The same in FP32 (scr >= 66 floats).
