@@ -29,16 +29,41 @@ __global__ void k_cols_bf16_b(Inst base, int nc, int c0, int interleave, __nv_bf
 }
 
 // S^T[q][t] = bf16(h_b[t] * sum_z part[z][q][t]), b = q / nc, with
-// h_b = psi''_b(z_b) in FP32 (k_hd_reduce1).  Grid (T/256, N).
+// h_b = psi''_b(z_b) in FP32 (k_hd_reduce1).  Grid (ceil(T / 1024), N): four
+// consecutive rows per thread, with 16-byte loads and one 8-byte store when
+// T is a multiple of 4 (rows then start 16-byte aligned; Tp is a multiple of 8).
 __global__ void k_reduce_hvp1_b(const float* part, int splits, int N, int nc, long long T, long long ldp,
                                 const float* Hf, __nv_bfloat16* S, long long Tp) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= T) return;
+  const long long t0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (t0 >= T) return;
   const int q = blockIdx.y;
-  float acc = 0.f;
+  const float* h = Hf + (size_t)(q / nc) * T;
+  __nv_bfloat16* out = S + (size_t)q * Tp;
+  if ((T & 3) == 0 && (ldp & 3) == 0) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
-  for (int z = 0; z < splits; ++z) acc += part[((size_t)z * N + q) * ldp + t];
-  S[(size_t)q * Tp + t] = __float2bfloat16(Hf[(size_t)(q / nc) * T + t] * acc);
+    for (int z = 0; z < splits; ++z) {
+      const float4 v = *reinterpret_cast<const float4*>(part + ((size_t)z * N + q) * ldp + t0);
+      acc.x += v.x;
+      acc.y += v.y;
+      acc.z += v.z;
+      acc.w += v.w;
+    }
+    const float4 hv = *reinterpret_cast<const float4*>(h + t0);
+    __nv_bfloat162 lo = __floats2bfloat162_rn(hv.x * acc.x, hv.y * acc.y);
+    __nv_bfloat162 hi = __floats2bfloat162_rn(hv.z * acc.z, hv.w * acc.w);
+    uint2 pk;
+    pk.x = *reinterpret_cast<uint32_t*>(&lo);
+    pk.y = *reinterpret_cast<uint32_t*>(&hi);
+    *reinterpret_cast<uint2*>(out + t0) = pk;
+    return;
+  }
+  for (long long t = t0; t < t0 + 4 && t < T; ++t) {
+    float acc = 0.f;
+#pragma unroll 4
+    for (int z = 0; z < splits; ++z) acc += part[((size_t)z * N + q) * ldp + t];
+    out[t] = __float2bfloat16(h[t] * acc);
+  }
 }
 
 // at_b = T^-1 sum_z part[z][b][i] (FP64 output: the back-projected correction).
@@ -521,7 +546,7 @@ mvsk_status tc_partials_n(mvsk_ctx* c, const void* Aop, int M, const void* Bop, 
 // epilogue when it needs no split-K.  P16 holds the BF16 columns already.
 mvsk_status hvp_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int nc, int* s2) {
   const int N = B * nc;
-  const unsigned gt = (unsigned)((c->T + 255) / 256);
+  const unsigned gt4 = (unsigned)((c->T + 1023) / 1024);
   const int bn = tc_bn(N), mt = (int)((c->T + 2 * kTcBM - 1) / (2 * kTcBM)), nt = (N + bn - 1) / bn;
   const int nk = (int)((c->ld + kTcBK - 1) / kTcBK);
   if (tc_wide(bn) && 2 * mt * nt >= c->nsm) {  // enough work without split-K: fuse the weighting
@@ -548,7 +573,7 @@ mvsk_status hvp_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int nc, int* s2) {
   } else {
     int s1 = 0;
     TRY(tc_partials_n(c, c->Alo, (int)c->T, bb.P16, N, c->ld, c->ld, bb.part, bb.part_floats, c->T, &s1));
-    PROF_LAUNCH(NK_HVP1, (k_reduce_hvp1_b<<<dim3(gt, N), 256, 0, c->stream>>>(bb.part, s1, N, nc, c->T, c->T, bb.Hf,
+    PROF_LAUNCH(NK_HVP1, (k_reduce_hvp1_b<<<dim3(gt4, N), 256, 0, c->stream>>>(bb.part, s1, N, nc, c->T, c->T, bb.Hf,
                                                                                bb.S16T, c->Tp)));
   }
   return tc_partials_n(c, c->A16T, c->n, bb.S16T, N, c->Tp, c->Tp, bb.part, bb.part_floats, c->ld, s2);
