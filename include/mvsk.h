@@ -246,7 +246,11 @@ mvsk_status mvsk_quartic_argmin(mvsk_ctx* ctx, const double coef[5], double amax
  * captured CUDA graphs as event nodes, read after each replay); (ctx, 0) stops.
  * mvsk_profile_only(ctx, prefix) restricts the brackets to kinds whose label
  * starts with `prefix` (NULL: all kinds), which keeps the event overhead of a
- * timed run to the kernel of interest.
+ * timed run to the kernel of interest.  mvsk_profile_stride(ctx, k) (k >= 1,
+ * default 1; reset by mvsk_profile_enable) brackets only every k-th launch of
+ * the selected kinds, counted in issue order (inside a captured graph, at
+ * capture): an event node between two kernels costs the graph part of their
+ * overlap, so a timed run samples its kernel.  EINVAL for k < 1.
  * mvsk_profile_read fills up to `max` entries, one per kind: its label
  * (streaming pass, tensor-core product, split FP64 product or named kernel),
  * launches, summed device time (ms) and the average algorithmic work per
@@ -264,6 +268,7 @@ typedef struct {
 
 mvsk_status mvsk_profile_enable(mvsk_ctx* ctx, int32_t on);
 mvsk_status mvsk_profile_only(mvsk_ctx* ctx, const char* prefix);
+mvsk_status mvsk_profile_stride(mvsk_ctx* ctx, int32_t k);
 mvsk_status mvsk_profile_read(mvsk_ctx* ctx, mvsk_prof_entry* out, int32_t max, int32_t* count,
                               int64_t* kernel_launches);
 

@@ -77,6 +77,7 @@ _SIGS = {
                                          _P, _P]),
     "mvsk_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "mvsk_profile_only": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "mvsk_profile_stride": (ctypes.c_int, [_P, ctypes.c_int32]),
     "mvsk_profile_read": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
     "mvsk_last_error": (ctypes.c_char_p, [_P]),
     "mvsk_destroy": (None, [_P]),
@@ -269,6 +270,10 @@ class MVSK:
     def profile_only(self, prefix=None):
         """Record only kinds whose label starts with `prefix` (None: all)."""
         self._check(self._lib.mvsk_profile_only(self._h, None if prefix is None else prefix.encode()))
+
+    def profile_stride(self, k: int = 1):
+        """Bracket only every k-th launch of the selected kinds (k >= 1)."""
+        self._check(self._lib.mvsk_profile_stride(self._h, int(k)))
 
     def profile_read(self):
         """({kind: {launches, total_ms, bytes_per_launch}}, kernel launches since enabling)."""

@@ -138,6 +138,8 @@ struct mvsk_ctx {
   std::vector<double> ev_work;                   // work of each recorded pair
   std::vector<char> prof_sel;                    // kinds recorded (mvsk_profile_only); empty = all
   bool prof_open = false;                        // a begun pair awaits its end event
+  int prof_stride = 1;                           // bracket every k-th selected launch (mvsk_profile_stride)
+  long long prof_count = 0;                      // selected launches seen since enabling
 };
 
 namespace {
@@ -377,6 +379,7 @@ enum NamedKernel : int {
 
 mvsk_status prof_begin(mvsk_ctx* c, int kind, double work) {
   if (!c->prof_on || (!c->prof_sel.empty() && !c->prof_sel[kind])) return MVSK_OK;
+  if (c->prof_count++ % c->prof_stride != 0) return MVSK_OK;
   c->prof_open = true;
   if (c->prof_n.empty()) {
     c->prof_n.assign(kProfKinds, 0);
@@ -1642,11 +1645,20 @@ mvsk_status mvsk_profile_only(mvsk_ctx* c, const char* prefix) {
   return MVSK_OK;
 }
 
+mvsk_status mvsk_profile_stride(mvsk_ctx* c, int32_t k) {
+  if (c == nullptr) return fail(MVSK_EINVAL, "null context");
+  if (k < 1) return fail(MVSK_EINVAL, "profile stride must be >= 1 (got %d)", (int)k);
+  c->prof_stride = k;
+  c->prof_count = 0;
+  return MVSK_OK;
+}
+
 mvsk_status mvsk_profile_enable(mvsk_ctx* c, int32_t on) {
   if (c == nullptr) return fail(MVSK_EINVAL, "null context");
   CU(cudaStreamSynchronize(c->stream));
   c->prof_on = on != 0;
   if (on) {
+    c->prof_count = 0;
     c->ev_used = 0;
     c->ev_kind.clear();
     c->ev_work.clear();
