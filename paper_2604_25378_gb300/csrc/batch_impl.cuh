@@ -15,17 +15,23 @@
 // Batches keep their Krylov vectors in FP32 (see the PCG kernels), so these
 // kernels use no FP64 arithmetic per element.
 // dst[(b*nc + j)*ld + i] = bf16(col_j of instance b): PCG column c0 + j, or the
-// interleaved (X_{1+k}, B_{1+k}) pairs when interleave != 0.  Grid (ld/256, B*nc).
+// interleaved (X_{1+k}, B_{1+k}) pairs when interleave != 0.  Grid
+// (ld/1024, B*nc): four coordinates per thread (ld is a multiple of 64, so the
+// 16-byte loads and 8-byte stores are aligned).
 __global__ void k_cols_bf16_b(Inst base, int nc, int c0, int interleave, __nv_bfloat16* dst) {
   const int ld = base.ld;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (i >= ld) return;
   const int q = blockIdx.y, b = q / nc, j = q % nc;
   const Inst s = inst_at(base, b);
-  float v;
-  if (interleave) v = (j & 1) ? kcol<float>(s.Bv, 1 + (j >> 1), ld)[i] : kcol<float>(s.X, 1 + (j >> 1), ld)[i];
-  else v = kcol<float>(s.P, c0 + j, ld)[i];
-  dst[(size_t)q * ld + i] = __float2bfloat16(v);
+  const float* col = interleave ? ((j & 1) ? kcol<float>(s.Bv, 1 + (j >> 1), ld) : kcol<float>(s.X, 1 + (j >> 1), ld))
+                                : kcol<float>(s.P, c0 + j, ld);
+  const float4 v = *reinterpret_cast<const float4*>(col + i);
+  __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+  uint2 pk;
+  pk.x = *reinterpret_cast<uint32_t*>(&lo);
+  pk.y = *reinterpret_cast<uint32_t*>(&hi);
+  *reinterpret_cast<uint2*>(dst + (size_t)q * ld + i) = pk;
 }
 
 // S^T[q][t] = bf16(h_b[t] * sum_z part[z][q][t]), b = q / nc, with
@@ -268,20 +274,23 @@ __global__ void __launch_bounds__(256) k_hd_reduce1(const float* part, int split
   const int b = blockIdx.y;
   Inst s = inst_at(base, b);
   if (s.si[SI_SKIPDIR] != 0) return;
-  const Psi psi{s.sd[SD_C2], s.sd[SD_C3], s.sd[SD_C4]};
+  // psi'' in FP32 (its consumers are FP32 and BF16); FP64 only for the sums
+  const float c2 = (float)s.sd[SD_C2], c3 = (float)s.sd[SD_C3], c4 = (float)s.sd[SD_C4];
   double a0 = 0.0, a1 = 0.0;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (long long)gridDim.x * blockDim.x) {
     float u = 0.f, v = 0.f;
+#pragma unroll 4
     for (int z = 0; z < splits; ++z) {
       u += part[((size_t)z * N + 2 * b) * ldp + t];
       v += part[((size_t)z * N + 2 * b + 1) * ldp + t];
     }
-    const double h = psi.d2(s.z[t]);
-    S[(size_t)b * Tp + t] = __float2bfloat16((float)(h * (double)u));
-    H[(size_t)b * Tp + t] = __float2bfloat16((float)h);
-    Hf[(size_t)b * T + t] = (float)h;
-    a0 += h * (double)u * (double)u;
-    a1 += h * (double)v * (double)v;
+    const float zt = (float)s.z[t];
+    const float h = 2.f * c2 - zt * (6.f * c3 - 12.f * c4 * zt);
+    S[(size_t)b * Tp + t] = __float2bfloat16(h * u);
+    H[(size_t)b * Tp + t] = __float2bfloat16(h);
+    Hf[(size_t)b * T + t] = h;
+    a0 += (double)(h * u * u);
+    a1 += (double)(h * v * v);
   }
   a0 = block_sum(a0, scr);
   a1 = block_sum(a1, scr);
@@ -582,8 +591,8 @@ mvsk_status hvp_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int nc, int* s2) {
 // rhat_b and at_b = T^-1 A^T (psi3_b(z_b) o rhat_b) for every instance.
 mvsk_status third_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int K) {
   const int N = B * 2 * K;
-  const unsigned gl = (unsigned)((c->ld + 255) / 256);
-  PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl, N), 256, 0, c->stream>>>(bb.base, 2 * K, 0, 1, bb.P16)));
+  const unsigned gl = (unsigned)((c->ld + 255) / 256), gl4 = (unsigned)((c->ld + 1023) / 1024);
+  PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl4, N), 256, 0, c->stream>>>(bb.base, 2 * K, 0, 1, bb.P16)));
   int s1 = 0, s2 = 0;
   TRY(tc_partials_n(c, c->Alo, (int)c->T, bb.P16, N, c->ld, c->ld, bb.part, bb.part_floats, c->T, &s1));
   PROF_LAUNCH(NK_RHAT, (k_reduce_rhat_b<<<dim3((unsigned)((c->T + 255) / 256), B), 256, 0, c->stream>>>(bb.part, s1, N, K, c->T, c->T, bb.base, bb.S16T,
@@ -672,9 +681,9 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     PROF_LAUNCH(NK_PROBE_FILL, (k_probe_fill<float><<<dim3((c->ld + 255) / 256, K, B), 256, 0, c->stream>>>(base, K)));
   PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gz, -1)));
   PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup_cols<float><<<dim3(ncol1, B), 512, 0, c->stream>>>(base)));
-  const unsigned gl = (unsigned)((c->ld + 255) / 256);
+  const unsigned gl = (unsigned)((c->ld + 255) / 256), gl4 = (unsigned)((c->ld + 1023) / 1024);
   const float invT = (float)(1.0 / (double)c->T);
-  PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl, B * ncol1), 256, 0, c->stream>>>(base, ncol1, 0, 0, bb.P16)));
+  PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl4, B * ncol1), 256, 0, c->stream>>>(base, ncol1, 0, 0, bb.P16)));
   for (int it = 0; it < kmax; ++it) {
     int s2 = 0;
     TRY(hvp_tc_batch(c, bb, B, ncol1, &s2));
@@ -687,7 +696,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     for (int b = 0; b < B; ++b) CU(cudaMemsetAsync(inst_at(base, b).at, 0, sizeof(double) * c->ld, c->stream));
   }
   PROF_LAUNCH(NK_PCG_SETUP2, (k_pcg_setup2<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca, ca / 2)));
-  PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl, B), 256, 0, c->stream>>>(base, 1, ca, 0, bb.P16)));
+  PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl4, B), 256, 0, c->stream>>>(base, 1, ca, 0, bb.P16)));
   for (int it = 0; it < kmax; ++it) {
     int s2 = 0;
     TRY(hvp_tc_batch(c, bb, B, 1, &s2));

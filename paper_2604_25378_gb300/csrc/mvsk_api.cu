@@ -1406,7 +1406,7 @@ mvsk_status mvsk_set_option(mvsk_ctx* c, const char* key, double v) {
   else if (k == "krylov_tol" && pos(v)) o.krylov_tol = v;
   else if (k == "krylov_maxit" && cnt(v, 1, 10000)) o.krylov_maxit = (int)v;
   else if (k == "reg" && (isnan(v) || (isfinite(v) && v >= 0.0))) o.reg = v;
-  else if (k == "probes" && cnt(v, 0, 16)) o.probes = (int)v;
+  else if (k == "probes" && cnt(v, 0, kMaxProbes)) o.probes = (int)v;
   else if (k == "probe_seed" && cnt(v, 0, 9007199254740992.0)) o.probe_seed = (unsigned long long)v;
   else if (k == "pref_scaling" && cnt(v, 0, 1)) o.pref_scaling = (int)v;
   else if (k == "release_ratio" && pos(v)) o.release_ratio = v;

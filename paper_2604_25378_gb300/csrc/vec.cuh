@@ -9,6 +9,7 @@
 namespace mvsk {
 
 constexpr int kVT = 1024;
+constexpr int kMaxProbes = 16;  // Hutchinson probes per direction (option "probes")
 
 // ---------------------------------------------------------------- state slots
 // Per-instance scalar state (device memory): doubles sd[kSD], ints si[kSI].

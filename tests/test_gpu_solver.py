@@ -226,3 +226,31 @@ def test_batched_more_than_64_instances():
         assert O.kkt_residual(W[b], g, 1e-8) <= 1e-9 * inf_ref.kkt0
         if O.convexity_certificate(c):
             assert np.max(np.abs(W[b] - x_ref)) <= 1e-9, (b, np.max(np.abs(W[b] - x_ref)))
+
+
+def test_profile_stride_samples_launches():
+    """mvsk_profile_stride(k) brackets every k-th launch of the selected kinds:
+    the same batched solve (deterministic; the iteration graph is captured per
+    solve, and the correction-column PCG step runs 15 times in it) profiled
+    with stride 1 and 3 records a third as many launches of that kind, over the
+    same kernel launches; a stride below 1 is EINVAL."""
+    import paper_2604_25378_gb300 as m
+    R = panels.sector_factor_panel(40, 600, 3)
+    lams = np.array([(1, 1, 1, 1), (1, 1, 0.5, 2)], dtype=float)
+    ctx = m.MVSK(R, "bf16")
+    ctx.solve_batch(lams, np.full(2, np.nan), m.PCG, 1e-10)  # buffers built
+    counts = {}
+    for k in (1, 3):
+        ctx.profile_only("k_pcg_step_a")
+        ctx.profile_stride(k)
+        ctx.profile_enable(True)
+        ctx.solve_batch(lams, np.full(2, np.nan), m.PCG, 1e-10)
+        prof, launches = ctx.profile_read()
+        ctx.profile_enable(False)
+        counts[k] = (prof["k_pcg_step_a"]["launches"], launches)
+    ctx.profile_stride(1)
+    ctx.profile_only(None)
+    assert counts[1][1] == counts[3][1] and counts[1][0] >= 15
+    assert counts[3][0] * 3 == counts[1][0], counts
+    with pytest.raises(Exception):
+        ctx.profile_stride(0)
