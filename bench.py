@@ -44,9 +44,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-its", type=int, default=1)
     ap.add_argument("--workload", default="c4",
-                    choices=["c4", "paper-synthetic", "paper-line-search", "paper-conditioning"],
+                    choices=["c4", "paper-synthetic", "paper-line-search", "paper-conditioning", "warm-start"],
                     help="c4: the batched C4 sweep (default); paper-*: the paper's own benchmarks "
-                         "(T=252 synthetic grid, exact vs Armijo step rule, CRRA conditioning sweep)")
+                         "(T=252 synthetic grid, exact vs Armijo step rule, CRRA conditioning sweep); "
+                         "warm-start: the learned warm start (C5 panel), cold vs warm held-out solves")
     return ap.parse_args()
 
 
@@ -480,6 +481,89 @@ def run_paper_conditioning(args, rank, world):
             "levels": out, "paper_reported_median_time_s_and_residual": PAPER_CONDITIONING}
 
 
+def run_warm_start(args, rank, world):
+    """The learned warm start on a C5-style panel (n = 5440, T = 12000, seed
+    100): solver outputs of WS_TRAIN requests train the network (features of
+    the request and the panel statistics -> n w*), then WS_TEST held-out
+    requests are solved through 64 lanes (continuous batching) from 1/n and
+    from the network's projected output; solves/s and mean YAND iterations of
+    both (requests with a target start their calibration from 1/n either way)."""
+    if rank != 0:
+        return None
+    import numpy as np
+    import torch
+
+    import panels
+    import paper_2604_25378_gb300 as m
+    n, T = 5440, 12000
+    R = panels.garch_sector_panel(n, T, 100)
+    ctx = m.MVSK(torch.from_numpy(R).cuda(), args.precision)
+    mu, sg = ctx.column_stats()
+    rng = np.random.default_rng(101)
+    qs_all = np.quantile(R.mean(axis=0), np.linspace(0.40, 0.85, 64))
+
+    def requests(k):
+        lam = np.column_stack([np.ones(k), np.ones(k), rng.choice([0.5, 1.0, 2.0], k) * rng.uniform(0.8, 1.25, k),
+                               rng.choice([0.5, 1.0, 2.0], k) * rng.uniform(0.8, 1.25, k)])
+        tg = np.where(rng.uniform(size=k) < 0.5, np.nan, rng.choice(qs_all, k))
+        return lam, tg
+
+    ctx.set_option("batch_lanes", 64)  # requests queue for 64 lanes (continuous batching)
+
+    def solve(lam, tg, W0=None):
+        out = torch.empty((lam.shape[0], n), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        W, infos = ctx.solve_batch(lam, tg, m.PCG, args.tol, W0=W0, out=out)
+        torch.cuda.synchronize()
+        assert all(i["status"] == "ok" for i in infos), [i["status"] for i in infos]
+        return W, [i["iters"] for i in infos], time.perf_counter() - t0
+
+    lam_tr, tg_tr = requests(WS_TRAIN)
+    Wtr, its_tr, t_data = solve(lam_tr, tg_tr)
+    X_tr = m.MLP.features(mu, sg, lam_tr, tg_tr, WS_SEED)
+    Y_tr = (Wtr * n).float().contiguous()
+    net = m.MLP(d_in=m.MLP_D_IN, d_hidden=512, n_hidden=4, d_out=n, max_batch=WS_TEST, seed=WS_SEED)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = []
+    for ep in range(WS_EPOCHS):
+        perm = torch.randperm(WS_TRAIN, device="cuda")
+        for k in range(WS_TRAIN // 128):
+            idx = perm[k * 128:(k + 1) * 128]
+            losses.append(net.train_step(X_tr[idx].contiguous(), Y_tr[idx].contiguous(),
+                                         1e-3 if ep < WS_EPOCHS * 2 // 3 else 2e-4))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    lam_te, tg_te = requests(WS_TEST)
+    solve(lam_te[:64], tg_te[:64])  # untimed warm-up
+    Wc, its_c, t_cold = solve(lam_te, tg_te)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X_te = m.MLP.features(mu, sg, lam_te, tg_te, WS_SEED)
+    W0 = net.warm_start(X_te, n, 1e-8)
+    torch.cuda.synchronize()
+    t_infer = time.perf_counter() - t0
+    Ww, its_w, t_warm = solve(lam_te, tg_te, W0)
+    dev = float((Ww - Wc).abs().max())
+    return {"metric": "solves/s of held-out requests with the learned warm start (C5 panel, 64 lanes)",
+            "value": WS_TEST / (t_warm + t_infer), "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "bf16+f64", "data": "synthetic",
+            "config": {"workload": "c5_warm_start_n5440_T12000", "n": n, "T": T, "panel_seed": 100,
+                       "train_requests": WS_TRAIN, "test_requests": WS_TEST, "epochs": WS_EPOCHS,
+                       "network": "128 -> 4 x 512 ReLU -> 5440, BF16 tcgen05 GEMMs, Adam", "tol": args.tol},
+            "cold": {"solves_per_s": WS_TEST / t_cold, "mean_iters": float(np.mean(its_c))},
+            "warm": {"solves_per_s": WS_TEST / (t_warm + t_infer), "mean_iters": float(np.mean(its_w)),
+                     "inference_s": t_infer},
+            "train": {"data_solve_s": t_data, "train_s": t_train, "first_loss": losses[0], "last_loss": losses[-1],
+                      "mean_iters_of_data": float(np.mean(its_tr))},
+            "max_abs_w_difference_warm_vs_cold": dev}
+
+
+# Learned warm start workload: requests solved for training data, held out, epochs.
+WS_TRAIN, WS_TEST, WS_EPOCHS, WS_SEED = 768, 256, 200, 31
+
+
 def main():
     args = parse()
     rank, world = dist_init(args.gpus)
@@ -491,6 +575,8 @@ def main():
         line = run_paper_line_search(args, rank, world)
     elif args.workload == "paper-conditioning":
         line = run_paper_conditioning(args, rank, world)
+    elif args.workload == "warm-start":
+        line = run_warm_start(args, rank, world)
     else:
         line = run_ours(args, rank, world)
     if rank == 0 and line is not None:

@@ -118,6 +118,10 @@ mvsk_status mvsk_set_prefs(mvsk_ctx* ctx, const double lambda[4], double target)
  *   captured CUDA graphs), "split_products" (1: in mvsk_solve_batch the FP64
  *   products A x, A^T psi'(z) and A d run as split BF16 tensor-core products
  *   with FP64 accuracy, see mvsk_product; 0: FP64 streaming passes),
+ *   "batch_lanes" (0: mvsk_solve_batch advances all B requests together; L
+ *   with 0 < L < B and split products: L lanes, a lane whose request has
+ *   finished takes the next one, so throughput follows the mean iteration
+ *   count rather than the slowest request of each batch),
  *   "line_search" (0: exact quartic step, Prop. quartic exact line search;
  *   1: Armijo backtracking on the same quartic, the paper's Armijo diagnostic
  *   of Table yand-line-search: the largest alpha_max 2^-j, j < 60, with
@@ -234,6 +238,12 @@ mvsk_status mvsk_oracle_direction(mvsk_ctx* ctx, mvsk_config cfg, const double* 
 
 /* Euclidean projection onto Delta(tau) (App. C.3 projected trial). */
 mvsk_status mvsk_project_slice(mvsk_ctx* ctx, const double* v, double tau, double* out);
+
+/* Column means mu (the centring of mvsk_create) and population standard
+ * deviations sigma_j = sqrt(T^-1 sum_t (R_tj - mu_j)^2) of the panel, n each
+ * (host or device pointers): the panel statistics of the warm-start features
+ * (mvsk_mlp.h). */
+mvsk_status mvsk_column_stats(mvsk_ctx* ctx, double* mu, double* sigma);
 
 /* Exact minimiser of A0 + A1 a + ... + A4 a^4 on [0, amax] by the device
  * routine the solver uses (candidates: 0, amax, real roots of the cubic). */

@@ -16,7 +16,9 @@ import os
 
 import numpy as np
 
-__all__ = ["load", "MVSK", "MvskError", "DIRECT", "PCG", "PREC", "lib_path", "eval_noalloc"]
+__all__ = ["load", "MVSK", "MLP", "MvskError", "DIRECT", "PCG", "PREC", "lib_path", "eval_noalloc", "MLP_D_IN"]
+
+MLP_D_IN = 128  # width of the warm-start request features (include/mvsk_mlp.h)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 lib_path = os.path.join(_HERE, "lib", "libmvsk.so")
@@ -79,6 +81,15 @@ _SIGS = {
     "mvsk_profile_only": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "mvsk_profile_stride": (ctypes.c_int, [_P, ctypes.c_int32]),
     "mvsk_profile_read": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
+    "mvsk_column_stats": (ctypes.c_int, [_P, _P, _P]),
+    "mvsk_mlp_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(_P)]),
+    "mvsk_mlp_destroy": (ctypes.c_int, [_P]),
+    "mvsk_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
+    "mvsk_mlp_train_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_float, _P]),
+    "mvsk_mlp_access": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "mvsk_mlp_features": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, ctypes.c_uint64, _P]),
+    "mvsk_mlp_warm_start": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, _P]),
     "mvsk_last_error": (ctypes.c_char_p, [_P]),
     "mvsk_destroy": (None, [_P]),
 }
@@ -258,6 +269,13 @@ class MVSK:
                                                     out.ctypes.data_as(ctypes.c_void_p)))
         return out
 
+    def column_stats(self):
+        """(mu, sigma): the panel's column means and population standard deviations."""
+        mu = _like(self._ref, self.n)
+        sg = _like(self._ref, self.n)
+        self._check(self._lib.mvsk_column_stats(self._h, _ptr(mu)[0], _ptr(sg)[0]))
+        return mu, sg
+
     def project_slice(self, v, tau=1e-8):
         pv, kv = _ptr(v)
         out = np.empty(self.n)
@@ -293,3 +311,93 @@ class MVSK:
         self._check(self._lib.mvsk_quartic_argmin(self._h, coef.ctypes.data_as(ctypes.c_void_p), float(amax),
                                                   ctypes.byref(a)))
         return a.value
+
+
+def _dptr(t, dtype):
+    """Device pointer of a contiguous CUDA torch tensor of the given dtype."""
+    if not hasattr(t, "data_ptr") or not t.is_cuda or not t.is_contiguous() or str(t.dtype) != dtype:
+        raise TypeError(f"expected a contiguous CUDA tensor of {dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class MLP:
+    """The learned warm start (include/mvsk_mlp.h): d_in -> n_hidden x d_hidden
+    (ReLU) -> d_out, trained by Adam on the mean-squared error.  Data arrays are
+    CUDA torch tensors (features and outputs float32, W0 float64)."""
+
+    def __init__(self, d_in=MLP_D_IN, d_hidden=512, n_hidden=4, d_out=8, max_batch=256, seed=1):
+        self._lib = load()
+        h = _P()
+        st = self._lib.mvsk_mlp_create(int(d_in), int(d_hidden), int(n_hidden), int(d_out), int(max_batch),
+                                       int(seed), ctypes.byref(h))
+        if st != 0:
+            raise MvskError(st, (self._lib.mvsk_last_error(None) or b"").decode())
+        self._h = h
+        self.dims = [int(d_in)] + [int(d_hidden)] * int(n_hidden) + [int(d_out)]
+
+    def _check(self, st):
+        if st != 0:
+            raise MvskError(st, (self._lib.mvsk_last_error(None) or b"").decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mvsk_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, X):
+        import torch
+        B = X.shape[0]
+        Y = torch.empty((B, self.dims[-1]), dtype=torch.float32, device=X.device)
+        self._check(self._lib.mvsk_mlp_forward(self._h, _dptr(X, "torch.float32"), B, _dptr(Y, "torch.float32")))
+        return Y
+
+    def train_step(self, X, Yt, lr):
+        loss = ctypes.c_double()
+        self._check(self._lib.mvsk_mlp_train_step(self._h, _dptr(X, "torch.float32"), _dptr(Yt, "torch.float32"),
+                                                  X.shape[0], float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def _access(self, layer, what, W=None, b=None):
+        pw = None if W is None else W.ctypes.data_as(ctypes.c_void_p)
+        pb = None if b is None else b.ctypes.data_as(ctypes.c_void_p)
+        self._check(self._lib.mvsk_mlp_access(self._h, int(layer), int(what), pw, pb))
+
+    def params(self, layer, grads=False):
+        """(W, b) of a layer (or its last gradients) as float32 numpy arrays."""
+        W = np.empty((self.dims[layer + 1], self.dims[layer]), dtype=np.float32)
+        b = np.empty(self.dims[layer + 1], dtype=np.float32)
+        self._access(layer, 2 if grads else 0, W, b)
+        return W, b
+
+    def set_params(self, layer, W, b):
+        self._access(layer, 1, np.ascontiguousarray(W, dtype=np.float32), np.ascontiguousarray(b, dtype=np.float32))
+
+    @staticmethod
+    def features(mu, sigma, lambdas, targets, seed):
+        """Request features (B x MLP_D_IN float32, CUDA) from the panel statistics
+        (CUDA float64) and the requests' lambda (B x 4) and targets (B)."""
+        import torch
+        lam = torch.as_tensor(np.ascontiguousarray(lambdas, dtype=np.float64).reshape(-1, 4), device=mu.device)
+        tg = torch.as_tensor(np.ascontiguousarray(targets, dtype=np.float64).reshape(-1), device=mu.device)
+        B = lam.shape[0]
+        X = torch.empty((B, MLP_D_IN), dtype=torch.float32, device=mu.device)
+        lib = load()
+        st = lib.mvsk_mlp_features(_dptr(mu, "torch.float64"), _dptr(sigma, "torch.float64"), mu.shape[0], B,
+                                   _dptr(lam, "torch.float64"), _dptr(tg, "torch.float64"), int(seed),
+                                   _dptr(X, "torch.float32"))
+        if st != 0:
+            raise MvskError(st, (lib.mvsk_last_error(None) or b"").decode())
+        return X
+
+    def warm_start(self, X, n, tau=1e-8):
+        import torch
+        W0 = torch.empty((X.shape[0], int(n)), dtype=torch.float64, device=X.device)
+        self._check(self._lib.mvsk_mlp_warm_start(self._h, _dptr(X, "torch.float32"), X.shape[0], int(n), float(tau),
+                                                  _dptr(W0, "torch.float64")))
+        return W0

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libmvsk.so")
-UNITS = ["mvsk_api.cu", "noalloc.cu", "rowpass_f64.cu", "rowpass_f32.cu", "rowpass_bf16.cu"]
+UNITS = ["mvsk_api.cu", "noalloc.cu", "rowpass_f64.cu", "rowpass_f32.cu", "rowpass_bf16.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", CSRC, "-I", INCLUDE]

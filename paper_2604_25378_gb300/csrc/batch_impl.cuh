@@ -796,51 +796,55 @@ mvsk_status kkt0_flush(mvsk_ctx* c, BatchBuf& bb) {
 mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* tg_h, double tol, const double* W0,
                         double* W_out, mvsk_info* infos) {
   BatchBuf& bb = c->batch;
-  TRY(ensure_tc_pcg(c));
-  TRY(batch_alloc(c, bb, B));
-  const auto t0 = std::chrono::steady_clock::now();
   const Options& o = c->opt;
+  // Lanes: instances advanced together by the lockstep graph.  With
+  // batch_lanes = L < B (split products only) the B requests queue for L lanes
+  // and a lane whose request has finished takes the next one (continuous
+  // batching): the graph reads every per-instance parameter on the device.
+  const bool split = o.split_products != 0;
+  const int L = (split && o.batch_lanes > 0 && o.batch_lanes < B) ? o.batch_lanes : B;
+  TRY(ensure_tc_pcg(c));
+  TRY(batch_alloc(c, bb, L));
+  const auto t0 = std::chrono::steady_clock::now();
   const double s_eq = c->s_equal;
   const bool stdz = o.pref_scaling == 1 && s_eq > 0.0 && isfinite(s_eq);
   const double scale = c->mu_absmax, gap_tol = o.cal_rel_tol * scale;
   const size_t ld = (size_t)c->ld;
-  std::vector<InstRun> run((size_t)B);
-  std::vector<std::array<double, 4>> cc((size_t)B);
-  for (int b = 0; b < B; ++b) {
-    InstRun& r = run[(size_t)b];
-    for (int q = 0; q < 4; ++q) {
-      r.lam[q] = lam_h[4 * b + q];
-      r.cc[q] = stdz ? r.lam[q] / pow(s_eq, q + 1) : r.lam[q];
+  // per-request data
+  std::vector<InstRun> req((size_t)B);
+  std::vector<std::array<double, 4>> ccq((size_t)B);
+  for (int q = 0; q < B; ++q) {
+    InstRun& r = req[(size_t)q];
+    for (int k = 0; k < 4; ++k) {
+      r.lam[k] = lam_h[4 * q + k];
+      r.cc[k] = stdz ? r.lam[k] / pow(s_eq, k + 1) : r.lam[k];
     }
-    r.target = tg_h[b];
-    cc[(size_t)b] = r.cc;
+    r.target = tg_h[q];
+    ccq[(size_t)q] = r.cc;
     r.c1_ref = fmax(r.cc[1], 1e-300) * s_eq * s_eq / fmax(scale, 1e-300);
     r.c1_max = 1e6 * r.c1_ref;
   }
+  std::vector<InstRun> run((size_t)L);
+  std::vector<int> lane_req((size_t)L, -1);
+  std::vector<std::array<double, 4>> cc(ccq.begin(), ccq.begin() + L);
   // device buffers for warm starts: instance scratch columns 20 (lo) and 21 (hi)
   auto xlo = [&](int b) { return inst_at(bb.base, b).tmp + (size_t)20 * ld; };
   auto xhi = [&](int b) { return inst_at(bb.base, b).tmp + (size_t)21 * ld; };
-  double* w0buf = nullptr;
+  std::vector<double> hw;  // validated warm starts (host), B x n
   if (W0 != nullptr) {
-    // W0 (B x n, host or device) into each instance's bestx slot first, validated on the host
-    std::vector<double> hw((size_t)B * c->n);
+    hw.resize((size_t)B * c->n);
     CU(cudaMemcpy(hw.data(), W0, sizeof(double) * hw.size(), cudaMemcpyDefault));
-    for (int b = 0; b < B; ++b) {
+    for (int q = 0; q < B; ++q) {
       double sm = 0.0, mn = INFINITY;
       for (int i = 0; i < c->n; ++i) {
-        sm += hw[(size_t)b * c->n + i];
-        mn = fmin(mn, hw[(size_t)b * c->n + i]);
+        sm += hw[(size_t)q * c->n + i];
+        mn = fmin(mn, hw[(size_t)q * c->n + i]);
       }
-      if (!(fabs(sm - 1.0) <= 1e-9) || mn < o.tau * (1.0 - 1e-9)) return fail(MVSK_EINVAL, "W0 row %d not in Delta(tau)", b);
-      CU(cudaMemsetAsync(inst_at(bb.base, b).xbar, 0, sizeof(double) * ld, c->stream));
-      CU(cudaMemcpyAsync(inst_at(bb.base, b).xbar, hw.data() + (size_t)b * c->n, sizeof(double) * c->n,
-                         cudaMemcpyHostToDevice, c->stream));
+      if (!(fabs(sm - 1.0) <= 1e-9) || mn < o.tau * (1.0 - 1e-9)) return fail(MVSK_EINVAL, "W0 row %d not in Delta(tau)", q);
     }
-    TRY(sync(c));
-    w0buf = (double*)1;  // marker: warm starts live in each instance's xbar
   }
-  if (c->opt.split_products != 0)  // digit planes of A are built outside the capture
-    for (int b0 = 0; b0 < B; b0 += kOzMaxB) TRY(oz_prepare(c, oz_bp(B - b0 < kOzMaxB ? B - b0 : kOzMaxB)));
+  if (split)  // digit planes of A are built outside the capture
+    for (int b0 = 0; b0 < L; b0 += kOzMaxB) TRY(oz_prepare(c, oz_bp(L - b0 < kOzMaxB ? L - b0 : kOzMaxB)));
   // graph of one lockstep iteration (c1 is read on the device, so calibration needs no re-capture)
   cudaGraphExec_t gexec = nullptr;
   long long per_graph = 0;
@@ -849,7 +853,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     const long long l0 = c->launches;
     c->ev_graph_begin = c->ev_kind.size();
-    const mvsk_status cs = batch_iteration(c, bb, B, cc);
+    const mvsk_status cs = batch_iteration(c, bb, L, cc);
     c->ev_graph_end = c->ev_kind.size();
     per_graph = c->launches - l0;
     c->launches = l0;
@@ -869,27 +873,47 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       if (e) cudaGraphExecDestroy(e);
     }
   } guard{gexec};
-  // c1-free part of the gradient at 1/n, once per instance (psi_b depends on c2..c4 only)
-  if (c->opt.split_products != 0) {
-    // z0 = A 1/n is shared: one FP64 pass, then psi'_b(z0) for every instance and
-    // one split product A^T W for all of them
+  // c1-free part of the gradient at 1/n, once per request (psi_q depends on c2..c4 only):
+  // in the lanes' G0 when every request has its lane, else per request in bb.Gq
+  double* G0q = bb.G0;
+  if (L < B) {
+    if (bb.qcap < B) {
+      if (bb.Gq != nullptr) cudaFree(bb.Gq);
+      bb.Gq = nullptr;
+      bb.qcap = 0;
+      if (cudaMalloc(&bb.Gq, sizeof(double) * ld * (size_t)B) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MVSK_ENOMEM, "request buffer allocation failed");
+      }
+      bb.qcap = B;
+    }
+    G0q = bb.Gq;
+  }
+  if (split) {
+    // z0 = A 1/n is shared: one FP64 pass, then psi'_q(z0) for the requests of
+    // each group of L and one split product A^T W per 64 of them
     const Inst s0 = inst_at(bb.base, 0);
     k_fill<<<(c->ld + 255) / 256, 256, 0, c->stream>>>(s0.x, c->n, c->ld, 1.0 / c->n);
     TRY(pass_fwd_z(c, s0.x, s0.z));
-    for (int b = 0; b < B; ++b)
-      k_dpsi_into<<<(unsigned)((c->T + 255) / 256), 256, 0, c->stream>>>(s0.z, c->T, cc[(size_t)b][1], cc[(size_t)b][2],
-                                                                     cc[(size_t)b][3], bb.Wt + (size_t)b * c->T);
-    c->launches += 1 + B;
-    CU(cudaGetLastError());
-    for (int b0 = 0; b0 < B; b0 += kOzMaxB) {
-      const int nb = B - b0 < kOzMaxB ? B - b0 : kOzMaxB;
-      int sp = 0;
-      TRY(oz_product(c, 1, bb.Wt + (size_t)b0 * c->T, c->T, nb, oz_bp(nb), nullptr, &sp));
-      k_oz_store<<<dim3((unsigned)((c->n + 255) / 256), (unsigned)nb), 256, 0, c->stream>>>(
-          c->oz.part, sp, oz_bp(nb), c->oz.MpB, c->n, nb, c->oz.eB, c->oz.fB, 1.0 / (double)c->T,
-          bb.G0 + (size_t)b0 * c->ld, c->ld);
-      c->launches += 1;
+    c->launches += 1;
+    for (int q0 = 0; q0 < B; q0 += L) {
+      const int nq = B - q0 < L ? B - q0 : L;
+      for (int j = 0; j < nq; ++j)
+        k_dpsi_into<<<(unsigned)((c->T + 255) / 256), 256, 0, c->stream>>>(
+            s0.z, c->T, ccq[(size_t)(q0 + j)][1], ccq[(size_t)(q0 + j)][2], ccq[(size_t)(q0 + j)][3],
+            bb.Wt + (size_t)j * c->T);
+      c->launches += nq;
       CU(cudaGetLastError());
+      for (int b0 = 0; b0 < nq; b0 += kOzMaxB) {
+        const int nb = nq - b0 < kOzMaxB ? nq - b0 : kOzMaxB;
+        int sp = 0;
+        TRY(oz_product(c, 1, bb.Wt + (size_t)b0 * c->T, c->T, nb, oz_bp(nb), nullptr, &sp));
+        k_oz_store<<<dim3((unsigned)((c->n + 255) / 256), (unsigned)nb), 256, 0, c->stream>>>(
+            c->oz.part, sp, oz_bp(nb), c->oz.MpB, c->n, nb, c->oz.eB, c->oz.fB, 1.0 / (double)c->T,
+            G0q + (size_t)(q0 + b0) * c->ld, c->ld);
+        c->launches += 1;
+        CU(cudaGetLastError());
+      }
     }
   } else {
     for (int b = 0; b < B; ++b) {
@@ -903,45 +927,104 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       c->launches += 1;
     }
   }
-  // start every instance
-  for (int b = 0; b < B; ++b) {
+  // request q into lane b: its state, its G0 and warm start, and the first inner solve
+  int next_req = 0;
+  auto assign = [&](int b) -> mvsk_status {
+    const int q = next_req++;
+    lane_req[(size_t)b] = q;
+    run[(size_t)b] = req[(size_t)q];
     InstRun& r = run[(size_t)b];
-    const double* w0 = w0buf ? inst_at(bb.base, b).xbar : nullptr;
+    const Inst s = inst_at(bb.base, b);
+    if (G0q != bb.G0)
+      CU(cudaMemcpyAsync(bb.G0 + (size_t)b * ld, G0q + (size_t)q * ld, sizeof(double) * ld, cudaMemcpyDeviceToDevice,
+                         c->stream));
+    const double* w0 = nullptr;
+    if (!hw.empty()) {
+      CU(cudaMemsetAsync(s.xbar, 0, sizeof(double) * ld, c->stream));
+      CU(cudaMemcpyAsync(s.xbar, hw.data() + (size_t)q * c->n, sizeof(double) * c->n, cudaMemcpyHostToDevice,
+                         c->stream));
+      w0 = s.xbar;
+    }
     if (isnan(r.target)) {
       r.cal = 0;
-      TRY(batch_start_run(c, bb, b, r, r.cc[0], w0, tol));
-    } else {
-      r.cal = 1;
-      TRY(batch_start_run(c, bb, b, r, 0.0, nullptr, tol));
+      return batch_start_run(c, bb, b, r, r.cc[0], w0, tol);
     }
-  }
+    r.cal = 1;
+    return batch_start_run(c, bb, b, r, 0.0, nullptr, tol);
+  };
+  // results of the request in lane b (at the end of its last inner solve)
+  std::vector<double> hx(ld);
+  mvsk_status first = MVSK_OK;
+  auto emit = [&](int b) -> mvsk_status {
+    InstRun& r = run[(size_t)b];
+    const int q = lane_req[(size_t)b];
+    const Inst s = inst_at(bb.base, b);
+    if (r.final_from_hi) {  // re-evaluate at the bracket end that is returned
+      PassArgs a = pass_args_inst(r.cc.data());
+      double c1 = r.cc[0];
+      CU(cudaMemcpyAsync(s.sd + SD_C1, &c1, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      a.in[0] = s.x;
+      a.rowout = s.z;
+      TRY(run_pass(c, P64, M_VALGRAD, 1, a, nullptr, s.spart));
+      TRY(reduce_cols(c, P64, 1, s.g, c->ld, c->mu, 0.0, nullptr, nullptr, s.sd + SD_C1));
+      k_eval_finish<<<1, kVT, 0, c->stream>>>(s, nullptr, c->grid, s.tmp + (size_t)23 * ld);
+      CU(cudaMemcpyAsync(r.ev, s.tmp + (size_t)23 * ld, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      TRY(sync(c));
+    }
+    CU(cudaMemcpyAsync(W_out + (size_t)q * c->n, s.x, sizeof(double) * c->n, cudaMemcpyDefault, c->stream));
+    if (infos != nullptr) {
+      CU(cudaMemcpyAsync(hx.data(), s.x, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream));
+      double k0 = 0.0;
+      CU(cudaMemcpyAsync(&k0, s.sd + SD_KKT0, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      int cnt[kSI];
+      CU(cudaMemcpyAsync(cnt, s.si, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+      TRY(sync(c));
+      mvsk_info& inf = infos[q];
+      memset(&inf, 0, sizeof(inf));
+      inf.iters = r.iters;
+      inf.restarts = r.restarts;
+      inf.krylov_iters = cnt[SI_KRY];
+      inf.third_calls = cnt[SI_THIRD];
+      inf.evals = r.evals;
+      inf.f = r.ev[0];
+      inf.kkt_residual = r.ev[1];
+      inf.kkt0 = k0;
+      inf.kkt_rel = r.ev[1] / fmax(k0, 1e-300);
+      for (int k = 0; k < 4; ++k) inf.c[k] = r.cc[k];
+      inf.achieved_mean = r.ev[2];
+      inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      inf.status = r.run_status;
+      int fc = 0;
+      for (int i = 0; i < c->n; ++i) fc += (hx[(size_t)i] - o.tau > o.eps_act);
+      inf.free_count = fc;
+    }
+    if (r.run_status != MVSK_OK && first == MVSK_OK) first = (mvsk_status)r.run_status;
+    return MVSK_OK;
+  };
+  // start the first L requests
+  for (int b = 0; b < L; ++b) TRY(assign(b));
   TRY(kkt0_flush(c, bb));
-  std::vector<int> si((size_t)B * kSI);
-  std::vector<double> evh((size_t)B * 4);
-  double* evd = c->vec_scratch + 64;  // not used concurrently with W0 checks (done above)
-  (void)evd;
+  std::vector<int> si((size_t)L * kSI);
+  std::vector<double> evh((size_t)L * 4);
   const double phase_eta[3] = {o.eta, o.restart_eta1, o.restart_eta2};
   const int phase_it[3] = {o.pcg_max_iter, o.restart_iter, o.restart_iter};
   int remaining = B;
-  const int every = 1;  // host checks after every iteration: finished inner solves restart at once
   long long guard_iters = 0;
   while (remaining > 0) {
-    for (int q = 0; q < every; ++q) {
-      CU(cudaGraphLaunch(gexec, c->stream));
-      c->launches += per_graph;
-      if (c->prof_on) {
-        CU(cudaStreamSynchronize(c->stream));
-        TRY(prof_collect(c, c->ev_graph_begin, c->ev_graph_end));
-      }
+    CU(cudaGraphLaunch(gexec, c->stream));
+    c->launches += per_graph;
+    if (c->prof_on) {
+      CU(cudaStreamSynchronize(c->stream));
+      TRY(prof_collect(c, c->ev_graph_begin, c->ev_graph_end));
     }
-    guard_iters += every;
+    guard_iters += 1;
     CU(cudaMemcpyAsync(si.data(), bb.base.si, sizeof(int) * si.size(), cudaMemcpyDeviceToHost, c->stream));
     TRY(sync(c));
-    // finished inner solves: evaluate them together
+    // finished inner solves (host checks after every iteration): evaluate them together
     std::vector<int> fin;
-    for (int b = 0; b < B; ++b) {
+    for (int b = 0; b < L; ++b) {
       InstRun& r = run[(size_t)b];
-      if (r.finished) continue;
+      if (lane_req[(size_t)b] < 0 || r.finished) continue;
       const int done = si[(size_t)b * kSI + SI_DONE];
       if (done == 0) {
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - r.t_start).count();
@@ -989,6 +1072,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       c->launches += 1;
     }
     TRY(sync(c));
+    std::vector<int> freed;
     for (int b : fin) {
       InstRun& r = run[(size_t)b];
       const Inst s = inst_at(bb.base, b);
@@ -1002,6 +1086,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
         }
         r.finished = true;
         remaining -= 1;
+        freed.push_back(b);
         return MVSK_OK;
       };
       auto illinois = [&]() -> mvsk_status {
@@ -1062,55 +1147,17 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
         }
       }
     }
+    // finished requests: results out, next requests in (their lanes idle once the queue is empty)
+    for (int b : freed) {
+      TRY(emit(b));
+      if (next_req < B) {
+        TRY(assign(b));
+      } else {
+        lane_req[(size_t)b] = -1;
+      }
+    }
     TRY(kkt0_flush(c, bb));
     if (guard_iters > 1000000) return fail(MVSK_ECUDA, "batched solve did not terminate");
-  }
-  // results
-  std::vector<double> hx(ld);
-  mvsk_status first = MVSK_OK;
-  for (int b = 0; b < B; ++b) {
-    InstRun& r = run[(size_t)b];
-    const Inst s = inst_at(bb.base, b);
-    if (r.final_from_hi) {  // re-evaluate at the bracket end that is returned
-      PassArgs a = pass_args_inst(r.cc.data());
-      double c1 = r.cc[0];
-      CU(cudaMemcpyAsync(s.sd + SD_C1, &c1, sizeof(double), cudaMemcpyHostToDevice, c->stream));
-      a.in[0] = s.x;
-      a.rowout = s.z;
-      TRY(run_pass(c, P64, M_VALGRAD, 1, a, nullptr, s.spart));
-      TRY(reduce_cols(c, P64, 1, s.g, c->ld, c->mu, 0.0, nullptr, nullptr, s.sd + SD_C1));
-      k_eval_finish<<<1, kVT, 0, c->stream>>>(s, nullptr, c->grid, s.tmp + (size_t)23 * ld);
-      CU(cudaMemcpyAsync(r.ev, s.tmp + (size_t)23 * ld, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      TRY(sync(c));
-    }
-    CU(cudaMemcpyAsync(W_out + (size_t)b * c->n, s.x, sizeof(double) * c->n, cudaMemcpyDefault, c->stream));
-    if (infos != nullptr) {
-      CU(cudaMemcpyAsync(hx.data(), s.x, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream));
-      double k0 = 0.0;
-      CU(cudaMemcpyAsync(&k0, s.sd + SD_KKT0, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      int cnt[kSI];
-      CU(cudaMemcpyAsync(cnt, s.si, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
-      TRY(sync(c));
-      mvsk_info& inf = infos[b];
-      memset(&inf, 0, sizeof(inf));
-      inf.iters = r.iters;
-      inf.restarts = r.restarts;
-      inf.krylov_iters = cnt[SI_KRY];
-      inf.third_calls = cnt[SI_THIRD];
-      inf.evals = r.evals;
-      inf.f = r.ev[0];
-      inf.kkt_residual = r.ev[1];
-      inf.kkt0 = k0;
-      inf.kkt_rel = r.ev[1] / fmax(k0, 1e-300);
-      for (int q = 0; q < 4; ++q) inf.c[q] = r.cc[q];
-      inf.achieved_mean = r.ev[2];
-      inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-      inf.status = r.run_status;
-      int fc = 0;
-      for (int i = 0; i < c->n; ++i) fc += (hx[(size_t)i] - o.tau > o.eps_act);
-      inf.free_count = fc;
-    }
-    if (r.run_status != MVSK_OK && first == MVSK_OK) first = (mvsk_status)r.run_status;
   }
   TRY(sync(c));
   return first;

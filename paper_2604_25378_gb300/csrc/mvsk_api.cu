@@ -33,6 +33,7 @@ struct Options {
   int max_iter = 300, pcg_max_iter = 40, restart_iter = 120, krylov_maxit = 15, probes = 8;
   int stall_window = 10, pref_scaling = 1, oracle_prec = 0, arc_halvings = 40, cal_max_evals = 40, trace = 0;
   int split_products = 1;  // batched solves: FP64 products on the tensor cores (ozaki.cuh)
+  int batch_lanes = 0;     // batched solves: concurrent instances (0: all requests at once)
   int line_search = 0;     // 0 exact quartic step, 1 Armijo backtracking on the quartic
   unsigned long long probe_seed = 0x5EEDull;
 };
@@ -54,6 +55,8 @@ struct BatchBuf {
   std::vector<double> kq_c1;
   void* kq_dev = nullptr;        // device copy: c1 (cap doubles) then indices
   int* need = nullptr;   // any instance needs the second line-search product
+  double* Gq = nullptr;  // G0 of every request when requests queue for fewer lanes (qcap x ld)
+  int qcap = 0;
 };
 
 // Digit planes and buffers of the emulated-FP64 tensor-core products (ozaki.cuh).
@@ -223,6 +226,24 @@ __global__ void k_colmean(const double* R, long long T, int n, int ld, double* m
     tot += s;
   }
   mu[j] = tot / (double)T;
+}
+
+// sigma[j] = sqrt(T^-1 sum_t A[t][j]^2) of the centred panel (population
+// standard deviation of column j), in the order of k_colmean.
+__global__ void k_colstd(const double* A, long long T, int n, int ld, double* sigma) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double tot = 0.0;
+  for (long long t0 = 0; t0 < T; t0 += 256) {
+    double s = 0.0;
+    const long long t1 = t0 + 256 < T ? t0 + 256 : T;
+    for (long long t = t0; t < t1; ++t) {
+      const double a = A[(size_t)t * ld + j];
+      s += a * a;
+    }
+    tot += s;
+  }
+  sigma[j] = sqrt(tot / (double)T);
 }
 
 template <typename TL>
@@ -1417,6 +1438,7 @@ mvsk_status mvsk_set_option(mvsk_ctx* c, const char* key, double v) {
   else if (k == "trace" && cnt(v, 0, 1)) o.trace = (int)v;
   else if (k == "graphs" && cnt(v, 0, 1)) c->use_graphs = v != 0.0;
   else if (k == "split_products" && cnt(v, 0, 1)) o.split_products = (int)v;
+  else if (k == "batch_lanes" && cnt(v, 0, 1000000)) o.batch_lanes = (int)v;
   else if (k == "line_search" && cnt(v, 0, 1)) o.line_search = (int)v;
   else return fail(MVSK_EINVAL, "unknown option or bad value: %s = %g", key, v);
   if (c->prefs_set && k == "pref_scaling") mvsk_set_prefs(c, c->lam, c->target);
@@ -1605,6 +1627,16 @@ mvsk_status mvsk_project_slice(mvsk_ctx* c, const double* v, double tau, double*
   return sync(c);
 }
 
+mvsk_status mvsk_column_stats(mvsk_ctx* c, double* mu, double* sigma) {
+  if (c == nullptr || mu == nullptr || sigma == nullptr) return fail(MVSK_EINVAL, "null argument");
+  Inst& s = c->in;
+  k_colstd<<<(c->n + 255) / 256, 256, 0, c->stream>>>(c->A64, c->T, c->n, c->ld, s.dstep);
+  CU(cudaGetLastError());
+  TRY(download_vec(c, mu, c->mu, c->n));
+  TRY(download_vec(c, sigma, s.dstep, c->n));
+  return sync(c);
+}
+
 mvsk_status mvsk_quartic_argmin(mvsk_ctx* c, const double coef[5], double amax, double* alpha) {
   if (c == nullptr || coef == nullptr || alpha == nullptr) return fail(MVSK_EINVAL, "null argument");
   double* dc = c->vec_scratch + 40;
@@ -1716,6 +1748,7 @@ void mvsk_destroy(mvsk_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void* p : c->batch.mem) cudaFree(p);
+  if (c->batch.Gq != nullptr) cudaFree(c->batch.Gq);
   if (c->own_stream != nullptr) cudaStreamDestroy(c->own_stream);
   delete c;
 }

@@ -1,5 +1,5 @@
 """The C-ABI library builds for sm_103a, loads, and exports every entry point
-that include/mvsk.h declares (no GPU needed: no compute calls here)."""
+that the headers under include/ declare (no GPU needed: no compute calls here)."""
 import ctypes
 import os
 import re
@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    text = open(os.path.join(ROOT, "include", "mvsk.h")).read()
+    inc = os.path.join(ROOT, "include")
+    text = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(mvsk_[a-z_0-9]+)\s*\(", text)))
 
@@ -26,7 +27,9 @@ def test_header_declares_the_boundary():
     syms = declared_symbols()
     for name in ("mvsk_create", "mvsk_set_prefs", "mvsk_solve", "mvsk_eval", "mvsk_solve_batch",
                  "mvsk_oracle_hvp", "mvsk_oracle_third", "mvsk_oracle_gram", "mvsk_oracle_ls",
-                 "mvsk_destroy", "mvsk_last_error"):
+                 "mvsk_destroy", "mvsk_last_error", "mvsk_column_stats", "mvsk_mlp_create", "mvsk_mlp_forward",
+                 "mvsk_mlp_train_step", "mvsk_mlp_access", "mvsk_mlp_features", "mvsk_mlp_warm_start",
+                 "mvsk_mlp_destroy"):
         assert name in syms
 
 

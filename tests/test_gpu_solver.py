@@ -254,3 +254,35 @@ def test_profile_stride_samples_launches():
     assert counts[3][0] * 3 == counts[1][0], counts
     with pytest.raises(Exception):
         ctx.profile_stride(0)
+
+
+def test_batch_lanes_queue_matches_all_at_once():
+    """batch_lanes = 8 for 40 requests (continuous batching: a lane whose
+    request has finished takes the next) gives the requests the same
+    solutions as advancing all 40 together; warm starts at those solutions
+    reach each request in its lane (a few iterations each)."""
+    import paper_2604_25378_gb300 as m
+    R = panels.sector_factor_panel(30, 400, 21)
+    mu, A = O.centre(R)
+    rng = np.random.default_rng(22)
+    k = 40
+    lams = np.column_stack([np.ones(k), np.ones(k), rng.uniform(0.4, 2.5, k), rng.uniform(0.4, 2.5, k)])
+    tg = np.where(rng.uniform(size=k) < 0.3, np.quantile(R.mean(0), 0.7), np.nan)
+    ctx = m.MVSK(R, "bf16")
+    W_all, inf_all = ctx.solve_batch(lams, tg, m.PCG, 1e-10)
+    ctx.set_option("batch_lanes", 8)
+    W_q, inf_q = ctx.solve_batch(lams, tg, m.PCG, 1e-10)
+    assert all(i["status"] == "ok" for i in inf_all + inf_q)
+    for b in range(k):
+        c = np.asarray(inf_q[b]["c"])
+        if O.convexity_certificate(c):
+            assert np.max(np.abs(W_q[b] - W_all[b])) <= 1e-8, (b, np.max(np.abs(W_q[b] - W_all[b])))
+        g = O.gradient(A, mu, c, W_q[b])
+        assert O.kkt_residual(W_q[b], g, 1e-8) <= 1e-9 * inf_q[b]["kkt0"]
+    free = np.isnan(tg)
+    W_w, inf_w = ctx.solve_batch(lams, tg, m.PCG, 1e-10, W0=W_q)
+    its_w = np.array([i["iters"] for i in inf_w])
+    its_c = np.array([i["iters"] for i in inf_q])
+    assert np.all(its_w[free] <= 3), its_w[free]
+    assert np.all(its_w[free] < its_c[free])
+    ctx.set_option("batch_lanes", 0)
