@@ -118,10 +118,12 @@ __global__ void k_reduce_rhat_b(const float* part, int splits, int N, int K, lon
 // partials to spart_b[g * ns + q], the layout the single-CTA kernels reduce.
 
 // z_b = A x_b (Prop. 1, z_t = a_t^T w); W_b = psi'_b(z_b); spart_b[g] = sum psi_b(z_t).
+// Runs only when *needz != 0: otherwise z_b is the cache that k_z_step keeps.
 __global__ void __launch_bounds__(256) k_oz_fin_z(const long long* part, int splits, int Bp, long long ldp,
                                                   const int* em, const int* fb, Inst base, int b0, double* W,
-                                                  long long ldw) {
+                                                  long long ldw, const int* needz) {
   __shared__ double scr[64];
+  if (*needz == 0) return;
   const int bl = blockIdx.y;
   Inst s = inst_at(base, b0 + bl);
   if (s.si[SI_DONE] != 0) return;
@@ -137,6 +139,50 @@ __global__ void __launch_bounds__(256) k_oz_fin_z(const long long* part, int spl
   if (threadIdx.x == 0) s.spart[blockIdx.x] = acc;
 }
 
+// The value terms from the cached z_b (when *needz == 0): W_b = psi'_b(z_b) and
+// spart_b[g] = sum psi_b(z_t) over the rows of CTA g, the layout of k_oz_fin_z.
+// The cache follows every step: A(x + alpha d) = z + alpha A d (proof of
+// Prop. 3), with A d the line-search product of the step (k_z_step); inner
+// solves start from the cached A 1/n or the cached z of their warm start.
+__global__ void __launch_bounds__(256) k_z_fin(Inst base, int b0, double* W, long long ldw, const int* needz) {
+  __shared__ double scr[64];
+  if (*needz != 0) return;
+  const int bl = blockIdx.y;
+  Inst s = inst_at(base, b0 + bl);
+  if (s.si[SI_DONE] != 0) return;
+  const Psi psi{s.sd[SD_C2], s.sd[SD_C3], s.sd[SD_C4]};
+  double acc = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < s.T; t += (long long)gridDim.x * blockDim.x) {
+    const double z = s.z[t];
+    W[(size_t)(b0 + bl) * ldw + t] = psi.d1(z);
+    acc += psi.f(z);
+  }
+  acc = block_sum(acc, scr);
+  if (threadIdx.x == 0) s.spart[blockIdx.x] = acc;
+}
+
+// z_b += alpha_b w_b, w_b = A d_b stored by the line-search finish, for the
+// instances whose step took that direction: phase 1 after k_decide1 (raw or
+// capped step along d), phase 2 after k_decide2 (the segment or face hand-off,
+// SKIPLS == 0).  Coordinates moved onto tau by the step's clamp (within
+// eps_act = 1e-15) are not followed.  Grid (Gz, B).
+__global__ void __launch_bounds__(256) k_z_step(Inst base, const double* wls, int phase) {
+  const int b = blockIdx.y;
+  Inst s = inst_at(base, b);
+  if (s.si[SI_DONE] != 0) return;
+  if (phase == 1) {
+    const int br = s.si[SI_BRANCH];
+    if (br != BR_RAW && br != BR_CAPPED) return;
+  } else if (s.si[SI_SKIPLS] != 0) {
+    return;
+  }
+  const double al = s.sd[SD_ALPHA];
+  if (al == 0.0) return;
+  const double* w = wls + (size_t)b * s.T;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < s.T; t += (long long)gridDim.x * blockDim.x)
+    s.z[t] += al * w[t];
+}
+
 // g_b = -c1_b mu + T^-1 A^T psi'_b(z_b) (Eq. operator-grad), zero padding to ld.
 __global__ void k_oz_fin_g(const long long* part, int splits, int Bp, long long ldp, const int* em, const int* fb,
                            Inst base, int b0) {
@@ -150,8 +196,11 @@ __global__ void k_oz_fin_g(const long long* part, int splits, int Bp, long long 
 }
 
 // The twelve power sums s_rs of (z_t, w_t = a_t^T d) (Prop. quartic line search).
+// w_b[t] (the projected direction) is also stored in wout[(b0 + b) * T + t]
+// for the cache update of z (k_z_step).
 __global__ void __launch_bounds__(256) k_oz_fin_ls(const long long* part, int splits, int Bp, long long ldp,
-                                                   const int* em, const int* fb, Inst base, int b0, int skip_slot) {
+                                                   const int* em, const int* fb, Inst base, int b0, int skip_slot,
+                                                   double* wout) {
   __shared__ double red[12][256];
   const int bl = blockIdx.y;
   Inst s = inst_at(base, b0 + bl);
@@ -161,6 +210,7 @@ __global__ void __launch_bounds__(256) k_oz_fin_ls(const long long* part, int sp
   for (int q = 0; q < 12; ++q) a[q] = 0.0;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < s.T; t += (long long)gridDim.x * blockDim.x) {
     const double zt = s.z[t], w = oz_value(part, splits, Bp, ldp, t, bl, em[t], fb[bl]);
+    wout[(size_t)(b0 + bl) * s.T + t] = w;
     const double z2 = zt * zt, w2 = w * w;
     a[0] += z2;            // s20
     a[1] += z2 * zt;       // s30
@@ -416,6 +466,14 @@ mvsk_status batch_alloc(mvsk_ctx* c, BatchBuf& bb, int B) {
   bb.need = (int*)p;
   TRY(get(sizeof(double) * ld * Bs, &p));
   bb.G0 = (double*)p;
+  TRY(get(sizeof(double) * T * Bs, &p));
+  bb.wls = (double*)p;
+  TRY(get(sizeof(double) * 2 * T * Bs, &p));
+  bb.zsave = (double*)p;
+  TRY(get(sizeof(double) * T, &p));
+  bb.z0 = (double*)p;
+  TRY(get(sizeof(int), &p));
+  bb.needz = (int*)p;
   TRY(get(sizeof(__nv_bfloat16) * (size_t)c->Tp * Bs, &p));
   bb.H16 = (__nv_bfloat16*)p;
   TRY(get(sizeof(float) * T * Bs, &p));
@@ -648,7 +706,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
       int sp = 0;
       TRY(oz_product(c, 0, dvec + (size_t)b0 * base.vs, base.vs, nb, oz_bp(nb), need, &sp));
       PROF_LAUNCH(NK_OZ_LS, (k_oz_fin_ls<<<dim3(Gl, nb), 256, 0, c->stream>>>(oz.part, sp, oz_bp(nb), oz.MpF, oz.eF,
-                                                                             oz.fF, base, b0, skip_slot)));
+                                                                             oz.fF, base, b0, skip_slot, bb.wls)));
     }
     return MVSK_OK;
   };
@@ -656,9 +714,10 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     for (int b0 = 0; b0 < B; b0 += kOzMaxB) {
       const int nb = B - b0 < kOzMaxB ? B - b0 : kOzMaxB, Bp = oz_bp(nb);
       int sp = 0;
-      TRY(oz_product(c, 0, base.x + (size_t)b0 * base.vs, base.vs, nb, Bp, nullptr, &sp));
+      TRY(oz_product(c, 0, base.x + (size_t)b0 * base.vs, base.vs, nb, Bp, bb.needz, &sp));
       PROF_LAUNCH(NK_OZ_Z, (k_oz_fin_z<<<dim3(Gz, nb), 256, 0, c->stream>>>(oz.part, sp, Bp, oz.MpF, oz.eF, oz.fF,
-                                                                           base, b0, bb.Wt, c->T)));
+                                                                           base, b0, bb.Wt, c->T, bb.needz)));
+      PROF_LAUNCH(NK_OZ_Z, (k_z_fin<<<dim3(Gz, nb), 256, 0, c->stream>>>(base, b0, bb.Wt, c->T, bb.needz)));
       TRY(oz_product(c, 1, bb.Wt + (size_t)b0 * c->T, c->T, nb, Bp, nullptr, &sp));
       PROF_LAUNCH(NK_OZ_G, (k_oz_fin_g<<<dim3((c->ld + 255) / 256, nb), 256, 0, c->stream>>>(
                                 oz.part, sp, Bp, oz.MpB, oz.eB, oz.fB, base, b0)));
@@ -717,6 +776,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     }
   }
   PROF_LAUNCH(NK_DECIDE1, (k_decide1<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gl)));
+  if (split) PROF_LAUNCH(NK_ZSTEP, (k_z_step<<<dim3(Gz, B), 256, 0, c->stream>>>(base, bb.wls, 1)));
   if (split) {
     PROF_LAUNCH(NK_NEED, (k_need_ls2<<<1, 64, 0, c->stream>>>(base, B, bb.need)));
     TRY(ls_split(base.dstep, SI_SKIPLS, bb.need));
@@ -731,6 +791,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     }
   }
   PROF_LAUNCH(NK_DECIDE2, (k_decide2<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gl)));
+  if (split) PROF_LAUNCH(NK_ZSTEP, (k_z_step<<<dim3(Gz, B), 256, 0, c->stream>>>(base, bb.wls, 2)));
   PROF_LAUNCH(NK_END_ITER, (k_end_iter<<<dim3(1, B), 32, 0, c->stream>>>(base)));
   return MVSK_OK;
 }
@@ -749,8 +810,11 @@ struct InstRun {
   double ev[3] = {0, 0, 0};
 };
 
-// Start an inner solve of instance b at c1 from warm start w0 (device vector or null).
-mvsk_status batch_start_run(mvsk_ctx* c, BatchBuf& bb, int b, InstRun& r, double c1, const double* w0, double tol) {
+// Start an inner solve of instance b at c1 from warm start w0 (device vector or
+// null: 1/n).  zw0: the cached A w0 (device, T) when known; without it the next
+// iteration recomputes z = A x (split products; a start from 1/n takes A 1/n).
+mvsk_status batch_start_run(mvsk_ctx* c, BatchBuf& bb, int b, InstRun& r, double c1, const double* w0, double tol,
+                            const double* zw0) {
   const Inst s = inst_at(bb.base, b);
   r.cc[0] = c1;
   const Options& o = c->opt;
@@ -767,6 +831,9 @@ mvsk_status batch_start_run(mvsk_ctx* c, BatchBuf& bb, int b, InstRun& r, double
   bb.kq_c1.push_back(c1);
   if (w0 != nullptr) CU(cudaMemcpyAsync(s.x, w0, sizeof(double) * c->ld, cudaMemcpyDeviceToDevice, c->stream));
   else k_fill<<<(c->ld + 255) / 256, 256, 0, c->stream>>>(s.x, c->n, c->ld, 1.0 / c->n);
+  const double* zs = w0 == nullptr ? bb.z0 : zw0;
+  if (zs != nullptr) CU(cudaMemcpyAsync(s.z, zs, sizeof(double) * c->T, cudaMemcpyDeviceToDevice, c->stream));
+  else bb.needz_req = 1;
   k_new_phase<<<1, 32, 0, c->stream>>>(s, o.eta, o.pcg_max_iter);
   c->launches += 5;
   CU(cudaGetLastError());
@@ -792,6 +859,9 @@ mvsk_status kkt0_flush(mvsk_ctx* c, BatchBuf& bb) {
   bb.kq_c1.clear();
   return MVSK_OK;
 }
+
+// Iterations between full recomputations of the cached z = A x of a batch.
+constexpr int kZRefresh = 32;
 
 mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* tg_h, double tol, const double* W0,
                         double* W_out, mvsk_info* infos) {
@@ -830,6 +900,13 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
   // device buffers for warm starts: instance scratch columns 20 (lo) and 21 (hi)
   auto xlo = [&](int b) { return inst_at(bb.base, b).tmp + (size_t)20 * ld; };
   auto xhi = [&](int b) { return inst_at(bb.base, b).tmp + (size_t)21 * ld; };
+  // their cached z = A x (split products)
+  auto zlo = [&](int b) { return bb.zsave + (size_t)(2 * b) * c->T; };
+  auto zhi = [&](int b) { return bb.zsave + (size_t)(2 * b + 1) * c->T; };
+  auto save_z = [&](double* dst, const double* src) -> mvsk_status {
+    if (split) CU(cudaMemcpyAsync(dst, src, sizeof(double) * c->T, cudaMemcpyDeviceToDevice, c->stream));
+    return MVSK_OK;
+  };
   std::vector<double> hw;  // validated warm starts (host), B x n
   if (W0 != nullptr) {
     hw.resize((size_t)B * c->n);
@@ -895,6 +972,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     const Inst s0 = inst_at(bb.base, 0);
     k_fill<<<(c->ld + 255) / 256, 256, 0, c->stream>>>(s0.x, c->n, c->ld, 1.0 / c->n);
     TRY(pass_fwd_z(c, s0.x, s0.z));
+    CU(cudaMemcpyAsync(bb.z0, s0.z, sizeof(double) * c->T, cudaMemcpyDeviceToDevice, c->stream));
     c->launches += 1;
     for (int q0 = 0; q0 < B; q0 += L) {
       const int nq = B - q0 < L ? B - q0 : L;
@@ -947,10 +1025,10 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     }
     if (isnan(r.target)) {
       r.cal = 0;
-      return batch_start_run(c, bb, b, r, r.cc[0], w0, tol);
+      return batch_start_run(c, bb, b, r, r.cc[0], w0, tol, nullptr);
     }
     r.cal = 1;
-    return batch_start_run(c, bb, b, r, 0.0, nullptr, tol);
+    return batch_start_run(c, bb, b, r, 0.0, nullptr, tol, nullptr);
   };
   // results of the request in lane b (at the end of its last inner solve)
   std::vector<double> hx(ld);
@@ -1010,7 +1088,16 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
   const int phase_it[3] = {o.pcg_max_iter, o.restart_iter, o.restart_iter};
   int remaining = B;
   long long guard_iters = 0;
+  int needz_dev = 0;  // value of bb.needz on the device
   while (remaining > 0) {
+    if (split) {  // z = A x recomputed for user warm starts and every kZRefresh iterations (bounds the drift)
+      const int want = (bb.needz_req || (guard_iters > 0 && guard_iters % kZRefresh == 0)) ? 1 : 0;
+      if (want != needz_dev) {
+        CU(cudaMemcpyAsync(bb.needz, &want, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        needz_dev = want;
+      }
+      bb.needz_req = 0;
+    }
     CU(cudaGraphLaunch(gexec, c->stream));
     c->launches += per_graph;
     if (c->prof_on) {
@@ -1093,9 +1180,9 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
         if (r.evals >= o.cal_max_evals) return finish(true);
         double cm = r.c_hi - r.h_hi * (r.c_hi - r.c_lo) / (r.h_hi - r.h_lo);
         if (!(r.c_lo < cm && cm < r.c_hi)) cm = 0.5 * (r.c_lo + r.c_hi);
-        const double* w0 = (cm - r.c_lo) <= (r.c_hi - cm) ? xlo(b) : xhi(b);
+        const bool lo = (cm - r.c_lo) <= (r.c_hi - cm);
         r.cal = 3;
-        return batch_start_run(c, bb, b, r, cm, w0, tol);
+        return batch_start_run(c, bb, b, r, cm, lo ? xlo(b) : xhi(b), tol, split ? (lo ? zlo(b) : zhi(b)) : nullptr);
       };
       if (r.cal == 0) {
         TRY(finish(false));
@@ -1104,21 +1191,24 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
           TRY(finish(false));
         } else {
           CU(cudaMemcpyAsync(xlo(b), s.x, sizeof(double) * ld, cudaMemcpyDeviceToDevice, c->stream));
+          TRY(save_z(zlo(b), s.z));
           r.c_lo = 0.0;
           r.h_lo = h;
           r.c_hi = r.lam[0] > 0.0 ? (stdz ? r.lam[0] / s_eq : r.lam[0]) : r.c1_ref;
           r.cal = 2;
-          TRY(batch_start_run(c, bb, b, r, r.c_hi, xlo(b), tol));
+          TRY(batch_start_run(c, bb, b, r, r.c_hi, xlo(b), tol, split ? zlo(b) : nullptr));
         }
       } else if (r.cal == 2) {
         r.h_hi = h;
         CU(cudaMemcpyAsync(xhi(b), s.x, sizeof(double) * ld, cudaMemcpyDeviceToDevice, c->stream));
+        TRY(save_z(zhi(b), s.z));
         if (h < 0.0 && r.c_hi < r.c1_max) {
           r.c_lo = r.c_hi;
           r.h_lo = r.h_hi;
           CU(cudaMemcpyAsync(xlo(b), xhi(b), sizeof(double) * ld, cudaMemcpyDeviceToDevice, c->stream));
+          TRY(save_z(zlo(b), zhi(b)));
           r.c_hi = fmin(8.0 * r.c_hi, r.c1_max);
-          TRY(batch_start_run(c, bb, b, r, r.c_hi, xlo(b), tol));
+          TRY(batch_start_run(c, bb, b, r, r.c_hi, xlo(b), tol, split ? zlo(b) : nullptr));
         } else if (h < 0.0 || fabs(h) <= gap_tol) {
           TRY(finish(false));
         } else {
@@ -1134,12 +1224,14 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
             r.c_lo = cm;
             r.h_lo = h;
             CU(cudaMemcpyAsync(xlo(b), s.x, sizeof(double) * ld, cudaMemcpyDeviceToDevice, c->stream));
+            TRY(save_z(zlo(b), s.z));
             if (r.side == -1) r.h_hi *= 0.5;
             r.side = -1;
           } else {
             r.c_hi = cm;
             r.h_hi = h;
             CU(cudaMemcpyAsync(xhi(b), s.x, sizeof(double) * ld, cudaMemcpyDeviceToDevice, c->stream));
+            TRY(save_z(zhi(b), s.z));
             if (r.side == 1) r.h_lo *= 0.5;
             r.side = 1;
           }

@@ -56,6 +56,11 @@ struct BatchBuf {
   void* kq_dev = nullptr;        // device copy: c1 (cap doubles) then indices
   int* need = nullptr;   // any instance needs the second line-search product
   double* Gq = nullptr;  // G0 of every request when requests queue for fewer lanes (qcap x ld)
+  double* wls = nullptr;    // projected line-search direction A d of every instance (T-strided)
+  double* zsave = nullptr;  // cached z of the warm-start brackets lo, hi (2 x T per instance)
+  double* z0 = nullptr;     // A 1/n (T)
+  int* needz = nullptr;     // the next iteration recomputes z = A x (device flag)
+  int needz_req = 0;        // host: a start without a cached z asks for that
   int qcap = 0;
 };
 
@@ -391,11 +396,11 @@ const char* const kKernelNames[] = {"k_face", "k_probe_fill", "k_pcg_setup", "k_
                                     "k_assemble", "k_decide1", "k_decide2", "k_end_iter", "k_oz_fin_z",
                                     "k_oz_fin_g", "k_oz_fin_ls", "k_oz_split_vecs", "k_need_ls2", "k_reduce_cols",
                                     "k_hd_cols", "k_hd_reduce1", "k_hd_reduce2", "k_hd_reduce_diag",
-                                    "k_pcg_step_a"};
+                                    "k_pcg_step_a", "k_z_step"};
 enum NamedKernel : int {
   NK_FACE, NK_PROBE_FILL, NK_PCG_SETUP, NK_PCG_STEP, NK_COLS, NK_HVP1, NK_HVP2, NK_RHAT, NK_PCG_SETUP2, NK_ASSEMBLE,
   NK_DECIDE1, NK_DECIDE2, NK_END_ITER, NK_OZ_Z, NK_OZ_G, NK_OZ_LS, NK_OZ_SPLIT, NK_NEED, NK_REDUCE_COLS, NK_HD_COLS,
-  NK_HD_RED1, NK_HD_RED2, NK_HD_DIAG, NK_PCG_STEP_A, NK_COUNT
+  NK_HD_RED1, NK_HD_RED2, NK_HD_DIAG, NK_PCG_STEP_A, NK_ZSTEP, NK_COUNT
 };
 
 mvsk_status prof_begin(mvsk_ctx* c, int kind, double work) {
