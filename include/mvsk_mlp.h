@@ -14,7 +14,9 @@
  * pre-activations, gradients, Adam moments and master weights are FP32.
  *
  * Pointers: every array argument is a DEVICE pointer unless marked "host or
- * device".  Row-major throughout.  No call allocates after mvsk_mlp_create.
+ * device".  Row-major throughout.  No call on a network allocates after
+ * mvsk_mlp_create; mvsk_mlp_features allocates and frees 544 bytes of device
+ * scratch and synchronises the device.
  * Errors: MVSK_EINVAL for bad sizes (B < 1 or B > max_batch, non-positive
  * dimensions, d_in not a multiple of 8), MVSK_ECUDA for CUDA failures or an
  * in-kernel wait that ran out (the GEMMs' bounded mbarrier waits).

@@ -896,6 +896,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
   }
   std::vector<InstRun> run((size_t)L);
   std::vector<int> lane_req((size_t)L, -1);
+  bb.needz_req = 0;
   std::vector<std::array<double, 4>> cc(ccq.begin(), ccq.begin() + L);
   // device buffers for warm starts: instance scratch columns 20 (lo) and 21 (hi)
   auto xlo = [&](int b) { return inst_at(bb.base, b).tmp + (size_t)20 * ld; };
@@ -1005,6 +1006,38 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       c->launches += 1;
     }
   }
+  // user warm starts on the device (Wq, ld-strided) with their z = A w0 (Zq, one
+  // split product per 64 requests), so that a lane taking such a request needs
+  // no recomputation of z for the whole batch
+  if (!hw.empty()) {
+    if (bb.wcap < B) {
+      if (bb.Wq != nullptr) cudaFree(bb.Wq);
+      if (bb.Zq != nullptr) cudaFree(bb.Zq);
+      bb.Wq = bb.Zq = nullptr;
+      bb.wcap = 0;
+      if (cudaMalloc(&bb.Wq, sizeof(double) * ld * (size_t)B) != cudaSuccess ||
+          cudaMalloc(&bb.Zq, sizeof(double) * (size_t)c->T * (size_t)B) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MVSK_ENOMEM, "warm-start buffer allocation failed");
+      }
+      bb.wcap = B;
+    }
+    CU(cudaMemsetAsync(bb.Wq, 0, sizeof(double) * ld * (size_t)B, c->stream));
+    CU(cudaMemcpy2DAsync(bb.Wq, sizeof(double) * ld, hw.data(), sizeof(double) * c->n, sizeof(double) * c->n,
+                         (size_t)B, cudaMemcpyHostToDevice, c->stream));
+    if (split) {
+      for (int q0 = 0; q0 < B; q0 += kOzMaxB) {
+        const int nb = B - q0 < kOzMaxB ? B - q0 : kOzMaxB;
+        int sp = 0;
+        TRY(oz_product(c, 0, bb.Wq + (size_t)q0 * ld, c->ld, nb, oz_bp(nb), nullptr, &sp));
+        k_oz_store<<<dim3((unsigned)((c->T + 255) / 256), (unsigned)nb), 256, 0, c->stream>>>(
+            c->oz.part, sp, oz_bp(nb), c->oz.MpF, c->T, nb, c->oz.eF, c->oz.fF, 1.0, bb.Zq + (size_t)q0 * c->T,
+            c->T);
+        c->launches += 1;
+        CU(cudaGetLastError());
+      }
+    }
+  }
   // request q into lane b: its state, its G0 and warm start, and the first inner solve
   int next_req = 0;
   auto assign = [&](int b) -> mvsk_status {
@@ -1018,14 +1051,13 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
                          c->stream));
     const double* w0 = nullptr;
     if (!hw.empty()) {
-      CU(cudaMemsetAsync(s.xbar, 0, sizeof(double) * ld, c->stream));
-      CU(cudaMemcpyAsync(s.xbar, hw.data() + (size_t)q * c->n, sizeof(double) * c->n, cudaMemcpyHostToDevice,
-                         c->stream));
+      CU(cudaMemcpyAsync(s.xbar, bb.Wq + (size_t)q * ld, sizeof(double) * ld, cudaMemcpyDeviceToDevice, c->stream));
       w0 = s.xbar;
     }
     if (isnan(r.target)) {
       r.cal = 0;
-      return batch_start_run(c, bb, b, r, r.cc[0], w0, tol, nullptr);
+      return batch_start_run(c, bb, b, r, r.cc[0], w0, tol,
+                             (w0 != nullptr && split) ? bb.Zq + (size_t)q * c->T : nullptr);
     }
     r.cal = 1;
     return batch_start_run(c, bb, b, r, 0.0, nullptr, tol, nullptr);
@@ -1088,7 +1120,8 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
   const int phase_it[3] = {o.pcg_max_iter, o.restart_iter, o.restart_iter};
   int remaining = B;
   long long guard_iters = 0;
-  int needz_dev = 0;  // value of bb.needz on the device
+  int needz_dev = 0;  // value of bb.needz on the device (a previous solve may have left 1)
+  if (split) CU(cudaMemsetAsync(bb.needz, 0, sizeof(int), c->stream));
   while (remaining > 0) {
     if (split) {  // z = A x recomputed for user warm starts and every kZRefresh iterations (bounds the drift)
       const int want = (bb.needz_req || (guard_iters > 0 && guard_iters % kZRefresh == 0)) ? 1 : 0;

@@ -61,6 +61,9 @@ struct BatchBuf {
   double* z0 = nullptr;     // A 1/n (T)
   int* needz = nullptr;     // the next iteration recomputes z = A x (device flag)
   int needz_req = 0;        // host: a start without a cached z asks for that
+  double* Wq = nullptr;     // user warm starts of the requests (wcap x ld) ...
+  double* Zq = nullptr;     // ... and their A w0 (wcap x T)
+  int wcap = 0;
   int qcap = 0;
 };
 
@@ -1754,6 +1757,8 @@ void mvsk_destroy(mvsk_ctx* c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void* p : c->batch.mem) cudaFree(p);
   if (c->batch.Gq != nullptr) cudaFree(c->batch.Gq);
+  if (c->batch.Wq != nullptr) cudaFree(c->batch.Wq);
+  if (c->batch.Zq != nullptr) cudaFree(c->batch.Zq);
   if (c->own_stream != nullptr) cudaStreamDestroy(c->own_stream);
   delete c;
 }
