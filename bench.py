@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=64, help="instances per step (<= 64)")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="concurrent instances of the batched solver (0: all requests at once)")
     ap.add_argument("--cpu-sample-its", type=int, default=1)
     ap.add_argument("--workload", default="c4",
                     choices=["c4", "paper-synthetic", "paper-line-search", "paper-conditioning", "warm-start"],
@@ -175,6 +177,8 @@ def run_ours(args, rank, world):
     ctx = m.MVSK(Rd, args.precision)
     out = torch.empty((B, R.shape[1]), dtype=torch.float64, device="cuda")
 
+    ctx.set_option("batch_lanes", args.lanes)
+
     def step():
         return ctx.solve_batch(lam_b, tg_b, m.PCG, args.tol, out=out)
 
@@ -263,6 +267,7 @@ def run_ours(args, rank, world):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             c2 = m.MVSK(Rh, args.precision)
+            c2.set_option("batch_lanes", args.lanes)
             c2.solve_batch(lam_b, tg_b, m.PCG, args.tol, out=Wh)
             c2.close()
         torch.cuda.synchronize()
