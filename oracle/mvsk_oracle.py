@@ -32,6 +32,8 @@ the design notes of the repository):
     violation.
   * Stall (PCG): max_iter reached or kkt not reduced by 1% over 10
     iterations; restarts at projected step 0.045 then 0.02 (120 its each).
+    The 1% test only triggers restarts: the last phase runs to the
+    tolerance or its 120 iterations.
   * Preference scaling RAW (c = lambda) or STANDARDISED (c_p = lambda_p/s^p,
     s = sqrt(m2(1/n))); a return target calibrates c1 >= 0 by a safeguarded
     secant/bisection root-find on mu^T x*(c1) = target.
@@ -758,7 +760,9 @@ def solve(A, mu, c, config="direct", tol=1e-8, w0=None, opts: Options | None = N
             if time.perf_counter() - t0 > opts.max_elapsed:
                 info.status = "timeout"
                 break
-            if (config == "pcg" and len(hist) > opts.stall_window
+            # the stall test ends a phase to restart it; the last phase has no
+            # restart after it and runs to the tolerance or its budget
+            if (config == "pcg" and ph + 1 < len(phases) and len(hist) > opts.stall_window
                     and hist[-1] > opts.stall_factor * hist[-1 - opts.stall_window]):
                 break
             active = working_set(x, g, opts, info.branches)
@@ -796,14 +800,15 @@ def _finish(A, mu, c, x, info, kkt, rel, opts, t0):
 
 
 def calibrate_target(A, mu, c, target, config="direct", tol=1e-8, opts=None,
-                     rel_tol=1e-9, bracket_tol=1e-12, max_evals=40, c1_max=None):
+                     rel_tol=1e-9, bracket_tol=1e-12, max_evals=40, c1_max=None, callback=None):
     """Find c1 >= 0 with mu^T x*(c1) = target (Illinois regula falsi).
 
     mu^T x*(c1) is non-decreasing in c1.  If x*(0) already meets the target,
     c1 = 0.  The upper end starts at c[0] (or c2 s^2 / max|mu| with s^2 = m2(1/n)
     when c[0] = 0) and grows x8 until the target is bracketed or c1_max =
     1e6 c2 s^2 / max|mu| is reached (then c1 = c1_max).  Each solve is warm-
-    started from the nearest bracket end.  Returns (c, x, info, evals).
+    started from the nearest bracket end.  `callback` is handed to every
+    inner solve.  Returns (c, x, info, evals).
     """
     c = np.asarray(c, dtype=np.float64).copy()
     scale = float(np.max(np.abs(mu)))
@@ -818,7 +823,7 @@ def calibrate_target(A, mu, c, target, config="direct", tol=1e-8, opts=None,
     def run(c1, w0):
         cc = c.copy()
         cc[0] = c1
-        x, inf = solve(A, mu, cc, config, tol, w0=w0, opts=opts)
+        x, inf = solve(A, mu, cc, config, tol, w0=w0, opts=opts, callback=callback)
         return x, inf, float(mu @ x) - target
 
     evals = 0

@@ -171,6 +171,41 @@ def test_alpha_max_feasibility_lemma():
             y = x + a * d
             assert abs(y.sum() - 1.0) <= 1e-14
             assert y.min() >= tau - 1e-16
+        # and it is the largest such step: any longer one leaves Delta(tau)
+        # (the coordinate that attains the minimum crosses tau)
+        y = x + (1.0 + 1e-9) * am * d
+        assert y.min() < tau
+
+
+def test_alpha_max_is_tight_and_infinite_without_decrease():
+    """alpha_max is the largest feasible step, not just a feasible one: on
+    drawn cases (interior points, points with coordinates at tau, directions
+    with a single negative coordinate) a step 1e-9 longer leaves Delta(tau),
+    brute-force over the coordinates gives the same value, and a direction with
+    no negative coordinate has alpha_max = +inf."""
+    rng = np.random.default_rng(17)
+    tau = 1e-8
+    for k in range(200):
+        n = int(rng.integers(2, 40))
+        x = O.project_slice(rng.dirichlet(np.ones(n) * rng.uniform(0.1, 3)), tau)
+        if k % 3 == 1:
+            x[rng.integers(0, n, size=max(1, n // 4))] = tau
+            x = O.project_slice(x, tau)
+        d = rng.standard_normal(n) * 10.0 ** rng.uniform(-3, 1)
+        if k % 5 == 2:
+            d = np.abs(d)
+            d[int(rng.integers(0, n))] = -float(np.sum(d))
+        d -= d.mean()
+        am = O.alpha_max(x, d, tau)
+        brute = min(((x[i] - tau) / -d[i] for i in range(n) if d[i] < 0), default=math.inf)
+        assert am == brute
+        if math.isfinite(am):
+            longer = (1.0 + 1e-9) * am if am > 0 else 1e-12   # am = 0: a coordinate at tau with d_i < 0
+            assert np.min(x + longer * d) < tau
+            if am > 0:
+                assert np.min(x + am * d) >= tau - 4 * np.finfo(float).eps
+    d = np.zeros(5)
+    assert O.alpha_max(np.full(5, 0.2), d, tau) == math.inf
 
 
 # ---------------------------------------------------- projection and KKT residual
