@@ -75,7 +75,8 @@ typedef struct {
   double achieved_mean;   /* mu^T x */
   double seconds;         /* wall time of the call */
   int32_t status;         /* mvsk_status of the solve */
-  int32_t reserved;
+  int32_t batch_iters;    /* mvsk_solve_batch: lockstep iterations the whole batch ran (every
+                             request of the call reports the same count); 0 otherwise */
 } mvsk_info;
 
 /*
@@ -109,7 +110,8 @@ mvsk_status mvsk_set_prefs(mvsk_ctx* ctx, const double lambda[4], double target)
 /*
  * mvsk_set_option -- numeric options (Table yand-core-parameters and the
  *   readings): "tau" (1e-8), "eta" (0.05), "max_iter" (300, direct),
- *   "pcg_max_iter" (40), "restart_iter" (120), "restart_eta1" (0.045),
+ *   "pcg_max_iter" (40), "restart_iter" (120: iterations of each restart
+ *   phase; "restart_iter1" / "restart_iter2" set one phase), "restart_eta1" (0.045),
  *   "restart_eta2" (0.02), "max_elapsed" (60 s), "krylov_tol" (1e-3),
  *   "krylov_maxit" (15), "reg" (NaN: 0 direct / 1e-4 PCG), "probes" (8),
  *   "probe_seed" (24301), "pref_scaling" (1), "release_ratio" (0.5),
@@ -220,6 +222,44 @@ mvsk_status mvsk_product(mvsk_ctx* ctx, int32_t transpose, int32_t nvec, const d
                          double* out, int64_t ldo);
 
 /*
+ * mvsk_batch_hvp -- the direction products of one lockstep iteration of
+ *   mvsk_solve_batch, for parity tests, on caller-given operands: B instances
+ *   with coefficients C (B x 4, c1..c4) at points X (B x n), each with nc
+ *   columns V (B x nc x n, column j of instance b at V + (b*nc + j)*n).
+ *   With z_b = A x_b (FP64) and G_b = T^-1 A^T Diag(psi''_b(z_b)) A (Prop. 2):
+ *     HV[b][j]  = G_b v_bj  (Eq. operator-hvp), B x nc x n;
+ *     Gnu[b]    = G_b nuhat_b, nuhat: B x n;      diagG[b] = diag(G_b), B x n.
+ *   They run exactly as in the solve: A in BF16 with FP32 accumulation on the
+ *   tensor cores (psi'' in FP32; v, nuhat and the weighted rows rounded to
+ *   BF16), the B*nc columns side by side in one product.  path[0] (nullable)
+ *   receives 1 when the first product A V took the fused psi''-weighting
+ *   epilogue, 0 when it took split-K partials and a separate weighting pass;
+ *   path[1] the split-K count of the second product A^T S.  Arguments are
+ *   host or device pointers.  Needs a MVSK_PREC_MIXED_BF16 context; 1 <= nc
+ *   <= 16, 1 <= B <= 4096.  Uses the batch buffers of mvsk_solve_batch and a
+ *   scratch allocation released before returning.  Errors: EINVAL, ENOMEM,
+ *   ECUDA.
+ */
+mvsk_status mvsk_batch_hvp(mvsk_ctx* ctx, int32_t B, const double* C, const double* X,
+                           const double* nuhat, int32_t nc, const double* V, double* HV,
+                           double* Gnu, double* diagG, int32_t path[2]);
+
+/*
+ * mvsk_batch_third -- the Hutchinson correction of the PCG configuration as
+ *   mvsk_solve_batch computes it (Eq. operator-third, Sec. 3.2), for parity
+ *   tests: for B instances with coefficients C (B x 4) at points X (B x n)
+ *   and K probe pairs (U, P) (each B x K x n, pair k of instance b at
+ *   (b*K + k)*n),
+ *     rhat_b = K^-1 sum_k (A u_bk) o (A p_bk),
+ *     at[b]  = T^-1 A^T (psi'''_b(z_b) o rhat_b),  z_b = A x_b,  B x n.
+ *   BF16 A and operands on the tensor cores, FP32 accumulation, the weighted
+ *   rows rounded to BF16.  Host or device pointers; MVSK_PREC_MIXED_BF16
+ *   context; 1 <= K <= 8.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+mvsk_status mvsk_batch_third(mvsk_ctx* ctx, int32_t B, const double* C, const double* X, int32_t K,
+                             const double* U, const double* P, double* at);
+
+/*
  * Prop. quartic exact line search: coef[5] = A0..A4 of f(w + alpha d) from
  * the power sums s_rs, and *alpha_max = alpha_max(w, d; tau) (Lemma cap;
  * +inf when no d_i < 0).  FP64 A.
@@ -255,12 +295,13 @@ mvsk_status mvsk_quartic_argmin(mvsk_ctx* ctx, const double coef[5], double amax
  * kernel launch with CUDA events on the context's stream (launches inside
  * captured CUDA graphs as event nodes, read after each replay); (ctx, 0) stops.
  * mvsk_profile_only(ctx, prefix) restricts the brackets to kinds whose label
- * starts with `prefix` (NULL: all kinds), which keeps the event overhead of a
- * timed run to the kernel of interest.  mvsk_profile_stride(ctx, k) (k >= 1,
- * default 1; reset by mvsk_profile_enable) brackets only every k-th launch of
- * the selected kinds, counted in issue order (inside a captured graph, at
+ * starts with `prefix`, or with one of the comma-separated prefixes it lists
+ * (NULL: all kinds), which keeps the event overhead of a timed run to the
+ * kernels of interest.  mvsk_profile_stride(ctx, k) (k >= 1, default 1; reset
+ * by mvsk_profile_enable) brackets only every k-th launch of each selected
+ * kind, counted per kind in issue order (inside a captured graph, at
  * capture): an event node between two kernels costs the graph part of their
- * overlap, so a timed run samples its kernel.  EINVAL for k < 1.
+ * overlap, so a timed run samples its kernels.  EINVAL for k < 1.
  * mvsk_profile_read fills up to `max` entries, one per kind: its label
  * (streaming pass, tensor-core product, split FP64 product or named kernel),
  * launches, summed device time (ms) and the average algorithmic work per

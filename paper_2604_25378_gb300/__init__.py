@@ -43,10 +43,10 @@ class Info(ctypes.Structure):
                 ("free_count", ctypes.c_int32), ("evals", ctypes.c_int32), ("f", ctypes.c_double),
                 ("kkt_residual", ctypes.c_double), ("kkt0", ctypes.c_double), ("kkt_rel", ctypes.c_double),
                 ("c", ctypes.c_double * 4), ("achieved_mean", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("batch_iters", ctypes.c_int32)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("c", "reserved")}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "c"}
         d["c"] = list(self.c)
         d["status"] = STATUS.get(self.status, self.status)
         return d
@@ -72,6 +72,8 @@ _SIGS = {
     "mvsk_oracle_gram": (ctypes.c_int, [_P, _P, _P]),
     "mvsk_product": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64, _P, ctypes.c_int64]),
     "mvsk_oracle_ls": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "mvsk_batch_hvp": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, _P, _P, _P, _P, _P]),
+    "mvsk_batch_third": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, _P]),
     "mvsk_oracle_direction": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int32, _P]),
     "mvsk_project_slice": (ctypes.c_int, [_P, _P, ctypes.c_double, _P]),
     "mvsk_quartic_argmin": (ctypes.c_int, [_P, _P, ctypes.c_double, _P]),
@@ -252,6 +254,37 @@ class MVSK:
         self._check(self._lib.mvsk_product(self._h, 1 if transpose else 0, V.shape[0], ctypes.c_void_p(V.data_ptr()),
                                            V.shape[1], ctypes.c_void_p(out.data_ptr()), m))
         return out
+
+    def batch_hvp(self, C, X, nuhat, V):
+        """Direction products of a lockstep batch iteration (mvsk_batch_hvp):
+        C (B x 4), X (B x n), nuhat (B x n), V (B x nc x n) -> (HV (B x nc x n),
+        Gnu (B x n), diagG (B x n), (fused first product, split count of the second))."""
+        C = np.ascontiguousarray(C, dtype=np.float64)
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        NU = np.ascontiguousarray(nuhat, dtype=np.float64)
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        B, nc = V.shape[0], V.shape[1]
+        HV = np.empty((B, nc, self.n))
+        Gn = np.empty((B, self.n))
+        Dg = np.empty((B, self.n))
+        path = (ctypes.c_int32 * 2)()
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        self._check(self._lib.mvsk_batch_hvp(self._h, B, vp(C), vp(X), vp(NU), nc, vp(V), vp(HV), vp(Gn), vp(Dg),
+                                             path))
+        return HV, Gn, Dg, (int(path[0]), int(path[1]))
+
+    def batch_third(self, C, X, U, P):
+        """Hutchinson correction of a lockstep batch (mvsk_batch_third): C (B x 4),
+        X (B x n), probe pairs U, P (B x K x n) -> at (B x n)."""
+        C = np.ascontiguousarray(C, dtype=np.float64)
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        B, K = U.shape[0], U.shape[1]
+        at = np.empty((B, self.n))
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        self._check(self._lib.mvsk_batch_third(self._h, B, vp(C), vp(X), K, vp(U), vp(P), vp(at)))
+        return at
 
     def line_search(self, w, d):
         pw, kw = _ptr(w)

@@ -611,12 +611,16 @@ mvsk_status tc_partials_n(mvsk_ctx* c, const void* Aop, int M, const void* Bop, 
 // the split partials of A^T S (the PCG step sums them):
 // S^T = bf16(psi''(z) o A P16) from the first product, fused into its
 // epilogue when it needs no split-K.  P16 holds the BF16 columns already.
-mvsk_status hvp_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int nc, int* s2) {
+// *fused (nullable) tells which form the first product took: 1 the fused
+// weighting epilogue, 0 split-K partials and k_reduce_hvp1_b.
+mvsk_status hvp_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int nc, int* s2, int* fused = nullptr) {
   const int N = B * nc;
   const unsigned gt4 = (unsigned)((c->T + 1023) / 1024);
   const int bn = tc_bn(N), mt = (int)((c->T + 2 * kTcBM - 1) / (2 * kTcBM)), nt = (N + bn - 1) / bn;
   const int nk = (int)((c->ld + kTcBK - 1) / kTcBK);
-  if (tc_wide(bn) && 2 * mt * nt >= c->nsm) {  // enough work without split-K: fuse the weighting
+  const bool fuse = tc_wide(bn) && 2 * mt * nt >= c->nsm;
+  if (fused != nullptr) *fused = fuse ? 1 : 0;
+  if (fuse) {  // enough work without split-K: fuse the weighting
     CUtensorMap ta, tb;
     TRY(make_tmap_bf16(&ta, c->Alo, (unsigned long long)c->ld, (unsigned long long)c->T,
                        (unsigned long long)c->ld * 2, kTcBK, kTcBM));
@@ -834,7 +838,7 @@ mvsk_status batch_start_run(mvsk_ctx* c, BatchBuf& bb, int b, InstRun& r, double
   const double* zs = w0 == nullptr ? bb.z0 : zw0;
   if (zs != nullptr) CU(cudaMemcpyAsync(s.z, zs, sizeof(double) * c->T, cudaMemcpyDeviceToDevice, c->stream));
   else bb.needz_req = 1;
-  k_new_phase<<<1, 32, 0, c->stream>>>(s, o.eta, o.pcg_max_iter);
+  k_new_phase<<<1, 32, 0, c->stream>>>(s, o.eta, o.pcg_max_iter, o.stall_window);
   c->launches += 5;
   CU(cudaGetLastError());
   r.phase = 0;
@@ -1117,7 +1121,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
   std::vector<int> si((size_t)L * kSI);
   std::vector<double> evh((size_t)L * 4);
   const double phase_eta[3] = {o.eta, o.restart_eta1, o.restart_eta2};
-  const int phase_it[3] = {o.pcg_max_iter, o.restart_iter, o.restart_iter};
+  const int phase_it[3] = {o.pcg_max_iter, o.restart_iter1, o.restart_iter2};
   int remaining = B;
   long long guard_iters = 0;
   int needz_dev = 0;  // value of bb.needz on the device (a previous solve may have left 1)
@@ -1161,7 +1165,8 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       if (d2 == 2 && r.phase + 1 < 3) {
         r.phase += 1;
         r.restarts += 1;
-        k_new_phase<<<1, 32, 0, c->stream>>>(inst_at(bb.base, b), phase_eta[r.phase], phase_it[r.phase]);
+        k_new_phase<<<1, 32, 0, c->stream>>>(inst_at(bb.base, b), phase_eta[r.phase], phase_it[r.phase],
+                                             r.phase + 1 < 3 ? o.stall_window : 0);
         c->launches += 1;
         CU(cudaGetLastError());
         continue;
@@ -1285,5 +1290,159 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     if (guard_iters > 1000000) return fail(MVSK_ECUDA, "batched solve did not terminate");
   }
   TRY(sync(c));
+  if (infos != nullptr)
+    for (int q = 0; q < B; ++q) infos[q].batch_iters = (int32_t)guard_iters;
   return first;
+}
+
+// ------------------------------------------------ parity exports of the batch
+// The direction products of one lockstep iteration on caller-given inputs
+// (mvsk_batch_hvp, mvsk_batch_third): the same kernels, launch shapes and
+// buffers as batch_iteration, with the operands loaded instead of produced by
+// the PCG recurrences, so that tests hold them against the plain products.
+
+// Column j < nc of instance b (b = blockIdx.y / nc) from src[(b*nc + j)*n + i]
+// in FP32, zero padding to ld: PCG column j (which = 0), X column 1 + j
+// (which = 1) or B column 1 + j (which = 2), the columns the products read.
+__global__ void k_load_cols_f32(Inst base, int nc, int which, const double* src) {
+  const int ld = base.ld, n = base.n;
+  const int q = blockIdx.y, b = q / nc, j = q % nc;
+  const Inst s = inst_at(base, b);
+  float* col = which == 0 ? kcol<float>(s.P, j, ld) : (which == 1 ? kcol<float>(s.X, 1 + j, ld)
+                                                                  : kcol<float>(s.Bv, 1 + j, ld));
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ld; i += gridDim.x * blockDim.x)
+    col[i] = i < n ? (float)src[((size_t)b * nc + j) * n + i] : 0.f;
+}
+
+// Instance b = blockIdx.x: c1..c4 from C[4b..4b+3] and 1/T.
+__global__ void k_set_coef(Inst base, const double* C, double invT) {
+  const Inst s = inst_at(base, blockIdx.x);
+  if (threadIdx.x < 4) s.sd[SD_C1 + threadIdx.x] = C[4 * blockIdx.x + threadIdx.x];
+  if (threadIdx.x == 0) s.sd[SD_INVT] = invT;
+}
+
+// v_b[i] = val for i < n, 0 for n <= i < ld, instance b = blockIdx.y (stride vs).
+__global__ void k_fill_inst(double* v, long long vs, int n, int ld, double val) {
+  double* p = v + (size_t)blockIdx.y * vs;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ld; i += gridDim.x * blockDim.x) p[i] = i < n ? val : 0.0;
+}
+
+// Device scratch of an export call, released when the call returns.
+struct TmpDev {
+  void* p = nullptr;
+  ~TmpDev() {
+    if (p != nullptr) cudaFree(p);
+  }
+  mvsk_status get(size_t bytes) {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      return fail(MVSK_ENOMEM, "scratch allocation of %zu bytes failed", bytes);
+    }
+    return MVSK_OK;
+  }
+};
+
+// Instances 0..B-1 of the batch buffers at points X (B x n) with coefficients
+// C (B x 4, host or device): x_b, c_b, every instance running, and the cached
+// z_b = A x_b of the iteration (the FP64 streaming pass).  dev: 4B + Bn doubles.
+mvsk_status batch_export_setup(mvsk_ctx* c, int B, const double* C, const double* X, double* dev) {
+  BatchBuf& bb = c->batch;
+  TRY(ensure_tc_pcg(c));
+  TRY(batch_alloc(c, bb, B));
+  const Inst& base = bb.base;
+  const size_t n = (size_t)c->n;
+  double* Cd = dev;
+  double* Xd = dev + 4 * (size_t)B;
+  CU(cudaMemcpyAsync(Cd, C, sizeof(double) * 4 * B, cudaMemcpyDefault, c->stream));
+  CU(cudaMemcpyAsync(Xd, X, sizeof(double) * n * B, cudaMemcpyDefault, c->stream));
+  CU(cudaMemsetAsync(base.si, 0, sizeof(int) * kSI * (size_t)B, c->stream));
+  CU(cudaMemsetAsync(base.x, 0, sizeof(double) * (size_t)base.vs * B, c->stream));
+  CU(cudaMemcpy2DAsync(base.x, sizeof(double) * base.vs, Xd, sizeof(double) * n, sizeof(double) * n, (size_t)B,
+                       cudaMemcpyDeviceToDevice, c->stream));
+  k_set_coef<<<B, 32, 0, c->stream>>>(base, Cd, 1.0 / (double)c->T);
+  c->launches += 1;
+  CU(cudaGetLastError());
+  for (int b = 0; b < B; ++b) {
+    const Inst s = inst_at(base, b);
+    TRY(pass_fwd_z(c, s.x, s.z));
+  }
+  return MVSK_OK;
+}
+
+mvsk_status batch_hvp_export(mvsk_ctx* c, int B, const double* C, const double* X, const double* NU, int nc,
+                             const double* V, double* HV, double* GNU, double* DIAG, int32_t* path) {
+  if (c->dir_prec != P16) return fail(MVSK_EINVAL, "the batched products need a BF16 context (MVSK_PREC_MIXED_BF16)");
+  if (B < 1 || B > 4096) return fail(MVSK_EINVAL, "B must be in [1, 4096]");
+  if (nc < 1 || nc > kTcCols) return fail(MVSK_EINVAL, "nc must be in [1, %d]", kTcCols);
+  const size_t n = (size_t)c->n, ld = (size_t)c->ld, N = (size_t)B * nc;
+  TmpDev tmp;
+  TRY(tmp.get(sizeof(double) * (4 * (size_t)B + 2 * n * B + N * n + N * ld)));
+  double* dev = (double*)tmp.p;
+  double* NUd = dev + 4 * (size_t)B + n * B;
+  double* Vd = NUd + n * B;
+  double* HVd = Vd + N * n;
+  TRY(batch_export_setup(c, B, C, X, dev));
+  BatchBuf& bb = c->batch;
+  const Inst& base = bb.base;
+  // the face data of the diagonal block: nuhat_b as given, every coordinate free
+  CU(cudaMemcpyAsync(NUd, NU, sizeof(double) * n * B, cudaMemcpyDefault, c->stream));
+  CU(cudaMemcpyAsync(Vd, V, sizeof(double) * n * N, cudaMemcpyDefault, c->stream));
+  CU(cudaMemsetAsync(base.nuhat, 0, sizeof(double) * (size_t)base.vs * B, c->stream));
+  CU(cudaMemcpy2DAsync(base.nuhat, sizeof(double) * base.vs, NUd, sizeof(double) * n, sizeof(double) * n, (size_t)B,
+                       cudaMemcpyDeviceToDevice, c->stream));
+  const unsigned gl = (unsigned)((ld + 255) / 256), gl4 = (unsigned)((ld + 1023) / 1024);
+  k_fill_inst<<<dim3(gl, B), 256, 0, c->stream>>>(base.maskF, base.vs, c->n, c->ld, 1.0);
+  c->launches += 1;
+  CU(cudaGetLastError());
+  TRY(hvpdiag_tc_batch(c, bb, B, oz_row_ctas(c)));
+  k_load_cols_f32<<<dim3(gl, (unsigned)N), 256, 0, c->stream>>>(base, nc, 0, Vd);
+  k_cols_bf16_b<<<dim3(gl4, (unsigned)N), 256, 0, c->stream>>>(base, nc, 0, 0, bb.P16);
+  c->launches += 2;
+  CU(cudaGetLastError());
+  int s2 = 0, fused = 0;
+  TRY(hvp_tc_batch(c, bb, B, nc, &s2, &fused));
+  k_reduce_hvp2<<<4 * c->nsm, 256, 0, c->stream>>>(bb.part, s2, (int)N, c->n, c->ld, c->ld, 1.0 / (double)c->T, HVd,
+                                                   nullptr);
+  c->launches += 1;
+  CU(cudaGetLastError());
+  CU(cudaMemcpy2DAsync(HV, sizeof(double) * n, HVd, sizeof(double) * ld, sizeof(double) * n, N, cudaMemcpyDefault,
+                       c->stream));
+  CU(cudaMemcpy2DAsync(GNU, sizeof(double) * n, base.Gnu, sizeof(double) * 2 * base.vs, sizeof(double) * n,
+                       (size_t)B, cudaMemcpyDefault, c->stream));
+  CU(cudaMemcpy2DAsync(DIAG, sizeof(double) * n, base.diagG, sizeof(double) * 2 * base.vs, sizeof(double) * n,
+                       (size_t)B, cudaMemcpyDefault, c->stream));
+  TRY(sync(c));
+  if (path != nullptr) {
+    path[0] = fused;
+    path[1] = s2;
+  }
+  return MVSK_OK;
+}
+
+mvsk_status batch_third_export(mvsk_ctx* c, int B, const double* C, const double* X, int K, const double* U,
+                               const double* P, double* AT) {
+  if (c->dir_prec != P16) return fail(MVSK_EINVAL, "the batched products need a BF16 context (MVSK_PREC_MIXED_BF16)");
+  if (B < 1 || B > 4096) return fail(MVSK_EINVAL, "B must be in [1, 4096]");
+  if (K < 1 || 2 * K > kTcCols) return fail(MVSK_EINVAL, "K must be in [1, %d]", kTcCols / 2);
+  const size_t n = (size_t)c->n, ld = (size_t)c->ld, NK = (size_t)B * K;
+  TmpDev tmp;
+  TRY(tmp.get(sizeof(double) * (4 * (size_t)B + n * B + 2 * NK * n)));
+  double* dev = (double*)tmp.p;
+  double* Ud = dev + 4 * (size_t)B + n * B;
+  double* Pd = Ud + NK * n;
+  TRY(batch_export_setup(c, B, C, X, dev));
+  BatchBuf& bb = c->batch;
+  const Inst& base = bb.base;
+  CU(cudaMemcpyAsync(Ud, U, sizeof(double) * n * NK, cudaMemcpyDefault, c->stream));
+  CU(cudaMemcpyAsync(Pd, P, sizeof(double) * n * NK, cudaMemcpyDefault, c->stream));
+  const unsigned gl = (unsigned)((ld + 255) / 256);
+  k_load_cols_f32<<<dim3(gl, (unsigned)NK), 256, 0, c->stream>>>(base, K, 1, Ud);
+  k_load_cols_f32<<<dim3(gl, (unsigned)NK), 256, 0, c->stream>>>(base, K, 2, Pd);
+  c->launches += 2;
+  CU(cudaGetLastError());
+  TRY(third_tc_batch(c, bb, B, K));
+  CU(cudaMemcpy2DAsync(AT, sizeof(double) * n, base.at, sizeof(double) * base.vs, sizeof(double) * n, (size_t)B,
+                       cudaMemcpyDefault, c->stream));
+  return sync(c);
 }

@@ -30,7 +30,7 @@ struct Options {
   double tau = 1e-8, eta = 0.05, max_elapsed = 60.0, krylov_tol = 1e-3, reg = NAN;
   double restart_eta1 = 0.045, restart_eta2 = 0.02, release_ratio = 0.5, eps_act = 1e-15;
   double descent_eps = 1e-10, stall_factor = 0.99, cal_rel_tol = 1e-9, cal_bracket_tol = 1e-12;
-  int max_iter = 300, pcg_max_iter = 40, restart_iter = 120, krylov_maxit = 15, probes = 8;
+  int max_iter = 300, pcg_max_iter = 40, restart_iter1 = 120, restart_iter2 = 120, krylov_maxit = 15, probes = 8;
   int stall_window = 10, pref_scaling = 1, oracle_prec = 0, arc_halvings = 40, cal_max_evals = 40, trace = 0;
   int split_products = 1;  // batched solves: FP64 products on the tensor cores (ozaki.cuh)
   int batch_lanes = 0;     // batched solves: concurrent instances (0: all requests at once)
@@ -150,7 +150,7 @@ struct mvsk_ctx {
   std::vector<char> prof_sel;                    // kinds recorded (mvsk_profile_only); empty = all
   bool prof_open = false;                        // a begun pair awaits its end event
   int prof_stride = 1;                           // bracket every k-th selected launch (mvsk_profile_stride)
-  long long prof_count = 0;                      // selected launches seen since enabling
+  std::vector<long long> prof_count;             // selected launches of each kind seen since enabling
 };
 
 namespace {
@@ -368,13 +368,17 @@ __global__ void k_init_state(Inst s0, double tol, double eta, int maxit, int pcg
   s.si[SI_LSRULE] = lsrule;
 }
 
-__global__ void k_new_phase(Inst s0, double eta, int maxit) {
+// A new phase of the PCG configuration: projected step eta, maxit iterations,
+// and the stall window (0: no stall test, the last phase, which has no
+// restart after it and runs until the tolerance or its iteration budget).
+__global__ void k_new_phase(Inst s0, double eta, int maxit, int stallwin) {
   Inst s = inst_at(s0, blockIdx.y);
   if (threadIdx.x != 0) return;
   s.si[SI_DONE] = 0;
   s.si[SI_PHASEIT] = 0;
   s.si[SI_HISTN] = 0;
   s.si[SI_MAXIT] = maxit;
+  s.si[SI_STALLWIN] = stallwin;
   s.sd[SD_ETA] = eta;
 }
 
@@ -408,7 +412,8 @@ enum NamedKernel : int {
 
 mvsk_status prof_begin(mvsk_ctx* c, int kind, double work) {
   if (!c->prof_on || (!c->prof_sel.empty() && !c->prof_sel[kind])) return MVSK_OK;
-  if (c->prof_count++ % c->prof_stride != 0) return MVSK_OK;
+  if (c->prof_count.empty()) c->prof_count.assign(kProfKinds, 0);
+  if (c->prof_count[kind]++ % c->prof_stride != 0) return MVSK_OK;
   c->prof_open = true;
   if (c->prof_n.empty()) {
     c->prof_n.assign(kProfKinds, 0);
@@ -1025,7 +1030,7 @@ mvsk_status solve_instance(mvsk_ctx* c, int cfg, double tol, const double* w0_de
   };
   std::vector<Phase> phases;
   if (cfg == MVSK_PCG) {
-    phases = {{o.eta, o.pcg_max_iter}, {o.restart_eta1, o.restart_iter}, {o.restart_eta2, o.restart_iter}};
+    phases = {{o.eta, o.pcg_max_iter}, {o.restart_eta1, o.restart_iter1}, {o.restart_eta2, o.restart_iter2}};
   } else {
     phases = {{o.eta, o.max_iter}};
   }
@@ -1065,7 +1070,8 @@ mvsk_status solve_instance(mvsk_ctx* c, int cfg, double tol, const double* w0_de
   const int every = graph ? 3 : 1;
   for (size_t ph = 0; ph < phases.size(); ++ph) {
     if (ph > 0) so->restarts += 1;
-    k_new_phase<<<1, 32, 0, c->stream>>>(s, phases[ph].eta, phases[ph].maxit);
+    k_new_phase<<<1, 32, 0, c->stream>>>(s, phases[ph].eta, phases[ph].maxit,
+                                         ph + 1 < phases.size() ? o.stall_window : 0);
     CU(cudaGetLastError());
     for (int it = 0; it <= phases[ph].maxit; ++it) {
       if (graph) {
@@ -1428,7 +1434,9 @@ mvsk_status mvsk_set_option(mvsk_ctx* c, const char* key, double v) {
   else if (k == "eta" && pos(v)) o.eta = v;
   else if (k == "max_iter" && cnt(v, 1, 1000000)) o.max_iter = (int)v;
   else if (k == "pcg_max_iter" && cnt(v, 1, 1000000)) o.pcg_max_iter = (int)v;
-  else if (k == "restart_iter" && cnt(v, 1, 1000000)) o.restart_iter = (int)v;
+  else if (k == "restart_iter" && cnt(v, 1, 1000000)) o.restart_iter1 = o.restart_iter2 = (int)v;
+  else if (k == "restart_iter1" && cnt(v, 1, 1000000)) o.restart_iter1 = (int)v;
+  else if (k == "restart_iter2" && cnt(v, 1, 1000000)) o.restart_iter2 = (int)v;
   else if (k == "restart_eta1" && pos(v)) o.restart_eta1 = v;
   else if (k == "restart_eta2" && pos(v)) o.restart_eta2 = v;
   else if (k == "max_elapsed" && v > 0.0) o.max_elapsed = v;
@@ -1585,6 +1593,21 @@ mvsk_status mvsk_product(mvsk_ctx* c, int32_t transpose, int32_t nvec, const dou
   return sync(c);
 }
 
+mvsk_status mvsk_batch_hvp(mvsk_ctx* c, int32_t B, const double* C, const double* X, const double* nuhat,
+                           int32_t nc, const double* V, double* HV, double* Gnu, double* diagG, int32_t path[2]) {
+  if (c == nullptr || C == nullptr || X == nullptr || nuhat == nullptr || V == nullptr || HV == nullptr ||
+      Gnu == nullptr || diagG == nullptr)
+    return fail(MVSK_EINVAL, "null argument");
+  return batch_hvp_export(c, B, C, X, nuhat, nc, V, HV, Gnu, diagG, path);
+}
+
+mvsk_status mvsk_batch_third(mvsk_ctx* c, int32_t B, const double* C, const double* X, int32_t K, const double* U,
+                             const double* P, double* at) {
+  if (c == nullptr || C == nullptr || X == nullptr || U == nullptr || P == nullptr || at == nullptr)
+    return fail(MVSK_EINVAL, "null argument");
+  return batch_third_export(c, B, C, X, K, U, P, at);
+}
+
 mvsk_status mvsk_oracle_ls(mvsk_ctx* c, const double* w, const double* d, double coef[5], double* alpha_max) {
   if (c == nullptr || w == nullptr || d == nullptr || coef == nullptr) return fail(MVSK_EINVAL, "null argument");
   if (!c->prefs_set) return fail(MVSK_ESTATE, "mvsk_set_prefs must come first");
@@ -1676,11 +1699,19 @@ mvsk_status mvsk_profile_only(mvsk_ctx* c, const char* prefix) {
   c->prof_sel.clear();
   if (prefix == nullptr) return MVSK_OK;
   c->prof_sel.assign(kProfKinds, 0);
-  const size_t len = strlen(prefix);
+  // a comma-separated list of prefixes selects the union of their kinds
+  const std::string all(prefix);
+  size_t p0 = 0;
   char nm[64];
-  for (int k = 0; k < kProfKinds; ++k) {
-    kind_name(k, nm, sizeof(nm));
-    c->prof_sel[k] = strncmp(nm, prefix, len) == 0 ? 1 : 0;
+  while (p0 <= all.size()) {
+    size_t p1 = all.find(',', p0);
+    if (p1 == std::string::npos) p1 = all.size();
+    const std::string pre = all.substr(p0, p1 - p0);
+    for (int k = 0; k < kProfKinds; ++k) {
+      kind_name(k, nm, sizeof(nm));
+      if (strncmp(nm, pre.c_str(), pre.size()) == 0) c->prof_sel[k] = 1;
+    }
+    p0 = p1 + 1;
   }
   return MVSK_OK;
 }
@@ -1689,7 +1720,7 @@ mvsk_status mvsk_profile_stride(mvsk_ctx* c, int32_t k) {
   if (c == nullptr) return fail(MVSK_EINVAL, "null context");
   if (k < 1) return fail(MVSK_EINVAL, "profile stride must be >= 1 (got %d)", (int)k);
   c->prof_stride = k;
-  c->prof_count = 0;
+  c->prof_count.clear();
   return MVSK_OK;
 }
 
@@ -1698,7 +1729,7 @@ mvsk_status mvsk_profile_enable(mvsk_ctx* c, int32_t on) {
   CU(cudaStreamSynchronize(c->stream));
   c->prof_on = on != 0;
   if (on) {
-    c->prof_count = 0;
+    c->prof_count.clear();
     c->ev_used = 0;
     c->ev_kind.clear();
     c->ev_work.clear();

@@ -1,0 +1,110 @@
+"""GPU parity of the batched direction products (the lockstep iteration of
+mvsk_solve_batch) against the plain FP64 products, at the full size of the
+n = 5440, T = 12000 frontier sweep and at small ragged sizes.
+
+mvsk_batch_hvp runs the same launches as the solver's Krylov steps: A P16
+with the psi'' weighting (fused into the GEMM epilogue when the product
+needs no split-K, otherwise split-K partials and a weighting pass), then
+A^T S split-K; plus the Gram-diagonal block (G nuhat, diag G).
+mvsk_batch_third runs the Hutchinson correction (rhat and A^T (psi''' o rhat)).
+The reference is numpy FP64 on the centred panel: Eq. operator-hvp
+T^-1 A^T (psi''(z) o A v), Prop. 2 for diag G, Eq. operator-third for the
+correction.  Bound: A, the columns and the weighted rows are rounded to BF16
+(2^-9 relative each) with FP32 accumulation, so every element is held to
+2e-2 of the same products on |A| and the absolute operands (the scale of the
+summation), the BF16 bound of the single-instance oracle tests.
+"""
+import numpy as np
+import pytest
+
+import panels
+from oracle import mvsk_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+C4 = (5440, 12000)
+LAMS = [(1.0, 1.0, 0.5, 0.5), (1.0, 1.0, 0.5, 2.0), (1.0, 1.0, 2.0, 0.5), (1.0, 1.0, 2.0, 2.0)]
+
+
+def _panel(n, T):
+    if (n, T) == C4:
+        return panels.garch_sector_panel(n, T, 3)
+    return panels.sector_factor_panel(n, T, n + T)
+
+
+def _inputs(n, T, B, seed):
+    R = _panel(n, T)
+    mu, A = O.centre(R)
+    rng = np.random.default_rng(seed)
+    C = np.array([O.scale_preferences(LAMS[b % 4], A, "standardised") for b in range(B)])
+    X = rng.dirichlet(np.ones(n) * 0.5, size=B)
+    return R, A, C, X, rng
+
+
+def _ctx(R):
+    import paper_2604_25378_gb300 as m
+    return m.MVSK(R, "bf16")
+
+
+# (n, T, B, nc, fused): the full sweep shape (64 instances x 9 PCG columns =
+# 576 columns, the fused-epilogue form) and small shapes (split-K form),
+# ragged in T, n and the column count.
+HVP_CASES = [(5440, 12000, 64, 9, 1), (300, 3001, 4, 9, 0), (130, 1000, 3, 5, 0), (1000, 2500, 7, 1, 0)]
+
+
+@pytest.mark.parametrize("n,T,B,nc,fused", HVP_CASES)
+def test_batch_hvp_matches_plain_products(n, T, B, nc, fused):
+    R, A, C, X, rng = _inputs(n, T, B, 11)
+    V = rng.standard_normal((B, nc, n))
+    NU = rng.standard_normal((B, n))
+    NU /= np.linalg.norm(NU, axis=1, keepdims=True)
+    ctx = _ctx(R)
+    HV, Gn, Dg, path = ctx.batch_hvp(C, X, NU, V)
+    assert path[0] == fused, path  # which form of the weighted product ran
+    Z = A @ X.T                                   # T x B
+    H = np.column_stack([O.d2psi(C[b], Z[:, b]) for b in range(B)])
+    Aa = np.abs(A)
+    # all columns at once: (A V)_t, weighted by the instance's psi''
+    AV = A @ V.reshape(B * nc, n).T               # T x (B nc)
+    AVa = Aa @ np.abs(V).reshape(B * nc, n).T
+    Hc = np.repeat(H, nc, axis=1)
+    ref = (A.T @ (Hc * AV)).T / T
+    scale = (Aa.T @ (np.abs(Hc) * AVa)).T / T
+    err = np.abs(HV.reshape(B * nc, n) - ref)
+    assert np.all(err <= 2e-2 * scale + 1e-300), float(np.max(err / (scale + 1e-300)))
+    # the Gram-diagonal block: G nuhat and diag G (Prop. 2)
+    refg = (A.T @ (H * (A @ NU.T))).T / T
+    scg = (Aa.T @ (np.abs(H) * (Aa @ np.abs(NU).T))).T / T
+    assert np.all(np.abs(Gn - refg) <= 2e-2 * scg + 1e-300)
+    refd = ((A * A).T @ H).T / T
+    scd = ((A * A).T @ np.abs(H)).T / T
+    assert np.all(np.abs(Dg - refd) <= 2e-2 * scd + 1e-300)
+    # the same call again gives the same bits (fixed reduction orders)
+    HV2, _, _, _ = ctx.batch_hvp(C, X, NU, V)
+    assert np.array_equal(HV, HV2)
+
+
+# (n, T, B, K): the full sweep (64 instances x 8 probe pairs) and small shapes.
+THIRD_CASES = [(5440, 12000, 64, 8), (300, 3001, 4, 8), (130, 1000, 3, 3)]
+
+
+@pytest.mark.parametrize("n,T,B,K", THIRD_CASES)
+def test_batch_third_matches_plain_products(n, T, B, K):
+    R, A, C, X, rng = _inputs(n, T, B, 12)
+    U = rng.standard_normal((B, K, n))
+    P = rng.standard_normal((B, K, n))
+    ctx = _ctx(R)
+    at = ctx.batch_third(C, X, U, P)
+    Z = A @ X.T
+    Aa = np.abs(A)
+    AU = (A @ U.reshape(B * K, n).T).reshape(T, B, K)
+    AP = (A @ P.reshape(B * K, n).T).reshape(T, B, K)
+    AUa = (Aa @ np.abs(U).reshape(B * K, n).T).reshape(T, B, K)
+    APa = (Aa @ np.abs(P).reshape(B * K, n).T).reshape(T, B, K)
+    rhat = np.mean(AU * AP, axis=2)               # T x B (Hutchinson pair products)
+    rhat_a = np.mean(AUa * APa, axis=2)
+    W3 = np.column_stack([O.d3psi(C[b], Z[:, b]) for b in range(B)])
+    ref = (A.T @ (W3 * rhat)).T / T
+    scale = (Aa.T @ (np.abs(W3) * rhat_a)).T / T
+    err = np.abs(at - ref)
+    assert np.all(err <= 2e-2 * scale + 1e-300), float(np.max(err / (scale + 1e-300)))

@@ -197,8 +197,11 @@ def test_batched_lockstep_matches_oracle(split_products):
             tol_w = 1e-7
             assert abs(infos[b]["achieved_mean"] - targets[b]) <= 1e-9 * np.max(np.abs(mu))
         assert infos[b]["status"] == "ok", (b, infos[b])
-        g = O.gradient(A, mu, c, W[b])
-        assert O.kkt_residual(W[b], g, 1e-8) <= 1e-10 * inf_ref.kkt0 * 1.0001 + 1e-300 or infos[b]["kkt_rel"] <= 1e-10
+        # judged by the oracle alone, for the coefficients the GPU solved with
+        cg = np.asarray(infos[b]["c"])
+        x0 = np.full(A.shape[1], 1.0 / A.shape[1])
+        k0 = O.kkt_residual(x0, O.gradient(A, mu, cg, x0), 1e-8)
+        assert O.kkt_residual(W[b], O.gradient(A, mu, cg, W[b]), 1e-8) <= 1.5e-10 * k0
         if O.convexity_certificate(c):
             assert np.max(np.abs(W[b] - x_ref)) <= tol_w, (b, np.max(np.abs(W[b] - x_ref)))
         else:

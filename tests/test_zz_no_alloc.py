@@ -4,9 +4,10 @@ Some callers cannot call cudaMalloc (a fixed memory budget, or a steady-state
 loop inside a framework that owns the allocator).  This entry point takes the
 caller's buffers only and keeps its scratch in a static device array.  The test
 calls it through the C ABI twice in a row (different points, so stale scratch
-from the first call would show) and compares f and grad f with mvsk_eval, and
-z with A x, within the FP64 bound the other parity tests use (1e-12 of the
-sum of |terms| of each reduction).
+from the first call would show) and compares f and grad f with mvsk_eval and
+with the CPU oracle (Eqs. operator-f and operator-grad), and z with A x, within
+the FP64 bound the other parity tests use (1e-12 of the sum of |terms| of each
+reduction).
 """
 import numpy as np
 import pytest
@@ -47,8 +48,10 @@ def test_noalloc_matches_eval_twice():
         z = A @ x
         scale = np.abs(A).T @ np.abs(O.dpsi(lam, z)) / T + abs(lam[0]) * np.abs(mu)
         np.testing.assert_array_less(np.abs(g_d.cpu().numpy() - g_ref), 1e-12 * scale + 1e-300)
+        np.testing.assert_array_less(np.abs(g_d.cpu().numpy() - O.gradient(A, mu, lam, x)), 1e-12 * scale + 1e-300)
         fs = abs(lam[0] * (mu @ x)) + np.sum(np.abs(O.psi(lam, z))) / T
         assert abs(float(f_d.item()) - f_ref) <= 1e-12 * fs
+        assert abs(float(f_d.item()) - O.objective(A, mu, lam, x)) <= 1e-12 * fs
         zs = np.abs(A) @ np.abs(x)
         np.testing.assert_array_less(np.abs(z_d.cpu().numpy() - z), 1e-12 * zs + 1e-300)
 
