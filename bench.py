@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--lanes", type=int, default=0,
                     help="concurrent instances of the batched solver (0: all requests at once)")
-    ap.add_argument("--cpu-sample-its", type=int, default=1)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 single-instance leg")
     ap.add_argument("--workload", default="c4",
                     choices=["c4", "paper-synthetic", "paper-line-search", "paper-conditioning", "warm-start"],
                     help="c4: the batched C4 sweep (default); paper-*: the paper's own benchmarks "
@@ -79,16 +79,54 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-def instances(batch):
-    import panels
-    R, lams, tg = panels.workload(WORKLOAD)
-    lam_b, tg_b = [], []
-    for l in lams:
-        for t in tg:
-            lam_b.append(l)
-            tg_b.append(t)
+def sweep_requests(world=1):
+    """The frontier sweep's requests: 4 preference vectors x 16 N return targets
+    at asset-mean quantiles evenly spaced in [0.40, 0.85] (N = world size; the
+    measured workload is N = 1: 64 requests, request q = 16 v + t).  More ranks
+    add distinct targets, so every rank solves requests of its own."""
     import numpy as np
-    return R, np.asarray(lam_b)[:batch], np.asarray(tg_b)[:batch]
+
+    import panels
+    R, lams, _ = panels.workload(WORKLOAD)
+    tg = panels.quantile_targets(R, np.linspace(0.40, 0.85, 16 * world))
+    lam_b = np.asarray([l for l in lams for _ in tg])
+    tg_b = np.asarray([t for _ in lams for t in tg])
+    return R, lam_b, tg_b
+
+
+def partition(n_requests, rank, world):
+    """Indices of the global requests that rank `rank` solves: rank r takes
+    r, r + N, r + 2N, ... (every request exactly once over the ranks)."""
+    return list(range(rank, n_requests, world))
+
+
+def gather_weights(W_local, idx_local, n_requests, world):
+    """The weights of every request on rank 0, in global request order (W_local:
+    rows of this rank's requests idx_local; host float64 array).  Other ranks
+    receive None.  One gather over the process group (gloo for host tensors)."""
+    import numpy as np
+    if world == 1:
+        out = np.empty((n_requests, W_local.shape[1]))
+        out[idx_local] = W_local
+        return out
+    import torch
+    import torch.distributed as dist
+    obj = (list(idx_local), np.ascontiguousarray(W_local))
+    parts = [None] * world if dist.get_rank() == 0 else None
+    dist.gather_object(obj, parts, dst=0)
+    if dist.get_rank() != 0:
+        return None
+    out = np.full((n_requests, W_local.shape[1]), np.nan)
+    for idx, W in parts:
+        out[idx] = W
+    return out
+
+
+def instances(batch, rank=0, world=1):
+    """This rank's share of the sweep (at most `batch` requests)."""
+    R, lam_b, tg_b = sweep_requests(world)
+    idx = partition(len(lam_b), rank, world)[:batch]
+    return R, lam_b[idx], tg_b[idx], idx
 
 
 class ClockSampler:
@@ -164,6 +202,73 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# Kinds whose launches the timed step samples: the tensor-core products of
+# the direction block (N = 576 fused / split, N = 64 second PCG round) and the
+# split FP64 products (value, gradient, line search).
+TIMED_KINDS = "gemm_tc_bf16_n192,gemm_tc_bf16_n64,oz_gemm"
+
+
+def roofline_entry(name, d, pk, pk_src, T, n, ms_step):
+    """Roofline of one profiled kind from its live CUDA-event durations.
+
+    Tensor-core products report TFLOP/s against the sustained BF16 peak (the
+    profiler's work figure is their FLOPs).  The N = 64 products and the split
+    FP64 products are bandwidth-bound: they report GB/s of the operand they must
+    stream once per launch (BF16 A: 2 T n bytes; the seven BF16 digit planes of
+    the split product: 14 T n bytes, and the FP64 A it stands for, 8 T n)."""
+    avg_s = d["total_ms"] / d["launches"] / 1e3
+    e = {"kernel": name, "launches": d["launches"], "sampled_every": PROF_STRIDE, "avg_us": round(avg_s * 1e6, 2),
+         "share_of_step": round(d["total_ms"] * PROF_STRIDE / ms_step, 4), "traffic": None}
+    tr = measured_traffic(name)
+    e["traffic"] = None if tr is None else round(tr)
+    if name.startswith("oz_gemm"):
+        byt = 14.0 * T * n
+        e.update({"bound": "hbm", "unit": "GB/s", "achieved": round(byt / avg_s / 1e9, 1), "peak": pk["hbm_gbs"],
+                  "algorithmic_bytes": byt, "fp64_equivalent_gbs": round(8.0 * T * n / avg_s / 1e9, 1),
+                  "peak_source": pk_src})
+    elif name == "gemm_tc_bf16_n64":
+        byt = 2.0 * T * n
+        e.update({"bound": "hbm", "unit": "GB/s", "achieved": round(byt / avg_s / 1e9, 1), "peak": pk["hbm_gbs"],
+                  "algorithmic_bytes": byt, "peak_source": pk_src})
+    elif name.startswith("gemm_tc"):
+        e.update({"bound": "tensor", "unit": "TFLOP/s", "achieved": round(d["bytes_per_launch"] / avg_s / 1e12, 2),
+                  "peak": pk["bf16_tflops_sustained"], "algorithmic_flops": d["bytes_per_launch"],
+                  "peak_source": pk_src + " (sustained bf16)"})
+    else:
+        e.update({"bound": "hbm", "unit": "GB/s", "achieved": round(d["bytes_per_launch"] / avg_s / 1e9, 1),
+                  "peak": pk["hbm_gbs"], "algorithmic_bytes": d["bytes_per_launch"], "peak_source": pk_src})
+    e["frac"] = round(e["achieved"] / e["peak"], 4)
+    return e
+
+
+def plain_fp64(R, lam_b, tg_b, tol, picks):
+    """The denominator of the headline ratio: the plain single-instance FP64
+    GPU path (mvsk_solve on an FP64 context: FP64 streaming passes, one request
+    at a time) on a stated subset of the same requests, each timed in full."""
+    import numpy as np
+    import torch
+
+    import paper_2604_25378_gb300 as m
+    ctx = m.MVSK(torch.from_numpy(R).cuda(), "fp64")
+    ctx.set_prefs(np.asarray(lam_b[picks[0]]), float(tg_b[picks[0]]))
+    ctx.solve(m.PCG, tol)  # untimed: first-use set-up of the context
+    rows, total = [], 0.0
+    for q in picks:
+        ctx.set_prefs(np.asarray(lam_b[q]), float(tg_b[q]))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info = ctx.solve(m.PCG, tol)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        total += dt
+        rows.append({"request": int(q), "seconds": round(dt, 3), "iters": info["iters"], "evals": info["evals"],
+                     "status": info["status"]})
+    ctx.close()
+    return {"solves_per_s": len(picks) / total, "requests": rows,
+            "what": "mvsk_solve, FP64 context (FP64 streaming passes and FP64 Krylov vectors), one calibrated "
+                    "request at a time, same tolerance"}
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -171,11 +276,12 @@ def run_ours(args, rank, world):
     import paper_2604_25378_gb300 as m
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    R, lam_b, tg_b = instances(args.batch)
+    R, lam_b, tg_b, idx = instances(args.batch, rank, world)
     B = len(lam_b)
+    T, n = R.shape
     Rd = torch.from_numpy(R).cuda()
     ctx = m.MVSK(Rd, args.precision)
-    out = torch.empty((B, R.shape[1]), dtype=torch.float64, device="cuda")
+    out = torch.empty((B, n), dtype=torch.float64, device="cuda")
 
     ctx.set_option("batch_lanes", args.lanes)
 
@@ -183,7 +289,7 @@ def run_ours(args, rank, world):
         return ctx.solve_batch(lam_b, tg_b, m.PCG, args.tol, out=out)
 
     # Warm-up; the last warm-up step runs with every launch profiled (the
-    # breakdown), and the timed steps profile only its dominant kernel kind.
+    # breakdown), and the timed steps profile only their main kernel kinds.
     for w in range(args.warmup):
         if w == args.warmup - 1:
             ctx.profile_only(None)
@@ -192,13 +298,12 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     breakdown, _ = ctx.profile_read()
     ctx.profile_enable(False)
-    bad = [i for i in infos if i["status"] != "ok" or i["kkt_rel"] > args.tol]
     timed_kinds = {k: v for k, v in breakdown.items() if v["bytes_per_launch"] > 0}
     dom_name = max(timed_kinds.items(), key=lambda kv: kv[1]["total_ms"])[0] if timed_kinds else None
     sampler = ClockSampler(torch.cuda.current_device())
-    ctx.profile_only(dom_name)
-    # every PROF_STRIDE-th launch of that kind (an odd stride alternates the two
-    # products of a Krylov step): each event node costs the graph an overlap
+    ctx.profile_only(TIMED_KINDS + ("," + dom_name if dom_name else ""))
+    # every PROF_STRIDE-th launch of each kind (an odd stride alternates the
+    # two products of a Krylov step): each event node costs the graph an overlap
     ctx.profile_stride(PROF_STRIDE)
     ctx.profile_enable(True)
     barrier(world)
@@ -207,11 +312,12 @@ def run_ours(args, rank, world):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    iters = []
+    iters, lock = [], []
     torch.cuda.nvtx.range_push("timed_step")  # lets ncu restrict a capture to the timed region
     for _ in range(args.steps):
         _, infos = step()
         iters.append(sum(i["iters"] for i in infos))
+        lock.append(infos[0]["batch_iters"])
     torch.cuda.nvtx.range_pop()
     e1.record()
     torch.cuda.synchronize()
@@ -223,45 +329,51 @@ def run_ours(args, rank, world):
     ctx.profile_stride(1)
     ms_max = max_over_ranks(ms, world)
     value = B * args.steps * world / (ms_max / 1e3)
+    bad = [i for i in infos if i["status"] != "ok" or i["kkt_rel"] > args.tol]
 
-    # Roofline of the dominant pass kind (live CUDA-event durations of the timed steps).
-    dom = (dom_name, prof[dom_name]) if dom_name in prof else None
+    # Rooflines from the live CUDA-event durations of the timed steps: the
+    # dominant kind, and the bandwidth-bound products beside it.
     pk, pk_src = peaks()
-    roof = None
-    if dom is not None:
-        name, d = dom
-        avg_s = d["total_ms"] / d["launches"] / 1e3
-        ach = d["bytes_per_launch"] / avg_s / 1e9
-        roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": round(ach / pk["hbm_gbs"], 4), "traffic": None,
-                "peak_source": pk_src, "launches": d["launches"], "sampled_every": PROF_STRIDE,
-                "avg_us": round(avg_s * 1e6, 2),
-                "share_of_step": round(d["total_ms"] * PROF_STRIDE / ms, 4)}
-        tr = measured_traffic(name)
-        roof["traffic"] = None if tr is None else round(tr)
-        if name.startswith("gemm_tc") or name.startswith("oz_gemm"):
-            # tensor-core product: bytes_per_launch carries its average FLOPs
-            roof["bound"] = "tensor"
-            roof["unit"] = "TFLOP/s"
-            roof["achieved"] = round(d["bytes_per_launch"] / avg_s / 1e12, 2)
-            roof["peak"] = pk["bf16_tflops_sustained"]
-            roof["frac"] = round(roof["achieved"] / roof["peak"], 4)
-            roof["peak_source"] = pk_src + " (sustained bf16)"
-        elif "fp64" in name:
-            roof["bound"] = "alu"
-            roof["unit"] = "TFLOP/s"
-            flops = 2.0 * R.shape[0] * R.shape[1] * (2 if "valgrad" in name or "hvp" in name else 1)
-            roof["achieved"] = round(flops / avg_s / 1e12, 4)
-            roof["peak"] = 1.25
-            roof["frac"] = round(roof["achieved"] / 1.25, 4)
-            roof["peak_source"] = "nominal GB300 FP64 rate (no measured FP64 peak)"
+    # lanes doing useful work: live instance-iterations / (lockstep iterations x lanes)
+    live = statistics.mean(iters) / (statistics.mean(lock) * B) if lock and lock[0] else None
+    roof, secondary = None, []
+    for name, d in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"]):
+        if d["launches"] == 0:
+            continue
+        e = roofline_entry(name, d, pk, pk_src, T, n, ms)
+        if roof is None:
+            roof = e
+            if live is not None:
+                roof["live_lane_fraction"] = round(live, 4)
+                roof["frac_useful"] = round(e["frac"] * live, 4)
+        else:
+            secondary.append(e)
+
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f64" if args.precision == "bf16" else
+            ("fp32+f64" if args.precision == "fp32" else "f64"), "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "T": T, "instances_per_gpu": B,
+                       "targets": 16, "preference_vectors": 4, "configuration": "pcg",
+                       "tol": args.tol, "start": "1/n (cold)",
+                       "l2": "inputs larger than L2: A is 522 MB FP64 + 131 MB BF16",
+                       "parallelism": f"request partition x{world}" if world > 1 else "single device"},
+            "precision": args.precision,
+            "gpu_launches": int(launches), "roofline": roof, "roofline_secondary": secondary, "clocks": clocks,
+            "solve_iterations_per_step": statistics.mean(iters) if iters else None,
+            "lockstep_iterations_per_step": statistics.mean(lock) if lock else None,
+            "request_iterations": {"min": min(i["iters"] for i in infos), "max": max(i["iters"] for i in infos),
+                                   "mean": statistics.mean(i["iters"] for i in infos)},
+            "request_inner_solves": {"min": min(i["evals"] for i in infos), "max": max(i["evals"] for i in infos),
+                                     "mean": statistics.mean(i["evals"] for i in infos)},
+            "unconverged_instances": len(bad)}
 
     e2e = None
     if not args.no_e2e:
         # Same metric through the public API with host buffers: pinned R in,
         # weights out, every step (context creation = H2D copy + centring).
         Rh = torch.from_numpy(R).pin_memory()
-        Wh = torch.empty((B, R.shape[1]), dtype=torch.float64).pin_memory()
+        Wh = torch.empty((B, n), dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
@@ -275,68 +387,110 @@ def run_ours(args, rank, world):
         e2e = {"value": B * args.steps * world / dt, "unit": "solves/s",
                "h2d_bytes_per_step": int(R.nbytes + lam_b.nbytes + tg_b.nbytes),
                "d2h_bytes_per_step": int(Wh.numel() * 8)}
-
-    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f64" if args.precision == "bf16" else
-            ("fp32+f64" if args.precision == "fp32" else "f64"), "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": R.shape[1], "T": R.shape[0], "instances_per_gpu": B,
-                       "targets": 16, "preference_vectors": 4, "configuration": "pcg",
-                       "precision": args.precision, "tol": args.tol, "start": "1/n (cold)",
-                       "l2": "inputs larger than L2: A is 522 MB FP64 + 131 MB BF16",
-                       "parallelism": f"replicas x{world}"},
-            "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "clocks": clocks,
-            "solve_iterations_per_step": statistics.mean(iters) if iters else None,
-            "unconverged_instances": len(bad)}
+        # every request's weights on rank 0, in global order (outside the timed region)
+        Wall = gather_weights(Wh.numpy(), idx, B * world, world)
+        if rank == 0:
+            line["gathered_requests"] = int(np.sum(np.isfinite(Wall).all(axis=1)))
+    line["e2e"] = e2e
+    ctx.close()
+    if rank == 0 and not args.no_plain:
+        # the plain FP64 single-instance path on one request of each preference
+        # vector (targets spread over the grid): the headline ratio's denominator
+        picks = [0, 21, 42, 63][: max(1, min(4, B))]
+        pf = plain_fp64(R, lam_b, tg_b, args.tol, picks)
+        line["plain_fp64"] = pf
+        line["speedup_vs_plain_fp64"] = round(value / world / pf["solves_per_s"], 2)
     if rank == 0 and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args, R, lam_b, tg_b, statistics.mean(iters) / B)
+        line["cpu_baseline"] = cpu_baseline(args, R, lam_b, tg_b)
     line["breakdown_last_warmup_step"] = {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3)}
                                           for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1]["total_ms"])}
     return line
 
 
-def cpu_baseline(args, R, lam_b, tg_b, iters_per_solve):
-    """The oracle, as it stands, on the host cores: a bounded sample of the
-    same workload (a few YAND iterations of instance 0 at its calibrated c1
-    guess), scaled to solves/s by the GPU's iterations per solve."""
-    import numpy as np
+def blas_threads():
+    """Threads the host BLAS uses (the oracle's only parallel part)."""
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        v = os.environ.get(k)
+        if v and v.isdigit():
+            return int(v)
+    return os.cpu_count()
 
+
+def oracle_request_solve(A, mu, lam, target, tol):
+    """One complete calibrated request as the oracle, as it stands, solves it:
+    standardised coefficients, c1 calibrated to the target (Sec. 6), every
+    inner solve Alg. 1 in the PCG configuration.  Returns (seconds, YAND
+    iterations summed over the inner solves, inner solves)."""
+    from oracle import mvsk_oracle as O
+    its = [0]
+
+    def count(it, x, rel):
+        its[0] += 1
+
+    c = O.scale_preferences(lam, A, "standardised")
+    t0 = time.perf_counter()
+    _, _, _, ev = O.calibrate_target(A, mu, c, target, "pcg", tol, opts=None, callback=count)
+    return time.perf_counter() - t0, its[0], ev
+
+
+# Requests of the sweep visited by the CPU legs, in this order: q = 17 i mod
+# 64 walks the four preference vectors and the targets together.
+def cpu_request_order(k, nreq=64):
+    return [(17 * i) % nreq for i in range(k)]
+
+
+def cpu_baseline(args, R, lam_b, tg_b):
+    """The oracle, as it stands, on the host cores: complete calibrated solves
+    of a bounded sample of the sweep's requests (CPU_REQUESTS of them)."""
     from oracle import mvsk_oracle as O
     mu, A = O.centre(R)
-    c = O.scale_preferences(lam_b[0], A, "standardised")
-    its = max(1, args.cpu_sample_its)
-    opts = O.Options(pcg_max_iter=its, restarts=())
-    t0 = time.perf_counter()
-    O.solve(A, mu, c, "pcg", args.tol, opts=opts)
-    dt = time.perf_counter() - t0
-    per_it = dt / (its + 1)
-    return {"value": 1.0 / (per_it * iters_per_solve), "unit": "solves/s", "cores": os.cpu_count(),
-            "kind": "oracle",
-            "sample": f"{its} PCG YAND iteration(s) + final evaluation of instance 0 on the n=5440, T=12000 "
-                      f"panel ({dt:.1f} s, numpy FP64 with its default BLAS threads), scaled by the GPU's "
-                      f"{iters_per_solve:.1f} iterations per calibrated solve"}
+    qs = cpu_request_order(CPU_REQUESTS, len(lam_b))
+    secs, its = 0.0, 0
+    for q in qs:
+        dt, it, _ = oracle_request_solve(A, mu, lam_b[q], tg_b[q], args.tol)
+        secs += dt
+        its += it
+    return {"value": len(qs) / secs, "unit": "solves/s", "cores": blas_threads(), "kind": "oracle",
+            "sample": f"complete calibrated oracle solves of requests {qs} of the sweep (numpy FP64, "
+                      f"{blas_threads()} BLAS threads): {secs:.1f} s, {its} YAND iterations"}
+
+
+CPU_REQUESTS = 2
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step is one complete calibrated
+    solve of one request of the sweep (requests in cpu_request_order), timed
+    with the wall clock; W untimed steps first."""
     if rank != 0:
         return None
-    R, lam_b, tg_b = instances(args.batch)
-    cb = None
-    times = []
-    for _ in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        cb = cpu_baseline(args, R, lam_b, tg_b, iters_per_solve=90.0)
-        times.append(time.perf_counter() - t0)
-    v = cb["value"]
+    from oracle import mvsk_oracle as O
+    R, lam_b, tg_b, _ = instances(args.batch)
+    mu, A = O.centre(R)
+    order = cpu_request_order(args.warmup + args.steps, len(lam_b))
+    times, its = [], 0
+    for k, q in enumerate(order):
+        dt, it, _ = oracle_request_solve(A, mu, lam_b[q], tg_b[q], args.tol)
+        if k >= args.warmup:
+            times.append(dt)
+            its += it
+    secs = sum(times)
+    v = len(times) / secs if secs > 0 else None
+    timed = order[args.warmup:]
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, len(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": R.shape[1], "T": R.shape[0], "instances_per_gpu": len(lam_b),
-                       "configuration": "pcg", "precision": "fp64 (CPU oracle)", "tol": args.tol},
-            "cpu_baseline": {**cb, "value": v},
+                       "targets": 16, "preference_vectors": 4, "configuration": "pcg",
+                       "tol": args.tol, "start": "1/n (cold)",
+                       "l2": "inputs larger than L2: A is 522 MB FP64 + 131 MB BF16",
+                       "parallelism": "single device"},
+            "precision": "fp64 (CPU oracle)",
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": blas_threads(), "kind": "oracle",
+                             "sample": f"one complete calibrated oracle solve per step, requests {timed} "
+                                       f"({its} YAND iterations in {secs:.1f} s)"},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "note": "the CPU oracle timed on a bounded sample per step (90 iterations per calibrated solve "
-                    "assumed for scaling)"}
+            "note": "the CPU oracle (numpy FP64) as it stands: there is no other reference implementation"}
 
 
 # The paper's published YAND-MVSK means on its synthetic benchmark (Table
