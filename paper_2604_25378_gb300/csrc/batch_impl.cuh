@@ -805,13 +805,35 @@ struct InstRun {
   double lam[4] = {0, 0, 0, 0}, target = NAN;
   std::array<double, 4> cc{};
   int phase = 0;
-  int cal = 0;  // 0 no target, 1 lower-end solve, 2 growing, 3 Illinois
+  // 0 no target, 1 lower-end solve, 2 growing, 3 Illinois, 4 first solve at
+  // a point of its group's c1 grid, 5 waiting for the rest of that grid
+  int cal = 0;
   double c_lo = 0, c_hi = 0, h_lo = 0, h_hi = 0, c1_ref = 0, c1_max = 0;
   int side = 0, evals = 0, iters = 0, restarts = 0;
   int run_status = MVSK_OK;
   bool finished = false, final_from_hi = false;
   std::chrono::steady_clock::time_point t_start;
   double ev[3] = {0, 0, 0};
+  double kkt0 = NAN;  // kkt_rel normaliser when the result is another lane's grid point
+};
+
+// Requests of one lockstep batch that share (c2, c3, c4) and each carry a
+// return target trace one curve m(c1) = mu^T x*(c1) (non-decreasing in c1).
+// Their first inner solves run at the points of a c1 grid, one per request:
+// c1 = 0 for the lowest target and c1_ref 2^(-6 .. 2) log-spaced for the
+// others (c1_ref: the c1 at which mean and variance trade evenly), all from
+// 1/n.  Every finished grid point (c1, its minimiser and z = A x*) is kept,
+// and each request brackets its own target from the whole grid before the
+// same Illinois iteration as a single request (or the growth x8 when the grid
+// stays below its target).  The root is the one each request would reach
+// alone: the calibration stops on the same tests.
+struct GroupPt {
+  double c1, mean, f, kkt, kkt0;
+  int slot;  // lane whose pool slot holds x*(c1) and z
+};
+struct CalGroup {
+  std::vector<GroupPt> pts;
+  int pending = 0;  // grid solves not finished yet
 };
 
 // Start an inner solve of instance b at c1 from warm start w0 (device vector or
@@ -1042,6 +1064,52 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       }
     }
   }
+  // Calibration groups (see CalGroup): every request has its own lane and no
+  // user warm start, with split products (the grid points keep their cached z).
+  std::vector<int> group_of((size_t)B, -1);
+  std::vector<double> grid_c1((size_t)B, 0.0);
+  std::vector<CalGroup> groups;
+  if (o.group_cal && split && L == B && hw.empty()) {
+    std::vector<int> idx;
+    for (int q = 0; q < B; ++q)
+      if (!isnan(req[(size_t)q].target)) idx.push_back(q);
+    std::vector<char> used((size_t)B, 0);
+    for (int q : idx) {
+      if (used[(size_t)q]) continue;
+      std::vector<int> mem;
+      for (int p2 : idx)
+        if (!used[(size_t)p2] && ccq[(size_t)p2][1] == ccq[(size_t)q][1] && ccq[(size_t)p2][2] == ccq[(size_t)q][2] &&
+            ccq[(size_t)p2][3] == ccq[(size_t)q][3]) {
+          mem.push_back(p2);
+          used[(size_t)p2] = 1;
+        }
+      if (mem.size() < 2) continue;
+      std::stable_sort(mem.begin(), mem.end(),
+                       [&](int a, int b2) { return req[(size_t)a].target < req[(size_t)b2].target; });
+      const int G = (int)mem.size();
+      for (int k = 0; k < G; ++k) {
+        group_of[(size_t)mem[(size_t)k]] = (int)groups.size();
+        const double e = G == 2 ? 0.0 : -6.0 + 8.0 * (double)(k - 1) / (double)(G - 2);
+        grid_c1[(size_t)mem[(size_t)k]] = k == 0 ? 0.0 : req[(size_t)mem[(size_t)k]].c1_ref * exp2(e);
+      }
+      CalGroup g;
+      g.pending = G;
+      groups.push_back(g);
+    }
+    if (!groups.empty() && bb.gcap < B) {
+      if (bb.gpool != nullptr) cudaFree(bb.gpool);
+      bb.gpool = nullptr;
+      bb.gcap = 0;
+      if (cudaMalloc(&bb.gpool, sizeof(double) * (ld + (size_t)c->T) * (size_t)B) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MVSK_ENOMEM, "calibration grid buffer allocation failed");
+      }
+      bb.gcap = B;
+    }
+  }
+  // pool slot of lane b: a grid point's x* (ld) and its cached z (T)
+  auto gx = [&](int b) { return bb.gpool + (size_t)b * (ld + (size_t)c->T); };
+  auto gz = [&](int b) { return gx(b) + ld; };
   // request q into lane b: its state, its G0 and warm start, and the first inner solve
   int next_req = 0;
   auto assign = [&](int b) -> mvsk_status {
@@ -1062,6 +1130,10 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       r.cal = 0;
       return batch_start_run(c, bb, b, r, r.cc[0], w0, tol,
                              (w0 != nullptr && split) ? bb.Zq + (size_t)q * c->T : nullptr);
+    }
+    if (group_of[(size_t)q] >= 0) {
+      r.cal = 4;
+      return batch_start_run(c, bb, b, r, grid_c1[(size_t)q], nullptr, tol, nullptr);
     }
     r.cal = 1;
     return batch_start_run(c, bb, b, r, 0.0, nullptr, tol, nullptr);
@@ -1089,7 +1161,8 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     if (infos != nullptr) {
       CU(cudaMemcpyAsync(hx.data(), s.x, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream));
       double k0 = 0.0;
-      CU(cudaMemcpyAsync(&k0, s.sd + SD_KKT0, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      if (isnan(r.kkt0))
+        CU(cudaMemcpyAsync(&k0, s.sd + SD_KKT0, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       int cnt[kSI];
       CU(cudaMemcpyAsync(cnt, s.si, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
       TRY(sync(c));
@@ -1102,6 +1175,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       inf.evals = r.evals;
       inf.f = r.ev[0];
       inf.kkt_residual = r.ev[1];
+      if (!isnan(r.kkt0)) k0 = r.kkt0;
       inf.kkt0 = k0;
       inf.kkt_rel = r.ev[1] / fmax(k0, 1e-300);
       for (int k = 0; k < 4; ++k) inf.c[k] = r.cc[k];
@@ -1148,7 +1222,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     std::vector<int> fin;
     for (int b = 0; b < L; ++b) {
       InstRun& r = run[(size_t)b];
-      if (lane_req[(size_t)b] < 0 || r.finished) continue;
+      if (lane_req[(size_t)b] < 0 || r.finished || r.cal == 5) continue;
       const int done = si[(size_t)b * kSI + SI_DONE];
       if (done == 0) {
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - r.t_start).count();
@@ -1198,30 +1272,107 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     }
     TRY(sync(c));
     std::vector<int> freed;
+    auto finish_b = [&](int b, bool from_hi) -> mvsk_status {
+      InstRun& r = run[(size_t)b];
+      if (from_hi) {
+        CU(cudaMemcpyAsync(inst_at(bb.base, b).x, xhi(b), sizeof(double) * ld, cudaMemcpyDeviceToDevice, c->stream));
+        r.cc[0] = r.c_hi;
+        r.final_from_hi = true;
+      }
+      r.finished = true;
+      remaining -= 1;
+      freed.push_back(b);
+      return MVSK_OK;
+    };
+    auto illinois_b = [&](int b) -> mvsk_status {
+      InstRun& r = run[(size_t)b];
+      if (r.evals >= o.cal_max_evals) return finish_b(b, true);
+      double cm = r.c_hi - r.h_hi * (r.c_hi - r.c_lo) / (r.h_hi - r.h_lo);
+      if (!(r.c_lo < cm && cm < r.c_hi)) cm = 0.5 * (r.c_lo + r.c_hi);
+      const bool lo = (cm - r.c_lo) <= (r.c_hi - cm);
+      r.cal = 3;
+      return batch_start_run(c, bb, b, r, cm, lo ? xlo(b) : xhi(b), tol, split ? (lo ? zlo(b) : zhi(b)) : nullptr);
+    };
+    // A grid request's next step from every finished point of its group: the
+    // result itself when a point meets the target (c1 = 0 when its mean is
+    // already high enough), else the tightest bracket for Illinois, else the
+    // growth from the highest point once the grid is complete; it waits while
+    // points that could bracket it are still running.
+    auto group_decide = [&](int b) -> mvsk_status {
+      InstRun& r = run[(size_t)b];
+      const CalGroup& G = groups[(size_t)group_of[(size_t)lane_req[(size_t)b]]];
+      const GroupPt *lo = nullptr, *hi = nullptr, *hit = nullptr, *zero = nullptr;
+      for (const GroupPt& p : G.pts) {
+        const double hp = p.mean - r.target;
+        if (p.c1 == 0.0) zero = &p;
+        if (fabs(hp) <= gap_tol && (hit == nullptr || fabs(hp) < fabs(hit->mean - r.target))) hit = &p;
+        if (hp < 0.0) {
+          if (lo == nullptr || p.c1 > lo->c1) lo = &p;
+        } else if (hi == nullptr || p.c1 < hi->c1) {
+          hi = &p;
+        }
+      }
+      const Inst s = inst_at(bb.base, b);
+      auto take = [&](const GroupPt& p) -> mvsk_status {  // p is this request's result
+        if (p.slot != b)
+          CU(cudaMemcpyAsync(s.x, gx(p.slot), sizeof(double) * ld, cudaMemcpyDeviceToDevice, c->stream));
+        r.cc[0] = p.c1;
+        r.ev[0] = p.f;
+        r.ev[1] = p.kkt;
+        r.ev[2] = p.mean;
+        r.kkt0 = p.kkt0;
+        return finish_b(b, false);
+      };
+      auto keep = [&](const GroupPt& p, double* xd, double* zd) -> mvsk_status {
+        CU(cudaMemcpyAsync(xd, gx(p.slot), sizeof(double) * ld, cudaMemcpyDeviceToDevice, c->stream));
+        CU(cudaMemcpyAsync(zd, gz(p.slot), sizeof(double) * c->T, cudaMemcpyDeviceToDevice, c->stream));
+        return MVSK_OK;
+      };
+      if (zero != nullptr && zero->mean - r.target >= -gap_tol) return take(*zero);
+      if (hit != nullptr) return take(*hit);
+      if (lo != nullptr && hi != nullptr) {
+        r.c_lo = lo->c1;
+        r.h_lo = lo->mean - r.target;
+        r.c_hi = hi->c1;
+        r.h_hi = hi->mean - r.target;
+        TRY(keep(*lo, xlo(b), zlo(b)));
+        TRY(keep(*hi, xhi(b), zhi(b)));
+        if (r.c_hi - r.c_lo <= o.cal_bracket_tol * r.c_hi) return take(*hi);
+        r.side = 0;
+        return illinois_b(b);
+      }
+      if (G.pending > 0) {  // the rest of the grid may still bracket the target
+        r.cal = 5;
+        return MVSK_OK;
+      }
+      if (lo == nullptr) {  // no point below the target (c1 = 0 did not finish): the single-request path
+        r.cal = 1;
+        return batch_start_run(c, bb, b, r, 0.0, nullptr, tol, nullptr);
+      }
+      if (lo->c1 >= r.c1_max) return take(*lo);
+      r.c_lo = lo->c1;
+      r.h_lo = lo->mean - r.target;
+      TRY(keep(*lo, xlo(b), zlo(b)));
+      r.c_hi = lo->c1 > 0.0 ? fmin(8.0 * lo->c1, r.c1_max) : (r.lam[0] > 0.0 ? (stdz ? r.lam[0] / s_eq : r.lam[0]) : r.c1_ref);
+      r.cal = 2;
+      return batch_start_run(c, bb, b, r, r.c_hi, xlo(b), tol, zlo(b));
+    };
     for (int b : fin) {
       InstRun& r = run[(size_t)b];
       const Inst s = inst_at(bb.base, b);
       for (int q = 0; q < 3; ++q) r.ev[q] = evh[4 * (size_t)b + q];
       const double h = r.ev[2] - r.target;
-      auto finish = [&](bool from_hi) -> mvsk_status {
-        if (from_hi) {
-          CU(cudaMemcpyAsync(s.x, xhi(b), sizeof(double) * ld, cudaMemcpyDeviceToDevice, c->stream));
-          r.cc[0] = r.c_hi;
-          r.final_from_hi = true;
-        }
-        r.finished = true;
-        remaining -= 1;
-        freed.push_back(b);
-        return MVSK_OK;
-      };
-      auto illinois = [&]() -> mvsk_status {
-        if (r.evals >= o.cal_max_evals) return finish(true);
-        double cm = r.c_hi - r.h_hi * (r.c_hi - r.c_lo) / (r.h_hi - r.h_lo);
-        if (!(r.c_lo < cm && cm < r.c_hi)) cm = 0.5 * (r.c_lo + r.c_hi);
-        const bool lo = (cm - r.c_lo) <= (r.c_hi - cm);
-        r.cal = 3;
-        return batch_start_run(c, bb, b, r, cm, lo ? xlo(b) : xhi(b), tol, split ? (lo ? zlo(b) : zhi(b)) : nullptr);
-      };
+      auto finish = [&](bool from_hi) -> mvsk_status { return finish_b(b, from_hi); };
+      auto illinois = [&]() -> mvsk_status { return illinois_b(b); };
+      if (r.cal == 4) {  // a grid point: into the group's pool, then the request's next step
+        CalGroup& G = groups[(size_t)group_of[(size_t)lane_req[(size_t)b]]];
+        CU(cudaMemcpyAsync(gx(b), s.x, sizeof(double) * ld, cudaMemcpyDeviceToDevice, c->stream));
+        CU(cudaMemcpyAsync(gz(b), s.z, sizeof(double) * c->T, cudaMemcpyDeviceToDevice, c->stream));
+        G.pts.push_back({r.cc[0], r.ev[2], r.ev[0], r.ev[1], evh[4 * (size_t)b + 3], b});
+        G.pending -= 1;
+        r.cal = 5;
+        continue;  // decided below, with every point of this round in the pool
+      }
       if (r.cal == 0) {
         TRY(finish(false));
       } else if (r.cal == 1) {
@@ -1277,6 +1428,9 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
         }
       }
     }
+    // grid requests waiting for their group's points
+    for (int b = 0; b < L; ++b)
+      if (lane_req[(size_t)b] >= 0 && !run[(size_t)b].finished && run[(size_t)b].cal == 5) TRY(group_decide(b));
     // finished requests: results out, next requests in (their lanes idle once the queue is empty)
     for (int b : freed) {
       TRY(emit(b));

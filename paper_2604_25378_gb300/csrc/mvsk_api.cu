@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <array>
 #include <chrono>
 #include <string>
@@ -35,6 +36,7 @@ struct Options {
   int split_products = 1;  // batched solves: FP64 products on the tensor cores (ozaki.cuh)
   int batch_lanes = 0;     // batched solves: concurrent instances (0: all requests at once)
   int line_search = 0;     // 0 exact quartic step, 1 Armijo backtracking on the quartic
+  int group_cal = 1;       // batched solves: requests sharing (c2, c3, c4) start calibration on a c1 grid
   unsigned long long probe_seed = 0x5EEDull;
 };
 
@@ -64,6 +66,8 @@ struct BatchBuf {
   double* Wq = nullptr;     // user warm starts of the requests (wcap x ld) ...
   double* Zq = nullptr;     // ... and their A w0 (wcap x T)
   int wcap = 0;
+  double* gpool = nullptr;  // calibration grid points: x* (ld) and z (T) per lane
+  int gcap = 0;
   int qcap = 0;
 };
 
@@ -1456,6 +1460,7 @@ mvsk_status mvsk_set_option(mvsk_ctx* c, const char* key, double v) {
   else if (k == "split_products" && cnt(v, 0, 1)) o.split_products = (int)v;
   else if (k == "batch_lanes" && cnt(v, 0, 1000000)) o.batch_lanes = (int)v;
   else if (k == "line_search" && cnt(v, 0, 1)) o.line_search = (int)v;
+  else if (k == "group_calibration" && cnt(v, 0, 1)) o.group_cal = (int)v;
   else return fail(MVSK_EINVAL, "unknown option or bad value: %s = %g", key, v);
   if (c->prefs_set && k == "pref_scaling") mvsk_set_prefs(c, c->lam, c->target);
   return MVSK_OK;
@@ -1790,6 +1795,7 @@ void mvsk_destroy(mvsk_ctx* c) {
   if (c->batch.Gq != nullptr) cudaFree(c->batch.Gq);
   if (c->batch.Wq != nullptr) cudaFree(c->batch.Wq);
   if (c->batch.Zq != nullptr) cudaFree(c->batch.Zq);
+  if (c->batch.gpool != nullptr) cudaFree(c->batch.gpool);
   if (c->own_stream != nullptr) cudaStreamDestroy(c->own_stream);
   delete c;
 }

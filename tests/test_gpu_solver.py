@@ -289,3 +289,54 @@ def test_batch_lanes_queue_matches_all_at_once():
     assert np.all(its_w[free] <= 3), its_w[free]
     assert np.all(its_w[free] < its_c[free])
     ctx.set_option("batch_lanes", 0)
+
+
+def test_group_calibration_matches_per_request():
+    """Requests that share (c2, c3, c4) and carry targets start their mean-
+    coefficient calibration on a shared c1 grid (option group_calibration, on
+    by default): each request must reach the same calibrated c1 and weights as
+    when every request runs its own sequence from c1 = 0.  The targets include
+    one met at c1 = 0 (below the minimum-risk portfolio's mean), ones inside
+    the grid and one beyond its top (growth), on two preference vectors; a
+    request without a target shares the batch."""
+    import paper_2604_25378_gb300 as m
+    R = panels.garch_sector_panel(300, 3000, 31)
+    mu, A = O.centre(R)
+    qs = panels.quantile_targets(R, [0.5, 0.7, 0.8, 0.9, 0.97, 0.995])
+    lams, tgs = [], []
+    for lam in [(1.0, 1.0, 0.5, 2.0), (1.0, 1.0, 2.0, 2.0)]:
+        c = O.scale_preferences(lam, A, "standardised")
+        c0 = c.copy()
+        c0[0] = 0.0
+        x0, _ = O.solve(A, mu, c0, "pcg", 1e-10)
+        low = float(mu @ x0) - 0.1 * float(np.std(mu))       # met at c1 = 0
+        for t in [low, *qs]:
+            lams.append(lam)
+            tgs.append(t)
+    lams.append((1.0, 1.0, 0.5, 2.0))
+    tgs.append(np.nan)
+    lams, tgs = np.asarray(lams), np.asarray(tgs)
+    ctx = m.MVSK(R, "bf16")
+    W1, inf1 = ctx.solve_batch(lams, tgs, m.PCG, 1e-10)
+    ctx.set_option("group_calibration", 0)
+    W0, inf0 = ctx.solve_batch(lams, tgs, m.PCG, 1e-10)
+    ctx.set_option("group_calibration", 1)
+    assert all(i["status"] == "ok" for i in inf1 + inf0)
+    scale = np.max(np.abs(mu))
+    for b in range(len(tgs)):
+        c1g, c10 = inf1[b]["c"][0], inf0[b]["c"][0]
+        if not np.isnan(tgs[b]):
+            assert abs(inf1[b]["achieved_mean"] - tgs[b]) <= 1e-9 * scale or c1g == 0.0, b
+        assert abs(c1g - c10) <= 1e-6 * max(c10, 1e-300) or (c1g == 0.0 and c10 == 0.0), (b, c1g, c10)
+        assert np.max(np.abs(W1[b] - W0[b])) <= 1e-8, (b, np.max(np.abs(W1[b] - W0[b])))
+        cg = np.asarray(inf1[b]["c"])
+        x0 = np.full(A.shape[1], 1.0 / A.shape[1])
+        k0 = O.kkt_residual(x0, O.gradient(A, mu, cg, x0), 1e-8)
+        assert O.kkt_residual(W1[b], O.gradient(A, mu, cg, W1[b]), 1e-8) <= 1.5e-10 * k0, b
+        assert inf1[b]["kkt0"] == pytest.approx(k0, rel=1e-9), b
+    assert inf1[0]["c"][0] == 0.0 and inf1[7]["c"][0] == 0.0   # the low targets
+    # the oracle's calibration of one grid request
+    b = 3
+    c = O.scale_preferences(lams[b], A, "standardised")
+    cc, x_ref, _, _ = O.calibrate_target(A, mu, c, tgs[b], "pcg", 1e-12, rel_tol=1e-12)
+    assert np.max(np.abs(W1[b] - x_ref)) <= 1e-7
