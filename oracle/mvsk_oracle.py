@@ -27,9 +27,9 @@ the design notes of the repository):
   * KKT residual: ||x - Pi_{Delta(tau)}(x - grad f)||_2, relative to its
     value at x0 = 1/n.
   * Face continuation: the coordinates at tau form the active face, except
-    the most violating one (largest nu_F - g_i > 0, nu_F the mean of g over
-    the coordinates above tau), released once ||gbar_F||_2 <= 0.5 of that
-    violation.
+    every one whose violation nu_F - g_i (nu_F the mean of g over the
+    coordinates above tau) is positive and at least 2 ||gbar_F||_2 (release
+    ratio 0.5): those are released together.
   * Stall (PCG): max_iter reached or kkt not reduced by 1% over 10
     iterations; restarts at projected step 0.045 then 0.02 (120 its each).
     The 1% test only triggers restarts: the last phase runs to the
@@ -631,22 +631,22 @@ def _ls_step(A, mu, c, x, z, d, amax, rule="exact"):
 def working_set(x, g, opts: Options, counts=None):
     """Active face of the boundary block (face continuation reading).
 
-    Every coordinate at tau is held at tau, except the most violating one
-    (largest nu_F - g_i > 0, nu_F the mean of g over the coordinates above
-    tau), which is released once ||gbar_F||_2 <= release_ratio * violation.
-    Returns the boolean mask of held coordinates.
+    Every coordinate at tau is held at tau, except those whose violation
+    nu_F - g_i (nu_F the mean of g over the coordinates above tau) is
+    positive and at least ||gbar_F||_2 / release_ratio: they are released
+    together.  Returns the boolean mask of held coordinates.
     """
     bound = x - opts.tau <= opts.eps_act
     F = ~bound
     nuF = float(np.mean(g[F]))
     gn = float(np.linalg.norm(g[F] - nuF))
     viol = np.where(bound, nuF - g, -math.inf)
-    j = int(np.argmax(viol))
-    if bound[j] and viol[j] > 0.0 and gn <= opts.release_ratio * viol[j]:
+    rel = bound & (viol > 0.0) & (gn <= opts.release_ratio * viol)
+    if np.any(rel):
         bound = bound.copy()
-        bound[j] = False
+        bound[rel] = False
         if counts is not None:
-            counts["release"] += 1
+            counts["release"] += int(np.sum(rel))
     return bound
 
 
@@ -807,7 +807,10 @@ def calibrate_target(A, mu, c, target, config="direct", tol=1e-8, opts=None,
     c1 = 0.  The upper end starts at c[0] (or c2 s^2 / max|mu| with s^2 = m2(1/n)
     when c[0] = 0) and grows x8 until the target is bracketed or c1_max =
     1e6 c2 s^2 / max|mu| is reached (then c1 = c1_max).  Each solve is warm-
-    started from the nearest bracket end.  `callback` is handed to every
+    started from the nearest bracket end.  Illinois stops at |gap| <= rel_tol
+    max|mu|, at a relative bracket width of bracket_tol, or at an inner solve
+    that needs no iteration from its warm start with |gap| within ten gap
+    tolerances (the inner tolerance then resolves the mean no finer).  `callback` is handed to every
     inner solve.  Returns (c, x, info, evals).
     """
     c = np.asarray(c, dtype=np.float64).copy()
@@ -857,7 +860,11 @@ def calibrate_target(A, mu, c, target, config="direct", tol=1e-8, opts=None,
         w0 = x_lo if (cm - c_lo) <= (c_hi - cm) else x_hi
         xm, infm, hm = run(cm, w0)
         evals += 1
-        if abs(hm) <= gap_tol or (c_hi - c_lo) <= bracket_tol * c_hi:
+        # an inner solve that needs no iteration from its warm start cannot
+        # resolve mu^T x*(c1) any finer: its point ends the calibration when
+        # its gap is within ten gap tolerances
+        if (abs(hm) <= gap_tol or (infm.iters == 0 and abs(hm) <= 10.0 * gap_tol)
+                or (c_hi - c_lo) <= bracket_tol * c_hi):
             c[0] = cm
             return c, xm, infm, evals
         if hm < 0.0:

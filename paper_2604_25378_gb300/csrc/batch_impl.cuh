@@ -815,6 +815,7 @@ struct InstRun {
   std::chrono::steady_clock::time_point t_start;
   double ev[3] = {0, 0, 0};
   double kkt0 = NAN;  // kkt_rel normaliser when the result is another lane's grid point
+  int last_its = -1;  // iterations of the last finished inner solve
 };
 
 // Requests of one lockstep batch that share (c2, c3, c4) and each carry a
@@ -1247,6 +1248,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       }
       r.run_status = d2 == 1 ? MVSK_OK : (d2 == 3 ? MVSK_ENUMERIC : (d2 == 4 ? MVSK_ETIMEOUT : MVSK_ENOTCONVERGED));
       r.iters += si[(size_t)b * kSI + SI_ITER];
+      r.last_its = si[(size_t)b * kSI + SI_ITER];
       const Inst s = inst_at(bb.base, b);
       if (r.run_status != MVSK_OK) CU(cudaMemcpyAsync(s.x, s.bestx, sizeof(double) * ld, cudaMemcpyDeviceToDevice, c->stream));
       fin.push_back(b);
@@ -1406,7 +1408,10 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
         }
       } else {
         const double cm = r.cc[0];
-        if (fabs(h) <= gap_tol || (r.c_hi - r.c_lo) <= o.cal_bracket_tol * r.c_hi) {
+        // a solve that needed no iteration from its warm start resolves the
+        // mean no finer: its point ends the calibration near the target
+        if (fabs(h) <= gap_tol || (r.last_its == 0 && fabs(h) <= 10.0 * gap_tol) ||
+            (r.c_hi - r.c_lo) <= o.cal_bracket_tol * r.c_hi) {
           TRY(finish(false));
         } else {
           if (h < 0.0) {

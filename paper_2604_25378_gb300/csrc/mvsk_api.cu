@@ -1155,7 +1155,7 @@ mvsk_status solve_with_target(mvsk_ctx* c, int cfg, double tol, const double* w0
   const size_t vb = sizeof(double) * c->ld;
   double* xlo = in.tmp + (size_t)20 * c->ld;
   double* xhi = xlo + c->ld;
-  int evals = 0, iters = 0, restarts = 0;
+  int evals = 0, iters = 0, restarts = 0, last_it = -1;
   SolveOut so;
   double ev[3];
   auto run = [&](double c1, const double* w0, double* h) -> mvsk_status {
@@ -1165,6 +1165,7 @@ mvsk_status solve_with_target(mvsk_ctx* c, int cfg, double tol, const double* w0
     int it = 0;
     TRY(read_ints(c, &it, SI_ITER, 1));
     iters += it;
+    last_it = it;
     restarts += o.restarts;
     so = o;
     evals += 1;
@@ -1207,7 +1208,11 @@ mvsk_status solve_with_target(mvsk_ctx* c, int cfg, double tol, const double* w0
           double hm;
           TRY(run(cm, w0, &hm));
           cc[0] = cm;
-          if (fabs(hm) <= gap_tol || (c_hi - c_lo) <= c->opt.cal_bracket_tol * c_hi) break;
+          // a solve that needed no iteration from its warm start resolves the
+          // mean no finer: its point ends the calibration near the target
+          if (fabs(hm) <= gap_tol || (last_it == 0 && fabs(hm) <= 10.0 * gap_tol) ||
+              (c_hi - c_lo) <= c->opt.cal_bracket_tol * c_hi)
+            break;
           if (hm < 0.0) {
             c_lo = cm;
             h_lo = hm;

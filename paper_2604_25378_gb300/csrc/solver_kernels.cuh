@@ -89,8 +89,6 @@ static __global__ void __launch_bounds__(kVT) k_eval_finish(Inst s0, const doubl
 static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spart, int G) {
   Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
-  __shared__ double sv[33];
-  __shared__ int si_[33];
   __shared__ double ps[2];
   __shared__ int s_stop;
   int* SI = s.si;
@@ -156,8 +154,8 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
     __syncthreads();
     if (s_stop) return;
   }
-  // Working face: coordinates at tau are held, except the most violating one,
-  // released once ||gbar_F|| <= release_ratio * violation.
+  // Working face: coordinates at tau are held, except every one whose
+  // violation nu_F - g_i is at least ||gbar_F|| / release_ratio.
   const double eps = SD[SD_EPSACT];
   double sg = 0.0, cf = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x)
@@ -165,27 +163,22 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
       sg += s.g[i];
       cf += 1.0;
     }
-  double nuF = block_sum2_fin(sg, cf, scr, [](double x, double y) { return make_double2(x / y, 0.0); }).z;
+  const double4 r1 = block_sum2_fin(sg, cf, scr, [](double x, double y) { return make_double2(x / y, 0.0); });
+  double nuF = r1.z;
+  const double free0 = r1.y;  // coordinates above tau
   double gq = 0.0;
-  double best = -INFINITY;
-  int bidx = 0x7fffffff;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
     if (s.x[i] - tau > eps) {
       const double e = s.g[i] - nuF;
       gq += e * e;
-    } else {
-      const double v = nuF - s.g[i];
-      if (v > best || (v == best && i < bidx)) {
-        best = v;
-        bidx = i;
-      }
     }
-  }
   const double gn0 = block_sum2_fin(gq, 0.0, scr, [](double x, double) { return make_double2(sqrt(x), 0.0); }).z;
-  block_argmax(best, bidx, sv, si_);
-  const bool rel_ok = bidx != 0x7fffffff && best > 0.0 && gn0 <= SD[SD_RELRATIO] * best;
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    s.maskF[i] = (s.x[i] - tau > eps || (rel_ok && i == bidx)) ? 1.0 : 0.0;
+  const double rr = SD[SD_RELRATIO];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const bool held = !(s.x[i] - tau > eps);
+    const double v = nuF - s.g[i];
+    s.maskF[i] = (!held || (v > 0.0 && gn0 <= rr * v)) ? 1.0 : 0.0;
+  }
   __syncthreads();
   sg = 0.0;
   cf = 0.0;
@@ -229,7 +222,7 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
     SD[SD_NUF] = nuF;
     SI[SI_M] = mi;
     SI[SI_SKIPDIR] = trivial ? 1 : 0;
-    if (rel_ok) SI[SI_NREL] += 1;
+    SI[SI_NREL] += mi - (int)free0;  // coordinates released this iteration
   }
 }
 
