@@ -227,7 +227,9 @@ def roofline_entry(name, d, pk, pk_src, T, n, ms_step):
                   "algorithmic_bytes": byt, "fp64_equivalent_gbs": round(8.0 * T * n / avg_s / 1e9, 1),
                   "peak_source": pk_src})
     elif name == "gemm_tc_bf16_n64":
-        byt = 2.0 * T * n
+        # the BF16 operand read once: FLOPs / N bytes (2 T K for K columns of A;
+        # K = |U| on the face-restricted path, which the profiler counts per launch)
+        byt = d["bytes_per_launch"] / 64.0
         e.update({"bound": "hbm", "unit": "GB/s", "achieved": round(byt / avg_s / 1e9, 1), "peak": pk["hbm_gbs"],
                   "algorithmic_bytes": byt, "peak_source": pk_src})
     elif name.startswith("gemm_tc"):

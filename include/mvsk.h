@@ -124,6 +124,11 @@ mvsk_status mvsk_set_prefs(mvsk_ctx* ctx, const double lambda[4], double target)
  *   with 0 < L < B and split products: L lanes, a lane whose request has
  *   finished takes the next one, so throughput follows the mean iteration
  *   count rather than the slowest request of each batch),
+ *   "group_calibration" (1: in mvsk_solve_batch, requests sharing (c2, c3,
+ *   c4) with targets start their calibration on a shared c1 grid; 0: each
+ *   request alone), "face_products" (1: in mvsk_solve_batch the direction
+ *   products run on the union of the instances' working faces; 0: on all
+ *   n columns of A),
  *   "line_search" (0: exact quartic step, Prop. quartic exact line search;
  *   1: Armijo backtracking on the same quartic, the paper's Armijo diagnostic
  *   of Table yand-line-search: the largest alpha_max 2^-j, j < 60, with
@@ -224,40 +229,47 @@ mvsk_status mvsk_product(mvsk_ctx* ctx, int32_t transpose, int32_t nvec, const d
 /*
  * mvsk_batch_hvp -- the direction products of one lockstep iteration of
  *   mvsk_solve_batch, for parity tests, on caller-given operands: B instances
- *   with coefficients C (B x 4, c1..c4) at points X (B x n), each with nc
+ *   with coefficients C (B x 4, c1..c4) at points X (B x n), working faces
+ *   maskF (B x n, 1 free / 0 held; NULL: every coordinate free), each with nc
  *   columns V (B x nc x n, column j of instance b at V + (b*nc + j)*n).
  *   With z_b = A x_b (FP64) and G_b = T^-1 A^T Diag(psi''_b(z_b)) A (Prop. 2):
  *     HV[b][j]  = G_b v_bj  (Eq. operator-hvp), B x nc x n;
  *     Gnu[b]    = G_b nuhat_b, nuhat: B x n;      diagG[b] = diag(G_b), B x n.
  *   They run exactly as in the solve: A in BF16 with FP32 accumulation on the
  *   tensor cores (psi'' in FP32; v, nuhat and the weighted rows rounded to
- *   BF16), the B*nc columns side by side in one product.  path[0] (nullable)
- *   receives 1 when the first product A V took the fused psi''-weighting
- *   epilogue, 0 when it took split-K partials and a separate weighting pass;
- *   path[1] the split-K count of the second product A^T S.  Arguments are
- *   host or device pointers.  Needs a MVSK_PREC_MIXED_BF16 context; 1 <= nc
- *   <= 16, 1 <= B <= 4096.  Uses the batch buffers of mvsk_solve_batch and a
- *   scratch allocation released before returning.  Errors: EINVAL, ENOMEM,
- *   ECUDA.
+ *   BF16), the B*nc columns side by side in one product.  With option
+ *   "face_products" = 1 (default) the products are restricted, as in the
+ *   solve, to the union U of the faces: the caller's v_bj and nuhat_b must
+ *   then be zero off face b, and the three outputs are given on U (zero
+ *   elsewhere).  path[0] (nullable) receives 1 when the first product A V
+ *   took the fused psi''-weighting epilogue, 0 when it took split-K partials
+ *   and a separate weighting pass; path[1] the split-K count of the second
+ *   product A^T S.  Arguments are host or device pointers.  Needs a
+ *   MVSK_PREC_MIXED_BF16 context; 1 <= nc <= 16, 1 <= B <= 4096.  Uses the
+ *   batch buffers of mvsk_solve_batch and a scratch allocation released
+ *   before returning.  Errors: EINVAL, ENOMEM, ECUDA.
  */
 mvsk_status mvsk_batch_hvp(mvsk_ctx* ctx, int32_t B, const double* C, const double* X,
-                           const double* nuhat, int32_t nc, const double* V, double* HV,
-                           double* Gnu, double* diagG, int32_t path[2]);
+                           const double* nuhat, const double* maskF, int32_t nc, const double* V,
+                           double* HV, double* Gnu, double* diagG, int32_t path[2]);
 
 /*
  * mvsk_batch_third -- the Hutchinson correction of the PCG configuration as
  *   mvsk_solve_batch computes it (Eq. operator-third, Sec. 3.2), for parity
- *   tests: for B instances with coefficients C (B x 4) at points X (B x n)
- *   and K probe pairs (U, P) (each B x K x n, pair k of instance b at
- *   (b*K + k)*n),
+ *   tests: for B instances with coefficients C (B x 4) at points X (B x n),
+ *   working faces maskF (B x n or NULL, as in mvsk_batch_hvp) and K probe
+ *   pairs (U, P) (each B x K x n, pair k of instance b at (b*K + k)*n),
  *     rhat_b = K^-1 sum_k (A u_bk) o (A p_bk),
- *     at[b]  = T^-1 A^T (psi'''_b(z_b) o rhat_b),  z_b = A x_b,  B x n.
- *   BF16 A and operands on the tensor cores, FP32 accumulation, the weighted
- *   rows rounded to BF16.  Host or device pointers; MVSK_PREC_MIXED_BF16
- *   context; 1 <= K <= 8.  Errors: EINVAL, ENOMEM, ECUDA.
+ *     at[b]  = T^-1 A^T (psi'''_b(z_b) o rhat_b),  z_b = A x_b,  B x n
+ *   (on the union of the faces, zero elsewhere, with face_products = 1; the
+ *   probe pairs must then be zero off their face).  BF16 A and operands on
+ *   the tensor cores, FP32 accumulation, the weighted rows rounded to BF16.
+ *   Host or device pointers; MVSK_PREC_MIXED_BF16 context; 1 <= K <= 8.
+ *   Errors: EINVAL, ENOMEM, ECUDA.
  */
-mvsk_status mvsk_batch_third(mvsk_ctx* ctx, int32_t B, const double* C, const double* X, int32_t K,
-                             const double* U, const double* P, double* at);
+mvsk_status mvsk_batch_third(mvsk_ctx* ctx, int32_t B, const double* C, const double* X,
+                             const double* maskF, int32_t K, const double* U, const double* P,
+                             double* at);
 
 /*
  * Prop. quartic exact line search: coef[5] = A0..A4 of f(w + alpha d) from

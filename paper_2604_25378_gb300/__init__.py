@@ -72,8 +72,8 @@ _SIGS = {
     "mvsk_oracle_gram": (ctypes.c_int, [_P, _P, _P]),
     "mvsk_product": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64, _P, ctypes.c_int64]),
     "mvsk_oracle_ls": (ctypes.c_int, [_P, _P, _P, _P, _P]),
-    "mvsk_batch_hvp": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, _P, _P, _P, _P, _P]),
-    "mvsk_batch_third": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, _P]),
+    "mvsk_batch_hvp": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32, _P, _P, _P, _P, _P]),
+    "mvsk_batch_third": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, _P, _P, _P]),
     "mvsk_oracle_direction": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int32, _P]),
     "mvsk_project_slice": (ctypes.c_int, [_P, _P, ctypes.c_double, _P]),
     "mvsk_quartic_argmin": (ctypes.c_int, [_P, _P, ctypes.c_double, _P]),
@@ -255,35 +255,39 @@ class MVSK:
                                            V.shape[1], ctypes.c_void_p(out.data_ptr()), m))
         return out
 
-    def batch_hvp(self, C, X, nuhat, V):
+    def batch_hvp(self, C, X, nuhat, V, mask=None):
         """Direction products of a lockstep batch iteration (mvsk_batch_hvp):
-        C (B x 4), X (B x n), nuhat (B x n), V (B x nc x n) -> (HV (B x nc x n),
-        Gnu (B x n), diagG (B x n), (fused first product, split count of the second))."""
+        C (B x 4), X (B x n), nuhat (B x n), V (B x nc x n), optional working
+        faces mask (B x n of 0/1) -> (HV (B x nc x n), Gnu (B x n), diagG (B x n),
+        (fused first product, split count of the second))."""
         C = np.ascontiguousarray(C, dtype=np.float64)
         X = np.ascontiguousarray(X, dtype=np.float64)
         NU = np.ascontiguousarray(nuhat, dtype=np.float64)
         V = np.ascontiguousarray(V, dtype=np.float64)
+        MK = None if mask is None else np.ascontiguousarray(mask, dtype=np.float64)
         B, nc = V.shape[0], V.shape[1]
         HV = np.empty((B, nc, self.n))
         Gn = np.empty((B, self.n))
         Dg = np.empty((B, self.n))
         path = (ctypes.c_int32 * 2)()
-        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
-        self._check(self._lib.mvsk_batch_hvp(self._h, B, vp(C), vp(X), vp(NU), nc, vp(V), vp(HV), vp(Gn), vp(Dg),
-                                             path))
+        vp = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        self._check(self._lib.mvsk_batch_hvp(self._h, B, vp(C), vp(X), vp(NU), vp(MK), nc, vp(V), vp(HV), vp(Gn),
+                                             vp(Dg), path))
         return HV, Gn, Dg, (int(path[0]), int(path[1]))
 
-    def batch_third(self, C, X, U, P):
+    def batch_third(self, C, X, U, P, mask=None):
         """Hutchinson correction of a lockstep batch (mvsk_batch_third): C (B x 4),
-        X (B x n), probe pairs U, P (B x K x n) -> at (B x n)."""
+        X (B x n), probe pairs U, P (B x K x n), optional working faces mask
+        (B x n of 0/1) -> at (B x n)."""
         C = np.ascontiguousarray(C, dtype=np.float64)
         X = np.ascontiguousarray(X, dtype=np.float64)
         U = np.ascontiguousarray(U, dtype=np.float64)
         P = np.ascontiguousarray(P, dtype=np.float64)
+        MK = None if mask is None else np.ascontiguousarray(mask, dtype=np.float64)
         B, K = U.shape[0], U.shape[1]
         at = np.empty((B, self.n))
-        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
-        self._check(self._lib.mvsk_batch_third(self._h, B, vp(C), vp(X), K, vp(U), vp(P), vp(at)))
+        vp = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        self._check(self._lib.mvsk_batch_third(self._h, B, vp(C), vp(X), vp(MK), K, vp(U), vp(P), vp(at)))
         return at
 
     def line_search(self, w, d):

@@ -39,9 +39,10 @@ __global__ void k_cols_bf16_b(Inst base, int nc, int c0, int interleave, __nv_bf
 // consecutive rows per thread, with 16-byte loads and one 8-byte store when
 // T is a multiple of 4 (rows then start 16-byte aligned; Tp is a multiple of 8).
 __global__ void k_reduce_hvp1_b(const float* part, int splits, int N, int nc, long long T, long long ldp,
-                                const float* Hf, __nv_bfloat16* S, long long Tp) {
+                                const float* Hf, __nv_bfloat16* S, long long Tp, const int* rts = nullptr) {
   const long long t0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (t0 >= T) return;
+  if (rts != nullptr) splits = rts[2];
   const int q = blockIdx.y;
   const float* h = Hf + (size_t)(q / nc) * T;
   __nv_bfloat16* out = S + (size_t)q * Tp;
@@ -73,16 +74,21 @@ __global__ void k_reduce_hvp1_b(const float* part, int splits, int N, int nc, lo
 }
 
 // at_b = T^-1 sum_z part[z][b][i] (FP64 output: the back-projected correction).
+// With upos (face-restricted products) the partial row of coordinate i is
+// upos[i] (< 0: outside the union of the faces, value 0) and the split count
+// rts[2] is the runtime one.
 __global__ void k_reduce_at_b(const float* part, int splits, int B, int n, int ld, long long ldp, double scale,
-                              Inst base) {
+                              Inst base, const int* rts = nullptr, const int* upos = nullptr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ld) return;
   const int b = blockIdx.y;
   const Inst s = inst_at(base, b);
+  if (rts != nullptr) splits = rts[2];
+  const int row = i < n ? (upos != nullptr ? upos[i] : i) : -1;
   float acc = 0.f;
-  if (i < n)
+  if (row >= 0)
 #pragma unroll 4
-    for (int z = 0; z < splits; ++z) acc += part[((size_t)z * B + b) * ldp + i];
+    for (int z = 0; z < splits; ++z) acc += part[((size_t)z * B + b) * ldp + row];
   s.at[i] = scale * (double)acc;
 }
 
@@ -91,10 +97,11 @@ __global__ void k_reduce_at_b(const float* part, int splits, int B, int n, int l
 // K of them lose nothing; only the BF16 weights are kept (the lockstep path has
 // no other reader of rhat).
 __global__ void k_reduce_rhat_b(const float* part, int splits, int N, int K, long long T, long long ldp, Inst base,
-                                __nv_bfloat16* S, long long Tp) {
+                                __nv_bfloat16* S, long long Tp, const int* rts = nullptr) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   if (t >= T) return;
+  if (rts != nullptr) splits = rts[2];
   const Inst s = inst_at(base, b);
   float r = 0.f;
   for (int k = 0; k < K; ++k) {
@@ -319,11 +326,12 @@ __global__ void k_hd_cols(Inst base, int B, __nv_bfloat16* dst) {
 // sum h (A 1_F)_t^2 over the rows t of CTA g.
 __global__ void __launch_bounds__(256) k_hd_reduce1(const float* part, int splits, int N, long long T, long long ldp,
                                                     Inst base, __nv_bfloat16* S, __nv_bfloat16* H, long long Tp,
-                                                    float* Hf) {
+                                                    float* Hf, const int* rts = nullptr) {
   __shared__ double scr[64];
   const int b = blockIdx.y;
   Inst s = inst_at(base, b);
   if (s.si[SI_SKIPDIR] != 0) return;
+  if (rts != nullptr) splits = rts[2];
   // psi'' in FP32 (its consumers are FP32 and BF16); FP64 only for the sums
   const float c2 = (float)s.sd[SD_C2], c3 = (float)s.sd[SD_C3], c4 = (float)s.sd[SD_C4];
   double a0 = 0.0, a1 = 0.0;
@@ -351,16 +359,19 @@ __global__ void __launch_bounds__(256) k_hd_reduce1(const float* part, int split
 }
 
 // out_b[i] = T^-1 sum_z part[z][b][i] into Gnu_b (which = 0) or diagG_b (which = 1).
+// upos / rts: as in k_reduce_at_b.
 __global__ void k_hd_reduce2(const float* part, int splits, int B, int n, int ld, long long ldp, double scale,
-                             Inst base, int which) {
+                             Inst base, int which, const int* rts = nullptr, const int* upos = nullptr) {
   const long long tot = (long long)B * ld;
+  if (rts != nullptr) splits = rts[2];
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(e / ld), i = (int)(e % ld);
     const Inst s = inst_at(base, b);
     if (s.si[SI_SKIPDIR] != 0) continue;
+    const int row = i < n ? (upos != nullptr ? upos[i] : i) : -1;
     double acc = 0.0;
-    if (i < n)
-      for (int z = 0; z < splits; ++z) acc += (double)part[((size_t)z * B + b) * ldp + i];
+    if (row >= 0)
+      for (int z = 0; z < splits; ++z) acc += (double)part[((size_t)z * B + b) * ldp + row];
     (which ? s.diagG : s.Gnu)[i] = scale * acc;
   }
 }
@@ -386,6 +397,180 @@ __global__ void k_square_t_bf16(const double* A, int lda, long long T, int n, __
     const long long t = t0 + threadIdx.x;
     if (j < n && t < Tp) out[(size_t)j * ldo + t] = __float2bfloat16(tile[threadIdx.x][threadIdx.y + 8 * k]);
   }
+}
+
+// Split-K count for `tiles` output tiles of nk k-blocks on `slots` resident
+// CTAs.  Tensor-bound tiles: the count minimising waves * (k-blocks per split)
+// + 6 per split (prologue, epilogue and partial traffic in k-block units).
+// Bandwidth-bound tiles: one wave of resident CTAs, so every SM streams A at
+// once.  At least 4 k-blocks per split, at most smax splits.
+__host__ __device__ inline int pick_splits(int tiles, int nk, int slots, bool tensor_bound, int smax) {
+  if (!tensor_bound) {
+    int sp = slots / tiles;
+    if (sp > smax) sp = smax;
+    if (sp > nk / 4) sp = nk / 4;
+    return sp < 1 ? 1 : sp;
+  }
+  int best = 1;
+  long long best_cost = -1;
+  for (int sp = 1; sp <= smax; ++sp) {
+    if (sp > 1 && nk < 4 * sp) break;
+    const long long waves = ((long long)tiles * sp + slots - 1) / slots;
+    const long long cost = waves * ((nk + sp - 1) / sp) + 6LL * sp;
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = sp;
+    }
+  }
+  return best;
+}
+
+
+// --------------------------------------------- face-restricted products (U)
+// After the face step every PCG vector of instance b lives on its working
+// face F_b (zero elsewhere), so A v reads only the columns of A in F_b and
+// the back-projection A^T s is needed only on F_b.  Per iteration the union U
+// of the running instances' faces (|U| is a few hundred once the faces have
+// collapsed, against n = 5440) is listed, the columns of A in U are gathered
+// in both orientations, and the direction products run with K = |U| (A P) or
+// |U| output rows (A^T S): the same sums over fewer zero terms.
+//
+// Runtime extents of the products: one spec per product launch (filled at
+// graph capture), completed per iteration by k_union_scan.
+constexpr int kUMaxProds = 16;
+constexpr int kUMaxSplits = 16;
+
+// flag[i] = 1 when coordinate i is on the working face of a running
+// instance that needs a direction (k_face wrote maskF this iteration).
+__global__ void k_union_flags(Inst base, int B, int* flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= base.ld) return;
+  int f = 0;
+  if (i < base.n)
+    for (int b = 0; b < B && !f; ++b) {
+      const int* si = base.si + (size_t)b * kSI;
+      if (si[SI_DONE] == 0 && si[SI_SKIPDIR] == 0 && base.maskF[(size_t)b * base.vs + i] != 0.0) f = 1;
+    }
+  flag[i] = f;
+}
+
+// One CTA of 1024 threads: U in increasing order (idx[j], j < |U|), the
+// position of each coordinate in it (pos[i], -1 outside), info[0] = |U|,
+// info[1] = |U| rounded up to 64 (at least 64), and the runtime extents
+// rt[4 p .. 4 p + 3] = {rows, K, splits, k-tiles per split} of product spec p
+// (every split non-empty, as the consumers sum that many partials).
+__global__ void __launch_bounds__(1024) k_union_scan(const int* flag, int ld, int* idx, int* pos, int* info,
+                                                     const UProd* specs, int nspec, int* rt) {
+  __shared__ int wsum[32];
+  const int per = (ld + 1023) / 1024, i0 = threadIdx.x * per;
+  int cnt = 0;
+  for (int i = i0; i < i0 + per && i < ld; ++i) cnt += flag[i];
+  // exclusive scan of cnt over the block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int v = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) wsum[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    int w = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += u;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  int p = v - cnt + (warp > 0 ? wsum[warp - 1] : 0);
+  for (int i = i0; i < i0 + per && i < ld; ++i) {
+    if (flag[i]) {
+      idx[p] = i;
+      pos[i] = p++;
+    } else {
+      pos[i] = -1;
+    }
+  }
+  if (threadIdx.x == 1023) {
+    const int ku = p, kup = ku < 1 ? kTcBK : (ku + kTcBK - 1) / kTcBK * kTcBK;
+    info[0] = ku;
+    info[1] = kup;
+    for (int q = 0; q < nspec; ++q) {
+      const UProd& sp = specs[q];
+      if (sp.mrows <= 0 || sp.nt <= 0) continue;  // unused slot
+      const int rows = sp.rows_dyn ? kup : sp.M, K = sp.rows_dyn ? sp.K : kup;
+      const int mt = (rows + sp.mrows - 1) / sp.mrows, nk = (K + kTcBK - 1) / kTcBK;
+      const int want = pick_splits(mt * sp.nt, nk, sp.slots, sp.tensor != 0, sp.smax);
+      const int ktps = (nk + want - 1) / want;
+      rt[4 * q] = rows;
+      rt[4 * q + 1] = K;
+      rt[4 * q + 2] = (nk + ktps - 1) / ktps;
+      rt[4 * q + 3] = ktps;
+    }
+  }
+}
+
+// dst row j = src row idx[j] for j < |U|, zero for |U| <= j < info[1]
+// (rows of cols BF16 values, cols a multiple of 8).  Grid (x, rows of dst).
+__global__ void k_gather_rows_bf16(const __nv_bfloat16* __restrict__ src, long long lds, const int* idx,
+                                   const int* info, __nv_bfloat16* __restrict__ dst, long long ldd, long long cols) {
+  const int j = blockIdx.y;
+  if (j >= info[1]) return;
+  const bool live = j < info[0];
+  const uint4* s4 = reinterpret_cast<const uint4*>(src + (size_t)(live ? idx[j] : 0) * lds);
+  uint4* d4 = reinterpret_cast<uint4*>(dst + (size_t)j * ldd);
+  const long long n8 = cols / 8;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n8; e += (long long)gridDim.x * blockDim.x)
+    d4[e] = live ? s4[e] : make_uint4(0u, 0u, 0u, 0u);
+}
+
+// dst[t][j] = srcT[j][t] for j < info[1], t < T (64 x 64 tiles through
+// shared memory; dst is T x ldd, srcT is rows x lds).  Grid (ceil(T/64),
+// ceil(rows/64)), block (64, 8).
+__global__ void k_transpose_u_bf16(const __nv_bfloat16* __restrict__ srcT, long long lds, const int* info,
+                                   long long T, __nv_bfloat16* __restrict__ dst, long long ldd) {
+  __shared__ __nv_bfloat16 tile[64][66];
+  const int j0 = blockIdx.y * 64;
+  if (j0 >= info[1]) return;
+  const long long t0 = (long long)blockIdx.x * 64;
+  for (int r = threadIdx.y; r < 64; r += 8) {
+    const long long t = t0 + threadIdx.x;
+    tile[r][threadIdx.x] = t < T ? srcT[(size_t)(j0 + r) * lds + t] : __float2bfloat16(0.f);
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 64; r += 8) {
+    const long long t = t0 + r;
+    if (t < T) dst[(size_t)t * ldd + j0 + threadIdx.x] = tile[threadIdx.x][r];
+  }
+}
+
+// BF16 columns in U coordinates: dst[q*ld + j] = bf16(col_q[idx[j]]) for
+// j < |U|, zero for |U| <= j < info[1]; col_q as in k_cols_bf16_b.
+__global__ void k_cols_bf16_u(Inst base, int nc, int c0, int interleave, const int* idx, const int* info,
+                              __nv_bfloat16* dst) {
+  const int ld = base.ld;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= info[1]) return;
+  const int q = blockIdx.y, b = q / nc, jj = q % nc;
+  const Inst s = inst_at(base, b);
+  const float* col = interleave ? ((jj & 1) ? kcol<float>(s.Bv, 1 + (jj >> 1), ld) : kcol<float>(s.X, 1 + (jj >> 1), ld))
+                                : kcol<float>(s.P, c0 + jj, ld);
+  dst[(size_t)q * ld + j] = __float2bfloat16(j < info[0] ? col[idx[j]] : 0.f);
+}
+
+// The nuhat / maskF columns of the Gram-diagonal block in U coordinates.
+__global__ void k_hd_cols_u(Inst base, const int* idx, const int* info, __nv_bfloat16* dst) {
+  const int ld = base.ld;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= info[1]) return;
+  const int q = blockIdx.y;
+  const Inst s = inst_at(base, q >> 1);
+  float v = 0.f;
+  if (j < info[0]) v = (float)((q & 1) ? s.maskF[idx[j]] : s.nuhat[idx[j]]);
+  dst[(size_t)q * ld + j] = __float2bfloat16(v);
 }
 
 // ---------------------------------------------------------------- host side
@@ -495,33 +680,6 @@ mvsk_status batch_alloc(mvsk_ctx* c, BatchBuf& bb, int B) {
   return MVSK_OK;
 }
 
-// Split-K tensor-core product with FP32 partials for N columns (N tile 16, 64 or 256).
-// Split-K count for `tiles` output tiles of nk k-blocks on `slots` resident
-// CTAs.  Tensor-bound tiles: the count minimising waves * (k-blocks per split)
-// + 6 per split (prologue, epilogue and partial traffic in k-block units).
-// Bandwidth-bound tiles: one wave of resident CTAs, so every SM streams A at
-// once.  At least 4 k-blocks per split, at most smax splits.
-int pick_splits(int tiles, int nk, int slots, bool tensor_bound, int smax) {
-  if (!tensor_bound) {
-    int sp = slots / tiles;
-    if (sp > smax) sp = smax;
-    if (sp > nk / 4) sp = nk / 4;
-    return sp < 1 ? 1 : sp;
-  }
-  int best = 1;
-  long long best_cost = -1;
-  for (int sp = 1; sp <= smax; ++sp) {
-    if (sp > 1 && nk < 4 * sp) break;
-    const long long waves = ((long long)tiles * sp + slots - 1) / slots;
-    const long long cost = waves * ((nk + sp - 1) / sp) + 6LL * sp;
-    if (best_cost < 0 || cost < best_cost) {
-      best_cost = cost;
-      best = sp;
-    }
-  }
-  return best;
-}
-
 // N tile and resident CTAs per SM of the batched products.  Wide products
 // take the tile among 128, 192 and 256 that pads N least (ties: the wider),
 // since padded columns still cost full MMA work.
@@ -544,30 +702,30 @@ inline bool tc_wide(int bn) { return bn >= 128; }
 // Launch of the two-subtile (256-row) product with N tile bn and epilogue epi.
 template <class Epi>
 void launch_tc2(int bn, dim3 grid, cudaStream_t st, const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K,
-                int ktps, const Epi& epi, int* err) {
+                int ktps, const Epi& epi, int* err, const int* rt = nullptr) {
   if (bn == 128)
     k_gemm_tc<128, 4, Epi, 2><<<grid, 128, tc_smem_bytes<128, 4, 2>(), st>>>(ta, tb, M, N, K, ktps, epi, err,
-                                                                            nullptr, nullptr);
+                                                                            nullptr, nullptr, rt);
   else if (bn == 192)
     k_gemm_tc<192, 4, Epi, 2><<<grid, 128, tc_smem_bytes<192, 4, 2>(), st>>>(ta, tb, M, N, K, ktps, epi, err,
-                                                                            nullptr, nullptr);
+                                                                            nullptr, nullptr, rt);
   else
     k_gemm_tc<256, 3, Epi, 2><<<grid, 128, tc_smem_bytes<256, 3, 2>(), st>>>(ta, tb, M, N, K, ktps, epi, err,
-                                                                            nullptr, nullptr);
+                                                                            nullptr, nullptr, rt);
 }
 
 // Split-K tensor-core product with FP32 partials for N columns (N tile 16, 64 or 256).
 template <class Epi>
 void launch_partials(int bn, dim3 grid, cudaStream_t st, const CUtensorMap& ta, const CUtensorMap& tb, int M, int N,
-                     int K, int ktps, const Epi& epi, int* err) {
+                     int K, int ktps, const Epi& epi, int* err, const int* rt = nullptr) {
   if (bn == 16)
     k_gemm_tc<16, 8, Epi><<<grid, 128, tc_smem_bytes<16, 8>(), st>>>(ta, tb, M, N, K, ktps, epi, err, nullptr,
-                                                                     nullptr);
+                                                                     nullptr, rt);
   else if (bn == 64)
     k_gemm_tc<64, 4, Epi><<<grid, 128, tc_smem_bytes<64, 4>(), st>>>(ta, tb, M, N, K, ktps, epi, err, nullptr,
-                                                                     nullptr);
+                                                                     nullptr, rt);
   else
-    launch_tc2(bn, grid, st, ta, tb, M, N, K, ktps, epi, err);
+    launch_tc2(bn, grid, st, ta, tb, M, N, K, ktps, epi, err, rt);
 }
 
 mvsk_status tc_partials_n(mvsk_ctx* c, const void* Aop, int M, const void* Bop, int N, long long K, long long ldk,
@@ -683,6 +841,201 @@ mvsk_status hvpdiag_tc_batch(mvsk_ctx* c, BatchBuf& bb, int B, int gz) {
   return MVSK_OK;
 }
 
+// ------------------------------------------ face-restricted products (host)
+// Spec slot of a product shape (find or add); the specs are uploaded before the
+// first replay of the graph and k_union_scan fills their runtime extents.
+int u_spec(BatchBuf& bb, const UProd& p) {
+  for (size_t q = 0; q < bb.u_hspec.size(); ++q) {
+    const UProd& o = bb.u_hspec[q];
+    if (o.rows_dyn == p.rows_dyn && o.M == p.M && o.K == p.K && o.mrows == p.mrows && o.nt == p.nt &&
+        o.slots == p.slots && o.tensor == p.tensor && o.smax == p.smax)
+      return (int)q;
+  }
+  bb.u_hspec.push_back(p);
+  return (int)bb.u_hspec.size() - 1;
+}
+
+// Spec of a product restricted to U (see UProd); fused: the psi''-weighted
+// A P without split-K.
+UProd u_shape(const mvsk_ctx* c, int rows_dyn, int Mmax, int N, long long K, size_t part_floats, long long ldp,
+              bool fused) {
+  const int bn = tc_bn(N);
+  const int mrows = tc_wide(bn) ? 2 * kTcBM : kTcBM;
+  const int nt = (N + bn - 1) / bn;
+  int smax = fused ? 1 : (int)(part_floats / ((size_t)N * ldp));
+  if (smax > kUMaxSplits) smax = kUMaxSplits;
+  if (smax < 1) smax = 1;
+  return UProd{rows_dyn, rows_dyn ? 0 : Mmax, rows_dyn ? (int)K : 0, mrows, nt,
+               c->nsm * (fused ? 1 : tc_ctas_per_sm(bn)), tc_wide(bn) ? 1 : 0, smax};
+}
+
+bool u_fused(const mvsk_ctx* c, int N) {
+  const int bn = tc_bn(N), mt = (int)((c->T + 2 * kTcBM - 1) / (2 * kTcBM)), nt = (N + bn - 1) / bn;
+  return tc_wide(bn) && 2 * mt * nt >= c->nsm;
+}
+
+// Every product shape a lockstep iteration (or a parity export) launches on U,
+// registered and uploaded before any of them runs: the Gram-diagonal block,
+// the Hessian-vector blocks of widths nc[0..nw), the Hutchinson block of K
+// probe pairs (K = 0: none).
+mvsk_status u_prepare(mvsk_ctx* c, BatchBuf& bb, int B, const int* nc, int nw, int K) {
+  bb.u_hspec.clear();
+  const size_t pf = bb.part_floats;
+  u_spec(bb, u_shape(c, 0, (int)c->T, 2 * B, c->ld, pf, c->T, false));
+  u_spec(bb, u_shape(c, 1, c->ld, B, c->Tp, pf, c->ld, false));
+  for (int w = 0; w < nw; ++w) {
+    const int N = B * nc[w];
+    const bool f = u_fused(c, N);
+    u_spec(bb, u_shape(c, 0, (int)c->T, N, c->ld, pf, c->T, f));
+    u_spec(bb, u_shape(c, 1, c->ld, N, c->Tp, pf, c->ld, false));
+  }
+  if (K > 0) u_spec(bb, u_shape(c, 0, (int)c->T, 2 * K * B, c->ld, pf, c->T, false));
+  if (bb.u_hspec.size() > (size_t)kUMaxProds) return fail(MVSK_ECUDA, "too many face-restricted product shapes");
+  std::vector<UProd> all((size_t)kUMaxProds, UProd{0, 0, 0, 0, 0, 0, 0, 0});
+  for (size_t q = 0; q < bb.u_hspec.size(); ++q) all[q] = bb.u_hspec[q];
+  CU(cudaMemcpyAsync(bb.u_specs, all.data(), sizeof(UProd) * kUMaxProds, cudaMemcpyHostToDevice, c->stream));
+  return sync(c);
+}
+
+// Slot of a registered shape (u_prepare), -1 if it was not registered.
+int u_find(const BatchBuf& bb, const UProd& p) {
+  for (size_t q = 0; q < bb.u_hspec.size(); ++q) {
+    const UProd& o = bb.u_hspec[q];
+    if (o.rows_dyn == p.rows_dyn && o.M == p.M && o.K == p.K && o.mrows == p.mrows && o.nt == p.nt &&
+        o.slots == p.slots && o.tensor == p.tensor && o.smax == p.smax)
+      return (int)q;
+  }
+  return -1;
+}
+
+// Split-K product restricted to the union U.  rows_dyn = 0: A P with A the
+// gathered T x |U| columns (K = |U|, output rows fixed); rows_dyn = 1: A^T S
+// with the gathered |U| rows (output rows |U|, K fixed).  Partials as in
+// tc_partials_n, with the runtime split count at (*rts_out)[2] (device).
+mvsk_status tc_partials_u(mvsk_ctx* c, BatchBuf& bb, int rows_dyn, const void* Aop, int Mmax, const void* Bop, int N,
+                          long long K, long long ldk, float* part, size_t part_floats, long long ldp,
+                          const int** rts_out) {
+  CUtensorMap ta, tb;
+  const int bn = tc_bn(N);
+  TRY(make_tmap_bf16(&ta, Aop, (unsigned long long)ldk, (unsigned long long)Mmax, (unsigned long long)ldk * 2, kTcBK,
+                     kTcBM));
+  TRY(make_tmap_bf16(&tb, Bop, (unsigned long long)ldk, (unsigned long long)N, (unsigned long long)ldk * 2, kTcBK,
+                     (unsigned)bn));
+  const UProd sp = u_shape(c, rows_dyn, Mmax, N, K, part_floats, ldp, false);
+  const int q = u_find(bb, sp);
+  if (q < 0) return fail(MVSK_ECUDA, "face-restricted product shape not registered");
+  const int* rt = bb.u_rt + 4 * q;
+  const int mt = (Mmax + sp.mrows - 1) / sp.mrows;
+  dim3 grid((unsigned)sp.nt, (unsigned)mt, (unsigned)sp.smax);
+  // profiler work: FLOPs per unit of |U| (scaled by the runtime |U| when read)
+  TRY(prof_begin_u(c, 400 + bn, 2.0 * (double)N * (double)(rows_dyn ? K : Mmax)));
+  if ((ldp * 4) % 16 == 0) {  // partials through bulk tensor stores
+    const cuuint64_t dims[3] = {(cuuint64_t)Mmax, (cuuint64_t)N, (cuuint64_t)sp.smax};
+    const cuuint64_t strides[2] = {(cuuint64_t)ldp * 4, (cuuint64_t)N * (cuuint64_t)ldp * 4};
+    const cuuint32_t box[3] = {32, (cuuint32_t)(bn < 32 ? bn : 32), 1};
+    EpiPartTma epi;
+    TRY(make_tmap_store(&epi.tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, part, dims, strides, box));
+    launch_partials(bn, grid, c->stream, ta, tb, Mmax, N, (int)K, 1, epi, c->err, rt);
+  } else {  // rows of partials not 16-byte aligned (T not a multiple of 4): plain stores
+    const EpiPartT epi{part, ldp, Mmax, N};
+    launch_partials(bn, grid, c->stream, ta, tb, Mmax, N, (int)K, 1, epi, c->err, rt);
+  }
+  c->launches += 1;
+  CU(cudaGetLastError());
+  TRY(prof_end(c));
+  *rts_out = rt;
+  return MVSK_OK;
+}
+
+// Union of the faces and the gathered operands of this iteration.
+mvsk_status union_gather(mvsk_ctx* c, BatchBuf& bb, int B) {
+  const unsigned gl = (unsigned)((c->ld + 255) / 256);
+  PROF_LAUNCH(NK_UNION, (k_union_flags<<<gl, 256, 0, c->stream>>>(bb.base, B, bb.u_flag)));
+  PROF_LAUNCH(NK_UNION, (k_union_scan<<<1, 1024, 0, c->stream>>>(bb.u_flag, c->ld, bb.u_idx, bb.u_pos, bb.u_info,
+                                                                  bb.u_specs, kUMaxProds, bb.u_rt)));
+  const unsigned gx = (unsigned)((c->Tp / 8 + 255) / 256);
+  PROF_LAUNCH(NK_GATHER, (k_gather_rows_bf16<<<dim3(gx, (unsigned)c->ld), 256, 0, c->stream>>>(
+                             c->A16T, c->Tp, bb.u_idx, bb.u_info, bb.u_AUT, c->Tp, c->Tp)));
+  PROF_LAUNCH(NK_GATHER, (k_gather_rows_bf16<<<dim3(gx, (unsigned)c->ld), 256, 0, c->stream>>>(
+                             c->A2_16T, c->Tp, bb.u_idx, bb.u_info, bb.u_A2UT, c->Tp, c->Tp)));
+  PROF_LAUNCH(NK_GATHER, (k_transpose_u_bf16<<<dim3((unsigned)((c->T + 63) / 64), (unsigned)(c->ld / 64)), dim3(64, 8),
+                                               0, c->stream>>>(bb.u_AUT, c->Tp, bb.u_info, c->T, bb.u_AU, c->ld)));
+  return MVSK_OK;
+}
+
+// hvpdiag_tc_batch on the union: Gnu, diagG and the two weighted squares.
+mvsk_status hvpdiag_tc_batch_u(mvsk_ctx* c, BatchBuf& bb, int B, int gz) {
+  const int N = 2 * B, gb = 4 * c->nsm;
+  const unsigned gl = (unsigned)((c->ld + 255) / 256);
+  PROF_LAUNCH(NK_HD_COLS, (k_hd_cols_u<<<dim3(gl, (unsigned)N), 256, 0, c->stream>>>(bb.base, bb.u_idx, bb.u_info,
+                                                                                      bb.P16)));
+  const int *r1 = nullptr, *r2 = nullptr, *r3 = nullptr;
+  TRY(tc_partials_u(c, bb, 0, bb.u_AU, (int)c->T, bb.P16, N, c->ld, c->ld, bb.part, bb.part_floats, c->T, &r1));
+  PROF_LAUNCH(NK_HD_RED1, (k_hd_reduce1<<<dim3(gz, B), 256, 0, c->stream>>>(bb.part, 1, N, c->T, c->T, bb.base,
+                                                                            bb.S16T, bb.H16, c->Tp, bb.Hf, r1)));
+  TRY(tc_partials_u(c, bb, 1, bb.u_AUT, c->ld, bb.S16T, B, c->Tp, c->Tp, bb.part, bb.part_floats, c->ld, &r2));
+  PROF_LAUNCH(NK_HD_RED2, (k_hd_reduce2<<<gb, 256, 0, c->stream>>>(bb.part, 1, B, c->n, c->ld, c->ld,
+                                                                   1.0 / (double)c->T, bb.base, 0, r2, bb.u_pos)));
+  TRY(tc_partials_u(c, bb, 1, bb.u_A2UT, c->ld, bb.H16, B, c->Tp, c->Tp, bb.part, bb.part_floats, c->ld, &r3));
+  PROF_LAUNCH(NK_HD_DIAG, (k_hd_reduce2<<<gb, 256, 0, c->stream>>>(bb.part, 1, B, c->n, c->ld, c->ld,
+                                                                   1.0 / (double)c->T, bb.base, 1, r3, bb.u_pos)));
+  return MVSK_OK;
+}
+
+// hvp_tc_batch on the union: P16 holds the columns in U coordinates; the
+// partials of A^T S come out in U coordinates (*rts: their split count).
+mvsk_status hvp_tc_batch_u(mvsk_ctx* c, BatchBuf& bb, int B, int nc, const int** rts) {
+  const int N = B * nc;
+  const unsigned gt4 = (unsigned)((c->T + 1023) / 1024);
+  const int bn = tc_bn(N), mt = (int)((c->T + 2 * kTcBM - 1) / (2 * kTcBM)), nt = (N + bn - 1) / bn;
+  if (u_fused(c, N)) {  // fused weighting, K = |U| at run time
+    CUtensorMap ta, tb;
+    TRY(make_tmap_bf16(&ta, bb.u_AU, (unsigned long long)c->ld, (unsigned long long)c->T,
+                       (unsigned long long)c->ld * 2, kTcBK, kTcBM));
+    TRY(make_tmap_bf16(&tb, bb.P16, (unsigned long long)c->ld, (unsigned long long)N, (unsigned long long)c->ld * 2,
+                       kTcBK, (unsigned)bn));
+    EpiHvp1Tma epi;
+    epi.Hf = bb.Hf;
+    epi.T = (int)c->T;
+    epi.N = N;
+    epi.nc = nc;
+    const cuuint64_t dims[2] = {(cuuint64_t)c->T, (cuuint64_t)N};
+    const cuuint64_t strides[1] = {(cuuint64_t)c->Tp * 2};
+    const cuuint32_t box[2] = {32, 32};
+    TRY(make_tmap_store(&epi.tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, bb.S16T, dims, strides, box));
+    const int q = u_find(bb, u_shape(c, 0, (int)c->T, N, c->ld, bb.part_floats, c->T, true));
+    if (q < 0) return fail(MVSK_ECUDA, "face-restricted product shape not registered");
+    TRY(prof_begin_u(c, 400 + bn, 2.0 * (double)c->T * (double)N));
+    launch_tc2(bn, dim3((unsigned)nt, (unsigned)mt, 1), c->stream, ta, tb, (int)c->T, N, c->ld, 1, epi, c->err,
+               bb.u_rt + 4 * q);
+    c->launches += 1;
+    CU(cudaGetLastError());
+    TRY(prof_end(c));
+  } else {
+    const int* r1 = nullptr;
+    TRY(tc_partials_u(c, bb, 0, bb.u_AU, (int)c->T, bb.P16, N, c->ld, c->ld, bb.part, bb.part_floats, c->T, &r1));
+    PROF_LAUNCH(NK_HVP1, (k_reduce_hvp1_b<<<dim3(gt4, N), 256, 0, c->stream>>>(bb.part, 1, N, nc, c->T, c->T, bb.Hf,
+                                                                               bb.S16T, c->Tp, r1)));
+  }
+  return tc_partials_u(c, bb, 1, bb.u_AUT, c->ld, bb.S16T, N, c->Tp, c->Tp, bb.part, bb.part_floats, c->ld, rts);
+}
+
+// third_tc_batch on the union.
+mvsk_status third_tc_batch_u(mvsk_ctx* c, BatchBuf& bb, int B, int K) {
+  const int N = B * 2 * K;
+  const unsigned gl = (unsigned)((c->ld + 255) / 256);
+  PROF_LAUNCH(NK_COLS, (k_cols_bf16_u<<<dim3(gl, (unsigned)N), 256, 0, c->stream>>>(bb.base, 2 * K, 0, 1, bb.u_idx,
+                                                                                     bb.u_info, bb.P16)));
+  const int *r1 = nullptr, *r2 = nullptr;
+  TRY(tc_partials_u(c, bb, 0, bb.u_AU, (int)c->T, bb.P16, N, c->ld, c->ld, bb.part, bb.part_floats, c->T, &r1));
+  PROF_LAUNCH(NK_RHAT, (k_reduce_rhat_b<<<dim3((unsigned)((c->T + 255) / 256), B), 256, 0, c->stream>>>(
+                           bb.part, 1, N, K, c->T, c->T, bb.base, bb.S16T, c->Tp, r1)));
+  TRY(tc_partials_u(c, bb, 1, bb.u_AUT, c->ld, bb.S16T, B, c->Tp, c->Tp, bb.part, bb.part_floats, c->ld, &r2));
+  PROF_LAUNCH(NK_HVP2, (k_reduce_at_b<<<dim3(gl, B), 256, 0, c->stream>>>(bb.part, 1, B, c->n, c->ld, c->ld,
+                                                                         1.0 / (double)c->T, bb.base, r2, bb.u_pos)));
+  return MVSK_OK;
+}
+
 PassArgs pass_args_inst(const double cc[4]) {
   PassArgs a;
   memset(&a, 0, sizeof(a));
@@ -739,31 +1092,61 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
   }
   PROF_LAUNCH(NK_FACE, (k_face<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gs)));
   (void)P;
-  TRY(hvpdiag_tc_batch(c, bb, B, Gz));
+  const bool U = bb.umode;  // direction products restricted to the union of the faces
+  if (U) {
+    TRY(union_gather(c, bb, B));
+    TRY(hvpdiag_tc_batch_u(c, bb, B, Gz));
+  } else {
+    TRY(hvpdiag_tc_batch(c, bb, B, Gz));
+  }
   if (K > 0)
     PROF_LAUNCH(NK_PROBE_FILL, (k_probe_fill<float><<<dim3((c->ld + 255) / 256, K, B), 256, 0, c->stream>>>(base, K)));
   PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gz, -1)));
   PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup_cols<float><<<dim3(ncol1, B), 512, 0, c->stream>>>(base)));
   const unsigned gl = (unsigned)((c->ld + 255) / 256), gl4 = (unsigned)((c->ld + 1023) / 1024);
   const float invT = (float)(1.0 / (double)c->T);
-  PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl4, B * ncol1), 256, 0, c->stream>>>(base, ncol1, 0, 0, bb.P16)));
+  if (U)
+    PROF_LAUNCH(NK_COLS, (k_cols_bf16_u<<<dim3(gl, B * ncol1), 256, 0, c->stream>>>(base, ncol1, 0, 0, bb.u_idx,
+                                                                                     bb.u_info, bb.P16)));
+  else
+    PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl4, B * ncol1), 256, 0, c->stream>>>(base, ncol1, 0, 0, bb.P16)));
   for (int it = 0; it < kmax; ++it) {
     int s2 = 0;
-    TRY(hvp_tc_batch(c, bb, B, ncol1, &s2));
-    const KPart kp{bb.part, s2, B * ncol1, ncol1, c->ld, invT, bb.P16};
+    KPart kp{bb.part, 0, B * ncol1, ncol1, c->ld, invT, bb.P16};
+    if (U) {
+      TRY(hvp_tc_batch_u(c, bb, B, ncol1, &kp.rts));
+      kp.upos = bb.u_pos;
+      kp.uidx = bb.u_idx;
+      kp.uinfo = bb.u_info;
+    } else {
+      TRY(hvp_tc_batch(c, bb, B, ncol1, &s2));
+      kp.splits = s2;
+    }
     PROF_LAUNCH(NK_PCG_STEP, (k_pcg_step_f<<<dim3(ncol1, B), 1024, 0, c->stream>>>(base, 0, kmax, kp)));
   }
   if (K > 0) {
-    TRY(third_tc_batch(c, bb, B, K));
+    TRY(U ? third_tc_batch_u(c, bb, B, K) : third_tc_batch(c, bb, B, K));
   } else {
     for (int b = 0; b < B; ++b) CU(cudaMemsetAsync(inst_at(base, b).at, 0, sizeof(double) * c->ld, c->stream));
   }
   PROF_LAUNCH(NK_PCG_SETUP2, (k_pcg_setup2<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca, ca / 2)));
-  PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl4, B), 256, 0, c->stream>>>(base, 1, ca, 0, bb.P16)));
+  if (U)
+    PROF_LAUNCH(NK_COLS, (k_cols_bf16_u<<<dim3(gl, B), 256, 0, c->stream>>>(base, 1, ca, 0, bb.u_idx, bb.u_info,
+                                                                             bb.P16)));
+  else
+    PROF_LAUNCH(NK_COLS, (k_cols_bf16_b<<<dim3(gl4, B), 256, 0, c->stream>>>(base, 1, ca, 0, bb.P16)));
   for (int it = 0; it < kmax; ++it) {
     int s2 = 0;
-    TRY(hvp_tc_batch(c, bb, B, 1, &s2));
-    const KPart kp{bb.part, s2, B, 1, c->ld, invT, bb.P16};
+    KPart kp{bb.part, 0, B, 1, c->ld, invT, bb.P16};
+    if (U) {
+      TRY(hvp_tc_batch_u(c, bb, B, 1, &kp.rts));
+      kp.upos = bb.u_pos;
+      kp.uidx = bb.u_idx;
+      kp.uinfo = bb.u_info;
+    } else {
+      TRY(hvp_tc_batch(c, bb, B, 1, &s2));
+      kp.splits = s2;
+    }
     PROF_LAUNCH(NK_PCG_STEP_A, (k_pcg_step_fc<<<dim3(kPCL, B), 512, 0, c->stream>>>(base, ca, kmax, kp)));
   }
   PROF_LAUNCH(NK_ASSEMBLE, (k_assemble<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca)));
@@ -887,6 +1270,33 @@ mvsk_status kkt0_flush(mvsk_ctx* c, BatchBuf& bb) {
   return MVSK_OK;
 }
 
+// Buffers of the face-restricted products (context lifetime; sizes depend on
+// T and n only).
+mvsk_status ensure_ubuf(mvsk_ctx* c, BatchBuf& bb) {
+  if (bb.u_AU != nullptr) return MVSK_OK;
+  void* p;
+  const size_t ld = (size_t)c->ld;
+  TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * (size_t)c->T * ld));
+  bb.u_AU = (__nv_bfloat16*)p;
+  TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * ld * (size_t)c->Tp));
+  bb.u_AUT = (__nv_bfloat16*)p;
+  TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * ld * (size_t)c->Tp));
+  bb.u_A2UT = (__nv_bfloat16*)p;
+  TRY(dalloc(c, &p, sizeof(int) * (3 * ld + 8 + 4 * kUMaxProds)));
+  bb.u_flag = (int*)p;
+  bb.u_idx = bb.u_flag + ld;
+  bb.u_pos = bb.u_idx + ld;
+  bb.u_info = bb.u_pos + ld;
+  bb.u_rt = bb.u_info + 8;
+  TRY(dalloc(c, &p, sizeof(UProd) * kUMaxProds));
+  bb.u_specs = (UProd*)p;
+  CU(cudaMemsetAsync(bb.u_AU, 0, sizeof(__nv_bfloat16) * (size_t)c->T * ld, c->stream));
+  CU(cudaMemsetAsync(bb.u_AUT, 0, sizeof(__nv_bfloat16) * ld * (size_t)c->Tp, c->stream));
+  CU(cudaMemsetAsync(bb.u_A2UT, 0, sizeof(__nv_bfloat16) * ld * (size_t)c->Tp, c->stream));
+  CU(cudaMemsetAsync(bb.u_specs, 0, sizeof(UProd) * kUMaxProds, c->stream));
+  return MVSK_OK;
+}
+
 // Iterations between full recomputations of the cached z = A x of a batch.
 constexpr int kZRefresh = 32;
 
@@ -950,6 +1360,14 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
   }
   if (split)  // digit planes of A are built outside the capture
     for (int b0 = 0; b0 < L; b0 += kOzMaxB) TRY(oz_prepare(c, oz_bp(L - b0 < kOzMaxB ? L - b0 : kOzMaxB)));
+  // face-restricted direction products: gathered operands and index lists
+  bb.umode = o.face_products != 0;
+  if (bb.umode) {
+    TRY(ensure_ubuf(c, bb));
+    const int widths[2] = {o.probes + 1, 1};
+    TRY(u_prepare(c, bb, L, widths, 2, o.probes));
+  }
+  c->prof_uinfo = bb.umode ? bb.u_info : nullptr;
   // graph of one lockstep iteration (c1 is read on the device, so calibration needs no re-capture)
   cudaGraphExec_t gexec = nullptr;
   long long per_graph = 0;
@@ -1486,6 +1904,22 @@ __global__ void k_fill_inst(double* v, long long vs, int n, int ld, double val) 
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ld; i += gridDim.x * blockDim.x) p[i] = i < n ? val : 0.0;
 }
 
+// out[q*ld + i] = scale * sum_z part[z][q][row(i)], row(i) = upos[i] (or i
+// without upos), 0 outside; z < rts[2] (or splits).  Grid-stride over N x ld.
+__global__ void k_reduce_cols_u(const float* part, int splits, const int* rts, int N, int n, int ld, long long ldp,
+                                double scale, const int* upos, double* out) {
+  if (rts != nullptr) splits = rts[2];
+  const long long tot = (long long)N * ld;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(e / ld), i = (int)(e % ld);
+    const int row = i < n ? (upos != nullptr ? upos[i] : i) : -1;
+    double acc = 0.0;
+    if (row >= 0)
+      for (int z = 0; z < splits; ++z) acc += (double)part[((size_t)z * N + q) * ldp + row];
+    out[e] = scale * acc;
+  }
+}
+
 // Device scratch of an export call, released when the call returns.
 struct TmpDev {
   void* p = nullptr;
@@ -1529,22 +1963,25 @@ mvsk_status batch_export_setup(mvsk_ctx* c, int B, const double* C, const double
   return MVSK_OK;
 }
 
-mvsk_status batch_hvp_export(mvsk_ctx* c, int B, const double* C, const double* X, const double* NU, int nc,
-                             const double* V, double* HV, double* GNU, double* DIAG, int32_t* path) {
+mvsk_status batch_hvp_export(mvsk_ctx* c, int B, const double* C, const double* X, const double* NU,
+                             const double* MASK, int nc, const double* V, double* HV, double* GNU, double* DIAG,
+                             int32_t* path) {
   if (c->dir_prec != P16) return fail(MVSK_EINVAL, "the batched products need a BF16 context (MVSK_PREC_MIXED_BF16)");
   if (B < 1 || B > 4096) return fail(MVSK_EINVAL, "B must be in [1, 4096]");
   if (nc < 1 || nc > kTcCols) return fail(MVSK_EINVAL, "nc must be in [1, %d]", kTcCols);
   const size_t n = (size_t)c->n, ld = (size_t)c->ld, N = (size_t)B * nc;
   TmpDev tmp;
-  TRY(tmp.get(sizeof(double) * (4 * (size_t)B + 2 * n * B + N * n + N * ld)));
+  TRY(tmp.get(sizeof(double) * (4 * (size_t)B + 3 * n * B + N * n + N * ld)));
   double* dev = (double*)tmp.p;
   double* NUd = dev + 4 * (size_t)B + n * B;
-  double* Vd = NUd + n * B;
+  double* MKd = NUd + n * B;
+  double* Vd = MKd + n * B;
   double* HVd = Vd + N * n;
   TRY(batch_export_setup(c, B, C, X, dev));
   BatchBuf& bb = c->batch;
   const Inst& base = bb.base;
-  // the face data of the diagonal block: nuhat_b as given, every coordinate free
+  // the face data of the diagonal block: nuhat_b as given, the working face
+  // as given (every coordinate free without a mask)
   CU(cudaMemcpyAsync(NUd, NU, sizeof(double) * n * B, cudaMemcpyDefault, c->stream));
   CU(cudaMemcpyAsync(Vd, V, sizeof(double) * n * N, cudaMemcpyDefault, c->stream));
   CU(cudaMemsetAsync(base.nuhat, 0, sizeof(double) * (size_t)base.vs * B, c->stream));
@@ -1554,17 +1991,38 @@ mvsk_status batch_hvp_export(mvsk_ctx* c, int B, const double* C, const double* 
   k_fill_inst<<<dim3(gl, B), 256, 0, c->stream>>>(base.maskF, base.vs, c->n, c->ld, 1.0);
   c->launches += 1;
   CU(cudaGetLastError());
-  TRY(hvpdiag_tc_batch(c, bb, B, oz_row_ctas(c)));
-  k_load_cols_f32<<<dim3(gl, (unsigned)N), 256, 0, c->stream>>>(base, nc, 0, Vd);
-  k_cols_bf16_b<<<dim3(gl4, (unsigned)N), 256, 0, c->stream>>>(base, nc, 0, 0, bb.P16);
-  c->launches += 2;
-  CU(cudaGetLastError());
+  if (MASK != nullptr) {
+    CU(cudaMemcpyAsync(MKd, MASK, sizeof(double) * n * B, cudaMemcpyDefault, c->stream));
+    CU(cudaMemcpy2DAsync(base.maskF, sizeof(double) * base.vs, MKd, sizeof(double) * n, sizeof(double) * n,
+                         (size_t)B, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  bb.umode = c->opt.face_products != 0;
   int s2 = 0, fused = 0;
-  TRY(hvp_tc_batch(c, bb, B, nc, &s2, &fused));
-  k_reduce_hvp2<<<4 * c->nsm, 256, 0, c->stream>>>(bb.part, s2, (int)N, c->n, c->ld, c->ld, 1.0 / (double)c->T, HVd,
-                                                   nullptr);
+  const int* rts = nullptr;
+  if (bb.umode) {  // the products restricted to the union of the given faces
+    TRY(ensure_ubuf(c, bb));
+    TRY(u_prepare(c, bb, B, &nc, 1, 0));
+    TRY(union_gather(c, bb, B));
+    TRY(hvpdiag_tc_batch_u(c, bb, B, oz_row_ctas(c)));
+    k_load_cols_f32<<<dim3(gl, (unsigned)N), 256, 0, c->stream>>>(base, nc, 0, Vd);
+    k_cols_bf16_u<<<dim3(gl, (unsigned)N), 256, 0, c->stream>>>(base, nc, 0, 0, bb.u_idx, bb.u_info, bb.P16);
+    c->launches += 2;
+    CU(cudaGetLastError());
+    fused = u_fused(c, (int)N) ? 1 : 0;
+    TRY(hvp_tc_batch_u(c, bb, B, nc, &rts));
+  } else {
+    TRY(hvpdiag_tc_batch(c, bb, B, oz_row_ctas(c)));
+    k_load_cols_f32<<<dim3(gl, (unsigned)N), 256, 0, c->stream>>>(base, nc, 0, Vd);
+    k_cols_bf16_b<<<dim3(gl4, (unsigned)N), 256, 0, c->stream>>>(base, nc, 0, 0, bb.P16);
+    c->launches += 2;
+    CU(cudaGetLastError());
+    TRY(hvp_tc_batch(c, bb, B, nc, &s2, &fused));
+  }
+  k_reduce_cols_u<<<4 * c->nsm, 256, 0, c->stream>>>(bb.part, s2, rts, (int)N, c->n, c->ld, c->ld,
+                                                     1.0 / (double)c->T, bb.umode ? bb.u_pos : nullptr, HVd);
   c->launches += 1;
   CU(cudaGetLastError());
+  if (rts != nullptr) CU(cudaMemcpyAsync(&s2, rts + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaMemcpy2DAsync(HV, sizeof(double) * n, HVd, sizeof(double) * ld, sizeof(double) * n, N, cudaMemcpyDefault,
                        c->stream));
   CU(cudaMemcpy2DAsync(GNU, sizeof(double) * n, base.Gnu, sizeof(double) * 2 * base.vs, sizeof(double) * n,
@@ -1579,16 +2037,17 @@ mvsk_status batch_hvp_export(mvsk_ctx* c, int B, const double* C, const double* 
   return MVSK_OK;
 }
 
-mvsk_status batch_third_export(mvsk_ctx* c, int B, const double* C, const double* X, int K, const double* U,
-                               const double* P, double* AT) {
+mvsk_status batch_third_export(mvsk_ctx* c, int B, const double* C, const double* X, const double* MASK, int K,
+                               const double* U, const double* P, double* AT) {
   if (c->dir_prec != P16) return fail(MVSK_EINVAL, "the batched products need a BF16 context (MVSK_PREC_MIXED_BF16)");
   if (B < 1 || B > 4096) return fail(MVSK_EINVAL, "B must be in [1, 4096]");
   if (K < 1 || 2 * K > kTcCols) return fail(MVSK_EINVAL, "K must be in [1, %d]", kTcCols / 2);
   const size_t n = (size_t)c->n, ld = (size_t)c->ld, NK = (size_t)B * K;
   TmpDev tmp;
-  TRY(tmp.get(sizeof(double) * (4 * (size_t)B + n * B + 2 * NK * n)));
+  TRY(tmp.get(sizeof(double) * (4 * (size_t)B + 2 * n * B + 2 * NK * n)));
   double* dev = (double*)tmp.p;
-  double* Ud = dev + 4 * (size_t)B + n * B;
+  double* MKd = dev + 4 * (size_t)B + n * B;
+  double* Ud = MKd + n * B;
   double* Pd = Ud + NK * n;
   TRY(batch_export_setup(c, B, C, X, dev));
   BatchBuf& bb = c->batch;
@@ -1596,11 +2055,26 @@ mvsk_status batch_third_export(mvsk_ctx* c, int B, const double* C, const double
   CU(cudaMemcpyAsync(Ud, U, sizeof(double) * n * NK, cudaMemcpyDefault, c->stream));
   CU(cudaMemcpyAsync(Pd, P, sizeof(double) * n * NK, cudaMemcpyDefault, c->stream));
   const unsigned gl = (unsigned)((ld + 255) / 256);
+  k_fill_inst<<<dim3(gl, B), 256, 0, c->stream>>>(base.maskF, base.vs, c->n, c->ld, 1.0);
   k_load_cols_f32<<<dim3(gl, (unsigned)NK), 256, 0, c->stream>>>(base, K, 1, Ud);
   k_load_cols_f32<<<dim3(gl, (unsigned)NK), 256, 0, c->stream>>>(base, K, 2, Pd);
-  c->launches += 2;
+  c->launches += 3;
   CU(cudaGetLastError());
-  TRY(third_tc_batch(c, bb, B, K));
+  if (MASK != nullptr) {
+    CU(cudaMemcpyAsync(MKd, MASK, sizeof(double) * n * B, cudaMemcpyDefault, c->stream));
+    CU(cudaMemcpy2DAsync(base.maskF, sizeof(double) * base.vs, MKd, sizeof(double) * n, sizeof(double) * n,
+                         (size_t)B, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  bb.umode = c->opt.face_products != 0;
+  if (bb.umode) {
+    TRY(ensure_ubuf(c, bb));
+    const int one = 1;
+    TRY(u_prepare(c, bb, B, &one, 1, K));
+    TRY(union_gather(c, bb, B));
+    TRY(third_tc_batch_u(c, bb, B, K));
+  } else {
+    TRY(third_tc_batch(c, bb, B, K));
+  }
   CU(cudaMemcpy2DAsync(AT, sizeof(double) * n, base.at, sizeof(double) * base.vs, sizeof(double) * n, (size_t)B,
                        cudaMemcpyDefault, c->stream));
   return sync(c);

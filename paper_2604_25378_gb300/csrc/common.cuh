@@ -178,4 +178,17 @@ struct Psi {
   __device__ __forceinline__ double d3(double s) const { return -6.0 * c3 + 24.0 * c4 * s; }
 };
 
+// Shape of one tensor-core product restricted to the union U of the working
+// faces of a lockstep batch (its runtime extents depend on |U|).
+struct UProd {
+  int rows_dyn;  // 1: output rows = |U| (A^T products), 0: rows fixed = M
+  int M;         // fixed rows (rows_dyn = 0)
+  int K;         // fixed K (rows_dyn = 1), else K = |U| rounded up to 64
+  int mrows;     // rows per CTA tile
+  int nt;        // N tiles
+  int slots;     // resident CTAs of the machine
+  int tensor;    // tensor-bound (split-K by the time model) or bandwidth-bound
+  int smax;      // largest split count the grid and the partial buffer allow
+};
+
 }  // namespace mvsk

@@ -321,11 +321,16 @@ struct EpiHvp1Tma {
 // k-tiles [z*ktps, min(nk, (z+1)*ktps)) and hands the epilogue its z.  MT = 2
 // stacks two 128-row subtiles that share each B tile (accumulators at TMEM
 // columns 0 and BN): a third fewer operand bytes per MAC than MT = 1.
+// rt (nullable, device): extents known only when the kernel runs (products
+// restricted to a face that changes every iteration): rt[0] rows (<= M),
+// rt[1] K (<= K), rt[2] split count (every split non-empty), rt[3] k-tiles
+// per split; the grid covers the largest values and CTAs outside the runtime
+// extents return before any set-up.
 template <int BN, int STAGES, class Epi, int MT = 1>
 __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
                                                     int ktps, const __grid_constant__ Epi epi, int* err,
-                                                    const int* skip, const int* live) {
+                                                    const int* skip, const int* live, const int* rt = nullptr) {
   static_assert(BN == 16 || BN == 32 || BN == 64 || BN == 128 || BN == 192 || BN == 256, "unsupported N tile");
   static_assert(MT == 1 || (MT == 2 && BN >= 32), "two subtiles need BN >= 32");
   constexpr int kTcStages = STAGES;
@@ -334,6 +339,14 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
   constexpr int CW = BN < 32 ? BN : 32;
   if (skip != nullptr && *skip != 0) return;
   if (live != nullptr && *live == 0) return;
+  if (rt != nullptr) {
+    const int mr = rt[0], kr = rt[1];
+    if (mr < M) M = mr;
+    if (kr < K) K = kr;
+    ktps = rt[3] > 0 ? rt[3] : 1;
+    if ((int)blockIdx.y * kTcBM * MT >= M) return;      // rows beyond the runtime extent
+    if ((int)blockIdx.z >= rt[2]) return;               // splits beyond the runtime count
+  }
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));

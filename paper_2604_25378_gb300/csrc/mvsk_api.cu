@@ -37,6 +37,7 @@ struct Options {
   int batch_lanes = 0;     // batched solves: concurrent instances (0: all requests at once)
   int line_search = 0;     // 0 exact quartic step, 1 Armijo backtracking on the quartic
   int group_cal = 1;       // batched solves: requests sharing (c2, c3, c4) start calibration on a c1 grid
+  int face_products = 1;   // batched solves: direction products restricted to the union of the faces
   unsigned long long probe_seed = 0x5EEDull;
 };
 
@@ -68,6 +69,15 @@ struct BatchBuf {
   int wcap = 0;
   double* gpool = nullptr;  // calibration grid points: x* (ld) and z (T) per lane
   int gcap = 0;
+  // face-restricted direction products (batch_impl.cuh): the gathered columns
+  // of A in the union U of the faces (T x ld and ld x Tp BF16, A^2 rows),
+  // flags, U itself, positions in U, {|U|, padded |U|}, runtime extents of
+  // the product specs (device) and the specs themselves (host copy)
+  __nv_bfloat16 *u_AU = nullptr, *u_AUT = nullptr, *u_A2UT = nullptr;
+  int *u_flag = nullptr, *u_idx = nullptr, *u_pos = nullptr, *u_info = nullptr, *u_rt = nullptr;
+  mvsk::UProd* u_specs = nullptr;
+  std::vector<mvsk::UProd> u_hspec;
+  bool umode = false;
   int qcap = 0;
 };
 
@@ -151,6 +161,8 @@ struct mvsk_ctx {
   std::vector<double> prof_ms;                   // accumulated device ms per kind id
   std::vector<double> prof_work;                 // accumulated algorithmic bytes (passes) or flops (GEMMs)
   std::vector<double> ev_work;                   // work of each recorded pair
+  std::vector<char> ev_uscale;                   // work given per unit of |U| (face-restricted products)
+  const int* prof_uinfo = nullptr;               // device {|U|, padded |U|} of the current batch
   std::vector<char> prof_sel;                    // kinds recorded (mvsk_profile_only); empty = all
   bool prof_open = false;                        // a begun pair awaits its end event
   int prof_stride = 1;                           // bracket every k-th selected launch (mvsk_profile_stride)
@@ -407,11 +419,11 @@ const char* const kKernelNames[] = {"k_face", "k_probe_fill", "k_pcg_setup", "k_
                                     "k_assemble", "k_decide1", "k_decide2", "k_end_iter", "k_oz_fin_z",
                                     "k_oz_fin_g", "k_oz_fin_ls", "k_oz_split_vecs", "k_need_ls2", "k_reduce_cols",
                                     "k_hd_cols", "k_hd_reduce1", "k_hd_reduce2", "k_hd_reduce_diag",
-                                    "k_pcg_step_a", "k_z_step"};
+                                    "k_pcg_step_a", "k_z_step", "k_union", "k_gather_u"};
 enum NamedKernel : int {
   NK_FACE, NK_PROBE_FILL, NK_PCG_SETUP, NK_PCG_STEP, NK_COLS, NK_HVP1, NK_HVP2, NK_RHAT, NK_PCG_SETUP2, NK_ASSEMBLE,
   NK_DECIDE1, NK_DECIDE2, NK_END_ITER, NK_OZ_Z, NK_OZ_G, NK_OZ_LS, NK_OZ_SPLIT, NK_NEED, NK_REDUCE_COLS, NK_HD_COLS,
-  NK_HD_RED1, NK_HD_RED2, NK_HD_DIAG, NK_PCG_STEP_A, NK_ZSTEP, NK_COUNT
+  NK_HD_RED1, NK_HD_RED2, NK_HD_DIAG, NK_PCG_STEP_A, NK_ZSTEP, NK_UNION, NK_GATHER, NK_COUNT
 };
 
 mvsk_status prof_begin(mvsk_ctx* c, int kind, double work) {
@@ -425,6 +437,7 @@ mvsk_status prof_begin(mvsk_ctx* c, int kind, double work) {
     c->prof_work.assign(kProfKinds, 0.0);
   }
   c->ev_work.push_back(work);
+  c->ev_uscale.push_back(0);
   cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
   CU(cudaStreamIsCapturing(c->stream, &cst));
   c->ev_in_graph.push_back(cst == cudaStreamCaptureStatusActive ? 1 : 0);
@@ -461,14 +474,33 @@ mvsk_status prof_end(mvsk_ctx* c) {
     c->launches += 1;                              \
   } while (0)
 
+// A pair whose work is given per unit of the padded |U| of the iteration
+// (face-restricted products: their K or their output rows is |U|).
+mvsk_status prof_begin_u(mvsk_ctx* c, int kind, double work_per_unit) {
+  const size_t before = c->ev_kind.size();
+  TRY(prof_begin(c, kind, work_per_unit));
+  if (c->ev_kind.size() > before) c->ev_uscale.back() = 1;
+  return MVSK_OK;
+}
+
 // Fold the event pairs [b, e) into the per-kind totals (stream must be idle).
 mvsk_status prof_collect(mvsk_ctx* c, size_t b, size_t e) {
+  double units = -1.0;
   for (size_t q = b; q < e; ++q) {
     float ms = 0.f;
     CU(cudaEventElapsedTime(&ms, c->ev_pool[2 * q], c->ev_pool[2 * q + 1]));
+    double w = c->ev_work[q];
+    if (c->ev_uscale[q]) {
+      if (units < 0.0) {
+        int info[2] = {0, 0};
+        if (c->prof_uinfo != nullptr) CU(cudaMemcpy(info, c->prof_uinfo, sizeof(info), cudaMemcpyDeviceToHost));
+        units = (double)info[1];
+      }
+      w *= units;
+    }
     c->prof_n[c->ev_kind[q]] += 1;
     c->prof_ms[c->ev_kind[q]] += ms;
-    c->prof_work[c->ev_kind[q]] += c->ev_work[q];
+    c->prof_work[c->ev_kind[q]] += w;
   }
   return MVSK_OK;
 }
@@ -795,7 +827,7 @@ mvsk_status gemm_tc_f64(mvsk_ctx* c, const __nv_bfloat16* A, int M, const __nv_b
   EpiStoreF64 epi{C, ldc, alpha, M, N};
   dim3 grid((unsigned)((N + 127) / 128), (unsigned)((M + kTcBM - 1) / kTcBM), 1);
   const int nk = (int)((K + kTcBK - 1) / kTcBK);
-  kern<<<grid, 128, smem, c->stream>>>(ta, tb, M, N, (int)K, nk, epi, c->err, nullptr, nullptr);
+  kern<<<grid, 128, smem, c->stream>>>(ta, tb, M, N, (int)K, nk, epi, c->err, nullptr, nullptr, nullptr);
   c->launches += 1;
   CU(cudaGetLastError());
   return MVSK_OK;
@@ -911,7 +943,7 @@ mvsk_status tc_partials(mvsk_ctx* c, const CUtensorMap& ta, const CUtensorMap& t
   const int splits = (nk + ktps - 1) / ktps;
   EpiPartT epi{c->part32, ldp, M, N};
   dim3 grid(1, (unsigned)mt, (unsigned)splits);
-  kern<<<grid, 128, smem, c->stream>>>(ta, tb, M, N, (int)K, ktps, epi, c->err, skip, live);
+  kern<<<grid, 128, smem, c->stream>>>(ta, tb, M, N, (int)K, ktps, epi, c->err, skip, live, nullptr);
   c->launches += 1;
   CU(cudaGetLastError());
   *splits_out = splits;
@@ -1466,6 +1498,7 @@ mvsk_status mvsk_set_option(mvsk_ctx* c, const char* key, double v) {
   else if (k == "batch_lanes" && cnt(v, 0, 1000000)) o.batch_lanes = (int)v;
   else if (k == "line_search" && cnt(v, 0, 1)) o.line_search = (int)v;
   else if (k == "group_calibration" && cnt(v, 0, 1)) o.group_cal = (int)v;
+  else if (k == "face_products" && cnt(v, 0, 1)) o.face_products = (int)v;
   else return fail(MVSK_EINVAL, "unknown option or bad value: %s = %g", key, v);
   if (c->prefs_set && k == "pref_scaling") mvsk_set_prefs(c, c->lam, c->target);
   return MVSK_OK;
@@ -1604,18 +1637,19 @@ mvsk_status mvsk_product(mvsk_ctx* c, int32_t transpose, int32_t nvec, const dou
 }
 
 mvsk_status mvsk_batch_hvp(mvsk_ctx* c, int32_t B, const double* C, const double* X, const double* nuhat,
-                           int32_t nc, const double* V, double* HV, double* Gnu, double* diagG, int32_t path[2]) {
+                           const double* maskF, int32_t nc, const double* V, double* HV, double* Gnu, double* diagG,
+                           int32_t path[2]) {
   if (c == nullptr || C == nullptr || X == nullptr || nuhat == nullptr || V == nullptr || HV == nullptr ||
       Gnu == nullptr || diagG == nullptr)
     return fail(MVSK_EINVAL, "null argument");
-  return batch_hvp_export(c, B, C, X, nuhat, nc, V, HV, Gnu, diagG, path);
+  return batch_hvp_export(c, B, C, X, nuhat, maskF, nc, V, HV, Gnu, diagG, path);
 }
 
-mvsk_status mvsk_batch_third(mvsk_ctx* c, int32_t B, const double* C, const double* X, int32_t K, const double* U,
-                             const double* P, double* at) {
+mvsk_status mvsk_batch_third(mvsk_ctx* c, int32_t B, const double* C, const double* X, const double* maskF,
+                             int32_t K, const double* U, const double* P, double* at) {
   if (c == nullptr || C == nullptr || X == nullptr || U == nullptr || P == nullptr || at == nullptr)
     return fail(MVSK_EINVAL, "null argument");
-  return batch_third_export(c, B, C, X, K, U, P, at);
+  return batch_third_export(c, B, C, X, maskF, K, U, P, at);
 }
 
 mvsk_status mvsk_oracle_ls(mvsk_ctx* c, const double* w, const double* d, double coef[5], double* alpha_max) {
@@ -1743,6 +1777,7 @@ mvsk_status mvsk_profile_enable(mvsk_ctx* c, int32_t on) {
     c->ev_used = 0;
     c->ev_kind.clear();
     c->ev_work.clear();
+    c->ev_uscale.clear();
     c->ev_in_graph.clear();
     c->launches = 0;
     c->prof_n.assign(kProfKinds, 0);

@@ -412,6 +412,15 @@ struct KPart {
   long long ldp;
   float scale;
   __nv_bfloat16* P16;
+  // face-restricted products (nullable): runtime split count rts[2], and the
+  // row of coordinate i in the partials and in P16, upos[i] (< 0: none)
+  const int* rts = nullptr;
+  const int* upos = nullptr;
+  // with uidx: the step runs over the union U only (uidx[j], j < uinfo[0]),
+  // whose position j is the partial and P16 row (every Krylov vector is zero
+  // off its instance's face, a subset of U)
+  const int* uidx = nullptr;
+  const int* uinfo = nullptr;
 };
 
 template <typename KT>
@@ -628,7 +637,9 @@ __device__ __forceinline__ void pcg_step_body(Inst s0, int c0, int kmaxit, const
   if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
   const int col = (int)(blockIdx.x / CL), c = c0 + col;
   if (SI[SI_ACT + c] == 0) return;
-  const int n = s.n, ld = s.ld;
+  const int ld = s.ld;
+  const int* __restrict__ uidx = kp.uidx;
+  const int n = uidx != nullptr ? kp.uinfo[0] : s.n;  // positions covered: U, or every coordinate
   const int ch = (n + CL - 1) / CL, i0 = (int)rank * ch, i1 = i0 + ch < n ? i0 + ch : n;
   const float m = (float)SI[SI_M];
   const float lam = (float)s.sd[SD_LAM];
@@ -645,13 +656,19 @@ __device__ __forceinline__ void pcg_step_body(Inst s0, int c0, int kmaxit, const
   const float* __restrict__ fdg = f0.dg;
   const size_t prow = (size_t)blockIdx.y * kp.nc + col;
   float q[PE], p[PE], r[PE], xv[PE], mf[PE], nh[PE], dg[PE];
+  int ci[PE];  // coordinate of each element (-1: none)
   float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // mf.Q, nu.Q, p.mf.Q, p.mf, p.nu, p.p
 #pragma unroll
   for (int e = 0; e < PE; ++e) {
-    const int i = i0 + threadIdx.x + e * NT;
+    const int jp = i0 + threadIdx.x + e * NT;
+    ci[e] = jp < i1 ? (uidx != nullptr ? uidx[jp] : jp) : -1;
+  }
+#pragma unroll
+  for (int e = 0; e < PE; ++e) {
+    const int i = ci[e];
     q[e] = p[e] = r[e] = xv[e] = mf[e] = nh[e] = 0.f;
     dg[e] = 1.f;
-    if (i < i1) {
+    if (i >= 0) {
       p[e] = P[i];
       r[e] = R[i];
       xv[e] = X[i];
@@ -664,19 +681,23 @@ __device__ __forceinline__ void pcg_step_body(Inst s0, int c0, int kmaxit, const
   // inside the coordinate loop made each coordinate a separate round trip)
   const size_t zstride = (size_t)kp.N * kp.ldp;
   const float* __restrict__ pz = kp.part + prow * kp.ldp;
+  const int nspl = kp.rts != nullptr ? kp.rts[2] : kp.splits;
+  const int* __restrict__ upos = kp.upos;
+  int row[PE];
+#pragma unroll
+  for (int e = 0; e < PE; ++e) {
+    const int jp = i0 + threadIdx.x + e * NT;
+    row[e] = jp < i1 ? (uidx != nullptr ? jp : (upos != nullptr ? upos[ci[e]] : jp)) : -1;
+  }
   int z = 0;
-  for (; z + 2 <= kp.splits; z += 2, pz += 2 * zstride)
+  for (; z + 2 <= nspl; z += 2, pz += 2 * zstride)
 #pragma unroll
-    for (int e = 0; e < PE; ++e) {
-      const int i = i0 + threadIdx.x + e * NT;
-      if (i < i1) q[e] += pz[i] + pz[zstride + i];
-    }
-  for (; z < kp.splits; ++z, pz += zstride)
+    for (int e = 0; e < PE; ++e)
+      if (row[e] >= 0) q[e] += pz[row[e]] + pz[zstride + row[e]];
+  for (; z < nspl; ++z, pz += zstride)
 #pragma unroll
-    for (int e = 0; e < PE; ++e) {
-      const int i = i0 + threadIdx.x + e * NT;
-      if (i < i1) q[e] += pz[i];
-    }
+    for (int e = 0; e < PE; ++e)
+      if (row[e] >= 0) q[e] += pz[row[e]];
 #pragma unroll
   for (int e = 0; e < PE; ++e) {
     q[e] *= kp.scale;
@@ -703,8 +724,8 @@ __device__ __forceinline__ void pcg_step_body(Inst s0, int c0, int kmaxit, const
   float b[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // r.r, mf.t, nu.t, r.mf.t, r.mf, r.nu
 #pragma unroll
   for (int e = 0; e < PE; ++e) {
-    const int i = i0 + threadIdx.x + e * NT;
-    if (i < i1) {
+    const int i = ci[e];
+    if (i >= 0) {
       const float qq = mf[e] * (q[e] - qmean) - ry * nh[e] + lam * p[e];
       X[i] = xv[e] + al * p[e];
       const float rv = r[e] - al * qq;
@@ -737,12 +758,12 @@ __device__ __forceinline__ void pcg_step_body(Inst s0, int c0, int kmaxit, const
   const float beta = rzn / (float)rz_old;
 #pragma unroll
   for (int e = 0; e < PE; ++e) {
-    const int i = i0 + threadIdx.x + e * NT;
-    if (i < i1) {
+    const int i = ci[e];
+    if (i >= 0) {
       const float zz = mf[e] * (q[e] - tmean) - tb2 * nh[e];
       const float pn = zz + beta * p[e];
       P[i] = pn;
-      P16[prow * ld + i] = __float2bfloat16(pn);
+      if (row[e] >= 0) P16[prow * ld + row[e]] = __float2bfloat16(pn);
     }
   }
   if (lead) {

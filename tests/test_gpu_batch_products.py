@@ -7,6 +7,9 @@ with the psi'' weighting (fused into the GEMM epilogue when the product
 needs no split-K, otherwise split-K partials and a weighting pass), then
 A^T S split-K; plus the Gram-diagonal block (G nuhat, diag G).
 mvsk_batch_third runs the Hutchinson correction (rhat and A^T (psi''' o rhat)).
+Both run, as the solver does by default, on the union of the instances'
+working faces (A's columns gathered), and on all columns with the option
+face_products = 0.
 The reference is numpy FP64 on the centred panel: Eq. operator-hvp
 T^-1 A^T (psi''(z) o A v), Prop. 2 for diag G, Eq. operator-third for the
 correction.  Bound: A, the columns and the weighted rows are rounded to BF16
@@ -46,21 +49,46 @@ def _ctx(R):
     return m.MVSK(R, "bf16")
 
 
-# (n, T, B, nc, fused): the full sweep shape (64 instances x 9 PCG columns =
-# 576 columns, the fused-epilogue form) and small shapes (split-K form),
-# ragged in T, n and the column count.
-HVP_CASES = [(5440, 12000, 64, 9, 1), (300, 3001, 4, 9, 0), (130, 1000, 3, 5, 0), (1000, 2500, 7, 1, 0)]
+def _faces(n, B, rng, sparse):
+    """Working faces (B x n of 0/1): every coordinate free, or faces of 40-80
+    coordinates drawn from a shared pool of 400 (the overlapping supports of a
+    frontier sweep), so that their union U is a few hundred coordinates."""
+    if not sparse:
+        return None
+    pool = rng.choice(n, size=min(n, 400), replace=False)
+    M = np.zeros((B, n))
+    for b in range(B):
+        M[b, rng.choice(pool, size=min(len(pool), int(rng.integers(40, 81))), replace=False)] = 1.0
+    return M
 
 
-@pytest.mark.parametrize("n,T,B,nc,fused", HVP_CASES)
-def test_batch_hvp_matches_plain_products(n, T, B, nc, fused):
+# (n, T, B, nc, fused, sparse faces, face_products): the full sweep shape (64
+# instances x 9 PCG columns = 576 columns, the fused-epilogue form) with all
+# coordinates free and with sparse faces, on the face-restricted path and on
+# the all-column path; small shapes (split-K form), ragged in T, n and the
+# column count.
+HVP_CASES = [(5440, 12000, 64, 9, 1, True, 1), (5440, 12000, 64, 9, 1, False, 1), (5440, 12000, 64, 9, 1, False, 0),
+             (300, 3001, 4, 9, 0, True, 1), (300, 3001, 4, 9, 0, False, 0), (130, 1000, 3, 5, 0, True, 1),
+             (1000, 2500, 7, 1, 0, True, 1)]
+
+
+@pytest.mark.parametrize("n,T,B,nc,fused,sparse,fp", HVP_CASES)
+def test_batch_hvp_matches_plain_products(n, T, B, nc, fused, sparse, fp):
     R, A, C, X, rng = _inputs(n, T, B, 11)
+    M = _faces(n, B, rng, sparse)
     V = rng.standard_normal((B, nc, n))
     NU = rng.standard_normal((B, n))
+    if M is not None:
+        V *= M[:, None, :]
+        NU *= M
     NU /= np.linalg.norm(NU, axis=1, keepdims=True)
     ctx = _ctx(R)
-    HV, Gn, Dg, path = ctx.batch_hvp(C, X, NU, V)
+    ctx.set_option("face_products", fp)
+    HV, Gn, Dg, path = ctx.batch_hvp(C, X, NU, V, M)
     assert path[0] == fused, path  # which form of the weighted product ran
+    # coordinates the products are defined on: the union of the faces on the
+    # face-restricted path, every coordinate otherwise (zero outside)
+    Umask = np.ones(n, dtype=bool) if (fp == 0 or M is None) else M.any(axis=0)
     Z = A @ X.T                                   # T x B
     H = np.column_stack([O.d2psi(C[b], Z[:, b]) for b in range(B)])
     Aa = np.abs(A)
@@ -70,31 +98,42 @@ def test_batch_hvp_matches_plain_products(n, T, B, nc, fused):
     Hc = np.repeat(H, nc, axis=1)
     ref = (A.T @ (Hc * AV)).T / T
     scale = (Aa.T @ (np.abs(Hc) * AVa)).T / T
-    err = np.abs(HV.reshape(B * nc, n) - ref)
-    assert np.all(err <= 2e-2 * scale + 1e-300), float(np.max(err / (scale + 1e-300)))
+    got = HV.reshape(B * nc, n)
+    err = np.abs(got[:, Umask] - ref[:, Umask])
+    assert np.all(err <= 2e-2 * scale[:, Umask] + 1e-300), float(np.max(err / (scale[:, Umask] + 1e-300)))
+    assert np.all(got[:, ~Umask] == 0.0)
     # the Gram-diagonal block: G nuhat and diag G (Prop. 2)
     refg = (A.T @ (H * (A @ NU.T))).T / T
     scg = (Aa.T @ (np.abs(H) * (Aa @ np.abs(NU).T))).T / T
-    assert np.all(np.abs(Gn - refg) <= 2e-2 * scg + 1e-300)
+    assert np.all(np.abs(Gn - refg)[:, Umask] <= 2e-2 * scg[:, Umask] + 1e-300)
     refd = ((A * A).T @ H).T / T
     scd = ((A * A).T @ np.abs(H)).T / T
-    assert np.all(np.abs(Dg - refd) <= 2e-2 * scd + 1e-300)
+    assert np.all(np.abs(Dg - refd)[:, Umask] <= 2e-2 * scd[:, Umask] + 1e-300)
+    assert np.all(Gn[:, ~Umask] == 0.0) and np.all(Dg[:, ~Umask] == 0.0)
     # the same call again gives the same bits (fixed reduction orders)
-    HV2, _, _, _ = ctx.batch_hvp(C, X, NU, V)
+    HV2, _, _, _ = ctx.batch_hvp(C, X, NU, V, M)
     assert np.array_equal(HV, HV2)
 
 
-# (n, T, B, K): the full sweep (64 instances x 8 probe pairs) and small shapes.
-THIRD_CASES = [(5440, 12000, 64, 8), (300, 3001, 4, 8), (130, 1000, 3, 3)]
+# (n, T, B, K, sparse faces, face_products): the full sweep (64 instances x 8
+# probe pairs) and small shapes.
+THIRD_CASES = [(5440, 12000, 64, 8, True, 1), (5440, 12000, 64, 8, False, 0), (300, 3001, 4, 8, True, 1),
+               (130, 1000, 3, 3, False, 1)]
 
 
-@pytest.mark.parametrize("n,T,B,K", THIRD_CASES)
-def test_batch_third_matches_plain_products(n, T, B, K):
+@pytest.mark.parametrize("n,T,B,K,sparse,fp", THIRD_CASES)
+def test_batch_third_matches_plain_products(n, T, B, K, sparse, fp):
     R, A, C, X, rng = _inputs(n, T, B, 12)
+    M = _faces(n, B, rng, sparse)
     U = rng.standard_normal((B, K, n))
     P = rng.standard_normal((B, K, n))
+    if M is not None:
+        U *= M[:, None, :]
+        P *= M[:, None, :]
     ctx = _ctx(R)
-    at = ctx.batch_third(C, X, U, P)
+    ctx.set_option("face_products", fp)
+    at = ctx.batch_third(C, X, U, P, M)
+    Umask = np.ones(n, dtype=bool) if (fp == 0 or M is None) else M.any(axis=0)
     Z = A @ X.T
     Aa = np.abs(A)
     AU = (A @ U.reshape(B * K, n).T).reshape(T, B, K)
@@ -106,5 +145,6 @@ def test_batch_third_matches_plain_products(n, T, B, K):
     W3 = np.column_stack([O.d3psi(C[b], Z[:, b]) for b in range(B)])
     ref = (A.T @ (W3 * rhat)).T / T
     scale = (Aa.T @ (np.abs(W3) * rhat_a)).T / T
-    err = np.abs(at - ref)
-    assert np.all(err <= 2e-2 * scale + 1e-300), float(np.max(err / (scale + 1e-300)))
+    err = np.abs(at - ref)[:, Umask]
+    assert np.all(err <= 2e-2 * scale[:, Umask] + 1e-300), float(np.max(err / (scale[:, Umask] + 1e-300)))
+    assert np.all(at[:, ~Umask] == 0.0)
