@@ -205,7 +205,7 @@ def peaks():
 # Kinds whose launches the timed step samples: the tensor-core products of
 # the direction block (N = 576 fused / split, N = 64 second PCG round) and the
 # split FP64 products (value, gradient, line search).
-TIMED_KINDS = "gemm_tc_bf16_n192,gemm_tc_bf16_n64,oz_gemm"
+TIMED_KINDS = "gemm_tc_bf16_n192,gemm_tc_bf16_n64,oz_gemm_fwd,oz_gemm_bwd"
 
 
 def roofline_entry(name, d, pk, pk_src, T, n, ms_step):
@@ -221,7 +221,7 @@ def roofline_entry(name, d, pk, pk_src, T, n, ms_step):
          "share_of_step": round(d["total_ms"] * PROF_STRIDE / ms_step, 4), "traffic": None}
     tr = measured_traffic(name)
     e["traffic"] = None if tr is None else round(tr)
-    if name.startswith("oz_gemm"):
+    if name.startswith("oz_gemm") and not name.endswith("_gated"):
         byt = 14.0 * T * n
         e.update({"bound": "hbm", "unit": "GB/s", "achieved": round(byt / avg_s / 1e9, 1), "peak": pk["hbm_gbs"],
                   "algorithmic_bytes": byt, "fp64_equivalent_gbs": round(8.0 * T * n / avg_s / 1e9, 1),
@@ -300,7 +300,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     breakdown, _ = ctx.profile_read()
     ctx.profile_enable(False)
-    timed_kinds = {k: v for k, v in breakdown.items() if v["bytes_per_launch"] > 0}
+    timed_kinds = {k: v for k, v in breakdown.items() if v["bytes_per_launch"] > 0 and not k.endswith("_gated")}
     dom_name = max(timed_kinds.items(), key=lambda kv: kv[1]["total_ms"])[0] if timed_kinds else None
     sampler = ClockSampler(torch.cuda.current_device())
     ctx.profile_only(TIMED_KINDS + ("," + dom_name if dom_name else ""))
@@ -340,7 +340,7 @@ def run_ours(args, rank, world):
     live = statistics.mean(iters) / (statistics.mean(lock) * B) if lock and lock[0] else None
     roof, secondary = None, []
     for name, d in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"]):
-        if d["launches"] == 0:
+        if d["launches"] == 0 or name.endswith("_gated"):  # gated launches may skip their work
             continue
         e = roofline_entry(name, d, pk, pk_src, T, n, ms)
         if roof is None:

@@ -573,6 +573,8 @@ __global__ void k_hd_cols_u(Inst base, const int* idx, const int* info, __nv_bfl
   dst[(size_t)q * ld + j] = __float2bfloat16(v);
 }
 
+#include "face_small.cuh"
+
 // ---------------------------------------------------------------- host side
 
 mvsk_status batch_alloc(mvsk_ctx* c, BatchBuf& bb, int B) {
@@ -668,6 +670,17 @@ mvsk_status batch_alloc(mvsk_ctx* c, BatchBuf& bb, int B) {
   bb.base.kfs = 3LL * c->ld;
   TRY(get(sizeof(double) * 2 * Bs, &p));
   bb.kq_dev = p;
+  {  // small-face direction block
+    const size_t nch = (size_t)((c->T + kFRows - 1) / kFRows);
+    TRY(get(sizeof(int) * ld * Bs, &p));
+    bb.f_list = (int*)p;
+    TRY(get(sizeof(float) * nch * kMF * kMF * Bs, &p));
+    bb.f_gp = (float*)p;
+    TRY(get(sizeof(float) * kMF * kMF * Bs, &p));
+    bb.f_gram = (float*)p;
+    TRY(get(sizeof(float) * nch * kMF * Bs, &p));
+    bb.f_ap = (float*)p;
+  }
   if (c->A2_16T == nullptr) {
     TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * (size_t)c->n * c->Tp));
     c->A2_16T = (__nv_bfloat16*)p;
@@ -956,8 +969,6 @@ mvsk_status union_gather(mvsk_ctx* c, BatchBuf& bb, int B) {
   const unsigned gx = (unsigned)((c->Tp / 8 + 255) / 256);
   PROF_LAUNCH(NK_GATHER, (k_gather_rows_bf16<<<dim3(gx, (unsigned)c->ld), 256, 0, c->stream>>>(
                              c->A16T, c->Tp, bb.u_idx, bb.u_info, bb.u_AUT, c->Tp, c->Tp)));
-  PROF_LAUNCH(NK_GATHER, (k_gather_rows_bf16<<<dim3(gx, (unsigned)c->ld), 256, 0, c->stream>>>(
-                             c->A2_16T, c->Tp, bb.u_idx, bb.u_info, bb.u_A2UT, c->Tp, c->Tp)));
   PROF_LAUNCH(NK_GATHER, (k_transpose_u_bf16<<<dim3((unsigned)((c->T + 63) / 64), (unsigned)(c->ld / 64)), dim3(64, 8),
                                                0, c->stream>>>(bb.u_AUT, c->Tp, bb.u_info, c->T, bb.u_AU, c->ld)));
   return MVSK_OK;
@@ -967,6 +978,9 @@ mvsk_status union_gather(mvsk_ctx* c, BatchBuf& bb, int B) {
 mvsk_status hvpdiag_tc_batch_u(mvsk_ctx* c, BatchBuf& bb, int B, int gz) {
   const int N = 2 * B, gb = 4 * c->nsm;
   const unsigned gl = (unsigned)((c->ld + 255) / 256);
+  const unsigned gx = (unsigned)((c->Tp / 8 + 255) / 256);
+  PROF_LAUNCH(NK_GATHER, (k_gather_rows_bf16<<<dim3(gx, (unsigned)c->ld), 256, 0, c->stream>>>(
+                             c->A2_16T, c->Tp, bb.u_idx, bb.u_info, bb.u_A2UT, c->Tp, c->Tp)));
   PROF_LAUNCH(NK_HD_COLS, (k_hd_cols_u<<<dim3(gl, (unsigned)N), 256, 0, c->stream>>>(bb.base, bb.u_idx, bb.u_info,
                                                                                       bb.P16)));
   const int *r1 = nullptr, *r2 = nullptr, *r3 = nullptr;
@@ -1047,7 +1061,16 @@ PassArgs pass_args_inst(const double cc[4]) {
 }
 
 // One lockstep iteration of every instance (captured once per batch solve).
-mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<std::array<double, 4>>& cc) {
+mvsk_status batch_iteration_tail(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<std::array<double, 4>>& cc);
+
+// part -1: the whole iteration; with face-restricted products (bb.umode) it
+// is captured as three graphs: part 0 the oracle block (value, gradient,
+// face, face lists, union of the faces and its gathered columns), then part 2
+// the small-face direction block (face_small.cuh) when every face has at most
+// kMF coordinates, else part 1 (tensor-core products on the union); both end
+// with the quartic step and the boundary block.
+mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<std::array<double, 4>>& cc,
+                            int part = -1) {
   const Inst& base = bb.base;
   const int K = c->opt.probes, ncol1 = K + 1, ca = K + 1, kmax = c->opt.krylov_maxit;
   const int P = c->dir_prec;
@@ -1067,7 +1090,8 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     }
     return MVSK_OK;
   };
-  if (split) {
+  const bool head = part <= 0, dir = part != 0;
+  if (head && split) {
     for (int b0 = 0; b0 < B; b0 += kOzMaxB) {
       const int nb = B - b0 < kOzMaxB ? B - b0 : kOzMaxB, Bp = oz_bp(nb);
       int sp = 0;
@@ -1079,7 +1103,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
       PROF_LAUNCH(NK_OZ_G, (k_oz_fin_g<<<dim3((c->ld + 255) / 256, nb), 256, 0, c->stream>>>(
                                 oz.part, sp, Bp, oz.MpB, oz.eB, oz.fB, base, b0)));
     }
-  } else {
+  } else if (head) {
     for (int b = 0; b < B; ++b) {
       const Inst s = inst_at(base, b);
       PassArgs a = pass_args_inst(cc[b].data());
@@ -1090,11 +1114,46 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
       TRY(reduce_cols(c, P64, 1, s.g, c->ld, c->mu, 0.0, s.si + SI_DONE, nullptr, s.sd + SD_C1));
     }
   }
-  PROF_LAUNCH(NK_FACE, (k_face<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gs)));
-  (void)P;
   const bool U = bb.umode;  // direction products restricted to the union of the faces
+  if (head) {
+    PROF_LAUNCH(NK_FACE, (k_face<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gs)));
+    if (U) {
+      PROF_LAUNCH(NK_FACE_LIST, (k_face_list<<<dim3(1, B), 1024, 0, c->stream>>>(base, bb.f_list)));
+      PROF_LAUNCH(NK_FACE_LIST, (k_small_mode<<<1, 256, 0, c->stream>>>(base, B, bb.u_info)));
+      TRY(union_gather(c, bb, B));
+    }
+  }
+  (void)P;
+  if (!dir) return MVSK_OK;
+  const unsigned nch = (unsigned)((c->T + kFRows - 1) / kFRows);
+  if (part == 2) {  // every face small: explicit face Grams, PCG rounds in shared memory
+    constexpr int kTri = (kMF / 4) * (kMF / 4 + 1) / 2;
+    PROF_LAUNCH(NK_GRAM, (k_face_gram<<<dim3(nch, B, (kTri + kFBlk - 1) / kFBlk), 256, 0, c->stream>>>(
+                             base, bb.f_list, bb.u_AU, bb.u_pos, bb.f_gp)));
+    PROF_LAUNCH(NK_GRAM, (k_face_gram_finish<<<B, 256, 0, c->stream>>>(base, bb.f_list, bb.f_gp, (int)nch,
+                                                                         bb.f_gram, Gz)));
+    if (K > 0)
+      PROF_LAUNCH(NK_PROBE_FILL,
+                  (k_probe_fill<float><<<dim3((c->ld + 255) / 256, K, B), 256, 0, c->stream>>>(base, K)));
+    PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gz, -1)));
+    PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup_cols<float><<<dim3(ncol1, B), 512, 0, c->stream>>>(base)));
+    const size_t gsm = sizeof(float) * kMF * (kMF + 1);
+    PROF_LAUNCH(NK_PCG_ROUND, (k_pcg_round_small<<<dim3(ncol1, B), kMF, gsm, c->stream>>>(base, 0, kmax, bb.f_list,
+                                                                                          bb.f_gram)));
+    if (K > 0) {
+      PROF_LAUNCH(NK_HUTCH, (k_face_hutch<<<dim3(nch, B), 256, 0, c->stream>>>(base, K, bb.f_list, bb.u_AU, bb.u_pos,
+                                                                                 bb.f_ap)));
+      PROF_LAUNCH(NK_HUTCH, (k_face_hutch_finish<<<B, 256, 0, c->stream>>>(base, bb.f_list, bb.f_ap, (int)nch)));
+    } else {
+      for (int b = 0; b < B; ++b) CU(cudaMemsetAsync(inst_at(base, b).at, 0, sizeof(double) * c->ld, c->stream));
+    }
+    PROF_LAUNCH(NK_PCG_SETUP2, (k_pcg_setup2<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca, ca / 2)));
+    PROF_LAUNCH(NK_PCG_ROUND, (k_pcg_round_small<<<dim3(1, B), kMF, gsm, c->stream>>>(base, ca, kmax, bb.f_list,
+                                                                                      bb.f_gram)));
+    PROF_LAUNCH(NK_ASSEMBLE, (k_assemble<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca)));
+    return batch_iteration_tail(c, bb, B, cc);
+  }
   if (U) {
-    TRY(union_gather(c, bb, B));
     TRY(hvpdiag_tc_batch_u(c, bb, B, Gz));
   } else {
     TRY(hvpdiag_tc_batch(c, bb, B, Gz));
@@ -1150,6 +1209,27 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     PROF_LAUNCH(NK_PCG_STEP_A, (k_pcg_step_fc<<<dim3(kPCL, B), 512, 0, c->stream>>>(base, ca, kmax, kp)));
   }
   PROF_LAUNCH(NK_ASSEMBLE, (k_assemble<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca)));
+  return batch_iteration_tail(c, bb, B, cc);
+}
+
+// The quartic step and the boundary block of one lockstep iteration (after
+// the direction block of batch_iteration).
+mvsk_status batch_iteration_tail(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<std::array<double, 4>>& cc) {
+  const Inst& base = bb.base;
+  const bool split = c->opt.split_products != 0;
+  const OzBuf& oz = c->oz;
+  const int Gz = oz_row_ctas(c);
+  const int Gl = split ? oz_ls_ctas(c) : c->grid;
+  auto ls_split = [&](double* dvec, int skip_slot, const int* need) -> mvsk_status {
+    for (int b0 = 0; b0 < B; b0 += kOzMaxB) {
+      const int nb = B - b0 < kOzMaxB ? B - b0 : kOzMaxB;
+      int sp = 0;
+      TRY(oz_product(c, 0, dvec + (size_t)b0 * base.vs, base.vs, nb, oz_bp(nb), need, &sp));
+      PROF_LAUNCH(NK_OZ_LS, (k_oz_fin_ls<<<dim3(Gl, nb), 256, 0, c->stream>>>(oz.part, sp, oz_bp(nb), oz.MpF, oz.eF,
+                                                                             oz.fF, base, b0, skip_slot, bb.wls)));
+    }
+    return MVSK_OK;
+  };
   if (split) {
     TRY(ls_split(base.d, SI_DONE, nullptr));
   } else {
@@ -1294,6 +1374,8 @@ mvsk_status ensure_ubuf(mvsk_ctx* c, BatchBuf& bb) {
   CU(cudaMemsetAsync(bb.u_AUT, 0, sizeof(__nv_bfloat16) * ld * (size_t)c->Tp, c->stream));
   CU(cudaMemsetAsync(bb.u_A2UT, 0, sizeof(__nv_bfloat16) * ld * (size_t)c->Tp, c->stream));
   CU(cudaMemsetAsync(bb.u_specs, 0, sizeof(UProd) * kUMaxProds, c->stream));
+  CU(cudaFuncSetAttribute(k_pcg_round_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)(sizeof(float) * kMF * (kMF + 1))));
   return MVSK_OK;
 }
 
@@ -1368,17 +1450,26 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     TRY(u_prepare(c, bb, L, widths, 2, o.probes));
   }
   c->prof_uinfo = bb.umode ? bb.u_info : nullptr;
-  // graph of one lockstep iteration (c1 is read on the device, so calibration needs no re-capture)
-  cudaGraphExec_t gexec = nullptr;
-  long long per_graph = 0;
-  {
+  // graphs of one lockstep iteration (c1 is read on the device, so calibration
+  // needs no re-capture): the whole iteration, or with face-restricted
+  // products the oracle block (part 0) and the two direction forms (parts 1, 2)
+  struct ItGraph {
+    cudaGraphExec_t e = nullptr;
+    long long launches = 0;
+    size_t ev_b = 0, ev_e = 0;
+    ~ItGraph() {
+      if (e) cudaGraphExecDestroy(e);
+    }
+  };
+  ItGraph gfull, ghead, glarge, gsmall;
+  auto capture = [&](int part, ItGraph& gr) -> mvsk_status {
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     const long long l0 = c->launches;
-    c->ev_graph_begin = c->ev_kind.size();
-    const mvsk_status cs = batch_iteration(c, bb, L, cc);
-    c->ev_graph_end = c->ev_kind.size();
-    per_graph = c->launches - l0;
+    gr.ev_b = c->ev_kind.size();
+    const mvsk_status cs = batch_iteration(c, bb, L, cc, part);
+    gr.ev_e = c->ev_kind.size();
+    gr.launches = c->launches - l0;
     c->launches = l0;
     const cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
     if (cs != MVSK_OK) {
@@ -1386,16 +1477,29 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       return cs;
     }
     CU(ce);
-    const cudaError_t ie = cudaGraphInstantiate(&gexec, g, 0);
+    const cudaError_t ie = cudaGraphInstantiate(&gr.e, g, 0);
     cudaGraphDestroy(g);
     CU(ie);
+    return MVSK_OK;
+  };
+  if (bb.umode) {
+    TRY(capture(0, ghead));
+    TRY(capture(1, glarge));
+    TRY(capture(2, gsmall));
+  } else {
+    TRY(capture(-1, gfull));
   }
-  struct GraphGuard {
-    cudaGraphExec_t e;
-    ~GraphGuard() {
-      if (e) cudaGraphExecDestroy(e);
+  // replay of one graph (profiled launches folded in after each replay)
+  auto replay = [&](ItGraph& gr) -> mvsk_status {
+    CU(cudaGraphLaunch(gr.e, c->stream));
+    c->launches += gr.launches;
+    if (c->prof_on) {
+      CU(cudaStreamSynchronize(c->stream));
+      TRY(prof_collect(c, gr.ev_b, gr.ev_e));
     }
-  } guard{gexec};
+    return MVSK_OK;
+  };
+  int small_dir = 0;  // host copy of the direction form chosen on the device
   // c1-free part of the gradient at 1/n, once per request (psi_q depends on c2..c4 only):
   // in the lanes' G0 when every request has its lane, else per request in bb.Gq
   double* G0q = bb.G0;
@@ -1628,11 +1732,16 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       }
       bb.needz_req = 0;
     }
-    CU(cudaGraphLaunch(gexec, c->stream));
-    c->launches += per_graph;
-    if (c->prof_on) {
-      CU(cudaStreamSynchronize(c->stream));
-      TRY(prof_collect(c, c->ev_graph_begin, c->ev_graph_end));
+    if (bb.umode) {  // oracle block, then the direction form every face allows
+      TRY(replay(ghead));
+      small_dir = 0;
+      if (o.face_small) {
+        CU(cudaMemcpyAsync(&small_dir, bb.u_info + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        TRY(sync(c));
+      }
+      TRY(replay(small_dir ? gsmall : glarge));
+    } else {
+      TRY(replay(gfull));
     }
     guard_iters += 1;
     CU(cudaMemcpyAsync(si.data(), bb.base.si, sizeof(int) * si.size(), cudaMemcpyDeviceToHost, c->stream));

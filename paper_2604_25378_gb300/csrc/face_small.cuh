@@ -1,0 +1,439 @@
+// Direction block of a lockstep batch when every working face is small
+// (included into batch_impl.cuh).
+//
+// After the first steps of a solve the working face F of an instance holds a
+// few dozen coordinates.  The PCG configuration then needs the tangent
+// Hessian only on F: G_F = T^-1 A_F^T Diag(psi''(z)) A_F (Prop. 2) is an
+// m x m matrix (m = |F| <= kMF), formed once per iteration from the columns of
+// A in F, after which every Hessian-vector product of both PCG rounds is
+// G_F p (Eq. operator-hvp restricted to F, the same numbers as
+// T^-1 A^T (psi'' o A p) for p supported on F) and a whole PCG round runs in
+// one CTA per (instance, column) with G_F in shared memory.  The Hutchinson
+// correction a = T^-1 A_F^T (psi''' o rhat), rhat = K^-1 sum_k (A_F X_k) o
+// (A_F p_k) (Eq. operator-third), takes one more pass over A_F.  The columns
+// of A come from the union gather of the face-restricted products (BF16, the
+// precision of the other direction products); sums are FP32.
+#pragma once
+
+constexpr int kMF = 224;       // largest face handled here (one coordinate per thread of a PCG CTA)
+constexpr int kFBlk = 768;     // 4 x 4 Gram blocks per CTA of k_face_gram (three per thread)
+constexpr int kFRows = 480;    // rows of A per CTA of the Gram and Hutchinson passes
+constexpr int kFTile = 32;     // rows staged in shared memory at a time
+
+// Face list of instance blockIdx.y: fl[k] = i for the coordinates of its
+// working face (maskF = 1) in increasing order, si[SI_FCNT] = their count.
+// One CTA of 1024 threads per instance.
+__global__ void __launch_bounds__(1024) k_face_list(Inst base, int* fl_base) {
+  const Inst s = inst_at(base, blockIdx.y);
+  if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
+  int* fl = fl_base + (size_t)blockIdx.y * s.vs;
+  __shared__ int wsum[32];
+  const int n = s.n, per = (n + 1023) / 1024, i0 = threadIdx.x * per;
+  int cnt = 0;
+  for (int i = i0; i < i0 + per && i < n; ++i) cnt += s.maskF[i] != 0.0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int v = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) wsum[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    int w = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += u;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  int p = v - cnt + (warp > 0 ? wsum[warp - 1] : 0);
+  for (int i = i0; i < i0 + per && i < n; ++i)
+    if (s.maskF[i] != 0.0) fl[p++] = i;
+  if (threadIdx.x == 1023) s.si[SI_FCNT] = p;
+}
+
+// info[2] = 1 when every instance that needs a direction this iteration has a
+// face of at most kMF coordinates (the small-face block runs), else 0.
+__global__ void k_small_mode(Inst base, int B, int* info) {
+  int big = 0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const int* si = base.si + (size_t)b * kSI;
+    if (si[SI_DONE] == 0 && si[SI_SKIPDIR] == 0 && si[SI_FCNT] > kMF) big = 1;
+  }
+  big = __syncthreads_or(big);
+  if (threadIdx.x == 0) info[2] = big ? 0 : 1;
+}
+
+// Partial face Grams: CTA (x, b, z) sums psi''_b(z_t) a_tk a_tl over its
+// kFRows rows for blocks [z kFBlk, (z + 1) kFBlk) of the upper triangle of
+// 4 x 4 blocks (k, l < m_b), a_tk = A[t][fl[k]] from the gathered columns AU
+// (T x ld, column upos[fl[k]]).  Thread j owns blocks j, j + 256, j + 512 of
+// its CTA's range (the triangle has at most 1596 blocks for m = 224).
+// Out: gp[((b * nchunk + x) * kMF + k) * kMF + l], upper blocks.
+__global__ void __launch_bounds__(256) k_face_gram(Inst base, const int* fl_base, const __nv_bfloat16* AU,
+                                                   const int* upos, float* gp) {
+  const int b = blockIdx.y;
+  const Inst s = inst_at(base, b);
+  if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
+  const int m = s.si[SI_FCNT];
+  if (m > kMF) return;
+  const int* fl = fl_base + (size_t)b * s.vs;
+  const int ld = s.ld;
+  const long long T = s.T;
+  const long long t0 = (long long)blockIdx.x * kFRows, t1 = t0 + kFRows < T ? t0 + kFRows : T;
+  __shared__ int col[kMF];
+  __shared__ float a[kFTile][kMF + 4];
+  __shared__ float h[kFTile];
+  for (int k = threadIdx.x; k < kMF; k += blockDim.x) col[k] = k < m ? upos[fl[k]] : -1;
+  const float c2 = (float)s.sd[SD_C2], c3 = (float)s.sd[SD_C3], c4 = (float)s.sd[SD_C4];
+  const int nb = (m + 3) / 4, ntri = nb * (nb + 1) / 2;
+  if ((int)blockIdx.z * kFBlk >= ntri) return;
+  int bi[3], bj[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int blk = (int)blockIdx.z * kFBlk + threadIdx.x + q * 256;
+    bi[q] = bj[q] = -1;
+    if (blk < ntri) {  // row-major upper triangle: block (i, j), i <= j
+      int i = 0, rem = blk;
+      while (rem >= nb - i) {
+        rem -= nb - i;
+        ++i;
+      }
+      bi[q] = i;
+      bj[q] = i + rem;
+    }
+  }
+  float acc[3][16];
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[q][e] = 0.f;
+  __syncthreads();
+  for (long long tb = t0; tb < t1; tb += kFTile) {
+    const int rows = (int)(t1 - tb < kFTile ? t1 - tb : kFTile);
+    const int mp = 4 * nb;  // columns the blocks read (zero beyond m)
+    for (int e = threadIdx.x; e < kFTile * mp; e += blockDim.x) {
+      const int r = e / mp, k = e - r * mp;
+      float v = 0.f;
+      if (r < rows && k < m) v = __bfloat162float(AU[(size_t)(tb + r) * ld + col[k]]);
+      a[r][k] = v;
+    }
+    if (threadIdx.x < kFTile) {
+      float hv = 0.f;
+      if ((int)threadIdx.x < rows) {
+        const float z = (float)s.z[tb + threadIdx.x];
+        hv = 2.f * c2 - z * (6.f * c3 - 12.f * c4 * z);
+      }
+      h[threadIdx.x] = hv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (bi[q] < 0) continue;
+      const int k0 = 4 * bi[q], l0 = 4 * bj[q];
+      for (int r = 0; r < rows; ++r) {
+        const float hr = h[r];
+        float x[4], y[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          x[e] = hr * a[r][k0 + e];
+          y[e] = a[r][l0 + e];
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) acc[q][e * 4 + f] = fmaf(x[e], y[f], acc[q][e * 4 + f]);
+      }
+    }
+    __syncthreads();
+  }
+  float* out = gp + ((size_t)b * gridDim.x + blockIdx.x) * kMF * kMF;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (bi[q] < 0) continue;
+    const int k0 = 4 * bi[q], l0 = 4 * bj[q];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        if (k0 + e < m && l0 + f < m) out[(size_t)(k0 + e) * kMF + l0 + f] = acc[q][e * 4 + f];
+  }
+}
+
+// Face Gram of instance blockIdx.x from the partials (fixed chunk order),
+// G[k][l] = T^-1 sum, symmetric, into gram[b * kMF * kMF]; then, on the face,
+// diag G, G nuhat (zero off the face) and the scalar partials of the
+// diagonal block: spart[0] = T nuhat^T G nuhat, spart[1] = T 1_F^T G 1_F,
+// spart[2 .. 2 G) = 0 (k_pcg_setup adds G pairs).  256 threads.
+__global__ void __launch_bounds__(256) k_face_gram_finish(Inst base, const int* fl_base, const float* gp, int nchunk,
+                                                          float* gram, int G) {
+  const int b = blockIdx.x;
+  Inst s = inst_at(base, b);
+  if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
+  const int m = s.si[SI_FCNT];
+  if (m > kMF) return;
+  const int* fl = fl_base + (size_t)b * s.vs;
+  float* Gm = gram + (size_t)b * kMF * kMF;
+  const float invT = (float)s.sd[SD_INVT];
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int k = e / m, l = e - k * m;
+    if (k > l) continue;
+    const float* src = gp + (size_t)b * nchunk * kMF * kMF + (size_t)k * kMF + l;
+    float v = 0.f;
+    for (int c = 0; c < nchunk; ++c) v += src[(size_t)c * kMF * kMF];
+    v *= invT;
+    Gm[(size_t)k * kMF + l] = v;
+    Gm[(size_t)l * kMF + k] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
+    s.Gnu[i] = 0.0;
+    s.diagG[i] = 0.0;
+  }
+  __syncthreads();
+  __shared__ float nh[kMF];
+  __shared__ float red[2][8];
+  for (int k = threadIdx.x; k < m; k += blockDim.x) nh[k] = (float)s.nuhat[fl[k]];
+  __syncthreads();
+  float sn = 0.f, s1 = 0.f;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    float gv = 0.f, g1 = 0.f;
+    for (int l = 0; l < m; ++l) {
+      const float gk = Gm[(size_t)k * kMF + l];
+      gv = fmaf(gk, nh[l], gv);
+      g1 += gk;
+    }
+    s.Gnu[fl[k]] = (double)gv;
+    s.diagG[fl[k]] = (double)Gm[(size_t)k * kMF + k];
+    sn = fmaf(nh[k], gv, sn);
+    s1 += g1;
+  }
+  sn = warp_sum(sn);
+  s1 = warp_sum(s1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][warp] = sn;
+    red[1][warp] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a0 = 0.f, a1 = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a0 += red[0][w];
+      a1 += red[1][w];
+    }
+    const double Td = (double)s.T;
+    s.spart[0] = Td * (double)a0;
+    s.spart[1] = Td * (double)a1;
+    for (int g = 1; g < G; ++g) s.spart[2 * g] = s.spart[2 * g + 1] = 0.0;
+  }
+}
+
+// Sums of six floats over a CTA of kMF threads (kMF / 32 warps), added in
+// warp order so that every thread holds the same totals.
+__device__ __forceinline__ void cta_sum6(float (&v)[6], float (*scr)[6]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) v[q] = warp_sum(v[q]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) scr[warp][q] = v[q];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < kMF / 32; ++w) t += scr[w][q];
+    v[q] = t;
+  }
+}
+
+// A whole PCG round of column c = c0 + blockIdx.x of instance blockIdx.y on
+// its face (m <= kMF coordinates, one per thread), with G_F from shared
+// memory: the recurrence of the batched step (k_pcg_step_f) with Q = G_F p
+// instead of the tensor-core products, from the state k_pcg_setup_cols (or
+// k_pcg_setup2) left (X = 0, R = B, P = Z, rz, rhsn, active flag), up to the
+// iteration budget; the final X, R, P and rz are written back on the face.
+__global__ void __launch_bounds__(kMF) k_pcg_round_small(Inst base, int c0, int kmaxit, const int* fl_base,
+                                                         const float* gram) {
+  const int b = blockIdx.y, c = c0 + blockIdx.x;
+  Inst s = inst_at(base, b);
+  int* SI = s.si;
+  if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
+  const int m = SI[SI_FCNT];
+  if (m > kMF || SI[SI_ACT + c] == 0) return;
+  extern __shared__ float gs[];  // G_F, kMF x (kMF + 1)
+  __shared__ float pv[kMF];
+  __shared__ float scr[kMF / 32][6];
+  const int* fl = fl_base + (size_t)b * s.vs;
+  const float* Gm = gram + (size_t)b * kMF * kMF;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int k = e / m, l = e - k * m;
+    gs[k * (kMF + 1) + l] = Gm[(size_t)k * kMF + l];
+  }
+  const int ld = s.ld, k = threadIdx.x;
+  const bool on = k < m;
+  const int i = on ? fl[k] : 0;
+  float* X = kcol<float>(s.X, c, ld);
+  float* R = kcol<float>(s.R, c, ld);
+  float* P = kcol<float>(s.P, c, ld);
+  const Face<float> f0 = face_of<float>(s);
+  float p = 0.f, r = 0.f, x = 0.f, nh = 0.f, dg = 1.f;
+  if (on) {
+    p = P[i];
+    r = R[i];
+    x = X[i];
+    nh = f0.nh[i];
+    dg = f0.dg[i];
+  }
+  const float mf = on ? 1.f : 0.f;
+  const float fm = (float)m, lam = (float)s.sd[SD_LAM];
+  const double ktol = s.sd[SD_KTOL] * s.rhsn[c];
+  float rz = (float)s.rz[c];
+  int its = SI[SI_CITS + c], act = 1;
+  while (act) {
+    pv[k] = p;
+    __syncthreads();
+    float q = 0.f;
+    if (on) {
+      const float* gr = gs + k * (kMF + 1);
+      for (int l = 0; l < m; ++l) q = fmaf(gr[l], pv[l], q);
+    }
+    float a6[6] = {mf * q, nh * q, p * mf * q, p * mf, p * nh, p * p};
+    cta_sum6(a6, scr);
+    const float qmean = a6[0] / fm, ry = a6[1];
+    const float pq = a6[2] - qmean * a6[3] - ry * a6[4] + lam * a6[5];
+    if (!(pq > 0.f)) {
+      act = 0;
+      break;
+    }
+    const float al = rz / pq;
+    const float qq = mf * (q - qmean) - ry * nh + lam * p;
+    x += al * p;
+    r -= al * qq;
+    const float t = r / dg;
+    float b6[6] = {r * r, mf * t, nh * t, r * mf * t, r * mf, r * nh};
+    cta_sum6(b6, scr);
+    its += 1;
+    if (sqrt((double)b6[0]) <= ktol) {
+      act = 0;
+      break;
+    }
+    const float tmean = b6[1] / fm, tb2 = b6[2];
+    const float rzn = b6[3] - tmean * b6[4] - tb2 * b6[5];
+    const float beta = rzn / rz;
+    p = mf * (t - tmean) - tb2 * nh + beta * p;
+    rz = rzn;
+    if (its >= kmaxit) {
+      act = 0;
+      break;
+    }
+    __syncthreads();  // pv is rewritten at the top of the next step
+  }
+  if (on) {
+    X[i] = x;
+    R[i] = r;
+    P[i] = p;
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(&SI[SI_KRY], its - SI[SI_CITS + c]);
+    SI[SI_CITS + c] = its;
+    SI[SI_ACT + c] = 0;
+    s.rz[c] = (double)rz;
+  }
+}
+
+// Partial Hutchinson corrections: CTA (x, b) over its kFRows rows t of A_F:
+// u_k = a_t . X_{1+k}, v_k = a_t . B_{1+k} (the PCG solutions and projected
+// probes on the face), rhat_t = K^-1 sum_k u_k v_k, w_t = psi'''(z_t) rhat_t,
+// out[l] = sum_t w_t a_tl.  One warp per row; lane j owns face coordinates
+// j, j + 32, ... .  Out: ap[(b * nchunk + x) * kMF + l].
+__global__ void __launch_bounds__(256) k_face_hutch(Inst base, int K, const int* fl_base, const __nv_bfloat16* AU,
+                                                    const int* upos, float* ap) {
+  const int b = blockIdx.y;
+  const Inst s = inst_at(base, b);
+  if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
+  const int m = s.si[SI_FCNT];
+  if (m > kMF) return;
+  constexpr int kE = kMF / 32;  // face coordinates per lane
+  __shared__ float xs[kMaxProbes][kMF], bs[kMaxProbes][kMF];
+  __shared__ int col[kMF];
+  __shared__ float red[8][kMF];
+  const int* fl = fl_base + (size_t)b * s.vs;
+  const int ld = s.ld;
+  for (int e = threadIdx.x; e < K * kMF; e += blockDim.x) {
+    const int kk = e / kMF, l = e - kk * kMF;
+    float xv = 0.f, bv = 0.f;
+    if (l < m) {
+      xv = kcol<float>(s.X, 1 + kk, ld)[fl[l]];
+      bv = kcol<float>(s.Bv, 1 + kk, ld)[fl[l]];
+    }
+    xs[kk][l] = xv;
+    bs[kk][l] = bv;
+  }
+  for (int l = threadIdx.x; l < kMF; l += blockDim.x) col[l] = l < m ? upos[fl[l]] : -1;
+  __syncthreads();
+  const float c3 = (float)s.sd[SD_C3], c4 = (float)s.sd[SD_C4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long T = s.T, t0 = (long long)blockIdx.x * kFRows, t1 = t0 + kFRows < T ? t0 + kFRows : T;
+  float acc[kE];
+#pragma unroll
+  for (int e = 0; e < kE; ++e) acc[e] = 0.f;
+  for (long long t = t0 + warp; t < t1; t += 8) {
+    float av[kE];
+#pragma unroll
+    for (int e = 0; e < kE; ++e) {
+      const int l = lane + 32 * e;
+      av[e] = l < m ? __bfloat162float(AU[(size_t)t * ld + col[l]]) : 0.f;
+    }
+    float rh = 0.f;
+    for (int kk = 0; kk < K; ++kk) {
+      float u = 0.f, v = 0.f;
+#pragma unroll
+      for (int e = 0; e < kE; ++e) {
+        u = fmaf(av[e], xs[kk][lane + 32 * e], u);
+        v = fmaf(av[e], bs[kk][lane + 32 * e], v);
+      }
+      u = warp_sum(u);
+      v = warp_sum(v);
+      rh = fmaf(u, v, rh);
+    }
+    const float z = (float)s.z[t];
+    const float w = (-6.f * c3 + 24.f * c4 * z) * (rh / (float)K);
+#pragma unroll
+    for (int e = 0; e < kE; ++e) acc[e] = fmaf(w, av[e], acc[e]);
+  }
+#pragma unroll
+  for (int e = 0; e < kE; ++e) red[warp][lane + 32 * e] = acc[e];
+  __syncthreads();
+  float* out = ap + ((size_t)b * gridDim.x + blockIdx.x) * kMF;
+  for (int l = threadIdx.x; l < m; l += blockDim.x) {
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) v += red[w][l];
+    out[l] = v;
+  }
+}
+
+// at_b = T^-1 sum over the chunks (fixed order) on the face, zero elsewhere.
+__global__ void k_face_hutch_finish(Inst base, const int* fl_base, const float* ap, int nchunk) {
+  const int b = blockIdx.x;
+  Inst s = inst_at(base, b);
+  if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
+  const int m = s.si[SI_FCNT];
+  if (m > kMF) return;
+  const int* fl = fl_base + (size_t)b * s.vs;
+  for (int i = threadIdx.x; i < s.ld; i += blockDim.x) s.at[i] = 0.0;
+  __syncthreads();
+  const double invT = s.sd[SD_INVT];
+  for (int l = threadIdx.x; l < m; l += blockDim.x) {
+    float v = 0.f;
+    for (int c = 0; c < nchunk; ++c) v += ap[((size_t)b * nchunk + c) * kMF + l];
+    s.at[fl[l]] = invT * (double)v;
+  }
+}

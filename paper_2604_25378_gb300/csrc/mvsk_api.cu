@@ -38,6 +38,7 @@ struct Options {
   int line_search = 0;     // 0 exact quartic step, 1 Armijo backtracking on the quartic
   int group_cal = 1;       // batched solves: requests sharing (c2, c3, c4) start calibration on a c1 grid
   int face_products = 1;   // batched solves: direction products restricted to the union of the faces
+  int face_small = 1;      // ... and, when every face is small, explicit face Grams instead of the products
   unsigned long long probe_seed = 0x5EEDull;
 };
 
@@ -78,6 +79,10 @@ struct BatchBuf {
   mvsk::UProd* u_specs = nullptr;
   std::vector<mvsk::UProd> u_hspec;
   bool umode = false;
+  // small-face direction block (face_small.cuh): face lists (ld ints per
+  // instance), partial and final face Grams, partial Hutchinson corrections
+  int* f_list = nullptr;
+  float *f_gp = nullptr, *f_gram = nullptr, *f_ap = nullptr;
   int qcap = 0;
 };
 
@@ -419,11 +424,13 @@ const char* const kKernelNames[] = {"k_face", "k_probe_fill", "k_pcg_setup", "k_
                                     "k_assemble", "k_decide1", "k_decide2", "k_end_iter", "k_oz_fin_z",
                                     "k_oz_fin_g", "k_oz_fin_ls", "k_oz_split_vecs", "k_need_ls2", "k_reduce_cols",
                                     "k_hd_cols", "k_hd_reduce1", "k_hd_reduce2", "k_hd_reduce_diag",
-                                    "k_pcg_step_a", "k_z_step", "k_union", "k_gather_u"};
+                                    "k_pcg_step_a", "k_z_step", "k_union", "k_gather_u", "k_face_list",
+                                    "k_face_gram", "k_pcg_round", "k_face_hutch"};
 enum NamedKernel : int {
   NK_FACE, NK_PROBE_FILL, NK_PCG_SETUP, NK_PCG_STEP, NK_COLS, NK_HVP1, NK_HVP2, NK_RHAT, NK_PCG_SETUP2, NK_ASSEMBLE,
   NK_DECIDE1, NK_DECIDE2, NK_END_ITER, NK_OZ_Z, NK_OZ_G, NK_OZ_LS, NK_OZ_SPLIT, NK_NEED, NK_REDUCE_COLS, NK_HD_COLS,
-  NK_HD_RED1, NK_HD_RED2, NK_HD_DIAG, NK_PCG_STEP_A, NK_ZSTEP, NK_UNION, NK_GATHER, NK_COUNT
+  NK_HD_RED1, NK_HD_RED2, NK_HD_DIAG, NK_PCG_STEP_A, NK_ZSTEP, NK_UNION, NK_GATHER, NK_FACE_LIST, NK_GRAM, NK_PCG_ROUND,
+  NK_HUTCH, NK_COUNT
 };
 
 mvsk_status prof_begin(mvsk_ctx* c, int kind, double work) {
@@ -1499,6 +1506,7 @@ mvsk_status mvsk_set_option(mvsk_ctx* c, const char* key, double v) {
   else if (k == "line_search" && cnt(v, 0, 1)) o.line_search = (int)v;
   else if (k == "group_calibration" && cnt(v, 0, 1)) o.group_cal = (int)v;
   else if (k == "face_products" && cnt(v, 0, 1)) o.face_products = (int)v;
+  else if (k == "face_small" && cnt(v, 0, 1)) o.face_small = (int)v;
   else return fail(MVSK_EINVAL, "unknown option or bad value: %s = %g", key, v);
   if (c->prefs_set && k == "pref_scaling") mvsk_set_prefs(c, c->lam, c->target);
   return MVSK_OK;
@@ -1730,8 +1738,8 @@ static void kind_name(int kind, char* out, size_t len) {
     snprintf(out, len, "rowpass_%s_%s_%d", precs[(kind / 128) % 3], modes[(kind / 8) % 16 % 8], kind % 8);
   else if (kind < 680)
     snprintf(out, len, "gemm_tc_bf16_n%d", kind - 400);
-  else if (kind == 680 || kind == 681)
-    snprintf(out, len, "oz_gemm_%s", kind == 680 ? "fwd" : "bwd");
+  else if (kind >= 680 && kind <= 683)
+    snprintf(out, len, "oz_gemm_%s%s", (kind & 1) ? "bwd" : "fwd", kind >= 682 ? "_gated" : "");
   else if (kind >= kKindNamed && kind < kKindNamed + NK_COUNT)
     snprintf(out, len, "%s", kKernelNames[kind - kKindNamed]);
   else

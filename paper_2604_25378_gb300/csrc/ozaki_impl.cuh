@@ -77,7 +77,9 @@ mvsk_status oz_product(mvsk_ctx* c, int trans, const double* V, long long vstrid
   const CUtensorMap& tx = trans ? o.tmXB : o.tmXF;
   // work: BF16 tensor FLOPs issued (kOzS (kOzS + 1) / 2 digit products)
   const double flops = 2.0 * (double)Mp * (double)((ldk + kTcBK - 1) / kTcBK * kTcBK) * Bp * (kOzS * (kOzS + 1) / 2);
-  TRY(prof_begin(c, kKindOz + trans, flops));
+  // launches gated by a device flag (z = A x on refreshes, the projected
+  // segment) have their own kind: when skipped they do no work
+  TRY(prof_begin(c, need != nullptr ? kKindOz + 2 + trans : kKindOz + trans, flops));
   switch (Bp) {
     case 16:
       k_oz_gemm<16><<<grid, 128, oz_smem_bytes(16), c->stream>>>(ad, tx, Mp, M, (int)K, nkt, o.part, Mp, c->err,

@@ -28,6 +28,7 @@ enum SI : int {
   SI_NREL, SI_KRY, SI_NCOL, SI_PROBES, SI_SEEDLO, SI_SEEDHI, SI_HISTN, SI_KMAXIT, SI_DIRONLY,
   SI_PASSES, SI_HVPS, SI_THIRD, SI_BR_RAW, SI_BR_SEG, SI_BR_CAP, SI_BR_FACE, SI_ARCMAX,
   SI_LSRULE,        // step rule along d: 0 exact quartic, 1 Armijo backtracking on the quartic
+  SI_FCNT,          // coordinates of the working face in the face list (lockstep batches)
   SI_LIVE = 30,     // live-column count per PCG group (10 groups of two columns)
   SI_ACT = 40,      // per-column active flags (20 columns)
   SI_CITS = 60,     // per-column PCG iteration counts (20 columns)

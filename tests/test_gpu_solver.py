@@ -241,6 +241,7 @@ def test_profile_stride_samples_launches():
     R = panels.sector_factor_panel(40, 600, 3)
     lams = np.array([(1, 1, 1, 1), (1, 1, 0.5, 2)], dtype=float)
     ctx = m.MVSK(R, "bf16")
+    ctx.set_option("face_small", 0)  # the per-step products and steps in every iteration
     ctx.solve_batch(lams, np.full(2, np.nan), m.PCG, 1e-10)  # buffers built
     counts = {}
     for k in (1, 3):
@@ -340,3 +341,33 @@ def test_group_calibration_matches_per_request():
     c = O.scale_preferences(lams[b], A, "standardised")
     cc, x_ref, _, _ = O.calibrate_target(A, mu, c, tgs[b], "pcg", 1e-12, rel_tol=1e-12)
     assert np.max(np.abs(W1[b] - x_ref)) <= 1e-7
+
+
+def test_small_face_direction_matches_products():
+    """Once every working face of a batch has at most 128 coordinates, the
+    direction block forms each face's Gram matrix and runs both PCG rounds
+    on it (option face_small, on by default) instead of the tensor-core
+    products on the union of the faces: both forms must reach the same
+    minimisers (judged by the oracle's KKT residual), and the products-only
+    form must agree with the oracle's own minimiser under the certificate."""
+    import paper_2604_25378_gb300 as m
+    R = panels.garch_sector_panel(600, 6000, 41)
+    mu, A = O.centre(R)
+    lams = np.array([(1, 1, 0.5, 2), (1, 1, 2, 0.5), (1, 1, 1, 1), (0.5, 1, 0.5, 2), (1, 1, 2, 2)], dtype=float)
+    tg = np.array([np.nan, np.nan, np.nan, panels.quantile_targets(R, [0.7])[0], np.nan])
+    ctx = m.MVSK(R, "bf16")
+    W1, inf1 = ctx.solve_batch(lams, tg, m.PCG, 1e-10)
+    ctx.set_option("face_small", 0)
+    W0, inf0 = ctx.solve_batch(lams, tg, m.PCG, 1e-10)
+    ctx.set_option("face_small", 1)
+    x0 = np.full(600, 1.0 / 600)
+    for b in range(len(lams)):
+        assert inf1[b]["status"] == "ok" and inf0[b]["status"] == "ok", (b, inf1[b], inf0[b])
+        cg = np.asarray(inf1[b]["c"])
+        k0 = O.kkt_residual(x0, O.gradient(A, mu, cg, x0), 1e-8)
+        assert O.kkt_residual(W1[b], O.gradient(A, mu, cg, W1[b]), 1e-8) <= 1.5e-10 * k0, b
+        if O.convexity_certificate(cg):
+            assert np.max(np.abs(W1[b] - W0[b])) <= 1e-8, (b, np.max(np.abs(W1[b] - W0[b])))
+    c = O.scale_preferences(lams[0], A, "standardised")
+    x_ref, _ = O.solve(A, mu, c, "pcg", 1e-12)
+    assert np.max(np.abs(W1[0] - x_ref)) <= 1e-9
