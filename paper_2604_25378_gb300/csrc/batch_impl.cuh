@@ -1127,11 +1127,11 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
   if (!dir) return MVSK_OK;
   const unsigned nch = (unsigned)((c->T + kFRows - 1) / kFRows);
   if (part == 2) {  // every face small: explicit face Grams, PCG rounds in shared memory
-    constexpr int kTri = (kMF / 4) * (kMF / 4 + 1) / 2;
-    PROF_LAUNCH(NK_GRAM, (k_face_gram<<<dim3(nch, B, (kTri + kFBlk - 1) / kFBlk), 256, 0, c->stream>>>(
+    constexpr int kTri = (kMF / 8) * (kMF / 8 + 1) / 2;  // 8 x 8 blocks of the largest face
+    PROF_LAUNCH(NK_GRAM, (k_face_gram<<<dim3(nch, B, (kTri + 255) / 256), 256, kGramSmem, c->stream>>>(
                              base, bb.f_list, bb.u_AU, bb.u_pos, bb.f_gp)));
-    PROF_LAUNCH(NK_GRAM, (k_face_gram_finish<<<B, 256, 0, c->stream>>>(base, bb.f_list, bb.f_gp, (int)nch,
-                                                                         bb.f_gram, Gz)));
+    PROF_LAUNCH(NK_GRAM, (k_face_gram_sum<<<dim3(16, B), 256, 0, c->stream>>>(base, bb.f_gp, (int)nch, bb.f_gram)));
+    PROF_LAUNCH(NK_GRAM, (k_face_gram_finish<<<B, 256, 0, c->stream>>>(base, bb.f_list, bb.f_gram, Gz)));
     if (K > 0)
       PROF_LAUNCH(NK_PROBE_FILL,
                   (k_probe_fill<float><<<dim3((c->ld + 255) / 256, K, B), 256, 0, c->stream>>>(base, K)));
@@ -1376,6 +1376,7 @@ mvsk_status ensure_ubuf(mvsk_ctx* c, BatchBuf& bb) {
   CU(cudaMemsetAsync(bb.u_specs, 0, sizeof(UProd) * kUMaxProds, c->stream));
   CU(cudaFuncSetAttribute(k_pcg_round_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)(sizeof(float) * kMF * (kMF + 1))));
+  CU(cudaFuncSetAttribute(k_face_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramSmem));
   return MVSK_OK;
 }
 

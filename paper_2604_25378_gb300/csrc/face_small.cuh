@@ -16,7 +16,7 @@
 #pragma once
 
 constexpr int kMF = 224;       // largest face handled here (one coordinate per thread of a PCG CTA)
-constexpr int kFBlk = 768;     // 4 x 4 Gram blocks per CTA of k_face_gram (three per thread)
+constexpr int kFRg = 8;        // largest number of row groups of a k_face_gram CTA
 constexpr int kFRows = 480;    // rows of A per CTA of the Gram and Hutchinson passes
 constexpr int kFTile = 32;     // rows staged in shared memory at a time
 
@@ -68,12 +68,19 @@ __global__ void k_small_mode(Inst base, int B, int* info) {
   if (threadIdx.x == 0) info[2] = big ? 0 : 1;
 }
 
-// Partial face Grams: CTA (x, b, z) sums psi''_b(z_t) a_tk a_tl over its
-// kFRows rows for blocks [z kFBlk, (z + 1) kFBlk) of the upper triangle of
-// 4 x 4 blocks (k, l < m_b), a_tk = A[t][fl[k]] from the gathered columns AU
-// (T x ld, column upos[fl[k]]).  Thread j owns blocks j, j + 256, j + 512 of
-// its CTA's range (the triangle has at most 1596 blocks for m = 224).
-// Out: gp[((b * nchunk + x) * kMF + k) * kMF + l], upper blocks.
+// Partial face Grams.  CTA (x, b, z) covers rows [x kFRows, (x + 1) kFRows)
+// of instance b: G_part[k][l] = sum_t psi2(z_t) a_tk a_tl (psi2 the second
+// derivative of psi) for k, l < m_b in 8 x 8 register blocks of the upper
+// triangle, a_tk = A[t][fl[k]] from the gathered columns AU (T x ld, column
+// upos[fl[k]]), staged kFTile rows at a time in shared memory.  With few
+// blocks (small faces) the rows of the chunk are also split among up to kFRg
+// row groups (thread j: block z * 256 + j mod nblk, row group j / nblk),
+// whose sums are added in shared memory in group order.  Out: slab (b, x) of
+// kMF^2 floats, element (k, l) at k mp + l (mp = m rounded up to 8), for the
+// blocks of this CTA.  Dynamic shared memory: kGramSmem bytes.
+constexpr int kGramRed = 256 * 65;  // row-group sums: 256 threads x 64 values (+1 pad)
+constexpr size_t kGramSmem = sizeof(float) * ((size_t)kGramRed + (size_t)kFTile * (kMF + 4) + kFTile) + sizeof(int) * kMF;
+
 __global__ void __launch_bounds__(256) k_face_gram(Inst base, const int* fl_base, const __nv_bfloat16* AU,
                                                    const int* upos, float* gp) {
   const int b = blockIdx.y;
@@ -81,41 +88,39 @@ __global__ void __launch_bounds__(256) k_face_gram(Inst base, const int* fl_base
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
   const int m = s.si[SI_FCNT];
   if (m > kMF) return;
+  const int nb = (m + 7) / 8, ntri = nb * (nb + 1) / 2, mp = 8 * nb;
+  if ((int)blockIdx.z * 256 >= ntri) return;
+  const int nblk = ntri - (int)blockIdx.z * 256 < 256 ? ntri - (int)blockIdx.z * 256 : 256;
+  int rg_n = ntri < 256 ? 256 / ntri : 1;  // row groups only when one CTA holds every block
+  if (rg_n > kFRg) rg_n = kFRg;
+  extern __shared__ __align__(16) float fsm[];
+  float* red = fsm;                                           // kGramRed
+  float (*a)[kMF + 4] = reinterpret_cast<float (*)[kMF + 4]>(fsm + kGramRed);
+  float* h = fsm + kGramRed + kFTile * (kMF + 4);
+  int* col = reinterpret_cast<int*>(h + kFTile);
   const int* fl = fl_base + (size_t)b * s.vs;
   const int ld = s.ld;
   const long long T = s.T;
   const long long t0 = (long long)blockIdx.x * kFRows, t1 = t0 + kFRows < T ? t0 + kFRows : T;
-  __shared__ int col[kMF];
-  __shared__ float a[kFTile][kMF + 4];
-  __shared__ float h[kFTile];
   for (int k = threadIdx.x; k < kMF; k += blockDim.x) col[k] = k < m ? upos[fl[k]] : -1;
   const float c2 = (float)s.sd[SD_C2], c3 = (float)s.sd[SD_C3], c4 = (float)s.sd[SD_C4];
-  const int nb = (m + 3) / 4, ntri = nb * (nb + 1) / 2;
-  if ((int)blockIdx.z * kFBlk >= ntri) return;
-  int bi[3], bj[3];
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const int blk = (int)blockIdx.z * kFBlk + threadIdx.x + q * 256;
-    bi[q] = bj[q] = -1;
-    if (blk < ntri) {  // row-major upper triangle: block (i, j), i <= j
-      int i = 0, rem = blk;
-      while (rem >= nb - i) {
-        rem -= nb - i;
-        ++i;
-      }
-      bi[q] = i;
-      bj[q] = i + rem;
+  const int blk = (int)threadIdx.x % nblk, rg = (int)threadIdx.x / nblk;
+  const bool act = rg < rg_n;
+  int bi = 0, bj = 0;
+  {  // block index -> (bi, bj) of the row-major upper triangle
+    int rem = (int)blockIdx.z * 256 + blk;
+    while (rem >= nb - bi) {
+      rem -= nb - bi;
+      ++bi;
     }
+    bj = bi + rem;
   }
-  float acc[3][16];
+  float acc[64];
 #pragma unroll
-  for (int q = 0; q < 3; ++q)
-#pragma unroll
-    for (int e = 0; e < 16; ++e) acc[q][e] = 0.f;
+  for (int e = 0; e < 64; ++e) acc[e] = 0.f;
   __syncthreads();
   for (long long tb = t0; tb < t1; tb += kFTile) {
     const int rows = (int)(t1 - tb < kFTile ? t1 - tb : kFTile);
-    const int mp = 4 * nb;  // columns the blocks read (zero beyond m)
     for (int e = threadIdx.x; e < kFTile * mp; e += blockDim.x) {
       const int r = e / mp, k = e - r * mp;
       float v = 0.f;
@@ -131,65 +136,85 @@ __global__ void __launch_bounds__(256) k_face_gram(Inst base, const int* fl_base
       h[threadIdx.x] = hv;
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      if (bi[q] < 0) continue;
-      const int k0 = 4 * bi[q], l0 = 4 * bj[q];
-      for (int r = 0; r < rows; ++r) {
+    if (act) {
+      const int k0 = 8 * bi, l0 = 8 * bj;
+      for (int r = rg; r < rows; r += rg_n) {
         const float hr = h[r];
-        float x[4], y[4];
+        const float4 x0 = *reinterpret_cast<const float4*>(&a[r][k0]);
+        const float4 x1 = *reinterpret_cast<const float4*>(&a[r][k0 + 4]);
+        const float4 y0 = *reinterpret_cast<const float4*>(&a[r][l0]);
+        const float4 y1 = *reinterpret_cast<const float4*>(&a[r][l0 + 4]);
+        const float x[8] = {hr * x0.x, hr * x0.y, hr * x0.z, hr * x0.w, hr * x1.x, hr * x1.y, hr * x1.z, hr * x1.w};
+        const float y[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          x[e] = hr * a[r][k0 + e];
-          y[e] = a[r][l0 + e];
-        }
+        for (int e = 0; e < 8; ++e)
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-#pragma unroll
-          for (int f = 0; f < 4; ++f) acc[q][e * 4 + f] = fmaf(x[e], y[f], acc[q][e * 4 + f]);
+          for (int f = 0; f < 8; ++f) acc[e * 8 + f] = fmaf(x[e], y[f], acc[e * 8 + f]);
       }
     }
     __syncthreads();
   }
-  float* out = gp + ((size_t)b * gridDim.x + blockIdx.x) * kMF * kMF;
+  // row groups: deposit, then group 0 adds them in order
+  if (rg_n > 1) {
+    if (act)
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    if (bi[q] < 0) continue;
-    const int k0 = 4 * bi[q], l0 = 4 * bj[q];
+      for (int e = 0; e < 64; ++e) red[(size_t)threadIdx.x * 65 + e] = acc[e];
+    __syncthreads();
+    if (act && rg == 0)
+      for (int g = 1; g < rg_n; ++g) {
+        const float* src = red + (size_t)(g * nblk + blk) * 65;
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
-#pragma unroll
-      for (int f = 0; f < 4; ++f)
-        if (k0 + e < m && l0 + f < m) out[(size_t)(k0 + e) * kMF + l0 + f] = acc[q][e * 4 + f];
+        for (int e = 0; e < 64; ++e) acc[e] += src[e];
+      }
   }
+  if (!act || rg != 0) return;
+  float* out = gp + ((size_t)b * gridDim.x + blockIdx.x) * kMF * kMF;
+  const int k0 = 8 * bi, l0 = 8 * bj;
+#pragma unroll
+  for (int e = 0; e < 8; ++e)
+#pragma unroll
+    for (int f = 0; f < 8; ++f)
+      if (k0 + e < m && l0 + f < m) out[(size_t)(k0 + e) * mp + l0 + f] = acc[e * 8 + f];
 }
 
-// Face Gram of instance blockIdx.x from the partials (fixed chunk order),
-// G[k][l] = T^-1 sum, symmetric, into gram[b * kMF * kMF]; then, on the face,
-// diag G, G nuhat (zero off the face) and the scalar partials of the
-// diagonal block: spart[0] = T nuhat^T G nuhat, spart[1] = T 1_F^T G 1_F,
-// spart[2 .. 2 G) = 0 (k_pcg_setup adds G pairs).  256 threads.
-__global__ void __launch_bounds__(256) k_face_gram_finish(Inst base, const int* fl_base, const float* gp, int nchunk,
-                                                          float* gram, int G) {
-  const int b = blockIdx.x;
-  Inst s = inst_at(base, b);
+// Face Gram of instance blockIdx.y from the chunk partials (added in chunk
+// order): entries e = k mp + l of the upper triangle handled by CTA
+// blockIdx.x (grid-stride), G[k][l] = G[l][k] = T^-1 sum, into
+// gram[b * kMF * kMF] (row stride kMF).
+__global__ void __launch_bounds__(256) k_face_gram_sum(Inst base, const float* gp, int nchunk, float* gram) {
+  const int b = blockIdx.y;
+  const Inst s = inst_at(base, b);
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
   const int m = s.si[SI_FCNT];
   if (m > kMF) return;
-  const int* fl = fl_base + (size_t)b * s.vs;
+  const int mp = 8 * ((m + 7) / 8);
   float* Gm = gram + (size_t)b * kMF * kMF;
   const float invT = (float)s.sd[SD_INVT];
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+  const float* src0 = gp + (size_t)b * nchunk * kMF * kMF;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
     const int k = e / m, l = e - k * m;
     if (k > l) continue;
-    const float* src = gp + (size_t)b * nchunk * kMF * kMF + (size_t)k * kMF + l;
+    const float* src = src0 + (size_t)k * mp + l;
     float v = 0.f;
     for (int c = 0; c < nchunk; ++c) v += src[(size_t)c * kMF * kMF];
     v *= invT;
     Gm[(size_t)k * kMF + l] = v;
     Gm[(size_t)l * kMF + k] = v;
   }
-  __syncthreads();
+}
+
+// On the face of instance blockIdx.x: diag G, G nuhat (zero off the face) and
+// the scalar partials of the diagonal block: spart[0] = T nuhat^T G nuhat,
+// spart[1] = T 1_F^T G 1_F, spart[2 .. 2 G) = 0 (k_pcg_setup adds G pairs).
+// 256 threads.
+__global__ void __launch_bounds__(256) k_face_gram_finish(Inst base, const int* fl_base, const float* gram, int G) {
+  const int b = blockIdx.x;
+  Inst s = inst_at(base, b);
+  if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
+  const int m = s.si[SI_FCNT];
+  if (m > kMF) return;
+  const int* fl = fl_base + (size_t)b * s.vs;
+  const float* Gm = gram + (size_t)b * kMF * kMF;
   for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
     s.Gnu[i] = 0.0;
     s.diagG[i] = 0.0;
@@ -348,11 +373,14 @@ __global__ void __launch_bounds__(kMF) k_pcg_round_small(Inst base, int c0, int 
   }
 }
 
-// Partial Hutchinson corrections: CTA (x, b) over its kFRows rows t of A_F:
-// u_k = a_t . X_{1+k}, v_k = a_t . B_{1+k} (the PCG solutions and projected
-// probes on the face), rhat_t = K^-1 sum_k u_k v_k, w_t = psi'''(z_t) rhat_t,
-// out[l] = sum_t w_t a_tl.  One warp per row; lane j owns face coordinates
-// j, j + 32, ... .  Out: ap[(b * nchunk + x) * kMF + l].
+// Partial Hutchinson corrections.  CTA (x, b) covers rows [x kFRows,
+// (x + 1) kFRows) of instance b: with w_2k = X_{1+k}, w_2k+1 = B_{1+k} (the
+// PCG solutions and projected probes on the face, k < K), u = a_t W (2K
+// values), rhat_t = K^-1 sum_k u_2k u_2k+1, s_t = psi3(z_t) rhat_t (psi3 the
+// third derivative of psi), and out[l] = sum_t s_t a_tl.  Rows are staged
+// kFTile at a time; eight threads per row split the face coordinates
+// (l = j mod 8) and add their 2K partial products by shuffles.
+// Out: ap[(b * nchunk + x) * kMF + l].
 __global__ void __launch_bounds__(256) k_face_hutch(Inst base, int K, const int* fl_base, const __nv_bfloat16* AU,
                                                     const int* upos, float* ap) {
   const int b = blockIdx.y;
@@ -360,64 +388,78 @@ __global__ void __launch_bounds__(256) k_face_hutch(Inst base, int K, const int*
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
   const int m = s.si[SI_FCNT];
   if (m > kMF) return;
-  constexpr int kE = kMF / 32;  // face coordinates per lane
-  __shared__ float xs[kMaxProbes][kMF], bs[kMaxProbes][kMF];
+  constexpr int kW = 16;  // 2K <= 16: the batched path takes at most 8 probes
+  __shared__ __align__(16) float wt[kMF][kW];  // W, row l: (X_1, B_1, X_2, B_2, ...)
+  __shared__ __align__(16) float a[kFTile][kMF + 4];
+  __shared__ float sw[kFTile];
   __shared__ int col[kMF];
-  __shared__ float red[8][kMF];
   const int* fl = fl_base + (size_t)b * s.vs;
-  const int ld = s.ld;
-  for (int e = threadIdx.x; e < K * kMF; e += blockDim.x) {
-    const int kk = e / kMF, l = e - kk * kMF;
-    float xv = 0.f, bv = 0.f;
-    if (l < m) {
-      xv = kcol<float>(s.X, 1 + kk, ld)[fl[l]];
-      bv = kcol<float>(s.Bv, 1 + kk, ld)[fl[l]];
-    }
-    xs[kk][l] = xv;
-    bs[kk][l] = bv;
+  const int ld = s.ld, K2 = 2 * K;
+  for (int e = threadIdx.x; e < kMF * kW; e += blockDim.x) {
+    const int l = e / kW, q = e - l * kW;
+    float v = 0.f;
+    if (l < m && q < K2) v = kcol<float>((q & 1) ? s.Bv : s.X, 1 + (q >> 1), ld)[fl[l]];
+    wt[l][q] = v;
   }
   for (int l = threadIdx.x; l < kMF; l += blockDim.x) col[l] = l < m ? upos[fl[l]] : -1;
-  __syncthreads();
   const float c3 = (float)s.sd[SD_C3], c4 = (float)s.sd[SD_C4];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long T = s.T, t0 = (long long)blockIdx.x * kFRows, t1 = t0 + kFRows < T ? t0 + kFRows : T;
-  float acc[kE];
-#pragma unroll
-  for (int e = 0; e < kE; ++e) acc[e] = 0.f;
-  for (long long t = t0 + warp; t < t1; t += 8) {
-    float av[kE];
-#pragma unroll
-    for (int e = 0; e < kE; ++e) {
-      const int l = lane + 32 * e;
-      av[e] = l < m ? __bfloat162float(AU[(size_t)t * ld + col[l]]) : 0.f;
-    }
-    float rh = 0.f;
-    for (int kk = 0; kk < K; ++kk) {
-      float u = 0.f, v = 0.f;
-#pragma unroll
-      for (int e = 0; e < kE; ++e) {
-        u = fmaf(av[e], xs[kk][lane + 32 * e], u);
-        v = fmaf(av[e], bs[kk][lane + 32 * e], v);
-      }
-      u = warp_sum(u);
-      v = warp_sum(v);
-      rh = fmaf(u, v, rh);
-    }
-    const float z = (float)s.z[t];
-    const float w = (-6.f * c3 + 24.f * c4 * z) * (rh / (float)K);
-#pragma unroll
-    for (int e = 0; e < kE; ++e) acc[e] = fmaf(w, av[e], acc[e]);
-  }
-#pragma unroll
-  for (int e = 0; e < kE; ++e) red[warp][lane + 32 * e] = acc[e];
+  const int r = threadIdx.x >> 3, j = threadIdx.x & 7;  // row of the tile, face-coordinate slice
+  float bacc = 0.f;                                      // back-projection of coordinate threadIdx.x
   __syncthreads();
-  float* out = ap + ((size_t)b * gridDim.x + blockIdx.x) * kMF;
-  for (int l = threadIdx.x; l < m; l += blockDim.x) {
-    float v = 0.f;
+  for (long long tb = t0; tb < t1; tb += kFTile) {
+    const int rows = (int)(t1 - tb < kFTile ? t1 - tb : kFTile);
+    for (int e = threadIdx.x; e < kFTile * m; e += blockDim.x) {
+      const int rr = e / m, l = e - rr * m;
+      a[rr][l] = rr < rows ? __bfloat162float(AU[(size_t)(tb + rr) * ld + col[l]]) : 0.f;
+    }
+    __syncthreads();
+    float u[kW];
 #pragma unroll
-    for (int w = 0; w < 8; ++w) v += red[w][l];
-    out[l] = v;
+    for (int q = 0; q < kW; ++q) u[q] = 0.f;
+    for (int l = j; l < m; l += 8) {
+      const float av = a[r][l];
+      const float4* w4 = reinterpret_cast<const float4*>(&wt[l][0]);
+#pragma unroll
+      for (int q4 = 0; q4 < kW / 4; ++q4) {
+        if (4 * q4 < K2) {
+          const float4 w = w4[q4];
+          u[4 * q4] = fmaf(av, w.x, u[4 * q4]);
+          u[4 * q4 + 1] = fmaf(av, w.y, u[4 * q4 + 1]);
+          u[4 * q4 + 2] = fmaf(av, w.z, u[4 * q4 + 2]);
+          u[4 * q4 + 3] = fmaf(av, w.w, u[4 * q4 + 3]);
+        }
+      }
+    }
+    // the eight slices of a row are lanes 8 r' .. 8 r' + 7 of one warp
+#pragma unroll
+    for (int q = 0; q < kW; ++q) {
+      if (q < K2) {
+        float v = u[q];
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        u[q] = v;
+      }
+    }
+    if (j == 0) {
+      float rh = 0.f;
+#pragma unroll
+      for (int k = 0; k < kW / 2; ++k)
+        if (k < K) rh = fmaf(u[2 * k], u[2 * k + 1], rh);
+      float wv = 0.f;
+      if (r < rows) {
+        const float z = (float)s.z[tb + r];
+        wv = (-6.f * c3 + 24.f * c4 * z) * (rh / (float)K);
+      }
+      sw[r] = wv;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < m)
+      for (int rr = 0; rr < rows; ++rr) bacc = fmaf(sw[rr], a[rr][threadIdx.x], bacc);
+    __syncthreads();
   }
+  if ((int)threadIdx.x < m) ap[((size_t)b * gridDim.x + blockIdx.x) * kMF + threadIdx.x] = bacc;
 }
 
 // at_b = T^-1 sum over the chunks (fixed order) on the face, zero elsewhere.
