@@ -79,7 +79,10 @@ __global__ void k_small_mode(Inst base, int B, int* info) {
 // kMF^2 floats, element (k, l) at k mp + l (mp = m rounded up to 8), for the
 // blocks of this CTA.  Dynamic shared memory: kGramSmem bytes.
 constexpr int kGramRed = 256 * 65;  // row-group sums: 256 threads x 64 values (+1 pad)
-constexpr size_t kGramSmem = sizeof(float) * ((size_t)kGramRed + (size_t)kFTile * (kMF + 4) + kFTile) + sizeof(int) * kMF;
+// staged row: element k at k + 4 (k / 8), so that the 8-wide blocks of
+// neighbouring threads start on different shared-memory banks
+constexpr int kGramRow = kMF + kMF / 2 + 16;
+constexpr size_t kGramSmem = sizeof(float) * ((size_t)kGramRed + (size_t)kFTile * kGramRow + kFTile) + sizeof(int) * kMF;
 
 __global__ void __launch_bounds__(256) k_face_gram(Inst base, const int* fl_base, const __nv_bfloat16* AU,
                                                    const int* upos, float* gp) {
@@ -95,8 +98,8 @@ __global__ void __launch_bounds__(256) k_face_gram(Inst base, const int* fl_base
   if (rg_n > kFRg) rg_n = kFRg;
   extern __shared__ __align__(16) float fsm[];
   float* red = fsm;                                           // kGramRed
-  float (*a)[kMF + 4] = reinterpret_cast<float (*)[kMF + 4]>(fsm + kGramRed);
-  float* h = fsm + kGramRed + kFTile * (kMF + 4);
+  float (*a)[kGramRow] = reinterpret_cast<float (*)[kGramRow]>(fsm + kGramRed);
+  float* h = fsm + kGramRed + kFTile * kGramRow;
   int* col = reinterpret_cast<int*>(h + kFTile);
   const int* fl = fl_base + (size_t)b * s.vs;
   const int ld = s.ld;
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(256) k_face_gram(Inst base, const int* fl_base
       const int r = e / mp, k = e - r * mp;
       float v = 0.f;
       if (r < rows && k < m) v = __bfloat162float(AU[(size_t)(tb + r) * ld + col[k]]);
-      a[r][k] = v;
+      a[r][k + 4 * (k >> 3)] = v;
     }
     if (threadIdx.x < kFTile) {
       float hv = 0.f;
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(256) k_face_gram(Inst base, const int* fl_base
     }
     __syncthreads();
     if (act) {
-      const int k0 = 8 * bi, l0 = 8 * bj;
+      const int k0 = 12 * bi, l0 = 12 * bj;  // padded offsets of the blocks
       for (int r = rg; r < rows; r += rg_n) {
         const float hr = h[r];
         const float4 x0 = *reinterpret_cast<const float4*>(&a[r][k0]);
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(256) k_face_gram(Inst base, const int* fl_base
   }
   if (!act || rg != 0) return;
   float* out = gp + ((size_t)b * gridDim.x + blockIdx.x) * kMF * kMF;
-  const int k0 = 8 * bi, l0 = 8 * bj;
+  const int k0 = 8 * bi, l0 = 8 * bj;  // face indices of the block
 #pragma unroll
   for (int e = 0; e < 8; ++e)
 #pragma unroll
@@ -389,8 +392,10 @@ __global__ void __launch_bounds__(256) k_face_hutch(Inst base, int K, const int*
   const int m = s.si[SI_FCNT];
   if (m > kMF) return;
   constexpr int kW = 16;  // 2K <= 16: the batched path takes at most 8 probes
-  __shared__ __align__(16) float wt[kMF][kW];  // W, row l: (X_1, B_1, X_2, B_2, ...)
-  __shared__ __align__(16) float a[kFTile][kMF + 4];
+  // W, row l: (X_1, B_1, X_2, B_2, ...); rows 20 floats apart and tile rows
+  // kMF + 8 apart, so that the threads of a warp hit distinct banks
+  __shared__ __align__(16) float wt[kMF][kW + 4];
+  __shared__ __align__(16) float a[kFTile][kMF + 8];
   __shared__ float sw[kFTile];
   __shared__ int col[kMF];
   const int* fl = fl_base + (size_t)b * s.vs;
