@@ -221,7 +221,13 @@ def roofline_entry(name, d, pk, pk_src, T, n, ms_step):
          "share_of_step": round(d["total_ms"] * PROF_STRIDE / ms_step, 4), "traffic": None}
     tr = measured_traffic(name)
     e["traffic"] = None if tr is None else round(tr)
-    if name.startswith("oz_gemm") and not name.endswith("_gated"):
+    if name == "oz_gemm_fwd_u":
+        # digit planes of the union's columns: 14 T |U| bytes; the profiler's
+        # work is 56 T Bp |U| FLOPs (28 digit products, Bp = 64 vectors)
+        byt = d["bytes_per_launch"] / (4.0 * 64)
+        e.update({"bound": "hbm", "unit": "GB/s", "achieved": round(byt / avg_s / 1e9, 1), "peak": pk["hbm_gbs"],
+                  "algorithmic_bytes": byt, "peak_source": pk_src})
+    elif name.startswith("oz_gemm") and not name.endswith("_gated"):
         byt = 14.0 * T * n
         e.update({"bound": "hbm", "unit": "GB/s", "achieved": round(byt / avg_s / 1e9, 1), "peak": pk["hbm_gbs"],
                   "algorithmic_bytes": byt, "fp64_equivalent_gbs": round(8.0 * T * n / avg_s / 1e9, 1),

@@ -205,11 +205,14 @@ __global__ void k_oz_fin_g(const long long* part, int splits, int Bp, long long 
 // The twelve power sums s_rs of (z_t, w_t = a_t^T d) (Prop. quartic line search).
 // w_b[t] (the projected direction) is also stored in wout[(b0 + b) * T + t]
 // for the cache update of z (k_z_step).
+// kinfo (nullable): the product ran on a coordinate list of padded length
+// kinfo[1]; its split count is then kinfo[1] / 512 rounded up.
 __global__ void __launch_bounds__(256) k_oz_fin_ls(const long long* part, int splits, int Bp, long long ldp,
                                                    const int* em, const int* fb, Inst base, int b0, int skip_slot,
-                                                   double* wout) {
+                                                   double* wout, const int* kinfo = nullptr) {
   __shared__ double red[12][256];
   const int bl = blockIdx.y;
+  if (kinfo != nullptr) splits = (kinfo[1] + kOzKc - 1) / kOzKc;
   Inst s = inst_at(base, b0 + bl);
   if (s.si[SI_DONE] != 0 || s.si[skip_slot] != 0) return;
   double a[12];
@@ -441,7 +444,8 @@ constexpr int kUMaxProds = 16;
 constexpr int kUMaxSplits = 16;
 
 // flag[i] = 1 when coordinate i is on the working face of a running
-// instance that needs a direction (k_face wrote maskF this iteration).
+// instance (k_face wrote maskF this iteration); the direction d of every
+// running instance, trivial faces included, is zero off its face.
 __global__ void k_union_flags(Inst base, int B, int* flag) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= base.ld) return;
@@ -449,7 +453,7 @@ __global__ void k_union_flags(Inst base, int B, int* flag) {
   if (i < base.n)
     for (int b = 0; b < B && !f; ++b) {
       const int* si = base.si + (size_t)b * kSI;
-      if (si[SI_DONE] == 0 && si[SI_SKIPDIR] == 0 && base.maskF[(size_t)b * base.vs + i] != 0.0) f = 1;
+      if (si[SI_DONE] == 0 && base.maskF[(size_t)b * base.vs + i] != 0.0) f = 1;
     }
   flag[i] = f;
 }
@@ -545,6 +549,14 @@ __global__ void k_transpose_u_bf16(const __nv_bfloat16* __restrict__ srcT, long 
     const long long t = t0 + r;
     if (t < T) dst[(size_t)t * ldd + j0 + threadIdx.x] = tile[threadIdx.x][r];
   }
+}
+
+// dst[b * ldd + j] = V[b * vs + idx[j]] for j < |U|, zero for |U| <= j < ldd
+// (the right-hand vectors of a split product restricted to U).  Grid (x, B).
+__global__ void k_gather_vec_u(const double* V, long long vs, const int* idx, const int* info, double* dst, int ldd) {
+  const int b = blockIdx.y, ku = info[0];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ldd; j += gridDim.x * blockDim.x)
+    dst[(size_t)b * ldd + j] = j < ku ? V[(size_t)b * vs + idx[j]] : 0.0;
 }
 
 // BF16 columns in U coordinates: dst[q*ld + j] = bf16(col_q[idx[j]]) for
@@ -1121,6 +1133,9 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
       PROF_LAUNCH(NK_FACE_LIST, (k_face_list<<<dim3(1, B), 1024, 0, c->stream>>>(base, bb.f_list)));
       PROF_LAUNCH(NK_FACE_LIST, (k_small_mode<<<1, 256, 0, c->stream>>>(base, B, bb.u_info)));
       TRY(union_gather(c, bb, B));
+      if (split && bb.u_AFU != nullptr)  // digit planes of A's columns in U (the line search along d)
+        PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_split_rows_u<<<4 * c->nsm, 256, 0, c->stream>>>(
+                                     c->A64, c->ld, c->T, bb.u_idx, bb.u_info, oz.eF, bb.u_AFU, oz.MpF)));
     }
   }
   (void)P;
@@ -1230,7 +1245,17 @@ mvsk_status batch_iteration_tail(mvsk_ctx* c, BatchBuf& bb, int B, const std::ve
     }
     return MVSK_OK;
   };
-  if (split) {
+  if (split && bb.umode && bb.u_AFU != nullptr) {  // d is zero off the faces: A d on the union
+    for (int b0 = 0; b0 < B; b0 += kOzMaxB) {
+      const int nb = B - b0 < kOzMaxB ? B - b0 : kOzMaxB;
+      PROF_LAUNCH(NK_OZ_SPLIT, (k_gather_vec_u<<<dim3((unsigned)((c->ld + 255) / 256), nb), 256, 0, c->stream>>>(
+                                   base.d + (size_t)b0 * base.vs, base.vs, bb.u_idx, bb.u_info, bb.u_DU, c->ld)));
+      TRY(oz_product_u(c, bb.u_DU, nb, oz_bp(nb), bb.u_AFU, bb.u_info));
+      PROF_LAUNCH(NK_OZ_LS, (k_oz_fin_ls<<<dim3(Gl, nb), 256, 0, c->stream>>>(oz.part, 0, oz_bp(nb), oz.MpF, oz.eF,
+                                                                             oz.fF, base, b0, SI_DONE, bb.wls,
+                                                                             bb.u_info)));
+    }
+  } else if (split) {
     TRY(ls_split(base.d, SI_DONE, nullptr));
   } else {
     for (int b = 0; b < B; ++b) {
@@ -1374,6 +1399,12 @@ mvsk_status ensure_ubuf(mvsk_ctx* c, BatchBuf& bb) {
   CU(cudaMemsetAsync(bb.u_AUT, 0, sizeof(__nv_bfloat16) * ld * (size_t)c->Tp, c->stream));
   CU(cudaMemsetAsync(bb.u_A2UT, 0, sizeof(__nv_bfloat16) * ld * (size_t)c->Tp, c->stream));
   CU(cudaMemsetAsync(bb.u_specs, 0, sizeof(UProd) * kUMaxProds, c->stream));
+  if (c->opt.split_products) {  // the line-search product on U
+    TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * kOzS * (size_t)c->oz.MpF * ld));
+    bb.u_AFU = (__nv_bfloat16*)p;
+    TRY(dalloc(c, &p, sizeof(double) * kOzMaxB * ld));
+    bb.u_DU = (double*)p;
+  }
   CU(cudaFuncSetAttribute(k_pcg_round_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)(sizeof(float) * kMF * (kMF + 1))));
   CU(cudaFuncSetAttribute(k_face_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramSmem));

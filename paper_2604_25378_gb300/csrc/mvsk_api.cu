@@ -76,6 +76,8 @@ struct BatchBuf {
   // the product specs (device) and the specs themselves (host copy)
   __nv_bfloat16 *u_AU = nullptr, *u_AUT = nullptr, *u_A2UT = nullptr;
   int *u_flag = nullptr, *u_idx = nullptr, *u_pos = nullptr, *u_info = nullptr, *u_rt = nullptr;
+  __nv_bfloat16* u_AFU = nullptr;  // digit planes of A's columns in U (split line-search product)
+  double* u_DU = nullptr;          // directions in U coordinates (64 x ld)
   mvsk::UProd* u_specs = nullptr;
   std::vector<mvsk::UProd> u_hspec;
   bool umode = false;
@@ -1740,6 +1742,8 @@ static void kind_name(int kind, char* out, size_t len) {
     snprintf(out, len, "gemm_tc_bf16_n%d", kind - 400);
   else if (kind >= 680 && kind <= 683)
     snprintf(out, len, "oz_gemm_%s%s", (kind & 1) ? "bwd" : "fwd", kind >= 682 ? "_gated" : "");
+  else if (kind == 684)
+    snprintf(out, len, "oz_gemm_fwd_u");
   else if (kind >= kKindNamed && kind < kKindNamed + NK_COUNT)
     snprintf(out, len, "%s", kKernelNames[kind - kKindNamed]);
   else

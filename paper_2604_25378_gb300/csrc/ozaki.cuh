@@ -141,6 +141,23 @@ static __global__ void k_oz_split_cols(const double* A, long long lda, long long
   }
 }
 
+// Digit planes of the columns of A in a coordinate list (idx[j], j < info[0];
+// zero up to the padded count info[1], a multiple of 64) in the same tiled
+// layout with nkt = info[1] / 64 k-tiles and plane stride Mp * info[1]; the
+// exponents e[m] of the full rows bound every selected entry.
+static __global__ void k_oz_split_rows_u(const double* A, long long lda, long long M, const int* idx, const int* info,
+                                         const int* e, __nv_bfloat16* out, long long Mp) {
+  const int ku = info[0], kup = info[1];
+  const size_t plane = (size_t)Mp * kup;
+  const int nkt = kup / 64;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
+    const long long m = (long long)(i / kup);
+    const int k = (int)(i % kup);
+    const double v = (m < M && k < ku) ? A[(size_t)m * lda + idx[k]] : 0.0;
+    oz_digits(v, e[m], out + oz_tiled(m, k, nkt), plane);
+  }
+}
+
 // Right-hand vectors: vector b (b < B) is V[b*vstride + k], k < K.  Exponent
 // pass: f[b] = max over chunks of the chunk exponent (f preset to kOzNoExp by
 // the caller; all-zero chunks leave it).  Grid (chunks of 1024, Bp).
@@ -179,13 +196,18 @@ template <int BP>
 __global__ void __launch_bounds__(128, 1) k_oz_gemm(const __nv_bfloat16* __restrict__ Ad,
                                                     const __grid_constant__ CUtensorMap tmX, long long Mp, long long M,
                                                     int K, int nkt, long long* part, long long ldp, int* err,
-                                                    const int* need) {
+                                                    const int* need, const int* kinfo = nullptr) {
   static_assert(BP % 16 == 0 && BP <= kOzMaxB, "vector count must be a multiple of 16, at most 64");
   constexpr int NL = kOzS * BP;                        // TMEM columns in use
   constexpr uint32_t TCOLS = NL <= 32 ? 32 : NL <= 64 ? 64 : NL <= 128 ? 128 : NL <= 256 ? 256 : 512;
   constexpr int ABYTES = kTcBM * kTcBK * 2;            // one left digit tile
   constexpr int XBYTES = kOzS * BP * kTcBK * 2;        // all right digits of one k-block
   if (need != nullptr && *need == 0) return;
+  if (kinfo != nullptr) {  // left operand restricted to a coordinate list: K = its padded count
+    K = kinfo[1];
+    nkt = K / kTcBK;
+    if ((int)blockIdx.y * (kOzKc / kTcBK) >= nkt) return;  // k-chunks beyond the runtime K
+  }
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));

@@ -105,6 +105,49 @@ mvsk_status oz_product(mvsk_ctx* c, int trans, const double* V, long long vstrid
   return MVSK_OK;
 }
 
+// A V with the left operand restricted to the columns of A in a coordinate
+// list (the union of the working faces of a batch): AU holds their digit
+// planes (k_oz_split_rows_u, padded count info[1]); V holds B vectors of ld
+// values in list coordinates (zero beyond the list).  Partials in c->oz.part
+// as from oz_product (ld Mp), split count info[1] / 512 rounded up, read by
+// the finishing kernel from info.
+mvsk_status oz_product_u(mvsk_ctx* c, const double* V, int B, int Bp, const __nv_bfloat16* AU, const int* info) {
+  TRY(oz_prepare(c, Bp));
+  OzBuf& o = c->oz;
+  const int K = c->ld;
+  CU(cudaMemsetAsync(o.fF, 0x80, sizeof(int) * Bp, c->stream));  // kOzNoExp
+  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_vec_exp<<<dim3((unsigned)((K + 1023) / 1024), Bp), 256, 0, c->stream>>>(
+                               V, c->ld, B, K, o.fF, nullptr)));
+  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_vec_digits<<<dim3((unsigned)((K + 255) / 256), Bp), 256, 0, c->stream>>>(
+                               V, c->ld, B, Bp, K, c->ld, o.fF, o.XF, nullptr)));
+  const int splits = (K + kOzKc - 1) / kOzKc;  // the grid covers every column; CTAs past info[1] return
+  const dim3 grid((unsigned)(o.MpF / kTcBM), (unsigned)splits);
+  // work per unit of the padded list length: 28 digit products of Mp x Bp
+  TRY(prof_begin_u(c, kKindOz + 4, 2.0 * (double)o.MpF * Bp * (kOzS * (kOzS + 1) / 2)));
+  switch (Bp) {
+    case 16:
+      k_oz_gemm<16><<<grid, 128, oz_smem_bytes(16), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part, o.MpF,
+                                                                     c->err, nullptr, info);
+      break;
+    case 32:
+      k_oz_gemm<32><<<grid, 128, oz_smem_bytes(32), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part, o.MpF,
+                                                                     c->err, nullptr, info);
+      break;
+    case 48:
+      k_oz_gemm<48><<<grid, 128, oz_smem_bytes(48), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part, o.MpF,
+                                                                     c->err, nullptr, info);
+      break;
+    default:
+      k_oz_gemm<64><<<grid, 128, oz_smem_bytes(64), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part, o.MpF,
+                                                                     c->err, nullptr, info);
+      break;
+  }
+  CU(cudaGetLastError());
+  TRY(prof_end(c));
+  c->launches += 1;
+  return MVSK_OK;
+}
+
 int oz_bp(int B) { return (B + 15) / 16 * 16; }
 
 // CTAs over t of the row-wise finishing kernels (at most c->grid: the scalar
