@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--lanes", type=int, default=0,
                     help="concurrent instances of the batched solver (0: all requests at once)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 single-instance leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
+    ap.add_argument("--sweep-panel", default="c4", choices=["c4", "c3"],
+                    help="panel of the batched sweep: c4 (n=5440, T=12000; the measured workload) or c3 "
+                         "(n=2000, T=12000: the same kernels on a smaller panel, for profiler captures)")
     ap.add_argument("--workload", default="c4",
                     choices=["c4", "paper-synthetic", "paper-line-search", "paper-conditioning", "warm-start"],
                     help="c4: the batched C4 sweep (default); paper-*: the paper's own benchmarks "
@@ -79,15 +83,18 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-def sweep_requests(world=1):
+def sweep_requests(world=1, panel="c4"):
     """The frontier sweep's requests: 4 preference vectors x 16 N return targets
     at asset-mean quantiles evenly spaced in [0.40, 0.85] (N = world size; the
     measured workload is N = 1: 64 requests, request q = 16 v + t).  More ranks
-    add distinct targets, so every rank solves requests of its own."""
+    add distinct targets, so every rank solves requests of its own.  panel
+    "c3" puts the same requests on the n = 2000, T = 12000 GARCH panel."""
     import numpy as np
 
     import panels
     R, lams, _ = panels.workload(WORKLOAD)
+    if panel == "c3":
+        R, _, _ = panels.workload("c3_pcg_n2000_T12000")
     tg = panels.quantile_targets(R, np.linspace(0.40, 0.85, 16 * world))
     lam_b = np.asarray([l for l in lams for _ in tg])
     tg_b = np.asarray([t for _ in lams for t in tg])
@@ -122,9 +129,9 @@ def gather_weights(W_local, idx_local, n_requests, world):
     return out
 
 
-def instances(batch, rank=0, world=1):
+def instances(batch, rank=0, world=1, panel="c4"):
     """This rank's share of the sweep (at most `batch` requests)."""
-    R, lam_b, tg_b = sweep_requests(world)
+    R, lam_b, tg_b = sweep_requests(world, panel)
     idx = partition(len(lam_b), rank, world)[:batch]
     return R, lam_b[idx], tg_b[idx], idx
 
@@ -176,8 +183,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# The timed step brackets every PROF_STRIDE-th launch of its dominant kernel
-# kind with CUDA events (the average duration behind roofline.achieved).
+# The timed step brackets every PROF_STRIDE-th captured launch of its timed
+# kinds with CUDA events (the average duration behind roofline.achieved).  A
+# launch inside a replayed CUDA graph is bracketed on every replay when it is
+# bracketed at capture, so the sampled count is not launches / PROF_STRIDE.
 PROF_STRIDE = 5
 
 
@@ -208,7 +217,7 @@ def peaks():
 TIMED_KINDS = "gemm_tc_bf16_n192,gemm_tc_bf16_n64,oz_gemm_fwd,oz_gemm_bwd"
 
 
-def roofline_entry(name, d, pk, pk_src, T, n, ms_step):
+def roofline_entry(name, d, pk, pk_src, T, n, ms_step, per_step=None):
     """Roofline of one profiled kind from its live CUDA-event durations.
 
     Tensor-core products report TFLOP/s against the sustained BF16 peak (the
@@ -217,8 +226,11 @@ def roofline_entry(name, d, pk, pk_src, T, n, ms_step):
     stream once per launch (BF16 A: 2 T n bytes; the seven BF16 digit planes of
     the split product: 14 T n bytes, and the FP64 A it stands for, 8 T n)."""
     avg_s = d["total_ms"] / d["launches"] / 1e3
-    e = {"kernel": name, "launches": d["launches"], "sampled_every": PROF_STRIDE, "avg_us": round(avg_s * 1e6, 2),
-         "share_of_step": round(d["total_ms"] * PROF_STRIDE / ms_step, 4), "traffic": None}
+    # share: the average launch times the launches of one step (per_step, from
+    # the fully profiled warm-up step), over the step's duration
+    e = {"kernel": name, "sampled_launches": d["launches"], "launches_per_step": per_step,
+         "avg_us": round(avg_s * 1e6, 2),
+         "share_of_step": None if per_step is None else round(avg_s * 1e3 * per_step / ms_step, 4), "traffic": None}
     tr = measured_traffic(name)
     e["traffic"] = None if tr is None else round(tr)
     if name == "oz_gemm_fwd_u":
@@ -284,7 +296,7 @@ def run_ours(args, rank, world):
     import paper_2604_25378_gb300 as m
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    R, lam_b, tg_b, idx = instances(args.batch, rank, world)
+    R, lam_b, tg_b, idx = instances(args.batch, rank, world, args.sweep_panel)
     B = len(lam_b)
     T, n = R.shape
     Rd = torch.from_numpy(R).cuda()
@@ -348,7 +360,8 @@ def run_ours(args, rank, world):
     for name, d in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"]):
         if d["launches"] == 0 or name.endswith("_gated"):  # gated launches may skip their work
             continue
-        e = roofline_entry(name, d, pk, pk_src, T, n, ms)
+        e = roofline_entry(name, d, pk, pk_src, T, n, ms / args.steps,
+                           breakdown[name]["launches"] if name in breakdown else None)
         if roof is None:
             roof = e
             if live is not None:
@@ -361,7 +374,8 @@ def run_ours(args, rank, world):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f64" if args.precision == "bf16" else
             ("fp32+f64" if args.precision == "fp32" else "f64"), "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "T": T, "instances_per_gpu": B,
+            "config": {"workload": WORKLOAD if args.sweep_panel == "c4" else "c3_panel_batch_n2000_T12000",
+                       "n": n, "T": T, "instances_per_gpu": B,
                        "targets": 16, "preference_vectors": 4, "configuration": "pcg",
                        "tol": args.tol, "start": "1/n (cold)",
                        "l2": "inputs larger than L2: A is 522 MB FP64 + 131 MB BF16",
@@ -408,7 +422,7 @@ def run_ours(args, rank, world):
         pf = plain_fp64(R, lam_b, tg_b, args.tol, picks)
         line["plain_fp64"] = pf
         line["speedup_vs_plain_fp64"] = round(value / world / pf["solves_per_s"], 2)
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args, R, lam_b, tg_b)
     line["breakdown_last_warmup_step"] = {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3)}
                                           for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1]["total_ms"])}

@@ -206,13 +206,13 @@ __global__ void k_oz_fin_g(const long long* part, int splits, int Bp, long long 
 // w_b[t] (the projected direction) is also stored in wout[(b0 + b) * T + t]
 // for the cache update of z (k_z_step).
 // kinfo (nullable): the product ran on a coordinate list of padded length
-// kinfo[1]; its split count is then kinfo[1] / 512 rounded up.
+// kinfo[1]; its slot count is then oz_slots(kinfo[1] / 64).
 __global__ void __launch_bounds__(256) k_oz_fin_ls(const long long* part, int splits, int Bp, long long ldp,
                                                    const int* em, const int* fb, Inst base, int b0, int skip_slot,
                                                    double* wout, const int* kinfo = nullptr) {
   __shared__ double red[12][256];
   const int bl = blockIdx.y;
-  if (kinfo != nullptr) splits = (kinfo[1] + kOzKc - 1) / kOzKc;
+  if (kinfo != nullptr) splits = oz_slots(kinfo[1] / kTcBK);
   Inst s = inst_at(base, b0 + bl);
   if (s.si[SI_DONE] != 0 || s.si[skip_slot] != 0) return;
   double a[12];

@@ -16,10 +16,11 @@
 // magnitude <= 2^14; products with s + u = l (level l) share one FP32 TMEM
 // accumulator.  Over kOzKc = 512 k-values every level l <= 5 stays within
 // 2^24 and is accumulated exactly; level 6 (weight 2^-42 of level 0) may round
-// by one unit.  Levels s + u >= 7 are dropped.  Each CTA folds its levels into
-// one 64-bit integer per output (sum_l L_l 2^(7(5-l)) + rint(L_6 / 2^7)), and
-// a finishing kernel sums the k-splits in integers and scales by
-// 2^(e_row + f_col - 49) once, in FP64.  The result is the exact product of
+// by one unit.  Levels s + u >= 7 are dropped.  The levels of every 512-value
+// chunk are folded into one 64-bit integer per output (sum_l L_l 2^(7(5-l)) +
+// rint(L_6 / 2^7)), chunks are summed in integers (slots of 16 chunks), and a
+// finishing kernel adds the slots and scales by 2^(e_row + f_col - 49) once,
+// in FP64.  The result is the exact product of
 // the 49-bit roundings of both operands, up to the dropped levels.
 //
 // GEMM layout.  Left operand: kOzS digit planes, each Mp x ldk BF16 stored as
@@ -39,9 +40,9 @@ namespace mvsk {
 
 constexpr int kOzS = 7;          // digits per operand
 constexpr int kOzBits = 7;       // bits per digit
-constexpr int kOzKc = 512;       // k-values per CTA (exact FP32 accumulation bound)
+constexpr int kOzKc = 512;       // k-values per TMEM accumulation (exact FP32 bound)
 constexpr int kOzMaxB = 64;      // right-hand vectors per product
-constexpr int kOzAStages = 6;    // left-digit tiles in flight (16 KB each)
+constexpr int kOzAStages = 7;    // left-digit tiles in flight (16 KB each)
 constexpr int kOzXStages = 2;    // right-digit k-blocks in flight (kOzS*Bp*128 bytes each)
 constexpr int kOzExp = kOzS * kOzBits;  // 49: fixed-point bits of one operand
 
@@ -190,24 +191,70 @@ static __global__ void k_oz_vec_digits(const double* V, long long vstride, int B
 }
 
 // ------------------------------------------------------------------ product
-// part[(z*Bp + b)*ldp + m] = folded levels of sum_{k in split z} A[m,k] V_b[k]
-// in units of 2^(e_m + f_b - 49).  Grid (Mp/128, splits); 128 threads.
+// Persistent split product.  Work units are (row tile mt, k-chunk ch): the
+// 128 rows of tile mt against the <= 8 k-blocks (512 k-values) of chunk ch,
+// U = (Mp / 128) * nch of them, ordered row-tile-major; CTA c of the G in the
+// grid takes units [c U / G, (c + 1) U / G).  Per unit the MMAs accumulate
+// the seven levels in TMEM (exact, as above), and the epilogue warps fold
+// them into 64-bit integers held in registers across the CTA's consecutive
+// units of one row tile and one group of kOzGroup chunks; at a change of
+// either (or the end of the range) the group sum goes to slot g = ch /
+// kOzGroup by 64-bit integer atomic addition, so that
+//     part[(g*Bp + b)*ldp + m] = sum over chunks of group g of the chunk's folded levels
+// whatever the order of the additions (integer sums are associative).  The
+// slots must be zero before the launch (k_oz_zero).  Each chunk's sum is
+// < 2^58.1 in magnitude, so a slot of 16 stays below 2^62.1.
+//
+// Roles: warp 0 streams the operands (one bulk copy per 16 KB left digit
+// tile, one TMA box per right digit block of a k-block), warp 1 issues the
+// MMAs, and kOzEpiWarps warps drain TMEM (four per TMEM lane quarter, 16
+// columns of each level apiece).  TMEM holds one unit: the MMAs of the next
+// unit wait until every epilogue warp has read the levels (tmem_empty), while
+// the loads run ahead through the shared-memory ring; the integer atomics of
+// a finished group overlap the next unit's MMAs.  Grid: at most one CTA per
+// SM (about 225 KB of shared memory), kOzThreads threads.
+constexpr int kOzEpiWarps = 16;
+constexpr int kOzThreads = 64 + 32 * kOzEpiWarps;
+constexpr int kOzGroup = 16;  // chunks per integer slot
+
+// Integer slots of a product over nkb k-blocks.
+__host__ __device__ constexpr int oz_slots(int nkb) { return ((nkb + 7) / 8 + kOzGroup - 1) / kOzGroup; }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Zero n int64 slots (skipped when *need == 0).
+static __global__ void k_oz_zero(long long* p, long long n, const int* need) {
+  if (need != nullptr && *need == 0) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = 0;
+}
+
+// kinfo (nullable): the left operand is restricted to a coordinate list whose
+// padded length kinfo[1] (a multiple of 64) replaces K.
 template <int BP>
-__global__ void __launch_bounds__(128, 1) k_oz_gemm(const __nv_bfloat16* __restrict__ Ad,
-                                                    const __grid_constant__ CUtensorMap tmX, long long Mp, long long M,
-                                                    int K, int nkt, long long* part, long long ldp, int* err,
-                                                    const int* need, const int* kinfo = nullptr) {
+__global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __nv_bfloat16* __restrict__ Ad,
+                                                           const __grid_constant__ CUtensorMap tmX, long long Mp,
+                                                           long long M, int K, int nkt, long long* part, long long ldp,
+                                                           int* err, const int* need, const int* kinfo = nullptr) {
   static_assert(BP % 16 == 0 && BP <= kOzMaxB, "vector count must be a multiple of 16, at most 64");
   constexpr int NL = kOzS * BP;                        // TMEM columns in use
   constexpr uint32_t TCOLS = NL <= 32 ? 32 : NL <= 64 ? 64 : NL <= 128 ? 128 : NL <= 256 ? 256 : 512;
   constexpr int ABYTES = kTcBM * kTcBK * 2;            // one left digit tile
   constexpr int XBYTES = kOzS * BP * kTcBK * 2;        // all right digits of one k-block
+  constexpr int NSL = BP / 16;                         // 16-column slices of a level
   if (need != nullptr && *need == 0) return;
-  if (kinfo != nullptr) {  // left operand restricted to a coordinate list: K = its padded count
+  if (kinfo != nullptr) {
     K = kinfo[1];
     nkt = K / kTcBK;
-    if ((int)blockIdx.y * (kOzKc / kTcBK) >= nkt) return;  // k-chunks beyond the runtime K
   }
+  const int nkb = (K + kTcBK - 1) / kTcBK;
+  const int nch = (nkb + 7) / 8;
+  const long long U = (Mp / kTcBM) * (long long)nch;
+  const long long u0 = (long long)blockIdx.x * U / gridDim.x, u1 = (long long)(blockIdx.x + 1) * U / gridDim.x;
+  if (u0 >= u1) return;  // uniform over the CTA: before any barrier or TMEM use
+
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -217,19 +264,16 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const __nv_bfloat16* __restr
   uint64_t* xempty = xfull + kOzXStages;
   uint64_t* afull = xempty + kOzXStages;
   uint64_t* aempty = afull + kOzAStages;
-  uint64_t* done = aempty + kOzAStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  __shared__ int s_abort;
-  __shared__ int s_xissued, s_aissued;
+  uint64_t* tfull = aempty + kOzAStages;  // a unit's levels are in TMEM
+  uint64_t* tempty = tfull + 1;           // every epilogue warp has read them
+  uint64_t* mdone = tempty + 1;           // every MMA issued has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
+  __shared__ int s_abort_raw, s_xissued, s_aissued;
+  volatile int* s_abort = &s_abort_raw;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long m0 = (long long)blockIdx.x * kTcBM;
-  const int nkb = (K + kTcBK - 1) / kTcBK;
-  const int kb0 = blockIdx.y * (kOzKc / kTcBK);
-  const int kb1 = kb0 + kOzKc / kTcBK < nkb ? kb0 + kOzKc / kTcBK : nkb;
-  const int nk = kb1 > kb0 ? kb1 - kb0 : 0;
   if (threadIdx.x == 0) {
-    s_abort = 0;
+    *s_abort = 0;
     s_xissued = 0;
     s_aissued = 0;
     for (int s = 0; s < kOzXStages; ++s) {
@@ -240,7 +284,9 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const __nv_bfloat16* __restr
       mbar_init(&afull[s], 1);
       mbar_init(&aempty[s], 1);
     }
-    mbar_init(done, 1);
+    mbar_init(tfull, 1);
+    mbar_init(tempty, kOzEpiWarps);
+    mbar_init(mdone, 1);
     fence_barrier_init();
   }
   if (warp == 0) tmem_alloc(tmem_slot, TCOLS);
@@ -249,93 +295,131 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const __nv_bfloat16* __restr
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    int ai = 0;
-    for (int i = 0; i < nk && !s_abort; ++i) {
-      const int xs = i % kOzXStages;
-      if (i >= kOzXStages && !mbar_wait_bounded(&xempty[xs], (uint32_t)(((i / kOzXStages) - 1) & 1))) {
-        s_abort = 1;
-        atomicOr(err, kErrWaitTimeout);
-        break;
-      }
-      mbar_expect_tx(&xfull[xs], XBYTES);
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      int i = 0, ai = 0;
+      bool ok = true;
+      for (long long u = u0; u < u1 && ok; ++u) {
+        const long long mt = u / nch;
+        const int kb0 = (int)(u % nch) * 8, kb1 = kb0 + 8 < nkb ? kb0 + 8 : nkb;
+        for (int kb = kb0; kb < kb1 && ok; ++kb, ++i) {
+          const int xs = i % kOzXStages;
+          if (*s_abort || (i >= kOzXStages && !mbar_wait_bounded(&xempty[xs], (uint32_t)(((i / kOzXStages) - 1) & 1)))) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&xfull[xs], XBYTES);
 #pragma unroll 1
-      for (int u = 0; u < kOzS; ++u)
-        tma_load_2d(sX + (size_t)xs * XBYTES + (size_t)u * BP * 128, &tmX, (kb0 + i) * kTcBK, u * BP, &xfull[xs]);
-      s_xissued = i + 1;
+          for (int v = 0; v < kOzS; ++v)
+            tma_load_2d(sX + (size_t)xs * XBYTES + (size_t)v * BP * 128, &tmX, kb * kTcBK, v * BP, &xfull[xs]);
+          s_xissued = i + 1;
 #pragma unroll 1
-      for (int s = 0; s < kOzS; ++s, ++ai) {
-        const int as = ai % kOzAStages;
-        if (ai >= kOzAStages && !mbar_wait_bounded(&aempty[as], (uint32_t)(((ai / kOzAStages) - 1) & 1))) {
-          s_abort = 1;
-          atomicOr(err, kErrWaitTimeout);
-          break;
+          for (int s = 0; s < kOzS; ++s, ++ai) {
+            const int as = ai % kOzAStages;
+            if (ai >= kOzAStages && !mbar_wait_bounded(&aempty[as], (uint32_t)(((ai / kOzAStages) - 1) & 1))) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(&afull[as], ABYTES);
+            bulk_g2s(sA + (size_t)as * ABYTES, Ad + (size_t)s * Mp * nkt * 64 + ((size_t)mt * nkt + (size_t)kb) * 8192,
+                     ABYTES, &afull[as]);
+            s_aissued = ai + 1;
+          }
         }
-        mbar_expect_tx(&afull[as], ABYTES);
-        bulk_g2s(sA + (size_t)as * ABYTES,
-                 Ad + (size_t)s * Mp * nkt * 64 + ((size_t)blockIdx.x * nkt + (size_t)(kb0 + i)) * 8192, ABYTES,
-                 &afull[as]);
-        s_aissued = ai + 1;
+      }
+      if (!ok) {
+        *s_abort = 1;
+        atomicOr(err, kErrWaitTimeout);
       }
     }
-  } else if (warp == 1 && lane == 0) {
-    int ai = 0;
-    for (int i = 0; i < nk && !s_abort; ++i) {
-      const int xs = i % kOzXStages;
-      if (!mbar_wait_bounded(&xfull[xs], (uint32_t)((i / kOzXStages) & 1))) {
-        s_abort = 1;
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issue
+      int i = 0, ai = 0, r = 0;
+      bool ok = true;
+      for (long long u = u0; u < u1 && ok; ++u, ++r) {
+        const int kb0 = (int)(u % nch) * 8, kb1 = kb0 + 8 < nkb ? kb0 + 8 : nkb;
+        if (r > 0) {
+          if (*s_abort || !mbar_wait_bounded(tempty, (uint32_t)((r - 1) & 1))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+        }
+        for (int kb = kb0; kb < kb1 && ok; ++kb, ++i) {
+          const int xs = i % kOzXStages;
+          if (*s_abort || !mbar_wait_bounded(&xfull[xs], (uint32_t)((i / kOzXStages) & 1))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const unsigned char* xb = sX + (size_t)xs * XBYTES;
+#pragma unroll 1
+          for (int s = 0; s < kOzS; ++s, ++ai) {
+            const int as = ai % kOzAStages;
+            if (!mbar_wait_bounded(&afull[as], (uint32_t)((ai / kOzAStages) & 1))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint64_t da = umma_desc_sw128(sA + (size_t)as * ABYTES);
+            const int ntot = (kOzS - s) * BP;
+#pragma unroll
+            for (int kk = 0; kk < kTcBK / 16; ++kk) {
+              const uint32_t acc = (kb > kb0 || s > 0 || kk > 0) ? 1u : 0u;
+#pragma unroll 1
+              for (int c0 = 0; c0 < ntot; c0 += 256) {
+                const int nn = ntot - c0 < 256 ? ntot - c0 : 256;
+                const uint64_t db = umma_desc_sw128(xb + (size_t)c0 * 128);
+                umma_bf16(tmem + (uint32_t)(s * BP + c0), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk),
+                          idesc_bf16_f32(kTcBM, nn), acc);
+              }
+            }
+            umma_commit(&aempty[as]);
+          }
+          if (ok) umma_commit(&xempty[xs]);
+        }
+        if (ok) umma_commit(tfull);
+      }
+      if (!ok) {
+        *s_abort = 1;
         atomicOr(err, kErrWaitTimeout);
+      }
+      umma_commit(mdone);  // arrives once every MMA issued above has completed
+      if (!mbar_wait_bounded(mdone, 0)) atomicOr(err, kErrDrainTimeout);
+    }
+  } else {  // epilogue: TMEM lane quarter q, columns [16 sl, 16 sl + 16) of each level
+    const int ew = warp - 2, q = warp & 3, sl = ew >> 2;
+    const bool act = sl < NSL;
+    const uint32_t lb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(sl * 16);
+    long long acc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = 0;
+    long long cur_mt = -1;
+    int cur_g = -1, r = 0;
+    auto flush = [&]() {
+      const long long m = cur_mt * kTcBM + q * 32 + lane;
+      if (act && m < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          atomicAdd(reinterpret_cast<unsigned long long*>(part + ((size_t)cur_g * BP + sl * 16 + j) * ldp + m),
+                    (unsigned long long)acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = 0;
+    };
+    bool ok = true;
+    for (long long u = u0; u < u1; ++u, ++r) {
+      const long long mt = u / nch;
+      const int g = (int)(u % nch) / kOzGroup;
+      if (cur_mt >= 0 && (mt != cur_mt || g != cur_g)) flush();
+      cur_mt = mt;
+      cur_g = g;
+      if (*s_abort || !mbar_wait_bounded(tfull, (uint32_t)(r & 1))) {
+        ok = false;
         break;
       }
       tc_fence_after();
-      const unsigned char* xb = sX + (size_t)xs * XBYTES;
-      bool ok = true;
-#pragma unroll 1
-      for (int s = 0; s < kOzS; ++s, ++ai) {
-        const int as = ai % kOzAStages;
-        if (!mbar_wait_bounded(&afull[as], (uint32_t)((ai / kOzAStages) & 1))) {
-          s_abort = 1;
-          atomicOr(err, kErrWaitTimeout);
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint64_t da = umma_desc_sw128(sA + (size_t)as * ABYTES);
-        const int ntot = (kOzS - s) * BP;
-#pragma unroll
-        for (int kk = 0; kk < kTcBK / 16; ++kk) {
-          const uint32_t acc = (i > 0 || s > 0 || kk > 0) ? 1u : 0u;
-#pragma unroll 1
-          for (int c0 = 0; c0 < ntot; c0 += 256) {
-            const int nn = ntot - c0 < 256 ? ntot - c0 : 256;
-            const uint64_t db = umma_desc_sw128(xb + (size_t)c0 * 128);
-            umma_bf16(tmem + (uint32_t)(s * BP + c0), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk),
-                      idesc_bf16_f32(kTcBM, nn), acc);
-          }
-        }
-        umma_commit(&aempty[as]);
-      }
-      if (!ok) break;
-      umma_commit(&xempty[xs]);
-    }
-    umma_commit(done);  // arrives once every MMA issued above has completed
-  }
-  __syncwarp();
-  const bool ok = mbar_wait_bounded(done, 0);
-  if (!ok) {
-    s_abort = 1;
-    atomicOr(err, kErrWaitTimeout);
-  }
-  tc_fence_after();
-  if (ok && !s_abort) {
-    const long long m = m0 + warp * 32 + lane;
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-    for (int b0 = 0; b0 < BP; b0 += 16) {
-      long long acc[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q] = 0;
-      if (nk > 0) {
+      if (act) {
         // Integer values of the FP32 levels by FP32/INT arithmetic only (a
         // float-to-int64 conversion runs on the FP64 pipe): for |w| < 2^22,
         // w + 1.5*2^23 rounds w to the nearest integer in the low mantissa bits.
@@ -344,33 +428,37 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const __nv_bfloat16* __restr
 #pragma unroll 1
         for (int l = 0; l < kOzS; ++l) {
           float v[16];
-          tmem_ld16(lane_base + (uint32_t)(l * BP + b0), v);
+          tmem_ld16(lb + (uint32_t)(l * BP), v);
           if (l < kOzS - 1) {  // exact integer, |v| <= 2^24: v = 4096 hi + lo
             const int sh = kOzBits * (kOzS - 2 - l);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              const float t = fmaf(v[q], 1.0f / 4096.0f, kMagic);
+            for (int j = 0; j < 16; ++j) {
+              const float t = fmaf(v[j], 1.0f / 4096.0f, kMagic);
               const int hi = __float_as_int(t) - kMagicBits;
-              const float lo = fmaf(-(t - kMagic), 4096.0f, v[q]);
+              const float lo = fmaf(-(t - kMagic), 4096.0f, v[j]);
               const int il = __float_as_int(lo + kMagic) - kMagicBits;
-              acc[q] += (long long)hi * (1LL << (sh + 12)) + (long long)il * (1LL << sh);
+              acc[j] += (long long)(hi * 4096 + il) * (1LL << sh);
             }
           } else {  // level kOzS-1 in units of 2^kOzBits of it, rounded
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
-              acc[q] += __float_as_int(fmaf(v[q], 1.0f / (float)(1 << kOzBits), kMagic)) - kMagicBits;
+            for (int j = 0; j < 16; ++j)
+              acc[j] += __float_as_int(fmaf(v[j], 1.0f / (float)(1 << kOzBits), kMagic)) - kMagicBits;
           }
         }
       }
-      if (m < M) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) part[((size_t)blockIdx.y * BP + b0 + q) * ldp + m] = acc[q];
-      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty);
+    }
+    if (ok && cur_mt >= 0) flush();
+    if (!ok) {
+      if (lane == 0) atomicOr(err, kErrWaitTimeout);
+      *s_abort = 1;
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (s_abort && threadIdx.x == 0) {
+  if (*s_abort && threadIdx.x == 0) {
     // drain: the latest copies issued into each stage must land before the CTA exits
     const int xi = s_xissued, ai = s_aissued;
     for (int i = xi - kOzXStages < 0 ? 0 : xi - kOzXStages; i < xi; ++i)
@@ -379,20 +467,17 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const __nv_bfloat16* __restr
       if (!mbar_wait_bounded(&afull[i % kOzAStages], (uint32_t)((i / kOzAStages) & 1))) atomicOr(err, kErrDrainTimeout);
   }
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, TCOLS);
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TCOLS);
+  }
 }
 
-// Sum of the split partials of output (m, b) scaled to its FP64 value.
-__device__ __forceinline__ double oz_value(const long long* part, int splits, int Bp, long long ldp, long long m, int b,
+// FP64 value of output (m, b) from its integer slots.
+__device__ __forceinline__ double oz_value(const long long* part, int slots, int Bp, long long ldp, long long m, int b,
                                            int em, int fb) {
   double v = 0.0;
-  for (int z0 = 0; z0 < splits; z0 += 16) {
-    long long s = 0;  // at most 16 partials of magnitude < 2^58.1: no overflow
-    const int z1 = z0 + 16 < splits ? z0 + 16 : splits;
-#pragma unroll 4
-    for (int z = z0; z < z1; ++z) s += part[((size_t)z * Bp + b) * ldp + m];
-    v += (double)s;
-  }
+  for (int z = 0; z < slots; ++z) v += (double)part[((size_t)z * Bp + b) * ldp + m];
   // digit weights 2^-7(s+1) and 2^-7(u+1), folded levels 2^(7(kOzS-2)):  2^(e + f - 49)
   return fb == kOzNoExp ? 0.0 : ldexp(v, em + fb - kOzExp);
 }

@@ -70,38 +70,43 @@ mvsk_status oz_product(mvsk_ctx* c, int trans, const double* V, long long vstrid
                                V, vstride, B, (int)K, f, need)));
   PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_vec_digits<<<dim3((unsigned)((ldk + 255) / 256), Bp), 256, 0, c->stream>>>(
                                V, vstride, B, Bp, (int)K, (int)ldk, f, trans ? o.XB : o.XF, need)));
-  const int splits = (int)((ldk + kOzKc - 1) / kOzKc);
-  const dim3 grid((unsigned)(Mp / kTcBM), (unsigned)splits);
+  const int nkb = (int)(ldk / kTcBK);
+  const int slots = oz_slots(nkb);
+  const long long units = Mp / kTcBM * ((nkb + 7) / 8);
+  const unsigned grid = (unsigned)(units < c->nsm ? units : c->nsm);
   const __nv_bfloat16* ad = trans ? o.AB : o.AF;
-  const int nkt = (int)(ldk / kTcBK);
+  const int nkt = nkb;
   const CUtensorMap& tx = trans ? o.tmXB : o.tmXF;
   // work: BF16 tensor FLOPs issued (kOzS (kOzS + 1) / 2 digit products)
   const double flops = 2.0 * (double)Mp * (double)((ldk + kTcBK - 1) / kTcBK * kTcBK) * Bp * (kOzS * (kOzS + 1) / 2);
+  const long long zn = (long long)slots * Bp * Mp;
+  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_zero<<<(unsigned)((zn + 1023) / 1024 < 4 * c->nsm ? (zn + 1023) / 1024 : 4 * c->nsm),
+                                        256, 0, c->stream>>>(o.part, zn, need)));
   // launches gated by a device flag (z = A x on refreshes, the projected
   // segment) have their own kind: when skipped they do no work
   TRY(prof_begin(c, need != nullptr ? kKindOz + 2 + trans : kKindOz + trans, flops));
   switch (Bp) {
     case 16:
-      k_oz_gemm<16><<<grid, 128, oz_smem_bytes(16), c->stream>>>(ad, tx, Mp, M, (int)K, nkt, o.part, Mp, c->err,
-                                                                     need);
+      k_oz_gemm<16><<<grid, kOzThreads, oz_smem_bytes(16), c->stream>>>(ad, tx, Mp, M, (int)K, nkt, o.part, Mp,
+                                                                         c->err, need);
       break;
     case 32:
-      k_oz_gemm<32><<<grid, 128, oz_smem_bytes(32), c->stream>>>(ad, tx, Mp, M, (int)K, nkt, o.part, Mp, c->err,
-                                                                     need);
+      k_oz_gemm<32><<<grid, kOzThreads, oz_smem_bytes(32), c->stream>>>(ad, tx, Mp, M, (int)K, nkt, o.part, Mp,
+                                                                         c->err, need);
       break;
     case 48:
-      k_oz_gemm<48><<<grid, 128, oz_smem_bytes(48), c->stream>>>(ad, tx, Mp, M, (int)K, nkt, o.part, Mp, c->err,
-                                                                     need);
+      k_oz_gemm<48><<<grid, kOzThreads, oz_smem_bytes(48), c->stream>>>(ad, tx, Mp, M, (int)K, nkt, o.part, Mp,
+                                                                         c->err, need);
       break;
     default:
-      k_oz_gemm<64><<<grid, 128, oz_smem_bytes(64), c->stream>>>(ad, tx, Mp, M, (int)K, nkt, o.part, Mp, c->err,
-                                                                     need);
+      k_oz_gemm<64><<<grid, kOzThreads, oz_smem_bytes(64), c->stream>>>(ad, tx, Mp, M, (int)K, nkt, o.part, Mp,
+                                                                         c->err, need);
       break;
   }
   CU(cudaGetLastError());
   TRY(prof_end(c));
   c->launches += 1;
-  *splits_out = splits;
+  *splits_out = slots;
   return MVSK_OK;
 }
 
@@ -109,8 +114,8 @@ mvsk_status oz_product(mvsk_ctx* c, int trans, const double* V, long long vstrid
 // list (the union of the working faces of a batch): AU holds their digit
 // planes (k_oz_split_rows_u, padded count info[1]); V holds B vectors of ld
 // values in list coordinates (zero beyond the list).  Partials in c->oz.part
-// as from oz_product (ld Mp), split count info[1] / 512 rounded up, read by
-// the finishing kernel from info.
+// as from oz_product (ld Mp), slot count oz_slots(info[1] / 64), read by the
+// finishing kernel from info.
 mvsk_status oz_product_u(mvsk_ctx* c, const double* V, int B, int Bp, const __nv_bfloat16* AU, const int* info) {
   TRY(oz_prepare(c, Bp));
   OzBuf& o = c->oz;
@@ -120,26 +125,32 @@ mvsk_status oz_product_u(mvsk_ctx* c, const double* V, int B, int Bp, const __nv
                                V, c->ld, B, K, o.fF, nullptr)));
   PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_vec_digits<<<dim3((unsigned)((K + 255) / 256), Bp), 256, 0, c->stream>>>(
                                V, c->ld, B, Bp, K, c->ld, o.fF, o.XF, nullptr)));
-  const int splits = (K + kOzKc - 1) / kOzKc;  // the grid covers every column; CTAs past info[1] return
-  const dim3 grid((unsigned)(o.MpF / kTcBM), (unsigned)splits);
+  // the grid and the zeroed slots cover every column; the kernel takes its
+  // k-extent from info[1] (CTAs without units return)
+  const int nkb = K / kTcBK;
+  const long long units = o.MpF / kTcBM * ((nkb + 7) / 8);
+  const unsigned grid = (unsigned)(units < c->nsm ? units : c->nsm);
+  const long long zn = (long long)oz_slots(nkb) * Bp * o.MpF;
+  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_zero<<<(unsigned)((zn + 1023) / 1024 < 4 * c->nsm ? (zn + 1023) / 1024 : 4 * c->nsm),
+                                        256, 0, c->stream>>>(o.part, zn, nullptr)));
   // work per unit of the padded list length: 28 digit products of Mp x Bp
   TRY(prof_begin_u(c, kKindOz + 4, 2.0 * (double)o.MpF * Bp * (kOzS * (kOzS + 1) / 2)));
   switch (Bp) {
     case 16:
-      k_oz_gemm<16><<<grid, 128, oz_smem_bytes(16), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part, o.MpF,
-                                                                     c->err, nullptr, info);
+      k_oz_gemm<16><<<grid, kOzThreads, oz_smem_bytes(16), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part,
+                                                                         o.MpF, c->err, nullptr, info);
       break;
     case 32:
-      k_oz_gemm<32><<<grid, 128, oz_smem_bytes(32), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part, o.MpF,
-                                                                     c->err, nullptr, info);
+      k_oz_gemm<32><<<grid, kOzThreads, oz_smem_bytes(32), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part,
+                                                                         o.MpF, c->err, nullptr, info);
       break;
     case 48:
-      k_oz_gemm<48><<<grid, 128, oz_smem_bytes(48), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part, o.MpF,
-                                                                     c->err, nullptr, info);
+      k_oz_gemm<48><<<grid, kOzThreads, oz_smem_bytes(48), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part,
+                                                                         o.MpF, c->err, nullptr, info);
       break;
     default:
-      k_oz_gemm<64><<<grid, 128, oz_smem_bytes(64), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part, o.MpF,
-                                                                     c->err, nullptr, info);
+      k_oz_gemm<64><<<grid, kOzThreads, oz_smem_bytes(64), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part,
+                                                                         o.MpF, c->err, nullptr, info);
       break;
   }
   CU(cudaGetLastError());

@@ -155,74 +155,105 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
     if (s_stop) return;
   }
   // Working face: coordinates at tau are held, except every one whose
-  // violation nu_F - g_i is at least ||gbar_F|| / release_ratio.
+  // violation nu_F - g_i is at least ||gbar_F|| / release_ratio.  Coordinate
+  // i = threadIdx.x + e kVT (n <= kSliceE kVT) is held in registers; bit e of
+  // fr / mf marks it above tau / on the face, so that the FP64 arithmetic
+  // runs on the face's coordinates only.
   const double eps = SD[SD_EPSACT];
-  double sg = 0.0, cf = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    if (s.x[i] - tau > eps) {
-      sg += s.g[i];
-      cf += 1.0;
+  double gv[kSliceE];
+  unsigned fr = 0;
+  double sg = 0.0;
+  int cf = 0;
+#pragma unroll
+  for (int e = 0; e < kSliceE; ++e) {
+    const int i = threadIdx.x + e * kVT;
+    gv[e] = 0.0;
+    if (i < n) {
+      gv[e] = s.g[i];
+      if (s.x[i] - tau > eps) {
+        fr |= 1u << e;
+        sg += gv[e];
+        cf += 1;
+      }
     }
-  const double4 r1 = block_sum2_fin(sg, cf, scr, [](double x, double y) { return make_double2(x / y, 0.0); });
+  }
+  const Sum2c r1 = block_sum2c_fin(sg, 0.0, cf, scr, [](double x, double, int k) { return make_double2(x / k, 0.0); });
   double nuF = r1.z;
-  const double free0 = r1.y;  // coordinates above tau
+  const int free0 = r1.k;  // coordinates above tau
   double gq = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    if (s.x[i] - tau > eps) {
-      const double e = s.g[i] - nuF;
-      gq += e * e;
+#pragma unroll
+  for (int e = 0; e < kSliceE; ++e)
+    if ((fr >> e) & 1u) {
+      const double d = gv[e] - nuF;
+      gq += d * d;
     }
   const double gn0 = block_sum2_fin(gq, 0.0, scr, [](double x, double) { return make_double2(sqrt(x), 0.0); }).z;
   const double rr = SD[SD_RELRATIO];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const bool held = !(s.x[i] - tau > eps);
-    const double v = nuF - s.g[i];
-    s.maskF[i] = (!held || (v > 0.0 && gn0 <= rr * v)) ? 1.0 : 0.0;
-  }
-  __syncthreads();
+  unsigned mf = fr;
   sg = 0.0;
-  cf = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    sg += s.maskF[i] * s.g[i];
-    cf += s.maskF[i];
+  int cm = 0;
+#pragma unroll
+  for (int e = 0; e < kSliceE; ++e) {
+    const int i = threadIdx.x + e * kVT;
+    if (i < n) {
+      if (!((fr >> e) & 1u)) {
+        const double v = nuF - gv[e];
+        if (v > 0.0 && gn0 <= rr * v) mf |= 1u << e;
+      }
+      const bool on = (mf >> e) & 1u;
+      s.maskF[i] = on ? 1.0 : 0.0;
+      if (on) {
+        sg += gv[e];
+        cm += 1;
+      }
+    }
   }
-  const double4 r = block_sum2_fin(sg, cf, scr, [](double x, double y) { return make_double2(x / y, 0.0); });
-  const double m = r.y;
+  const Sum2c r = block_sum2c_fin(sg, 0.0, cm, scr, [](double x, double, int k) { return make_double2(x / k, 0.0); });
+  const double m = (double)r.k;
   nuF = r.z;
   // gbar = P_F g, centred twice: the second pass removes the rounding of the
   // first relative to gbar itself (not to g), so 1_F^T nu stays at rounding
   // level even when ||gbar|| << |g| near a stationary point.
   double sb = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double e = s.maskF[i] * (s.g[i] - nuF);
-    s.nuhat[i] = e;
-    sb += e;
+#pragma unroll
+  for (int e = 0; e < kSliceE; ++e) {
+    gv[e] = ((mf >> e) & 1u) ? gv[e] - nuF : 0.0;
+    sb += gv[e];
   }
   const double mb = block_sum2_fin(sb, 0.0, scr, [=](double x, double) { return make_double2(x / m, 0.0); }).z;
   gq = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double e = s.maskF[i] * (s.nuhat[i] - mb);
-    s.nuhat[i] = e;
-    gq += e * e;
-  }
+#pragma unroll
+  for (int e = 0; e < kSliceE; ++e)
+    if ((mf >> e) & 1u) {
+      gv[e] -= mb;
+      gq += gv[e] * gv[e];
+    }
   const double4 rg = block_sum2_fin(gq, 0.0, scr, [](double x, double) {
     const double v = sqrt(x);
     return make_double2(v, v > 0.0 ? 1.0 / v : 0.0);
   });
   const double gn = rg.z, inv_gn = rg.w;  // one FP64 division instead of n
-  const int mi = (int)m;
+  const int mi = r.k;
   const bool trivial = mi <= 2 || !(gn > 0.0);
-  for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
-    const double nh = (i < n && gn > 0.0) ? s.nuhat[i] * inv_gn : 0.0;
-    s.nuhat[i] = nh;
-    if (trivial) s.d[i] = (mi == 2) ? -nh : 0.0;
+#pragma unroll
+  for (int e = 0; e < kSliceE; ++e) {
+    const int i = threadIdx.x + e * kVT;
+    if (i < n) {
+      const double nh = (((mf >> e) & 1u) && gn > 0.0) ? gv[e] * inv_gn : 0.0;
+      s.nuhat[i] = nh;
+      if (trivial) s.d[i] = (mi == 2) ? -nh : 0.0;
+    }
+  }
+  for (int i = n + threadIdx.x; i < s.ld; i += kVT) {
+    s.nuhat[i] = 0.0;
+    if (trivial) s.d[i] = 0.0;
   }
   if (threadIdx.x == 0) {
     SD[SD_GN] = gn;
     SD[SD_NUF] = nuF;
     SI[SI_M] = mi;
     SI[SI_SKIPDIR] = trivial ? 1 : 0;
-    SI[SI_NREL] += mi - (int)free0;  // coordinates released this iteration
+    SI[SI_NREL] += mi - free0;  // coordinates released this iteration
   }
 }
 
@@ -914,13 +945,25 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
   double* u = s.tmp + s.ld;  // x + eta_k d - tau of the current trial (slice_theta scratch)
   double th = 0.0;
   for (int h = 0; h <= hmax; ++h) {
-    th = slice_theta(s.x, s.d, eta_k, n, tau, scr, u);
     double gd = 0.0, dd = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const double xb = tau + fmax(u[i] - th, 0.0);
-      const double db = xb - s.x[i];
-      gd += s.g[i] * db;
-      dd += db * db;
+    {
+      // the trial point xb = Pi(x + eta_k d): u and its threshold in registers
+      // (coordinate threadIdx.x + e kVT; n <= kSliceE kVT)
+      double uu[kSliceE];
+      float uf[kSliceE];
+      th = slice_theta_r(s.x, s.d, eta_k, n, tau, scr, u, uu, uf);
+      const float thf = (float)th;
+#pragma unroll
+      for (int e = 0; e < kSliceE; ++e) {
+        const int i = threadIdx.x + e * kVT;
+        if (i < n) {
+          const int c = gt_screen(uf[e], thf);
+          const double xb = (c > 0 || (c < 0 && uu[e] > th)) ? tau + (uu[e] - th) : tau;
+          const double db = xb - s.x[i];
+          gd += s.g[i] * db;
+          dd += db * db;
+        }
+      }
     }
     descent = block_sum2_fin(gd, dd, scr, [=](double x, double y) {
                 return make_double2(x < -deps * gt * sqrt(y) ? 1.0 : 0.0, 0.0);

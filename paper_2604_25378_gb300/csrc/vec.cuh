@@ -158,14 +158,216 @@ __device__ __forceinline__ void block_sum2k(KT& a, KT& b, double* scr) {
   }
 }
 
+// FP32 block sums of three values by warp shuffles (FP32 and integer pipes
+// only); scr holds >= 99 floats.  Every thread receives the sums.
+__device__ __forceinline__ float3 block_sum3f(float a, float b, float c, float* scr) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  __syncthreads();
+  if (lane == 0) {
+    scr[warp] = a;
+    scr[32 + warp] = b;
+    scr[64 + warp] = c;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float ta = lane < nw ? scr[lane] : 0.f, tb = lane < nw ? scr[32 + lane] : 0.f, tc = lane < nw ? scr[64 + lane] : 0.f;
+    ta = warp_sum(ta);
+    tb = warp_sum(tb);
+    tc = warp_sum(tc);
+    if (lane == 0) {
+      scr[96] = ta;
+      scr[97] = tb;
+      scr[98] = tc;
+    }
+  }
+  __syncthreads();
+  return make_float3(scr[96], scr[97], scr[98]);
+}
+
+// Block sums of two doubles and an int count (staged like block_sum2_fin);
+// fin(a, b, k) -> (z, w) runs once, on the thread completing the sums.
+struct Sum2c {
+  double a, b, z, w;
+  int k;
+};
+template <typename F>
+__device__ __forceinline__ Sum2c block_sum2c_fin(double a, double b, int k, double* scr, F fin) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* st = red_stage();
+  int* sti = red_stage_i();
+  __syncthreads();
+  st[threadIdx.x] = a;
+  st[1024 + threadIdx.x] = b;
+  sti[threadIdx.x] = k;
+  __syncthreads();
+  if (warp == 0) {
+    double a0 = 0.0, b0 = 0.0;
+    int k0 = 0;
+    for (int w = 0; w < nw; ++w) {
+      a0 += st[w * 32 + lane];
+      b0 += st[1024 + w * 32 + lane];
+      k0 += sti[w * 32 + lane];
+    }
+    const double ta = warp_sum(a0), tb = warp_sum(b0);
+    const int tk = warp_sum(k0);
+    if (lane == 0) {
+      const double2 zw = fin(ta, tb, tk);
+      scr[64] = ta;
+      scr[65] = tb;
+      scr[66] = zw.x;
+      scr[67] = zw.y;
+      scr[68] = (double)tk;
+    }
+  }
+  __syncthreads();
+  return {scr[64], scr[65], scr[66], scr[67], (int)scr[68]};
+}
+
+// u > th decided in FP32 from uf = (float)u and thf = (float)th: 1 or 0 when
+// the FP32 values settle it, -1 when the FP64 compare must.  Conversions
+// round to nearest (relative error <= 2^-24 in the normal range, absolute
+// <= 2^-149 below it), so a gap of 1e-6 (|uf| + |thf|) + 1e-30 leaves a
+// margin of more than 10x over both conversions and the FP32 sum.
+__device__ __forceinline__ int gt_screen(float uf, float thf) {
+  if (!(fabsf(uf) < 1e30f) || !(fabsf(thf) < 1e30f)) return -1;
+  const float gap = 1e-6f * (fabsf(uf) + fabsf(thf)) + 1e-30f;
+  if (uf > thf + gap) return 1;
+  if (uf < thf - gap) return 0;
+  return -1;
+}
+
 // Threshold theta of the projection onto Delta(tau) of v = base + s*dir
-// (dir may be null): Pi(v)_i = tau + max(v_i - tau - theta, 0).
-// Michelot (1986): iterate theta = (sum_{u_i > theta} u_i - b)/#{u_i > theta},
-// u = v - tau, from the full set until the set stops shrinking.  With a
-// scratch vector u is formed once (each iteration then costs one FP64 compare
-// and add per coordinate; FP64 runs at ~2 ops/clk/SM here) and left in it.
+// (dir may be null): Pi(v)_i = tau + max(v_i - tau - theta, 0), i.e. the root
+// of phi(theta) = sum_i max(u_i - theta, 0) - b, u = v - tau, b = 1 - n tau.
+// Michelot (1986): theta_{k+1} = (sum_{u_i > theta_k} u_i - b) / #{u_i > theta_k}
+// increases monotonically to the root from any theta_0 with phi(theta_0) >= 0
+// (the set {u_i > theta_k} only shrinks), and stops when the set does; the
+// mean start theta_0 = (sum_i u_i - b) / n always qualifies.  u (nullable)
+// receives v - tau.
+//
+// Coordinates are held in registers (n <= kSliceE blockDim.x; larger n take
+// slice_theta_mem) and the iteration runs twice: in FP32 from the mean start
+// to an estimate thf, then in FP64 from theta_0 = thf - delta, delta well
+// above the FP32 error, with phi(theta_0) >= 0 checked on the first FP64 step
+// (else FP64 from the mean start).  Coordinates left below a threshold stay
+// out (monotonicity), and FP32 screening (gt_screen) settles most compares,
+// so the FP64 pipe sees about one pass over the coordinates plus the final
+// set rather than one pass per iteration.
+constexpr int kSliceE = (kMaxCols + kVT - 1) / kVT;
+
+inline __device__ double slice_theta_mem(const double* base, const double* dir, double s, int n, double tau,
+                                         double* scr, double* u);
+
+// The register form (n <= kSliceE blockDim.x): uu[e], uf[e] receive u_i and
+// (float)u_i of coordinate i = threadIdx.x + e blockDim.x (0 beyond n).
+__device__ __forceinline__ double slice_theta_r(const double* base, const double* dir, double s, int n, double tau,
+                                                double* scr, double* u, double (&uu)[kSliceE], float (&uf)[kSliceE]) {
+  const double b = 1.0 - (double)n * tau;
+  unsigned all = 0;
+  double su = 0.0;
+  float sabs = 0.f;
+#pragma unroll
+  for (int e = 0; e < kSliceE; ++e) {
+    const int i = threadIdx.x + e * blockDim.x;
+    double ui = 0.0;
+    if (i < n) {
+      ui = (dir ? base[i] + s * dir[i] : base[i]) - tau;
+      if (u) u[i] = ui;
+      su += ui;
+      all |= 1u << e;
+    }
+    uu[e] = ui;
+    uf[e] = (float)ui;
+    sabs += fabsf(uf[e]);
+  }
+  const double4 r0 = block_sum2_fin(su, (double)sabs, scr,
+                                    [=](double x, double) { return make_double2((x - b) / (double)n, 0.0); });
+  const double theta_mean = r0.z;
+  // FP32 pass: an estimate of the root and the scale of its error
+  float thf = (float)theta_mean;
+  double scale = r0.y / (double)n;  // mean |u| over the current set
+  {
+    unsigned in = all;
+    int cnt = n;
+    for (int it = 0; it < 64; ++it) {
+      float sa = 0.f, sb = 0.f;
+      int ka = 0;
+      unsigned nin = 0;
+#pragma unroll
+      for (int e = 0; e < kSliceE; ++e)
+        if (((in >> e) & 1u) && uf[e] > thf) {
+          sa += uf[e];
+          sb += fabsf(uf[e]);
+          ka += 1;
+          nin |= 1u << e;
+        }
+      in = nin;
+      const float3 r = block_sum3f(sa, sb, (float)ka, reinterpret_cast<float*>(scr));
+      const int k = (int)r.z;
+      if (k == cnt || k == 0) break;
+      cnt = k;
+      thf = (r.x - (float)b) / r.z;
+      scale = (double)(r.y / r.z);
+    }
+  }
+  // FP64 pass from just below the estimate
+  double th = (double)thf - 1e-4 * (fabs((double)thf) + scale);
+  if (!(th > theta_mean)) th = theta_mean;
+  unsigned in = all;
+  int cnt = -1;
+  bool first = true;
+  for (int it = 0; it <= n + 1; ++it) {
+    const float tf = (float)th;
+    double sa = 0.0;
+    int ka = 0;
+    unsigned nin = 0;
+#pragma unroll
+    for (int e = 0; e < kSliceE; ++e)
+      if ((in >> e) & 1u) {
+        const int c = gt_screen(uf[e], tf);
+        if (c > 0 || (c < 0 && uu[e] > th)) {
+          sa += uu[e];
+          ka += 1;
+          nin |= 1u << e;
+        }
+      }
+    const double thc = th;
+    const Sum2c r = block_sum2c_fin(sa, 0.0, ka, scr, [=](double x, double, int k) {
+      // next iterate; phi(th) = sum_{u > th} (u - th) - b >= 0 (th at or below the root)
+      return make_double2(k > 0 ? (x - b) / (double)k : 0.0, (x - (double)k * thc - b) >= 0.0 ? 1.0 : 0.0);
+    });
+    if (first) {
+      first = false;
+      if (r.w == 0.0 && th > theta_mean) {  // started above the root: restart from the mean start
+        th = theta_mean;
+        in = all;
+        first = true;
+        continue;
+      }
+    }
+    if (r.k == cnt || r.k == 0) break;
+    cnt = r.k;
+    th = r.z;
+    in = nin;
+  }
+  return th;
+}
+
 inline __device__ double slice_theta(const double* base, const double* dir, double s, int n, double tau, double* scr,
                                      double* u = nullptr) {
+  if (n > kSliceE * (int)blockDim.x) return slice_theta_mem(base, dir, s, n, tau, scr, u);
+  double uu[kSliceE];
+  float uf[kSliceE];
+  return slice_theta_r(base, dir, s, n, tau, scr, u, uu, uf);
+}
+
+// The same with the coordinates in memory (any n): plain FP64 Michelot from
+// the mean start, u formed once into the scratch vector when one is given.
+inline __device__ double slice_theta_mem(const double* base, const double* dir, double s, int n, double tau,
+                                         double* scr, double* u) {
   const double b = 1.0 - (double)n * tau;
   double su = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -200,14 +402,31 @@ inline __device__ double slice_theta(const double* base, const double* dir, doub
 // residual and its relative value; tmp receives x - g - tau.
 inline __device__ double2 kkt_residual_rel(const double* x, const double* g, int n, double tau, double* scr,
                                            double* tmp, double norm) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) tmp[i] = x[i] - g[i];
-  __syncthreads();
-  const double th = slice_theta(tmp, nullptr, 0.0, n, tau, scr, tmp);
   double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double p = tau + fmax(tmp[i] - th, 0.0);
-    const double e = x[i] - p;
-    s += e * e;
+  if (n > kSliceE * (int)blockDim.x) {
+    const double th = slice_theta_mem(x, g, -1.0, n, tau, scr, tmp);  // tmp = (x - g) - tau
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double p = tau + fmax(tmp[i] - th, 0.0);
+      const double e = x[i] - p;
+      s += e * e;
+    }
+  } else {
+    double uu[kSliceE];
+    float uf[kSliceE];
+    const double th = slice_theta_r(x, g, -1.0, n, tau, scr, tmp, uu, uf);
+    const float thf = (float)th;
+#pragma unroll
+    for (int e = 0; e < kSliceE; ++e) {
+      const int i = threadIdx.x + e * blockDim.x;
+      if (i < n) {
+        // p = tau + max(u - theta, 0): u - theta > 0 exactly when u > theta
+        const int c = gt_screen(uf[e], thf);
+        const double p = (c > 0 || (c < 0 && uu[e] > th)) ? tau + (uu[e] - th) : tau;
+        const double d = x[i] - p;
+        s += d * d;
+      }
+    }
   }
   const double4 r = block_sum2_fin(s, 0.0, scr, [=](double x2, double) {
     const double k = sqrt(x2);

@@ -96,6 +96,42 @@ def test_projection(n):
         np.testing.assert_allclose(p, O.project_slice(v, tau), rtol=0, atol=1e-15)
 
 
+# Inputs that stress the two-stage threshold search (FP32 estimate, FP64
+# finish): cancellation between large values, a few huge entries among tiny
+# ones, ties, constant and subnormal-scale vectors, and a C4-sized x - g.
+def _hard_vectors(n, rng):
+    big = rng.choice([-1.0, 1.0], n) * 1e6 + rng.standard_normal(n)
+    spiky = rng.standard_normal(n) * 1e-9
+    spiky[rng.choice(n, size=min(n, 3), replace=False)] = [5e3, -7e3, 2e3][: min(n, 3)]
+    ties = np.repeat(rng.standard_normal(max(1, n // 50)), 50)[:n]
+    ties = np.concatenate([ties, np.zeros(n - len(ties))])
+    const = np.full(n, 0.25)
+    tiny = rng.standard_normal(n) * 1e-310
+    xg = np.full(n, 1.0 / n) - rng.standard_normal(n) * 0.05 - 0.2 * (rng.random(n) < 0.01)
+    return {"big": big, "spiky": spiky, "ties": ties, "const": const, "tiny": tiny, "xg": xg}
+
+
+@pytest.mark.parametrize("n", [5, 1000, 5440, 6144])
+def test_projection_hard_cases(n):
+    rng = np.random.default_rng(100 + n)
+    R = panels.single_factor_panel(n, 8, 0)
+    ctx = _ctx(R)
+    for name, v in _hard_vectors(n, rng).items():
+        for tau in (1e-8, 0.0):
+            p = ctx.project_slice(v, tau)
+            ref = O.project_slice(v, tau)
+            # theta = (sum_S u - b) / |S| is summed in another order on each
+            # side (the oracle by a running sum): each differs from the exact
+            # value by at most about eps (sum_S |u| + |b|) (the running sum's
+            # bound |S| eps sum_S |u|, over |S|), so the projections agree to
+            # a few times that
+            S = ref > tau
+            scale = 1.0 + np.sum(np.abs(v[S])) + np.max(np.abs(v))
+            np.testing.assert_allclose(p, ref, rtol=0, atol=8 * 2.0**-52 * scale, err_msg=name)
+            assert np.all(p >= tau), name
+            assert abs(np.sum(p) - 1.0) <= 1e-12 * scale * max(1, np.sum(p > tau)), name
+
+
 def test_quartic_argmin_matches_oracle_routine():
     R = panels.single_factor_panel(3, 8, 0)
     ctx = _ctx(R)

@@ -48,16 +48,19 @@ def test_product_random(n, T, nvec, transpose):
     _check_bound(got, A, V, transpose)
 
 
+# (n, half of T, entry bits): K <= 4096 (one integer slot), and T = 10000
+# for A^T V (20 chunks of 512: two slots of 16 chunks)
+@pytest.mark.parametrize("n,half,bits", [(600, 1100, 20), (300, 5000, 18)])
 @pytest.mark.parametrize("transpose", [False, True])
-def test_product_integer_panel_is_exact(transpose):
+def test_product_integer_panel_is_exact(transpose, n, half, bits):
     """Columns of R with exactly zero mean (rows +R0 and -R0): A = R exactly.
-    Entries below 2^20 and K <= 4096 keep every FP64 partial sum exact."""
+    Entries below 2^bits with 2 bits + log2 K <= 53 keep every FP64 partial
+    sum of the reference exact."""
     import torch
     rng = np.random.default_rng(7)
-    n, half = 600, 1100
-    R0 = rng.integers(-(1 << 20), 1 << 20, size=(half, n)).astype(np.float64)
+    R0 = rng.integers(-(1 << bits), 1 << bits, size=(half, n)).astype(np.float64)
     # left-operand rows (rows of A, or columns for A^T) of very different
-    # magnitude; each row keeps 21 significant bits, so it fits 49 bits
+    # magnitude; each row keeps bits + 1 significant bits, so it fits 49 bits
     # relative to its own maximum
     if transpose:
         R0 *= 2.0 ** -rng.integers(0, 12, size=(1, n))
@@ -68,7 +71,7 @@ def test_product_integer_panel_is_exact(transpose):
     assert np.all(mu == 0.0) and np.array_equal(A, R)
     T = R.shape[0]
     nvec = 64
-    V = rng.integers(-(1 << 20), 1 << 20, size=(nvec, T if transpose else n)).astype(np.float64)
+    V = rng.integers(-(1 << bits), 1 << bits, size=(nvec, T if transpose else n)).astype(np.float64)
     V *= 2.0 ** -rng.integers(0, 12, size=(nvec, 1))
     ctx = _ctx(R)
     got = ctx.product(torch.from_numpy(V).cuda(), transpose=transpose).cpu().numpy()
