@@ -450,11 +450,15 @@ __global__ void k_union_flags(Inst base, int B, int* flag) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= base.ld) return;
   int f = 0;
-  if (i < base.n)
-    for (int b = 0; b < B && !f; ++b) {
-      const int* si = base.si + (size_t)b * kSI;
-      if (si[SI_DONE] == 0 && base.maskF[(size_t)b * base.vs + i] != 0.0) f = 1;
+  if (i < base.n) {
+    // independent loads (no early exit), so that they are all in flight at once
+#pragma unroll 8
+    for (int b = 0; b < B; ++b) {
+      // mask != 0 tested on the bits (integer pipe): nonzero apart from the sign
+      const long long mb = __double_as_longlong(base.maskF[(size_t)b * base.vs + i]);
+      f |= (int)(base.si[(size_t)b * kSI + SI_DONE] == 0) & (int)((mb << 1) != 0);
     }
+  }
   flag[i] = f;
 }
 

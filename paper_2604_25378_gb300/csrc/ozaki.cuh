@@ -64,15 +64,42 @@ __device__ __forceinline__ int oz_exponent(double vmax) {
   return e;
 }
 
+// R = round(v * 2^(kOzExp - e)) (nearest, ties to even) for |v| < 2^e, from
+// the bits of v with integer operations only: an FP64 scaling and conversion
+// would take the FP64 pipe (about 2 operations/clk/SM on this part).  The
+// mantissa m (implicit bit included) times 2^(E - 1075) is shifted right by
+// k = 1075 - E - kOzExp + e places (k >= 4 for normal v, |v| < 2^e; a
+// subnormal v may take a left shift).  0 for k >= 64 and for non-finite v.
+__device__ __forceinline__ long long oz_fixed(double v, int e) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  if (E == 0x7FF) return 0;
+  const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (E != 0 ? (1ull << 52) : 0ull);
+  const int k = (E != 0 ? 1075 - E : 1074) - kOzExp + e;
+  if (k >= 64 || m == 0) return 0;
+  unsigned long long q;
+  if (k <= 0) {
+    q = m << (-k);  // subnormal v with e <= -1025: exact (q < 2^49 by the contract)
+  } else {
+    q = m >> k;
+    const unsigned long long rem = m & ((1ull << k) - 1ull), half = 1ull << (k - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+  }
+  return (bits >> 63) ? -(long long)q : (long long)q;
+}
+
 // The kOzS digits of v * 2^-e (|v| < 2^e) as BF16, written plane-strided.
+// Digit values |q| <= 128 are exact in FP32 and BF16; the FP32 value comes
+// from the integer by the 1.5 * 2^23 offset (FP32 pipe, no conversion unit).
 __device__ __forceinline__ void oz_digits(double v, int e, __nv_bfloat16* out, size_t plane) {
-  long long R = __double2ll_rn(ldexp(v, kOzExp - e));  // |R| <= 2^49
+  long long R = oz_fixed(v, e);  // |R| <= 2^49
 #pragma unroll
   for (int s = 0; s < kOzS; ++s) {
     const int sh = kOzBits * (kOzS - 1 - s);
     const long long q = sh > 0 ? ((R + (1LL << (sh - 1))) >> sh) : R;  // nearest, ties up
     R -= q * (1LL << sh);
-    out[(size_t)s * plane] = __float2bfloat16_rn((float)q);
+    const float qf = __int_as_float(0x4B400000 + (int)q) - 12582912.0f;
+    out[(size_t)s * plane] = __float2bfloat16_rn(qf);
   }
 }
 
@@ -216,9 +243,15 @@ static __global__ void k_oz_vec_digits(const double* V, long long vstride, int B
 constexpr int kOzEpiWarps = 16;
 constexpr int kOzThreads = 64 + 32 * kOzEpiWarps;
 constexpr int kOzGroup = 16;  // chunks per integer slot
+constexpr int kOzPrefetch = 3;  // k-blocks of left digits prefetched into L2 ahead of the copies
 
 // Integer slots of a product over nkb k-blocks.
 __host__ __device__ constexpr int oz_slots(int nkb) { return ((nkb + 7) / 8 + kOzGroup - 1) / kOzGroup; }
+
+// Prefetch of [src, src + bytes) into L2 (16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -299,10 +332,35 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __nv_bfloat16* 
     if (lane == 0) {  // producer
       int i = 0, ai = 0;
       bool ok = true;
+      // L2 prefetch cursor (pu, pkb), kOzPrefetch k-blocks ahead of the
+      // copies into shared memory: the ring holds about one k-block of left
+      // digits, and a tile's slot frees only when the MMAs of the previous
+      // k-block have read it, so the copies themselves cannot run far ahead;
+      // the prefetches keep the DRAM requests of the next k-blocks in flight.
+      long long pu = u0;
+      int pkb = (int)(u0 % nch) * 8;
+      auto advance = [&]() {
+        const int e = ((int)(pu % nch) * 8 + 8 < nkb) ? (int)(pu % nch) * 8 + 8 : nkb;
+        if (++pkb >= e) {
+          ++pu;
+          pkb = (int)(pu % nch) * 8;
+        }
+      };
+      auto prefetch = [&]() {
+        if (pu >= u1) return;
+        const long long pmt = pu / nch;
+#pragma unroll 1
+        for (int s = 0; s < kOzS; ++s)
+          bulk_prefetch_l2(Ad + (size_t)s * Mp * nkt * 64 + ((size_t)pmt * nkt + (size_t)pkb) * 8192, ABYTES);
+        advance();
+      };
+      advance();  // the first k-block is copied at once
+      for (int d = 0; d < kOzPrefetch; ++d) prefetch();
       for (long long u = u0; u < u1 && ok; ++u) {
         const long long mt = u / nch;
         const int kb0 = (int)(u % nch) * 8, kb1 = kb0 + 8 < nkb ? kb0 + 8 : nkb;
         for (int kb = kb0; kb < kb1 && ok; ++kb, ++i) {
+          prefetch();
           const int xs = i % kOzXStages;
           if (*s_abort || (i >= kOzXStages && !mbar_wait_bounded(&xempty[xs], (uint32_t)(((i / kOzXStages) - 1) & 1)))) {
             ok = false;

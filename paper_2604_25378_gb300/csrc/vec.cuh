@@ -452,6 +452,64 @@ __device__ __forceinline__ double decrease(const double* c, double a) {
 // real roots of phi'' (cancellation-free quadratic formula) split the interval
 // into pieces on which phi' is monotone; a sign change brackets one root, found
 // by bisection down to adjacent doubles.  Ties keep the smallest alpha.
+__device__ __forceinline__ double ddphi(const double* c, double a) {
+  return (12.0 * c[4] * a + 6.0 * c[3]) * a + 2.0 * c[2];
+}
+
+// The root of phi' in [lo, hi], where phi' is monotone and changes sign
+// (flo = phi'(lo) != 0).  The FP64 pipe of this part runs about 2 FMA/clk/SM
+// (a warp-wide FP64 instruction occupies it for ~64 cycles, whatever the
+// active lanes), so plain bisection to adjacent doubles (~60 dependent
+// steps) costs tens of microseconds on the one thread that runs it.  Here:
+// (1) the cubic q(t) = phi'(lo + t w), w = hi - lo, is rescaled by a power of
+// two to coefficients of magnitude <= 1 and bisected in FP32 on [0, 1] to
+// 2^-20; (2) FP64 Newton steps on phi' from that start, each kept inside the
+// FP64 bracket [a, b] (updated from the sign of phi' at every iterate; a step
+// leaving it is replaced by the midpoint), until a step is below 4 ulps.  A
+// simple root converges in two or three steps.  At most 80 steps in all,
+// ending, like bisection, at the midpoint of adjacent doubles.  The result
+// lies within a few ulps of the root; the decrease phi(alpha) - phi(0) then
+// agrees with that of the exact root to rounding, being stationary there.
+__device__ __forceinline__ double dphi_root(const double* c, double lo, double hi, double flo) {
+  const double w = hi - lo;
+  // q(t) = d0 + d1 t + d2 t^2 + d3 t^3 (Taylor expansion of phi' at lo)
+  const double d0 = flo, d1 = ddphi(c, lo) * w, d2 = (3.0 * c[3] + 12.0 * c[4] * lo) * w * w,
+               d3 = 4.0 * c[4] * w * w * w;
+  const double dm = fmax(fmax(fabs(d0), fabs(d1)), fmax(fabs(d2), fabs(d3)));
+  int ex = 0;
+  frexp(dm, &ex);
+  const float e0 = (float)ldexp(d0, -ex), e1 = (float)ldexp(d1, -ex), e2 = (float)ldexp(d2, -ex),
+              e3 = (float)ldexp(d3, -ex);
+  float ta = 0.f, tb = 1.f;
+  const bool neg = flo < 0.0;
+  for (int it = 0; it < 20; ++it) {
+    const float tm = 0.5f * (ta + tb);
+    const float q = fmaf(fmaf(fmaf(e3, tm, e2), tm, e1), tm, e0);
+    if (q == 0.f) {
+      ta = tb = tm;
+      break;
+    }
+    if ((q < 0.f) == neg) ta = tm; else tb = tm;
+  }
+  double a = lo, b = hi;
+  double x = lo + (double)(0.5f * (ta + tb)) * w;
+  if (!(x > a && x < b)) x = 0.5 * (a + b);
+  for (int it = 0; it < 80; ++it) {
+    const double f = dphi(c, x);
+    if (f == 0.0) return x;
+    if ((f < 0.0) == neg) a = x; else b = x;
+    const double m = 0.5 * (a + b);
+    if (m <= a || m >= b) break;  // adjacent doubles
+    const double fp = ddphi(c, x);
+    double xn = x - f / fp;
+    if (!(xn > a && xn < b)) xn = m;  // also NaN (fp = 0)
+    const double step = fabs(xn - x);
+    x = xn;
+    if (step <= 8.9e-16 * fabs(x)) return x;  // below 4 ulps
+  }
+  return (a != b) ? 0.5 * (a + b) : a;
+}
+
 inline __device__ double quartic_argmin(const double* c, double amax) {
   if (!(amax > 0.0)) return 0.0;
   double brk[4];
@@ -489,15 +547,7 @@ inline __device__ double quartic_argmin(const double* c, double amax) {
     if (flo == 0.0) { cand[nc++] = lo; continue; }
     if (fhi == 0.0) { cand[nc++] = hi; continue; }
     if ((flo < 0.0) == (fhi < 0.0)) continue;
-    double a = lo, b = hi;
-    for (int it = 0; it < 200; ++it) {
-      const double m = 0.5 * (a + b);
-      if (m <= a || m >= b) break;
-      const double fm = dphi(c, m);
-      if (fm == 0.0) { a = b = m; break; }
-      if ((fm < 0.0) == (flo < 0.0)) a = m; else b = m;
-    }
-    cand[nc++] = (a != b) ? 0.5 * (a + b) : a;
+    cand[nc++] = dphi_root(c, lo, hi, flo);
   }
   // sort ascending (tiny insertion sort), then keep the first strict minimum
   for (int i = 1; i < nc; ++i) {
