@@ -324,7 +324,8 @@ __global__ void k_project(const double* v, int n, double tau, double* out) {
 }
 
 __global__ void k_quartic(const double* coef, double amax, double* out) {
-  if (threadIdx.x == 0) *out = quartic_argmin(coef, amax);
+  const double v = quartic_argmin_w(coef, amax);  // one warp
+  if (threadIdx.x == 0) *out = v;
 }
 
 __global__ void k_alpha_max(const double* x, const double* d, int n, double tau, double* out) {

@@ -243,15 +243,9 @@ static __global__ void k_oz_vec_digits(const double* V, long long vstride, int B
 constexpr int kOzEpiWarps = 16;
 constexpr int kOzThreads = 64 + 32 * kOzEpiWarps;
 constexpr int kOzGroup = 16;  // chunks per integer slot
-constexpr int kOzPrefetch = 3;  // k-blocks of left digits prefetched into L2 ahead of the copies
 
 // Integer slots of a product over nkb k-blocks.
 __host__ __device__ constexpr int oz_slots(int nkb) { return ((nkb + 7) / 8 + kOzGroup - 1) / kOzGroup; }
-
-// Prefetch of [src, src + bytes) into L2 (16-byte aligned, bytes a multiple of 16).
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -332,35 +326,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __nv_bfloat16* 
     if (lane == 0) {  // producer
       int i = 0, ai = 0;
       bool ok = true;
-      // L2 prefetch cursor (pu, pkb), kOzPrefetch k-blocks ahead of the
-      // copies into shared memory: the ring holds about one k-block of left
-      // digits, and a tile's slot frees only when the MMAs of the previous
-      // k-block have read it, so the copies themselves cannot run far ahead;
-      // the prefetches keep the DRAM requests of the next k-blocks in flight.
-      long long pu = u0;
-      int pkb = (int)(u0 % nch) * 8;
-      auto advance = [&]() {
-        const int e = ((int)(pu % nch) * 8 + 8 < nkb) ? (int)(pu % nch) * 8 + 8 : nkb;
-        if (++pkb >= e) {
-          ++pu;
-          pkb = (int)(pu % nch) * 8;
-        }
-      };
-      auto prefetch = [&]() {
-        if (pu >= u1) return;
-        const long long pmt = pu / nch;
-#pragma unroll 1
-        for (int s = 0; s < kOzS; ++s)
-          bulk_prefetch_l2(Ad + (size_t)s * Mp * nkt * 64 + ((size_t)pmt * nkt + (size_t)pkb) * 8192, ABYTES);
-        advance();
-      };
-      advance();  // the first k-block is copied at once
-      for (int d = 0; d < kOzPrefetch; ++d) prefetch();
       for (long long u = u0; u < u1 && ok; ++u) {
         const long long mt = u / nch;
         const int kb0 = (int)(u % nch) * 8, kb1 = kb0 + 8 < nkb ? kb0 + 8 : nkb;
         for (int kb = kb0; kb < kb1 && ok; ++kb, ++i) {
-          prefetch();
           const int xs = i % kOzXStages;
           if (*s_abort || (i >= kOzXStages && !mbar_wait_bounded(&xempty[xs], (uint32_t)(((i / kOzXStages) - 1) & 1)))) {
             ok = false;

@@ -90,7 +90,8 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
   Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
   __shared__ double ps[2];
-  __shared__ int s_stop;
+  __shared__ int s_stop, s_better;
+  __shared__ long long s_klo, s_khi;
   int* SI = s.si;
   double* SD = s.sd;
   if (SI[SI_DONE] != 0) return;
@@ -104,11 +105,11 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
     if (!isfinite(s.g[i])) nonfin += 1.0;
   }
   const double2 r0 = block_sum2(mx, nonfin, scr);
-  const double f = -SD[SD_C1] * r0.x + ps[0];
   if (threadIdx.x == 0) s_stop = 0;
   __syncthreads();
   if (!dir_only) {
     if (threadIdx.x == 0) {
+      const double f = -SD[SD_C1] * r0.x + ps[0];
       SD[SD_F] = f;
       SD[SD_MUX] = r0.x;
       if (r0.y > 0.0 || !isfinite(f)) {
@@ -127,10 +128,9 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
     if (s_stop) return;
     const double2 kr = kkt_residual_rel(s.x, s.g, n, tau, scr, s.tmp, SD[SD_KKT0]);
     const double kkt = kr.x, rel = kr.y;
-    const bool better = rel < SD[SD_BEST];
-    if (better)
-      for (int i = threadIdx.x; i < n; i += blockDim.x) s.bestx[i] = s.x[i];
     if (threadIdx.x == 0) {
+      const bool better = rel < SD[SD_BEST];
+      s_better = better;
       SD[SD_KKT] = kkt;
       SD[SD_KKTREL] = rel;
       if (better) SD[SD_BEST] = rel;
@@ -152,6 +152,8 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
       }
     }
     __syncthreads();
+    if (s_better)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) s.bestx[i] = s.x[i];
     if (s_stop) return;
   }
   // Working face: coordinates at tau are held, except every one whose
@@ -170,7 +172,8 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
     gv[e] = 0.0;
     if (i < n) {
       gv[e] = s.g[i];
-      if (s.x[i] - tau > eps) {
+      const double xi = s.x[i];
+      if (!same_bits(xi, tau) && xi - tau > eps) {  // x = tau: 0 <= eps
         fr |= 1u << e;
         sg += gv[e];
         cf += 1;
@@ -187,8 +190,26 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
       const double d = gv[e] - nuF;
       gq += d * d;
     }
-  const double gn0 = block_sum2_fin(gq, 0.0, scr, [](double x, double) { return make_double2(sqrt(x), 0.0); }).z;
   const double rr = SD[SD_RELRATIO];
+  // The release test v = nuF - g_i > 0 and gn0 <= rr v holds for g_i below
+  // T = nuF - gn0 / rr and fails above it; integer keys of T -+ delta (delta
+  // far above the rounding of either form) settle all but a narrow band,
+  // which takes the FP64 test itself.  (INT64_MIN: no screening.)
+  long long* pklo = &s_klo;
+  long long* pkhi = &s_khi;
+  const double gn0 = block_sum2_fin(gq, 0.0, scr, [=](double x, double) {
+                       const double g0 = sqrt(x);
+                       long long lo = INT64_MIN, hi = INT64_MIN;
+                       if (rr > 0.0 && g0 >= 0.0 && isfinite(rr) && isfinite(g0) && isfinite(nuF)) {
+                         const double q = g0 / rr, T = nuF - q, dl = 1e-9 * (fabs(nuF) + q + fabs(T)) + 1e-300;
+                         lo = dkey(T - dl);
+                         hi = dkey(T + dl);
+                       }
+                       *pklo = lo;
+                       *pkhi = hi;
+                       return make_double2(g0, 0.0);
+                     }).z;
+  const long long klo = s_klo, khi = s_khi;
   unsigned mf = fr;
   sg = 0.0;
   int cm = 0;
@@ -197,8 +218,18 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
     const int i = threadIdx.x + e * kVT;
     if (i < n) {
       if (!((fr >> e) & 1u)) {
-        const double v = nuF - gv[e];
-        if (v > 0.0 && gn0 <= rr * v) mf |= 1u << e;
+        const long long kg = dkey(gv[e]);
+        const bool fin = ((__double_as_longlong(gv[e]) >> 52) & 0x7FF) != 0x7FF;
+        bool rel;
+        if (fin && kg < klo) {
+          rel = true;
+        } else if (fin && kg > khi && khi != INT64_MIN) {
+          rel = false;
+        } else {
+          const double v = nuF - gv[e];
+          rel = v > 0.0 && gn0 <= rr * v;
+        }
+        if (rel) mf |= 1u << e;
       }
       const bool on = (mf >> e) & 1u;
       s.maskF[i] = on ? 1.0 : 0.0;
@@ -209,7 +240,7 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
     }
   }
   const Sum2c r = block_sum2c_fin(sg, 0.0, cm, scr, [](double x, double, int k) { return make_double2(x / k, 0.0); });
-  const double m = (double)r.k;
+  const int mi = r.k;
   nuF = r.z;
   // gbar = P_F g, centred twice: the second pass removes the rounding of the
   // first relative to gbar itself (not to g), so 1_F^T nu stays at rounding
@@ -220,7 +251,7 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
     gv[e] = ((mf >> e) & 1u) ? gv[e] - nuF : 0.0;
     sb += gv[e];
   }
-  const double mb = block_sum2_fin(sb, 0.0, scr, [=](double x, double) { return make_double2(x / m, 0.0); }).z;
+  const double mb = block_sum2_fin(sb, 0.0, scr, [=](double x, double) { return make_double2(x / (double)mi, 0.0); }).z;
   gq = 0.0;
 #pragma unroll
   for (int e = 0; e < kSliceE; ++e)
@@ -233,13 +264,13 @@ static __global__ void __launch_bounds__(kVT) k_face(Inst s0, const double* spar
     return make_double2(v, v > 0.0 ? 1.0 / v : 0.0);
   });
   const double gn = rg.z, inv_gn = rg.w;  // one FP64 division instead of n
-  const int mi = r.k;
-  const bool trivial = mi <= 2 || !(gn > 0.0);
+  const bool gpos = !is_zero_bits(inv_gn);   // gn > 0 (inv_gn is 0 otherwise)
+  const bool trivial = mi <= 2 || !gpos;
 #pragma unroll
   for (int e = 0; e < kSliceE; ++e) {
     const int i = threadIdx.x + e * kVT;
     if (i < n) {
-      const double nh = (((mf >> e) & 1u) && gn > 0.0) ? gv[e] * inv_gn : 0.0;
+      const double nh = (((mf >> e) & 1u) && gpos) ? gv[e] * inv_gn : 0.0;
       s.nuhat[i] = nh;
       if (trivial) s.d[i] = (mi == 2) ? -nh : 0.0;
     }
@@ -860,7 +891,10 @@ inline __device__ void ls_coefficients(Inst& s, const double* spart, int G, cons
                                 double* ps) {
   reduce_spart(spart, G, 12, s.sd[SD_INVT], ps);
   double md = 0.0;
-  for (int i = threadIdx.x; i < s.n; i += blockDim.x) md += s.mu[i] * dir[i];
+  for (int i = threadIdx.x; i < s.n; i += blockDim.x) {
+    const double di = dir[i];
+    if (!is_zero_bits(di)) md += s.mu[i] * di;  // a zero term leaves the sum as it is
+  }
   md = block_sum2(md, 0.0, scr).x;
   if (threadIdx.x == 0) {
     const double c1 = s.sd[SD_C1], c2 = s.sd[SD_C2], c3 = s.sd[SD_C3], c4 = s.sd[SD_C4];
@@ -879,8 +913,15 @@ inline __device__ void ls_coefficients(Inst& s, const double* spart, int G, cons
 inline __device__ void take_step(Inst& s, const double* dir, double al, const double* xbar_or_null) {
   const double tau = s.sd[SD_TAU], eps = s.sd[SD_EPSACT];
   for (int i = threadIdx.x; i < s.n; i += blockDim.x) {
-    double v = xbar_or_null ? xbar_or_null[i] : s.x[i] + al * dir[i];
-    if (v - tau <= eps) v = tau;
+    double v;
+    if (xbar_or_null) {
+      v = xbar_or_null[i];
+    } else {
+      const double xi = s.x[i], di = dir[i];
+      if (same_bits(xi, tau) && is_zero_bits(di)) continue;  // stays at tau
+      v = xi + al * di;
+    }
+    if (!same_bits(v, tau) && v - tau <= eps) v = tau;
     s.x[i] = v;
   }
   __syncthreads();
@@ -900,22 +941,28 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
   const int n = s.n;
   const double tau = SD[SD_TAU], eta = SD[SD_ETA];
   ls_coefficients(s, s.spart, G, s.d, coef, scr, ps);
-  // The exact step on [0, eta] (one thread; read after the reductions below).
-  if (threadIdx.x == 0) s_eq = quartic_argmin(coef, eta);
+  // The exact step on [0, eta] (warp 0; read after the reductions below).
+  if (threadIdx.x < 32) {
+    const double v = quartic_argmin_w(coef, eta);
+    if (threadIdx.x == 0) s_eq = v;
+  }
   // alpha_max = min over d_i < 0 of (x_i - tau) / (-d_i), exactly rounded: FP32
   // ratios screen the candidates within 1e-5 of their minimum, and only those
   // take the FP64 division (tens of FP64-pipe operations each on this part).
   // (Ratios beyond the FP32 range count as +inf.)
   float am32 = INFINITY;
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    if (s.d[i] < 0.0) am32 = fminf(am32, (float)(s.x[i] - tau) / (float)(-s.d[i]));
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double di = s.d[i];
+    if (neg_bits(di)) am32 = fminf(am32, (float)(s.x[i] - tau) / (float)(-di));
+  }
   am32 = (float)block_min((double)am32, scr);
   double am = INFINITY;
   if (am32 < INFINITY) {
     const float thr = am32 * (1.0f + 1e-5f);
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-      if (s.d[i] < 0.0 && (float)(s.x[i] - tau) / (float)(-s.d[i]) <= thr)
-        am = fmin(am, (s.x[i] - tau) / (-s.d[i]));
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double di = s.d[i];
+      if (neg_bits(di) && (float)(s.x[i] - tau) / (float)(-di) <= thr) am = fmin(am, (s.x[i] - tau) / (-di));
+    }
     am = block_min(am, scr);
   }
   double eta_k = fmin(eta, s_eq);
@@ -958,10 +1005,14 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
         const int i = threadIdx.x + e * kVT;
         if (i < n) {
           const int c = gt_screen(uf[e], thf);
-          const double xb = (c > 0 || (c < 0 && uu[e] > th)) ? tau + (uu[e] - th) : tau;
-          const double db = xb - s.x[i];
-          gd += s.g[i] * db;
-          dd += db * db;
+          const bool above = c > 0 || (c < 0 && uu[e] > th);
+          const double xi = s.x[i];
+          if (above || !same_bits(xi, tau)) {  // else xb = x = tau: no term
+            const double xb = above ? tau + (uu[e] - th) : tau;
+            const double db = xb - xi;
+            gd += s.g[i] * db;
+            dd += db * db;
+          }
         }
       }
     }

@@ -226,11 +226,59 @@ __device__ __forceinline__ Sum2c block_sum2c_fin(double a, double b, int k, doub
   return {scr[64], scr[65], scr[66], scr[67], (int)scr[68]};
 }
 
-// u > th decided in FP32 from uf = (float)u and thf = (float)th: 1 or 0 when
-// the FP32 values settle it, -1 when the FP64 compare must.  Conversions
-// round to nearest (relative error <= 2^-24 in the normal range, absolute
-// <= 2^-149 below it), so a gap of 1e-6 (|uf| + |thf|) + 1e-30 leaves a
-// margin of more than 10x over both conversions and the FP32 sum.
+// Bit tests and conversions on the integer pipe.  The FP64 pipe of this part
+// runs about 2 operations/clk/SM, and most coordinates of a working face sit
+// at tau with a zero direction, so exact integer tests on the bits let the
+// per-instance passes skip their FP64 arithmetic there.
+__device__ __forceinline__ bool is_zero_bits(double v) { return (__double_as_longlong(v) << 1) == 0; }
+__device__ __forceinline__ bool same_bits(double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b); }
+// v < 0 and nonzero (a negative NaN also passes; callers then see a NaN ratio)
+__device__ __forceinline__ bool neg_bits(double v) {
+  const long long b = __double_as_longlong(v);
+  return b < 0 && (b << 1) != 0;
+}
+// Order-preserving integer key of a non-NaN double (-0 sorts below +0).
+__device__ __forceinline__ long long dkey(double v) {
+  const long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+// (float)v truncated toward zero (relative error < 2^-23; 0 below 2^-126,
+// +-inf above the FP32 range, NaN kept), by integer operations: a screening
+// value, not a rounding.
+__device__ __forceinline__ float f32_trunc(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (unsigned)((b >> 29) & 0x7FFFFFu) | ((b << 12) != 0 ? 1u : 0u));
+  const int fe = E - 896;  // FP32 biased exponent
+  if (fe <= 0) return __uint_as_float(sign);
+  if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+}
+
+// The double of a finite FP32 value, by integer operations (exact).
+__device__ __forceinline__ double f64_from_f32(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  int E = (int)((b >> 23) & 0xFF);
+  unsigned long long m = b & 0x7FFFFFu;
+  if (E == 0) {
+    if (m == 0) return __longlong_as_double((long long)sign);
+    while ((m & 0x800000u) == 0) {  // subnormal: normalise
+      m <<= 1;
+      --E;
+    }
+    m &= 0x7FFFFFu;
+    ++E;
+  }
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(E + 896) << 52) | (m << 29)));
+}
+
+// u > th decided in FP32 from uf and thf, FP32 values of u and th within a
+// relative 2^-23 (f32_trunc or a rounding) or an absolute 2^-126: 1 or 0 when
+// the FP32 values settle it, -1 when the FP64 compare must.  A gap of 1e-6
+// (|uf| + |thf|) + 1e-30 leaves a margin of more than 5x over both errors and
+// the FP32 arithmetic of the test.
 __device__ __forceinline__ int gt_screen(float uf, float thf) {
   if (!(fabsf(uf) < 1e30f) || !(fabsf(thf) < 1e30f)) return -1;
   const float gap = 1e-6f * (fabsf(uf) + fabsf(thf)) + 1e-30f;
@@ -265,7 +313,9 @@ inline __device__ double slice_theta_mem(const double* base, const double* dir, 
 // (float)u_i of coordinate i = threadIdx.x + e blockDim.x (0 beyond n).
 __device__ __forceinline__ double slice_theta_r(const double* base, const double* dir, double s, int n, double tau,
                                                 double* scr, double* u, double (&uu)[kSliceE], float (&uf)[kSliceE]) {
-  const double b = 1.0 - (double)n * tau;
+  // Scalar FP64 arithmetic runs only on the thread that completes each
+  // reduction (its fin): on this part a uniform FP64 operation executed by
+  // every thread of the block costs as much as one per coordinate.
   unsigned all = 0;
   double su = 0.0;
   float sabs = 0.f;
@@ -274,21 +324,32 @@ __device__ __forceinline__ double slice_theta_r(const double* base, const double
     const int i = threadIdx.x + e * blockDim.x;
     double ui = 0.0;
     if (i < n) {
-      ui = (dir ? base[i] + s * dir[i] : base[i]) - tau;
+      const double bi = base[i];
+      // base tau with a zero direction gives u = +0 exactly (tau + s*0 = tau)
+      if (!(same_bits(bi, tau) && (dir == nullptr || is_zero_bits(dir[i])))) {
+        ui = (dir ? bi + s * dir[i] : bi) - tau;
+        su += ui;
+      }
       if (u) u[i] = ui;
-      su += ui;
       all |= 1u << e;
     }
     uu[e] = ui;
-    uf[e] = (float)ui;
+    uf[e] = f32_trunc(ui);
     sabs += fabsf(uf[e]);
   }
-  const double4 r0 = block_sum2_fin(su, (double)sabs, scr,
-                                    [=](double x, double) { return make_double2((x - b) / (double)n, 0.0); });
+  const double4 r0 = block_sum2_fin(su, (double)sabs, scr, [=](double x, double y) {
+    const double b = 1.0 - (double)n * tau;
+    // Michelot's mean start; its FP32 value and the mean |u| as bit patterns
+    const double tm = (x - b) / (double)n;
+    return make_double2(tm, __longlong_as_double(((long long)__float_as_int((float)tm) << 32) |
+                                                 (unsigned)__float_as_int((float)(y / (double)n))));
+  });
   const double theta_mean = r0.z;
+  const long long pk = __double_as_longlong(r0.w);
   // FP32 pass: an estimate of the root and the scale of its error
-  float thf = (float)theta_mean;
-  double scale = r0.y / (double)n;  // mean |u| over the current set
+  float thf = __int_as_float((int)(pk >> 32));
+  float scale = __int_as_float((int)(pk & 0xFFFFFFFFll));  // mean |u| over the current set
+  const float bf = 1.f - (float)n * f32_trunc(tau);
   {
     unsigned in = all;
     int cnt = n;
@@ -309,18 +370,23 @@ __device__ __forceinline__ double slice_theta_r(const double* base, const double
       const int k = (int)r.z;
       if (k == cnt || k == 0) break;
       cnt = k;
-      thf = (r.x - (float)b) / r.z;
-      scale = (double)(r.y / r.z);
+      thf = (r.x - bf) / r.z;
+      scale = r.y / r.z;
     }
   }
-  // FP64 pass from just below the estimate
-  double th = (double)thf - 1e-4 * (fabs((double)thf) + scale);
-  if (!(th > theta_mean)) th = theta_mean;
+  // FP64 pass from just below the estimate (start formed in FP32 and widened
+  // exactly; never below the mean start, which always qualifies)
+  const float t0 = thf - 1e-4f * (fabsf(thf) + scale);
+  double th = theta_mean;
+  if (fabsf(t0) < 1e30f) {
+    const double t0d = f64_from_f32(t0);
+    if (dkey(t0d) > dkey(theta_mean)) th = t0d;
+  }
   unsigned in = all;
   int cnt = -1;
   bool first = true;
   for (int it = 0; it <= n + 1; ++it) {
-    const float tf = (float)th;
+    const float tf = f32_trunc(th);
     double sa = 0.0;
     int ka = 0;
     unsigned nin = 0;
@@ -335,13 +401,18 @@ __device__ __forceinline__ double slice_theta_r(const double* base, const double
         }
       }
     const double thc = th;
+    const bool fst = first;
     const Sum2c r = block_sum2c_fin(sa, 0.0, ka, scr, [=](double x, double, int k) {
-      // next iterate; phi(th) = sum_{u > th} (u - th) - b >= 0 (th at or below the root)
-      return make_double2(k > 0 ? (x - b) / (double)k : 0.0, (x - (double)k * thc - b) >= 0.0 ? 1.0 : 0.0);
+      // next iterate, and on the first step of a start above the mean start
+      // whether phi(th) = sum_{u > th} (u - th) - b < 0 (th above the root):
+      // then w = 1 and the iteration restarts from the mean start
+      const double b = 1.0 - (double)n * tau;
+      const bool restart = fst && thc > theta_mean && !((x - (double)k * thc - b) >= 0.0);
+      return make_double2(k > 0 ? (x - b) / (double)k : 0.0, restart ? 1.0 : 0.0);
     });
     if (first) {
       first = false;
-      if (r.w == 0.0 && th > theta_mean) {  // started above the root: restart from the mean start
+      if (!is_zero_bits(r.w)) {
         th = theta_mean;
         in = all;
         first = true;
@@ -415,16 +486,21 @@ inline __device__ double2 kkt_residual_rel(const double* x, const double* g, int
     double uu[kSliceE];
     float uf[kSliceE];
     const double th = slice_theta_r(x, g, -1.0, n, tau, scr, tmp, uu, uf);
-    const float thf = (float)th;
+    const float thf = f32_trunc(th);
 #pragma unroll
     for (int e = 0; e < kSliceE; ++e) {
       const int i = threadIdx.x + e * blockDim.x;
       if (i < n) {
-        // p = tau + max(u - theta, 0): u - theta > 0 exactly when u > theta
+        // p = tau + max(u - theta, 0): u - theta > 0 exactly when u > theta;
+        // x - p is exactly 0 for x = p = tau
         const int c = gt_screen(uf[e], thf);
-        const double p = (c > 0 || (c < 0 && uu[e] > th)) ? tau + (uu[e] - th) : tau;
-        const double d = x[i] - p;
-        s += d * d;
+        const bool above = c > 0 || (c < 0 && uu[e] > th);
+        const double xi = x[i];
+        if (above || !same_bits(xi, tau)) {
+          const double p = above ? tau + (uu[e] - th) : tau;
+          const double d = xi - p;
+          s += d * d;
+        }
       }
     }
   }
@@ -447,70 +523,55 @@ __device__ __forceinline__ double decrease(const double* c, double a) {
   return a * (c[1] + a * (c[2] + a * (c[3] + a * c[4])));
 }
 
-// Minimiser of A0 + A1 a + ... + A4 a^4 on [0, amax] (Prop. quartic exact line
-// search): candidates 0, amax and the real roots of phi' in (0, amax).  The
-// real roots of phi'' (cancellation-free quadratic formula) split the interval
-// into pieces on which phi' is monotone; a sign change brackets one root, found
-// by bisection down to adjacent doubles.  Ties keep the smallest alpha.
-__device__ __forceinline__ double ddphi(const double* c, double a) {
-  return (12.0 * c[4] * a + 6.0 * c[3]) * a + 2.0 * c[2];
-}
-
-// The root of phi' in [lo, hi], where phi' is monotone and changes sign
-// (flo = phi'(lo) != 0).  The FP64 pipe of this part runs about 2 FMA/clk/SM
-// (a warp-wide FP64 instruction occupies it for ~64 cycles, whatever the
-// active lanes), so plain bisection to adjacent doubles (~60 dependent
-// steps) costs tens of microseconds on the one thread that runs it.  Here:
-// (1) the cubic q(t) = phi'(lo + t w), w = hi - lo, is rescaled by a power of
-// two to coefficients of magnitude <= 1 and bisected in FP32 on [0, 1] to
-// 2^-20; (2) FP64 Newton steps on phi' from that start, each kept inside the
-// FP64 bracket [a, b] (updated from the sign of phi' at every iterate; a step
-// leaving it is replaced by the midpoint), until a step is below 4 ulps.  A
-// simple root converges in two or three steps.  At most 80 steps in all,
-// ending, like bisection, at the midpoint of adjacent doubles.  The result
-// lies within a few ulps of the root; the decrease phi(alpha) - phi(0) then
-// agrees with that of the exact root to rounding, being stationary there.
-__device__ __forceinline__ double dphi_root(const double* c, double lo, double hi, double flo) {
-  const double w = hi - lo;
-  // q(t) = d0 + d1 t + d2 t^2 + d3 t^3 (Taylor expansion of phi' at lo)
-  const double d0 = flo, d1 = ddphi(c, lo) * w, d2 = (3.0 * c[3] + 12.0 * c[4] * lo) * w * w,
-               d3 = 4.0 * c[4] * w * w * w;
-  const double dm = fmax(fmax(fabs(d0), fabs(d1)), fmax(fabs(d2), fabs(d3)));
-  int ex = 0;
-  frexp(dm, &ex);
-  const float e0 = (float)ldexp(d0, -ex), e1 = (float)ldexp(d1, -ex), e2 = (float)ldexp(d2, -ex),
-              e3 = (float)ldexp(d3, -ex);
-  float ta = 0.f, tb = 1.f;
+// The root of phi' in [lo, hi] (0 <= lo < hi) where phi' is monotone and
+// changes sign (flo = phi'(lo) != 0), to adjacent doubles, by the 32 lanes of
+// one warp (every lane calls; all return the same value).  Non-negative
+// doubles are ordered like their bit patterns, so the bracket is searched in
+// integer space: each round evaluates phi' at 31 points spaced evenly in the
+// bit patterns strictly inside the bracket and keeps the sub-bracket where
+// the sign changes (five bits per round, <= 13 rounds).  On this part a lone
+// thread's dependent FP64 operation takes about as long as a whole warp's
+// (the FP64 pipe is ~2 operations/clk/SM), so the 31 evaluations of a round
+// cost about one bisection step.  Like bisection it ends at the midpoint of
+// adjacent doubles bracketing the sign change (or at an exact zero of phi',
+// the smallest one evaluated).
+__device__ __forceinline__ double dphi_root_w(const double* c, double lo, double hi, double flo) {
+  const int lane = threadIdx.x & 31;
   const bool neg = flo < 0.0;
-  for (int it = 0; it < 20; ++it) {
-    const float tm = 0.5f * (ta + tb);
-    const float q = fmaf(fmaf(fmaf(e3, tm, e2), tm, e1), tm, e0);
-    if (q == 0.f) {
-      ta = tb = tm;
-      break;
-    }
-    if ((q < 0.f) == neg) ta = tm; else tb = tm;
+  unsigned long long ia = (unsigned long long)__double_as_longlong(lo), ib = (unsigned long long)__double_as_longlong(hi);
+  for (int it = 0; it < 16 && ib - ia > 1ull; ++it) {
+    const unsigned long long span = ib - ia;
+    // point j (j < 31): ia + floor(span (j + 1) / 32), without overflow
+    auto point = [&](int j) -> unsigned long long {
+      const unsigned long long q = (unsigned long long)(j + 1);
+      return ia + (span >> 5) * q + (((span & 31ull) * q) >> 5);
+    };
+    const unsigned long long ij = point(lane);
+    const bool valid = lane < 31 && ij > ia && ij < ib;
+    const double x = __longlong_as_double((long long)ij);
+    const double f = valid ? dphi(c, x) : 1.0;
+    const unsigned zero = __ballot_sync(0xffffffffu, valid && f == 0.0);
+    if (zero != 0u) return __shfl_sync(0xffffffffu, x, __ffs(zero) - 1);
+    const unsigned los = __ballot_sync(0xffffffffu, valid && ((f < 0.0) == neg));
+    const unsigned his = __ballot_sync(0xffffffffu, valid && !((f < 0.0) == neg));
+    const int kh = his != 0u ? __ffs(his) - 1 : 31;  // first point on the side of hi
+    const unsigned below = kh >= 31 ? los : (los & ((1u << kh) - 1u));
+    const unsigned long long nb = kh < 31 ? point(kh) : ib;
+    if (below != 0u) ia = point(31 - __clz(below));  // last point on the side of lo before it
+    ib = nb;
   }
-  double a = lo, b = hi;
-  double x = lo + (double)(0.5f * (ta + tb)) * w;
-  if (!(x > a && x < b)) x = 0.5 * (a + b);
-  for (int it = 0; it < 80; ++it) {
-    const double f = dphi(c, x);
-    if (f == 0.0) return x;
-    if ((f < 0.0) == neg) a = x; else b = x;
-    const double m = 0.5 * (a + b);
-    if (m <= a || m >= b) break;  // adjacent doubles
-    const double fp = ddphi(c, x);
-    double xn = x - f / fp;
-    if (!(xn > a && xn < b)) xn = m;  // also NaN (fp = 0)
-    const double step = fabs(xn - x);
-    x = xn;
-    if (step <= 8.9e-16 * fabs(x)) return x;  // below 4 ulps
-  }
+  const double a = __longlong_as_double((long long)ia), b = __longlong_as_double((long long)ib);
   return (a != b) ? 0.5 * (a + b) : a;
 }
 
-inline __device__ double quartic_argmin(const double* c, double amax) {
+// Minimiser of A0 + A1 a + ... + A4 a^4 on [0, amax] (Prop. quartic exact line
+// search): candidates 0, amax and the real roots of phi' in (0, amax).  The
+// real roots of phi'' (cancellation-free quadratic formula) split the interval
+// into pieces on which phi' is monotone; a sign change brackets one root,
+// found to adjacent doubles (dphi_root_w).  Ties keep the smallest alpha.
+// Warp-cooperative: every lane of one warp calls with the same arguments and
+// receives the result.
+inline __device__ double quartic_argmin_w(const double* c, double amax) {
   if (!(amax > 0.0)) return 0.0;
   double brk[4];
   int nb = 0;
@@ -547,7 +608,7 @@ inline __device__ double quartic_argmin(const double* c, double amax) {
     if (flo == 0.0) { cand[nc++] = lo; continue; }
     if (fhi == 0.0) { cand[nc++] = hi; continue; }
     if ((flo < 0.0) == (fhi < 0.0)) continue;
-    cand[nc++] = dphi_root(c, lo, hi, flo);
+    cand[nc++] = dphi_root_w(c, lo, hi, flo);
   }
   // sort ascending (tiny insertion sort), then keep the first strict minimum
   for (int i = 1; i < nc; ++i) {
@@ -569,28 +630,35 @@ inline __device__ double quartic_argmin(const double* c, double amax) {
 
 // Armijo backtracking on the same quartic (the paper's Armijo diagnostic,
 // Table yand-line-search): the largest alpha = amax 2^-j, j < 60, with
-// phi(alpha) - phi(0) <= 1e-4 alpha phi'(0); 0 when phi'(0) >= 0.
-inline __device__ double armijo_step(const double* c, double amax) {
+// phi(alpha) - phi(0) <= 1e-4 alpha phi'(0); 0 when phi'(0) >= 0.  Lane j of
+// the warp tests j and j + 32 (amax 2^-j formed by ldexp: the repeated
+// halving, exactly, while it stays in the normal range).  Warp-cooperative.
+inline __device__ double armijo_step_w(const double* c, double amax) {
   if (!(amax > 0.0) || !(c[1] < 0.0)) return 0.0;
-  double a = amax;
-  for (int j = 0; j < 60; ++j) {
-    if (decrease(c, a) <= 1e-4 * a * c[1]) return a;
-    a *= 0.5;
+  const int lane = threadIdx.x & 31;
+  for (int j0 = 0; j0 < 60; j0 += 32) {
+    const int j = j0 + lane;
+    const double a = ldexp(amax, -j);
+    const unsigned ok = __ballot_sync(0xffffffffu, j < 60 && decrease(c, a) <= 1e-4 * a * c[1]);
+    if (ok != 0u) return ldexp(amax, -(j0 + __ffs(ok) - 1));
   }
   return 0.0;
 }
 
-// Step along a direction on [0, amax] by rule (SI_LSRULE).
-inline __device__ double line_step(const double* c, double amax, int rule) {
-  return rule == 1 ? armijo_step(c, amax) : quartic_argmin(c, amax);
+// Step along a direction on [0, amax] by rule (SI_LSRULE); warp-cooperative.
+inline __device__ double line_step_w(const double* c, double amax, int rule) {
+  return rule == 1 ? armijo_step_w(c, amax) : quartic_argmin_w(c, amax);
 }
 
-// line_step evaluated by thread 0 and broadcast through the shared *slot: the
-// bisection is a few hundred dependent FP64 operations, which every warp of
-// the block would otherwise repeat on the FP64 pipe.  Block-uniform call.
+// line_step_w by warp 0, broadcast through the shared *slot (the search is a
+// chain of dependent FP64 operations, which every warp of the block would
+// otherwise repeat on the FP64 pipe).  Block-uniform call.
 inline __device__ double block_line_step(const double* c, double amax, int rule, double* slot) {
   __syncthreads();
-  if (threadIdx.x == 0) *slot = line_step(c, amax, rule);
+  if (threadIdx.x < 32) {
+    const double v = line_step_w(c, amax, rule);
+    if (threadIdx.x == 0) *slot = v;
+  }
   __syncthreads();
   return *slot;
 }
