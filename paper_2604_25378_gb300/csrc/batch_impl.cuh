@@ -209,8 +209,10 @@ __global__ void k_oz_fin_g(const long long* part, int splits, int Bp, long long 
 // kinfo[1]; its slot count is then oz_slots(kinfo[1] / 64).
 __global__ void __launch_bounds__(256) k_oz_fin_ls(const long long* part, int splits, int Bp, long long ldp,
                                                    const int* em, const int* fb, Inst base, int b0, int skip_slot,
-                                                   double* wout, const int* kinfo = nullptr) {
+                                                   double* wout, const int* kinfo = nullptr,
+                                                   const int* need = nullptr) {
   __shared__ double red[12][256];
+  if (need != nullptr && *need == 0) return;  // the product did not run
   const int bl = blockIdx.y;
   if (kinfo != nullptr) splits = oz_slots(kinfo[1] / kTcBK);
   Inst s = inst_at(base, b0 + bl);
@@ -295,15 +297,24 @@ __global__ void k_dpsi_into(const double* z, long long T, double c2, double c3, 
   if (t < T) w[t] = Psi{c2, c3, c4}.d1(z[t]);
 }
 
-// need = 1 when some running instance takes the projected segment (second line search).
-__global__ void k_need_ls2(Inst base, int B, int* need) {
-  int any = 0;
+// Second line-search product, over the running instances that take the
+// projected segment (SKIPLS == 0): need[0] = 1 when it runs on all columns of
+// A, need[1] = 1 when it runs on the union of the working faces (umode, and
+// every such segment vanishes off the union: SI_LS2OUT == 0).
+__global__ void k_need_ls2(Inst base, int B, int* need, int umode) {
+  int any = 0, out = 0;
   for (int b = threadIdx.x; b < B; b += blockDim.x) {
     const int* si = base.si + (size_t)b * kSI;
-    any |= (si[SI_DONE] == 0 && si[SI_SKIPLS] == 0);
+    const int take = si[SI_DONE] == 0 && si[SI_SKIPLS] == 0;
+    any |= take;
+    out |= take && (umode == 0 || si[SI_LS2OUT] != 0);
   }
   any = __syncthreads_or(any);
-  if (threadIdx.x == 0) *need = any;
+  out = __syncthreads_or(out);
+  if (threadIdx.x == 0) {
+    need[0] = out;
+    need[1] = any && !out;
+  }
 }
 
 // ------------------------------------- diagonal and nu-products (tensor cores)
@@ -557,7 +568,9 @@ __global__ void k_transpose_u_bf16(const __nv_bfloat16* __restrict__ srcT, long 
 
 // dst[b * ldd + j] = V[b * vs + idx[j]] for j < |U|, zero for |U| <= j < ldd
 // (the right-hand vectors of a split product restricted to U).  Grid (x, B).
-__global__ void k_gather_vec_u(const double* V, long long vs, const int* idx, const int* info, double* dst, int ldd) {
+__global__ void k_gather_vec_u(const double* V, long long vs, const int* idx, const int* info, double* dst, int ldd,
+                               const int* need = nullptr) {
+  if (need != nullptr && *need == 0) return;
   const int b = blockIdx.y, ku = info[0];
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ldd; j += gridDim.x * blockDim.x)
     dst[(size_t)b * ldd + j] = j < ku ? V[(size_t)b * vs + idx[j]] : 0.0;
@@ -665,7 +678,7 @@ mvsk_status batch_alloc(mvsk_ctx* c, BatchBuf& bb, int B) {
   bb.part = (float*)p;
   TRY(get(sizeof(double) * T * Bs, &p));
   bb.Wt = (double*)p;
-  TRY(get(sizeof(int), &p));
+  TRY(get(sizeof(int) * 4, &p));
   bb.need = (int*)p;
   TRY(get(sizeof(double) * ld * Bs, &p));
   bb.G0 = (double*)p;
@@ -1245,20 +1258,27 @@ mvsk_status batch_iteration_tail(mvsk_ctx* c, BatchBuf& bb, int B, const std::ve
       int sp = 0;
       TRY(oz_product(c, 0, dvec + (size_t)b0 * base.vs, base.vs, nb, oz_bp(nb), need, &sp));
       PROF_LAUNCH(NK_OZ_LS, (k_oz_fin_ls<<<dim3(Gl, nb), 256, 0, c->stream>>>(oz.part, sp, oz_bp(nb), oz.MpF, oz.eF,
-                                                                             oz.fF, base, b0, skip_slot, bb.wls)));
+                                                                             oz.fF, base, b0, skip_slot, bb.wls,
+                                                                             nullptr, need)));
     }
     return MVSK_OK;
   };
-  if (split && bb.umode && bb.u_AFU != nullptr) {  // d is zero off the faces: A d on the union
+  const bool uls = split && bb.umode && bb.u_AFU != nullptr;
+  // A v on the union of the faces for B vectors v (zero off the union), gated by need (nullable)
+  auto ls_union = [&](double* dvec, int skip_slot, const int* need) -> mvsk_status {
     for (int b0 = 0; b0 < B; b0 += kOzMaxB) {
       const int nb = B - b0 < kOzMaxB ? B - b0 : kOzMaxB;
       PROF_LAUNCH(NK_OZ_SPLIT, (k_gather_vec_u<<<dim3((unsigned)((c->ld + 255) / 256), nb), 256, 0, c->stream>>>(
-                                   base.d + (size_t)b0 * base.vs, base.vs, bb.u_idx, bb.u_info, bb.u_DU, c->ld)));
-      TRY(oz_product_u(c, bb.u_DU, nb, oz_bp(nb), bb.u_AFU, bb.u_info));
+                                   dvec + (size_t)b0 * base.vs, base.vs, bb.u_idx, bb.u_info, bb.u_DU, c->ld, need)));
+      TRY(oz_product_u(c, bb.u_DU, nb, oz_bp(nb), bb.u_AFU, bb.u_info, need));
       PROF_LAUNCH(NK_OZ_LS, (k_oz_fin_ls<<<dim3(Gl, nb), 256, 0, c->stream>>>(oz.part, 0, oz_bp(nb), oz.MpF, oz.eF,
-                                                                             oz.fF, base, b0, SI_DONE, bb.wls,
-                                                                             bb.u_info)));
+                                                                             oz.fF, base, b0, skip_slot, bb.wls,
+                                                                             bb.u_info, need)));
     }
+    return MVSK_OK;
+  };
+  if (uls) {  // d is zero off the faces: A d on the union
+    TRY(ls_union(base.d, SI_DONE, nullptr));
   } else if (split) {
     TRY(ls_split(base.d, SI_DONE, nullptr));
   } else {
@@ -1271,11 +1291,14 @@ mvsk_status batch_iteration_tail(mvsk_ctx* c, BatchBuf& bb, int B, const std::ve
       TRY(run_pass(c, P64, M_LS, 1, a, nullptr, s.spart));
     }
   }
-  PROF_LAUNCH(NK_DECIDE1, (k_decide1<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gl)));
+  PROF_LAUNCH(NK_DECIDE1, (k_decide1<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gl, uls ? bb.u_pos : nullptr)));
   if (split) PROF_LAUNCH(NK_ZSTEP, (k_z_step<<<dim3(Gz, B), 256, 0, c->stream>>>(base, bb.wls, 1)));
   if (split) {
-    PROF_LAUNCH(NK_NEED, (k_need_ls2<<<1, 64, 0, c->stream>>>(base, B, bb.need)));
+    // the segment: on the union of the faces when every taken one vanishes
+    // off it (checked exactly by k_decide1), else on all columns
+    PROF_LAUNCH(NK_NEED, (k_need_ls2<<<1, 64, 0, c->stream>>>(base, B, bb.need, uls ? 1 : 0)));
     TRY(ls_split(base.dstep, SI_SKIPLS, bb.need));
+    if (uls) TRY(ls_union(base.dstep, SI_SKIPLS, bb.need + 1));
   } else {
     for (int b = 0; b < B; ++b) {
       const Inst s = inst_at(base, b);

@@ -418,8 +418,9 @@ PassArgs pass_args(mvsk_ctx* c) {
 }
 
 // Profiling: kind ids 0..383 are streaming passes ((prec*16 + mode)*8 + nin);
-// 400 + bn are tensor-core products with N tile bn; 680/681 the split FP64
-// products; 700 + i the named kernels of kKernelNames.
+// 400 + bn are tensor-core products with N tile bn; 680..685 the split FP64
+// products (A V, A^T V, the same gated by a device flag, A V on the union of
+// the faces, the same gated); 700 + i the named kernels of kKernelNames.
 constexpr int kProfKinds = 760;
 constexpr int kKindNamed = 700;
 const char* const kKernelNames[] = {"k_face", "k_probe_fill", "k_pcg_setup", "k_pcg_step", "k_cols_bf16_b",
@@ -1011,7 +1012,7 @@ mvsk_status launch_iteration(mvsk_ctx* c, int cfg) {
   c->launches += 5;  // k_face, k_decide1, k_decide2, k_end_iter (+1 below)
   TRY(direction(c, cfg));
   TRY(pass_ls(c, s.d, done));
-  k_decide1<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid);
+  k_decide1<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid, nullptr);
   CU(cudaGetLastError());
   TRY(pass_ls(c, s.dstep, s.si + SI_SKIPLS));
   k_decide2<<<1, kVT, 0, c->stream>>>(s, c->spart, c->grid);
@@ -1743,8 +1744,8 @@ static void kind_name(int kind, char* out, size_t len) {
     snprintf(out, len, "gemm_tc_bf16_n%d", kind - 400);
   else if (kind >= 680 && kind <= 683)
     snprintf(out, len, "oz_gemm_%s%s", (kind & 1) ? "bwd" : "fwd", kind >= 682 ? "_gated" : "");
-  else if (kind == 684)
-    snprintf(out, len, "oz_gemm_fwd_u");
+  else if (kind == 684 || kind == 685)
+    snprintf(out, len, "oz_gemm_fwd_u%s", kind == 685 ? "_gated" : "");
   else if (kind >= kKindNamed && kind < kKindNamed + NK_COUNT)
     snprintf(out, len, "%s", kKernelNames[kind - kKindNamed]);
   else

@@ -115,16 +115,17 @@ mvsk_status oz_product(mvsk_ctx* c, int trans, const double* V, long long vstrid
 // planes (k_oz_split_rows_u, padded count info[1]); V holds B vectors of ld
 // values in list coordinates (zero beyond the list).  Partials in c->oz.part
 // as from oz_product (ld Mp), slot count oz_slots(info[1] / 64), read by the
-// finishing kernel from info.
-mvsk_status oz_product_u(mvsk_ctx* c, const double* V, int B, int Bp, const __nv_bfloat16* AU, const int* info) {
+// finishing kernel from info.  need: device flag (nullable) as in oz_product.
+mvsk_status oz_product_u(mvsk_ctx* c, const double* V, int B, int Bp, const __nv_bfloat16* AU, const int* info,
+                         const int* need) {
   TRY(oz_prepare(c, Bp));
   OzBuf& o = c->oz;
   const int K = c->ld;
   CU(cudaMemsetAsync(o.fF, 0x80, sizeof(int) * Bp, c->stream));  // kOzNoExp
   PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_vec_exp<<<dim3((unsigned)((K + 1023) / 1024), Bp), 256, 0, c->stream>>>(
-                               V, c->ld, B, K, o.fF, nullptr)));
+                               V, c->ld, B, K, o.fF, need)));
   PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_vec_digits<<<dim3((unsigned)((K + 255) / 256), Bp), 256, 0, c->stream>>>(
-                               V, c->ld, B, Bp, K, c->ld, o.fF, o.XF, nullptr)));
+                               V, c->ld, B, Bp, K, c->ld, o.fF, o.XF, need)));
   // the grid and the zeroed slots cover every column; the kernel takes its
   // k-extent from info[1] (CTAs without units return)
   const int nkb = K / kTcBK;
@@ -132,25 +133,26 @@ mvsk_status oz_product_u(mvsk_ctx* c, const double* V, int B, int Bp, const __nv
   const unsigned grid = (unsigned)(units < c->nsm ? units : c->nsm);
   const long long zn = (long long)oz_slots(nkb) * Bp * o.MpF;
   PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_zero<<<(unsigned)((zn + 1023) / 1024 < 4 * c->nsm ? (zn + 1023) / 1024 : 4 * c->nsm),
-                                        256, 0, c->stream>>>(o.part, zn, nullptr)));
+                                        256, 0, c->stream>>>(o.part, zn, need)));
   // work per unit of the padded list length: 28 digit products of Mp x Bp
-  TRY(prof_begin_u(c, kKindOz + 4, 2.0 * (double)o.MpF * Bp * (kOzS * (kOzS + 1) / 2)));
+  TRY(prof_begin_u(c, need != nullptr ? kKindOz + 5 : kKindOz + 4,
+                   2.0 * (double)o.MpF * Bp * (kOzS * (kOzS + 1) / 2)));
   switch (Bp) {
     case 16:
       k_oz_gemm<16><<<grid, kOzThreads, oz_smem_bytes(16), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part,
-                                                                         o.MpF, c->err, nullptr, info);
+                                                                         o.MpF, c->err, need, info);
       break;
     case 32:
       k_oz_gemm<32><<<grid, kOzThreads, oz_smem_bytes(32), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part,
-                                                                         o.MpF, c->err, nullptr, info);
+                                                                         o.MpF, c->err, need, info);
       break;
     case 48:
       k_oz_gemm<48><<<grid, kOzThreads, oz_smem_bytes(48), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part,
-                                                                         o.MpF, c->err, nullptr, info);
+                                                                         o.MpF, c->err, need, info);
       break;
     default:
       k_oz_gemm<64><<<grid, kOzThreads, oz_smem_bytes(64), c->stream>>>(AU, o.tmXF, o.MpF, c->T, K, K / 64, o.part,
-                                                                         o.MpF, c->err, nullptr, info);
+                                                                         o.MpF, c->err, need, info);
       break;
   }
   CU(cudaGetLastError());

@@ -929,7 +929,10 @@ inline __device__ void take_step(Inst& s, const double* dir, double al, const do
 
 // After the line-search pass along d: alpha_max, the damped nominal step
 // eta_k, and the branch of the boundary block (App. C.3).
-static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* spart, int G) {
+// upos (nullable): positions of the coordinates in the union of the working
+// faces of a lockstep batch (-1 outside); SI_LS2OUT then records whether the
+// segment dstep of a taken projection has entries outside it (else 1).
+static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* spart, int G, const int* upos) {
   Inst s = inst_at(s0, blockIdx.y);
   __shared__ double scr[80];
   __shared__ double ps[16];
@@ -1024,12 +1027,17 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
   }
   if (threadIdx.x == 0) SD[SD_ETAK] = eta_k;
   if (descent) {  // u and th still hold the accepted trial
+    int out = 0;
     for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
       const double xb = i < n ? tau + fmax(u[i] - th, 0.0) : 0.0;
       s.xbar[i] = xb;
-      s.dstep[i] = i < n ? xb - s.x[i] : 0.0;
+      const double db = i < n ? xb - s.x[i] : 0.0;
+      s.dstep[i] = db;
+      out |= (upos == nullptr || upos[i] < 0) && !is_zero_bits(db);
     }
+    out = __syncthreads_or(out);
     if (threadIdx.x == 0) {
+      SI[SI_LS2OUT] = (upos == nullptr || out) ? 1 : 0;
       SI[SI_BRANCH] = BR_SEGMENT;
       SI[SI_BR_SEG] += 1;
       SI[SI_SKIPLS] = 0;
@@ -1056,15 +1064,19 @@ static __global__ void __launch_bounds__(kVT) k_decide1(Inst s0, const double* s
   __syncthreads();
   th = slice_theta(s.x, s.tmp, sc, n, tau, scr, u);
   double gd = 0.0;
+  int out = 0;
   for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
     const double xb = i < n ? tau + fmax(u[i] - th, 0.0) : 0.0;
     s.xbar[i] = xb;
     const double db = i < n ? xb - s.x[i] : 0.0;
     s.dstep[i] = db;
     if (i < n) gd += s.g[i] * db;
+    out |= (upos == nullptr || upos[i] < 0) && !is_zero_bits(db);
   }
+  out = __syncthreads_or(out);
   gd = block_sum2(gd, 0.0, scr).x;
   if (threadIdx.x == 0) {
+    SI[SI_LS2OUT] = (upos == nullptr || out) ? 1 : 0;
     SI[SI_BRANCH] = BR_FACE;
     SI[SI_BR_FACE] += 1;
     SI[SI_SKIPLS] = gd < 0.0 ? 0 : 1;

@@ -29,6 +29,7 @@ enum SI : int {
   SI_PASSES, SI_HVPS, SI_THIRD, SI_BR_RAW, SI_BR_SEG, SI_BR_CAP, SI_BR_FACE, SI_ARCMAX,
   SI_LSRULE,        // step rule along d: 0 exact quartic, 1 Armijo backtracking on the quartic
   SI_FCNT,          // coordinates of the working face in the face list (lockstep batches)
+  SI_LS2OUT,        // the step segment dstep has entries off the union of the faces (lockstep batches)
   SI_LIVE = 30,     // live-column count per PCG group (10 groups of two columns)
   SI_ACT = 40,      // per-column active flags (20 columns)
   SI_CITS = 60,     // per-column PCG iteration counts (20 columns)
