@@ -566,16 +566,6 @@ __global__ void k_transpose_u_bf16(const __nv_bfloat16* __restrict__ srcT, long 
   }
 }
 
-// dst[b * ldd + j] = V[b * vs + idx[j]] for j < |U|, zero for |U| <= j < ldd
-// (the right-hand vectors of a split product restricted to U).  Grid (x, B).
-__global__ void k_gather_vec_u(const double* V, long long vs, const int* idx, const int* info, double* dst, int ldd,
-                               const int* need = nullptr) {
-  if (need != nullptr && *need == 0) return;
-  const int b = blockIdx.y, ku = info[0];
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ldd; j += gridDim.x * blockDim.x)
-    dst[(size_t)b * ldd + j] = j < ku ? V[(size_t)b * vs + idx[j]] : 0.0;
-}
-
 // BF16 columns in U coordinates: dst[q*ld + j] = bf16(col_q[idx[j]]) for
 // j < |U|, zero for |U| <= j < info[1]; col_q as in k_cols_bf16_b.
 __global__ void k_cols_bf16_u(Inst base, int nc, int c0, int interleave, const int* idx, const int* info,
@@ -1268,9 +1258,7 @@ mvsk_status batch_iteration_tail(mvsk_ctx* c, BatchBuf& bb, int B, const std::ve
   auto ls_union = [&](double* dvec, int skip_slot, const int* need) -> mvsk_status {
     for (int b0 = 0; b0 < B; b0 += kOzMaxB) {
       const int nb = B - b0 < kOzMaxB ? B - b0 : kOzMaxB;
-      PROF_LAUNCH(NK_OZ_SPLIT, (k_gather_vec_u<<<dim3((unsigned)((c->ld + 255) / 256), nb), 256, 0, c->stream>>>(
-                                   dvec + (size_t)b0 * base.vs, base.vs, bb.u_idx, bb.u_info, bb.u_DU, c->ld, need)));
-      TRY(oz_product_u(c, bb.u_DU, nb, oz_bp(nb), bb.u_AFU, bb.u_info, need));
+      TRY(oz_product_u(c, dvec + (size_t)b0 * base.vs, base.vs, bb.u_idx, nb, oz_bp(nb), bb.u_AFU, bb.u_info, need));
       PROF_LAUNCH(NK_OZ_LS, (k_oz_fin_ls<<<dim3(Gl, nb), 256, 0, c->stream>>>(oz.part, 0, oz_bp(nb), oz.MpF, oz.eF,
                                                                              oz.fF, base, b0, skip_slot, bb.wls,
                                                                              bb.u_info, need)));
@@ -1429,8 +1417,6 @@ mvsk_status ensure_ubuf(mvsk_ctx* c, BatchBuf& bb) {
   if (c->opt.split_products) {  // the line-search product on U
     TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * kOzS * (size_t)c->oz.MpF * ld));
     bb.u_AFU = (__nv_bfloat16*)p;
-    TRY(dalloc(c, &p, sizeof(double) * kOzMaxB * ld));
-    bb.u_DU = (double*)p;
   }
   CU(cudaFuncSetAttribute(k_pcg_round_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)(sizeof(float) * kMF * (kMF + 1))));

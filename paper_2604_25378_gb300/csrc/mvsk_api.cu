@@ -77,7 +77,6 @@ struct BatchBuf {
   __nv_bfloat16 *u_AU = nullptr, *u_AUT = nullptr, *u_A2UT = nullptr;
   int *u_flag = nullptr, *u_idx = nullptr, *u_pos = nullptr, *u_info = nullptr, *u_rt = nullptr;
   __nv_bfloat16* u_AFU = nullptr;  // digit planes of A's columns in U (split line-search product)
-  double* u_DU = nullptr;          // directions in U coordinates (64 x ld)
   mvsk::UProd* u_specs = nullptr;
   std::vector<mvsk::UProd> u_hspec;
   bool umode = false;

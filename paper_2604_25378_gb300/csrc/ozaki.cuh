@@ -186,35 +186,67 @@ static __global__ void k_oz_split_rows_u(const double* A, long long lda, long lo
   }
 }
 
-// Right-hand vectors: vector b (b < B) is V[b*vstride + k], k < K.  Exponent
-// pass: f[b] = max over chunks of the chunk exponent (f preset to kOzNoExp by
-// the caller; all-zero chunks leave it).  Grid (chunks of 1024, Bp).
+// Right-hand vectors, one launch per product: vector b < B has elements
+// v_k = V[b*vstride + k] for k < K (gidx null) or v_k = V[b*vstride + gidx[k]]
+// for k < ginfo[0] (a gathered coordinate list), zero up to the row length
+// ldo (ginfo[1] when gathered); vectors B <= b < Bp are zero.  CTA (x, b)
+// finds the exponent of vector b from the largest magnitude, taken as the
+// largest bit pattern of |v_k| (integer pipe; the order of non-negative
+// doubles), and writes the digits of its share of the row: rows u*Bp + b of
+// out (ldo BF16 each).  CTA (0, b) stores f[b] (kOzNoExp for a zero or absent
+// vector).  The zn int64 slots at zp are zeroed over the whole grid (the
+// product's integer slots).  Grid (chunks, Bp), 512 threads.
 constexpr int kOzNoExp = (int)0x80808080;  // byte-fill 0x80: below every exponent
-static __global__ void __launch_bounds__(256) k_oz_vec_exp(const double* V, long long vstride, int B, int K, int* f,
-                                                           const int* need) {
+static __global__ void __launch_bounds__(512) k_oz_vec_split(const double* V, long long vstride, int B, int K, int ldo,
+                                                             const int* gidx, const int* ginfo, int* f,
+                                                             __nv_bfloat16* out, int Bp, long long* zp, long long zn,
+                                                             const int* need) {
   if (need != nullptr && *need == 0) return;
   const int b = blockIdx.y;
-  if (b >= B) return;
-  const double* v = V + (size_t)b * vstride;
-  double mx = 0.0;
-  for (int k = blockIdx.x * 1024 + threadIdx.x; k < K && k < (blockIdx.x + 1) * 1024; k += blockDim.x)
-    mx = fmax(mx, fabs(v[k]));
+  const long long nth = (long long)gridDim.x * gridDim.y * blockDim.x;
+  for (long long i = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x; i < zn; i += nth)
+    zp[i] = 0;
+  const int kv = gidx != nullptr ? ginfo[0] : K;     // elements that may be nonzero
+  const int row = gidx != nullptr ? ginfo[1] : ldo;  // digits written (the product reads no further)
+  const double* v = V + (size_t)(b < B ? b : 0) * vstride;
+  __shared__ unsigned long long wm[16];
+  __shared__ int s_e;
+  unsigned long long mx = 0;
+  if (b < B)
+    for (int k = threadIdx.x; k < kv; k += blockDim.x) {
+      const double x = gidx != nullptr ? v[gidx[k]] : v[k];
+      const unsigned long long m = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+      mx = m > mx ? m : mx;
+    }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(&f[b], oz_exponent(mx));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = t > mx ? t : mx;
+  }
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = wm[w] > m ? wm[w] : m;
+    const int e = m != 0 ? oz_exponent(__longlong_as_double((long long)m)) : kOzNoExp;
+    s_e = e;
+    if (blockIdx.x == 0) f[b] = e;
+  }
+  __syncthreads();
+  const int e = s_e;
+  const int chunk = (row + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int k0 = (int)blockIdx.x * chunk, k1 = k0 + chunk < row ? k0 + chunk : row;
+  for (int k = k0 + (int)threadIdx.x; k < k1; k += blockDim.x) {
+    double x = 0.0;
+    if (e != kOzNoExp && k < kv) x = gidx != nullptr ? v[gidx[k]] : v[k];
+    oz_digits(x, e != kOzNoExp ? e : 0, out + (size_t)b * ldo + k, (size_t)Bp * ldo);
+  }
 }
 
-// Digit pass: rows u*Bp + b of out (ldo BF16 each), zero for k >= K, b >= B or
-// an all-zero vector.  Grid (ldo / 256, Bp).
-static __global__ void k_oz_vec_digits(const double* V, long long vstride, int B, int Bp, int K, int ldo,
-                                       const int* f, __nv_bfloat16* out, const int* need) {
-  if (need != nullptr && *need == 0) return;
-  const int b = blockIdx.y;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= ldo) return;
-  const int e = b < B ? f[b] : kOzNoExp;
-  const double x = (e != kOzNoExp && k < K) ? V[(size_t)b * vstride + k] : 0.0;
-  oz_digits(x, e != kOzNoExp ? e : 0, out + (size_t)b * ldo + k, (size_t)Bp * ldo);
+// CTAs per vector of k_oz_vec_split for rows of ldo digits.
+inline int oz_split_chunks(long long ldo) {
+  const long long s = (ldo + 2047) / 2048;
+  return (int)(s < 1 ? 1 : s > 8 ? 8 : s);
 }
 
 // ------------------------------------------------------------------ product
@@ -229,7 +261,7 @@ static __global__ void k_oz_vec_digits(const double* V, long long vstride, int B
 // kOzGroup by 64-bit integer atomic addition, so that
 //     part[(g*Bp + b)*ldp + m] = sum over chunks of group g of the chunk's folded levels
 // whatever the order of the additions (integer sums are associative).  The
-// slots must be zero before the launch (k_oz_zero).  Each chunk's sum is
+// slots must be zero before the launch (k_oz_vec_split clears them).  Each chunk's sum is
 // < 2^58.1 in magnitude, so a slot of 16 stays below 2^62.1.
 //
 // Roles: warp 0 streams the operands (one bulk copy per 16 KB left digit
@@ -249,13 +281,6 @@ __host__ __device__ constexpr int oz_slots(int nkb) { return ((nkb + 7) / 8 + kO
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Zero n int64 slots (skipped when *need == 0).
-static __global__ void k_oz_zero(long long* p, long long n, const int* need) {
-  if (need != nullptr && *need == 0) return;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    p[i] = 0;
 }
 
 // kinfo (nullable): the left operand is restricted to a coordinate list whose

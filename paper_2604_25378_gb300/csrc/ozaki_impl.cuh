@@ -65,11 +65,6 @@ mvsk_status oz_product(mvsk_ctx* c, int trans, const double* V, long long vstrid
   const long long M = trans ? c->n : c->T;
   const long long Mp = trans ? o.MpB : o.MpF;
   int* f = trans ? o.fB : o.fF;
-  CU(cudaMemsetAsync(f, 0x80, sizeof(int) * Bp, c->stream));  // kOzNoExp
-  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_vec_exp<<<dim3((unsigned)((K + 1023) / 1024), Bp), 256, 0, c->stream>>>(
-                               V, vstride, B, (int)K, f, need)));
-  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_vec_digits<<<dim3((unsigned)((ldk + 255) / 256), Bp), 256, 0, c->stream>>>(
-                               V, vstride, B, Bp, (int)K, (int)ldk, f, trans ? o.XB : o.XF, need)));
   const int nkb = (int)(ldk / kTcBK);
   const int slots = oz_slots(nkb);
   const long long units = Mp / kTcBM * ((nkb + 7) / 8);
@@ -80,8 +75,9 @@ mvsk_status oz_product(mvsk_ctx* c, int trans, const double* V, long long vstrid
   // work: BF16 tensor FLOPs issued (kOzS (kOzS + 1) / 2 digit products)
   const double flops = 2.0 * (double)Mp * (double)((ldk + kTcBK - 1) / kTcBK * kTcBK) * Bp * (kOzS * (kOzS + 1) / 2);
   const long long zn = (long long)slots * Bp * Mp;
-  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_zero<<<(unsigned)((zn + 1023) / 1024 < 4 * c->nsm ? (zn + 1023) / 1024 : 4 * c->nsm),
-                                        256, 0, c->stream>>>(o.part, zn, need)));
+  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_vec_split<<<dim3((unsigned)oz_split_chunks(ldk), (unsigned)Bp), 512, 0, c->stream>>>(
+                               V, vstride, B, (int)K, (int)ldk, nullptr, nullptr, f, trans ? o.XB : o.XF, Bp, o.part,
+                               zn, need)));
   // launches gated by a device flag (z = A x on refreshes, the projected
   // segment) have their own kind: when skipped they do no work
   TRY(prof_begin(c, need != nullptr ? kKindOz + 2 + trans : kKindOz + trans, flops));
@@ -112,28 +108,23 @@ mvsk_status oz_product(mvsk_ctx* c, int trans, const double* V, long long vstrid
 
 // A V with the left operand restricted to the columns of A in a coordinate
 // list (the union of the working faces of a batch): AU holds their digit
-// planes (k_oz_split_rows_u, padded count info[1]); V holds B vectors of ld
-// values in list coordinates (zero beyond the list).  Partials in c->oz.part
+// planes (k_oz_split_rows_u, padded count info[1]); the B vectors are
+// V[b*vstride + idx[j]], j < info[0] (the list), zero beyond it.  Partials in c->oz.part
 // as from oz_product (ld Mp), slot count oz_slots(info[1] / 64), read by the
 // finishing kernel from info.  need: device flag (nullable) as in oz_product.
-mvsk_status oz_product_u(mvsk_ctx* c, const double* V, int B, int Bp, const __nv_bfloat16* AU, const int* info,
-                         const int* need) {
+mvsk_status oz_product_u(mvsk_ctx* c, const double* V, long long vstride, const int* idx, int B, int Bp,
+                         const __nv_bfloat16* AU, const int* info, const int* need) {
   TRY(oz_prepare(c, Bp));
   OzBuf& o = c->oz;
   const int K = c->ld;
-  CU(cudaMemsetAsync(o.fF, 0x80, sizeof(int) * Bp, c->stream));  // kOzNoExp
-  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_vec_exp<<<dim3((unsigned)((K + 1023) / 1024), Bp), 256, 0, c->stream>>>(
-                               V, c->ld, B, K, o.fF, need)));
-  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_vec_digits<<<dim3((unsigned)((K + 255) / 256), Bp), 256, 0, c->stream>>>(
-                               V, c->ld, B, Bp, K, c->ld, o.fF, o.XF, need)));
   // the grid and the zeroed slots cover every column; the kernel takes its
   // k-extent from info[1] (CTAs without units return)
   const int nkb = K / kTcBK;
   const long long units = o.MpF / kTcBM * ((nkb + 7) / 8);
   const unsigned grid = (unsigned)(units < c->nsm ? units : c->nsm);
   const long long zn = (long long)oz_slots(nkb) * Bp * o.MpF;
-  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_zero<<<(unsigned)((zn + 1023) / 1024 < 4 * c->nsm ? (zn + 1023) / 1024 : 4 * c->nsm),
-                                        256, 0, c->stream>>>(o.part, zn, need)));
+  PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_vec_split<<<dim3((unsigned)oz_split_chunks(K), (unsigned)Bp), 512, 0, c->stream>>>(
+                               V, vstride, B, K, c->ld, idx, info, o.fF, o.XF, Bp, o.part, zn, need)));
   // work per unit of the padded list length: 28 digit products of Mp x Bp
   TRY(prof_begin_u(c, need != nullptr ? kKindOz + 5 : kKindOz + 4,
                    2.0 * (double)o.MpF * Bp * (kOzS * (kOzS + 1) / 2)));
