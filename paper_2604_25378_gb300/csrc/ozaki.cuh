@@ -386,7 +386,18 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __nv_bfloat16* 
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issue
-      int i = 0, ai = 0, r = 0;
+      // With as many left-digit slots as digits, tile s of every k-block
+      // sits in slot s (filled for k-block i in phase i & 1).  The loops over
+      // digits, k-steps and N pieces are unrolled, so that every MMA is one
+      // instruction on precomputed descriptors and a constant instruction
+      // descriptor: a single thread issues them, and per-MMA bookkeeping
+      // would otherwise hold the tensor pipe back on the narrow pieces.
+      static_assert(kOzAStages == kOzS && kOzXStages == 2, "slot s holds digit s; two right-digit slots");
+      uint64_t adesc[kOzS];
+#pragma unroll
+      for (int s = 0; s < kOzS; ++s) adesc[s] = umma_desc_sw128(sA + (size_t)s * ABYTES);
+      const uint64_t xdesc0 = umma_desc_sw128(sX), xdesc1 = umma_desc_sw128(sX + XBYTES);
+      int i = 0, r = 0;
       bool ok = true;
       for (long long u = u0; u < u1 && ok; ++u, ++r) {
         const int kb0 = (int)(u % nch) * 8, kb1 = kb0 + 8 < nkb ? kb0 + 8 : nkb;
@@ -398,35 +409,33 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const __nv_bfloat16* 
           tc_fence_after();
         }
         for (int kb = kb0; kb < kb1 && ok; ++kb, ++i) {
-          const int xs = i % kOzXStages;
-          if (*s_abort || !mbar_wait_bounded(&xfull[xs], (uint32_t)((i / kOzXStages) & 1))) {
+          const int xs = i & 1;
+          if (*s_abort || !mbar_wait_bounded(&xfull[xs], (uint32_t)((i >> 1) & 1))) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const unsigned char* xb = sX + (size_t)xs * XBYTES;
-#pragma unroll 1
-          for (int s = 0; s < kOzS; ++s, ++ai) {
-            const int as = ai % kOzAStages;
-            if (!mbar_wait_bounded(&afull[as], (uint32_t)((ai / kOzAStages) & 1))) {
+          const uint64_t xd = xs ? xdesc1 : xdesc0;
+          const uint32_t ph = (uint32_t)(i & 1);
+          const bool first = kb == kb0;
+#pragma unroll
+          for (int s = 0; s < kOzS; ++s) {
+            if (!mbar_wait_bounded(&afull[s], ph)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint64_t da = umma_desc_sw128(sA + (size_t)as * ABYTES);
-            const int ntot = (kOzS - s) * BP;
 #pragma unroll
             for (int kk = 0; kk < kTcBK / 16; ++kk) {
-              const uint32_t acc = (kb > kb0 || s > 0 || kk > 0) ? 1u : 0u;
-#pragma unroll 1
-              for (int c0 = 0; c0 < ntot; c0 += 256) {
-                const int nn = ntot - c0 < 256 ? ntot - c0 : 256;
-                const uint64_t db = umma_desc_sw128(xb + (size_t)c0 * 128);
-                umma_bf16(tmem + (uint32_t)(s * BP + c0), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk),
-                          idesc_bf16_f32(kTcBM, nn), acc);
+              const uint32_t acc = (!first || s > 0 || kk > 0) ? 1u : 0u;
+#pragma unroll
+              for (int c0 = 0; c0 < (kOzS - s) * BP; c0 += 256) {
+                const int nn = (kOzS - s) * BP - c0 < 256 ? (kOzS - s) * BP - c0 : 256;
+                umma_bf16(tmem + (uint32_t)(s * BP + c0), adesc[s] + (uint64_t)(2 * kk),
+                          xd + (uint64_t)(c0 * 8 + 2 * kk), idesc_bf16_f32(kTcBM, nn), acc);
               }
             }
-            umma_commit(&aempty[as]);
+            umma_commit(&aempty[s]);
           }
           if (ok) umma_commit(&xempty[xs]);
         }
