@@ -1149,10 +1149,10 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
   if (!dir) return MVSK_OK;
   const unsigned nch = (unsigned)((c->T + kFRows - 1) / kFRows);
   if (part == 2) {  // every face small: explicit face Grams, PCG rounds in shared memory
-    constexpr int kTri = (kMF / 8) * (kMF / 8 + 1) / 2;  // 8 x 8 blocks of the largest face
-    PROF_LAUNCH(NK_GRAM, (k_face_gram<<<dim3(nch, B, (kTri + 255) / 256), 256, kGramSmem, c->stream>>>(
-                             base, bb.f_list, bb.u_AU, bb.u_pos, bb.f_gp)));
-    PROF_LAUNCH(NK_GRAM, (k_face_gram_sum<<<dim3(16, B), 256, 0, c->stream>>>(base, bb.f_gp, (int)nch, bb.f_gram)));
+    // face Grams on the tensor cores, rows of A in kGramSplit shares per instance
+    PROF_LAUNCH(NK_GRAM, (k_face_gram_tc<<<dim3(kGramSplit, B), 256, kGramTcSmem, c->stream>>>(
+                             base, bb.f_list, bb.u_AUT, c->Tp, bb.u_pos, bb.f_gp, c->err)));
+    PROF_LAUNCH(NK_GRAM, (k_face_gram_sum<<<dim3(16, B), 256, 0, c->stream>>>(base, bb.f_gp, kGramSplit, bb.f_gram)));
     PROF_LAUNCH(NK_GRAM, (k_face_gram_finish<<<B, 256, 0, c->stream>>>(base, bb.f_list, bb.f_gram, Gz)));
     if (K > 0)
       PROF_LAUNCH(NK_PROBE_FILL,
@@ -1163,8 +1163,8 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     PROF_LAUNCH(NK_PCG_ROUND, (k_pcg_round_small<<<dim3(ncol1, B), kMF, gsm, c->stream>>>(base, 0, kmax, bb.f_list,
                                                                                           bb.f_gram)));
     if (K > 0) {
-      PROF_LAUNCH(NK_HUTCH, (k_face_hutch<<<dim3(nch, B), 256, 0, c->stream>>>(base, K, bb.f_list, bb.u_AU, bb.u_pos,
-                                                                                 bb.f_ap)));
+      PROF_LAUNCH(NK_HUTCH, (k_face_hutch<<<dim3(nch, B), 256, 0, c->stream>>>(base, K, bb.f_list, bb.u_AUT, c->Tp,
+                                                                                 bb.u_pos, bb.f_ap)));
       PROF_LAUNCH(NK_HUTCH, (k_face_hutch_finish<<<B, 256, 0, c->stream>>>(base, bb.f_list, bb.f_ap, (int)nch)));
     } else {
       for (int b = 0; b < B; ++b) CU(cudaMemsetAsync(inst_at(base, b).at, 0, sizeof(double) * c->ld, c->stream));
@@ -1420,7 +1420,7 @@ mvsk_status ensure_ubuf(mvsk_ctx* c, BatchBuf& bb) {
   }
   CU(cudaFuncSetAttribute(k_pcg_round_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)(sizeof(float) * kMF * (kMF + 1))));
-  CU(cudaFuncSetAttribute(k_face_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramSmem));
+  CU(cudaFuncSetAttribute(k_face_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramTcSmem));
   return MVSK_OK;
 }
 

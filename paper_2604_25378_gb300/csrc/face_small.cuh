@@ -12,11 +12,12 @@
 // correction a = T^-1 A_F^T (psi''' o rhat), rhat = K^-1 sum_k (A_F X_k) o
 // (A_F p_k) (Eq. operator-third), takes one more pass over A_F.  The columns
 // of A come from the union gather of the face-restricted products (BF16, the
-// precision of the other direction products); sums are FP32.
+// precision of the other direction products).  G_F is formed on the tensor
+// cores (BF16 data, the psi''-weighted operand carried in two BF16 parts,
+// FP32 accumulation); the other sums are FP32.
 #pragma once
 
 constexpr int kMF = 224;       // largest face handled here (one coordinate per thread of a PCG CTA)
-constexpr int kFRg = 8;        // largest number of row groups of a k_face_gram CTA
 constexpr int kFRows = 480;    // rows of A per CTA of the Gram and Hutchinson passes
 constexpr int kFTile = 32;     // rows staged in shared memory at a time
 
@@ -68,116 +69,184 @@ __global__ void k_small_mode(Inst base, int B, int* info) {
   if (threadIdx.x == 0) info[2] = big ? 0 : 1;
 }
 
-// Partial face Grams.  CTA (x, b, z) covers rows [x kFRows, (x + 1) kFRows)
-// of instance b: G_part[k][l] = sum_t psi2(z_t) a_tk a_tl (psi2 the second
-// derivative of psi) for k, l < m_b in 8 x 8 register blocks of the upper
-// triangle, a_tk = A[t][fl[k]] from the gathered columns AU (T x ld, column
-// upos[fl[k]]), staged kFTile rows at a time in shared memory.  With few
-// blocks (small faces) the rows of the chunk are also split among up to kFRg
-// row groups (thread j: block z * 256 + j mod nblk, row group j / nblk),
-// whose sums are added in shared memory in group order.  Out: slab (b, x) of
-// kMF^2 floats, element (k, l) at k mp + l (mp = m rounded up to 8), for the
-// blocks of this CTA.  Dynamic shared memory: kGramSmem bytes.
-constexpr int kGramRed = 256 * 65;  // row-group sums: 256 threads x 64 values (+1 pad)
-// staged row: element k at k + 4 (k / 8), so that the 8-wide blocks of
-// neighbouring threads start on different shared-memory banks
-constexpr int kGramRow = kMF + kMF / 2 + 16;
-constexpr size_t kGramSmem = sizeof(float) * ((size_t)kGramRed + (size_t)kFTile * kGramRow + kFTile) + sizeof(int) * kMF;
+// Face Grams on the tensor cores.  CTA (x, b) accumulates over the 64-row
+// blocks [x nkb / S, (x + 1) nkb / S) of instance b (S = gridDim.x) the
+// product D = P Q^T with P[k][t] = a_tk (face coordinate k, a row of the
+// gathered A^T: AUT row upos[fl[k]], ldt BF16 apart, contiguous in t) and
+// Q[l][t] = psi2(z_t) a_tl split into BF16 parts Q = Qhi + Qlo (Qhi the
+// rounding of the FP32 product, Qlo that of the rest; together ~16 bits), so
+// that D = P Qhi^T + P Qlo^T is sum_t psi2(z_t) a_tk a_tl to about the
+// precision of FP32 products of the BF16 data (FP32 accumulation in TMEM): M = one or two 128-row tiles of
+// the face, N = m rounded up to 16 (<= kMF), K = 64 rows of A per stage.  The
+// 256 threads stage both operands (16-byte loads along t, as 128-byte
+// swizzled K-major rows, the layout the MMA descriptors read) into one of two
+// stages while the MMAs of the other run; thread 0 issues the MMAs.  Out:
+// element (k, l), k <= l < m, of slab (b, x) at k mp8 + l (mp8 = m rounded up
+// to 8): the partial layout k_face_gram_sum adds.  Dynamic shared memory
+// kGramTcSmem; waits are bounded (err |= kErrWaitTimeout on expiry).
+constexpr int kGTBytesA = 2 * 128 * 128;  // two M tiles of 128 rows x 64 BF16
+constexpr int kGTBytesB = kMF * 128;      // up to kMF rows x 64 BF16 (one of Qhi, Qlo)
+constexpr size_t kGramTcSmem = 1024 + (size_t)2 * (kGTBytesA + 2 * kGTBytesB) + 256;
+constexpr int kGramSplit = 2;  // shares of the rows of A per instance (64 instances: 128 CTAs, one wave)
+static_assert(kMF % 16 == 0 && kMF <= 256, "the N extent of the face Gram MMA");
 
-__global__ void __launch_bounds__(256) k_face_gram(Inst base, const int* fl_base, const __nv_bfloat16* AU,
-                                                   const int* upos, float* gp) {
+__device__ __forceinline__ int sw128_off(int r, int j) {
+  return ((r >> 3) << 10) + ((r & 7) << 7) + (((j ^ r) & 7) << 4);
+}
+
+// 8 BF16 values (a uint4) times h[0..7] in FP32, split into BF16 parts:
+// *hi the rounding of each product, *lo the rounding of its remainder.
+__device__ __forceinline__ void bf16x8_scale2(uint4 v, const float* h, uint4* hi, uint4* lo) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  uint32_t a[4], c[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float p0 = __uint_as_float(w[q] << 16) * h[2 * q], p1 = __uint_as_float(w[q] & 0xFFFF0000u) * h[2 * q + 1];
+    const __nv_bfloat162 r2 = __floats2bfloat162_rn(p0, p1);
+    const float2 rf = __bfloat1622float2(r2);
+    const __nv_bfloat162 e2 = __floats2bfloat162_rn(p0 - rf.x, p1 - rf.y);
+    a[q] = *reinterpret_cast<const uint32_t*>(&r2);
+    c[q] = *reinterpret_cast<const uint32_t*>(&e2);
+  }
+  *hi = make_uint4(a[0], a[1], a[2], a[3]);
+  *lo = make_uint4(c[0], c[1], c[2], c[3]);
+}
+
+__global__ void __launch_bounds__(256, 1) k_face_gram_tc(Inst base, const int* fl_base, const __nv_bfloat16* AUT,
+                                                         long long ldt, const int* upos, float* gp, int* err) {
   const int b = blockIdx.y;
   const Inst s = inst_at(base, b);
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
   const int m = s.si[SI_FCNT];
-  if (m > kMF) return;
-  const int nb = (m + 7) / 8, ntri = nb * (nb + 1) / 2, mp = 8 * nb;
-  if ((int)blockIdx.z * 256 >= ntri) return;
-  const int nblk = ntri - (int)blockIdx.z * 256 < 256 ? ntri - (int)blockIdx.z * 256 : 256;
-  int rg_n = ntri < 256 ? 256 / ntri : 1;  // row groups only when one CTA holds every block
-  if (rg_n > kFRg) rg_n = kFRg;
-  extern __shared__ __align__(16) float fsm[];
-  float* red = fsm;                                           // kGramRed
-  float (*a)[kGramRow] = reinterpret_cast<float (*)[kGramRow]>(fsm + kGramRed);
-  float* h = fsm + kGramRed + kFTile * kGramRow;
-  int* col = reinterpret_cast<int*>(h + kFTile);
-  const int* fl = fl_base + (size_t)b * s.vs;
-  const int ld = s.ld;
+  if (m > kMF || m <= 0) return;
+  const int n16 = (m + 15) & ~15, mp8 = (m + 7) & ~7, nmt = m > 128 ? 2 : 1;
   const long long T = s.T;
-  const long long t0 = (long long)blockIdx.x * kFRows, t1 = t0 + kFRows < T ? t0 + kFRows : T;
-  for (int k = threadIdx.x; k < kMF; k += blockDim.x) col[k] = k < m ? upos[fl[k]] : -1;
-  const float c2 = (float)s.sd[SD_C2], c3 = (float)s.sd[SD_C3], c4 = (float)s.sd[SD_C4];
-  const int blk = (int)threadIdx.x % nblk, rg = (int)threadIdx.x / nblk;
-  const bool act = rg < rg_n;
-  int bi = 0, bj = 0;
-  {  // block index -> (bi, bj) of the row-major upper triangle
-    int rem = (int)blockIdx.z * 256 + blk;
-    while (rem >= nb - bi) {
-      rem -= nb - bi;
-      ++bi;
-    }
-    bj = bi + rem;
+  const int nkb = (int)((T + 63) / 64);
+  const int kb0 = (int)((long long)blockIdx.x * nkb / gridDim.x);
+  const int kb1 = (int)((long long)(blockIdx.x + 1) * nkb / gridDim.x);
+  if (kb0 >= kb1) return;  // uniform over the CTA, before any barrier or TMEM use
+  extern __shared__ unsigned char gsm_raw[];
+  unsigned char* sm =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sA = sm;
+  unsigned char* sB = sm + 2 * kGTBytesA;  // per stage: Qhi, then Qlo
+  uint64_t* mdone = reinterpret_cast<uint64_t*>(sB + 4 * kGTBytesB);  // [2]: the MMAs of a stage completed
+  uint64_t* fin = mdone + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
+  __shared__ float h[2 * 64];  // weights of the rows of the block in each stage
+  __shared__ int roww[256];
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int* fl = fl_base + (size_t)b * s.vs;
+  roww[tid] = tid < m ? upos[fl[tid]] : -1;
+  if (tid == 0) {
+    mbar_init(&mdone[0], 1);
+    mbar_init(&mdone[1], 1);
+    mbar_init(fin, 1);
+    fence_barrier_init();
+    s_abort = 0;
   }
-  float acc[64];
-#pragma unroll
-  for (int e = 0; e < 64; ++e) acc[e] = 0.f;
+  if (warp == 0) tmem_alloc(tslot, 512);
+  tc_fence_before();
   __syncthreads();
-  for (long long tb = t0; tb < t1; tb += kFTile) {
-    const int rows = (int)(t1 - tb < kFTile ? t1 - tb : kFTile);
-    for (int e = threadIdx.x; e < kFTile * mp; e += blockDim.x) {
-      const int r = e / mp, k = e - r * mp;
-      float v = 0.f;
-      if (r < rows && k < m) v = __bfloat162float(AU[(size_t)(tb + r) * ld + col[k]]);
-      a[r][k + 4 * (k >> 3)] = v;
-    }
-    if (threadIdx.x < kFTile) {
-      float hv = 0.f;
-      if ((int)threadIdx.x < rows) {
-        const float z = (float)s.z[tb + threadIdx.x];
-        hv = 2.f * c2 - z * (6.f * c3 - 12.f * c4 * z);
-      }
-      h[threadIdx.x] = hv;
-    }
-    __syncthreads();
-    if (act) {
-      const int k0 = 12 * bi, l0 = 12 * bj;  // padded offsets of the blocks
-      for (int r = rg; r < rows; r += rg_n) {
-        const float hr = h[r];
-        const float4 x0 = *reinterpret_cast<const float4*>(&a[r][k0]);
-        const float4 x1 = *reinterpret_cast<const float4*>(&a[r][k0 + 4]);
-        const float4 y0 = *reinterpret_cast<const float4*>(&a[r][l0]);
-        const float4 y1 = *reinterpret_cast<const float4*>(&a[r][l0 + 4]);
-        const float x[8] = {hr * x0.x, hr * x0.y, hr * x0.z, hr * x0.w, hr * x1.x, hr * x1.y, hr * x1.z, hr * x1.w};
-        const float y[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const float c2 = (float)s.sd[SD_C2], c3 = (float)s.sd[SD_C3], c4 = (float)s.sd[SD_C4];
+  const uint32_t idesc = idesc_bf16_f32(kTcBM, n16);
+  // Thread tid takes the 16-byte chunks tid + 256 q (row c / 8, chunk c % 8)
+  // of a 64-row block, and threads < 64 the weight of row tid.  The loads of
+  // block i + 1 are issued at the top of iteration i (registers vn, zn), so
+  // that their latency passes while the MMAs of block i - 1 and the staging
+  // of block i run.
+  uint4 vn[8];
+  double zn = 0.0;
+  auto fetch = [&](int kb) {
+    const long long t0 = (long long)kb * 64;
 #pragma unroll
-        for (int e = 0; e < 8; ++e)
+    for (int q = 0; q < 8; ++q) {
+      const int c = tid + 256 * q, r = c >> 3, j = c & 7;
+      const long long t = t0 + 8 * j;
+      vn[q] = make_uint4(0u, 0u, 0u, 0u);
+      if (q < 4 * nmt && r < m && t < ldt)
+        vn[q] = __ldg(reinterpret_cast<const uint4*>(AUT + (size_t)roww[r] * ldt + t));
+    }
+    if (tid < 64 && t0 + tid < T) zn = s.z[t0 + tid];
+  };
+  auto weight = [&](double z64, long long t) {
+    const float z = (float)z64;
+    return t < T ? 2.f * c2 - z * (6.f * c3 - 12.f * c4 * z) : 0.f;
+  };
+  fetch(kb0);
+  if (tid < 64) h[tid] = weight(zn, (long long)kb0 * 64 + tid);
+  int i = 0;
+  for (int kb = kb0; kb < kb1; ++kb, ++i) {
+    const int st = i & 1;
+    uint4 v[8];
 #pragma unroll
-          for (int f = 0; f < 8; ++f) acc[e * 8 + f] = fmaf(x[e], y[f], acc[e * 8 + f]);
+    for (int q = 0; q < 8; ++q) v[q] = vn[q];
+    if (kb + 1 < kb1) fetch(kb + 1);
+    if (i >= 2 && !mbar_wait_bounded(&mdone[st], (uint32_t)(((i - 2) >> 1) & 1))) {
+      atomicOr(err, kErrWaitTimeout);
+      s_abort = 1;
+    }
+    __syncthreads();  // stage st is free; h[st] holds the weights of this block
+    if (s_abort) break;
+    unsigned char* pa = sA + (size_t)st * kGTBytesA;
+    unsigned char* pb = sB + (size_t)st * 2 * kGTBytesB;
+    const float* hb = h + 64 * st;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (q >= 4 * nmt) break;
+      const int c = tid + 256 * q, r = c >> 3, j = c & 7;
+      const int off = sw128_off(r, j);
+      *reinterpret_cast<uint4*>(pa + off) = v[q];
+      if (r < n16) {
+        uint4 qh, ql;
+        bf16x8_scale2(v[q], hb + 8 * j, &qh, &ql);
+        *reinterpret_cast<uint4*>(pb + off) = qh;
+        *reinterpret_cast<uint4*>(pb + kGTBytesB + off) = ql;
       }
     }
+    if (tid < 64 && kb + 1 < kb1) h[64 * (st ^ 1) + tid] = weight(zn, (long long)(kb + 1) * 64 + tid);
+    fence_proxy_async_smem();
     __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint64_t dbh = umma_desc_sw128(pb), dbl = umma_desc_sw128(pb + kGTBytesB);
+      for (int mt = 0; mt < nmt; ++mt) {
+        const uint64_t da = umma_desc_sw128(pa + mt * 16384);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          umma_bf16(tmem + (uint32_t)(mt * 256), da + (uint64_t)(2 * kk), dbh + (uint64_t)(2 * kk), idesc,
+                    (i > 0 || kk > 0) ? 1u : 0u);
+          umma_bf16(tmem + (uint32_t)(mt * 256), da + (uint64_t)(2 * kk), dbl + (uint64_t)(2 * kk), idesc, 1u);
+        }
+      }
+      umma_commit(&mdone[st]);
+    }
   }
-  // row groups: deposit, then group 0 adds them in order
-  if (rg_n > 1) {
-    if (act)
+  if (tid == 0) umma_commit(fin);  // arrives once every MMA issued above has completed
+  const bool ok = mbar_wait_bounded(fin, 0);
+  if (!ok && tid == 0) atomicOr(err, kErrWaitTimeout);
+  tc_fence_after();
+  const int mt = warp >> 2, q = warp & 3;
+  if (ok && !s_abort && mt < nmt) {
+    const int k = mt * 128 + q * 32 + lane;
+    float* out = gp + ((size_t)b * gridDim.x + blockIdx.x) * kMF * kMF;
+    for (int c0 = 0; c0 < n16; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * 256 + c0), v);
+      if (k < m)
 #pragma unroll
-      for (int e = 0; e < 64; ++e) red[(size_t)threadIdx.x * 65 + e] = acc[e];
-    __syncthreads();
-    if (act && rg == 0)
-      for (int g = 1; g < rg_n; ++g) {
-        const float* src = red + (size_t)(g * nblk + blk) * 65;
-#pragma unroll
-        for (int e = 0; e < 64; ++e) acc[e] += src[e];
-      }
+        for (int jj = 0; jj < 16; ++jj) {
+          const int l = c0 + jj;
+          if (l >= k && l < m) out[(size_t)k * mp8 + l] = v[jj];
+        }
+    }
   }
-  if (!act || rg != 0) return;
-  float* out = gp + ((size_t)b * gridDim.x + blockIdx.x) * kMF * kMF;
-  const int k0 = 8 * bi, l0 = 8 * bj;  // face indices of the block
-#pragma unroll
-  for (int e = 0; e < 8; ++e)
-#pragma unroll
-    for (int f = 0; f < 8; ++f)
-      if (k0 + e < m && l0 + f < m) out[(size_t)(k0 + e) * mp + l0 + f] = acc[e * 8 + f];
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 // Face Gram of instance blockIdx.y from the chunk partials (added in chunk
@@ -381,11 +450,12 @@ __global__ void __launch_bounds__(kMF) k_pcg_round_small(Inst base, int c0, int 
 // PCG solutions and projected probes on the face, k < K), u = a_t W (2K
 // values), rhat_t = K^-1 sum_k u_2k u_2k+1, s_t = psi3(z_t) rhat_t (psi3 the
 // third derivative of psi), and out[l] = sum_t s_t a_tl.  Rows are staged
-// kFTile at a time; eight threads per row split the face coordinates
+// kFTile at a time from the gathered rows of A^T (AUT, row upos[fl[l]],
+// contiguous in t); eight threads per row split the face coordinates
 // (l = j mod 8) and add their 2K partial products by shuffles.
 // Out: ap[(b * nchunk + x) * kMF + l].
-__global__ void __launch_bounds__(256) k_face_hutch(Inst base, int K, const int* fl_base, const __nv_bfloat16* AU,
-                                                    const int* upos, float* ap) {
+__global__ void __launch_bounds__(256) k_face_hutch(Inst base, int K, const int* fl_base, const __nv_bfloat16* AUT,
+                                                    long long ldt, const int* upos, float* ap) {
   const int b = blockIdx.y;
   const Inst s = inst_at(base, b);
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
@@ -414,9 +484,9 @@ __global__ void __launch_bounds__(256) k_face_hutch(Inst base, int K, const int*
   __syncthreads();
   for (long long tb = t0; tb < t1; tb += kFTile) {
     const int rows = (int)(t1 - tb < kFTile ? t1 - tb : kFTile);
-    for (int e = threadIdx.x; e < kFTile * m; e += blockDim.x) {
-      const int rr = e / m, l = e - rr * m;
-      a[rr][l] = rr < rows ? __bfloat162float(AU[(size_t)(tb + rr) * ld + col[l]]) : 0.f;
+    for (int e = threadIdx.x; e < kFTile * m; e += blockDim.x) {  // consecutive threads: consecutive t
+      const int l = e / kFTile, rr = e - l * kFTile;
+      a[rr][l] = rr < rows ? __bfloat162float(AUT[(size_t)col[l] * ldt + tb + rr]) : 0.f;
     }
     __syncthreads();
     float u[kW];
