@@ -693,7 +693,7 @@ mvsk_status batch_alloc(mvsk_ctx* c, BatchBuf& bb, int B) {
     const size_t nch = (size_t)((c->T + kFRows - 1) / kFRows);
     TRY(get(sizeof(int) * ld * Bs, &p));
     bb.f_list = (int*)p;
-    TRY(get(sizeof(float) * nch * kMF * kMF * Bs, &p));
+    TRY(get(sizeof(float) * kGramSplit * kMF * kMF * Bs, &p));  // partial Grams, one slab per share of T
     bb.f_gp = (float*)p;
     TRY(get(sizeof(float) * kMF * kMF * Bs, &p));
     bb.f_gram = (float*)p;
@@ -1150,7 +1150,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
   const unsigned nch = (unsigned)((c->T + kFRows - 1) / kFRows);
   if (part == 2) {  // every face small: explicit face Grams, PCG rounds in shared memory
     // face Grams on the tensor cores, rows of A in kGramSplit shares per instance
-    PROF_LAUNCH(NK_GRAM, (k_face_gram_tc<<<dim3(kGramSplit, B), 256, kGramTcSmem, c->stream>>>(
+    PROF_LAUNCH(NK_GRAM, (k_face_gram_tc<<<dim3(kGramSplit, B, (kMF + 127) / 128), 256, kGramTcSmem, c->stream>>>(
                              base, bb.f_list, bb.u_AUT, c->Tp, bb.u_pos, bb.f_gp, c->err)));
     PROF_LAUNCH(NK_GRAM, (k_face_gram_sum<<<dim3(16, B), 256, 0, c->stream>>>(base, bb.f_gp, kGramSplit, bb.f_gram)));
     PROF_LAUNCH(NK_GRAM, (k_face_gram_finish<<<B, 256, 0, c->stream>>>(base, bb.f_list, bb.f_gram, Gz)));
@@ -1159,11 +1159,11 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
                   (k_probe_fill<float><<<dim3((c->ld + 255) / 256, K, B), 256, 0, c->stream>>>(base, K)));
     PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gz, -1)));
     PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup_cols<float><<<dim3(ncol1, B), 512, 0, c->stream>>>(base)));
-    const size_t gsm = sizeof(float) * kMF * (kMF + 1);
+    const size_t gsm = sizeof(float) * face_tri_max_words();
     PROF_LAUNCH(NK_PCG_ROUND, (k_pcg_round_small<<<dim3(ncol1, B), kMF, gsm, c->stream>>>(base, 0, kmax, bb.f_list,
                                                                                           bb.f_gram)));
     if (K > 0) {
-      PROF_LAUNCH(NK_HUTCH, (k_face_hutch<<<dim3(nch, B), 256, 0, c->stream>>>(base, K, bb.f_list, bb.u_AUT, c->Tp,
+      PROF_LAUNCH(NK_HUTCH, (k_face_hutch<<<dim3(nch, B), 256, kHutchSmem, c->stream>>>(base, K, bb.f_list, bb.u_AUT, c->Tp,
                                                                                  bb.u_pos, bb.f_ap)));
       PROF_LAUNCH(NK_HUTCH, (k_face_hutch_finish<<<B, 256, 0, c->stream>>>(base, bb.f_list, bb.f_ap, (int)nch)));
     } else {
@@ -1419,7 +1419,8 @@ mvsk_status ensure_ubuf(mvsk_ctx* c, BatchBuf& bb) {
     bb.u_AFU = (__nv_bfloat16*)p;
   }
   CU(cudaFuncSetAttribute(k_pcg_round_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)(sizeof(float) * kMF * (kMF + 1))));
+                          (int)(sizeof(float) * face_tri_max_words())));
+  CU(cudaFuncSetAttribute(k_face_hutch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHutchSmem));
   CU(cudaFuncSetAttribute(k_face_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramTcSmem));
   return MVSK_OK;
 }

@@ -17,7 +17,7 @@
 // FP32 accumulation); the other sums are FP32.
 #pragma once
 
-constexpr int kMF = 224;       // largest face handled here (one coordinate per thread of a PCG CTA)
+constexpr int kMF = 320;       // largest face handled here (one coordinate per thread of a PCG CTA)
 constexpr int kFRows = 480;    // rows of A per CTA of the Gram and Hutchinson passes
 constexpr int kFTile = 32;     // rows staged in shared memory at a time
 
@@ -69,26 +69,29 @@ __global__ void k_small_mode(Inst base, int B, int* info) {
   if (threadIdx.x == 0) info[2] = big ? 0 : 1;
 }
 
-// Face Grams on the tensor cores.  CTA (x, b) accumulates over the 64-row
-// blocks [x nkb / S, (x + 1) nkb / S) of instance b (S = gridDim.x) the
-// product D = P Q^T with P[k][t] = a_tk (face coordinate k, a row of the
-// gathered A^T: AUT row upos[fl[k]], ldt BF16 apart, contiguous in t) and
-// Q[l][t] = psi2(z_t) a_tl split into BF16 parts Q = Qhi + Qlo (Qhi the
-// rounding of the FP32 product, Qlo that of the rest; together ~16 bits), so
-// that D = P Qhi^T + P Qlo^T is sum_t psi2(z_t) a_tk a_tl to about the
-// precision of FP32 products of the BF16 data (FP32 accumulation in TMEM): M = one or two 128-row tiles of
-// the face, N = m rounded up to 16 (<= kMF), K = 64 rows of A per stage.  The
-// 256 threads stage both operands (16-byte loads along t, as 128-byte
-// swizzled K-major rows, the layout the MMA descriptors read) into one of two
-// stages while the MMAs of the other run; thread 0 issues the MMAs.  Out:
-// element (k, l), k <= l < m, of slab (b, x) at k mp8 + l (mp8 = m rounded up
-// to 8): the partial layout k_face_gram_sum adds.  Dynamic shared memory
-// kGramTcSmem; waits are bounded (err |= kErrWaitTimeout on expiry).
-constexpr int kGTBytesA = 2 * 128 * 128;  // two M tiles of 128 rows x 64 BF16
-constexpr int kGTBytesB = kMF * 128;      // up to kMF rows x 64 BF16 (one of Qhi, Qlo)
+// Face Grams on the tensor cores.  CTA (x, b, t) accumulates over the 64-row
+// blocks [x nkb / S, (x + 1) nkb / S) of instance b (S = gridDim.x) the rows
+// 128 t .. 128 t + 127 of D = P Q^T with P[k][t] = a_tk (face coordinate k,
+// a row of the gathered A^T: AUT row upos[fl[k]], ldt BF16 apart, contiguous
+// in t) and Q[l][t] = psi2(z_t) a_tl split into BF16 parts Q = Qhi + Qlo (Qhi
+// the rounding of the FP32 product, Qlo that of the rest; together ~16 bits),
+// so that D = P Qhi^T + P Qlo^T is sum_t psi2(z_t) a_tk a_tl to about the
+// precision of FP32 products of the BF16 data (FP32 accumulation in TMEM):
+// M = 128 (this CTA's tile of the face), N = m rounded up to 16 (<= kMF, in
+// pieces of at most 256), K = 64 rows of A per stage.  The 256 threads stage
+// the operands (16-byte loads along t, as 128-byte swizzled K-major rows, the
+// layout the MMA descriptors read) into one of two stages while the MMAs of
+// the other run, the loads of the next block in flight; thread 0 issues the
+// MMAs.  Out: element (k, l), k <= l < m, k in the tile, of slab (b, x) at
+// k mp8 + l (mp8 = m rounded up to 8): the partial layout k_face_gram_sum
+// adds.  Dynamic shared memory kGramTcSmem; waits are bounded (err |=
+// kErrWaitTimeout on expiry).
+constexpr int kGTBytesA = 128 * 128;  // one M tile of 128 rows x 64 BF16
+constexpr int kGTBytesB = kMF * 128;  // up to kMF rows x 64 BF16 (one of Qhi, Qlo)
+constexpr int kGTChunks = (((kMF + 127) / 128) * 128 > kMF ? ((kMF + 127) / 128) * 128 : kMF) * 8 / 256;
 constexpr size_t kGramTcSmem = 1024 + (size_t)2 * (kGTBytesA + 2 * kGTBytesB) + 256;
-constexpr int kGramSplit = 2;  // shares of the rows of A per instance (64 instances: 128 CTAs, one wave)
-static_assert(kMF % 16 == 0 && kMF <= 256, "the N extent of the face Gram MMA");
+constexpr int kGramSplit = 2;  // shares of the rows of A per instance
+static_assert(kMF % 16 == 0 && kMF <= 512, "the N extent of the face Gram MMA");
 
 __device__ __forceinline__ int sw128_off(int r, int j) {
   return ((r >> 3) << 10) + ((r & 7) << 7) + (((j ^ r) & 7) << 4);
@@ -114,12 +117,13 @@ __device__ __forceinline__ void bf16x8_scale2(uint4 v, const float* h, uint4* hi
 
 __global__ void __launch_bounds__(256, 1) k_face_gram_tc(Inst base, const int* fl_base, const __nv_bfloat16* AUT,
                                                          long long ldt, const int* upos, float* gp, int* err) {
-  const int b = blockIdx.y;
+  const int b = blockIdx.y, mt = blockIdx.z;
   const Inst s = inst_at(base, b);
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
   const int m = s.si[SI_FCNT];
-  if (m > kMF || m <= 0) return;
-  const int n16 = (m + 15) & ~15, mp8 = (m + 7) & ~7, nmt = m > 128 ? 2 : 1;
+  if (m > kMF || m <= 0 || mt * 128 >= m) return;
+  const int n16 = (m + 15) & ~15, mp8 = (m + 7) & ~7;
+  const int rows = n16 > mt * 128 + 128 ? n16 : mt * 128 + 128;  // rows staged: Q's and this tile's
   const long long T = s.T;
   const int nkb = (int)((T + 63) / 64);
   const int kb0 = (int)((long long)blockIdx.x * nkb / gridDim.x);
@@ -134,11 +138,11 @@ __global__ void __launch_bounds__(256, 1) k_face_gram_tc(Inst base, const int* f
   uint64_t* fin = mdone + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
   __shared__ float h[2 * 64];  // weights of the rows of the block in each stage
-  __shared__ int roww[256];
+  __shared__ int roww[kGTChunks * 32];
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int* fl = fl_base + (size_t)b * s.vs;
-  roww[tid] = tid < m ? upos[fl[tid]] : -1;
+  for (int r = tid; r < kGTChunks * 32; r += 256) roww[r] = r < m ? upos[fl[r]] : -1;
   if (tid == 0) {
     mbar_init(&mdone[0], 1);
     mbar_init(&mdone[1], 1);
@@ -152,23 +156,23 @@ __global__ void __launch_bounds__(256, 1) k_face_gram_tc(Inst base, const int* f
   tc_fence_after();
   const uint32_t tmem = *tslot;
   const float c2 = (float)s.sd[SD_C2], c3 = (float)s.sd[SD_C3], c4 = (float)s.sd[SD_C4];
-  const uint32_t idesc = idesc_bf16_f32(kTcBM, n16);
+  const int nn0 = n16 < 256 ? n16 : 256, nn1 = n16 - nn0;
+  const uint32_t idesc0 = idesc_bf16_f32(kTcBM, nn0), idesc1 = idesc_bf16_f32(kTcBM, nn1 > 0 ? nn1 : 16);
   // Thread tid takes the 16-byte chunks tid + 256 q (row c / 8, chunk c % 8)
   // of a 64-row block, and threads < 64 the weight of row tid.  The loads of
   // block i + 1 are issued at the top of iteration i (registers vn, zn), so
   // that their latency passes while the MMAs of block i - 1 and the staging
   // of block i run.
-  uint4 vn[8];
+  uint4 vn[kGTChunks];
   double zn = 0.0;
   auto fetch = [&](int kb) {
     const long long t0 = (long long)kb * 64;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < kGTChunks; ++q) {
       const int c = tid + 256 * q, r = c >> 3, j = c & 7;
       const long long t = t0 + 8 * j;
       vn[q] = make_uint4(0u, 0u, 0u, 0u);
-      if (q < 4 * nmt && r < m && t < ldt)
-        vn[q] = __ldg(reinterpret_cast<const uint4*>(AUT + (size_t)roww[r] * ldt + t));
+      if (r < m && t < ldt) vn[q] = __ldg(reinterpret_cast<const uint4*>(AUT + (size_t)roww[r] * ldt + t));
     }
     if (tid < 64 && t0 + tid < T) zn = s.z[t0 + tid];
   };
@@ -181,9 +185,9 @@ __global__ void __launch_bounds__(256, 1) k_face_gram_tc(Inst base, const int* f
   int i = 0;
   for (int kb = kb0; kb < kb1; ++kb, ++i) {
     const int st = i & 1;
-    uint4 v[8];
+    uint4 v[kGTChunks];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = vn[q];
+    for (int q = 0; q < kGTChunks; ++q) v[q] = vn[q];
     if (kb + 1 < kb1) fetch(kb + 1);
     if (i >= 2 && !mbar_wait_bounded(&mdone[st], (uint32_t)(((i - 2) >> 1) & 1))) {
       atomicOr(err, kErrWaitTimeout);
@@ -195,14 +199,14 @@ __global__ void __launch_bounds__(256, 1) k_face_gram_tc(Inst base, const int* f
     unsigned char* pb = sB + (size_t)st * 2 * kGTBytesB;
     const float* hb = h + 64 * st;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if (q >= 4 * nmt) break;
+    for (int q = 0; q < kGTChunks; ++q) {
       const int c = tid + 256 * q, r = c >> 3, j = c & 7;
-      const int off = sw128_off(r, j);
-      *reinterpret_cast<uint4*>(pa + off) = v[q];
+      if (r >= rows) break;
+      if (r >= mt * 128 && r < mt * 128 + 128) *reinterpret_cast<uint4*>(pa + sw128_off(r - mt * 128, j)) = v[q];
       if (r < n16) {
         uint4 qh, ql;
         bf16x8_scale2(v[q], hb + 8 * j, &qh, &ql);
+        const int off = sw128_off(r, j);
         *reinterpret_cast<uint4*>(pb + off) = qh;
         *reinterpret_cast<uint4*>(pb + kGTBytesB + off) = ql;
       }
@@ -212,14 +216,16 @@ __global__ void __launch_bounds__(256, 1) k_face_gram_tc(Inst base, const int* f
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
+      const uint64_t da = umma_desc_sw128(pa);
       const uint64_t dbh = umma_desc_sw128(pb), dbl = umma_desc_sw128(pb + kGTBytesB);
-      for (int mt = 0; mt < nmt; ++mt) {
-        const uint64_t da = umma_desc_sw128(pa + mt * 16384);
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          umma_bf16(tmem + (uint32_t)(mt * 256), da + (uint64_t)(2 * kk), dbh + (uint64_t)(2 * kk), idesc,
-                    (i > 0 || kk > 0) ? 1u : 0u);
-          umma_bf16(tmem + (uint32_t)(mt * 256), da + (uint64_t)(2 * kk), dbl + (uint64_t)(2 * kk), idesc, 1u);
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+        umma_bf16(tmem, da + (uint64_t)(2 * kk), dbh + (uint64_t)(2 * kk), idesc0, acc);
+        umma_bf16(tmem, da + (uint64_t)(2 * kk), dbl + (uint64_t)(2 * kk), idesc0, 1u);
+        if (nn1 > 0) {  // N rows 256.. of Q: descriptor start 256 rows (32 KB) further
+          umma_bf16(tmem + 256u, da + (uint64_t)(2 * kk), dbh + (uint64_t)(256 * 8 + 2 * kk), idesc1, acc);
+          umma_bf16(tmem + 256u, da + (uint64_t)(2 * kk), dbl + (uint64_t)(256 * 8 + 2 * kk), idesc1, 1u);
         }
       }
       umma_commit(&mdone[st]);
@@ -229,13 +235,15 @@ __global__ void __launch_bounds__(256, 1) k_face_gram_tc(Inst base, const int* f
   const bool ok = mbar_wait_bounded(fin, 0);
   if (!ok && tid == 0) atomicOr(err, kErrWaitTimeout);
   tc_fence_after();
-  const int mt = warp >> 2, q = warp & 3;
-  if (ok && !s_abort && mt < nmt) {
+  if (ok && !s_abort) {
+    // warps w and w + 4 read lane quarter w % 4: the first and second half of the columns
+    const int q = warp & 3, half = ((n16 / 2) + 15) & ~15;
     const int k = mt * 128 + q * 32 + lane;
+    const int ca = warp < 4 ? 0 : half, cb = warp < 4 ? half : n16;
     float* out = gp + ((size_t)b * gridDim.x + blockIdx.x) * kMF * kMF;
-    for (int c0 = 0; c0 < n16; c0 += 16) {
+    for (int c0 = ca; c0 < cb; c0 += 16) {
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * 256 + c0), v);
+      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
       if (k < m)
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
@@ -350,9 +358,32 @@ __device__ __forceinline__ void cta_sum6(float (&v)[6], float (*scr)[6]) {
   }
 }
 
+// Upper triangle of a symmetric m x m matrix in shared memory: row i from
+// its diagonal at word start(i) (element (i, j), j >= i, at start(i) + j - i),
+// start(0) = 0 and start(i + 1) the first word >= start(i) + m - i that is
+// congruent to 2 (i + 1) mod 32.  Then, for a fixed j, threads i (= 32
+// consecutive rows) reading (min(i, j), max(i, j)) hit 32 distinct banks:
+// start(j) + i - j for i > j, start(i) + j - i = 2i + j (mod 32) for i <= j.
+// Words used for m rows (the shared-memory size of k_pcg_round_small).
+__host__ __device__ constexpr int face_tri_words(int m) {
+  int st = 0;
+  for (int i = 0; i < m; ++i) {
+    const int nx = st + (m - i);
+    st = nx + (((2 * (i + 1) - nx) % 32) + 32) % 32;
+  }
+  return st;
+}
+__host__ __device__ constexpr int face_tri_max_words() {
+  int w = 0;
+  for (int m = 1; m <= kMF; ++m) w = face_tri_words(m) > w ? face_tri_words(m) : w;
+  return w;
+}
+
 // A whole PCG round of column c = c0 + blockIdx.x of instance blockIdx.y on
-// its face (m <= kMF coordinates, one per thread), with G_F from shared
-// memory: the recurrence of the batched step (k_pcg_step_f) with Q = G_F p
+// its face (m <= kMF coordinates, one per thread), with G_F in shared memory:
+// the full matrix (rows m + 1 words apart) when it fits, else the upper
+// triangle in the layout above (the full matrix of a 320-coordinate face does
+// not fit): the recurrence of the batched step (k_pcg_step_f) with Q = G_F p
 // instead of the tensor-core products, from the state k_pcg_setup_cols (or
 // k_pcg_setup2) left (X = 0, R = B, P = Z, rz, rhsn, active flag), up to the
 // iteration budget; the final X, R, P and rz are written back on the face.
@@ -364,14 +395,27 @@ __global__ void __launch_bounds__(kMF) k_pcg_round_small(Inst base, int c0, int 
   if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
   const int m = SI[SI_FCNT];
   if (m > kMF || SI[SI_ACT + c] == 0) return;
-  extern __shared__ float gs[];  // G_F, kMF x (kMF + 1)
+  extern __shared__ float gs[];  // upper triangle of G_F: element (i, j) at rs[i] + j (j >= i)
   __shared__ float pv[kMF];
+  __shared__ int rs[kMF];
   __shared__ float scr[kMF / 32][6];
   const int* fl = fl_base + (size_t)b * s.vs;
   const float* Gm = gram + (size_t)b * kMF * kMF;
+  // faces whose full matrix fits (rows m + 1 words apart: distinct banks)
+  // keep it; larger ones keep the upper triangle
+  const bool full = m * (m + 1) <= face_tri_max_words();
+  if (threadIdx.x == 0) {
+    int st = 0;
+    for (int i = 0; i < m; ++i) {
+      rs[i] = full ? i * (m + 1) : st - i;
+      const int nx = st + (m - i);
+      st = nx + (((2 * (i + 1) - nx) % 32) + 32) % 32;
+    }
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int k = e / m, l = e - k * m;
-    gs[k * (kMF + 1) + l] = Gm[(size_t)k * kMF + l];
+    const int i = e / m, j = e - i * m;
+    if (full || j >= i) gs[rs[i] + j] = Gm[(size_t)i * kMF + j];
   }
   const int ld = s.ld, k = threadIdx.x;
   const bool on = k < m;
@@ -397,9 +441,14 @@ __global__ void __launch_bounds__(kMF) k_pcg_round_small(Inst base, int c0, int 
     pv[k] = p;
     __syncthreads();
     float q = 0.f;
-    if (on) {
-      const float* gr = gs + k * (kMF + 1);
-      for (int l = 0; l < m; ++l) q = fmaf(gr[l], pv[l], q);
+    if (on) {  // q_k = sum_l G[k][l] p_l, l ascending
+      const float* gr = gs + rs[k];
+      if (full) {
+        for (int l = 0; l < m; ++l) q = fmaf(gr[l], pv[l], q);
+      } else {  // (l, k) from row l below the diagonal, (k, l) from row k
+        for (int l = 0; l < k; ++l) q = fmaf(gs[rs[l] + k], pv[l], q);
+        for (int l = k; l < m; ++l) q = fmaf(gr[l], pv[l], q);
+      }
     }
     float a6[6] = {mf * q, nh * q, p * mf * q, p * mf, p * nh, p * p};
     cta_sum6(a6, scr);
@@ -465,7 +514,8 @@ __global__ void __launch_bounds__(256) k_face_hutch(Inst base, int K, const int*
   // W, row l: (X_1, B_1, X_2, B_2, ...); rows 20 floats apart and tile rows
   // kMF + 8 apart, so that the threads of a warp hit distinct banks
   __shared__ __align__(16) float wt[kMF][kW + 4];
-  __shared__ __align__(16) float a[kFTile][kMF + 8];
+  extern __shared__ __align__(16) float hsm[];  // the row tile: kFTile rows, kMF + 8 apart (kHutchSmem bytes)
+  float (*a)[kMF + 8] = reinterpret_cast<float (*)[kMF + 8]>(hsm);
   __shared__ float sw[kFTile];
   __shared__ int col[kMF];
   const int* fl = fl_base + (size_t)b * s.vs;
@@ -480,7 +530,9 @@ __global__ void __launch_bounds__(256) k_face_hutch(Inst base, int K, const int*
   const float c3 = (float)s.sd[SD_C3], c4 = (float)s.sd[SD_C4];
   const long long T = s.T, t0 = (long long)blockIdx.x * kFRows, t1 = t0 + kFRows < T ? t0 + kFRows : T;
   const int r = threadIdx.x >> 3, j = threadIdx.x & 7;  // row of the tile, face-coordinate slice
-  float bacc = 0.f;                                      // back-projection of coordinate threadIdx.x
+  float bacc[(kMF + 255) / 256];  // back-projection of coordinates threadIdx.x + 256 e
+#pragma unroll
+  for (int e = 0; e < (kMF + 255) / 256; ++e) bacc[e] = 0.f;
   __syncthreads();
   for (long long tb = t0; tb < t1; tb += kFTile) {
     const int rows = (int)(t1 - tb < kFTile ? t1 - tb : kFTile);
@@ -530,12 +582,21 @@ __global__ void __launch_bounds__(256) k_face_hutch(Inst base, int K, const int*
       sw[r] = wv;
     }
     __syncthreads();
-    if ((int)threadIdx.x < m)
-      for (int rr = 0; rr < rows; ++rr) bacc = fmaf(sw[rr], a[rr][threadIdx.x], bacc);
+#pragma unroll
+    for (int e = 0; e < (kMF + 255) / 256; ++e) {
+      const int l = (int)threadIdx.x + 256 * e;
+      if (l < m)
+        for (int rr = 0; rr < rows; ++rr) bacc[e] = fmaf(sw[rr], a[rr][l], bacc[e]);
+    }
     __syncthreads();
   }
-  if ((int)threadIdx.x < m) ap[((size_t)b * gridDim.x + blockIdx.x) * kMF + threadIdx.x] = bacc;
+#pragma unroll
+  for (int e = 0; e < (kMF + 255) / 256; ++e) {
+    const int l = (int)threadIdx.x + 256 * e;
+    if (l < m) ap[((size_t)b * gridDim.x + blockIdx.x) * kMF + l] = bacc[e];
+  }
 }
+constexpr size_t kHutchSmem = sizeof(float) * kFTile * (kMF + 8);
 
 // at_b = T^-1 sum over the chunks (fixed order) on the face, zero elsewhere.
 __global__ void k_face_hutch_finish(Inst base, const int* fl_base, const float* ap, int nchunk) {
