@@ -98,12 +98,15 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
 }
 
 // Reductions of the single-CTA-per-instance kernels (up to 1024 threads).
-// The values are staged in shared memory; warp 0 folds the nw = blockDim.x / 32
-// rows column by column (lane l takes entries l, l + 32, ...) and finishes with
-// one 5-level shuffle: nw + 5 warp-wide FP64 operations per value instead of a
-// shuffle tree in every warp (5 per warp, ~160 for 1024 threads) on a pipe of
-// ~2 FMA/clk/SM.  Staging: 2 x 1024 doubles and 1024 ints per kernel that uses
-// them.
+// The values are staged in shared memory; the nw = blockDim.x / 32 rows are
+// folded column by column (lane l takes entries l, l + 32, ...) and finished
+// with one 5-level shuffle: about nw + 5 warp-wide FP64 operations per value
+// instead of a shuffle tree in every warp (5 per warp, ~160 for 1024 threads)
+// on a pipe of ~2 FMA/clk/SM.  A warp-wide FP64 instruction occupies its
+// scheduler's FP64 pipe ~64 cycles, so the sums (block_sum2_fin,
+// block_sum2c_fin) fold in two stages: warps 0..3, one per scheduler, each a
+// quarter of the rows, then warp 0 the four partial rows.  Staging: 2 x 1024
+// doubles and 1024 ints per kernel that uses them, plus the second stage.
 __device__ __forceinline__ double* red_stage() {
   __shared__ double st[2 * 1024];
   return st;
@@ -111,6 +114,17 @@ __device__ __forceinline__ double* red_stage() {
 __device__ __forceinline__ int* red_stage_i() {
   __shared__ int sti[1024];
   return sti;
+}
+// Second stage of the folds below: warps 0..3 (one per scheduler) each fold a
+// quarter of the staged rows, so that the FP64 additions of the first stage
+// run on four pipes at once; 2 x 128 doubles and 128 ints.
+__device__ __forceinline__ double* red_stage2() {
+  __shared__ double st2[256];
+  return st2;
+}
+__device__ __forceinline__ int* red_stage2_i() {
+  __shared__ int st2i[128];
+  return st2i;
 }
 
 __device__ __forceinline__ double block_min(double v, double* scratch) {

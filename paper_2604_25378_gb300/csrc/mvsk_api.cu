@@ -308,7 +308,7 @@ __global__ void k_centre<__nv_bfloat16>(double* A, __nv_bfloat16* lo, long long 
   }
 }
 
-__global__ void k_sumsq(const double* z, long long T, double* out) {
+__global__ void __launch_bounds__(kVT) k_sumsq(const double* z, long long T, double* out) {
   __shared__ double scr[80];
   double s = 0.0;
   for (long long t = threadIdx.x; t < T; t += blockDim.x) s += z[t] * z[t];
@@ -316,7 +316,7 @@ __global__ void k_sumsq(const double* z, long long T, double* out) {
   if (threadIdx.x == 0) *out = s;
 }
 
-__global__ void k_project(const double* v, int n, double tau, double* out) {
+__global__ void __launch_bounds__(kVT) k_project(const double* v, int n, double tau, double* out) {
   __shared__ double scr[80];
   const double th = slice_theta(v, nullptr, 0.0, n, tau, scr);
   for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = tau + fmax(v[i] - tau - th, 0.0);
@@ -327,7 +327,7 @@ __global__ void k_quartic(const double* coef, double amax, double* out) {
   if (threadIdx.x == 0) *out = v;
 }
 
-__global__ void k_alpha_max(const double* x, const double* d, int n, double tau, double* out) {
+__global__ void __launch_bounds__(kVT) k_alpha_max(const double* x, const double* d, int n, double tau, double* out) {
   __shared__ double scr[80];
   double am = INFINITY;
   for (int i = threadIdx.x; i < n; i += blockDim.x)
@@ -336,7 +336,7 @@ __global__ void k_alpha_max(const double* x, const double* d, int n, double tau,
   if (threadIdx.x == 0) *out = am;
 }
 
-__global__ void k_ls_coef_only(Inst s, const double* spart, int G, const double* dir, double* out) {
+__global__ void __launch_bounds__(kVT) k_ls_coef_only(Inst s, const double* spart, int G, const double* dir, double* out) {
   __shared__ double scr[80];
   __shared__ double ps[16];
   __shared__ double coef[5];

@@ -119,7 +119,7 @@ static __global__ void k_oz_row_exp(const double* A, long long lda, long long M,
 
 // e[j] for the columns j < N of a row-major M x N FP64 matrix (zero for N <= j < Np).
 // Block (32, 32): 32 columns, rows strided over threadIdx.y.
-static __global__ void k_oz_col_exp(const double* A, long long lda, long long M, int N, int* e, int Np) {
+static __global__ void __launch_bounds__(1024) k_oz_col_exp(const double* A, long long lda, long long M, int N, int* e, int Np) {
   __shared__ double red[32][33];
   const int j = blockIdx.x * 32 + threadIdx.x;
   double mx = 0.0;

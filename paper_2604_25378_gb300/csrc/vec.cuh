@@ -76,7 +76,8 @@ __host__ __device__ __forceinline__ Inst inst_at(const Inst& a, int b) {
 }
 
 // Block sums of two values (see red_stage: staged in shared memory, folded by
-// warp 0); scr holds >= 68 doubles, slots 64/65 broadcast the sums.
+// warps 0..3 and then warp 0); scr holds >= 68 doubles, slots 64/65
+// broadcast the sums.
 // block_sum2_fin also evaluates fin(x, y) -> (z, w) (a division, a square
 // root, a test) once, on the thread that completes the sums, and broadcasts it
 // with them: an FP64 division or square root is about ten FP64-pipe
@@ -86,24 +87,28 @@ template <typename F>
 __device__ __forceinline__ double4 block_sum2_fin(double a, double b, double* scr, F fin) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double* st = red_stage();
+  double* s2 = red_stage2();
   __syncthreads();
   st[threadIdx.x] = a;
   st[1024 + threadIdx.x] = b;
   __syncthreads();
+  if (warp < 4) {  // rows w, w + 4, ... of warp w
+    double pa = 0.0, pb = 0.0;
+    for (int k = warp; k < nw; k += 4) {
+      pa += st[k * 32 + lane];
+      pb += st[1024 + k * 32 + lane];
+    }
+    s2[warp * 32 + lane] = pa;
+    s2[128 + warp * 32 + lane] = pb;
+  }
+  __syncthreads();
   if (warp == 0) {
-    double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
-    int k = 0;
-    for (; k + 2 <= nw; k += 2) {
-      a0 += st[k * 32 + lane];
-      a1 += st[(k + 1) * 32 + lane];
-      b0 += st[1024 + k * 32 + lane];
-      b1 += st[1024 + (k + 1) * 32 + lane];
+    double ra = s2[lane], rb = s2[128 + lane];
+    for (int w = 1; w < (nw < 4 ? nw : 4); ++w) {
+      ra += s2[w * 32 + lane];
+      rb += s2[128 + w * 32 + lane];
     }
-    if (k < nw) {
-      a0 += st[k * 32 + lane];
-      b0 += st[1024 + k * 32 + lane];
-    }
-    const double ta = warp_sum(a0 + a1), tb = warp_sum(b0 + b1);
+    const double ta = warp_sum(ra), tb = warp_sum(rb);
     if (lane == 0) {
       const double2 zw = fin(ta, tb);
       scr[64] = ta;
@@ -199,21 +204,36 @@ __device__ __forceinline__ Sum2c block_sum2c_fin(double a, double b, int k, doub
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double* st = red_stage();
   int* sti = red_stage_i();
+  double* s2 = red_stage2();
+  int* s2i = red_stage2_i();
   __syncthreads();
   st[threadIdx.x] = a;
   st[1024 + threadIdx.x] = b;
   sti[threadIdx.x] = k;
   __syncthreads();
-  if (warp == 0) {
-    double a0 = 0.0, b0 = 0.0;
-    int k0 = 0;
-    for (int w = 0; w < nw; ++w) {
-      a0 += st[w * 32 + lane];
-      b0 += st[1024 + w * 32 + lane];
-      k0 += sti[w * 32 + lane];
+  if (warp < 4) {  // rows w, w + 4, ... of warp w
+    double pa = 0.0, pb = 0.0;
+    int pk = 0;
+    for (int w = warp; w < nw; w += 4) {
+      pa += st[w * 32 + lane];
+      pb += st[1024 + w * 32 + lane];
+      pk += sti[w * 32 + lane];
     }
-    const double ta = warp_sum(a0), tb = warp_sum(b0);
-    const int tk = warp_sum(k0);
+    s2[warp * 32 + lane] = pa;
+    s2[128 + warp * 32 + lane] = pb;
+    s2i[warp * 32 + lane] = pk;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double ra = s2[lane], rb = s2[128 + lane];
+    int rk = s2i[lane];
+    for (int w = 1; w < (nw < 4 ? nw : 4); ++w) {
+      ra += s2[w * 32 + lane];
+      rb += s2[128 + w * 32 + lane];
+      rk += s2i[w * 32 + lane];
+    }
+    const double ta = warp_sum(ra), tb = warp_sum(rb);
+    const int tk = warp_sum(rk);
     if (lane == 0) {
       const double2 zw = fin(ta, tb, tk);
       scr[64] = ta;
