@@ -129,8 +129,10 @@ mvsk_status mvsk_set_prefs(mvsk_ctx* ctx, const double lambda[4], double target)
  *   request alone), "face_products" (1: in mvsk_solve_batch the direction
  *   products run on the union of the instances' working faces; 0: on all
  *   n columns of A), "face_small" (1: when every working face of the batch
- *   has at most 128 coordinates, the direction block forms each face's
- *   Gram matrix and runs the PCG rounds on it; 0: always the products),
+ *   has at most 320 coordinates, the direction block forms each face's
+ *   Gram matrix and runs the PCG rounds on it, in a narrower launch shape
+ *   when every face has at most 128; 2: the same with the 320-coordinate
+ *   shape for every small face; 0: always the products),
  *   "line_search" (0: exact quartic step, Prop. quartic exact line search;
  *   1: Armijo backtracking on the same quartic, the paper's Armijo diagnostic
  *   of Table yand-line-search: the largest alpha_max 2^-j, j < 60, with

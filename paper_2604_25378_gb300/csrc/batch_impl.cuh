@@ -1082,6 +1082,43 @@ PassArgs pass_args_inst(const double cc[4]) {
 // One lockstep iteration of every instance (captured once per batch solve).
 mvsk_status batch_iteration_tail(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<std::array<double, 4>>& cc);
 
+// Direction block of an iteration whose working faces all have at most NM
+// coordinates (face_small.cuh): face Grams on the tensor cores, both PCG
+// rounds in shared memory, the Hutchinson correction between them.
+template <int NM>
+mvsk_status small_face_direction(mvsk_ctx* c, BatchBuf& bb, int B) {
+  const Inst& base = bb.base;
+  const int K = c->opt.probes, ncol1 = K + 1, ca = K + 1, kmax = c->opt.krylov_maxit;
+  const int Gz = oz_row_ctas(c);
+  const unsigned nch = (unsigned)((c->T + kFRows - 1) / kFRows);
+  using GT = GramTc<NM>;
+  // face Grams on the tensor cores, rows of A in GT::kSplit shares per instance
+  PROF_LAUNCH(NK_GRAM, (k_face_gram_tc<NM><<<dim3(GT::kSplit, B, (NM + 127) / 128), 256, GT::kSmem, c->stream>>>(
+                           base, bb.f_list, bb.u_AUT, c->Tp, bb.u_pos, bb.f_gp, c->err)));
+  PROF_LAUNCH(NK_GRAM, (k_face_gram_sum<NM><<<dim3(16, B), 256, 0, c->stream>>>(base, bb.f_gp, GT::kSplit, bb.f_gram)));
+  PROF_LAUNCH(NK_GRAM, (k_face_gram_finish<NM><<<B, 256, 0, c->stream>>>(base, bb.f_list, bb.f_gram, Gz)));
+  if (K > 0)
+    PROF_LAUNCH(NK_PROBE_FILL, (k_probe_fill<float><<<dim3((c->ld + 255) / 256, K, B), 256, 0, c->stream>>>(base, K)));
+  PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gz, -1)));
+  PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup_cols<float><<<dim3(ncol1, B), 512, 0, c->stream>>>(base)));
+  const size_t gsm = sizeof(float) * face_gram_words<NM>();
+  PROF_LAUNCH(NK_PCG_ROUND, (k_pcg_round_small<NM><<<dim3(ncol1, B), NM, gsm, c->stream>>>(base, 0, kmax, bb.f_list,
+                                                                                          bb.f_gram)));
+  if (K > 0) {
+    PROF_LAUNCH(NK_HUTCH, (k_face_hutch<NM><<<dim3(nch, B), 256, kHutchSmem<NM>, c->stream>>>(
+                              base, K, bb.f_list, bb.u_AUT, c->Tp, bb.u_pos, bb.f_ap)));
+    PROF_LAUNCH(NK_HUTCH, (k_face_hutch_finish<NM><<<B, 256, 0, c->stream>>>(base, bb.f_list, bb.f_ap, (int)nch)));
+  } else {
+    for (int b = 0; b < B; ++b) CU(cudaMemsetAsync(inst_at(base, b).at, 0, sizeof(double) * c->ld, c->stream));
+  }
+  PROF_LAUNCH(NK_PCG_SETUP2, (k_pcg_setup2<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca, ca / 2)));
+  PROF_LAUNCH(NK_PCG_ROUND, (k_pcg_round_small<NM><<<dim3(1, B), NM, gsm, c->stream>>>(base, ca, kmax, bb.f_list,
+                                                                                      bb.f_gram)));
+  PROF_LAUNCH(NK_ASSEMBLE, (k_assemble<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca)));
+  return MVSK_OK;
+}
+
+
 // part -1: the whole iteration; with face-restricted products (bb.umode) it
 // is captured as three graphs: part 0 the oracle block (value, gradient,
 // face, face lists, union of the faces and its gathered columns), then part 2
@@ -1138,7 +1175,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     PROF_LAUNCH(NK_FACE, (k_face<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gs)));
     if (U) {
       PROF_LAUNCH(NK_FACE_LIST, (k_face_list<<<dim3(1, B), 1024, 0, c->stream>>>(base, bb.f_list)));
-      PROF_LAUNCH(NK_FACE_LIST, (k_small_mode<<<1, 256, 0, c->stream>>>(base, B, bb.u_info)));
+      PROF_LAUNCH(NK_FACE_LIST, (k_small_mode<<<1, 256, 0, c->stream>>>(base, B, c->opt.face_small == 2, bb.u_info)));
       TRY(union_gather(c, bb, B));
       if (split && bb.u_AFU != nullptr)  // digit planes of A's columns in U (the line search along d)
         PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_split_rows_u<<<4 * c->nsm, 256, 0, c->stream>>>(
@@ -1147,32 +1184,8 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
   }
   (void)P;
   if (!dir) return MVSK_OK;
-  const unsigned nch = (unsigned)((c->T + kFRows - 1) / kFRows);
-  if (part == 2) {  // every face small: explicit face Grams, PCG rounds in shared memory
-    // face Grams on the tensor cores, rows of A in kGramSplit shares per instance
-    PROF_LAUNCH(NK_GRAM, (k_face_gram_tc<<<dim3(kGramSplit, B, (kMF + 127) / 128), 256, kGramTcSmem, c->stream>>>(
-                             base, bb.f_list, bb.u_AUT, c->Tp, bb.u_pos, bb.f_gp, c->err)));
-    PROF_LAUNCH(NK_GRAM, (k_face_gram_sum<<<dim3(16, B), 256, 0, c->stream>>>(base, bb.f_gp, kGramSplit, bb.f_gram)));
-    PROF_LAUNCH(NK_GRAM, (k_face_gram_finish<<<B, 256, 0, c->stream>>>(base, bb.f_list, bb.f_gram, Gz)));
-    if (K > 0)
-      PROF_LAUNCH(NK_PROBE_FILL,
-                  (k_probe_fill<float><<<dim3((c->ld + 255) / 256, K, B), 256, 0, c->stream>>>(base, K)));
-    PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gz, -1)));
-    PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup_cols<float><<<dim3(ncol1, B), 512, 0, c->stream>>>(base)));
-    const size_t gsm = sizeof(float) * face_tri_max_words();
-    PROF_LAUNCH(NK_PCG_ROUND, (k_pcg_round_small<<<dim3(ncol1, B), kMF, gsm, c->stream>>>(base, 0, kmax, bb.f_list,
-                                                                                          bb.f_gram)));
-    if (K > 0) {
-      PROF_LAUNCH(NK_HUTCH, (k_face_hutch<<<dim3(nch, B), 256, kHutchSmem, c->stream>>>(base, K, bb.f_list, bb.u_AUT, c->Tp,
-                                                                                 bb.u_pos, bb.f_ap)));
-      PROF_LAUNCH(NK_HUTCH, (k_face_hutch_finish<<<B, 256, 0, c->stream>>>(base, bb.f_list, bb.f_ap, (int)nch)));
-    } else {
-      for (int b = 0; b < B; ++b) CU(cudaMemsetAsync(inst_at(base, b).at, 0, sizeof(double) * c->ld, c->stream));
-    }
-    PROF_LAUNCH(NK_PCG_SETUP2, (k_pcg_setup2<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca, ca / 2)));
-    PROF_LAUNCH(NK_PCG_ROUND, (k_pcg_round_small<<<dim3(1, B), kMF, gsm, c->stream>>>(base, ca, kmax, bb.f_list,
-                                                                                      bb.f_gram)));
-    PROF_LAUNCH(NK_ASSEMBLE, (k_assemble<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca)));
+  if (part >= 2) {  // every face small: explicit face Grams, PCG rounds in shared memory
+    TRY(part == 3 ? small_face_direction<kMFt>(c, bb, B) : small_face_direction<kMF>(c, bb, B));
     return batch_iteration_tail(c, bb, B, cc);
   }
   if (U) {
@@ -1418,10 +1431,15 @@ mvsk_status ensure_ubuf(mvsk_ctx* c, BatchBuf& bb) {
     TRY(dalloc(c, &p, sizeof(__nv_bfloat16) * kOzS * (size_t)c->oz.MpF * ld));
     bb.u_AFU = (__nv_bfloat16*)p;
   }
-  CU(cudaFuncSetAttribute(k_pcg_round_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)(sizeof(float) * face_tri_max_words())));
-  CU(cudaFuncSetAttribute(k_face_hutch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHutchSmem));
-  CU(cudaFuncSetAttribute(k_face_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramTcSmem));
+  CU(cudaFuncSetAttribute(k_pcg_round_small<kMF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)(sizeof(float) * face_gram_words<kMF>())));
+  CU(cudaFuncSetAttribute(k_pcg_round_small<kMFt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)(sizeof(float) * face_gram_words<kMFt>())));
+  CU(cudaFuncSetAttribute(k_face_hutch<kMF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHutchSmem<kMF>));
+  CU(cudaFuncSetAttribute(k_face_hutch<kMFt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHutchSmem<kMFt>));
+  CU(cudaFuncSetAttribute(k_face_gram_tc<kMF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GramTc<kMF>::kSmem));
+  CU(cudaFuncSetAttribute(k_face_gram_tc<kMFt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)GramTc<kMFt>::kSmem));
   return MVSK_OK;
 }
 
@@ -1507,7 +1525,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       if (e) cudaGraphExecDestroy(e);
     }
   };
-  ItGraph gfull, ghead, glarge, gsmall;
+  ItGraph gfull, ghead, glarge, gsmall, gnarrow;
   auto capture = [&](int part, ItGraph& gr) -> mvsk_status {
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -1532,6 +1550,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     TRY(capture(0, ghead));
     TRY(capture(1, glarge));
     TRY(capture(2, gsmall));
+    TRY(capture(3, gnarrow));
   } else {
     TRY(capture(-1, gfull));
   }
@@ -1785,7 +1804,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
         CU(cudaMemcpyAsync(&small_dir, bb.u_info + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         TRY(sync(c));
       }
-      TRY(replay(small_dir ? gsmall : glarge));
+      TRY(replay(small_dir == 2 ? gnarrow : (small_dir == 1 ? gsmall : glarge)));
     } else {
       TRY(replay(gfull));
     }

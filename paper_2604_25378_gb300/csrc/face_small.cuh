@@ -18,6 +18,7 @@
 #pragma once
 
 constexpr int kMF = 320;       // largest face handled here (one coordinate per thread of a PCG CTA)
+constexpr int kMFt = 128;      // faces up to this size take the narrow instantiation (NM = kMFt)
 constexpr int kFRows = 480;    // rows of A per CTA of the Gram and Hutchinson passes
 constexpr int kFTile = 32;     // rows staged in shared memory at a time
 
@@ -57,16 +58,22 @@ __global__ void __launch_bounds__(1024) k_face_list(Inst base, int* fl_base) {
   if (threadIdx.x == 1023) s.si[SI_FCNT] = p;
 }
 
-// info[2] = 1 when every instance that needs a direction this iteration has a
-// face of at most kMF coordinates (the small-face block runs), else 0.
-__global__ void k_small_mode(Inst base, int B, int* info) {
-  int big = 0;
+// info[2] = 2 when every instance that needs a direction this iteration has a
+// face of at most kMFt coordinates (the narrow small-face block runs), else 1
+// when every such face has at most kMF (the wide one), else 0.  wide != 0
+// takes the wide block for every small face.
+__global__ void k_small_mode(Inst base, int B, int wide, int* info) {
+  int big = 0, mid = 0;
   for (int b = threadIdx.x; b < B; b += blockDim.x) {
     const int* si = base.si + (size_t)b * kSI;
-    if (si[SI_DONE] == 0 && si[SI_SKIPDIR] == 0 && si[SI_FCNT] > kMF) big = 1;
+    if (si[SI_DONE] == 0 && si[SI_SKIPDIR] == 0) {
+      big |= si[SI_FCNT] > kMF;
+      mid |= si[SI_FCNT] > kMFt;
+    }
   }
   big = __syncthreads_or(big);
-  if (threadIdx.x == 0) info[2] = big ? 0 : 1;
+  mid = __syncthreads_or(mid | wide);
+  if (threadIdx.x == 0) info[2] = big ? 0 : (mid ? 1 : 2);
 }
 
 // Face Grams on the tensor cores.  CTA (x, b, t) accumulates over the 64-row
@@ -87,11 +94,19 @@ __global__ void k_small_mode(Inst base, int B, int* info) {
 // adds.  Dynamic shared memory kGramTcSmem; waits are bounded (err |=
 // kErrWaitTimeout on expiry).
 constexpr int kGTBytesA = 128 * 128;  // one M tile of 128 rows x 64 BF16
-constexpr int kGTBytesB = kMF * 128;  // up to kMF rows x 64 BF16 (one of Qhi, Qlo)
-constexpr int kGTChunks = (((kMF + 127) / 128) * 128 > kMF ? ((kMF + 127) / 128) * 128 : kMF) * 8 / 256;
-constexpr size_t kGramTcSmem = 1024 + (size_t)2 * (kGTBytesA + 2 * kGTBytesB) + 256;
-constexpr int kGramSplit = 2;  // shares of the rows of A per instance
-static_assert(kMF % 16 == 0 && kMF <= 512, "the N extent of the face Gram MMA");
+// Shapes of the instantiation for faces of at most NM coordinates.
+template <int NM>
+struct GramTc {
+  static constexpr int kBytesB = NM * 128;              // up to NM rows x 64 BF16 (one of Qhi, Qlo)
+  static constexpr int kChunks = ((NM + 127) / 128) * 128 * 8 / 256;  // 16-byte chunks per thread and block
+  static constexpr size_t kSmem = 1024 + (size_t)2 * (kGTBytesA + 2 * kBytesB) + 256;
+  static constexpr int kTmemCols = NM <= 128 ? 128 : (NM <= 256 ? 256 : 512);
+  static constexpr int kSplit = NM <= kMFt ? 4 : 2;     // shares of the rows of A per instance
+  static constexpr int kMinBlocks = NM <= kMFt ? 2 : 1;  // resident CTAs per SM (shared memory)
+  static_assert(NM % 16 == 0 && NM <= 512, "the N extent of the face Gram MMA");
+};
+constexpr int kGramSplit = GramTc<kMF>::kSplit;
+static_assert(GramTc<kMFt>::kSplit * kMFt * kMFt <= kGramSplit * kMF * kMF, "partial Grams of the narrow block");
 
 __device__ __forceinline__ int sw128_off(int r, int j) {
   return ((r >> 3) << 10) + ((r & 7) << 7) + (((j ^ r) & 7) << 4);
@@ -115,13 +130,17 @@ __device__ __forceinline__ void bf16x8_scale2(uint4 v, const float* h, uint4* hi
   *lo = make_uint4(c[0], c[1], c[2], c[3]);
 }
 
-__global__ void __launch_bounds__(256, 1) k_face_gram_tc(Inst base, const int* fl_base, const __nv_bfloat16* AUT,
-                                                         long long ldt, const int* upos, float* gp, int* err) {
+template <int NM>
+__global__ void __launch_bounds__(256, GramTc<NM>::kMinBlocks)
+    k_face_gram_tc(Inst base, const int* fl_base, const __nv_bfloat16* AUT, long long ldt, const int* upos, float* gp,
+                   int* err) {
+  using G = GramTc<NM>;
+  constexpr int kGTBytesB = G::kBytesB, kGTChunks = G::kChunks;
   const int b = blockIdx.y, mt = blockIdx.z;
   const Inst s = inst_at(base, b);
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
   const int m = s.si[SI_FCNT];
-  if (m > kMF || m <= 0 || mt * 128 >= m) return;
+  if (m > NM || m <= 0 || mt * 128 >= m) return;
   const int n16 = (m + 15) & ~15, mp8 = (m + 7) & ~7;
   const int rows = n16 > mt * 128 + 128 ? n16 : mt * 128 + 128;  // rows staged: Q's and this tile's
   const long long T = s.T;
@@ -150,7 +169,7 @@ __global__ void __launch_bounds__(256, 1) k_face_gram_tc(Inst base, const int* f
     fence_barrier_init();
     s_abort = 0;
   }
-  if (warp == 0) tmem_alloc(tslot, 512);
+  if (warp == 0) tmem_alloc(tslot, G::kTmemCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -240,7 +259,7 @@ __global__ void __launch_bounds__(256, 1) k_face_gram_tc(Inst base, const int* f
     const int q = warp & 3, half = ((n16 / 2) + 15) & ~15;
     const int k = mt * 128 + q * 32 + lane;
     const int ca = warp < 4 ? 0 : half, cb = warp < 4 ? half : n16;
-    float* out = gp + ((size_t)b * gridDim.x + blockIdx.x) * kMF * kMF;
+    float* out = gp + ((size_t)b * gridDim.x + blockIdx.x) * NM * NM;
     for (int c0 = ca; c0 < cb; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
@@ -254,32 +273,33 @@ __global__ void __launch_bounds__(256, 1) k_face_gram_tc(Inst base, const int* f
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, 512);
+  if (warp == 0) tmem_dealloc(tmem, G::kTmemCols);
 }
 
 // Face Gram of instance blockIdx.y from the chunk partials (added in chunk
 // order): entries e = k mp + l of the upper triangle handled by CTA
 // blockIdx.x (grid-stride), G[k][l] = G[l][k] = T^-1 sum, into
-// gram[b * kMF * kMF] (row stride kMF).
+// gram[b * NM * NM] (row stride NM).
+template <int NM>
 __global__ void __launch_bounds__(256) k_face_gram_sum(Inst base, const float* gp, int nchunk, float* gram) {
   const int b = blockIdx.y;
   const Inst s = inst_at(base, b);
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
   const int m = s.si[SI_FCNT];
-  if (m > kMF) return;
+  if (m > NM) return;
   const int mp = 8 * ((m + 7) / 8);
-  float* Gm = gram + (size_t)b * kMF * kMF;
+  float* Gm = gram + (size_t)b * NM * NM;
   const float invT = (float)s.sd[SD_INVT];
-  const float* src0 = gp + (size_t)b * nchunk * kMF * kMF;
+  const float* src0 = gp + (size_t)b * nchunk * NM * NM;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
     const int k = e / m, l = e - k * m;
     if (k > l) continue;
     const float* src = src0 + (size_t)k * mp + l;
     float v = 0.f;
-    for (int c = 0; c < nchunk; ++c) v += src[(size_t)c * kMF * kMF];
+    for (int c = 0; c < nchunk; ++c) v += src[(size_t)c * NM * NM];
     v *= invT;
-    Gm[(size_t)k * kMF + l] = v;
-    Gm[(size_t)l * kMF + k] = v;
+    Gm[(size_t)k * NM + l] = v;
+    Gm[(size_t)l * NM + k] = v;
   }
 }
 
@@ -287,20 +307,21 @@ __global__ void __launch_bounds__(256) k_face_gram_sum(Inst base, const float* g
 // the scalar partials of the diagonal block: spart[0] = T nuhat^T G nuhat,
 // spart[1] = T 1_F^T G 1_F, spart[2 .. 2 G) = 0 (k_pcg_setup adds G pairs).
 // 256 threads.
+template <int NM>
 __global__ void __launch_bounds__(256) k_face_gram_finish(Inst base, const int* fl_base, const float* gram, int G) {
   const int b = blockIdx.x;
   Inst s = inst_at(base, b);
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
   const int m = s.si[SI_FCNT];
-  if (m > kMF) return;
+  if (m > NM) return;
   const int* fl = fl_base + (size_t)b * s.vs;
-  const float* Gm = gram + (size_t)b * kMF * kMF;
+  const float* Gm = gram + (size_t)b * NM * NM;
   for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
     s.Gnu[i] = 0.0;
     s.diagG[i] = 0.0;
   }
   __syncthreads();
-  __shared__ float nh[kMF];
+  __shared__ float nh[NM];
   __shared__ float red[2][8];
   for (int k = threadIdx.x; k < m; k += blockDim.x) nh[k] = (float)s.nuhat[fl[k]];
   __syncthreads();
@@ -308,12 +329,12 @@ __global__ void __launch_bounds__(256) k_face_gram_finish(Inst base, const int* 
   for (int k = threadIdx.x; k < m; k += blockDim.x) {
     float gv = 0.f, g1 = 0.f;
     for (int l = 0; l < m; ++l) {
-      const float gk = Gm[(size_t)k * kMF + l];
+      const float gk = Gm[(size_t)k * NM + l];
       gv = fmaf(gk, nh[l], gv);
       g1 += gk;
     }
     s.Gnu[fl[k]] = (double)gv;
-    s.diagG[fl[k]] = (double)Gm[(size_t)k * kMF + k];
+    s.diagG[fl[k]] = (double)Gm[(size_t)k * NM + k];
     sn = fmaf(nh[k], gv, sn);
     s1 += g1;
   }
@@ -338,8 +359,9 @@ __global__ void __launch_bounds__(256) k_face_gram_finish(Inst base, const int* 
   }
 }
 
-// Sums of six floats over a CTA of kMF threads (kMF / 32 warps), added in
+// Sums of six floats over a CTA of NM threads (NM / 32 warps), added in
 // warp order so that every thread holds the same totals.
+template <int NM>
 __device__ __forceinline__ void cta_sum6(float (&v)[6], float (*scr)[6]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -353,7 +375,7 @@ __device__ __forceinline__ void cta_sum6(float (&v)[6], float (*scr)[6]) {
   for (int q = 0; q < 6; ++q) {
     float t = 0.f;
 #pragma unroll
-    for (int w = 0; w < kMF / 32; ++w) t += scr[w][q];
+    for (int w = 0; w < NM / 32; ++w) t += scr[w][q];
     v[q] = t;
   }
 }
@@ -364,7 +386,7 @@ __device__ __forceinline__ void cta_sum6(float (&v)[6], float (*scr)[6]) {
 // congruent to 2 (i + 1) mod 32.  Then, for a fixed j, threads i (= 32
 // consecutive rows) reading (min(i, j), max(i, j)) hit 32 distinct banks:
 // start(j) + i - j for i > j, start(i) + j - i = 2i + j (mod 32) for i <= j.
-// Words used for m rows (the shared-memory size of k_pcg_round_small).
+// Words used for m rows.
 __host__ __device__ constexpr int face_tri_words(int m) {
   int st = 0;
   for (int i = 0; i < m; ++i) {
@@ -373,37 +395,45 @@ __host__ __device__ constexpr int face_tri_words(int m) {
   }
   return st;
 }
-__host__ __device__ constexpr int face_tri_max_words() {
+__host__ __device__ constexpr int face_tri_max_words(int nm) {
   int w = 0;
-  for (int m = 1; m <= kMF; ++m) w = face_tri_words(m) > w ? face_tri_words(m) : w;
+  for (int m = 1; m <= nm; ++m) w = face_tri_words(m) > w ? face_tri_words(m) : w;
   return w;
+}
+// Shared-memory words of k_pcg_round_small<NM>: the full matrix of any face
+// of at most NM coordinates when that fits in the upper triangle's space of
+// the widest block, else that space.
+template <int NM>
+__host__ __device__ constexpr int face_gram_words() {
+  return NM * (NM + 1) <= face_tri_max_words(kMF) ? NM * (NM + 1) : face_tri_max_words(NM);
 }
 
 // A whole PCG round of column c = c0 + blockIdx.x of instance blockIdx.y on
-// its face (m <= kMF coordinates, one per thread), with G_F in shared memory:
+// its face (m <= NM coordinates, one per thread), with G_F in shared memory:
 // the full matrix (rows m + 1 words apart) when it fits, else the upper
 // triangle in the layout above (the full matrix of a 320-coordinate face does
 // not fit): the recurrence of the batched step (k_pcg_step_f) with Q = G_F p
 // instead of the tensor-core products, from the state k_pcg_setup_cols (or
 // k_pcg_setup2) left (X = 0, R = B, P = Z, rz, rhsn, active flag), up to the
 // iteration budget; the final X, R, P and rz are written back on the face.
-__global__ void __launch_bounds__(kMF) k_pcg_round_small(Inst base, int c0, int kmaxit, const int* fl_base,
-                                                         const float* gram) {
+template <int NM>
+__global__ void __launch_bounds__(NM) k_pcg_round_small(Inst base, int c0, int kmaxit, const int* fl_base,
+                                                        const float* gram) {
   const int b = blockIdx.y, c = c0 + blockIdx.x;
   Inst s = inst_at(base, b);
   int* SI = s.si;
   if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
   const int m = SI[SI_FCNT];
-  if (m > kMF || SI[SI_ACT + c] == 0) return;
+  if (m > NM || SI[SI_ACT + c] == 0) return;
   extern __shared__ float gs[];  // upper triangle of G_F: element (i, j) at rs[i] + j (j >= i)
-  __shared__ float pv[kMF];
-  __shared__ int rs[kMF];
-  __shared__ float scr[kMF / 32][6];
+  __shared__ float pv[NM];
+  __shared__ int rs[NM];
+  __shared__ float scr[NM / 32][6];
   const int* fl = fl_base + (size_t)b * s.vs;
-  const float* Gm = gram + (size_t)b * kMF * kMF;
+  const float* Gm = gram + (size_t)b * NM * NM;
   // faces whose full matrix fits (rows m + 1 words apart: distinct banks)
   // keep it; larger ones keep the upper triangle
-  const bool full = m * (m + 1) <= face_tri_max_words();
+  const bool full = m * (m + 1) <= face_gram_words<NM>();
   if (threadIdx.x == 0) {
     int st = 0;
     for (int i = 0; i < m; ++i) {
@@ -415,7 +445,7 @@ __global__ void __launch_bounds__(kMF) k_pcg_round_small(Inst base, int c0, int 
   __syncthreads();
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int i = e / m, j = e - i * m;
-    if (full || j >= i) gs[rs[i] + j] = Gm[(size_t)i * kMF + j];
+    if (full || j >= i) gs[rs[i] + j] = Gm[(size_t)i * NM + j];
   }
   const int ld = s.ld, k = threadIdx.x;
   const bool on = k < m;
@@ -451,7 +481,7 @@ __global__ void __launch_bounds__(kMF) k_pcg_round_small(Inst base, int c0, int 
       }
     }
     float a6[6] = {mf * q, nh * q, p * mf * q, p * mf, p * nh, p * p};
-    cta_sum6(a6, scr);
+    cta_sum6<NM>(a6, scr);
     const float qmean = a6[0] / fm, ry = a6[1];
     const float pq = a6[2] - qmean * a6[3] - ry * a6[4] + lam * a6[5];
     if (!(pq > 0.f)) {
@@ -464,7 +494,7 @@ __global__ void __launch_bounds__(kMF) k_pcg_round_small(Inst base, int c0, int 
     r -= al * qq;
     const float t = r / dg;
     float b6[6] = {r * r, mf * t, nh * t, r * mf * t, r * mf, r * nh};
-    cta_sum6(b6, scr);
+    cta_sum6<NM>(b6, scr);
     its += 1;
     if (sqrt((double)b6[0]) <= ktol) {
       act = 0;
@@ -502,37 +532,38 @@ __global__ void __launch_bounds__(kMF) k_pcg_round_small(Inst base, int c0, int 
 // kFTile at a time from the gathered rows of A^T (AUT, row upos[fl[l]],
 // contiguous in t); eight threads per row split the face coordinates
 // (l = j mod 8) and add their 2K partial products by shuffles.
-// Out: ap[(b * nchunk + x) * kMF + l].
+// Out: ap[(b * nchunk + x) * NM + l].
+template <int NM>
 __global__ void __launch_bounds__(256) k_face_hutch(Inst base, int K, const int* fl_base, const __nv_bfloat16* AUT,
                                                     long long ldt, const int* upos, float* ap) {
   const int b = blockIdx.y;
   const Inst s = inst_at(base, b);
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
   const int m = s.si[SI_FCNT];
-  if (m > kMF) return;
+  if (m > NM) return;
   constexpr int kW = 16;  // 2K <= 16: the batched path takes at most 8 probes
   // W, row l: (X_1, B_1, X_2, B_2, ...); rows 20 floats apart and tile rows
-  // kMF + 8 apart, so that the threads of a warp hit distinct banks
-  __shared__ __align__(16) float wt[kMF][kW + 4];
-  extern __shared__ __align__(16) float hsm[];  // the row tile: kFTile rows, kMF + 8 apart (kHutchSmem bytes)
-  float (*a)[kMF + 8] = reinterpret_cast<float (*)[kMF + 8]>(hsm);
+  // NM + 8 apart, so that the threads of a warp hit distinct banks
+  __shared__ __align__(16) float wt[NM][kW + 4];
+  extern __shared__ __align__(16) float hsm[];  // the row tile: kFTile rows, NM + 8 apart (kHutchSmem<NM> bytes)
+  float (*a)[NM + 8] = reinterpret_cast<float (*)[NM + 8]>(hsm);
   __shared__ float sw[kFTile];
-  __shared__ int col[kMF];
+  __shared__ int col[NM];
   const int* fl = fl_base + (size_t)b * s.vs;
   const int ld = s.ld, K2 = 2 * K;
-  for (int e = threadIdx.x; e < kMF * kW; e += blockDim.x) {
+  for (int e = threadIdx.x; e < NM * kW; e += blockDim.x) {
     const int l = e / kW, q = e - l * kW;
     float v = 0.f;
     if (l < m && q < K2) v = kcol<float>((q & 1) ? s.Bv : s.X, 1 + (q >> 1), ld)[fl[l]];
     wt[l][q] = v;
   }
-  for (int l = threadIdx.x; l < kMF; l += blockDim.x) col[l] = l < m ? upos[fl[l]] : -1;
+  for (int l = threadIdx.x; l < NM; l += blockDim.x) col[l] = l < m ? upos[fl[l]] : -1;
   const float c3 = (float)s.sd[SD_C3], c4 = (float)s.sd[SD_C4];
   const long long T = s.T, t0 = (long long)blockIdx.x * kFRows, t1 = t0 + kFRows < T ? t0 + kFRows : T;
   const int r = threadIdx.x >> 3, j = threadIdx.x & 7;  // row of the tile, face-coordinate slice
-  float bacc[(kMF + 255) / 256];  // back-projection of coordinates threadIdx.x + 256 e
+  float bacc[(NM + 255) / 256];  // back-projection of coordinates threadIdx.x + 256 e
 #pragma unroll
-  for (int e = 0; e < (kMF + 255) / 256; ++e) bacc[e] = 0.f;
+  for (int e = 0; e < (NM + 255) / 256; ++e) bacc[e] = 0.f;
   __syncthreads();
   for (long long tb = t0; tb < t1; tb += kFTile) {
     const int rows = (int)(t1 - tb < kFTile ? t1 - tb : kFTile);
@@ -583,7 +614,7 @@ __global__ void __launch_bounds__(256) k_face_hutch(Inst base, int K, const int*
     }
     __syncthreads();
 #pragma unroll
-    for (int e = 0; e < (kMF + 255) / 256; ++e) {
+    for (int e = 0; e < (NM + 255) / 256; ++e) {
       const int l = (int)threadIdx.x + 256 * e;
       if (l < m)
         for (int rr = 0; rr < rows; ++rr) bacc[e] = fmaf(sw[rr], a[rr][l], bacc[e]);
@@ -591,27 +622,29 @@ __global__ void __launch_bounds__(256) k_face_hutch(Inst base, int K, const int*
     __syncthreads();
   }
 #pragma unroll
-  for (int e = 0; e < (kMF + 255) / 256; ++e) {
+  for (int e = 0; e < (NM + 255) / 256; ++e) {
     const int l = (int)threadIdx.x + 256 * e;
-    if (l < m) ap[((size_t)b * gridDim.x + blockIdx.x) * kMF + l] = bacc[e];
+    if (l < m) ap[((size_t)b * gridDim.x + blockIdx.x) * NM + l] = bacc[e];
   }
 }
-constexpr size_t kHutchSmem = sizeof(float) * kFTile * (kMF + 8);
+template <int NM>
+constexpr size_t kHutchSmem = sizeof(float) * kFTile * (NM + 8);
 
 // at_b = T^-1 sum over the chunks (fixed order) on the face, zero elsewhere.
+template <int NM>
 __global__ void k_face_hutch_finish(Inst base, const int* fl_base, const float* ap, int nchunk) {
   const int b = blockIdx.x;
   Inst s = inst_at(base, b);
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
   const int m = s.si[SI_FCNT];
-  if (m > kMF) return;
+  if (m > NM) return;
   const int* fl = fl_base + (size_t)b * s.vs;
   for (int i = threadIdx.x; i < s.ld; i += blockDim.x) s.at[i] = 0.0;
   __syncthreads();
   const double invT = s.sd[SD_INVT];
   for (int l = threadIdx.x; l < m; l += blockDim.x) {
     float v = 0.f;
-    for (int c = 0; c < nchunk; ++c) v += ap[((size_t)b * nchunk + c) * kMF + l];
+    for (int c = 0; c < nchunk; ++c) v += ap[((size_t)b * nchunk + c) * NM + l];
     s.at[fl[l]] = invT * (double)v;
   }
 }

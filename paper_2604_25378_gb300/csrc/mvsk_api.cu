@@ -1509,7 +1509,7 @@ mvsk_status mvsk_set_option(mvsk_ctx* c, const char* key, double v) {
   else if (k == "line_search" && cnt(v, 0, 1)) o.line_search = (int)v;
   else if (k == "group_calibration" && cnt(v, 0, 1)) o.group_cal = (int)v;
   else if (k == "face_products" && cnt(v, 0, 1)) o.face_products = (int)v;
-  else if (k == "face_small" && cnt(v, 0, 1)) o.face_small = (int)v;
+  else if (k == "face_small" && cnt(v, 0, 2)) o.face_small = (int)v;
   else return fail(MVSK_EINVAL, "unknown option or bad value: %s = %g", key, v);
   if (c->prefs_set && k == "pref_scaling") mvsk_set_prefs(c, c->lam, c->target);
   return MVSK_OK;

@@ -344,12 +344,14 @@ def test_group_calibration_matches_per_request():
 
 
 def test_small_face_direction_matches_products():
-    """Once every working face of a batch has at most 128 coordinates, the
+    """Once every working face of a batch has at most 320 coordinates, the
     direction block forms each face's Gram matrix and runs both PCG rounds
-    on it (option face_small, on by default) instead of the tensor-core
-    products on the union of the faces: both forms must reach the same
-    minimisers (judged by the oracle's KKT residual), and the products-only
-    form must agree with the oracle's own minimiser under the certificate."""
+    on it (option face_small, on by default; in the narrow launch shape while
+    every face has at most 128, option value 2 keeps the wide one) instead of
+    the tensor-core products on the union of the faces: every form must reach
+    the same minimisers (judged by the oracle's KKT residual), and the
+    products-only form must agree with the oracle's own minimiser under the
+    certificate."""
     import paper_2604_25378_gb300 as m
     R = panels.garch_sector_panel(600, 6000, 41)
     mu, A = O.centre(R)
@@ -359,15 +361,21 @@ def test_small_face_direction_matches_products():
     W1, inf1 = ctx.solve_batch(lams, tg, m.PCG, 1e-10)
     ctx.set_option("face_small", 0)
     W0, inf0 = ctx.solve_batch(lams, tg, m.PCG, 1e-10)
+    ctx.set_option("face_small", 2)
+    W2, inf2 = ctx.solve_batch(lams, tg, m.PCG, 1e-10)
     ctx.set_option("face_small", 1)
     x0 = np.full(600, 1.0 / 600)
     for b in range(len(lams)):
         assert inf1[b]["status"] == "ok" and inf0[b]["status"] == "ok", (b, inf1[b], inf0[b])
+        assert inf2[b]["status"] == "ok", (b, inf2[b])
         cg = np.asarray(inf1[b]["c"])
         k0 = O.kkt_residual(x0, O.gradient(A, mu, cg, x0), 1e-8)
         assert O.kkt_residual(W1[b], O.gradient(A, mu, cg, W1[b]), 1e-8) <= 1.5e-10 * k0, b
+        cg2 = np.asarray(inf2[b]["c"])
+        assert O.kkt_residual(W2[b], O.gradient(A, mu, cg2, W2[b]), 1e-8) <= 1.5e-10 * k0, b
         if O.convexity_certificate(cg):
             assert np.max(np.abs(W1[b] - W0[b])) <= 1e-8, (b, np.max(np.abs(W1[b] - W0[b])))
+            assert np.max(np.abs(W1[b] - W2[b])) <= 1e-8, (b, np.max(np.abs(W1[b] - W2[b])))
     c = O.scale_preferences(lams[0], A, "standardised")
     x_ref, _ = O.solve(A, mu, c, "pcg", 1e-12)
     assert np.max(np.abs(W1[0] - x_ref)) <= 1e-9
