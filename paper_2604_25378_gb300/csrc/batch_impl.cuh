@@ -690,7 +690,7 @@ mvsk_status batch_alloc(mvsk_ctx* c, BatchBuf& bb, int B) {
   TRY(get(sizeof(double) * 2 * Bs, &p));
   bb.kq_dev = p;
   {  // small-face direction block
-    const size_t nch = (size_t)((c->T + kFRows - 1) / kFRows);
+    const size_t nch = (size_t)kHutchChunks(c->T);
     TRY(get(sizeof(int) * ld * Bs, &p));
     bb.f_list = (int*)p;
     TRY(get(sizeof(float) * kGramSplit * kMF * kMF * Bs, &p));  // partial Grams, one slab per share of T
@@ -1090,7 +1090,7 @@ mvsk_status small_face_direction(mvsk_ctx* c, BatchBuf& bb, int B) {
   const Inst& base = bb.base;
   const int K = c->opt.probes, ncol1 = K + 1, ca = K + 1, kmax = c->opt.krylov_maxit;
   const int Gz = oz_row_ctas(c);
-  const unsigned nch = (unsigned)((c->T + kFRows - 1) / kFRows);
+  const unsigned nch = (unsigned)kHutchChunks(c->T);
   using GT = GramTc<NM>;
   // face Grams on the tensor cores, rows of A in GT::kSplit shares per instance
   PROF_LAUNCH(NK_GRAM, (k_face_gram_tc<NM><<<dim3(GT::kSplit, B, (NM + 127) / 128), 256, GT::kSmem, c->stream>>>(
@@ -1105,8 +1105,8 @@ mvsk_status small_face_direction(mvsk_ctx* c, BatchBuf& bb, int B) {
   PROF_LAUNCH(NK_PCG_ROUND, (k_pcg_round_small<NM><<<dim3(ncol1, B), NM, gsm, c->stream>>>(base, 0, kmax, bb.f_list,
                                                                                           bb.f_gram)));
   if (K > 0) {
-    PROF_LAUNCH(NK_HUTCH, (k_face_hutch<NM><<<dim3(nch, B), 256, kHutchSmem<NM>, c->stream>>>(
-                              base, K, bb.f_list, bb.u_AUT, c->Tp, bb.u_pos, bb.f_ap)));
+    PROF_LAUNCH(NK_HUTCH, (k_face_hutch<NM><<<dim3(nch, B), 256, HutchTc<NM>::kSmem, c->stream>>>(
+                              base, K, bb.f_list, bb.u_AUT, c->Tp, bb.u_pos, bb.f_ap, c->err)));
     PROF_LAUNCH(NK_HUTCH, (k_face_hutch_finish<NM><<<B, 256, 0, c->stream>>>(base, bb.f_list, bb.f_ap, (int)nch)));
   } else {
     for (int b = 0; b < B; ++b) CU(cudaMemsetAsync(inst_at(base, b).at, 0, sizeof(double) * c->ld, c->stream));
@@ -1115,6 +1115,17 @@ mvsk_status small_face_direction(mvsk_ctx* c, BatchBuf& bb, int B) {
   PROF_LAUNCH(NK_PCG_ROUND, (k_pcg_round_small<NM><<<dim3(1, B), NM, gsm, c->stream>>>(base, ca, kmax, bb.f_list,
                                                                                       bb.f_gram)));
   PROF_LAUNCH(NK_ASSEMBLE, (k_assemble<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca)));
+  return MVSK_OK;
+}
+
+// The Hutchinson correction of the small-face block alone (NM-coordinate
+// launch shape), from the face lists and union gather already in place.
+template <int NM>
+mvsk_status small_face_third(mvsk_ctx* c, BatchBuf& bb, int B, int K) {
+  const unsigned nch = (unsigned)kHutchChunks(c->T);
+  PROF_LAUNCH(NK_HUTCH, (k_face_hutch<NM><<<dim3(nch, B), 256, HutchTc<NM>::kSmem, c->stream>>>(
+                            bb.base, K, bb.f_list, bb.u_AUT, c->Tp, bb.u_pos, bb.f_ap, c->err)));
+  PROF_LAUNCH(NK_HUTCH, (k_face_hutch_finish<NM><<<B, 256, 0, c->stream>>>(bb.base, bb.f_list, bb.f_ap, (int)nch)));
   return MVSK_OK;
 }
 
@@ -1435,8 +1446,10 @@ mvsk_status ensure_ubuf(mvsk_ctx* c, BatchBuf& bb) {
                           (int)(sizeof(float) * face_gram_words<kMF>())));
   CU(cudaFuncSetAttribute(k_pcg_round_small<kMFt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)(sizeof(float) * face_gram_words<kMFt>())));
-  CU(cudaFuncSetAttribute(k_face_hutch<kMF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHutchSmem<kMF>));
-  CU(cudaFuncSetAttribute(k_face_hutch<kMFt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHutchSmem<kMFt>));
+  CU(cudaFuncSetAttribute(k_face_hutch<kMF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)HutchTc<kMF>::kSmem));
+  CU(cudaFuncSetAttribute(k_face_hutch<kMFt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)HutchTc<kMFt>::kSmem));
   CU(cudaFuncSetAttribute(k_face_gram_tc<kMF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GramTc<kMF>::kSmem));
   CU(cudaFuncSetAttribute(k_face_gram_tc<kMFt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)GramTc<kMFt>::kSmem));
@@ -2245,7 +2258,22 @@ mvsk_status batch_third_export(mvsk_ctx* c, int B, const double* C, const double
     const int one = 1;
     TRY(u_prepare(c, bb, B, &one, 1, K));
     TRY(union_gather(c, bb, B));
-    TRY(third_tc_batch_u(c, bb, B, K));
+    int mode = 0;  // the small-face block's kernels when every face allows them (option face_small)
+    if (c->opt.face_small) {
+      k_face_list<<<dim3(1, B), 1024, 0, c->stream>>>(base, bb.f_list);
+      k_small_mode<<<1, 256, 0, c->stream>>>(base, B, c->opt.face_small == 2, bb.u_info);
+      c->launches += 2;
+      CU(cudaGetLastError());
+      CU(cudaMemcpyAsync(&mode, bb.u_info + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      TRY(sync(c));
+    }
+    if (mode == 2) {
+      TRY(small_face_third<kMFt>(c, bb, B, K));
+    } else if (mode == 1) {
+      TRY(small_face_third<kMF>(c, bb, B, K));
+    } else {
+      TRY(third_tc_batch_u(c, bb, B, K));
+    }
   } else {
     TRY(third_tc_batch(c, bb, B, K));
   }

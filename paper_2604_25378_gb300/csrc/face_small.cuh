@@ -19,8 +19,6 @@
 
 constexpr int kMF = 320;       // largest face handled here (one coordinate per thread of a PCG CTA)
 constexpr int kMFt = 128;      // faces up to this size take the narrow instantiation (NM = kMFt)
-constexpr int kFRows = 480;    // rows of A per CTA of the Gram and Hutchinson passes
-constexpr int kFTile = 32;     // rows staged in shared memory at a time
 
 // Face list of instance blockIdx.y: fl[k] = i for the coordinates of its
 // working face (maskF = 1) in increasing order, si[SI_FCNT] = their count.
@@ -524,111 +522,227 @@ __global__ void __launch_bounds__(NM) k_pcg_round_small(Inst base, int c0, int k
   }
 }
 
-// Partial Hutchinson corrections.  CTA (x, b) covers rows [x kFRows,
-// (x + 1) kFRows) of instance b: with w_2k = X_{1+k}, w_2k+1 = B_{1+k} (the
-// PCG solutions and projected probes on the face, k < K), u = a_t W (2K
-// values), rhat_t = K^-1 sum_k u_2k u_2k+1, s_t = psi3(z_t) rhat_t (psi3 the
-// third derivative of psi), and out[l] = sum_t s_t a_tl.  Rows are staged
-// kFTile at a time from the gathered rows of A^T (AUT, row upos[fl[l]],
-// contiguous in t); eight threads per row split the face coordinates
-// (l = j mod 8) and add their 2K partial products by shuffles.
-// Out: ap[(b * nchunk + x) * NM + l].
+// Partial Hutchinson corrections on the tensor cores.  CTA (x, b) covers
+// rows [x kHRows, (x + 1) kHRows) of instance b in tiles of kHT = 128 rows:
+// with w_2k = X_{1+k}, w_2k+1 = B_{1+k} (the PCG solutions and projected
+// probes on the face, k < K <= 8), u_t = a_t W (2K values), rhat_t = K^-1
+// sum_k u_t,2k u_t,2k+1, s_t = psi3(z_t) rhat_t (psi3 the third derivative of
+// psi), and out[l] = sum_t s_t a_tl.  Both contractions read one staged tile
+// of the face columns: coordinate l's 128 rows (AUT row upos[fl[l]],
+// contiguous in t) as two 128-byte swizzled rows, one in each half tile of 64
+// rows, so that the tile is
+//   * MN-major for U = A_F W (M = 128 rows t, K = face coordinates l, 8-row
+//     l groups 1024 bytes apart, the second half of t one half tile further):
+//     D1[t][q] = sum_l a_tl W[q][l] with W split into BF16 parts (columns
+//     0..15 Whi, 16..31 Wlo), and
+//   * K-major for out = A_F^T s (M = 128 coordinates, K = 128 rows t):
+//     D2[l][n] += sum_t a_tl S[n][t], S rows 0 and 1 the BF16 parts of s.
+// FP32 accumulation in TMEM; the tile's copies are cp.async 16-byte
+// transfers one tile ahead (zero-filled past the padded row end); thread 0
+// issues the MMAs, threads 0..127 (one TMEM lane each) form s.  Waits are
+// bounded (err |= kErrWaitTimeout on expiry).  Out: ap[(b * nchunk + x) * NM + l].
+constexpr int kHT = 128;      // rows of A per tile (M of the row products, K of the back-projection)
+constexpr int kHRows = 1024;  // rows of A per CTA
 template <int NM>
-__global__ void __launch_bounds__(256) k_face_hutch(Inst base, int K, const int* fl_base, const __nv_bfloat16* AUT,
-                                                    long long ldt, const int* upos, float* ap) {
+struct HutchTc {
+  static_assert(NM % 64 == 0, "face rows staged in whole 8-row atoms, weights in 64-coordinate blocks");
+  static constexpr int kHalf = NM * 128;             // bytes of a half tile: 64 rows t of each of NM coordinates
+  static constexpr int kStage = 2 * kHalf;           // one staged tile
+  static constexpr int kWBytes = (NM / 64) * 4096;   // W: per 64 coordinates, 32 rows (Whi, Wlo) x 128 bytes
+  static constexpr int kSBytes = 2 * 2048;           // S: per half tile, 16 rows x 128 bytes
+  static constexpr int kMT = (NM + 127) / 128;       // M tiles of the back-projection
+  static constexpr size_t kSmem = 1024 + 2 * (size_t)kStage + kWBytes + 2 * kSBytes;
+  static constexpr int kMinBlocks = NM <= kMFt ? 2 : 1;
+};
+constexpr int kHutchChunks(long long T) { return (int)((T + kHRows - 1) / kHRows); }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool full) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(full ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Shared-memory matrix descriptor of an MN-major tile with 128-byte swizzle:
+// 64 consecutive MN elements per 128-byte row, 8 K rows per 1024-byte atom,
+// K atoms 1024 bytes apart, the next 64 MN elements mn_stride bytes further.
+__device__ __forceinline__ uint64_t umma_desc_sw128_mn(const void* tile, uint32_t mn_stride) {
+  const uint32_t a = smem_u32(tile);
+  uint64_t d = 0;
+  d |= (uint64_t)((a >> 4) & 0x3FFFu);
+  d |= (uint64_t)((mn_stride >> 4) & 0x3FFFu) << 16;  // leading byte offset: between 64-element MN blocks
+  d |= (uint64_t)(1024 >> 4) << 32;                   // stride byte offset: between 8-row K atoms
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+template <int NM>
+__global__ void __launch_bounds__(256, HutchTc<NM>::kMinBlocks)
+    k_face_hutch(Inst base, int K, const int* fl_base, const __nv_bfloat16* AUT, long long ldt, const int* upos,
+                 float* ap, int* err) {
+  using H = HutchTc<NM>;
   const int b = blockIdx.y;
   const Inst s = inst_at(base, b);
   if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
   const int m = s.si[SI_FCNT];
-  if (m > NM) return;
-  constexpr int kW = 16;  // 2K <= 16: the batched path takes at most 8 probes
-  // W, row l: (X_1, B_1, X_2, B_2, ...); rows 20 floats apart and tile rows
-  // NM + 8 apart, so that the threads of a warp hit distinct banks
-  __shared__ __align__(16) float wt[NM][kW + 4];
-  extern __shared__ __align__(16) float hsm[];  // the row tile: kFTile rows, NM + 8 apart (kHutchSmem<NM> bytes)
-  float (*a)[NM + 8] = reinterpret_cast<float (*)[NM + 8]>(hsm);
-  __shared__ float sw[kFTile];
+  if (m > NM || m <= 0) return;
+  const long long T = s.T, t0 = (long long)blockIdx.x * kHRows;
+  const long long t1 = t0 + kHRows < T ? t0 + kHRows : T;
+  if (t0 >= t1) return;  // uniform over the CTA, before any barrier or TMEM use
+  const int ntile = (int)((t1 - t0 + kHT - 1) / kHT);
+  extern __shared__ unsigned char hsm_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(hsm_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sA = sm;                         // [2] staged tiles
+  unsigned char* sW = sm + 2 * H::kStage;         // W (B operand of the row products)
+  unsigned char* sS = sW + H::kWBytes;            // [2] S (B operand of the back-projection)
+  __shared__ __align__(8) uint64_t bar[4];        // u_done, a_free[2], fin
+  __shared__ uint32_t tslot;
   __shared__ int col[NM];
+  __shared__ int s_abort;
+  uint64_t* u_done = &bar[0];
+  uint64_t* a_free = &bar[1];
+  uint64_t* fin = &bar[3];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int* fl = fl_base + (size_t)b * s.vs;
-  const int ld = s.ld, K2 = 2 * K;
-  for (int e = threadIdx.x; e < NM * kW; e += blockDim.x) {
-    const int l = e / kW, q = e - l * kW;
+  const int ld = s.ld, K2 = 2 * K, m16 = (m + 15) & ~15;
+  for (int l = tid; l < NM; l += 256) col[l] = l < m ? upos[fl[l]] : 0;
+  // W in BF16 parts: row q < 16 the rounding of w_q, row 16 + q that of the rest
+  for (int e = tid; e < NM * 16; e += 256) {
+    const int l = e >> 4, q = e & 15;
     float v = 0.f;
     if (l < m && q < K2) v = kcol<float>((q & 1) ? s.Bv : s.X, 1 + (q >> 1), ld)[fl[l]];
-    wt[l][q] = v;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    unsigned char* blk = sW + (l >> 6) * 4096;
+    const int jj = (l & 63) >> 3, ee = l & 7;
+    *reinterpret_cast<__nv_bfloat16*>(blk + sw128_off(q, jj) + 2 * ee) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(blk + sw128_off(16 + q, jj) + 2 * ee) = lo;
   }
-  for (int l = threadIdx.x; l < NM; l += blockDim.x) col[l] = l < m ? upos[fl[l]] : -1;
-  const float c3 = (float)s.sd[SD_C3], c4 = (float)s.sd[SD_C4];
-  const long long T = s.T, t0 = (long long)blockIdx.x * kFRows, t1 = t0 + kFRows < T ? t0 + kFRows : T;
-  const int r = threadIdx.x >> 3, j = threadIdx.x & 7;  // row of the tile, face-coordinate slice
-  float bacc[(NM + 255) / 256];  // back-projection of coordinates threadIdx.x + 256 e
-#pragma unroll
-  for (int e = 0; e < (NM + 255) / 256; ++e) bacc[e] = 0.f;
+  // rows m .. m16 of both tiles enter the row products (K = m16): zero them
+  // once (the copies write rows < m only); S rows 2..15 stay zero
+  for (int e = tid; e < 2 * 2 * (m16 - m) * 8; e += 256) {
+    const int st = e / (2 * (m16 - m) * 8), r = e - st * 2 * (m16 - m) * 8;
+    const int h = r / ((m16 - m) * 8), rr = r - h * (m16 - m) * 8;
+    const int l = m + (rr >> 3), jj = rr & 7;
+    *reinterpret_cast<uint4*>(sA + st * H::kStage + h * H::kHalf + sw128_off(l, jj)) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  for (int e = tid; e < 2 * H::kSBytes / 16; e += 256) reinterpret_cast<uint4*>(sS)[e] = make_uint4(0u, 0u, 0u, 0u);
+  if (tid == 0) {
+    for (int q = 0; q < 4; ++q) mbar_init(&bar[q], 1);
+    fence_barrier_init();
+    s_abort = 0;
+  }
+  if (warp == 0) tmem_alloc(&tslot, 128);
+  fence_proxy_async_smem();
+  tc_fence_before();
   __syncthreads();
-  for (long long tb = t0; tb < t1; tb += kFTile) {
-    const int rows = (int)(t1 - tb < kFTile ? t1 - tb : kFTile);
-    for (int e = threadIdx.x; e < kFTile * m; e += blockDim.x) {  // consecutive threads: consecutive t
-      const int l = e / kFTile, rr = e - l * kFTile;
-      a[rr][l] = rr < rows ? __bfloat162float(AUT[(size_t)col[l] * ldt + tb + rr]) : 0.f;
+  tc_fence_after();
+  const uint32_t tmem = tslot;  // columns 0..31 D1, 32 + 16 mt D2 of M tile mt
+  const float c3 = (float)s.sd[SD_C3], c4 = (float)s.sd[SD_C4], invK = 1.f / (float)K;
+  // the copies of tile i into stage i & 1: chunk c = (coordinate l, half h, 16-byte piece j)
+  auto stage_tile = [&](int i) {
+    unsigned char* dst = sA + (i & 1) * H::kStage;
+    const long long tb = t0 + (long long)i * kHT;
+    for (int c = tid; c < m * 16; c += 256) {
+      const int l = c >> 4, h = (c >> 3) & 1, jj = c & 7;
+      const long long t = tb + 64 * h + 8 * jj;
+      const bool in = t < ldt;
+      const __nv_bfloat16* src = AUT + (size_t)col[l] * ldt + (in ? t : 0);
+      cp_async16(dst + h * H::kHalf + sw128_off(l, jj), src, in);
     }
+    cp_async_commit();
+  };
+  const uint32_t id1 = idesc_bf16_f32(kTcBM, 32) | (1u << 15);  // A MN-major
+  const uint32_t id2 = idesc_bf16_f32(kTcBM, 16);
+  bool bad = false;
+  stage_tile(0);
+  int i = 0;
+  for (; i < ntile; ++i) {
+    const int st = i & 1;
+    if (i >= 1 && !mbar_wait_bounded(&a_free[st ^ 1], (uint32_t)(((i - 1) >> 1) & 1))) bad = true;
+    if (i + 1 < ntile) stage_tile(i + 1);
+    else cp_async_commit();  // an empty group keeps the count
+    cp_async_wait<1>();      // the copies of tile i are done
+    fence_proxy_async_smem();
+    if (bad) s_abort = 1;
     __syncthreads();
-    float u[kW];
-#pragma unroll
-    for (int q = 0; q < kW; ++q) u[q] = 0.f;
-    for (int l = j; l < m; l += 8) {
-      const float av = a[r][l];
-      const float4* w4 = reinterpret_cast<const float4*>(&wt[l][0]);
-#pragma unroll
-      for (int q4 = 0; q4 < kW / 4; ++q4) {
-        if (4 * q4 < K2) {
-          const float4 w = w4[q4];
-          u[4 * q4] = fmaf(av, w.x, u[4 * q4]);
-          u[4 * q4 + 1] = fmaf(av, w.y, u[4 * q4 + 1]);
-          u[4 * q4 + 2] = fmaf(av, w.z, u[4 * q4 + 2]);
-          u[4 * q4 + 3] = fmaf(av, w.w, u[4 * q4 + 3]);
-        }
+    if (s_abort) break;
+    unsigned char* pa = sA + st * H::kStage;
+    if (tid == 0) {
+      tc_fence_after();
+      for (int kk = 0; kk < m16 / 16; ++kk) {
+        const uint64_t da = umma_desc_sw128_mn(pa + kk * 2048, (uint32_t)H::kHalf);
+        const uint64_t dw = umma_desc_sw128(sW + (kk >> 2) * 4096 + (kk & 3) * 32);
+        umma_bf16(tmem, da, dw, id1, kk > 0 ? 1u : 0u);
       }
+      umma_commit(u_done);
     }
-    // the eight slices of a row are lanes 8 r' .. 8 r' + 7 of one warp
-#pragma unroll
-    for (int q = 0; q < kW; ++q) {
-      if (q < K2) {
-        float v = u[q];
-        v += __shfl_xor_sync(0xffffffffu, v, 4);
-        v += __shfl_xor_sync(0xffffffffu, v, 2);
-        v += __shfl_xor_sync(0xffffffffu, v, 1);
-        u[q] = v;
-      }
-    }
-    if (j == 0) {
+    unsigned char* ps = sS + st * H::kSBytes;
+    if (warp < 4) {
+      if (!mbar_wait_bounded(u_done, (uint32_t)(i & 1))) bad = true;
+      tc_fence_after();
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
       float rh = 0.f;
 #pragma unroll
-      for (int k = 0; k < kW / 2; ++k)
-        if (k < K) rh = fmaf(u[2 * k], u[2 * k + 1], rh);
-      float wv = 0.f;
-      if (r < rows) {
-        const float z = (float)s.z[tb + r];
-        wv = (-6.f * c3 + 24.f * c4 * z) * (rh / (float)K);
+      for (int k = 0; k < 8; ++k) rh = fmaf(v[2 * k] + v[16 + 2 * k], v[2 * k + 1] + v[17 + 2 * k], rh);
+      const long long t = t0 + (long long)i * kHT + tid;
+      float sv = 0.f;
+      if (t < t1) {
+        const float z = (float)s.z[t];
+        sv = (-6.f * c3 + 24.f * c4 * z) * (rh * invK);
       }
-      sw[r] = wv;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(sv);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(sv - __bfloat162float(hi));
+      const int h = tid >> 6, jj = (tid & 63) >> 3, ee = tid & 7;
+      *reinterpret_cast<__nv_bfloat16*>(ps + h * 2048 + sw128_off(0, jj) + 2 * ee) = hi;
+      *reinterpret_cast<__nv_bfloat16*>(ps + h * 2048 + sw128_off(1, jj) + 2 * ee) = lo;
+      fence_proxy_async_smem();
+      tc_fence_before();
     }
+    if (bad) s_abort = 1;
     __syncthreads();
+    if (s_abort) break;
+    if (tid == 0) {
+      tc_fence_after();
 #pragma unroll
-    for (int e = 0; e < (NM + 255) / 256; ++e) {
-      const int l = (int)threadIdx.x + 256 * e;
-      if (l < m)
-        for (int rr = 0; rr < rows; ++rr) bacc[e] = fmaf(sw[rr], a[rr][l], bacc[e]);
+      for (int mt = 0; mt < H::kMT; ++mt) {
+        const int r0 = mt * 128 < NM - 128 ? mt * 128 : NM - 128;  // the last M tile ends at row NM
+        if (mt * 128 >= m) break;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const int h = kk >> 2;
+          const uint64_t da = umma_desc_sw128(pa + h * H::kHalf + (r0 >> 3) * 1024 + (kk & 3) * 32);
+          const uint64_t ds = umma_desc_sw128(ps + h * 2048 + (kk & 3) * 32);
+          umma_bf16(tmem + 32u + 16u * mt, da, ds, id2, (i > 0 || kk > 0) ? 1u : 0u);
+        }
+      }
+      umma_commit(&a_free[st]);
     }
-    __syncthreads();
   }
+  cp_async_wait<0>();
+  if (tid == 0) umma_commit(fin);  // arrives once every MMA issued above has completed
+  const bool ok = mbar_wait_bounded(fin, 0);
+  if (!ok && tid == 0) atomicOr(err, kErrWaitTimeout);
+  if (s_abort && tid == 0) atomicOr(err, kErrWaitTimeout);
+  tc_fence_after();
+  if (ok && !s_abort && warp < 4) {
 #pragma unroll
-  for (int e = 0; e < (NM + 255) / 256; ++e) {
-    const int l = (int)threadIdx.x + 256 * e;
-    if (l < m) ap[((size_t)b * gridDim.x + blockIdx.x) * NM + l] = bacc[e];
+    for (int mt = 0; mt < H::kMT; ++mt) {
+      const int r0 = mt * 128 < NM - 128 ? mt * 128 : NM - 128;
+      if (mt * 128 >= m) break;
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 32u + 16u * mt, v);
+      const int l = r0 + tid;
+      if (l >= mt * 128 && l < m) ap[((size_t)b * gridDim.x + blockIdx.x) * NM + l] = v[0] + v[1];
+    }
   }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 128);
 }
-template <int NM>
-constexpr size_t kHutchSmem = sizeof(float) * kFTile * (NM + 8);
 
 // at_b = T^-1 sum over the chunks (fixed order) on the face, zero elsewhere.
 template <int NM>

@@ -49,16 +49,16 @@ def _ctx(R):
     return m.MVSK(R, "bf16")
 
 
-def _faces(n, B, rng, sparse):
+def _faces(n, B, rng, sparse, sizes=(40, 81), pool=400):
     """Working faces (B x n of 0/1): every coordinate free, or faces of 40-80
     coordinates drawn from a shared pool of 400 (the overlapping supports of a
     frontier sweep), so that their union U is a few hundred coordinates."""
     if not sparse:
         return None
-    pool = rng.choice(n, size=min(n, 400), replace=False)
+    pool = rng.choice(n, size=min(n, pool), replace=False)
     M = np.zeros((B, n))
     for b in range(B):
-        M[b, rng.choice(pool, size=min(len(pool), int(rng.integers(40, 81))), replace=False)] = 1.0
+        M[b, rng.choice(pool, size=min(len(pool), int(rng.integers(*sizes))), replace=False)] = 1.0
     return M
 
 
@@ -115,16 +115,20 @@ def test_batch_hvp_matches_plain_products(n, T, B, nc, fused, sparse, fp):
     assert np.array_equal(HV, HV2)
 
 
-# (n, T, B, K, sparse faces, face_products): the full sweep (64 instances x 8
-# probe pairs) and small shapes.
-THIRD_CASES = [(5440, 12000, 64, 8, True, 1), (5440, 12000, 64, 8, False, 0), (300, 3001, 4, 8, True, 1),
-               (130, 1000, 3, 3, False, 1)]
+# (n, T, B, K, sparse faces, face_products, face_small): the full sweep (64
+# instances x 8 probe pairs) and small shapes; with sparse faces on the
+# union products (face_small = 0) and on the small-face block's tensor-core
+# kernel in its narrow (faces <= 128) and wide (<= 320) launch shapes.
+THIRD_CASES = [(5440, 12000, 64, 8, True, 1, 0), (5440, 12000, 64, 8, False, 0, 0), (300, 3001, 4, 8, True, 1, 0),
+               (130, 1000, 3, 3, False, 1, 0), (5440, 12000, 64, 8, True, 1, 1), (5440, 12000, 64, 8, True, 1, 2),
+               (300, 3001, 4, 8, True, 1, 1), (700, 2999, 5, 5, True, 1, 2), (130, 1000, 3, 3, True, 1, 1)]
 
 
-@pytest.mark.parametrize("n,T,B,K,sparse,fp", THIRD_CASES)
-def test_batch_third_matches_plain_products(n, T, B, K, sparse, fp):
+@pytest.mark.parametrize("n,T,B,K,sparse,fp,fs", THIRD_CASES)
+def test_batch_third_matches_plain_products(n, T, B, K, sparse, fp, fs):
     R, A, C, X, rng = _inputs(n, T, B, 12)
-    M = _faces(n, B, rng, sparse)
+    # the wide small-face shape on faces of 130-320 coordinates (all three of its M tiles)
+    M = _faces(n, B, rng, sparse, (130, 321), 600) if fs == 2 else _faces(n, B, rng, sparse)
     U = rng.standard_normal((B, K, n))
     P = rng.standard_normal((B, K, n))
     if M is not None:
@@ -132,8 +136,16 @@ def test_batch_third_matches_plain_products(n, T, B, K, sparse, fp):
         P *= M[:, None, :]
     ctx = _ctx(R)
     ctx.set_option("face_products", fp)
+    ctx.set_option("face_small", fs)
     at = ctx.batch_third(C, X, U, P, M)
-    Umask = np.ones(n, dtype=bool) if (fp == 0 or M is None) else M.any(axis=0)
+    # the union products give the correction on the union of the faces, the
+    # small-face block on each instance's own face
+    if fp == 0 or M is None:
+        keep = np.ones((B, n), dtype=bool)
+    elif fs == 0:
+        keep = np.broadcast_to(M.any(axis=0), (B, n))
+    else:
+        keep = M > 0
     Z = A @ X.T
     Aa = np.abs(A)
     AU = (A @ U.reshape(B * K, n).T).reshape(T, B, K)
@@ -145,6 +157,6 @@ def test_batch_third_matches_plain_products(n, T, B, K, sparse, fp):
     W3 = np.column_stack([O.d3psi(C[b], Z[:, b]) for b in range(B)])
     ref = (A.T @ (W3 * rhat)).T / T
     scale = (Aa.T @ (np.abs(W3) * rhat_a)).T / T
-    err = np.abs(at - ref)[:, Umask]
-    assert np.all(err <= 2e-2 * scale[:, Umask] + 1e-300), float(np.max(err / (scale[:, Umask] + 1e-300)))
-    assert np.all(at[:, ~Umask] == 0.0)
+    err = np.abs(at - ref)[keep]
+    assert np.all(err <= 2e-2 * scale[keep] + 1e-300), float(np.max(err / (scale[keep] + 1e-300)))
+    assert np.all(at[~keep] == 0.0)
