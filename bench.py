@@ -46,6 +46,8 @@ def parse():
                     help="concurrent instances of the batched solver (0: all requests at once)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 single-instance leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
+    ap.add_argument("--max-elapsed", type=float, default=0.0,
+                    help="per-request time limit in seconds (0: the library's); a profiler slows every launch")
     ap.add_argument("--sweep-panel", default="c4", choices=["c4", "c3"],
                     help="panel of the batched sweep: c4 (n=5440, T=12000; the measured workload) or c3 "
                          "(n=2000, T=12000: the same kernels on a smaller panel, for profiler captures)")
@@ -304,6 +306,8 @@ def run_ours(args, rank, world):
     out = torch.empty((B, n), dtype=torch.float64, device="cuda")
 
     ctx.set_option("batch_lanes", args.lanes)
+    if args.max_elapsed > 0:
+        ctx.set_option("max_elapsed", args.max_elapsed)
 
     def step():
         return ctx.solve_batch(lam_b, tg_b, m.PCG, args.tol, out=out)

@@ -1089,32 +1089,26 @@ template <int NM>
 mvsk_status small_face_direction(mvsk_ctx* c, BatchBuf& bb, int B) {
   const Inst& base = bb.base;
   const int K = c->opt.probes, ncol1 = K + 1, ca = K + 1, kmax = c->opt.krylov_maxit;
-  const int Gz = oz_row_ctas(c);
   const unsigned nch = (unsigned)kHutchChunks(c->T);
   using GT = GramTc<NM>;
   // face Grams on the tensor cores, rows of A in GT::kSplit shares per instance
   PROF_LAUNCH(NK_GRAM, (k_face_gram_tc<NM><<<dim3(GT::kSplit, B, (NM + 127) / 128), 256, GT::kSmem, c->stream>>>(
                            base, bb.f_list, bb.u_AUT, c->Tp, bb.u_pos, bb.f_gp, c->err)));
-  PROF_LAUNCH(NK_GRAM, (k_face_gram_sum<NM><<<dim3(16, B), 256, 0, c->stream>>>(base, bb.f_gp, GT::kSplit, bb.f_gram)));
-  PROF_LAUNCH(NK_GRAM, (k_face_gram_finish<NM><<<B, 256, 0, c->stream>>>(base, bb.f_list, bb.f_gram, Gz)));
-  if (K > 0)
-    PROF_LAUNCH(NK_PROBE_FILL, (k_probe_fill<float><<<dim3((c->ld + 255) / 256, K, B), 256, 0, c->stream>>>(base, K)));
-  PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gz, -1)));
-  PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup_cols<float><<<dim3(ncol1, B), 512, 0, c->stream>>>(base)));
+  PROF_LAUNCH(NK_GRAM_FIN, (k_face_gram_sum<NM><<<dim3(16, B), 256, 0, c->stream>>>(base, bb.f_gp, GT::kSplit,
+                                                                                      bb.f_gram)));
+  // every Krylov vector of both rounds lives on the face: setups on F only
+  PROF_LAUNCH(NK_PCG_SETUP, (k_face_setup<NM><<<dim3(ncol1, B), NM, 0, c->stream>>>(base, bb.f_list, bb.f_gram)));
   const size_t gsm = sizeof(float) * face_gram_words<NM>();
   PROF_LAUNCH(NK_PCG_ROUND, (k_pcg_round_small<NM><<<dim3(ncol1, B), NM, gsm, c->stream>>>(base, 0, kmax, bb.f_list,
-                                                                                          bb.f_gram)));
-  if (K > 0) {
+                                                                                          bb.f_gram, 0)));
+  if (K > 0)
     PROF_LAUNCH(NK_HUTCH, (k_face_hutch<NM><<<dim3(nch, B), 256, HutchTc<NM>::kSmem, c->stream>>>(
                               base, K, bb.f_list, bb.u_AUT, c->Tp, bb.u_pos, bb.f_ap, c->err)));
-    PROF_LAUNCH(NK_HUTCH, (k_face_hutch_finish<NM><<<B, 256, 0, c->stream>>>(base, bb.f_list, bb.f_ap, (int)nch)));
-  } else {
-    for (int b = 0; b < B; ++b) CU(cudaMemsetAsync(inst_at(base, b).at, 0, sizeof(double) * c->ld, c->stream));
-  }
-  PROF_LAUNCH(NK_PCG_SETUP2, (k_pcg_setup2<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca, ca / 2)));
+  PROF_LAUNCH(NK_PCG_SETUP2, (k_face_setup2<NM><<<dim3(1, B), NM, 0, c->stream>>>(base, bb.f_list, bb.f_ap,
+                                                                                  K > 0 ? (int)nch : 0, ca, ca / 2)));
+  // the second round's CTA also assembles d on the face
   PROF_LAUNCH(NK_PCG_ROUND, (k_pcg_round_small<NM><<<dim3(1, B), NM, gsm, c->stream>>>(base, ca, kmax, bb.f_list,
-                                                                                      bb.f_gram)));
-  PROF_LAUNCH(NK_ASSEMBLE, (k_assemble<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, ca)));
+                                                                                      bb.f_gram, 1)));
   return MVSK_OK;
 }
 
@@ -1189,7 +1183,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
       PROF_LAUNCH(NK_FACE_LIST, (k_small_mode<<<1, 256, 0, c->stream>>>(base, B, c->opt.face_small == 2, bb.u_info)));
       TRY(union_gather(c, bb, B));
       if (split && bb.u_AFU != nullptr)  // digit planes of A's columns in U (the line search along d)
-        PROF_LAUNCH(NK_OZ_SPLIT, (k_oz_split_rows_u<<<4 * c->nsm, 256, 0, c->stream>>>(
+        PROF_LAUNCH(NK_OZ_SPLIT_U, (k_oz_split_rows_u<<<4 * c->nsm, 256, 0, c->stream>>>(
                                      c->A64, c->ld, c->T, bb.u_idx, bb.u_info, oz.eF, bb.u_AFU, oz.MpF)));
     }
   }
@@ -1207,7 +1201,7 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
   if (K > 0)
     PROF_LAUNCH(NK_PROBE_FILL, (k_probe_fill<float><<<dim3((c->ld + 255) / 256, K, B), 256, 0, c->stream>>>(base, K)));
   PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup<float><<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gz, -1)));
-  PROF_LAUNCH(NK_PCG_SETUP, (k_pcg_setup_cols<float><<<dim3(ncol1, B), 512, 0, c->stream>>>(base)));
+  PROF_LAUNCH(NK_PCG_SETUP_COLS, (k_pcg_setup_cols<float><<<dim3(ncol1, B), 512, 0, c->stream>>>(base)));
   const unsigned gl = (unsigned)((c->ld + 255) / 256), gl4 = (unsigned)((c->ld + 1023) / 1024);
   const float invT = (float)(1.0 / (double)c->T);
   if (U)

@@ -301,62 +301,6 @@ __global__ void __launch_bounds__(256) k_face_gram_sum(Inst base, const float* g
   }
 }
 
-// On the face of instance blockIdx.x: diag G, G nuhat (zero off the face) and
-// the scalar partials of the diagonal block: spart[0] = T nuhat^T G nuhat,
-// spart[1] = T 1_F^T G 1_F, spart[2 .. 2 G) = 0 (k_pcg_setup adds G pairs).
-// 256 threads.
-template <int NM>
-__global__ void __launch_bounds__(256) k_face_gram_finish(Inst base, const int* fl_base, const float* gram, int G) {
-  const int b = blockIdx.x;
-  Inst s = inst_at(base, b);
-  if (s.si[SI_DONE] != 0 || s.si[SI_SKIPDIR] != 0) return;
-  const int m = s.si[SI_FCNT];
-  if (m > NM) return;
-  const int* fl = fl_base + (size_t)b * s.vs;
-  const float* Gm = gram + (size_t)b * NM * NM;
-  for (int i = threadIdx.x; i < s.ld; i += blockDim.x) {
-    s.Gnu[i] = 0.0;
-    s.diagG[i] = 0.0;
-  }
-  __syncthreads();
-  __shared__ float nh[NM];
-  __shared__ float red[2][8];
-  for (int k = threadIdx.x; k < m; k += blockDim.x) nh[k] = (float)s.nuhat[fl[k]];
-  __syncthreads();
-  float sn = 0.f, s1 = 0.f;
-  for (int k = threadIdx.x; k < m; k += blockDim.x) {
-    float gv = 0.f, g1 = 0.f;
-    for (int l = 0; l < m; ++l) {
-      const float gk = Gm[(size_t)k * NM + l];
-      gv = fmaf(gk, nh[l], gv);
-      g1 += gk;
-    }
-    s.Gnu[fl[k]] = (double)gv;
-    s.diagG[fl[k]] = (double)Gm[(size_t)k * NM + k];
-    sn = fmaf(nh[k], gv, sn);
-    s1 += g1;
-  }
-  sn = warp_sum(sn);
-  s1 = warp_sum(s1);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) {
-    red[0][warp] = sn;
-    red[1][warp] = s1;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float a0 = 0.f, a1 = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      a0 += red[0][w];
-      a1 += red[1][w];
-    }
-    const double Td = (double)s.T;
-    s.spart[0] = Td * (double)a0;
-    s.spart[1] = Td * (double)a1;
-    for (int g = 1; g < G; ++g) s.spart[2 * g] = s.spart[2 * g + 1] = 0.0;
-  }
-}
-
 // Sums of six floats over a CTA of NM threads (NM / 32 warps), added in
 // warp order so that every thread holds the same totals.
 template <int NM>
@@ -376,6 +320,145 @@ __device__ __forceinline__ void cta_sum6(float (&v)[6], float (*scr)[6]) {
     for (int w = 0; w < NM / 32; ++w) t += scr[w][q];
     v[q] = t;
   }
+}
+
+// Sums of Q doubles over a CTA of NM threads, added in warp order so that
+// every thread holds the same totals.
+template <int NM, int Q>
+__device__ __forceinline__ void cta_sumd(double (&v)[Q], double (*scr)[Q]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) v[q] = warp_sum(v[q]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < Q; ++q) scr[warp][q] = v[q];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < NM / 32; ++w) t += scr[w][q];
+    v[q] = t;
+  }
+  __syncthreads();  // scr is free again
+}
+
+// d = X_h - (||gbar|| / m) X_a - nuhat on F, re-centred on F (1^T d = 0 to
+// rounding), zero elsewhere: k_assemble restricted to F (X_h, X_a and nuhat
+// vanish off F), with xa this thread's coordinate of X_a.
+template <int NM>
+__device__ __forceinline__ void face_assemble(Inst& s, const int* fl_base, int ca, float xa) {
+  __shared__ double ascr[NM / 32][1];
+  const int m = s.si[SI_FCNT], k = threadIdx.x;
+  const bool on = k < m;
+  const int* fl = fl_base + (size_t)blockIdx.y * s.vs;
+  const int i = on ? fl[k] : 0;
+  const double mdim = (double)s.si[SI_M], coef = s.sd[SD_GN] / mdim;
+  const double v = on ? (double)kcol<float>(s.X, 0, s.ld)[i] - coef * (double)xa - s.nuhat[i] : 0.0;
+  for (int j = threadIdx.x; j < s.ld; j += blockDim.x) s.d[j] = 0.0;
+  double sv[1] = {v};
+  cta_sumd<NM, 1>(sv, ascr);  // its barriers also order the zeros before the face values
+  if (on) s.d[i] = v - sv[0] / mdim;
+}
+
+// Start of PCG column c on the face (one coordinate k < m per thread, i =
+// fl[k]): right-hand side B = P_V v (v = G nuhat for c = 0, the probe
+// otherwise; P_V v = v - mean_F v - (nuhat^T v) nuhat on F), X = 0, R = B,
+// P = Z = P_V(B / dg), rz = R^T Z, rhsn = ||B||, active flag, step count 0:
+// k_pcg_setup_cols / pcg_init_col restricted to F, where every vector of the
+// round lives.  Returns B.
+template <int NM>
+__device__ __forceinline__ float face_col_start(Inst& s, int c, bool on, int i, float v, float nh, float dg,
+                                                double m, double (*scr)[2]) {
+  double ab[2] = {on ? (double)v : 0.0, on ? (double)(nh * v) : 0.0};
+  cta_sumd<NM, 2>(ab, scr);
+  const float mean = (float)(ab[0] / m), ny = (float)ab[1];
+  const float Bk = on ? (v - mean) - ny * nh : 0.f;
+  const float tk = on ? Bk / dg : 0.f;
+  double ab2[2] = {(double)tk, (double)(nh * tk)};
+  cta_sumd<NM, 2>(ab2, scr);
+  const float mean2 = (float)(ab2[0] / m), ny2 = (float)ab2[1];
+  const float Zk = on ? (tk - mean2) - ny2 * nh : 0.f;
+  double rn[2] = {(double)(Bk * Zk), (double)(Bk * Bk)};
+  cta_sumd<NM, 2>(rn, scr);
+  const int ld = s.ld;
+  if (on) {
+    kcol<float>(s.Bv, c, ld)[i] = Bk;
+    kcol<float>(s.X, c, ld)[i] = 0.f;
+    kcol<float>(s.R, c, ld)[i] = Bk;
+    kcol<float>(s.P, c, ld)[i] = Zk;
+  }
+  if (threadIdx.x == 0) {
+    s.rz[c] = rn[0];
+    s.rhsn[c] = sqrt(rn[1]);
+    s.si[SI_ACT + c] = rn[1] > 0.0 ? 1 : 0;
+    s.si[SI_CITS + c] = 0;
+  }
+  return Bk;
+}
+
+// First-round setup of the small-face block, column c = blockIdx.x <= K of
+// instance blockIdx.y, one face coordinate per thread, from G_F (gram, row
+// stride NM): G nuhat, diag G, nuhat^T G nuhat and 1_F^T G 1_F (the face
+// part of k_face_gram_finish), the Jacobi floor and lambda of k_pcg_setup
+// (CTA 0 writes SD_LAM, diag G and the FP32 face data kf on F), and the start
+// of column c (k_probe_fill and k_pcg_setup_cols on F; probes from the same
+// counter-based generator).  Every other coordinate of these vectors is
+// never read while the faces stay small.
+template <int NM>
+__global__ void __launch_bounds__(NM) k_face_setup(Inst base, const int* fl_base, const float* gram) {
+  const int b = blockIdx.y, c = blockIdx.x;
+  Inst s = inst_at(base, b);
+  int* SI = s.si;
+  if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0 || c > SI[SI_PROBES]) return;
+  const int m = SI[SI_FCNT];
+  if (m > NM) return;
+  __shared__ float nhs[NM];
+  __shared__ double scr[NM / 32][2];
+  const int k = threadIdx.x, ld = s.ld;
+  const bool on = k < m;
+  const int* fl = fl_base + (size_t)b * s.vs;
+  const int i = on ? fl[k] : 0;
+  const double nhd = on ? s.nuhat[i] : 0.0;
+  const float nh = (float)nhd;
+  nhs[k] = nh;
+  __syncthreads();
+  const float* Gm = gram + (size_t)b * NM * NM;
+  float gv = 0.f, g1 = 0.f, gd = 0.f;
+  if (on) {  // column k of the symmetric G_F (consecutive threads: consecutive addresses)
+    for (int l = 0; l < m; ++l) {
+      const float gk = Gm[(size_t)l * NM + k];
+      gv = fmaf(gk, nhs[l], gv);
+      g1 += gk;
+    }
+    gd = Gm[(size_t)k * NM + k];
+  }
+  const double T = (double)s.T, invT = s.sd[SD_INVT], md = (double)SI[SI_M];
+  double q4[2] = {(double)(nh * gv), (double)g1};
+  cta_sumd<NM, 2>(q4, scr);
+  const double psum0 = (T * q4[0]) * invT, psum1 = (T * q4[1]) * invT;  // nu^T G nu, 1_F^T G 1_F
+  double dd[2] = {on ? (double)gd : 0.0, on ? fabs((double)gd) : 0.0};
+  cta_sumd<NM, 2>(dd, scr);
+  const double floor_ = 1e-300 + 1e-12 * (dd[1] / md);
+  const double trG = dd[0] - psum1 / md - psum0;
+  const double dgd = on ? fmax(fabs((double)gd), floor_) : 1.0;
+  if (c == 0) {
+    if (on) {
+      s.diagG[i] = dgd;
+      s.kf[i] = 1.f;
+      s.kf[ld + i] = nh;
+      s.kf[2 * (size_t)ld + i] = (float)dgd;
+    }
+    if (threadIdx.x == 0) s.sd[SD_LAM] = s.sd[SD_REG] * fabs(trG) / (md - 2.0);
+  }
+  float v = gv;
+  if (c > 0 && on) {
+    const unsigned long long seed =
+        ((unsigned long long)(unsigned)SI[SI_SEEDHI] << 32) | (unsigned long long)(unsigned)SI[SI_SEEDLO];
+    v = probe_value_f(seed, SI[SI_ITER], c - 1, i);
+  }
+  face_col_start<NM>(s, c, on, i, v, nh, (float)dgd, md, scr);
 }
 
 // Upper triangle of a symmetric m x m matrix in shared memory: row i from
@@ -416,13 +499,17 @@ __host__ __device__ constexpr int face_gram_words() {
 // iteration budget; the final X, R, P and rz are written back on the face.
 template <int NM>
 __global__ void __launch_bounds__(NM) k_pcg_round_small(Inst base, int c0, int kmaxit, const int* fl_base,
-                                                        const float* gram) {
+                                                        const float* gram, int assemble) {
   const int b = blockIdx.y, c = c0 + blockIdx.x;
   Inst s = inst_at(base, b);
   int* SI = s.si;
   if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
   const int m = SI[SI_FCNT];
-  if (m > NM || SI[SI_ACT + c] == 0) return;
+  if (m > NM) return;
+  if (SI[SI_ACT + c] == 0) {
+    if (assemble) face_assemble<NM>(s, fl_base, c, 0.f);
+    return;
+  }
   extern __shared__ float gs[];  // upper triangle of G_F: element (i, j) at rs[i] + j (j >= i)
   __shared__ float pv[NM];
   __shared__ int rs[NM];
@@ -519,6 +606,41 @@ __global__ void __launch_bounds__(NM) k_pcg_round_small(Inst base, int c0, int k
     SI[SI_CITS + c] = its;
     SI[SI_ACT + c] = 0;
     s.rz[c] = (double)rz;
+  }
+  if (assemble) face_assemble<NM>(s, fl_base, c, x);
+}
+
+// The Hutchinson correction at = T^-1 (sum over the nchunk partials, in
+// chunk order) on the face, then the second round's column ca from it: B =
+// P_V at and the start of the column (k_face_hutch_finish followed by
+// k_pcg_setup2, restricted to F; nchunk = 0 gives at = 0).  One CTA of NM
+// threads per instance.
+template <int NM>
+__global__ void __launch_bounds__(NM) k_face_setup2(Inst base, const int* fl_base, const float* ap, int nchunk, int ca,
+                                                    int group) {
+  const int b = blockIdx.y;
+  Inst s = inst_at(base, b);
+  int* SI = s.si;
+  if (SI[SI_DONE] != 0 || SI[SI_SKIPDIR] != 0) return;
+  const int m = SI[SI_FCNT];
+  if (m > NM) return;
+  __shared__ double scr[NM / 32][2];
+  const int k = threadIdx.x;
+  const bool on = k < m;
+  const int* fl = fl_base + (size_t)b * s.vs;
+  const int i = on ? fl[k] : 0;
+  float v = 0.f;
+  if (on) {
+    float a = 0.f;
+    for (int c = 0; c < nchunk; ++c) a += ap[((size_t)b * nchunk + c) * NM + k];
+    v = (float)(s.sd[SD_INVT] * (double)a);
+  }
+  const Face<float> f = face_of<float>(s);
+  const float nh = on ? f.nh[i] : 0.f, dg = on ? f.dg[i] : 1.f;
+  face_col_start<NM>(s, ca, on, i, v, nh, dg, (double)SI[SI_M], scr);
+  if (threadIdx.x == 0) {
+    SI[SI_LIVE + group] = SI[SI_ACT + ca];
+    SI[SI_THIRD] += 1;
   }
 }
 

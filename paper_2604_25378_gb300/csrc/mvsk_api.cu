@@ -428,13 +428,16 @@ const char* const kKernelNames[] = {"k_face", "k_probe_fill", "k_pcg_setup", "k_
                                     "k_oz_fin_g", "k_oz_fin_ls", "k_oz_split_vecs", "k_need_ls2", "k_reduce_cols",
                                     "k_hd_cols", "k_hd_reduce1", "k_hd_reduce2", "k_hd_reduce_diag",
                                     "k_pcg_step_a", "k_z_step", "k_union", "k_gather_u", "k_face_list",
-                                    "k_face_gram", "k_pcg_round", "k_face_hutch"};
+                                    "k_face_gram", "k_pcg_round", "k_face_hutch", "k_oz_split_u", "k_face_gram_fin",
+                                    "k_pcg_setup_cols"};
 enum NamedKernel : int {
   NK_FACE, NK_PROBE_FILL, NK_PCG_SETUP, NK_PCG_STEP, NK_COLS, NK_HVP1, NK_HVP2, NK_RHAT, NK_PCG_SETUP2, NK_ASSEMBLE,
   NK_DECIDE1, NK_DECIDE2, NK_END_ITER, NK_OZ_Z, NK_OZ_G, NK_OZ_LS, NK_OZ_SPLIT, NK_NEED, NK_REDUCE_COLS, NK_HD_COLS,
   NK_HD_RED1, NK_HD_RED2, NK_HD_DIAG, NK_PCG_STEP_A, NK_ZSTEP, NK_UNION, NK_GATHER, NK_FACE_LIST, NK_GRAM, NK_PCG_ROUND,
-  NK_HUTCH, NK_COUNT
+  NK_HUTCH, NK_OZ_SPLIT_U, NK_GRAM_FIN, NK_PCG_SETUP_COLS, NK_COUNT
 };
+static_assert(sizeof(kKernelNames) / sizeof(kKernelNames[0]) == NK_COUNT && kKindNamed + NK_COUNT <= kProfKinds,
+              "named kernel kinds");
 
 mvsk_status prof_begin(mvsk_ctx* c, int kind, double work) {
   if (!c->prof_on || (!c->prof_sel.empty() && !c->prof_sel[kind])) return MVSK_OK;
