@@ -99,12 +99,26 @@ struct GramTc {
   static constexpr int kChunks = ((NM + 127) / 128) * 128 * 8 / 256;  // 16-byte chunks per thread and block
   static constexpr size_t kSmem = 1024 + (size_t)2 * (kGTBytesA + 2 * kBytesB) + 256;
   static constexpr int kTmemCols = NM <= 128 ? 128 : (NM <= 256 ? 256 : 512);
-  static constexpr int kSplit = NM <= kMFt ? 4 : 2;     // shares of the rows of A per instance
+  static constexpr int kSplit = NM <= kMFt ? 8 : 2;     // shares of the rows of A per instance
+  static constexpr int kDepth = NM <= kMFt ? 2 : 1;     // 64-row blocks loaded ahead
   static constexpr int kMinBlocks = NM <= kMFt ? 2 : 1;  // resident CTAs per SM (shared memory)
   static_assert(NM % 16 == 0 && NM <= 512, "the N extent of the face Gram MMA");
 };
 constexpr int kGramSplit = GramTc<kMF>::kSplit;
 static_assert(GramTc<kMFt>::kSplit * kMFt * kMFt <= kGramSplit * kMF * kMF, "partial Grams of the narrow block");
+
+// Asynchronous global -> shared copies (cp.async): 16 bytes (zero-filled
+// when !full), 4 bytes; groups committed and waited for by each thread.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool full) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(full ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
 
 __device__ __forceinline__ int sw128_off(int r, int j) {
   return ((r >> 3) << 10) + ((r & 7) << 7) + (((j ^ r) & 7) << 4);
@@ -180,24 +194,27 @@ __global__ void __launch_bounds__(256, GramTc<NM>::kMinBlocks)
   // block i + 1 are issued at the top of iteration i (registers vn, zn), so
   // that their latency passes while the MMAs of block i - 1 and the staging
   // of block i run.
-  uint4 vn[kGTChunks];
-  double zn = 0.0;
-  auto fetch = [&](int kb) {
+  // block i + 1 in (vn, zn); with G::kDepth = 2 also block i + 2 in (vn2, zn2)
+  uint4 vn[kGTChunks], vn2[kGTChunks];
+  double zn = 0.0, zn2 = 0.0;
+  auto fetch_into = [&](int kb, uint4 (&dst)[kGTChunks], double& zd) {
     const long long t0 = (long long)kb * 64;
 #pragma unroll
     for (int q = 0; q < kGTChunks; ++q) {
       const int c = tid + 256 * q, r = c >> 3, j = c & 7;
       const long long t = t0 + 8 * j;
-      vn[q] = make_uint4(0u, 0u, 0u, 0u);
-      if (r < m && t < ldt) vn[q] = __ldg(reinterpret_cast<const uint4*>(AUT + (size_t)roww[r] * ldt + t));
+      dst[q] = make_uint4(0u, 0u, 0u, 0u);
+      if (r < m && t < ldt) dst[q] = __ldg(reinterpret_cast<const uint4*>(AUT + (size_t)roww[r] * ldt + t));
     }
-    if (tid < 64 && t0 + tid < T) zn = s.z[t0 + tid];
+    if (tid < 64 && t0 + tid < T) zd = s.z[t0 + tid];
   };
+  auto fetch = [&](int kb) { fetch_into(kb, vn, zn); };
   auto weight = [&](double z64, long long t) {
     const float z = (float)z64;
     return t < T ? 2.f * c2 - z * (6.f * c3 - 12.f * c4 * z) : 0.f;
   };
   fetch(kb0);
+  if (G::kDepth == 2 && kb0 + 1 < kb1) fetch_into(kb0 + 1, vn2, zn2);
   if (tid < 64) h[tid] = weight(zn, (long long)kb0 * 64 + tid);
   int i = 0;
   for (int kb = kb0; kb < kb1; ++kb, ++i) {
@@ -205,7 +222,14 @@ __global__ void __launch_bounds__(256, GramTc<NM>::kMinBlocks)
     uint4 v[kGTChunks];
 #pragma unroll
     for (int q = 0; q < kGTChunks; ++q) v[q] = vn[q];
-    if (kb + 1 < kb1) fetch(kb + 1);
+    if (G::kDepth == 2) {  // (vn, zn) <- block kb + 1, then block kb + 2 in flight
+#pragma unroll
+      for (int q = 0; q < kGTChunks; ++q) vn[q] = vn2[q];
+      zn = zn2;
+      if (kb + 2 < kb1) fetch_into(kb + 2, vn2, zn2);
+    } else if (kb + 1 < kb1) {
+      fetch(kb + 1);
+    }
     if (i >= 2 && !mbar_wait_bounded(&mdone[st], (uint32_t)(((i - 2) >> 1) & 1))) {
       atomicOr(err, kErrWaitTimeout);
       s_abort = 1;
@@ -427,6 +451,7 @@ __global__ void __launch_bounds__(NM) k_face_setup(Inst base, const int* fl_base
   const float* Gm = gram + (size_t)b * NM * NM;
   float gv = 0.f, g1 = 0.f, gd = 0.f;
   if (on) {  // column k of the symmetric G_F (consecutive threads: consecutive addresses)
+#pragma unroll 8
     for (int l = 0; l < m; ++l) {
       const float gk = Gm[(size_t)l * NM + k];
       gv = fmaf(gk, nhs[l], gv);
@@ -519,18 +544,23 @@ __global__ void __launch_bounds__(NM) k_pcg_round_small(Inst base, int c0, int k
   // faces whose full matrix fits (rows m + 1 words apart: distinct banks)
   // keep it; larger ones keep the upper triangle
   const bool full = m * (m + 1) <= face_gram_words<NM>();
-  if (threadIdx.x == 0) {
+  if (full) {
+    if (threadIdx.x < m) rs[threadIdx.x] = threadIdx.x * (m + 1);
+  } else if (threadIdx.x == 0) {
     int st = 0;
     for (int i = 0; i < m; ++i) {
-      rs[i] = full ? i * (m + 1) : st - i;
+      rs[i] = st - i;
       const int nx = st + (m - i);
       st = nx + (((2 * (i + 1) - nx) % 32) + 32) % 32;
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int i = e / m, j = e - i * m;
-    if (full || j >= i) gs[rs[i] + j] = Gm[(size_t)i * NM + j];
+  {  // G_F into shared memory: one warp per row, every copy in flight at once
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < m; r += NM / 32)
+      for (int j = (full ? 0 : r) + lane; j < m; j += 32) cp_async4(gs + rs[r] + j, Gm + (size_t)r * NM + j);
+    cp_async_commit();
+    cp_async_wait<0>();
   }
   const int ld = s.ld, k = threadIdx.x;
   const bool on = k < m;
@@ -678,13 +708,6 @@ struct HutchTc {
 };
 constexpr int kHutchChunks(long long T) { return (int)((T + kHRows - 1) / kHRows); }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool full) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(full ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Shared-memory matrix descriptor of an MN-major tile with 128-byte swizzle:
 // 64 consecutive MN elements per 128-byte row, 8 K rows per 1024-byte atom,
