@@ -1383,7 +1383,7 @@ mvsk_status batch_start_run(mvsk_ctx* c, BatchBuf& bb, int b, InstRun& r, double
   if (zs != nullptr) CU(cudaMemcpyAsync(s.z, zs, sizeof(double) * c->T, cudaMemcpyDeviceToDevice, c->stream));
   else bb.needz_req = 1;
   k_new_phase<<<1, 32, 0, c->stream>>>(s, o.eta, o.pcg_max_iter, o.stall_window);
-  c->launches += 5;
+  c->launches += w0 != nullptr ? 2 : 3;  // k_init_state, k_new_phase and the 1/n fill (the copies are not kernels)
   CU(cudaGetLastError());
   r.phase = 0;
   r.evals += 1;
@@ -1548,6 +1548,19 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       return cs;
     }
     CU(ce);
+    {  // a replay launches exactly the graph's kernel nodes
+      size_t nn = 0;
+      CU(cudaGraphGetNodes(g, nullptr, &nn));
+      std::vector<cudaGraphNode_t> nodes(nn);
+      CU(cudaGraphGetNodes(g, nodes.data(), &nn));
+      long long nk = 0;
+      for (size_t q = 0; q < nn; ++q) {
+        cudaGraphNodeType t;
+        CU(cudaGraphNodeGetType(nodes[q], &t));
+        nk += t == cudaGraphNodeTypeKernel;
+      }
+      gr.launches = nk;
+    }
     const cudaError_t ie = cudaGraphInstantiate(&gr.e, g, 0);
     cudaGraphDestroy(g);
     CU(ie);

@@ -187,7 +187,11 @@ __global__ void __launch_bounds__(256, GramTc<NM>::kMinBlocks)
   tc_fence_after();
   const uint32_t tmem = *tslot;
   const float c2 = (float)s.sd[SD_C2], c3 = (float)s.sd[SD_C3], c4 = (float)s.sd[SD_C4];
-  const int nn0 = n16 < 256 ? n16 : 256, nn1 = n16 - nn0;
+  // G is symmetric and only its upper triangle (l >= k) is kept: the tile of
+  // rows nbase .. nbase + 127 needs the columns l >= nbase only (Q rows
+  // nbase .. n16, N = n16 - nbase in pieces of at most 256)
+  const int nbase = mt * 128, ntot = n16 - nbase, cbase = nbase * 8;
+  const int nn0 = ntot < 256 ? ntot : 256, nn1 = ntot - nn0;
   const uint32_t idesc0 = idesc_bf16_f32(kTcBM, nn0), idesc1 = idesc_bf16_f32(kTcBM, nn1 > 0 ? nn1 : 16);
   // Thread tid takes the 16-byte chunks tid + 256 q (row c / 8, chunk c % 8)
   // of a 64-row block, and threads < 64 the weight of row tid.  The loads of
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(256, GramTc<NM>::kMinBlocks)
     const long long t0 = (long long)kb * 64;
 #pragma unroll
     for (int q = 0; q < kGTChunks; ++q) {
-      const int c = tid + 256 * q, r = c >> 3, j = c & 7;
+      const int c = cbase + tid + 256 * q, r = c >> 3, j = c & 7;
       const long long t = t0 + 8 * j;
       dst[q] = make_uint4(0u, 0u, 0u, 0u);
       if (r < m && t < ldt) dst[q] = __ldg(reinterpret_cast<const uint4*>(AUT + (size_t)roww[r] * ldt + t));
@@ -241,9 +245,9 @@ __global__ void __launch_bounds__(256, GramTc<NM>::kMinBlocks)
     const float* hb = h + 64 * st;
 #pragma unroll
     for (int q = 0; q < kGTChunks; ++q) {
-      const int c = tid + 256 * q, r = c >> 3, j = c & 7;
+      const int c = cbase + tid + 256 * q, r = c >> 3, j = c & 7;
       if (r >= rows) break;
-      if (r >= mt * 128 && r < mt * 128 + 128) *reinterpret_cast<uint4*>(pa + sw128_off(r - mt * 128, j)) = v[q];
+      if (r < nbase + 128) *reinterpret_cast<uint4*>(pa + sw128_off(r - nbase, j)) = v[q];
       if (r < n16) {
         uint4 qh, ql;
         bf16x8_scale2(v[q], hb + 8 * j, &qh, &ql);
@@ -258,7 +262,7 @@ __global__ void __launch_bounds__(256, GramTc<NM>::kMinBlocks)
     if (tid == 0) {
       tc_fence_after();
       const uint64_t da = umma_desc_sw128(pa);
-      const uint64_t dbh = umma_desc_sw128(pb), dbl = umma_desc_sw128(pb + kGTBytesB);
+      const uint64_t dbh = umma_desc_sw128(pb + nbase * 128), dbl = umma_desc_sw128(pb + kGTBytesB + nbase * 128);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
@@ -278,9 +282,9 @@ __global__ void __launch_bounds__(256, GramTc<NM>::kMinBlocks)
   tc_fence_after();
   if (ok && !s_abort) {
     // warps w and w + 4 read lane quarter w % 4: the first and second half of the columns
-    const int q = warp & 3, half = ((n16 / 2) + 15) & ~15;
-    const int k = mt * 128 + q * 32 + lane;
-    const int ca = warp < 4 ? 0 : half, cb = warp < 4 ? half : n16;
+    const int q = warp & 3, half = ((ntot / 2) + 15) & ~15;
+    const int k = nbase + q * 32 + lane;
+    const int ca = warp < 4 ? 0 : half, cb = warp < 4 ? half : ntot;
     float* out = gp + ((size_t)b * gridDim.x + blockIdx.x) * NM * NM;
     for (int c0 = ca; c0 < cb; c0 += 16) {
       float v[16];
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(256, GramTc<NM>::kMinBlocks)
       if (k < m)
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
-          const int l = c0 + jj;
+          const int l = nbase + c0 + jj;
           if (l >= k && l < m) out[(size_t)k * mp8 + l] = v[jj];
         }
     }
@@ -449,26 +453,31 @@ __global__ void __launch_bounds__(NM) k_face_setup(Inst base, const int* fl_base
   nhs[k] = nh;
   __syncthreads();
   const float* Gm = gram + (size_t)b * NM * NM;
+  // G nuhat and the sums of lambda on the right-hand side's CTA only; every
+  // CTA takes the diagonal for the Jacobi floor
   float gv = 0.f, g1 = 0.f, gd = 0.f;
-  if (on) {  // column k of the symmetric G_F (consecutive threads: consecutive addresses)
+  if (on) {
+    if (c == 0) {  // column k of the symmetric G_F (consecutive threads: consecutive addresses)
 #pragma unroll 8
-    for (int l = 0; l < m; ++l) {
-      const float gk = Gm[(size_t)l * NM + k];
-      gv = fmaf(gk, nhs[l], gv);
-      g1 += gk;
+      for (int l = 0; l < m; ++l) {
+        const float gk = Gm[(size_t)l * NM + k];
+        gv = fmaf(gk, nhs[l], gv);
+        g1 += gk;
+      }
     }
     gd = Gm[(size_t)k * NM + k];
   }
-  const double T = (double)s.T, invT = s.sd[SD_INVT], md = (double)SI[SI_M];
-  double q4[2] = {(double)(nh * gv), (double)g1};
-  cta_sumd<NM, 2>(q4, scr);
-  const double psum0 = (T * q4[0]) * invT, psum1 = (T * q4[1]) * invT;  // nu^T G nu, 1_F^T G 1_F
+  const double md = (double)SI[SI_M];
   double dd[2] = {on ? (double)gd : 0.0, on ? fabs((double)gd) : 0.0};
   cta_sumd<NM, 2>(dd, scr);
   const double floor_ = 1e-300 + 1e-12 * (dd[1] / md);
-  const double trG = dd[0] - psum1 / md - psum0;
   const double dgd = on ? fmax(fabs((double)gd), floor_) : 1.0;
   if (c == 0) {
+    const double T = (double)s.T, invT = s.sd[SD_INVT];
+    double q4[2] = {(double)(nh * gv), (double)g1};
+    cta_sumd<NM, 2>(q4, scr);
+    const double psum0 = (T * q4[0]) * invT, psum1 = (T * q4[1]) * invT;  // nu^T G nu, 1_F^T G 1_F
+    const double trG = dd[0] - psum1 / md - psum0;
     if (on) {
       s.diagG[i] = dgd;
       s.kf[i] = 1.f;
@@ -803,9 +812,16 @@ __global__ void __launch_bounds__(256, HutchTc<NM>::kMinBlocks)
   const uint32_t id2 = idesc_bf16_f32(kTcBM, 16);
   bool bad = false;
   stage_tile(0);
+  // z of this thread's row of the current tile (threads < 128), loaded a tile ahead
+  auto z_of = [&](int it) {
+    const long long t = t0 + (long long)it * kHT + tid;
+    return (tid < kHT && it < ntile && t < t1) ? (float)s.z[t] : 0.f;
+  };
+  float zc = z_of(0);
   int i = 0;
   for (; i < ntile; ++i) {
     const int st = i & 1;
+    const float zn = z_of(i + 1);
     if (i >= 1 && !mbar_wait_bounded(&a_free[st ^ 1], (uint32_t)(((i - 1) >> 1) & 1))) bad = true;
     if (i + 1 < ntile) stage_tile(i + 1);
     else cp_async_commit();  // an empty group keeps the count
@@ -835,10 +851,7 @@ __global__ void __launch_bounds__(256, HutchTc<NM>::kMinBlocks)
       for (int k = 0; k < 8; ++k) rh = fmaf(v[2 * k] + v[16 + 2 * k], v[2 * k + 1] + v[17 + 2 * k], rh);
       const long long t = t0 + (long long)i * kHT + tid;
       float sv = 0.f;
-      if (t < t1) {
-        const float z = (float)s.z[t];
-        sv = (-6.f * c3 + 24.f * c4 * z) * (rh * invK);
-      }
+      if (t < t1) sv = (-6.f * c3 + 24.f * c4 * zc) * (rh * invK);
       const __nv_bfloat16 hi = __float2bfloat16_rn(sv);
       const __nv_bfloat16 lo = __float2bfloat16_rn(sv - __bfloat162float(hi));
       const int h = tid >> 6, jj = (tid & 63) >> 3, ee = tid & 7;
@@ -866,6 +879,7 @@ __global__ void __launch_bounds__(256, HutchTc<NM>::kMinBlocks)
       }
       umma_commit(&a_free[st]);
     }
+    zc = zn;
   }
   cp_async_wait<0>();
   if (tid == 0) umma_commit(fin);  // arrives once every MMA issued above has completed
