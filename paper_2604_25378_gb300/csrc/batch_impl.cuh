@@ -1800,8 +1800,21 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
   // start the first L requests
   for (int b = 0; b < L; ++b) TRY(assign(b));
   TRY(kkt0_flush(c, bb));
-  std::vector<int> si((size_t)L * kSI);
-  std::vector<double> evh((size_t)L * 4);
+  if (bb.hcap < L) {  // pinned, so that the per-iteration copies are asynchronous
+    if (bb.si_h != nullptr) cudaFreeHost(bb.si_h);
+    if (bb.ev_h != nullptr) cudaFreeHost(bb.ev_h);
+    bb.si_h = nullptr;
+    bb.ev_h = nullptr;
+    bb.hcap = 0;
+    if (cudaMallocHost(&bb.si_h, sizeof(int) * kSI * (size_t)L) != cudaSuccess ||
+        cudaMallocHost(&bb.ev_h, sizeof(double) * 4 * (size_t)L) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MVSK_ENOMEM, "pinned host state allocation failed");
+    }
+    bb.hcap = L;
+  }
+  int* const si = bb.si_h;
+  double* const evh = bb.ev_h;
   const double phase_eta[3] = {o.eta, o.restart_eta1, o.restart_eta2};
   const int phase_it[3] = {o.pcg_max_iter, o.restart_iter1, o.restart_iter2};
   int remaining = B;
@@ -1821,15 +1834,16 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       TRY(replay(ghead));
       small_dir = 0;
       if (o.face_small) {
-        CU(cudaMemcpyAsync(&small_dir, bb.u_info + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaMemcpyAsync(c->hword + 1, bb.u_info + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         TRY(sync(c));
+        small_dir = c->hword[1];
       }
       TRY(replay(small_dir == 2 ? gnarrow : (small_dir == 1 ? gsmall : glarge)));
     } else {
       TRY(replay(gfull));
     }
     guard_iters += 1;
-    CU(cudaMemcpyAsync(si.data(), bb.base.si, sizeof(int) * si.size(), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(si, bb.base.si, sizeof(int) * kSI * (size_t)L, cudaMemcpyDeviceToHost, c->stream));
     TRY(sync(c));
     // finished inner solves (host checks after every iteration): evaluate them together
     std::vector<int> fin;
@@ -1878,9 +1892,9 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
         TRY(reduce_cols(c, P64, 1, s.g, c->ld, c->mu, 0.0, nullptr, nullptr, s.sd + SD_C1));
         k_eval_finish<<<1, kVT, 0, c->stream>>>(s, nullptr, c->grid, s.tmp + (size_t)23 * ld);
       }
-      CU(cudaMemcpyAsync(evh.data() + 4 * (size_t)b, s.tmp + (size_t)23 * ld, 3 * sizeof(double),
+      CU(cudaMemcpyAsync(evh + 4 * (size_t)b, s.tmp + (size_t)23 * ld, 3 * sizeof(double),
                          cudaMemcpyDeviceToHost, c->stream));
-      CU(cudaMemcpyAsync(evh.data() + 4 * (size_t)b + 3, s.sd + SD_KKT0, sizeof(double), cudaMemcpyDeviceToHost,
+      CU(cudaMemcpyAsync(evh + 4 * (size_t)b + 3, s.sd + SD_KKT0, sizeof(double), cudaMemcpyDeviceToHost,
                          c->stream));
       c->launches += 1;
     }

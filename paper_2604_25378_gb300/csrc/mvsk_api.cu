@@ -47,6 +47,11 @@ struct BatchBuf {
   int cap = 0;
   mvsk::Inst base{};
   std::vector<void*> mem;
+  // pinned host copies of the lanes' state words and evaluations (read every
+  // iteration: asynchronous copies, one synchronisation)
+  int* si_h = nullptr;
+  double* ev_h = nullptr;
+  int hcap = 0;
   __nv_bfloat16* P16 = nullptr;
   __nv_bfloat16* S16T = nullptr;
   float* part = nullptr;
@@ -127,8 +132,7 @@ struct mvsk_ctx {
   double* hd = nullptr;     // Gnu | diagG
   double* vec_scratch = nullptr;  // host<->device staging for vector arguments
   int* err = nullptr;
-  double* hpin = nullptr;   // pinned host staging
-  size_t hpin_bytes = 0;
+  int* hword = nullptr;     // pinned host words: [0] the error word's copy, [1] the direction form
   int ncolmax = 0;
   // preferences
   bool prefs_set = false;
@@ -232,11 +236,14 @@ mvsk_status download_vec(mvsk_ctx* c, double* dst, const double* src, size_t n) 
   return MVSK_OK;
 }
 
+// Waits for the stream; the error word comes back by an asynchronous copy
+// into pinned memory queued ahead of the wait (one round trip).
 mvsk_status sync(mvsk_ctx* c) {
+  CU(cudaMemcpyAsync(c->hword, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
-  int e = 0;
-  CU(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+  const int e = c->hword[0];
   if (e != 0) {
+    c->hword[0] = 0;
     cudaMemset(c->err, 0, sizeof(int));
     return fail(MVSK_ECUDA, "in-kernel bounded wait ran out (error word %d)", e);
   }
@@ -1388,6 +1395,10 @@ mvsk_status mvsk_create(const double* R, int64_t T, int64_t n, int64_t ld, uint3
   if (flags == MVSK_PREC_MIXED_FP32) ALLOC(c->Alo, sizeof(float) * c->ld * (size_t)T);
   ALLOC(c->mu, ldb);
   ALLOC(c->err, 64);
+  if (cudaMallocHost(&c->hword, 64) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(MVSK_ENOMEM, "pinned host word allocation failed"));
+  }
   if (cudaMemcpy2DAsync(c->A64, ldb, R, sizeof(double) * ld, sizeof(double) * n, T, cudaMemcpyDefault, c->stream) !=
       cudaSuccess)
     return bail(fail(MVSK_ECUDA, "copy of R failed"));
@@ -1852,6 +1863,9 @@ void mvsk_destroy(mvsk_ctx* c) {
   if (c->batch.Wq != nullptr) cudaFree(c->batch.Wq);
   if (c->batch.Zq != nullptr) cudaFree(c->batch.Zq);
   if (c->batch.gpool != nullptr) cudaFree(c->batch.gpool);
+  if (c->batch.si_h != nullptr) cudaFreeHost(c->batch.si_h);
+  if (c->batch.ev_h != nullptr) cudaFreeHost(c->batch.ev_h);
+  if (c->hword != nullptr) cudaFreeHost(c->hword);
   if (c->own_stream != nullptr) cudaStreamDestroy(c->own_stream);
   delete c;
 }
