@@ -280,17 +280,6 @@ __global__ void __launch_bounds__(kVT) k_kkt0_batch(Inst base, const int* idx, c
   if (threadIdx.x == 0) s.sd[SD_KKT0] = k0;
 }
 
-// (f, KKT residual, mu^T x) of a converged inner solve from its iteration state:
-// the oracle block that declared convergence evaluated them at the current x.
-__global__ void k_eval_state(Inst s0, double* out3) {
-  const Inst s = inst_at(s0, blockIdx.y);
-  if (threadIdx.x == 0) {
-    out3[0] = s.sd[SD_F];
-    out3[1] = s.sd[SD_KKT];
-    out3[2] = s.sd[SD_MUX];
-  }
-}
-
 // w[t] = psi'(z[t]) with coefficients (c2, c3, c4), t < T.
 __global__ void k_dpsi_into(const double* z, long long T, double c2, double c3, double c4, double* w) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1802,11 +1791,14 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
   TRY(kkt0_flush(c, bb));
   if (bb.hcap < L) {  // pinned, so that the per-iteration copies are asynchronous
     if (bb.si_h != nullptr) cudaFreeHost(bb.si_h);
+    if (bb.sd_h != nullptr) cudaFreeHost(bb.sd_h);
     if (bb.ev_h != nullptr) cudaFreeHost(bb.ev_h);
     bb.si_h = nullptr;
+    bb.sd_h = nullptr;
     bb.ev_h = nullptr;
     bb.hcap = 0;
     if (cudaMallocHost(&bb.si_h, sizeof(int) * kSI * (size_t)L) != cudaSuccess ||
+        cudaMallocHost(&bb.sd_h, sizeof(double) * kSD * (size_t)L) != cudaSuccess ||
         cudaMallocHost(&bb.ev_h, sizeof(double) * 4 * (size_t)L) != cudaSuccess) {
       cudaGetLastError();
       return fail(MVSK_ENOMEM, "pinned host state allocation failed");
@@ -1814,6 +1806,7 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     bb.hcap = L;
   }
   int* const si = bb.si_h;
+  const double* const sdh = bb.sd_h;
   double* const evh = bb.ev_h;
   const double phase_eta[3] = {o.eta, o.restart_eta1, o.restart_eta2};
   const int phase_it[3] = {o.pcg_max_iter, o.restart_iter1, o.restart_iter2};
@@ -1843,7 +1836,10 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       TRY(replay(gfull));
     }
     guard_iters += 1;
+    // the lanes' integer and scalar states (an inner solve that converged is
+    // evaluated from them: f, KKT residual, mu^T x and its kkt0 normaliser)
     CU(cudaMemcpyAsync(si, bb.base.si, sizeof(int) * kSI * (size_t)L, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(bb.sd_h, bb.base.sd, sizeof(double) * kSD * (size_t)L, cudaMemcpyDeviceToHost, c->stream));
     TRY(sync(c));
     // finished inner solves (host checks after every iteration): evaluate them together
     std::vector<int> fin;
@@ -1880,10 +1876,15 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       fin.push_back(b);
     }
     if (fin.empty()) continue;
+    bool restored = false;
     for (int b : fin) {
       const Inst s = inst_at(bb.base, b);
-      if (run[(size_t)b].run_status == MVSK_OK) {
-        k_eval_state<<<1, 32, 0, c->stream>>>(s, s.tmp + (size_t)23 * ld);
+      const double* sdb = sdh + (size_t)b * kSD;
+      evh[4 * (size_t)b + 3] = sdb[SD_KKT0];
+      if (run[(size_t)b].run_status == MVSK_OK) {  // the oracle block that declared convergence evaluated x
+        evh[4 * (size_t)b] = sdb[SD_F];
+        evh[4 * (size_t)b + 1] = sdb[SD_KKT];
+        evh[4 * (size_t)b + 2] = sdb[SD_MUX];
       } else {  // the best iterate was restored: evaluate it
         PassArgs a = pass_args_inst(run[(size_t)b].cc.data());
         a.in[0] = s.x;
@@ -1891,14 +1892,13 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
         TRY(run_pass(c, P64, M_VALGRAD, 1, a, nullptr, s.spart));
         TRY(reduce_cols(c, P64, 1, s.g, c->ld, c->mu, 0.0, nullptr, nullptr, s.sd + SD_C1));
         k_eval_finish<<<1, kVT, 0, c->stream>>>(s, nullptr, c->grid, s.tmp + (size_t)23 * ld);
+        CU(cudaMemcpyAsync(evh + 4 * (size_t)b, s.tmp + (size_t)23 * ld, 3 * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream));
+        c->launches += 1;
+        restored = true;
       }
-      CU(cudaMemcpyAsync(evh + 4 * (size_t)b, s.tmp + (size_t)23 * ld, 3 * sizeof(double),
-                         cudaMemcpyDeviceToHost, c->stream));
-      CU(cudaMemcpyAsync(evh + 4 * (size_t)b + 3, s.sd + SD_KKT0, sizeof(double), cudaMemcpyDeviceToHost,
-                         c->stream));
-      c->launches += 1;
     }
-    TRY(sync(c));
+    if (restored) TRY(sync(c));
     std::vector<int> freed;
     auto finish_b = [&](int b, bool from_hi) -> mvsk_status {
       InstRun& r = run[(size_t)b];

@@ -50,6 +50,7 @@ struct BatchBuf {
   // pinned host copies of the lanes' state words and evaluations (read every
   // iteration: asynchronous copies, one synchronisation)
   int* si_h = nullptr;
+  double* sd_h = nullptr;
   double* ev_h = nullptr;
   int hcap = 0;
   __nv_bfloat16* P16 = nullptr;
@@ -1865,6 +1866,7 @@ void mvsk_destroy(mvsk_ctx* c) {
   if (c->batch.gpool != nullptr) cudaFree(c->batch.gpool);
   if (c->batch.si_h != nullptr) cudaFreeHost(c->batch.si_h);
   if (c->batch.ev_h != nullptr) cudaFreeHost(c->batch.ev_h);
+  if (c->batch.sd_h != nullptr) cudaFreeHost(c->batch.sd_h);
   if (c->hword != nullptr) cudaFreeHost(c->hword);
   if (c->own_stream != nullptr) cudaStreamDestroy(c->own_stream);
   delete c;
