@@ -1564,13 +1564,18 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     TRY(capture(-1, gfull));
   }
   // replay of one graph (profiled launches folded in after each replay)
+  // replays queue no wait: the profiled event pairs of the iteration's graphs
+  // are read after the iteration's state copy (one wait per iteration)
+  std::vector<const ItGraph*> pend;
   auto replay = [&](ItGraph& gr) -> mvsk_status {
     CU(cudaGraphLaunch(gr.e, c->stream));
     c->launches += gr.launches;
-    if (c->prof_on) {
-      CU(cudaStreamSynchronize(c->stream));
-      TRY(prof_collect(c, gr.ev_b, gr.ev_e));
-    }
+    if (c->prof_on) pend.push_back(&gr);
+    return MVSK_OK;
+  };
+  auto collect = [&]() -> mvsk_status {  // after a wait that followed the replays
+    for (const ItGraph* g : pend) TRY(prof_collect(c, g->ev_b, g->ev_e, c->prof_uinfo != nullptr ? c->hword + 2 : nullptr));
+    pend.clear();
     return MVSK_OK;
   };
   int small_dir = 0;  // host copy of the direction form chosen on the device
@@ -1840,7 +1845,10 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     // evaluated from them: f, KKT residual, mu^T x and its kkt0 normaliser)
     CU(cudaMemcpyAsync(si, bb.base.si, sizeof(int) * kSI * (size_t)L, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(bb.sd_h, bb.base.sd, sizeof(double) * kSD * (size_t)L, cudaMemcpyDeviceToHost, c->stream));
+    if (c->prof_on && c->prof_uinfo != nullptr)
+      CU(cudaMemcpyAsync(c->hword + 2, c->prof_uinfo, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     TRY(sync(c));
+    TRY(collect());
     // finished inner solves (host checks after every iteration): evaluate them together
     std::vector<int> fin;
     for (int b = 0; b < L; ++b) {

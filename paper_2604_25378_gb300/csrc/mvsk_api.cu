@@ -505,8 +505,11 @@ mvsk_status prof_begin_u(mvsk_ctx* c, int kind, double work_per_unit) {
 }
 
 // Fold the event pairs [b, e) into the per-kind totals (stream must be idle).
-mvsk_status prof_collect(mvsk_ctx* c, size_t b, size_t e) {
-  double units = -1.0;
+// Event pairs [b, e) after the stream has passed them; union-scaled work is
+// multiplied by the union size, read from uinfo_host when given (a copy
+// queued before the wait), else from the device.
+mvsk_status prof_collect(mvsk_ctx* c, size_t b, size_t e, const int* uinfo_host = nullptr) {
+  double units = uinfo_host != nullptr ? (double)uinfo_host[1] : -1.0;
   for (size_t q = b; q < e; ++q) {
     float ms = 0.f;
     CU(cudaEventElapsedTime(&ms, c->ev_pool[2 * q], c->ev_pool[2 * q + 1]));
