@@ -1169,7 +1169,9 @@ mvsk_status batch_iteration(mvsk_ctx* c, BatchBuf& bb, int B, const std::vector<
     PROF_LAUNCH(NK_FACE, (k_face<<<dim3(1, B), kVT, 0, c->stream>>>(base, nullptr, Gs)));
     if (U) {
       PROF_LAUNCH(NK_FACE_LIST, (k_face_list<<<dim3(1, B), 1024, 0, c->stream>>>(base, bb.f_list)));
-      PROF_LAUNCH(NK_FACE_LIST, (k_small_mode<<<1, 256, 0, c->stream>>>(base, B, c->opt.face_small == 2, bb.u_info)));
+      PROF_LAUNCH(NK_FACE_LIST, (k_small_mode<<<1, 256, 0, c->stream>>>(base, B, c->opt.face_small != 0,
+                                                                         c->opt.face_small == 2, bb.u_info, bb.cond,
+                                                                         bb.has_cond)));
       TRY(union_gather(c, bb, B));
       if (split && bb.u_AFU != nullptr)  // digit planes of A's columns in U (the line search along d)
         PROF_LAUNCH(NK_OZ_SPLIT_U, (k_oz_split_rows_u<<<4 * c->nsm, 256, 0, c->stream>>>(
@@ -1515,13 +1517,15 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
   // products the oracle block (part 0) and the two direction forms (parts 1, 2)
   struct ItGraph {
     cudaGraphExec_t e = nullptr;
+    cudaGraph_t g = nullptr;  // the captured graph (a child of the one-graph iteration)
     long long launches = 0;
     size_t ev_b = 0, ev_e = 0;
     ~ItGraph() {
       if (e) cudaGraphExecDestroy(e);
+      if (g) cudaGraphDestroy(g);
     }
   };
-  ItGraph gfull, ghead, glarge, gsmall, gnarrow;
+  ItGraph gfull, ghead, glarge, gsmall, gnarrow, giter;
   auto capture = [&](int part, ItGraph& gr) -> mvsk_status {
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -1550,16 +1554,53 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       }
       gr.launches = nk;
     }
-    const cudaError_t ie = cudaGraphInstantiate(&gr.e, g, 0);
-    cudaGraphDestroy(g);
-    CU(ie);
+    gr.g = g;
+    CU(cudaGraphInstantiate(&gr.e, g, 0));
     return MVSK_OK;
   };
+  // With face-restricted products the iteration is one graph when the
+  // direction bodies hold no profiler events (conditional bodies take kernels,
+  // copies and child graphs only): the oracle block, then a switch node over
+  // the three direction forms on the value k_small_mode sets on the device,
+  // so that no host round trip separates them.  Otherwise the host reads the
+  // form after the oracle block and replays its graph.
+  bool one_graph = false;
   if (bb.umode) {
-    TRY(capture(0, ghead));
     TRY(capture(1, glarge));
     TRY(capture(2, gsmall));
     TRY(capture(3, gnarrow));
+    one_graph = o.face_small != 0 && glarge.ev_e == glarge.ev_b && gsmall.ev_e == gsmall.ev_b &&
+                gnarrow.ev_e == gnarrow.ev_b;
+    if (one_graph) {
+      CU(cudaGraphCreate(&giter.g, 0));
+      if (cudaGraphConditionalHandleCreate(&bb.cond, giter.g, 0, 0) != cudaSuccess) {
+        cudaGetLastError();
+        one_graph = false;
+      }
+    }
+    bb.has_cond = one_graph ? 1 : 0;  // captured into k_small_mode's arguments
+    const mvsk_status hs = capture(0, ghead);
+    bb.has_cond = 0;
+    TRY(hs);
+    if (one_graph) {
+      cudaGraphNode_t nh = nullptr, nc = nullptr;
+      CU(cudaGraphAddChildGraphNode(&nh, giter.g, nullptr, 0, ghead.g));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = bb.cond;
+      cp.conditional.type = cudaGraphCondTypeSwitch;
+      cp.conditional.size = 3;  // body f runs for the form f: 0 large faces, 1 wide, 2 narrow small faces
+      CU(cudaGraphAddNode(&nc, giter.g, &nh, nullptr, 1, &cp));
+      const ItGraph* body[3] = {&glarge, &gsmall, &gnarrow};
+      for (int q = 0; q < 3; ++q) {
+        cudaGraphNode_t nb = nullptr;
+        CU(cudaGraphAddChildGraphNode(&nb, cp.conditional.phGraph_out[q], nullptr, 0, body[q]->g));
+      }
+      CU(cudaGraphInstantiate(&giter.e, giter.g, 0));
+      giter.launches = ghead.launches;  // plus the body's, counted once the form is read back
+      giter.ev_b = ghead.ev_b;
+      giter.ev_e = ghead.ev_e;
+    }
   } else {
     TRY(capture(-1, gfull));
   }
@@ -1828,7 +1869,10 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       }
       bb.needz_req = 0;
     }
-    if (bb.umode) {  // oracle block, then the direction form every face allows
+    if (one_graph) {  // oracle block and the direction form it chose, one replay
+      TRY(replay(giter));
+      CU(cudaMemcpyAsync(c->hword + 1, bb.u_info + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    } else if (bb.umode) {  // oracle block, then the direction form every face allows
       TRY(replay(ghead));
       small_dir = 0;
       if (o.face_small) {
@@ -1849,6 +1893,10 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       CU(cudaMemcpyAsync(c->hword + 2, c->prof_uinfo, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     TRY(sync(c));
     TRY(collect());
+    if (one_graph) {
+      const int f = c->hword[1];
+      c->launches += (f == 2 ? gnarrow : (f == 1 ? gsmall : glarge)).launches;
+    }
     // finished inner solves (host checks after every iteration): evaluate them together
     std::vector<int> fin;
     for (int b = 0; b < L; ++b) {
@@ -2290,7 +2338,7 @@ mvsk_status batch_third_export(mvsk_ctx* c, int B, const double* C, const double
     int mode = 0;  // the small-face block's kernels when every face allows them (option face_small)
     if (c->opt.face_small) {
       k_face_list<<<dim3(1, B), 1024, 0, c->stream>>>(base, bb.f_list);
-      k_small_mode<<<1, 256, 0, c->stream>>>(base, B, c->opt.face_small == 2, bb.u_info);
+      k_small_mode<<<1, 256, 0, c->stream>>>(base, B, 1, c->opt.face_small == 2, bb.u_info, 0, 0);
       c->launches += 2;
       CU(cudaGetLastError());
       CU(cudaMemcpyAsync(&mode, bb.u_info + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));

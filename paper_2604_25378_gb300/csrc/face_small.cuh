@@ -58,9 +58,12 @@ __global__ void __launch_bounds__(1024) k_face_list(Inst base, int* fl_base) {
 
 // info[2] = 2 when every instance that needs a direction this iteration has a
 // face of at most kMFt coordinates (the narrow small-face block runs), else 1
-// when every such face has at most kMF (the wide one), else 0.  wide != 0
-// takes the wide block for every small face.
-__global__ void k_small_mode(Inst base, int B, int wide, int* info) {
+// when every such face has at most kMF (the wide one), else 0 (also when
+// small = 0).  wide != 0 takes the wide block for every small face.  With
+// has_cond the same value selects the body of the iteration graph's switch
+// node (handle cond).
+__global__ void k_small_mode(Inst base, int B, int small, int wide, int* info, cudaGraphConditionalHandle cond,
+                             int has_cond) {
   int big = 0, mid = 0;
   for (int b = threadIdx.x; b < B; b += blockDim.x) {
     const int* si = base.si + (size_t)b * kSI;
@@ -71,7 +74,11 @@ __global__ void k_small_mode(Inst base, int B, int wide, int* info) {
   }
   big = __syncthreads_or(big);
   mid = __syncthreads_or(mid | wide);
-  if (threadIdx.x == 0) info[2] = big ? 0 : (mid ? 1 : 2);
+  if (threadIdx.x == 0) {
+    const int f = (big || !small) ? 0 : (mid ? 1 : 2);
+    info[2] = f;
+    if (has_cond) cudaGraphSetConditional(cond, (unsigned)f);
+  }
 }
 
 // Face Grams on the tensor cores.  CTA (x, b, t) accumulates over the 64-row

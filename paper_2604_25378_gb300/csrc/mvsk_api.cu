@@ -51,6 +51,9 @@ struct BatchBuf {
   // iteration: asynchronous copies, one synchronisation)
   int* si_h = nullptr;
   double* sd_h = nullptr;
+  // switch handle of the one-graph iteration (valid while has_cond is set during its capture)
+  cudaGraphConditionalHandle cond = 0;
+  int has_cond = 0;
   double* ev_h = nullptr;
   int hcap = 0;
   __nv_bfloat16* P16 = nullptr;
