@@ -1352,29 +1352,72 @@ struct CalGroup {
 // Start an inner solve of instance b at c1 from warm start w0 (device vector or
 // null: 1/n).  zw0: the cached A w0 (device, T) when known; without it the next
 // iteration recomputes z = A x (split products; a start from 1/n takes A 1/n).
+// Start of an inner solve in lane b, one launch: the state of k_init_state
+// (options h, iteration budget, probes, ...) followed by the first phase of
+// k_new_phase (thread 0), x from w0 (ld values) or 1/n on the n coordinates,
+// and z = A x from zs when given (T values).
+struct LaneStart {
+  double h[12];
+  double tol, eta;
+  int maxit, stallwin, probes, kmaxit, arcmax, lsrule;
+  unsigned long long seed;
+};
+__global__ void __launch_bounds__(256) k_start_lane(Inst base, int b, LaneStart a, const double* w0,
+                                                    const double* zs) {
+  const Inst s = inst_at(base, b);
+  const int n = s.n, ld = s.ld;
+  const double inv_n = 1.0 / (double)n;
+  for (int i = threadIdx.x; i < ld; i += blockDim.x) s.x[i] = w0 != nullptr ? w0[i] : (i < n ? inv_n : 0.0);
+  if (zs != nullptr)
+    for (long long t = threadIdx.x; t < s.T; t += blockDim.x) s.z[t] = zs[t];
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kSI; ++q) s.si[q] = 0;
+    for (int q = SD_HIST; q < kSD; ++q) s.sd[q] = 0.0;
+    s.sd[SD_TOL] = a.tol;
+    s.sd[SD_BEST] = INFINITY;
+    s.sd[SD_TAU] = a.h[0];
+    s.sd[SD_EPSACT] = a.h[1];
+    s.sd[SD_RELRATIO] = a.h[2];
+    s.sd[SD_REG] = a.h[3];
+    s.sd[SD_KTOL] = a.h[4];
+    s.sd[SD_C1] = a.h[5];
+    s.sd[SD_C2] = a.h[6];
+    s.sd[SD_C3] = a.h[7];
+    s.sd[SD_C4] = a.h[8];
+    s.sd[SD_INVT] = a.h[9];
+    s.sd[SD_DESCEPS] = a.h[10];
+    s.sd[SD_STALLF] = a.h[11];
+    s.si[SI_PCG] = 1;
+    s.si[SI_PROBES] = a.probes;
+    s.si[SI_SEEDLO] = (int)(unsigned)(a.seed & 0xffffffffull);
+    s.si[SI_SEEDHI] = (int)(unsigned)(a.seed >> 32);
+    s.si[SI_KMAXIT] = a.kmaxit;
+    s.si[SI_ARCMAX] = a.arcmax;
+    s.si[SI_LSRULE] = a.lsrule;
+    // first phase (SI_DONE, SI_PHASEIT, SI_HISTN are zero from above)
+    s.si[SI_MAXIT] = a.maxit;
+    s.si[SI_STALLWIN] = a.stallwin;
+    s.sd[SD_ETA] = a.eta;
+  }
+}
+
 mvsk_status batch_start_run(mvsk_ctx* c, BatchBuf& bb, int b, InstRun& r, double c1, const double* w0, double tol,
                             const double* zw0) {
-  const Inst s = inst_at(bb.base, b);
   r.cc[0] = c1;
   const Options& o = c->opt;
   const double reg = isnan(o.reg) ? 1e-4 : o.reg;
-  double h[12] = {o.tau, o.eps_act, o.release_ratio, reg, o.krylov_tol, r.cc[0], r.cc[1], r.cc[2], r.cc[3],
-                  1.0 / (double)c->T, o.descent_eps, o.stall_factor};
-  double* dopts = s.tmp + (size_t)22 * c->ld;  // 12 doubles of the instance's scratch
-  CU(cudaMemcpyAsync(dopts, h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
-  k_init_state<<<1, 32, 0, c->stream>>>(s, tol, o.eta, o.pcg_max_iter, 1, o.stall_window, o.probes, o.probe_seed,
-                                        o.krylov_maxit, o.arc_halvings, o.line_search, dopts);
+  LaneStart a{{o.tau, o.eps_act, o.release_ratio, reg, o.krylov_tol, r.cc[0], r.cc[1], r.cc[2], r.cc[3],
+               1.0 / (double)c->T, o.descent_eps, o.stall_factor},
+              tol, o.eta, o.pcg_max_iter, o.stall_window, o.probes, o.krylov_maxit, o.arc_halvings, o.line_search,
+              o.probe_seed};
   // the KKT residual at the 1/n start (kkt_rel normaliser) of every instance
   // started in this round is evaluated by one k_kkt0_batch (kkt0_flush)
   bb.kq_idx.push_back(b);
   bb.kq_c1.push_back(c1);
-  if (w0 != nullptr) CU(cudaMemcpyAsync(s.x, w0, sizeof(double) * c->ld, cudaMemcpyDeviceToDevice, c->stream));
-  else k_fill<<<(c->ld + 255) / 256, 256, 0, c->stream>>>(s.x, c->n, c->ld, 1.0 / c->n);
   const double* zs = w0 == nullptr ? bb.z0 : zw0;
-  if (zs != nullptr) CU(cudaMemcpyAsync(s.z, zs, sizeof(double) * c->T, cudaMemcpyDeviceToDevice, c->stream));
-  else bb.needz_req = 1;
-  k_new_phase<<<1, 32, 0, c->stream>>>(s, o.eta, o.pcg_max_iter, o.stall_window);
-  c->launches += w0 != nullptr ? 2 : 3;  // k_init_state, k_new_phase and the 1/n fill (the copies are not kernels)
+  if (zs == nullptr) bb.needz_req = 1;
+  k_start_lane<<<1, 256, 0, c->stream>>>(bb.base, b, a, w0, zs);
+  c->launches += 1;
   CU(cudaGetLastError());
   r.phase = 0;
   r.evals += 1;
@@ -1781,13 +1824,28 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     r.cal = 1;
     return batch_start_run(c, bb, b, r, 0.0, nullptr, tol, nullptr);
   };
-  // results of the request in lane b (at the end of its last inner solve)
-  std::vector<double> hx(ld);
+  // results of the request in lane b (at the end of its last inner solve):
+  // W out, and the request's counters and evaluations copied into pinned
+  // per-request slots that the infos read after the final wait (no wait here)
+  if (infos != nullptr && bb.qhcap < B) {
+    if (bb.q_si != nullptr) cudaFreeHost(bb.q_si);
+    if (bb.q_ev != nullptr) cudaFreeHost(bb.q_ev);
+    bb.q_si = nullptr;
+    bb.q_ev = nullptr;
+    bb.qhcap = 0;
+    if (cudaMallocHost(&bb.q_si, sizeof(int) * kSI * (size_t)B) != cudaSuccess ||
+        cudaMallocHost(&bb.q_ev, sizeof(double) * 4 * (size_t)B) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MVSK_ENOMEM, "pinned request slot allocation failed");
+    }
+    bb.qhcap = B;
+  }
   mvsk_status first = MVSK_OK;
   auto emit = [&](int b) -> mvsk_status {
     InstRun& r = run[(size_t)b];
     const int q = lane_req[(size_t)b];
     const Inst s = inst_at(bb.base, b);
+    double* qe = infos != nullptr ? bb.q_ev + 4 * (size_t)q : nullptr;
     if (r.final_from_hi) {  // re-evaluate at the bracket end that is returned
       PassArgs a = pass_args_inst(r.cc.data());
       double c1 = r.cc[0];
@@ -1797,37 +1855,25 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
       TRY(run_pass(c, P64, M_VALGRAD, 1, a, nullptr, s.spart));
       TRY(reduce_cols(c, P64, 1, s.g, c->ld, c->mu, 0.0, nullptr, nullptr, s.sd + SD_C1));
       k_eval_finish<<<1, kVT, 0, c->stream>>>(s, nullptr, c->grid, s.tmp + (size_t)23 * ld);
-      CU(cudaMemcpyAsync(r.ev, s.tmp + (size_t)23 * ld, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      TRY(sync(c));
+      c->launches += 1;
+      if (qe != nullptr)
+        CU(cudaMemcpyAsync(qe, s.tmp + (size_t)23 * ld, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    } else if (qe != nullptr) {
+      for (int k = 0; k < 3; ++k) qe[k] = r.ev[k];
     }
     CU(cudaMemcpyAsync(W_out + (size_t)q * c->n, s.x, sizeof(double) * c->n, cudaMemcpyDefault, c->stream));
     if (infos != nullptr) {
-      CU(cudaMemcpyAsync(hx.data(), s.x, sizeof(double) * ld, cudaMemcpyDeviceToHost, c->stream));
-      double k0 = 0.0;
-      if (isnan(r.kkt0))
-        CU(cudaMemcpyAsync(&k0, s.sd + SD_KKT0, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      int cnt[kSI];
-      CU(cudaMemcpyAsync(cnt, s.si, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
-      TRY(sync(c));
+      if (isnan(r.kkt0)) CU(cudaMemcpyAsync(qe + 3, s.sd + SD_KKT0, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      else qe[3] = r.kkt0;
+      CU(cudaMemcpyAsync(bb.q_si + (size_t)q * kSI, s.si, sizeof(int) * kSI, cudaMemcpyDeviceToHost, c->stream));
       mvsk_info& inf = infos[q];
       memset(&inf, 0, sizeof(inf));
       inf.iters = r.iters;
       inf.restarts = r.restarts;
-      inf.krylov_iters = cnt[SI_KRY];
-      inf.third_calls = cnt[SI_THIRD];
       inf.evals = r.evals;
-      inf.f = r.ev[0];
-      inf.kkt_residual = r.ev[1];
-      if (!isnan(r.kkt0)) k0 = r.kkt0;
-      inf.kkt0 = k0;
-      inf.kkt_rel = r.ev[1] / fmax(k0, 1e-300);
       for (int k = 0; k < 4; ++k) inf.c[k] = r.cc[k];
-      inf.achieved_mean = r.ev[2];
       inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       inf.status = r.run_status;
-      int fc = 0;
-      for (int i = 0; i < c->n; ++i) fc += (hx[(size_t)i] - o.tau > o.eps_act);
-      inf.free_count = fc;
     }
     if (r.run_status != MVSK_OK && first == MVSK_OK) first = (mvsk_status)r.run_status;
     return MVSK_OK;
@@ -2131,8 +2177,26 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     if (guard_iters > 1000000) return fail(MVSK_ECUDA, "batched solve did not terminate");
   }
   TRY(sync(c));
-  if (infos != nullptr)
-    for (int q = 0; q < B; ++q) infos[q].batch_iters = (int32_t)guard_iters;
+  if (infos != nullptr) {  // the per-request slots, and the free counts from W
+    std::vector<double> hw((size_t)B * c->n);
+    CU(cudaMemcpy(hw.data(), W_out, sizeof(double) * hw.size(), cudaMemcpyDefault));
+    for (int q = 0; q < B; ++q) {
+      mvsk_info& inf = infos[q];
+      const double* qe = bb.q_ev + 4 * (size_t)q;
+      const int* cnt = bb.q_si + (size_t)q * kSI;
+      inf.krylov_iters = cnt[SI_KRY];
+      inf.third_calls = cnt[SI_THIRD];
+      inf.f = qe[0];
+      inf.kkt_residual = qe[1];
+      inf.achieved_mean = qe[2];
+      inf.kkt0 = qe[3];
+      inf.kkt_rel = qe[1] / fmax(qe[3], 1e-300);
+      int fc = 0;
+      for (int i = 0; i < c->n; ++i) fc += (hw[(size_t)q * c->n + i] - o.tau > o.eps_act);
+      inf.free_count = fc;
+      inf.batch_iters = (int32_t)guard_iters;
+    }
+  }
   return first;
 }
 

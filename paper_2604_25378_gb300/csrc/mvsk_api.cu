@@ -51,6 +51,9 @@ struct BatchBuf {
   // iteration: asynchronous copies, one synchronisation)
   int* si_h = nullptr;
   double* sd_h = nullptr;
+  int* q_si = nullptr;      // per request: the state words at its end
+  double* q_ev = nullptr;   // per request: f, KKT residual, mu^T x, kkt0
+  int qhcap = 0;
   // switch handle of the one-graph iteration (valid while has_cond is set during its capture)
   cudaGraphConditionalHandle cond = 0;
   int has_cond = 0;
@@ -1873,6 +1876,8 @@ void mvsk_destroy(mvsk_ctx* c) {
   if (c->batch.si_h != nullptr) cudaFreeHost(c->batch.si_h);
   if (c->batch.ev_h != nullptr) cudaFreeHost(c->batch.ev_h);
   if (c->batch.sd_h != nullptr) cudaFreeHost(c->batch.sd_h);
+  if (c->batch.q_si != nullptr) cudaFreeHost(c->batch.q_si);
+  if (c->batch.q_ev != nullptr) cudaFreeHost(c->batch.q_ev);
   if (c->hword != nullptr) cudaFreeHost(c->hword);
   if (c->own_stream != nullptr) cudaStreamDestroy(c->own_stream);
   delete c;
