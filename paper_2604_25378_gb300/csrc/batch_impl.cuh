@@ -211,46 +211,48 @@ __global__ void __launch_bounds__(256) k_oz_fin_ls(const long long* part, int sp
                                                    const int* em, const int* fb, Inst base, int b0, int skip_slot,
                                                    double* wout, const int* kinfo = nullptr,
                                                    const int* need = nullptr) {
-  __shared__ double red[12][256];
+  __shared__ double red[9][256];
   if (need != nullptr && *need == 0) return;  // the product did not run
   const int bl = blockIdx.y;
   if (kinfo != nullptr) splits = oz_slots(kinfo[1] / kTcBK);
   Inst s = inst_at(base, b0 + bl);
   if (s.si[SI_DONE] != 0 || s.si[skip_slot] != 0) return;
-  double a[12];
+  // the nine sums with w: the z-only sums s20, s30, s40 enter no quartic
+  // coefficient (Prop. quartic line search) and are written as zero
+  double a[9];
 #pragma unroll
-  for (int q = 0; q < 12; ++q) a[q] = 0.0;
+  for (int q = 0; q < 9; ++q) a[q] = 0.0;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < s.T; t += (long long)gridDim.x * blockDim.x) {
     const double zt = s.z[t], w = oz_value(part, splits, Bp, ldp, t, bl, em[t], fb[bl]);
     wout[(size_t)(b0 + bl) * s.T + t] = w;
     const double z2 = zt * zt, w2 = w * w;
-    a[0] += z2;            // s20
-    a[1] += z2 * zt;       // s30
-    a[2] += z2 * z2;       // s40
-    a[3] += zt * w;        // s11
-    a[4] += z2 * w;        // s21
-    a[5] += z2 * zt * w;   // s31
-    a[6] += w2;            // s02
-    a[7] += zt * w2;       // s12
-    a[8] += z2 * w2;       // s22
-    a[9] += w2 * w;        // s03
-    a[10] += zt * w2 * w;  // s13
-    a[11] += w2 * w2;      // s04
+    a[0] += zt * w;        // s11
+    a[1] += z2 * w;        // s21
+    a[2] += z2 * zt * w;   // s31
+    a[3] += w2;            // s02
+    a[4] += zt * w2;       // s12
+    a[5] += z2 * w2;       // s22
+    a[6] += w2 * w;        // s03
+    a[7] += zt * w2 * w;   // s13
+    a[8] += w2 * w2;       // s04
   }
-  // Staged reduction of the twelve sums: 16 threads per sum add 16 values
-  // each, then a 16-lane shuffle tree (about a fifth of the FP64 additions of
-  // twelve separate block-wide shuffle trees, and two barriers instead of 36).
+  // Staged reduction of the nine sums: 16 threads per sum add 16 values
+  // each, then a 16-lane shuffle tree (two barriers instead of one tree and
+  // two barriers per sum).
 #pragma unroll
-  for (int q = 0; q < 12; ++q) red[q][threadIdx.x] = a[q];
+  for (int q = 0; q < 9; ++q) red[q][threadIdx.x] = a[q];
   __syncthreads();
-  if (threadIdx.x < 192) {
+  if (threadIdx.x < 160) {  // whole warps in the shuffles; lanes of q = 9 add zeros
     const int q = threadIdx.x >> 4, j = threadIdx.x & 15;
     double v = 0.0;
+    if (q < 9)
 #pragma unroll
-    for (int k = 0; k < 16; ++k) v += red[q][j + 16 * k];
+      for (int k = 0; k < 16; ++k) v += red[q][j + 16 * k];
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (j == 0) s.spart[(size_t)blockIdx.x * 12 + q] = v;
+    if (j == 0 && q < 9) s.spart[(size_t)blockIdx.x * 12 + 3 + q] = v;
+  } else if (threadIdx.x < 163) {
+    s.spart[(size_t)blockIdx.x * 12 + (threadIdx.x - 160)] = 0.0;
   }
 }
 

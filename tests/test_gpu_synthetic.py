@@ -32,7 +32,11 @@ def test_paper_synthetic_grid_matches_oracle(n, cfg):
         assert O.kkt_residual(w, g_w, 1e-8) <= 1e-10 * inf_ref.kkt0 * 1.0001
         f_w = O.objective(A, mu, c, w)
         if O.convexity_certificate(c):
-            assert np.max(np.abs(w - x_ref)) <= 1e-8, (n, prof, np.max(np.abs(w - x_ref)))
+            # both stop at a relative KKT residual <= 1e-10; on these panels the
+            # reduced Hessian's smallest eigenvalue puts each stopping point
+            # within 1e-10 kkt0 / lambda_min <= 9.4e-11 of the minimiser
+            # (oracle-computed for every certified case of this grid)
+            assert np.max(np.abs(w - x_ref)) <= 1e-9, (n, prof, np.max(np.abs(w - x_ref)))
         assert f_w <= inf_ref.f + 1e-6 * max(1.0, abs(inf_ref.f)), (n, prof, f_w, inf_ref.f)
 
 
@@ -54,7 +58,8 @@ def test_armijo_rule_matches_oracle(n):
         w, info = ctx.solve(m.DIRECT, 1e-10)
         x_ref, inf_ref = O.solve(A, mu, c, "direct", 1e-10, opts=O.Options(line_search="armijo", max_iter=120))
         assert info["status"] == "ok" and inf_ref.status == "converged"
-        assert np.max(np.abs(w - x_ref)) <= 1e-8, (n, prof, np.max(np.abs(w - x_ref)))
+        # each stopping point within 1e-10 kkt0 / lambda_min <= 7.8e-11 of the minimiser
+        assert np.max(np.abs(w - x_ref)) <= 1e-9, (n, prof, np.max(np.abs(w - x_ref)))
 
 
 @pytest.mark.parametrize("kappa", [10.0, 1000.0])
@@ -72,4 +77,7 @@ def test_crra_conditioning_matches_oracle(kappa):
     w, info = ctx.solve(m.PCG, 1e-10)
     x_ref, inf_ref = O.solve(A, mu, c, "pcg", 1e-10)
     assert info["status"] == "ok" and inf_ref.status == "converged"
+    # ill-conditioned by construction: the reduced Hessian's smallest
+    # eigenvalue (3.5e-4 at kappa = 10, 8.7e-5 at kappa = 1000) puts a point
+    # with relative KKT residual 1e-10 up to 1.1e-9 / 4.6e-9 from the minimiser
     assert np.max(np.abs(w - x_ref)) <= 1e-8, np.max(np.abs(w - x_ref))
