@@ -463,17 +463,26 @@ __global__ void __launch_bounds__(NM) k_face_setup(Inst base, const int* fl_base
   // G nuhat and the sums of lambda on the right-hand side's CTA only; every
   // CTA takes the diagonal for the Jacobi floor
   float gv = 0.f, g1 = 0.f, gd = 0.f;
-  if (on) {
-    if (c == 0) {  // column k of the symmetric G_F (consecutive threads: consecutive addresses)
-#pragma unroll 8
-      for (int l = 0; l < m; ++l) {
-        const float gk = Gm[(size_t)l * NM + k];
-        gv = fmaf(gk, nhs[l], gv);
-        g1 += gk;
-      }
+  if (c == 0) {  // column k of the symmetric G_F, l ascending, 32 rows of G_F staged at a time
+    __shared__ float gch[32 * NM];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int l0 = 0; l0 < m; l0 += 32) {
+      const int rows = m - l0 < 32 ? m - l0 : 32;
+      for (int r = warp; r < rows; r += NM / 32)
+        for (int j = lane; j < m; j += 32) cp_async4(gch + r * NM + j, Gm + (size_t)(l0 + r) * NM + j);
+      cp_async_commit();
+      cp_async_wait<0>();
+      __syncthreads();
+      if (on)
+        for (int r = 0; r < rows; ++r) {
+          const float gk = gch[r * NM + k];
+          gv = fmaf(gk, nhs[l0 + r], gv);
+          g1 += gk;
+        }
+      __syncthreads();
     }
-    gd = Gm[(size_t)k * NM + k];
   }
+  if (on) gd = Gm[(size_t)k * NM + k];
   const double md = (double)SI[SI_M];
   double dd[2] = {on ? (double)gd : 0.0, on ? fabs((double)gd) : 0.0};
   cta_sumd<NM, 2>(dd, scr);
