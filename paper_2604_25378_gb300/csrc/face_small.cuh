@@ -12,9 +12,11 @@
 // correction a = T^-1 A_F^T (psi''' o rhat), rhat = K^-1 sum_k (A_F X_k) o
 // (A_F p_k) (Eq. operator-third), takes one more pass over A_F.  The columns
 // of A come from the union gather of the face-restricted products (BF16, the
-// precision of the other direction products).  G_F is formed on the tensor
-// cores (BF16 data, the psi''-weighted operand carried in two BF16 parts,
-// FP32 accumulation); the other sums are FP32.
+// precision of the other direction products).  G_F and the correction's two
+// contractions run on the tensor cores (BF16 data, the weighted or iterate
+// operand carried in two BF16 parts, FP32 accumulation); the PCG recurrences
+// and the set-ups are FP32 with FP64 block sums.  Two launch shapes: NM =
+// kMFt while every face has at most kMFt coordinates, NM = kMF otherwise.
 #pragma once
 
 constexpr int kMF = 320;       // largest face handled here (one coordinate per thread of a PCG CTA)
@@ -435,8 +437,8 @@ __device__ __forceinline__ float face_col_start(Inst& s, int c, bool on, int i, 
 
 // First-round setup of the small-face block, column c = blockIdx.x <= K of
 // instance blockIdx.y, one face coordinate per thread, from G_F (gram, row
-// stride NM): G nuhat, diag G, nuhat^T G nuhat and 1_F^T G 1_F (the face
-// part of k_face_gram_finish), the Jacobi floor and lambda of k_pcg_setup
+// stride NM): G nuhat, diag G, nuhat^T G nuhat and 1_F^T G 1_F, the Jacobi
+// floor and lambda of k_pcg_setup
 // (CTA 0 writes SD_LAM, diag G and the FP32 face data kf on F), and the start
 // of column c (k_probe_fill and k_pcg_setup_cols on F; probes from the same
 // counter-based generator).  Every other coordinate of these vectors is
