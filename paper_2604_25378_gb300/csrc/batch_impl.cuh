@@ -1649,9 +1649,8 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
   } else {
     TRY(capture(-1, gfull));
   }
-  // replay of one graph (profiled launches folded in after each replay)
-  // replays queue no wait: the profiled event pairs of the iteration's graphs
-  // are read after the iteration's state copy (one wait per iteration)
+  // A replay queues no wait: the profiled event pairs of the iteration's
+  // graphs are read after the iteration's state copy (one wait per iteration).
   std::vector<const ItGraph*> pend;
   auto replay = [&](ItGraph& gr) -> mvsk_status {
     CU(cudaGraphLaunch(gr.e, c->stream));
@@ -1660,7 +1659,8 @@ mvsk_status batch_solve(mvsk_ctx* c, int B, const double* lam_h, const double* t
     return MVSK_OK;
   };
   auto collect = [&]() -> mvsk_status {  // after a wait that followed the replays
-    for (const ItGraph* g : pend) TRY(prof_collect(c, g->ev_b, g->ev_e, c->prof_uinfo != nullptr ? c->hword + 2 : nullptr));
+    const int* uinfo = c->prof_uinfo != nullptr ? c->hword + 2 : nullptr;  // copied with the state
+    for (const ItGraph* g : pend) TRY(prof_collect(c, g->ev_b, g->ev_e, uinfo));
     pend.clear();
     return MVSK_OK;
   };
